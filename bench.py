@@ -1,0 +1,320 @@
+"""Benchmark of the GB300-native MDFS information-gain scan.
+
+One step = one MDFS scan job on the synthetic parity-structured data with
+Madelon's shapes (N = 2000 objects, M = 500 variables, binary decision):
+the k = 2 scan and the k = 3 scan, each over 30 random discretisations into
+2 classes (range 0.5, pseudocount xi 0.25).  The metric is unordered
+tuple x discretisation evaluations per second:
+    (C(500, 2) + C(500, 3)) * 30 = 6.249e8 evaluations per step.
+
+Default arm: inputs resident in HBM, each step timed with CUDA events on the
+launching stream, L2 flushed (512 MB write) between steps.  ``e2e`` repeats
+the steps through the C ABI with pinned host inputs and host outputs.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload (the method has no other reference implementation here).
+
+Multi-GPU (torchrun): every rank runs its own independent job (weak scaling,
+no data-path collective); value = all ranks' evaluations / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_OBJ, M_VAR, DISC, DIV, RANGE, XI = 2000, 500, 30, 1, 0.5, 0.25
+UNITS_K2 = math.comb(M_VAR, 2) * DISC
+UNITS_K3 = math.comb(M_VAR, 3) * DISC
+UNITS = UNITS_K2 + UNITS_K3
+METRIC = "k-tuple*discretization IG evals/sec (k=2,3; N=2000, M=500)"
+UNIT = "tuple*disc/s"
+WORKLOAD = "mdfs_scan_parity_N2000_M500_k2+k3_D30_c2"
+
+
+def _config(extra=None):
+    cfg = {"workload": WORKLOAD, "N": N_OBJ, "M": M_VAR, "k": [2, 3], "discretizations": DISC,
+           "divisions": DIV, "range": RANGE, "pc_xi": XI, "l2": "flushed (512 MB write) between timed steps",
+           "data": "synthetic Madelon-shaped 5-bit parity set (seeded numpy PCG64)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(n2: int, n3: int, seed: int = 11):
+    """Times the FP64 oracle on n2 variables at k=2 and n3 variables at k=3
+    (full partner scans over all 30 discretisations).  Returns
+    (unordered tuple*disc equivalents processed, seconds, threads)."""
+    import oracle
+    from paper_1811_00631_gb300 import synth
+    ds = synth.madelon_like()
+    t0 = time.perf_counter()
+    codes = oracle.discretize(ds.x, DIV, DISC, RANGE, seed)
+    if n2:
+        oracle.max_ig(codes, ds.y, DIV + 1, 2, XI, variables=np.arange(n2, dtype=np.int32))
+    if n3:
+        oracle.max_ig(codes, ds.y, DIV + 1, 3, XI, variables=np.arange(n3, dtype=np.int32))
+    dt = time.perf_counter() - t0
+    # each variable's scan covers C(M-1, k-1) * D (variable, partner set) roles;
+    # an unordered k-tuple carries k roles
+    units = n2 * (M_VAR - 1) * DISC / 2 + n3 * math.comb(M_VAR - 1, 2) * DISC / 3
+    return units, dt, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    threads = oracle.num_threads()
+    n3 = max(1, threads // 2)
+    n2 = 64
+    for _ in range(args.warmup):
+        oracle_sample(n2, 0)
+    times, units = [], 0.0
+    for _ in range(args.steps):
+        u, dt, _ = oracle_sample(n2, n3)
+        times.append(dt)
+        units += u
+    total = sum(times)
+    value = units / total
+    sample = (f"{n2} variables at k=2 and {n3} at k=3, each a full partner scan over "
+              f"{DISC} discretisations of the 2000x500 data, per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config({"oracle": "FP64 brute-force C (OpenMP)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1811_00631_gb300 import build, mdfs, synth
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ds = synth.madelon_like(seed=2 + rank)  # an independent job per rank
+    x = torch.from_numpy(ds.x).to(dev)
+    y = torch.from_numpy(ds.y).to(dev)
+    M = M_VAR
+    outs = {k: (torch.empty(M, dtype=torch.float32, device=dev), torch.empty((M, max(k - 1, 1)), dtype=torch.int32,
+                                                                              device=dev),
+                torch.empty(M, dtype=torch.int32, device=dev)) for k in (2, 3)}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    launches = [0]
+
+    def step(seed):
+        for k in (2, 3):
+            mdfs.max_ig(x, y, k, DIV, DISC, RANGE, XI, seed, out=outs[k])
+            launches[0] += mdfs.last_launch_count()
+
+    for w in range(args.warmup):
+        step(100 + w)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    mdfs.profile(True)
+    launches[0] = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step(1 + i)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = mdfs.profile_report()
+    mdfs.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * UNITS * args.steps / total_s
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    x_h = torch.empty(ds.x.shape, dtype=torch.float32, pin_memory=True)
+    x_h.copy_(torch.from_numpy(ds.x))
+    y_h = torch.empty(ds.y.shape, dtype=torch.uint8, pin_memory=True)
+    y_h.copy_(torch.from_numpy(ds.y))
+    host_out = {k: (np.empty(M, np.float32), np.empty((M, max(k - 1, 1)), np.int32), np.empty(M, np.int32))
+                for k in (2, 3)}
+    for k in (2, 3):
+        mdfs.max_ig(x_h, y_h, k, DIV, DISC, RANGE, XI, 99, out=host_out[k])
+    e2e_t = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in (2, 3):
+            mdfs.max_ig(x_h, y_h, k, DIV, DISC, RANGE, XI, 1 + i, out=host_out[k])
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = 2 * (x_h.numel() * 4 + y_h.numel())
+    d2h = sum(a.nbytes for k in (2, 3) for a in host_out[k][: 1 + (k > 1)]) + sum(host_out[k][2].nbytes for k in (2, 3))
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (k = 3 triple counting) ----
+    roof = None
+    k3 = prof.get("k3", None)
+    if k3 and k3["count"]:
+        avg_s = k3["ms"] / k3["count"] / 1e3
+        n = N_OBJ
+        # algorithmic work of one launch: every (triple, discretisation) ANDs and
+        # popcounts the (c-1)^3 plane combinations over N sample bits -> N/32 popc
+        popc = math.comb(M, 3) * DISC * DIV ** 3 * n / 32.0
+        achieved = popc / avg_s / 1e12
+        peak = float(args.popc_peak)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k3_kernel<2>", "launch_ms": 1e3 * avg_s,
+                "peak_note": "152 SM x 16 popc/clk/SM x 2.07 GHz (unit count x max clock)"}
+    shares = {}
+    tot = sum(v["ms"] for v in prof.values()) or 1.0
+    for kname, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        shares[kname] = {"launches": v["count"], "ms": round(v["ms"], 4), "share": round(v["ms"] / tot, 4)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32 counts + int64 fixed-point entropy",
+            "data": "synthetic",
+            "config": _config({"parallelism": f"independent job per GPU x{world}"}),
+            "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
+            "wall_s_timed_region": wall,
+            "gpu_launches": launches[0],
+            "clocks": clk,
+            "e2e": {"value": world * UNITS * args.steps / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roof,
+            "kernels": shares}
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        th = oracle.num_threads()
+        n3 = max(1, th // 2)
+        u, dt, th = oracle_sample(64, n3)
+        line["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": th, "kind": "oracle",
+                                "sample": f"64 variables at k=2 and {n3} at k=3, full partner scans, "
+                                          f"{DISC} discretisations, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--popc-peak", type=float, default=152 * 16 * 2.07e9 / 1e12)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return 0
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,155 @@
+/*
+ * mdfs.h -- C ABI of the GB300-native MDFS information-gain scan.
+ *
+ * MDFS (Piliszek et al., arXiv 1811.00631) ranks variables by
+ *     IG^k_max(y; x_i) = N max_S [ H(y | S) - H(y | S, x_i) ]            (Eq. 1)
+ * where S runs over all (k-1)-subsets of the other variables and, in
+ * addition, over several random discretisations of the data (section
+ * "Algorithm and implementation").  This library computes that scan on one
+ * GPU (sm_103a) for k = 1..3 and fits the chi^2 / extreme-value null that
+ * turns the result into p-values (section "Theory").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers: every array argument may be a host pointer or a device pointer of
+ *   the current CUDA device; the library tells them apart with
+ *   cudaPointerGetAttributes.  Host inputs are copied to the device inside the
+ *   call; host outputs are written before the call returns.  All outputs are
+ *   owned by the caller.  The library keeps only a cached device workspace per
+ *   (device, stream), which mdfs_release() frees.
+ * Layout: x is variable-major, x[v * N + s] is sample s of variable v
+ *   (an N x M column-major matrix with leading dimension N).
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  A
+ *   call with device outputs is stream-ordered on `stream` but waits once for
+ *   the 16-byte validation result of its inputs; a call with host outputs, or
+ *   with stream == NULL, returns after its results are complete.  Calls on
+ *   different streams may run concurrently; calls sharing one stream from
+ *   several host threads must be serialised by the caller.
+ * Errors: 0 on success, a negative MDFS_E* code otherwise; mdfs_last_error()
+ *   then describes the failure (thread-local string).  On error no output is
+ *   guaranteed to have been written.
+ * Limits: 1 <= divisions <= 3 (c = divisions + 1 classes per variable,
+ *   section "Algorithm and implementation": the same c for all variables);
+ *   2 <= c <= N <= 32768; 1 <= discretizations <= 1024; k <= M <= 65535;
+ *   for k = 2, discretizations * M < 2^32; for k = 3,
+ *   discretizations * M * M < 2^32.
+ */
+#ifndef MDFS_H
+#define MDFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define MDFS_OK 0
+#define MDFS_EINVAL (-1)      /* argument out of range, or y not in {0, 1}           */
+#define MDFS_EDEGENERATE (-2) /* one decision class is empty (Eq. beta undefined)    */
+#define MDFS_ENONFINITE (-3)  /* x holds NaN or +-Inf                                 */
+#define MDFS_ENOMEM (-4)      /* device workspace allocation failed                   */
+#define MDFS_ECUDA (-5)       /* a CUDA runtime call or kernel launch failed          */
+#define MDFS_ETIMEOUT (-6)    /* reserved for bounded device-side waits               */
+
+/* x element types */
+#define MDFS_F32 0
+#define MDFS_I8 1
+
+typedef struct mdfs_data {
+    int dtype;          /* MDFS_F32 or MDFS_I8                                       */
+    const void* x;      /* [M][N] variable-major data, host or device               */
+    const uint8_t* y;   /* [N] binary decision in {0, 1}, host or device (section
+                           "Algorithm and implementation": binary decisions only);
+                           may be NULL for mdfs_discretize                          */
+    int N;              /* number of objects (samples)                              */
+    int M;              /* number of variables                                      */
+} mdfs_data;
+
+/*
+ * Randomised rank-based discretisation (section "Algorithm and
+ * implementation").  For each variable v and discretisation d the c class
+ * shares are drawn uniformly from [1-range, 1+range) (Philox4x32-10, key =
+ * seed, counter = (j/4, v, d, 0x4D444653), 20-bit fixed point), turned into
+ * c-1 strictly increasing 0-based positions in [1, N-1] of the sorted
+ * variable, and the values at those positions become the thresholds t_j;
+ * code(x) = #{ j : x >= t_j } (ties go to the upper class).
+ *
+ * codes: [discretizations][M][N] uint8, caller-owned, host or device.
+ * range: 0 (equipotent split) .. 1 (completely random split).
+ */
+int mdfs_discretize(const mdfs_data* data, int divisions, int discretizations, double range,
+                    uint64_t seed, uint8_t* codes, void* stream);
+
+/*
+ * IG^k_max (Eq. 1; Eq. 3 for k = 1), maximised over all (k-1)-subsets S of
+ * the other variables and over all discretisations.  Entropies are the
+ * pseudocount-regularised, N-scaled conditional entropies of Eqs. H, p and
+ * beta, in nats:
+ *     SH(S) = sum_v [ f(n_v + b0 + b1) - f(n0_v + b0) - f(n1_v + b1) ],
+ *     f(t) = t ln t,  b^d = pc_xi * N^d / min(N^0, N^1),
+ * summed over all c^|S| voxels v, and IG(i | S) = SH(S) - SH(S + {i}).
+ *
+ * k:          1, 2 or 3.
+ * pc_xi:      the pseudocount parameter xi, 0 < pc_xi < 1.
+ * ig:         [M] float, the maximum per variable (may be slightly negative
+ *             when the pseudocounts dominate).
+ * tuples:     [M][k-1] int32 or NULL: the partner set of the maximum in
+ *             ascending order (ignored for k = 1).
+ * best_disc:  [M] int32 or NULL: the discretisation of the maximum.
+ * Ties are broken towards the lowest (discretisation, lexicographic S).
+ * The discretisation is the one mdfs_discretize produces for the same seed.
+ */
+int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations, double range,
+                double pc_xi, uint64_t seed, float* ig, int32_t* tuples, int32_t* best_disc,
+                void* stream);
+
+/*
+ * Significance of IG^k_max (section "Theory"): a single tuple's 2 IG is
+ * chi^2 with df = (c-1) c^(k-1) degrees of freedom; the maximum over T
+ * effective tests has CDF F_df(2 g)^T.  T is fitted by maximum likelihood on
+ * the irrelevant variables (T = -n / sum ln F_df(2 IG_i); variables with
+ * IG <= 0 carry no likelihood term), then
+ *     p_i    = 1 - F_df(2 IG_i)^T,
+ *     IG_lim = F_df^{-1}((1 - alpha)^(1/T)) / 2.
+ * Runs in FP64 on the device.
+ *
+ * ig:               [M] float, host or device (an mdfs_max_ig result).
+ * discretizations:  recorded only; the fit absorbs it into T.
+ * irrelevant_mask:  [M] uint8 or NULL (NULL = every variable is used).
+ * p_values:         [M] double, host or device.
+ * ig_lim, n_eff:    one double each, host or device (n_eff = fitted T).
+ * Returns MDFS_EDEGENERATE when no variable contributes to the fit.
+ */
+int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretizations,
+                const uint8_t* irrelevant_mask, double alpha, double* p_values, double* ig_lim,
+                double* n_eff, void* stream);
+
+/* Thread-local description of the last failure of this thread ("" if none). */
+const char* mdfs_last_error(void);
+
+/* Frees every cached device workspace of this process.  No call may be in
+ * flight.  Returns 0. */
+int mdfs_release(void);
+
+/* ABI version, currently 1. */
+int mdfs_abi_version(void);
+
+/* Tracing: while enabled (enable != 0), every kernel launch of the library is
+ * bracketed by CUDA events on its stream.  Process-wide switch; returns 0. */
+int mdfs_profile(int enable);
+
+/* Writes one line "name launches total_ms" per kernel recorded since the last
+ * report into buf (len bytes, NUL-terminated), waiting for the events, and
+ * clears the record.  Returns MDFS_EINVAL if the text was truncated. */
+int mdfs_profile_report(char* buf, int len);
+
+/* Diagnostic: number of kernels the calling thread's most recent mdfs_* call
+ * launched (0 if it failed before its first launch). */
+int mdfs_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDFS_H */

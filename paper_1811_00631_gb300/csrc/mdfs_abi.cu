@@ -1,0 +1,521 @@
+// Host side of the MDFS C ABI (include/mdfs.h): argument checks, input staging,
+// per-(device, stream) workspaces and the launch sequence of the scan.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mdfs.h"
+#include "mdfs_internal.cuh"
+
+using namespace mdfs;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int g_launches = 0;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+struct Buffer {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct Workspace {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Buffer x, y, stats, perm, tab, planes, cnt1, sh1, keys, sh2, cnt2, items, ig, tuples, disc, codes, mask, pv, res;
+    int* host_stats = nullptr;  // pinned, 16 ints
+    double* host_res = nullptr; // pinned, 4 doubles
+    int items_M = -1, items_c = -1, n_items = 0;
+
+    ~Workspace() {
+        Buffer* all[] = {&x, &y, &stats, &perm, &tab, &planes, &cnt1, &sh1, &keys, &sh2,
+                         &cnt2, &items, &ig, &tuples, &disc, &codes, &mask, &pv, &res};
+        for (Buffer* b : all)
+            if (b->p) cudaFree(b->p);
+        if (host_stats) cudaFreeHost(host_stats);
+        if (host_res) cudaFreeHost(host_res);
+    }
+
+    // Grows a buffer to at least `bytes`; waits for the stream before freeing.
+    bool ensure(Buffer& b, size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        if (b.cap >= bytes) return true;
+        if (b.p) {
+            cudaStreamSynchronize(stream);
+            cudaFree(b.p);
+            b.p = nullptr;
+            b.cap = 0;
+        }
+        size_t want = bytes + bytes / 8;
+        if (cudaMalloc(&b.p, want) != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return false;
+        }
+        b.cap = want;
+        return true;
+    }
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, std::unique_ptr<Workspace>> g_ws;
+
+Workspace* get_ws(cudaStream_t st, int* err) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        *err = fail(MDFS_ECUDA, "no CUDA device is available");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto key = std::make_pair(dev, st);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) return it->second.get();
+    std::unique_ptr<Workspace> ws(new Workspace());
+    ws->device = dev;
+    ws->stream = st;
+    if (cudaMallocHost(&ws->host_stats, 16 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ws->host_res, 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        *err = fail(MDFS_ENOMEM, "pinned host staging allocation failed");
+        return nullptr;
+    }
+    Workspace* raw = ws.get();
+    g_ws[key] = std::move(ws);
+    return raw;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define MDFS_CUDA_TRY(expr)                                                                         \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess) return fail(MDFS_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e));     \
+    } while (0)
+
+// ---- optional per-kernel CUDA-event timing (mdfs_profile) -------------------
+struct ProfRec {
+    const char* name;
+    cudaEvent_t ev0, ev1;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_pool;
+
+cudaEvent_t prof_event() {
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+#define MDFS_LAUNCH(name, stream, expr)                                                             \
+    do {                                                                                            \
+        ++g_launches;                                                                               \
+        cudaEvent_t _e0 = nullptr, _e1 = nullptr;                                                   \
+        bool _prof;                                                                                 \
+        {                                                                                           \
+            std::lock_guard<std::mutex> _l(g_prof_mu);                                              \
+            _prof = g_prof_on;                                                                      \
+            if (_prof) {                                                                            \
+                _e0 = prof_event();                                                                 \
+                _e1 = prof_event();                                                                 \
+            }                                                                                       \
+        }                                                                                           \
+        if (_prof) cudaEventRecord(_e0, (stream));                                                  \
+        cudaError_t _e = (expr);                                                                    \
+        if (_prof) {                                                                                \
+            cudaEventRecord(_e1, (stream));                                                         \
+            std::lock_guard<std::mutex> _l(g_prof_mu);                                              \
+            g_prof_recs.push_back(ProfRec{(name), _e0, _e1});                                       \
+        }                                                                                           \
+        if (_e != cudaSuccess) return fail(MDFS_ECUDA, "%s: %s", #expr, cudaGetErrorString(_e));     \
+    } while (0)
+
+#define MDFS_ENSURE(ws, buf, bytes)                                                                 \
+    do {                                                                                            \
+        if (!(ws)->ensure((ws)->buf, (bytes)))                                                      \
+            return fail(MDFS_ENOMEM, "device allocation of %zu bytes failed", (size_t)(bytes));      \
+    } while (0)
+
+int check_data(const mdfs_data* data, bool need_y) {
+    if (!data) return fail(MDFS_EINVAL, "data is NULL");
+    if (data->dtype != MDFS_F32 && data->dtype != MDFS_I8) return fail(MDFS_EINVAL, "dtype must be MDFS_F32 or MDFS_I8");
+    if (!data->x) return fail(MDFS_EINVAL, "x is NULL");
+    if (need_y && !data->y) return fail(MDFS_EINVAL, "y is NULL");
+    if (data->N < 2 || data->N > kMaxN) return fail(MDFS_EINVAL, "N = %d outside [2, %d]", data->N, kMaxN);
+    if (data->M < 1 || data->M > 65535) return fail(MDFS_EINVAL, "M = %d outside [1, 65535]", data->M);
+    return MDFS_OK;
+}
+
+// Stages x (and y) on the device and runs the validation kernels.  On success
+// *n1 is the number of class-1 objects and ws->perm holds the class-sorted order.
+int stage_inputs(Workspace* ws, const mdfs_data* data, bool need_y, const void** xd, const uint8_t** yd, int* n1) {
+    cudaStream_t st = ws->stream;
+    const size_t xbytes = (size_t)data->M * data->N * (data->dtype == MDFS_F32 ? 4 : 1);
+    *xd = data->x;
+    if (!is_device_ptr(data->x)) {
+        MDFS_ENSURE(ws, x, xbytes);
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->x.p, data->x, xbytes, cudaMemcpyHostToDevice, st));
+        *xd = ws->x.p;
+    }
+    MDFS_ENSURE(ws, stats, 16 * sizeof(int));
+    MDFS_CUDA_TRY(cudaMemsetAsync(ws->stats.p, 0, 16 * sizeof(int), st));
+    int* stats = (int*)ws->stats.p;
+    if (need_y) {
+        *yd = data->y;
+        if (!is_device_ptr(data->y)) {
+            MDFS_ENSURE(ws, y, (size_t)data->N);
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->y.p, data->y, (size_t)data->N, cudaMemcpyHostToDevice, st));
+            *yd = (const uint8_t*)ws->y.p;
+        }
+        MDFS_ENSURE(ws, perm, (size_t)data->N * sizeof(int));
+        MDFS_LAUNCH("stats", st, launch_stats(*yd, data->N, stats, (int*)ws->perm.p, st));
+    }
+    if (data->dtype == MDFS_F32)
+        MDFS_LAUNCH("check_finite", st, launch_check_finite((const float*)*xd, (long long)data->M * data->N, stats + 2, st));
+    MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats, stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    const int* hs = ws->host_stats;
+    if (hs[2] != 0) return fail(MDFS_ENONFINITE, "x holds NaN or Inf values");
+    if (need_y) {
+        if (hs[1] != 0) return fail(MDFS_EINVAL, "y holds %d values outside {0, 1}", hs[1]);
+        *n1 = hs[0];
+        if (*n1 == 0 || *n1 == data->N)
+            return fail(MDFS_EDEGENERATE, "decision has a single class (N0 = %d, N1 = %d)", data->N - *n1, *n1);
+    }
+    return MDFS_OK;
+}
+
+// Output target: the caller's device pointer, or a staging buffer copied back later.
+template <typename T>
+struct Out {
+    T* user = nullptr;
+    T* dev = nullptr;
+    size_t bytes = 0;
+    bool staged = false;
+};
+
+template <typename T>
+int bind_out(Workspace* ws, Buffer& buf, T* user, size_t count, Out<T>* o) {
+    o->user = user;
+    o->bytes = count * sizeof(T);
+    if (!user) return MDFS_OK;
+    if (is_device_ptr(user)) {
+        o->dev = user;
+        return MDFS_OK;
+    }
+    if (!ws->ensure(buf, o->bytes)) return fail(MDFS_ENOMEM, "device allocation of %zu bytes failed", o->bytes);
+    o->dev = (T*)buf.p;
+    o->staged = true;
+    return MDFS_OK;
+}
+
+template <typename T>
+int copy_back(Workspace* ws, const Out<T>& o) {
+    if (o.staged) MDFS_CUDA_TRY(cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, ws->stream));
+    return MDFS_OK;
+}
+
+void build_k3_items(int M, int c, std::vector<int2>& items) {
+    const int TB = k3_tile_b(c), TE = k3_tile_e(c);
+    items.clear();
+    for (int a = 0; a + 2 < M; ++a) {
+        const int L = M - 1 - a;
+        const int nbt = (L + TB - 1) / TB, net = (L + TE - 1) / TE;
+        for (int tb = 0; tb < nbt; ++tb) {
+            const int bmin = a + 1 + tb * TB;
+            if (bmin > M - 2) break;
+            for (int te = 0; te < net; ++te) {
+                const int emin = a + 1 + te * TE;
+                if (emin > M - 1) break;
+                const int emax = std::min(emin + TE - 1, M - 1);
+                if (emax <= bmin) continue;
+                items.push_back(make_int2(a, (tb << 16) | te));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdfs_abi_version(void) { return 1; }
+
+const char* mdfs_last_error(void) { return g_err.c_str(); }
+
+int mdfs_last_launch_count(void) { return g_launches; }
+
+int mdfs_profile(int enable) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof_on = enable != 0;
+    return MDFS_OK;
+}
+
+int mdfs_profile_report(char* buf, int len) {
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        recs.swap(g_prof_recs);
+    }
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int> cnt;
+    int rc = MDFS_OK;
+    for (const ProfRec& r : recs) {
+        float t = 0.0f;
+        if (cudaEventSynchronize(r.ev1) != cudaSuccess || cudaEventElapsedTime(&t, r.ev0, r.ev1) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(MDFS_ECUDA, "profile event query failed");
+            continue;
+        }
+        size_t j = 0;
+        while (j < names.size() && names[j] != r.name) ++j;
+        if (j == names.size()) {
+            names.push_back(r.name);
+            ms.push_back(0.0);
+            cnt.push_back(0);
+        }
+        ms[j] += t;
+        cnt[j] += 1;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        for (const ProfRec& r : recs) {
+            g_prof_pool.push_back(r.ev0);
+            g_prof_pool.push_back(r.ev1);
+        }
+    }
+    std::string out;
+    char line[160];
+    for (size_t j = 0; j < names.size(); ++j) {
+        snprintf(line, sizeof line, "%s %d %.6f\n", names[j].c_str(), cnt[j], ms[j]);
+        out += line;
+    }
+    if (buf && len > 0) {
+        strncpy(buf, out.c_str(), (size_t)len - 1);
+        buf[len - 1] = 0;
+    }
+    if (rc == MDFS_OK && (int)out.size() >= len) rc = fail(MDFS_EINVAL, "report truncated (%zu bytes)", out.size());
+    return rc;
+}
+
+int mdfs_release(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_ws.clear();
+    return MDFS_OK;
+}
+
+int mdfs_discretize(const mdfs_data* data, int divisions, int discretizations, double range, uint64_t seed,
+                    uint8_t* codes, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, false);
+    if (rc) return rc;
+    const int c = divisions + 1;
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (data->N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", data->N, c);
+    if (discretizations < 1 || discretizations > kMaxD)
+        return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", discretizations, kMaxD);
+    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
+    if (!codes) return fail(MDFS_EINVAL, "codes is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    rc = stage_inputs(ws, data, false, &xd, &yd, &n1);
+    if (rc) return rc;
+    Out<uint8_t> oc;
+    rc = bind_out(ws, ws->codes, codes, (size_t)discretizations * data->M * data->N, &oc);
+    if (rc) return rc;
+    PlaneGeom g = make_geom(data->N, data->N);
+    MDFS_LAUNCH("discretize", st, launch_discretize(xd, data->dtype, data->N, data->M, c, discretizations, range, seed, nullptr, g,
+                                  nullptr, oc.dev, nullptr, st));
+    rc = copy_back(ws, oc);
+    if (rc) return rc;
+    if (oc.staged || st == nullptr) MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations, double range, double pc_xi,
+                uint64_t seed, float* ig, int32_t* tuples, int32_t* best_disc, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, true);
+    if (rc) return rc;
+    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    if (k < 1 || k > 3) return fail(MDFS_EINVAL, "k = %d outside [1, 3]", k);
+    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
+    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
+    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
+    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if (!ig) return fail(MDFS_EINVAL, "ig is NULL");
+    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
+    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    rc = stage_inputs(ws, data, true, &xd, &yd, &n1);
+    if (rc) return rc;
+    const int n0 = N - n1;
+    const double mn = (double)(n0 < n1 ? n0 : n1);
+    const double b0 = pc_xi * n0 / mn, b1 = pc_xi * n1 / mn;
+    const PlaneGeom g = make_geom(N, n0);
+    const int P = c - 1;
+
+    MDFS_ENSURE(ws, tab, (size_t)3 * (N + 1) * sizeof(long long));
+    MDFS_ENSURE(ws, planes, (size_t)D * M * P * g.Ws * sizeof(uint32_t));
+    MDFS_ENSURE(ws, cnt1, (size_t)D * M * P * 2 * sizeof(int));
+    MDFS_ENSURE(ws, sh1, (size_t)D * M * sizeof(long long));
+    MDFS_ENSURE(ws, keys, (size_t)M * sizeof(unsigned long long));
+    long long* tab = (long long*)ws->tab.p;
+    uint32_t* planes = (uint32_t*)ws->planes.p;
+    int* cnt1 = (int*)ws->cnt1.p;
+    long long* sh1 = (long long*)ws->sh1.p;
+    unsigned long long* keys = (unsigned long long*)ws->keys.p;
+
+    MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
+    MDFS_LAUNCH("discretize", st, launch_discretize(xd, data->dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g, planes, nullptr,
+                                  nullptr, st));
+    MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
+    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
+    if (k == 2) {
+        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, st));
+    } else if (k == 3) {
+        const size_t per_disc = (size_t)M * M * (sizeof(long long) + (size_t)P * P * 2 * sizeof(int));
+        size_t budget = (size_t)4 << 30;
+        if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
+        int nd = (int)(budget / per_disc);
+        if (nd < 1) nd = 1;
+        if (nd > D) nd = D;
+        MDFS_ENSURE(ws, sh2, (size_t)nd * M * M * sizeof(long long));
+        MDFS_ENSURE(ws, cnt2, (size_t)nd * M * M * P * P * 2 * sizeof(int));
+        if (ws->items_M != M || ws->items_c != c) {
+            std::vector<int2> items;
+            build_k3_items(M, c, items);
+            MDFS_ENSURE(ws, items, items.size() * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items_M = M;
+            ws->items_c = c;
+            ws->n_items = (int)items.size();
+        }
+        for (int d0 = 0; d0 < D; d0 += nd) {
+            const int nn = std::min(nd, D - d0);
+            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, (long long*)ws->sh2.p,
+                                  (int*)ws->cnt2.p, st));
+            MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p, ws->n_items, tab, cnt1,
+                                        (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
+        }
+    }
+
+    Out<float> oig;
+    Out<int32_t> otu, odi;
+    rc = bind_out(ws, ws->ig, ig, (size_t)M, &oig);
+    if (rc) return rc;
+    rc = bind_out(ws, ws->tuples, k > 1 ? tuples : (int32_t*)nullptr, (size_t)M * (k > 1 ? k - 1 : 1), &otu);
+    if (rc) return rc;
+    rc = bind_out(ws, ws->disc, best_disc, (size_t)M, &odi);
+    if (rc) return rc;
+    MDFS_LAUNCH("finalize", st, launch_finalize(keys, M, k, oig.dev, otu.dev, odi.dev, st));
+    if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
+    if (oig.staged || otu.staged || odi.staged || st == nullptr) MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretizations, const uint8_t* irrelevant_mask,
+                double alpha, double* p_values, double* ig_lim, double* n_eff, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    (void)discretizations;
+    if (!ig || !p_values) return fail(MDFS_EINVAL, "ig and p_values must not be NULL");
+    if (M < 1) return fail(MDFS_EINVAL, "M = %d < 1", M);
+    if (k < 1 || k > 3) return fail(MDFS_EINVAL, "k = %d outside [1, 3]", k);
+    const int c = divisions + 1;
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(MDFS_EINVAL, "alpha must lie in (0, 1)");
+    int df = c - 1;
+    for (int j = 1; j < k; ++j) df *= c;
+    int rc = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const float* igd = ig;
+    if (!is_device_ptr(ig)) {
+        MDFS_ENSURE(ws, ig, (size_t)M * sizeof(float));
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->ig.p, ig, (size_t)M * sizeof(float), cudaMemcpyHostToDevice, st));
+        igd = (const float*)ws->ig.p;
+    }
+    const uint8_t* maskd = irrelevant_mask;
+    if (irrelevant_mask && !is_device_ptr(irrelevant_mask)) {
+        MDFS_ENSURE(ws, mask, (size_t)M);
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->mask.p, irrelevant_mask, (size_t)M, cudaMemcpyHostToDevice, st));
+        maskd = (const uint8_t*)ws->mask.p;
+    }
+    Out<double> op;
+    rc = bind_out(ws, ws->pv, p_values, (size_t)M, &op);
+    if (rc) return rc;
+    MDFS_ENSURE(ws, res, 4 * sizeof(double));
+    double* res = (double*)ws->res.p;
+    MDFS_CUDA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(double), st));
+    MDFS_LAUNCH("ig_lim", st, launch_ig_lim(igd, M, df, maskd, alpha, op.dev, res, st));
+    MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_res, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(ws->host_res[2] > 0.0) || !(ws->host_res[1] > 0.0))
+        return fail(MDFS_EDEGENERATE, "no variable with IG > 0 in the fitted set");
+    rc = copy_back(ws, op);
+    if (rc) return rc;
+    if (ig_lim) {
+        if (is_device_ptr(ig_lim)) MDFS_CUDA_TRY(cudaMemcpyAsync(ig_lim, res, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        else *ig_lim = ws->host_res[0];
+    }
+    if (n_eff) {
+        if (is_device_ptr(n_eff)) MDFS_CUDA_TRY(cudaMemcpyAsync(n_eff, res + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        else *n_eff = ws->host_res[1];
+    }
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Device helpers of the MDFS kernels: Philox4x32-10, max/argmax keys, entropy tables.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdfs {
+
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
+// ten rounds of two 32x32->64 multiplications with the published multipliers
+// and Weyl key schedule.
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// Order-preserving map of an IEEE float to uint32 (larger float -> larger key).
+__device__ __forceinline__ uint32_t float_order_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_bits_float(uint32_t o) {
+    const uint32_t b = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+    return __uint_as_float(b);
+}
+
+// Packed max/argmax key: high word = ordered IG, low word = ~index, so that a
+// larger key is a larger IG and, on an exact tie, a smaller index.
+__device__ __forceinline__ unsigned long long pack_key(float ig, uint32_t index) {
+    return ((unsigned long long)float_order_bits(ig) << 32) | (unsigned long long)(~index);
+}
+
+// Fixed-point IG (multiples of 2^-32) to float with a single rounding.
+__device__ __forceinline__ float fx_to_float(long long v) {
+    return __ll2float_rn(v) * 2.3283064365386963e-10f;  // exact scaling by 2^-32
+}
+
+// Counts index the [0, n] tables; a count outside that range cannot arise from
+// consistent inputs, and clamping keeps every table read inside its buffer.
+__device__ __forceinline__ int clamp_count(int v, int n) { return min(max(v, 0), n); }
+
+// Regularised voxel entropy h(n0, n1) = f(n0+n1+b0+b1) - f(n0+b0) - f(n1+b1)
+// from the [3][N+1] fixed-point tables.
+__device__ __forceinline__ long long voxel_h(const long long* __restrict__ tab, int np1, int n0, int n1) {
+    const int n = np1 - 1;
+    n0 = clamp_count(n0, n);
+    n1 = clamp_count(n1, n);
+    return __ldg(tab + 2 * np1 + clamp_count(n0 + n1, n)) - __ldg(tab + n0) - __ldg(tab + np1 + n1);
+}
+
+}  // namespace mdfs

@@ -1,0 +1,86 @@
+// Internal declarations shared by the CUDA translation units of the MDFS library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdfs {
+
+// Fixed-point scale of the entropy tables: values are int64 multiples of 2^-32.
+// Integer accumulation makes every SH sum exact and order-independent; the only
+// rounding is one 2^-33 per table entry (tables are built in FP64).
+constexpr double kFxScale = 4294967296.0;  // 2^32
+constexpr int kMaxC = 4;                   // classes per variable (divisions <= 3)
+constexpr int kMaxN = 32768;               // samples (bounded by the in-CTA sort)
+constexpr int kMaxD = 1024;                // discretisations
+constexpr uint32_t kPhiloxTag = 0x4D444653u;  // 'MDFS', fourth counter word
+
+// Geometry of the class-sorted bit planes: class-0 samples occupy words
+// [0, W0), class-1 samples words [W0, W0 + W1); rows are padded to Ws words
+// (a multiple of 4) with zero words.
+struct PlaneGeom {
+    int N, N0, N1;
+    int W0, W1, W, Ws;
+};
+
+inline PlaneGeom make_geom(int N, int N0) {
+    PlaneGeom g;
+    g.N = N;
+    g.N0 = N0;
+    g.N1 = N - N0;
+    g.W0 = (g.N0 + 31) / 32;
+    g.W1 = (g.N1 + 31) / 32;
+    g.W = g.W0 + g.W1;
+    g.Ws = (g.W + 3) & ~3;
+    return g;
+}
+
+// ---- launchers (all asynchronous on `st`) -----------------------------------
+// stats[0] = N1 (count of y == 1), stats[1] = number of y not in {0,1},
+// stats[2] = number of non-finite x.  perm = class-stable sample order.
+cudaError_t launch_stats(const uint8_t* y, int N, int* stats, int* perm, cudaStream_t st);
+cudaError_t launch_check_finite(const float* x, long long count, int* flag, cudaStream_t st);
+
+// int64 fixed-point tables T0[n] = f(n + b0), T1[n] = f(n + b1), TB[n] = f(n + b0 + b1),
+// n = 0..N, f(t) = t ln t; laid out as [3][N + 1].
+cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStream_t st);
+
+// One CTA per variable: sort, thresholds, and codes and/or class-sorted bit planes.
+// planes: [D][M][c-1][Ws] u32 (NULL = skip); codes: [D][M][N] u8 (NULL = skip);
+// thr: [D][M][c-1] f32 (NULL = skip).
+cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
+                              uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
+                              uint8_t* codes, float* thr, cudaStream_t st);
+
+// Per (disc, variable): class counts of bins 1..c-1 -> cnt1 [D][M][c-1][2] i32,
+// SH1 [D][M] i64.  If keys != NULL also folds IG^1 = SH0 - SH1 into keys.
+cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, const long long* tab,
+                      int* cnt1, long long* sh1, unsigned long long* keys, cudaStream_t st);
+
+// Pair pass over discretisations [d0, d0 + nd).  keys != NULL: fold the two IG
+// roles of every pair into keys (k = 2).  sh2/cnt2 != NULL: store the pair
+// tables (k = 3): sh2 [nd][M][M] i64, cnt2 [nd][M][M][(c-1)^2][2] i32 (i < m only).
+cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd,
+                      const long long* tab, const int* cnt1, const long long* sh1,
+                      unsigned long long* keys, long long* sh2, int* cnt2, cudaStream_t st);
+
+// Triple pass over discretisations [d0, d0 + nd), using the pair tables of the
+// same chunk.  Folds the three IG roles of every triple into keys.  items[j] =
+// (a, tb << 16 | te): one variable a, a tile tb of b (k3_tile_b(c) variables
+// starting at a + 1 + tb * tile) and a tile te of e (k3_tile_e(c) variables).
+int k3_tile_b(int c);
+int k3_tile_e(int c);
+cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, int d0, int nd, const int2* items,
+                            int n_items, const long long* tab, const int* cnt1, const long long* sh2,
+                            const int* cnt2, unsigned long long* keys, cudaStream_t st);
+
+// keys [M] -> ig [M] f32, tuples [M][k-1] i32 (NULL ok), disc [M] i32 (NULL ok).
+cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,
+                            int* disc, cudaStream_t st);
+
+// chi^2 / extreme-value fit in FP64 (one CTA).  res[0] = IG_lim, res[1] = T,
+// res[2] = number of variables in the fit.
+cudaError_t launch_ig_lim(const float* ig, int M, int df, const uint8_t* mask, double alpha,
+                          double* p_values, double* res, cudaStream_t st);
+
+}  // namespace mdfs

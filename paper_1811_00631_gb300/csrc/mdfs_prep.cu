@@ -1,0 +1,258 @@
+// Input staging kernels of the MDFS scan: decision statistics and class-sorted
+// sample order, the fixed-point entropy tables (Eqs. H, p, beta) and the
+// randomised rank-based discretiser (section "Algorithm and implementation").
+#include <math.h>
+
+#include "mdfs_device.cuh"
+#include "mdfs_internal.cuh"
+
+namespace mdfs {
+
+// ---------------------------------------------------------------------------
+// Decision statistics and the class-stable sample permutation (one CTA).
+// perm[0 .. N0) = indices with y == 0 in ascending order, perm[N0 .. N) = the
+// indices with y == 1 in ascending order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) stats_kernel(const uint8_t* __restrict__ y, int N,
+                                                     int* __restrict__ stats, int* __restrict__ perm) {
+    __shared__ int warp_sum[32];
+    __shared__ int warp_bad[32];
+    __shared__ int s_n1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+
+    // pass 1: count ones and invalid labels
+    int ones = 0, bad = 0;
+    for (int s = tid; s < N; s += blockDim.x) {
+        const int v = y[s];
+        ones += (v == 1);
+        bad += (v > 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ones += __shfl_xor_sync(0xffffffffu, ones, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+        warp_sum[warp] = ones;
+        warp_bad[warp] = bad;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int t1 = 0, tb = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            t1 += warp_sum[w];
+            tb += warp_bad[w];
+        }
+        s_n1 = t1;
+        stats[0] = t1;
+        stats[1] = tb;
+    }
+    __syncthreads();
+    const int n0 = N - s_n1;
+
+    // pass 2: stable scatter, one block-wide exclusive scan per chunk
+    int base0 = 0, base1 = n0;
+    for (int chunk = 0; chunk < N; chunk += blockDim.x) {
+        const int s = chunk + tid;
+        const int is1 = (s < N) ? (y[s] == 1) : 0;
+        const int is0 = (s < N) ? (1 - is1) : 0;
+        const unsigned b1 = __ballot_sync(0xffffffffu, is1);
+        const unsigned b0 = __ballot_sync(0xffffffffu, is0);
+        const unsigned lt = (1u << lane) - 1u;
+        const int pre1 = __popc(b1 & lt), pre0 = __popc(b0 & lt);
+        __syncthreads();
+        if (lane == 0) {
+            warp_sum[warp] = __popc(b0);
+            warp_bad[warp] = __popc(b1);
+        }
+        __syncthreads();
+        int off0 = 0, off1 = 0, tot0 = 0, tot1 = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            const int c0 = warp_sum[w], c1 = warp_bad[w];
+            if (w < warp) {
+                off0 += c0;
+                off1 += c1;
+            }
+            tot0 += c0;
+            tot1 += c1;
+        }
+        if (is0) perm[base0 + off0 + pre0] = s;
+        if (is1) perm[base1 + off1 + pre1] = s;
+        base0 += tot0;
+        base1 += tot1;
+    }
+}
+
+cudaError_t launch_stats(const uint8_t* y, int N, int* stats, int* perm, cudaStream_t st) {
+    stats_kernel<<<1, 1024, 0, st>>>(y, N, stats, perm);
+    return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const float* __restrict__ x, long long count, int* __restrict__ flag) {
+    int bad = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        bad |= !isfinite(x[i]);
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicAdd(flag, 1);
+}
+
+cudaError_t launch_check_finite(const float* x, long long count, int* flag, cudaStream_t st) {
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    check_finite_kernel<<<(int)blocks, 256, 0, st>>>(x, count, flag);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Entropy tables (Eqs. H, p, beta).  f(t) = t ln t in FP64, stored as int64
+// multiples of 2^-32 (round to nearest).
+// ---------------------------------------------------------------------------
+__global__ void ftable_kernel(int N, double b0, double b1, long long* __restrict__ tab) {
+    const int np1 = N + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * np1) return;
+    const int which = i / np1, n = i - which * np1;
+    const double beta = which == 0 ? b0 : (which == 1 ? b1 : b0 + b1);
+    const double t = (double)n + beta;
+    const double f = t > 0.0 ? t * log(t) : 0.0;
+    tab[i] = __double2ll_rn(f * kFxScale);
+}
+
+cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStream_t st) {
+    const int total = 3 * (N + 1);
+    ftable_kernel<<<(total + 255) / 256, 256, 0, st>>>(N, b0, b1, tab);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Discretiser: one CTA per variable.
+//   1. bitonic sort of the column in shared memory (padded with +inf),
+//   2. per discretisation: c Philox shares -> c-1 cut positions -> thresholds,
+//   3. codes (original sample order) and/or bit planes of bins 1..c-1 in the
+//      class-sorted sample order (one ballot per 32 samples).
+// Share j of (v, d): w_j = W - R + floor(u_j * 2R / 2^32), W = 2^20,
+// R = round(range * 2^20), u_j = word j%4 of Philox(counter (j/4, v, d, tag),
+// key = seed).  Positions p_j = floor(N S_j / S_c) with S_j = w_0 + .. + w_{j-1},
+// clamped to [j, N-c+j] and made strictly increasing.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x, int N, int M, int c, int D,
+                                                         uint32_t R, uint32_t key0, uint32_t key1, int npad,
+                                                         const int* __restrict__ perm, PlaneGeom g,
+                                                         uint32_t* __restrict__ planes, uint8_t* __restrict__ codes,
+                                                         float* __restrict__ thr_out) {
+    extern __shared__ float smem[];
+    float* s = smem;           // [npad] sorted column
+    float* thr = smem + npad;  // [D][c-1] thresholds
+    const int v = blockIdx.x;
+    const int tid = threadIdx.x;
+    const T* xv = x + (size_t)v * N;
+
+    for (int i = tid; i < npad; i += blockDim.x) s[i] = (i < N) ? (float)xv[i] : INFINITY;
+    __syncthreads();
+    for (int k = 2; k <= npad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < npad; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const float a = s[i], b = s[ixj];
+                    const bool ascending = (i & k) == 0;
+                    if ((a > b) == ascending) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    const int cm1 = c - 1;
+    const long long W = 1LL << 20;
+    for (int d = tid; d < D; d += blockDim.x) {
+        long long share[kMaxC];
+        uint32_t u[4];
+        for (int j = 0; j < c; ++j) {
+            if ((j & 3) == 0) philox4x32_10((uint32_t)(j >> 2), (uint32_t)v, (uint32_t)d, kPhiloxTag, key0, key1, u);
+            const unsigned long long draw = ((unsigned long long)u[j & 3] * (unsigned long long)(2u * R)) >> 32;
+            share[j] = W - (long long)R + (long long)draw;
+        }
+        long long total = 0;
+        for (int j = 0; j < c; ++j) total += share[j];
+        long long cum = 0, prev = 0;
+        for (int j = 1; j < c; ++j) {
+            cum += share[j - 1];
+            long long p = total > 0 ? (long long)(((unsigned long long)N * (unsigned long long)cum) /
+                                                  (unsigned long long)total)
+                                    : ((long long)N * j) / c;
+            if (p < j) p = j;
+            if (p > N - c + j) p = N - c + j;
+            if (j > 1 && p <= prev) p = prev + 1;
+            prev = p;
+            const float t = s[p];
+            thr[d * cm1 + (j - 1)] = t;
+            if (thr_out) thr_out[((size_t)d * M + v) * cm1 + (j - 1)] = t;
+        }
+    }
+    __syncthreads();
+
+    if (codes) {
+        for (int i = tid; i < N; i += blockDim.x) {
+            const float xs = (float)xv[i];
+            for (int d = 0; d < D; ++d) {
+                int code = 0;
+                for (int j = 0; j < cm1; ++j) code += (xs >= thr[d * cm1 + j]);
+                codes[((size_t)d * M + v) * N + i] = (uint8_t)code;
+            }
+        }
+    }
+
+    if (planes) {
+        const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+        for (int w = warp; w < g.Ws; w += nwarps) {
+            int sidx = -1;
+            if (w < g.W0) {
+                const int q = w * 32 + lane;
+                if (q < g.N0) sidx = perm[q];
+            } else if (w < g.W) {
+                const int q = (w - g.W0) * 32 + lane;
+                if (q < g.N1) sidx = perm[g.N0 + q];
+            }
+            const float xs = sidx >= 0 ? (float)xv[sidx] : 0.0f;
+            for (int d = 0; d < D; ++d) {
+                int code = 0;
+                for (int j = 0; j < cm1; ++j) code += (xs >= thr[d * cm1 + j]);
+                for (int a = 1; a <= cm1; ++a) {
+                    const unsigned m = __ballot_sync(0xffffffffu, sidx >= 0 && code == a);
+                    if (lane == 0) planes[(((size_t)d * M + v) * cm1 + (a - 1)) * g.Ws + w] = m;
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
+                              uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
+                              uint8_t* codes, float* thr, cudaStream_t st) {
+    int npad = 1;
+    while (npad < N) npad <<= 1;
+    const size_t smem = sizeof(float) * ((size_t)npad + (size_t)D * (c - 1));
+    const uint32_t R = (uint32_t)floor(range * 1048576.0 + 0.5);
+    const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
+    cudaError_t e;
+    if (dtype == 0) {
+        e = cudaFuncSetAttribute(discretize_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        discretize_kernel<float><<<M, 512, smem, st>>>((const float*)x, N, M, c, D, R, k0, k1, npad, perm, g,
+                                                       planes, codes, thr);
+    } else {
+        e = cudaFuncSetAttribute(discretize_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        discretize_kernel<int8_t><<<M, 512, smem, st>>>((const int8_t*)x, N, M, c, D, R, k0, k1, npad, perm, g,
+                                                        planes, codes, thr);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mdfs

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of the MDFS C ABI (``include/mdfs.h``).
+
+Argument marshalling only: every step of the scan runs in the CUDA library
+``libmdfs_gb300.so``.  Inputs may be CUDA tensors (device pointers are passed
+through, outputs are allocated on the same device and the current torch stream
+is used) or host arrays (numpy arrays or CPU tensors; outputs are numpy arrays
+and the library copies inputs to the device inside the call).  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdfs_gb300.so")
+
+MDFS_F32 = 0
+MDFS_I8 = 1
+
+_ERRORS = {
+    -1: "MDFS_EINVAL",
+    -2: "MDFS_EDEGENERATE",
+    -3: "MDFS_ENONFINITE",
+    -4: "MDFS_ENOMEM",
+    -5: "MDFS_ECUDA",
+    -6: "MDFS_ETIMEOUT",
+}
+
+EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
+            "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report")
+
+
+class MdfsError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {message}")
+        self.code = code
+
+
+class _Data(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("N", ctypes.c_int), ("M", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"MDFS CUDA library not built ({path} missing); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        lib.mdfs_discretize.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_uint64, P, P]
+        lib.mdfs_discretize.restype = ctypes.c_int
+        lib.mdfs_max_ig.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
+        lib.mdfs_max_ig.restype = ctypes.c_int
+        lib.mdfs_ig_lim.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                    ctypes.c_double, P, P, P, P]
+        lib.mdfs_ig_lim.restype = ctypes.c_int
+        lib.mdfs_last_error.argtypes = []
+        lib.mdfs_last_error.restype = ctypes.c_char_p
+        lib.mdfs_release.argtypes = []
+        lib.mdfs_release.restype = ctypes.c_int
+        lib.mdfs_abi_version.argtypes = []
+        lib.mdfs_abi_version.restype = ctypes.c_int
+        lib.mdfs_last_launch_count.argtypes = []
+        lib.mdfs_last_launch_count.restype = ctypes.c_int
+        lib.mdfs_profile.argtypes = [ctypes.c_int]
+        lib.mdfs_profile.restype = ctypes.c_int
+        lib.mdfs_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int]
+        lib.mdfs_profile_report.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load().mdfs_last_error().decode(errors="replace")
+        raise MdfsError(rc, msg)
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream_of(a):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+
+
+def _host(a, dtype):
+    if hasattr(a, "detach"):  # CPU torch tensor
+        a = a.detach().numpy()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _x_info(x):
+    """(pointer, dtype code, keep-alive) of the variable-major (M, N) array."""
+    if _is_cuda(x):
+        import torch
+        x = x.contiguous()
+        if x.dtype == torch.float32:
+            return x.data_ptr(), MDFS_F32, x
+        if x.dtype == torch.int8:
+            return x.data_ptr(), MDFS_I8, x
+        raise TypeError("x must be float32 or int8")
+    arr = x.detach().numpy() if hasattr(x, "detach") else np.asarray(x)
+    if arr.dtype == np.int8:
+        arr = np.ascontiguousarray(arr)
+        return arr.ctypes.data, MDFS_I8, arr
+    arr = np.ascontiguousarray(arr, dtype=np.float32)
+    return arr.ctypes.data, MDFS_F32, arr
+
+
+def _data(x, y):
+    xp, dt, xk = _x_info(x)
+    M, N = int(x.shape[0]), int(x.shape[1])
+    yk = None
+    yp = None
+    if y is not None:
+        if _is_cuda(y):
+            import torch
+            yk = y.contiguous().to(torch.uint8)
+            yp = yk.data_ptr()
+        else:
+            yk = _host(y, np.uint8)
+            yp = yk.ctypes.data
+        if int(y.shape[0]) != N:
+            raise ValueError("y must have N entries")
+    return _Data(dt, xp, yp, N, M), (xk, yk)
+
+
+def discretize(x, divisions: int = 1, discretizations: int = 1, range_: float = 0.0, seed: int = 0):
+    """Codes u8[D][M][N] (section "Algorithm and implementation" of arXiv 1811.00631)."""
+    lib = load()
+    data, keep = _data(x, None)
+    D, M, N = discretizations, data.M, data.N
+    if _is_cuda(x):
+        import torch
+        out = torch.empty((D, M, N), dtype=torch.uint8, device=x.device)
+        rc = lib.mdfs_discretize(ctypes.byref(data), divisions, D, float(range_), int(seed) & (2**64 - 1),
+                                 ctypes.c_void_p(out.data_ptr()), _stream_of(x))
+    else:
+        out = np.empty((D, M, N), dtype=np.uint8)
+        rc = lib.mdfs_discretize(ctypes.byref(data), divisions, D, float(range_), int(seed) & (2**64 - 1),
+                                 ctypes.c_void_p(out.ctypes.data), None)
+    _check(rc)
+    del keep
+    return out
+
+
+def max_ig(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range_: float = 0.0,
+           pc_xi: float = 0.25, seed: int = 0, out=None):
+    """IG^k_max per variable (Eq. 1 of arXiv 1811.00631) with its argmax tuple and discretisation.
+
+    Returns (ig f32[M], tuples i32[M, k-1], disc i32[M]) on the device of x
+    (torch tensors) or on the host (numpy arrays).  ``out`` may pass
+    preallocated (ig, tuples, disc) of the matching kind.
+    """
+    lib = load()
+    data, keep = _data(x, y)
+    M = data.M
+    kk = max(k - 1, 1)
+    if _is_cuda(x):
+        import torch
+        if out is None:
+            ig = torch.empty(M, dtype=torch.float32, device=x.device)
+            tu = torch.empty((M, kk), dtype=torch.int32, device=x.device)
+            di = torch.empty(M, dtype=torch.int32, device=x.device)
+        else:
+            ig, tu, di = out
+        ptrs = (ig.data_ptr(), tu.data_ptr(), di.data_ptr())
+        stream = _stream_of(x)
+    else:
+        if out is None:
+            ig = np.empty(M, dtype=np.float32)
+            tu = np.empty((M, kk), dtype=np.int32)
+            di = np.empty(M, dtype=np.int32)
+        else:
+            ig, tu, di = out
+        ptrs = (ig.ctypes.data, tu.ctypes.data, di.ctypes.data)
+        stream = None
+    rc = lib.mdfs_max_ig(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
+                         int(seed) & (2**64 - 1), ctypes.c_void_p(ptrs[0]),
+                         ctypes.c_void_p(ptrs[1]) if k > 1 else None, ctypes.c_void_p(ptrs[2]), stream)
+    _check(rc)
+    del keep
+    return ig, tu[:, : k - 1], di
+
+
+def max_ig_raw(data_ptr_x, dtype: int, data_ptr_y, N: int, M: int, k: int, divisions: int, discretizations: int,
+               range_: float, pc_xi: float, seed: int, ig_ptr, tuples_ptr, disc_ptr, stream_ptr):
+    """Direct pass-through of raw pointers (host or device) to mdfs_max_ig."""
+    lib = load()
+    data = _Data(dtype, data_ptr_x, data_ptr_y, N, M)
+    rc = lib.mdfs_max_ig(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
+                         int(seed) & (2**64 - 1), ctypes.c_void_p(ig_ptr),
+                         ctypes.c_void_p(tuples_ptr) if tuples_ptr else None,
+                         ctypes.c_void_p(disc_ptr) if disc_ptr else None,
+                         ctypes.c_void_p(stream_ptr) if stream_ptr else None)
+    _check(rc)
+
+
+def ig_lim(ig, k: int, divisions: int, discretizations: int = 1, irrelevant_mask=None, alpha: float = 0.05):
+    """chi^2 / extreme-value fit (section "Theory"): (p_values f64[M], IG_lim, T_hat)."""
+    lib = load()
+    M = int(ig.shape[0])
+    lim = ctypes.c_double()
+    neff = ctypes.c_double()
+    if _is_cuda(ig):
+        import torch
+        igc = ig.contiguous().float()
+        p = torch.empty(M, dtype=torch.float64, device=ig.device)
+        mk = None
+        if irrelevant_mask is not None:
+            mk = torch.as_tensor(irrelevant_mask, device=ig.device).to(torch.uint8).contiguous()
+        rc = lib.mdfs_ig_lim(ctypes.c_void_p(igc.data_ptr()), M, k, divisions, discretizations,
+                             ctypes.c_void_p(mk.data_ptr()) if mk is not None else None, float(alpha),
+                             ctypes.c_void_p(p.data_ptr()), ctypes.byref(lim), ctypes.byref(neff), _stream_of(ig))
+    else:
+        igc = _host(ig, np.float32)
+        p = np.empty(M, dtype=np.float64)
+        mk = _host(irrelevant_mask, np.uint8) if irrelevant_mask is not None else None
+        rc = lib.mdfs_ig_lim(ctypes.c_void_p(igc.ctypes.data), M, k, divisions, discretizations,
+                             ctypes.c_void_p(mk.ctypes.data) if mk is not None else None, float(alpha),
+                             ctypes.c_void_p(p.ctypes.data), ctypes.byref(lim), ctypes.byref(neff), None)
+    _check(rc)
+    return p, lim.value, neff.value
+
+
+def last_launch_count() -> int:
+    return load().mdfs_last_launch_count()
+
+
+def profile(enable: bool) -> None:
+    """Switches per-kernel CUDA-event timing of every library launch on or off."""
+    _check(load().mdfs_profile(1 if enable else 0))
+
+
+def profile_report() -> dict:
+    """{kernel name: {"count": launches, "ms": total milliseconds}} since the last report."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().mdfs_profile_report(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = {"count": int(cnt), "ms": float(ms)}
+    return out
+
+
+def release() -> None:
+    _check(load().mdfs_release())
+
+
+def abi_version() -> int:
+    return load().mdfs_abi_version()

@@ -1,0 +1,63 @@
+"""The C ABI library loads on a machine without a GPU and exports every entry
+point declared in include/*.h (no compute calls are made here)."""
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mdfs_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1811_00631_gb300 import build, mdfs
+    build.build()
+    return mdfs.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared():
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_abi_version_and_error_string(lib):
+    assert lib.mdfs_abi_version() == 1
+    assert lib.mdfs_last_error() == b""
+
+
+def test_binding_names_match_header():
+    from paper_1811_00631_gb300 import mdfs
+    assert set(mdfs.EXPORTED) <= set(_declared())
+
+
+def test_argument_errors_need_no_gpu(lib):
+    """Host-side argument checks fail before any CUDA call."""
+    import ctypes
+    from paper_1811_00631_gb300 import mdfs
+    import numpy as np
+    x = np.zeros((4, 10), dtype=np.float32)
+    y = np.zeros(10, dtype=np.uint8)
+    d = mdfs._Data(0, x.ctypes.data, y.ctypes.data, 10, 4)
+    ig = np.zeros(4, dtype=np.float32)
+    rc = lib.mdfs_max_ig(ctypes.byref(d), 4, 1, 1, 0.0, 0.25, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
+    assert rc == -1 and b"k = 4" in lib.mdfs_last_error()
+    rc = lib.mdfs_max_ig(ctypes.byref(d), 2, 1, 1, 0.0, 1.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
+    assert rc == -1 and b"pc_xi" in lib.mdfs_last_error()
+    rc = lib.mdfs_max_ig(ctypes.byref(d), 2, 9, 1, 0.0, 0.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
+    assert rc == -1 and b"divisions" in lib.mdfs_last_error()

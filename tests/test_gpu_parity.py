@@ -1,0 +1,235 @@
+"""GPU (sm_103a) parity of the MDFS scan against the FP64 CPU oracle.
+
+Every call goes through the C ABI (ctypes binding).  Inputs are seeded and
+synthetic; expected values come from the oracle only.  Tolerances follow the
+statement of the method's precision target: discretised codes bit-exact,
+IG within 1e-4 absolute + 1e-5 relative of the FP64 oracle, argmax tuples
+equal unless the GPU's tuple is an equally good alternative (its oracle IG
+lies within the same tolerance of the oracle's maximum).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_00631_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ATOL, RTOL = 1e-4, 1e-5
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_00631_gb300 import build
+    build.build()
+    return torch
+
+
+def _gpu_max_ig(torch, x, y, k, div, D, rng_, xi, seed, host=False):
+    from paper_1811_00631_gb300 import mdfs
+    if host:
+        ig, tu, di = mdfs.max_ig(x, y, k, div, D, rng_, xi, seed)
+        return np.asarray(ig, dtype=np.float64), np.asarray(tu), np.asarray(di)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    yt = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+    ig, tu, di = mdfs.max_ig(xt, yt, k, div, D, rng_, xi, seed)
+    torch.cuda.synchronize()
+    return ig.cpu().numpy().astype(np.float64), tu.cpu().numpy(), di.cpu().numpy()
+
+
+def _check(codes, y, c, k, xi, g_ig, g_tu, g_di, ref, variables):
+    """Compare the GPU result for ``variables`` with the oracle's (ref rows align with variables)."""
+    for row, i in enumerate(variables):
+        o = ref["ig"][row]
+        tol = ATOL + RTOL * abs(o)
+        assert abs(g_ig[i] - o) <= tol, f"var {i}: gpu {g_ig[i]!r} oracle {o!r}"
+        same = g_di[i] == ref["disc"][row] and (k == 1 or tuple(g_tu[i]) == tuple(ref["tuples"][row]))
+        if not same:
+            # another (d, S) reached the max within tolerance: it must be a valid maximiser
+            S = list(g_tu[i]) if k > 1 else []
+            assert 0 <= g_di[i] < codes.shape[0]
+            assert i not in S and len(set(S)) == len(S) and S == sorted(S)
+            alt = oracle.ig_one(codes, y, c, xi, int(g_di[i]), int(i), S)
+            assert abs(alt - o) <= 2 * tol, f"var {i}: gpu argmax {g_di[i], S} gives {alt}, oracle max {o}"
+            assert abs(ref["second"][row] - o) <= 2 * tol or abs(alt - o) <= tol
+
+
+def test_discretize_bit_exact(cuda):
+    from paper_1811_00631_gb300 import mdfs
+    torch = cuda
+    rng = np.random.default_rng(1)
+    for (M, N, div, D, r) in [(7, 333, 1, 4, 0.5), (5, 2000, 2, 3, 1.0), (3, 97, 3, 5, 0.0), (2, 4, 3, 2, 0.9)]:
+        x = rng.standard_normal((M, N)).astype(np.float32)
+        want = oracle.discretize(x, div, D, r, seed=1234567890123)
+        got = mdfs.discretize(torch.from_numpy(x).cuda(), div, D, r, seed=1234567890123).cpu().numpy()
+        assert np.array_equal(got, want)
+        got_h = mdfs.discretize(x, div, D, r, seed=1234567890123)
+        assert np.array_equal(got_h, want)
+
+
+def test_discretize_int8_and_ties(cuda):
+    from paper_1811_00631_gb300 import mdfs
+    torch = cuda
+    rng = np.random.default_rng(2)
+    x = synth.to_int8(rng.standard_normal((9, 501)), scale=3.0)  # heavy ties
+    want = oracle.discretize(x.astype(np.float32), 2, 6, 0.7, seed=5)
+    got = mdfs.discretize(torch.from_numpy(x).cuda(), 2, 6, 0.7, seed=5).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("k,div,M,N,D", [
+    (1, 1, 70, 333, 3), (1, 3, 40, 1000, 2),
+    (2, 1, 70, 333, 3), (2, 2, 67, 290, 2), (2, 3, 33, 257, 2),
+    (3, 1, 150, 200, 2), (3, 2, 45, 161, 2), (3, 3, 36, 130, 1),
+])
+def test_max_ig_small(cuda, k, div, M, N, D):
+    """Several tiles with ragged tails in M and N, all k and class counts."""
+    rng = np.random.default_rng(100 * k + 10 * div + D)
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[3] > 0.2) ^ (rng.random(N) < 0.2)).astype(np.uint8)
+    xi, r, seed = 0.25, 0.5, 77 + k
+    c = div + 1
+    codes = oracle.discretize(x, div, D, r, seed)
+    ref = oracle.max_ig(codes, y, c, k, xi)
+    g = _gpu_max_ig(cuda, x, y, k, div, D, r, xi, seed)
+    _check(codes, y, c, k, xi, *g, ref, range(M))
+
+
+def test_max_ig_host_pointers_match_device(cuda):
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((50, 300)).astype(np.float32)
+    y = (rng.random(300) < 0.3).astype(np.uint8)
+    dev = _gpu_max_ig(cuda, x, y, 2, 2, 3, 0.5, 0.3, 9)
+    host = _gpu_max_ig(cuda, x, y, 2, 2, 3, 0.5, 0.3, 9, host=True)
+    for a, b in zip(dev, host):
+        assert np.array_equal(a, b)
+
+
+def test_xor_small_config(cuda):
+    """N=200, M=50 XOR data, 2 bins, 1 discretisation, range 0.25, xi 0.25, seed 1."""
+    ds = synth.xor_small()
+    codes = oracle.discretize(ds.x, 1, 1, 0.25, 1)
+    ref = oracle.max_ig(codes, ds.y, 2, 2, 0.25)
+    g = _gpu_max_ig(cuda, ds.x, ds.y, 2, 1, 1, 0.25, 0.25, 1)
+    _check(codes, ds.y, 2, 2, 0.25, *g, ref, range(50))
+    assert set(np.argsort(-g[0])[:2].tolist()) == {0, 1}
+    assert g[1][0, 0] == 1 and g[1][1, 0] == 0
+
+
+@pytest.mark.parametrize("k,div", [(1, 1), (1, 2), (2, 1), (2, 2)])
+def test_madelon_like_full_size_sampled(cuda, k, div):
+    """N=2000, M=500, 30 discretisations, range 0.5, xi 0.25: the full GPU
+    scan, compared on every informative variable and a random sample of noise
+    variables (the oracle computes those rows one by one)."""
+    ds = synth.madelon_like()
+    D, r, xi, seed = 30, 0.5, 0.25, 11
+    c = div + 1
+    codes = oracle.discretize(ds.x, div, D, r, seed)
+    g = _gpu_max_ig(cuda, ds.x, ds.y, k, div, D, r, xi, seed)
+    rng = np.random.default_rng(3)
+    noise = np.setdiff1d(np.arange(500), ds.informative)
+    variables = np.concatenate([ds.informative, rng.choice(noise, 20, replace=False)]).astype(np.int32)
+    ref = oracle.max_ig(codes, ds.y, c, k, xi, variables=variables)
+    _check(codes, ds.y, c, k, xi, *g, ref, variables)
+    if k == 2:
+        # the 20 informative variables lead the ranking
+        top = set(np.argsort(-g[0])[:20].tolist())
+        assert len(top & set(ds.informative.tolist())) >= 18
+
+
+def test_madelon_like_k3_full_size_sampled(cuda):
+    """k=3 on the 2000 x 500 parity data, 30 discretisations, 2 bins: the
+    full triple scan, compared on a sample of variables."""
+    ds = synth.madelon_like()
+    D, r, xi, seed = 30, 0.5, 0.25, 11
+    codes = oracle.discretize(ds.x, 1, D, r, seed)
+    g = _gpu_max_ig(cuda, ds.x, ds.y, 3, 1, D, r, xi, seed)
+    variables = np.array([ds.info["base"][0], ds.info["comb"][0], 7, 499], dtype=np.int32)
+    ref = oracle.max_ig(codes, ds.y, 2, 3, xi, variables=variables)
+    _check(codes, ds.y, 2, 3, xi, *g, ref, variables)
+
+
+def test_edge_minimal_sizes(cuda):
+    rng = np.random.default_rng(8)
+    for k, M, N, div in [(1, 1, 2, 1), (2, 2, 3, 2), (3, 3, 4, 3), (3, 4, 33, 1), (2, 5, 32, 1), (2, 5, 64, 1)]:
+        x = rng.standard_normal((M, N)).astype(np.float32)
+        y = (np.arange(N) % 2).astype(np.uint8)
+        codes = oracle.discretize(x, div, 2, 0.3, 3)
+        ref = oracle.max_ig(codes, y, div + 1, k, 0.5)
+        g = _gpu_max_ig(cuda, x, y, k, div, 2, 0.3, 0.5, 3)
+        _check(codes, y, div + 1, k, 0.5, *g, ref, range(M))
+
+
+def test_unbalanced_classes_and_int8(cuda):
+    rng = np.random.default_rng(9)
+    M, N = 40, 777
+    x8 = synth.to_int8(rng.standard_normal((M, N)), scale=4.0)
+    y = (rng.random(N) < 0.07).astype(np.uint8)
+    for k in (1, 2, 3):
+        codes = oracle.discretize(x8.astype(np.float32), 2, 3, 0.8, 21)
+        ref = oracle.max_ig(codes, y, 3, k, 0.1)
+        g = _gpu_max_ig(cuda, x8, y, k, 2, 3, 0.8, 0.1, 21)
+        _check(codes, y, 3, k, 0.1, *g, ref, range(M))
+
+
+def test_errors(cuda):
+    from paper_1811_00631_gb300 import mdfs
+    torch = cuda
+    x = torch.randn(10, 50, device="cuda")
+    with pytest.raises(mdfs.MdfsError) as e:
+        mdfs.max_ig(x, torch.zeros(50, dtype=torch.uint8, device="cuda"), 2, 1, 1)
+    assert e.value.code == -2
+    y = torch.zeros(50, dtype=torch.uint8, device="cuda")
+    y[3] = 2
+    with pytest.raises(mdfs.MdfsError) as e:
+        mdfs.max_ig(x, y, 2, 1, 1)
+    assert e.value.code == -1
+    x2 = x.clone()
+    x2[4, 7] = float("nan")
+    y[3] = 1
+    with pytest.raises(mdfs.MdfsError) as e:
+        mdfs.max_ig(x2, y, 2, 1, 1)
+    assert e.value.code == -3
+    # the context is still usable after host-detected errors
+    ig, _, _ = mdfs.max_ig(x, y, 2, 1, 1)
+    torch.cuda.synchronize()
+    assert torch.isfinite(ig).all()
+
+
+def test_ig_lim_matches_oracle(cuda):
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(31)
+    for df_k, T in [(1, 50), (2, 400), (3, 2000)]:
+        c = 2
+        df = (c - 1) * c ** (df_k - 1)
+        ig = (0.5 * rng.chisquare(df, size=(3000, T)).max(axis=1)).astype(np.float32)
+        mask = (rng.random(3000) < 0.8).astype(np.uint8)
+        p_o, lim_o, t_o = oracle.ig_lim(ig.astype(np.float64), df_k, 1, mask, alpha=0.01)
+        p_g, lim_g, t_g = mdfs.ig_lim(ig, df_k, 1, 1, mask, alpha=0.01)
+        assert t_g == pytest.approx(t_o, rel=1e-10)
+        assert lim_g == pytest.approx(lim_o, rel=1e-9)
+        assert np.allclose(p_g, p_o, rtol=1e-9, atol=1e-14)
+        p_d, lim_d, t_d = mdfs.ig_lim(cuda.from_numpy(ig).cuda(), df_k, 1, 1, mask, alpha=0.01)
+        assert np.allclose(p_d.cpu().numpy(), p_o, rtol=1e-9, atol=1e-14)
+
+
+def test_repeatable_and_stream_ordered(cuda):
+    """Same inputs, same outputs, bit for bit, on the default and a side stream."""
+    torch = cuda
+    from paper_1811_00631_gb300 import mdfs
+    ds = synth.madelon_like(N=500, M=120, seed=3)
+    x = torch.from_numpy(ds.x).cuda()
+    y = torch.from_numpy(ds.y).cuda()
+    a = mdfs.max_ig(x, y, 3, 1, 4, 0.5, 0.25, 5)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b = mdfs.max_ig(x, y, 3, 1, 4, 0.5, 0.25, 5)
+    s.synchronize()
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
