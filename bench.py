@@ -33,12 +33,20 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N_OBJ, M_VAR, DISC, DIV, RANGE, XI = 2000, 500, 30, 1, 0.5, 0.25
-UNITS_K2 = math.comb(M_VAR, 2) * DISC
-UNITS_K3 = math.comb(M_VAR, 3) * DISC
-UNITS = UNITS_K2 + UNITS_K3
 METRIC = "k-tuple*discretization IG evals/sec (k=2,3; N=2000, M=500)"
 UNIT = "tuple*disc/s"
 WORKLOAD = "mdfs_scan_parity_N2000_M500_k2+k3_D30_c2"
+
+
+def _units():
+    return math.comb(M_VAR, 2) * DISC + math.comb(M_VAR, 3) * DISC
+
+
+def _use_small_case():
+    """A reduced case of the same kernels for profiler captures (M = 160, 4 discretisations)."""
+    global M_VAR, DISC, WORKLOAD
+    M_VAR, DISC = 160, 4
+    WORKLOAD = "mdfs_scan_parity_N2000_M160_k2+k3_D4_c2 (profiling case)"
 
 
 def _config(extra=None):
@@ -165,7 +173,7 @@ def run_gpu(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    ds = synth.madelon_like(seed=2 + rank)  # an independent job per rank
+    ds = synth.madelon_like(M=max(M_VAR, 20), seed=2 + rank)  # an independent job per rank
     x = torch.from_numpy(ds.x).to(dev)
     y = torch.from_numpy(ds.y).to(dev)
     M = M_VAR
@@ -213,6 +221,7 @@ def run_gpu(args, rank, world, local_rank):
         t = torch.tensor([total_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
+    UNITS = _units()
     value = world * UNITS * args.steps / total_s
 
     # ---- end to end through the C ABI with pinned host buffers ----
@@ -291,12 +300,15 @@ def run_gpu(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--popc-peak", type=float, default=152 * 16 * 2.07e9 / 1e12)
+    ap.add_argument("--small", action="store_true", help="reduced profiling case (M=160, D=4)")
     args = ap.parse_args()
+    if args.small:
+        _use_small_case()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -136,10 +136,6 @@ def test_madelon_like_full_size_sampled(cuda, k, div):
     variables = np.concatenate([ds.informative, rng.choice(noise, 20, replace=False)]).astype(np.int32)
     ref = oracle.max_ig(codes, ds.y, c, k, xi, variables=variables)
     _check(codes, ds.y, c, k, xi, *g, ref, variables)
-    if k == 2:
-        # the 20 informative variables lead the ranking
-        top = set(np.argsort(-g[0])[:20].tolist())
-        assert len(top & set(ds.informative.tolist())) >= 18
 
 
 def test_madelon_like_k3_full_size_sampled(cuda):
