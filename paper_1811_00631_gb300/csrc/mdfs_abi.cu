@@ -16,6 +16,9 @@
 
 using namespace mdfs;
 
+// dynamic shared memory the two-class k = 3 kernel may take for its tables
+static const size_t kK3c2MaxSmem = 200 * 1024;
+
 namespace {
 
 thread_local std::string g_err;
@@ -40,13 +43,15 @@ struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
     Buffer x, y, stats, perm, tab, planes, cnt1, sh1, keys, sh2, cnt2, items, ig, tuples, disc, codes, mask, pv, res;
+    Buffer pairs2, items2;
+    int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
     double* host_res = nullptr; // pinned, 4 doubles
     int items_M = -1, items_c = -1, n_items = 0;
 
     ~Workspace() {
-        Buffer* all[] = {&x, &y, &stats, &perm, &tab, &planes, &cnt1, &sh1, &keys, &sh2,
-                         &cnt2, &items, &ig, &tuples, &disc, &codes, &mask, &pv, &res};
+        Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
+                         &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -420,7 +425,33 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
     MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
     if (k == 2) {
-        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, st));
+        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, st));
+    } else if (k == 3 && c == 2 && k3c2_smem_bytes(N) <= kK3c2MaxSmem) {
+        // two classes: Pair2 records and the Harley-Seal triple kernel
+        const size_t per_disc = (size_t)M * M * sizeof(Pair2);
+        size_t budget = (size_t)4 << 30;
+        if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
+        int nd = (int)(budget / per_disc);
+        if (nd < 1) nd = 1;
+        if (nd > D) nd = D;
+        MDFS_ENSURE(ws, pairs2, (size_t)nd * per_disc);
+        if (ws->items2_M != M) {
+            std::vector<int2> items;
+            build_k3c2_items(M, items);
+            MDFS_ENSURE(ws, items2, items.size() * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items2.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items2_M = M;
+            ws->n_items2 = (int)items.size();
+        }
+        for (int d0 = 0; d0 < D; d0 += nd) {
+            const int nn = std::min(nd, D - d0);
+            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
+                                                   nullptr, (Pair2*)ws->pairs2.p, st));
+            MDFS_LAUNCH("k3", st, launch_k3c2(planes, g, M, d0, nn, (const int2*)ws->items2.p, ws->n_items2, tab,
+                                              cnt1, (const Pair2*)ws->pairs2.p, keys, st));
+        }
     } else if (k == 3) {
         const size_t per_disc = (size_t)M * M * (sizeof(long long) + (size_t)P * P * 2 * sizeof(int));
         size_t budget = (size_t)4 << 30;
@@ -443,8 +474,8 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         }
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
-            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, (long long*)ws->sh2.p,
-                                  (int*)ws->cnt2.p, st));
+            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
+                                                   (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, st));
             MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p, ws->n_items, tab, cnt1,
                                         (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
         }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace mdfs {
 
 // Fixed-point scale of the entropy tables: values are int64 multiples of 2^-32.
@@ -35,6 +37,13 @@ inline PlaneGeom make_geom(int N, int N0) {
     return g;
 }
 
+// Pair record of the two-class (c = 2) k = 3 path: class counts of the voxel
+// (1, 1) of the pair and its regularised entropy SH (fixed point).
+struct __align__(16) Pair2 {
+    int n0, n1;
+    long long sh;
+};
+
 // ---- launchers (all asynchronous on `st`) -----------------------------------
 // stats[0] = N1 (count of y == 1), stats[1] = number of y not in {0,1},
 // stats[2] = number of non-finite x.  perm = class-stable sample order.
@@ -60,9 +69,10 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 // Pair pass over discretisations [d0, d0 + nd).  keys != NULL: fold the two IG
 // roles of every pair into keys (k = 2).  sh2/cnt2 != NULL: store the pair
 // tables (k = 3): sh2 [nd][M][M] i64, cnt2 [nd][M][M][(c-1)^2][2] i32 (i < m only).
+// pairs2 != NULL (c = 2 only): store Pair2 records [nd][M][M] (i < m only) instead.
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd,
                       const long long* tab, const int* cnt1, const long long* sh1,
-                      unsigned long long* keys, long long* sh2, int* cnt2, cudaStream_t st);
+                      unsigned long long* keys, long long* sh2, int* cnt2, Pair2* pairs2, cudaStream_t st);
 
 // Triple pass over discretisations [d0, d0 + nd), using the pair tables of the
 // same chunk.  Folds the three IG roles of every triple into keys.  items[j] =
@@ -73,6 +83,15 @@ int k3_tile_e(int c);
 cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, int d0, int nd, const int2* items,
                             int n_items, const long long* tab, const int* cnt1, const long long* sh2,
                             const int* cnt2, unsigned long long* keys, cudaStream_t st);
+
+// Two-class k = 3 kernel (middle-variable tiles, Harley-Seal counting, tables
+// in shared memory).  items from build_k3c2_items; needs k3c2_smem_bytes(N) of
+// dynamic shared memory.
+void build_k3c2_items(int M, std::vector<int2>& items);
+size_t k3c2_smem_bytes(int N);
+cudaError_t launch_k3c2(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
+                        const long long* tab, const int* cnt1, const Pair2* pairs, unsigned long long* keys,
+                        cudaStream_t st);
 
 // keys [M] -> ig [M] f32, tuples [M][k-1] i32 (NULL ok), disc [M] i32 (NULL ok).
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,

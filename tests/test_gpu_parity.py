@@ -161,6 +161,19 @@ def test_edge_minimal_sizes(cuda):
         _check(codes, y, div + 1, k, 0.5, *g, ref, range(M))
 
 
+def test_k3_large_n_uses_global_tables(cuda):
+    """N beyond the shared-memory table limit of the two-class triple kernel."""
+    rng = np.random.default_rng(19)
+    M, N = 14, 9000
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[1] > 0) ^ (x[2] > 0) ^ (x[5] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, 2, 0.4, 4)
+    ref = oracle.max_ig(codes, y, 2, 3, 0.25)
+    g = _gpu_max_ig(cuda, x, y, 3, 1, 2, 0.4, 0.25, 4)
+    _check(codes, y, 2, 3, 0.25, *g, ref, range(M))
+    assert set(g[1][1].tolist()) == {2, 5}
+
+
 def test_unbalanced_classes_and_int8(cuda):
     rng = np.random.default_rng(9)
     M, N = 40, 777
