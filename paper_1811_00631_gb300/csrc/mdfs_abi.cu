@@ -16,8 +16,8 @@
 
 using namespace mdfs;
 
-// dynamic shared memory the two-class k = 3 kernel may take for its tables
-static const size_t kK3c2MaxSmem = 200 * 1024;
+// dynamic shared memory the tensor-core k = 3 kernel may take (stages + tables)
+static const size_t kK3tcMaxSmem = 218 * 1024;
 
 namespace {
 
@@ -43,7 +43,7 @@ struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
     Buffer x, y, stats, perm, tab, planes, cnt1, sh1, keys, sh2, cnt2, items, ig, tuples, disc, codes, mask, pv, res;
-    Buffer pairs2, items2;
+    Buffer pairs2, items2, onehot, err;
     int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
     double* host_res = nullptr; // pinned, 4 doubles
@@ -51,7 +51,8 @@ struct Workspace {
 
     ~Workspace() {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
-                         &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2};
+                         &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
+                         &onehot, &err};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -367,8 +368,8 @@ int mdfs_discretize(const mdfs_data* data, int divisions, int discretizations, d
     rc = bind_out(ws, ws->codes, codes, (size_t)discretizations * data->M * data->N, &oc);
     if (rc) return rc;
     PlaneGeom g = make_geom(data->N, data->N);
-    MDFS_LAUNCH("discretize", st, launch_discretize(xd, data->dtype, data->N, data->M, c, discretizations, range, seed, nullptr, g,
-                                  nullptr, oc.dev, nullptr, st));
+    MDFS_LAUNCH("discretize", st, launch_discretize(xd, data->dtype, data->N, data->M, c, discretizations, range, seed,
+                                                    nullptr, g, nullptr, oc.dev, nullptr, nullptr, TcGeom{}, st));
     rc = copy_back(ws, oc);
     if (rc) return rc;
     if (oc.staged || st == nullptr) MDFS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -420,14 +421,23 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     unsigned long long* keys = (unsigned long long*)ws->keys.p;
 
     MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
-    MDFS_LAUNCH("discretize", st, launch_discretize(xd, data->dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g, planes, nullptr,
-                                  nullptr, st));
+    // tensor-core triple path: two classes and tables that fit in shared memory
+    const bool use_tc3 = (k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
+    TcGeom tg = make_tc_geom(n0, n1);
+    uint8_t* onehot = nullptr;
+    if (use_tc3) {
+        MDFS_ENSURE(ws, onehot, (size_t)D * M * tg.Kp);
+        onehot = (uint8_t*)ws->onehot.p;
+    }
+    MDFS_LAUNCH("discretize", st, launch_discretize(xd, data->dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g,
+                                                    planes, nullptr, nullptr, onehot, tg, st));
     MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
     MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
+    bool check_err = false;
     if (k == 2) {
         MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, st));
-    } else if (k == 3 && c == 2 && k3c2_smem_bytes(N) <= kK3c2MaxSmem) {
-        // two classes: Pair2 records and the Harley-Seal triple kernel
+    } else if (use_tc3) {
+        // two classes: symmetric Pair2 records and the tcgen05 triple kernel
         const size_t per_disc = (size_t)M * M * sizeof(Pair2);
         size_t budget = (size_t)4 << 30;
         if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
@@ -435,9 +445,11 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         if (nd < 1) nd = 1;
         if (nd > D) nd = D;
         MDFS_ENSURE(ws, pairs2, (size_t)nd * per_disc);
+        MDFS_ENSURE(ws, err, sizeof(int));
+        MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
         if (ws->items2_M != M) {
             std::vector<int2> items;
-            build_k3c2_items(M, items);
+            build_k3tc_items(M, items);
             MDFS_ENSURE(ws, items2, items.size() * sizeof(int2));
             MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items2.p, items.data(), items.size() * sizeof(int2),
                                           cudaMemcpyHostToDevice, st));
@@ -445,13 +457,16 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
             ws->items2_M = M;
             ws->n_items2 = (int)items.size();
         }
+        CUtensorMap map;
+        MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M, D, tg.Kp));
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
                                                    nullptr, (Pair2*)ws->pairs2.p, st));
-            MDFS_LAUNCH("k3", st, launch_k3c2(planes, g, M, d0, nn, (const int2*)ws->items2.p, ws->n_items2, tab,
-                                              cnt1, (const Pair2*)ws->pairs2.p, keys, st));
+            MDFS_LAUNCH("k3", st, launch_k3tc(map, onehot, tg, M, d0, nn, (const int2*)ws->items2.p, ws->n_items2,
+                                              tab, cnt1, (const Pair2*)ws->pairs2.p, keys, (int*)ws->err.p, st));
         }
+        check_err = true;
     } else if (k == 3) {
         const size_t per_disc = (size_t)M * M * (sizeof(long long) + (size_t)P * P * 2 * sizeof(int));
         size_t budget = (size_t)4 << 30;
@@ -491,7 +506,14 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     if (rc) return rc;
     MDFS_LAUNCH("finalize", st, launch_finalize(keys, M, k, oig.dev, otu.dev, odi.dev, st));
     if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
-    if (oig.staged || otu.staged || odi.staged || st == nullptr) MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (check_err) {
+        // the tensor-core kernel reports bounded-wait timeouts through this flag
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (ws->host_stats[8] != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in the triple kernel");
+    } else if (oig.staged || otu.staged || odi.staged || st == nullptr) {
+        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     return MDFS_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of the MDFS library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,6 +38,13 @@ inline PlaneGeom make_geom(int N, int N0) {
     return g;
 }
 
+// K geometry of the one-hot tensor-core operands: class-0 samples in
+// [0, N0), zero padding to K0p (a multiple of 128), class-1 samples in
+// [K0p, K0p + N1), zero padding to Kp.
+struct TcGeom {
+    int N0, N1, K0p, Kp, nkb0, nkb;
+};
+
 // Pair record of the two-class (c = 2) k = 3 path: class counts of the voxel
 // (1, 1) of the pair and its regularised entropy SH (fixed point).
 struct __align__(16) Pair2 {
@@ -57,9 +65,11 @@ cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStrea
 // One CTA per variable: sort, thresholds, and codes and/or class-sorted bit planes.
 // planes: [D][M][c-1][Ws] u32 (NULL = skip); codes: [D][M][N] u8 (NULL = skip);
 // thr: [D][M][c-1] f32 (NULL = skip).
+// onehot: [D][M (c-1)][Kp] bytes, E4M3 1.0 (0x38) where the sample falls in
+// bin a >= 1 of the row (v, a), class-sorted with the TcGeom padding (NULL = skip).
 cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
                               uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
-                              uint8_t* codes, float* thr, cudaStream_t st);
+                              uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st);
 
 // Per (disc, variable): class counts of bins 1..c-1 -> cnt1 [D][M][c-1][2] i32,
 // SH1 [D][M] i64.  If keys != NULL also folds IG^1 = SH0 - SH1 into keys.
@@ -69,7 +79,8 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 // Pair pass over discretisations [d0, d0 + nd).  keys != NULL: fold the two IG
 // roles of every pair into keys (k = 2).  sh2/cnt2 != NULL: store the pair
 // tables (k = 3): sh2 [nd][M][M] i64, cnt2 [nd][M][M][(c-1)^2][2] i32 (i < m only).
-// pairs2 != NULL (c = 2 only): store Pair2 records [nd][M][M] (i < m only) instead.
+// pairs2 != NULL (c = 2 only): store Pair2 records [nd][M][M] instead, at
+// both [i][m] and [m][i].
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd,
                       const long long* tab, const int* cnt1, const long long* sh1,
                       unsigned long long* keys, long long* sh2, int* cnt2, Pair2* pairs2, cudaStream_t st);
@@ -92,6 +103,18 @@ size_t k3c2_smem_bytes(int N);
 cudaError_t launch_k3c2(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                         const long long* tab, const int* cnt1, const Pair2* pairs, unsigned long long* keys,
                         cudaStream_t st);
+
+// Two-class k = 3 kernel on the tensor cores (tcgen05 kind::f8f6f4): one-hot
+// operands through TMA, counts in TMEM, fused entropy epilogue.  pairs must be
+// symmetric ([i][m] and [m][i] both written).  err: device flag set on a
+// bounded-wait timeout.
+TcGeom make_tc_geom(int N0, int N1);
+void build_k3tc_items(int M, std::vector<int2>& items);
+size_t k3tc_smem_bytes(int N0, int N1);
+cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D, int Kp);
+cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
+                        const int2* items, int n_items, const long long* tab, const int* cnt1, const Pair2* pairs,
+                        unsigned long long* keys, int* err, cudaStream_t st);
 
 // keys [M] -> ig [M] f32, tuples [M][k-1] i32 (NULL ok), disc [M] i32 (NULL ok).
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,

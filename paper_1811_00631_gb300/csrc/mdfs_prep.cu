@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
                                                          uint32_t R, uint32_t key0, uint32_t key1, int npad,
                                                          const int* __restrict__ perm, PlaneGeom g,
                                                          uint32_t* __restrict__ planes, uint8_t* __restrict__ codes,
-                                                         float* __restrict__ thr_out) {
+                                                         float* __restrict__ thr_out, uint8_t* __restrict__ onehot,
+                                                         TcGeom tg) {
     extern __shared__ float smem[];
     float* s = smem;           // [npad] sorted column
     float* thr = smem + npad;  // [D][c-1] thresholds
@@ -208,6 +209,25 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
         }
     }
 
+    if (onehot) {
+        for (int pos = tid; pos < tg.Kp; pos += blockDim.x) {
+            int sidx = -1;
+            if (pos < tg.K0p) {
+                if (pos < g.N0) sidx = perm[pos];
+            } else if (pos - tg.K0p < g.N1) {
+                sidx = perm[g.N0 + pos - tg.K0p];
+            }
+            const float xs = sidx >= 0 ? (float)xv[sidx] : 0.0f;
+            for (int d = 0; d < D; ++d) {
+                int code = 0;
+                for (int j = 0; j < cm1; ++j) code += (xs >= thr[d * cm1 + j]);
+                for (int a = 1; a <= cm1; ++a)
+                    onehot[(((size_t)d * M + v) * cm1 + (a - 1)) * tg.Kp + pos] =
+                        (sidx >= 0 && code == a) ? (uint8_t)0x38 : (uint8_t)0;
+            }
+        }
+    }
+
     if (planes) {
         const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
         for (int w = warp; w < g.Ws; w += nwarps) {
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
 
 cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
                               uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
-                              uint8_t* codes, float* thr, cudaStream_t st) {
+                              uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st) {
     int npad = 1;
     while (npad < N) npad <<= 1;
     const size_t smem = sizeof(float) * ((size_t)npad + (size_t)D * (c - 1));
@@ -245,12 +265,12 @@ cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int
         e = cudaFuncSetAttribute(discretize_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<float><<<M, 512, smem, st>>>((const float*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                       planes, codes, thr);
+                                                       planes, codes, thr, onehot, tg);
     } else {
         e = cudaFuncSetAttribute(discretize_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<int8_t><<<M, 512, smem, st>>>((const int8_t*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                        planes, codes, thr);
+                                                        planes, codes, thr, onehot, tg);
     }
     return cudaGetLastError();
 }

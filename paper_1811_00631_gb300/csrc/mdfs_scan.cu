@@ -304,7 +304,9 @@ __global__ void __launch_bounds__(256) k2_kernel(const uint32_t* __restrict__ pl
                 atomicMax(&kmax[TI + tx], pack_key(ig_m, (uint32_t)(d * M + i)));
             }
             if (pairs2) {
-                pairs2[((size_t)dl * M + i) * M + m] = Pair2{X0[0][0], X1[0][0], sh};
+                const Pair2 rec{X0[0][0], X1[0][0], sh};
+                pairs2[((size_t)dl * M + i) * M + m] = rec;
+                pairs2[((size_t)dl * M + m) * M + i] = rec;
             }
             if (sh2) {
                 const size_t pidx = ((size_t)dl * M + i) * M + m;

@@ -174,6 +174,35 @@ def test_k3_large_n_uses_global_tables(cuda):
     assert set(g[1][1].tolist()) == {2, 5}
 
 
+def test_k3_two_class_beyond_shared_tables(cuda):
+    """N too large for the tensor-core triple kernel's shared-memory tables."""
+    rng = np.random.default_rng(23)
+    M, N = 12, 20000
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[4] > 0) ^ (x[7] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, 2, 0.4, 6)
+    ref = oracle.max_ig(codes, y, 2, 3, 0.25)
+    g = _gpu_max_ig(cuda, x, y, 3, 1, 2, 0.4, 0.25, 6)
+    _check(codes, y, 2, 3, 0.25, *g, ref, range(M))
+    assert set(g[1][0].tolist()) == {4, 7}
+
+
+@pytest.mark.parametrize("M,N", [(130, 300), (260, 129), (3, 5)])
+def test_k3_tensor_core_tiles(cuda, M, N):
+    """Two-class triples across several 128-wide a/e tiles, K blocks with
+    padding in both classes, and the smallest sizes."""
+    rng = np.random.default_rng(M + N)
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[M // 2] > 0) ^ (x[M - 1] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    if y.min() == y.max():
+        y[0] ^= 1
+    D = 2
+    codes = oracle.discretize(x, 1, D, 0.5, 8)
+    ref = oracle.max_ig(codes, y, 2, 3, 0.25)
+    g = _gpu_max_ig(cuda, x, y, 3, 1, D, 0.5, 0.25, 8)
+    _check(codes, y, 2, 3, 0.25, *g, ref, range(M))
+
+
 def test_unbalanced_classes_and_int8(cuda):
     rng = np.random.default_rng(9)
     M, N = 40, 777
