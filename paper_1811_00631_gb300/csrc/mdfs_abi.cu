@@ -510,7 +510,9 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         // the tensor-core kernel reports bounded-wait timeouts through this flag
         MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
-        if (ws->host_stats[8] != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in the triple kernel");
+        const int flag = ws->host_stats[8];
+        if (flag & 2) return fail(MDFS_ECUDA, "triple kernel: dynamic shared memory smaller than its table layout");
+        if (flag != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in the triple kernel");
     } else if (oig.staged || otu.staged || odi.staged || st == nullptr) {
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     }

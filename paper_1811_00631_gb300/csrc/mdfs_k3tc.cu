@@ -90,8 +90,17 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int* c1 = cnt1 + (size_t)d * M * 2;
     volatile int* abort = &s_abort;
 
+    // the layout above must fit the dynamic shared memory this launch received
+    uint32_t dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    const bool fits = (size_t)(base - dsmem_raw) + kTabOffset + (size_t)(2 * N + 3) * sizeof(long long) <= dyn_bytes;
+    if (!fits) {
+        sT0 = sT1 = sTB = nullptr;  // never dereferenced: the block aborts below
+    }
+
     if (tid == 0) {
-        s_abort = *(volatile int*)err;  // an earlier block timed out: skip the work
+        // an earlier block failed (skip the work), or the layout has no room (reason 2)
+        s_abort = (*(volatile int*)err ? 1 : 0) | (fits ? 0 : 2);
         s_committed = 0;
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&bar_full[s], 1);
@@ -105,9 +114,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         tc::tmem_alloc(&s_tmem, kTmemCols);
         tc::tmem_relinquish();
     }
-    for (int i = tid; i <= N0; i += kThreads) sT0[i] = tab[i];
-    for (int i = tid; i <= N1; i += kThreads) sT1[i] = tab[np1 + i];
-    for (int i = tid; i <= N; i += kThreads) sTB[i] = tab[2 * np1 + i];
+    if (fits) {
+        for (int i = tid; i <= N0; i += kThreads) sT0[i] = tab[i];
+        for (int i = tid; i <= N1; i += kThreads) sT1[i] = tab[np1 + i];
+        for (int i = tid; i <= N; i += kThreads) sTB[i] = tab[2 * np1 + i];
+    }
     for (int r = tid; r < kTile; r += kThreads) {
         const int e = e0 + r;
         const bool ok = e < M;
@@ -292,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
-    if (tid == 0 && *abort) atomicExch(err, 1);
+    if (tid == 0 && *abort) atomicOr(err, *abort);  // 1: bounded wait gave up, 2: shared layout too small
 }
 
 void build_k3tc_items(int M, std::vector<int2>& items) {
@@ -305,8 +316,9 @@ void build_k3tc_items(int M, std::vector<int2>& items) {
     }
 }
 
+// stages + tables T0[0..N0], T1[0..N1], TB[0..N0+N1] + alignment slack
 size_t k3tc_smem_bytes(int N0, int N1) {
-    return kTabOffset + (size_t)(N0 + N1 + 3) * sizeof(long long) + 1024;
+    return kTabOffset + (size_t)(2 * (N0 + N1) + 3) * sizeof(long long) + 1024;
 }
 
 TcGeom make_tc_geom(int N0, int N1) {
