@@ -17,7 +17,7 @@
 using namespace mdfs;
 
 // dynamic shared memory the tensor-core k = 3 kernel may take (stages + tables)
-static const size_t kK3tcMaxSmem = 218 * 1024;
+static const size_t kK3tcMaxSmem = 212 * 1024;
 
 namespace {
 

@@ -11,14 +11,22 @@
 // the counts are exact integers.  Class-0 and class-1 samples occupy separate
 // K ranges and accumulate into two TMEM accumulators.
 //
-// Block = one (b, 128 a, 128 e) tile, 256 threads:
-//   thread 0   issues the TMA loads of A, B (128B-swizzled) and OH[b] per K block,
-//   all        AND the A tile with OH[b] in shared memory,
-//   thread 32  issues 4 MMAs (K = 32 each) per K block and commits,
-//   all        read the accumulators back (tcgen05.ld) and run the entropy
-//              epilogue: 8-voxel tables by inclusion-exclusion, SH3 from the
-//              fixed-point tables in shared memory, three IG roles, packed max.
-// Every mbarrier wait is bounded; on timeout the block records an error,
+// Persistent, warp-specialised kernel (one CTA per SM, 384 threads):
+//   warp 0       TMA producer: A (a rows), B (e rows), OH[b] row per K block,
+//   warp 1       TMEM owner and MMA issuer (4 MMAs of K = 32 per K block),
+//   warps 2-3    AND the A tile with OH[b] in shared memory (128B swizzle),
+//   warps 4-11   epilogue: tcgen05.ld of both class accumulators, the 8-voxel
+//                tables by inclusion-exclusion, SH3 from fixed-point tables
+//                in shared memory, three IG roles, packed max keys.
+// Four shared-memory stages and two TMEM accumulator buffers (2 x 256
+// columns) let the epilogue of one tile overlap the MMAs of the next.
+//
+// Entropy arithmetic: the FP64-built int64 tables (multiples of 2^-32) are
+// rounded to int32 multiples of 2^-s and summed with wrap-around; the IG
+// difference is exact modulo 2^32 and |IG| 2^s < 2^31 recovers it.  Error per
+// IG <= 25 * 2^-(s+1) (24 table entries and the rounded pair entropy).
+//
+// Every mbarrier wait is bounded; on timeout the kernel records an error,
 // drains its copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -31,18 +39,21 @@ namespace mdfs {
 
 namespace {
 
-constexpr int kTile = 128;               // a rows, e columns
-constexpr int kBK = 128;                 // K bytes (samples) per stage
-constexpr int kStages = 2;
+constexpr int kTile = 128;                    // a rows, e columns
+constexpr int kBK = 128;                      // K bytes (samples) per stage
+constexpr int kStages = 4;
 constexpr uint32_t kTileBytes = kTile * kBK;  // 16 KB
-constexpr uint32_t kTmemCols = 256;      // two classes x 128 columns
-constexpr int kThreads = 256;
+constexpr uint32_t kAccCols = 2 * kTile;      // class 0 and class 1 accumulators
+constexpr uint32_t kTmemCols = 2 * kAccCols;  // double buffer
+constexpr int kThreads = 384;
+constexpr int kMaskWarp0 = 2, kMaskThreads = 64;
+constexpr int kEpiWarp0 = 4, kEpiThreads = 256;
+constexpr int kColsPerWarp = 64;
 constexpr size_t kTabOffset = 2 * kStages * kTileBytes + kStages * kBK;  // after A, B, OH[b] rows
 
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 
-// Waits for completion regardless of an abort (draining in-flight copies/MMAs);
-// still bounded in time.
+// Waits for completion regardless of an abort (draining in-flight work); bounded.
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
     const unsigned long long t0 = tc::global_ns();
     while (!tc::mbar_try_wait(bar, parity))
@@ -57,19 +68,33 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
+// int64 multiple of 2^-32  ->  int32 multiple of 2^-s (round to nearest, mod 2^32)
+__device__ __forceinline__ int fx_narrow(long long v, int s) {
+    const int shift = 32 - s;
+    return (int)((v + (1ll << (shift - 1))) >> shift);
+}
+
+__device__ __forceinline__ int tab32(const int* t, int n, int nmax) { return t[min((unsigned)n, (unsigned)nmax)]; }
+
+struct ColCtx {
+    int n0, n1;    // pair (b, e): class counts of voxel (1, 1)
+    int sh;        // pair (b, e): entropy, int32 fixed point
+    int ne0, ne1;  // single e: class counts of bin 1
+};
+
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     k3tc_kernel(const __grid_constant__ CUtensorMap map_oh, const uint8_t* __restrict__ oh, TcGeom tg, int M, int d0,
-                const int2* __restrict__ items, const long long* __restrict__ tab, const int* __restrict__ cnt1,
-                const Pair2* __restrict__ pairs, unsigned long long* __restrict__ keys, int* __restrict__ err) {
+                int nd, const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
+                const int* __restrict__ cnt1, const Pair2* __restrict__ pairs, unsigned long long* __restrict__ keys,
+                int* __restrict__ err) {
     extern __shared__ uint8_t dsmem_raw[];
-    __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages], bar_done;
+    __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
+    __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort, s_committed;
-    __shared__ Pair2 s_pbe[kTile];
-    __shared__ int2 s_ne[kTile];
-    __shared__ unsigned long long s_ka[kTile], s_ke[kTile], s_kb;
+    __shared__ int s_abort;
+    __shared__ ColCtx s_col[kEpiThreads / 32][kColsPerWarp];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* base = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
@@ -77,93 +102,140 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint8_t* sB = base + kStages * kTileBytes;
     uint8_t* sOHb = base + 2 * kStages * kTileBytes;
     const int N0 = tg.N0, N1 = tg.N1, N = N0 + N1, np1 = N + 1;
-    long long* sT0 = reinterpret_cast<long long*>(base + kTabOffset);
-    long long* sT1 = sT0 + (N0 + 1);
-    long long* sTB = sT1 + (N1 + 1);
-
-    const int2 item = items[blockIdx.x];
-    const int b = item.x;
-    const int a0 = (item.y >> 16) * kTile;
-    const int e0 = b + 1 + (item.y & 0xFFFF) * kTile;
-    const int dl = blockIdx.y, d = d0 + dl;
-    const Pair2* pd = pairs + (size_t)dl * M * M;  // symmetric: [i][m] == [m][i]
-    const int* c1 = cnt1 + (size_t)d * M * 2;
+    int* sT0 = reinterpret_cast<int*>(base + kTabOffset);
+    int* sT1 = sT0 + (N0 + 1);
+    int* sTB = sT1 + (N1 + 1);
     volatile int* abort = &s_abort;
 
     // the layout above must fit the dynamic shared memory this launch received
     uint32_t dyn_bytes;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
-    const bool fits = (size_t)(base - dsmem_raw) + kTabOffset + (size_t)(2 * N + 3) * sizeof(long long) <= dyn_bytes;
-    if (!fits) {
-        sT0 = sT1 = sTB = nullptr;  // never dereferenced: the block aborts below
-    }
+    const bool fits = (size_t)(base - dsmem_raw) + kTabOffset + (size_t)(2 * N + 3) * sizeof(int) <= dyn_bytes;
 
     if (tid == 0) {
-        // an earlier block failed (skip the work), or the layout has no room (reason 2)
+        // an earlier launch failed (skip the work), or the layout has no room (reason 2)
         s_abort = (*(volatile int*)err ? 1 : 0) | (fits ? 0 : 2);
-        s_committed = 0;
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&bar_full[s], 1);
-            tc::mbar_init(&bar_ready[s], kThreads);
+            tc::mbar_init(&bar_ready[s], kMaskThreads);
             tc::mbar_init(&bar_empty[s], 1);
         }
-        tc::mbar_init(&bar_done, 1);
+        for (int j = 0; j < 2; ++j) {
+            tc::mbar_init(&bar_tfull[j], 1);
+            tc::mbar_init(&bar_tempty[j], kEpiThreads);
+        }
+        tc::mbar_init(&bar_drain, 1);
         tc::mbar_fence_init();
     }
-    if (warp == 0) {
+    if (warp == 1) {
         tc::tmem_alloc(&s_tmem, kTmemCols);
         tc::tmem_relinquish();
     }
     if (fits) {
-        for (int i = tid; i <= N0; i += kThreads) sT0[i] = tab[i];
-        for (int i = tid; i <= N1; i += kThreads) sT1[i] = tab[np1 + i];
-        for (int i = tid; i <= N; i += kThreads) sTB[i] = tab[2 * np1 + i];
+        for (int i = tid; i <= N0; i += kThreads) sT0[i] = fx_narrow(tab[i], fbits);
+        for (int i = tid; i <= N1; i += kThreads) sT1[i] = fx_narrow(tab[np1 + i], fbits);
+        for (int i = tid; i <= N; i += kThreads) sTB[i] = fx_narrow(tab[2 * np1 + i], fbits);
     }
-    for (int r = tid; r < kTile; r += kThreads) {
-        const int e = e0 + r;
-        const bool ok = e < M;
-        s_pbe[r] = ok ? pd[(size_t)b * M + e] : Pair2{0, 0, 0};
-        s_ne[r] = ok ? make_int2(c1[2 * e], c1[2 * e + 1]) : make_int2(0, 0);
-        s_ke[r] = 0ull;
-        s_ka[r] = 0ull;
-    }
-    if (tid == 0) s_kb = 0ull;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
+    const int n_tiles = n_items * nd;
+    const int nkb = tg.nkb;
 
-    // ---------------- main loop: TMA -> mask -> MMA -------------------------
-    int pending = 0;                 // thread 0: stages with a TMA not yet observed complete
-    uint32_t pending_use[kStages] = {0, 0};
-    bool mma_issued = false;         // thread 32
-    const uint32_t idesc = tc::idesc_e4m3_f32(kTile, kTile);
-    if (!*abort) {
-        for (int kb = 0; kb < tg.nkb; ++kb) {
-            if (*abort) break;
-            const int s = kb % kStages;
-            const uint32_t use = (uint32_t)(kb / kStages);
-            if (tid == 0) {
+    if (warp == 0) {
+        // ------------------------------ TMA producer ------------------------------
+        if (lane == 0 && !*abort) {
+            uint32_t g = 0;  // running K-block counter across this CTA's tiles
+            int pend_mask = 0;
+            uint32_t pend_use[kStages] = {0, 0, 0, 0};
+            for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
+                const int2 item = items[t % n_items];
+                const int d = d0 + t / n_items;
+                const int b = item.x, a0 = (item.y >> 16) * kTile, e0 = b + 1 + (item.y & 0xFFFF) * kTile;
+                const uint8_t* ohb = oh + ((size_t)d * M + b) * tg.Kp;
                 bool ok = true;
-                if (kb >= kStages) ok = tc::mbar_wait(&bar_empty[s], (use - 1) & 1, abort);
-                if (ok) {
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t use = g / kStages;
+                    if (use > 0 && !tc::mbar_wait(&bar_empty[s], (use - 1) & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
                     tc::mbar_arrive_expect_tx(&bar_full[s], 2 * kTileBytes + kBK);
                     tc::tma_load_3d(sA + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, a0, d);
                     tc::tma_load_3d(sB + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, e0, d);
-                    tc::bulk_load(sOHb + s * kBK, oh + ((size_t)d * M + b) * tg.Kp + (size_t)kb * kBK, kBK,
-                                  &bar_full[s]);
-                    pending |= 1 << s;
-                    pending_use[s] = use;
+                    tc::bulk_load(sOHb + s * kBK, ohb + (size_t)kb * kBK, kBK, &bar_full[s]);
+                    pend_mask |= 1 << s;
+                    pend_use[s] = use;
                 }
+                if (!ok) break;
             }
-            if (!tc::mbar_wait(&bar_full[s], use & 1, abort)) break;
-            if (tid == 0) pending &= ~(1 << s);
-            {
+            // the newest copy of every stage completes its phase; waiting for
+            // those (bounded) covers every copy this thread issued
+            for (int s = 0; s < kStages; ++s)
+                if (pend_mask & (1 << s)) mbar_drain(&bar_full[s], pend_use[s] & 1);
+        }
+    } else if (warp == 1) {
+        // ------------------------------ MMA issuer --------------------------------
+        if (lane == 0 && !*abort) {
+            const uint32_t idesc = tc::idesc_e4m3_f32(kTile, kTile);
+            uint32_t g = 0;
+            int i = 0;
+            bool issued = false;
+            for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
+                const int buf = i & 1;
+                const uint32_t tuse = (uint32_t)(i >> 1);
+                if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort)) break;
+                tc::tc_fence_after();
+                const uint32_t dbase = tmem + (uint32_t)buf * kAccCols;
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t use = g / kStages;
+                    if (!tc::mbar_wait(&bar_ready[s], use & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t d_tmem = dbase + (kb >= tg.nkb0 ? (uint32_t)kTile : 0u);
+                    const uint32_t a_addr = tc::smem_u32(sA + s * kTileBytes);
+                    const uint32_t b_addr = tc::smem_u32(sB + s * kTileBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 32; ++kk) {
+                        const uint32_t acc = (kb != 0 && kb != tg.nkb0) || kk > 0;
+                        tc::mma_f8(d_tmem, tc::sw128_kmajor_desc(a_addr + 32 * kk),
+                                   tc::sw128_kmajor_desc(b_addr + 32 * kk), idesc, acc);
+                    }
+                    tc::mma_commit(&bar_empty[s]);
+                    issued = true;
+                }
+                if (!ok) break;
+                tc::mma_commit(&bar_tfull[buf]);
+            }
+            // every MMA this thread issued completes before TMEM and the stages are released
+            if (issued) {
+                tc::mma_commit(&bar_drain);
+                mbar_drain(&bar_drain, 0);
+            }
+        }
+    } else if (warp < kEpiWarp0) {
+        // ------------------------------ A-tile maskers ----------------------------
+        const int mt = tid - kMaskWarp0 * 32;
+        uint32_t g = 0;
+        for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
+            bool ok = true;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int s = (int)(g % kStages);
+                const uint32_t use = g / kStages;
+                if (!tc::mbar_wait(&bar_full[s], use & 1, abort)) {
+                    ok = false;
+                    break;
+                }
                 uint8_t* A = sA + s * kTileBytes;
                 const uint8_t* mrow = sOHb + s * kBK;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int idx = tid + kThreads * i;
+#pragma unroll 4
+                for (int idx = mt; idx < kTile * 8; idx += kMaskThreads) {
                     const int r = idx >> 3, slot = idx & 7;
                     const int j = slot ^ (r & 7);  // 128-byte swizzle: chunk slot = chunk ^ (row % 8)
                     uint4* p = reinterpret_cast<uint4*>(A + r * kBK + slot * 16);
@@ -175,134 +247,151 @@ __global__ void __launch_bounds__(kThreads, 2)
                     v.w &= m.w;
                     *p = v;
                 }
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(&bar_ready[s]);
             }
-            tc::fence_proxy_async_smem();
-            tc::mbar_arrive(&bar_ready[s]);
-            if (tid == 32) {
-                if (!tc::mbar_wait(&bar_ready[s], use & 1, abort)) break;
-                tc::tc_fence_after();
-                const uint32_t d_tmem = tmem + (kb >= tg.nkb0 ? (uint32_t)kTile : 0u);
-                const uint32_t a_addr = tc::smem_u32(sA + s * kTileBytes);
-                const uint32_t b_addr = tc::smem_u32(sB + s * kTileBytes);
-#pragma unroll
-                for (int kk = 0; kk < kBK / 32; ++kk) {
-                    const uint32_t acc = (kb != 0 && kb != tg.nkb0) || kk > 0;
-                    tc::mma_f8(d_tmem, tc::sw128_kmajor_desc(a_addr + 32 * kk), tc::sw128_kmajor_desc(b_addr + 32 * kk),
-                               idesc, acc);
-                }
-                tc::mma_commit(&bar_empty[s]);
-                mma_issued = true;
-            }
+            if (!ok) break;
         }
-    }
-    // ---------------- drain -------------------------------------------------
-    if (tid == 32) {
-        if (mma_issued) tc::mma_commit(&bar_done);
-        s_committed = mma_issued ? 1 : 0;
-    }
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s)
-            if (pending & (1 << s)) mbar_drain(&bar_full[s], pending_use[s] & 1);
-    }
-    __syncthreads();
-    if (s_committed) mbar_drain(&bar_done, 0);
-    tc::tc_fence_after();
-    __syncthreads();
-
-    // ---------------- epilogue ----------------------------------------------
-    if (!*abort && s_committed) {
-        const int q = warp & 3, h = warp >> 2;
+    } else {
+        // ------------------------------ epilogue ----------------------------------
+        const int ew = warp - kEpiWarp0;      // 0..7
+        const int q = warp & 3, h = ew >> 2;  // TMEM lane quarter (warp % 4), column half
         const int row = 32 * q + lane;
-        const int a = a0 + row;
-        const bool arow = a < b;
-        const Pair2 pab = arow ? pd[(size_t)b * M + a] : Pair2{0, 0, 0};
-        const int na0 = arow ? c1[2 * a] : 0, na1 = arow ? c1[2 * a + 1] : 0;
-        const int nb0 = c1[2 * b], nb1 = c1[2 * b + 1];
-        const uint32_t dM = (uint32_t)d * (uint32_t)M;
-        unsigned long long ka = 0ull, kbest = 0ull;
-#pragma unroll 1
-        for (int chunk = 0; chunk < 2; ++chunk) {
-            const int cbase = 64 * h + 32 * chunk;
-            uint32_t r0[32], r1[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cbase, r0);
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTile + cbase), r1);
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = cbase + j;
-                const int e = e0 + col;
-                unsigned long long k_e = 0ull;
-                if (arow && e < M) {
-                    const int x0 = (int)__uint_as_float(r0[j]);
-                    const int x1 = (int)__uint_as_float(r1[j]);
-                    const Pair2 pbe = s_pbe[col];
-                    const int2 ne = s_ne[col];
-                    const Pair2 pae = pd[(size_t)e * M + a];
-                    long long sh3 = 0;
-                    int t[8];
-                    {
-                        int v[8];
-                        v[7] = x0;
-                        v[3] = pbe.n0 - x0;
-                        v[5] = pae.n0 - x0;
-                        v[6] = pab.n0 - x0;
-                        v[1] = ne.x - pae.n0 - pbe.n0 + x0;
-                        v[2] = nb0 - pab.n0 - pbe.n0 + x0;
-                        v[4] = na0 - pab.n0 - pae.n0 + x0;
-                        v[0] = N0 - na0 - nb0 - ne.x + pab.n0 + pae.n0 + pbe.n0 - x0;
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            sh3 -= sT0[clamp_count(v[u], N0)];
-                            t[u] = v[u];
-                        }
-                    }
-                    {
-                        int v[8];
-                        v[7] = x1;
-                        v[3] = pbe.n1 - x1;
-                        v[5] = pae.n1 - x1;
-                        v[6] = pab.n1 - x1;
-                        v[1] = ne.y - pae.n1 - pbe.n1 + x1;
-                        v[2] = nb1 - pab.n1 - pbe.n1 + x1;
-                        v[4] = na1 - pab.n1 - pae.n1 + x1;
-                        v[0] = N1 - na1 - nb1 - ne.y + pab.n1 + pae.n1 + pbe.n1 - x1;
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            sh3 -= sT1[clamp_count(v[u], N1)];
-                            t[u] += v[u];
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) sh3 += sTB[clamp_count(t[u], N)];
-                    // IG(a | b,e), IG(b | a,e), IG(e | a,b)
-                    const unsigned long long k_a =
-                        pack_key(fx_to_float(pbe.sh - sh3), (dM + (uint32_t)b) * (uint32_t)M + (uint32_t)e);
-                    const unsigned long long k_b =
-                        pack_key(fx_to_float(pae.sh - sh3), (dM + (uint32_t)a) * (uint32_t)M + (uint32_t)e);
-                    k_e = pack_key(fx_to_float(pab.sh - sh3), (dM + (uint32_t)a) * (uint32_t)M + (uint32_t)b);
-                    ka = umax64(ka, k_a);
-                    kbest = umax64(kbest, k_b);
+        const float inv_scale = __int_as_float((127 - fbits) << 23);  // 2^-fbits
+        ColCtx* cc = s_col[ew];
+        int i = 0;
+        for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            const uint32_t tuse = (uint32_t)(i >> 1);
+            const int2 item = items[t % n_items];
+            const int dl = t / n_items, d = d0 + dl;
+            const int b = item.x, a0 = (item.y >> 16) * kTile, e0 = b + 1 + (item.y & 0xFFFF) * kTile;
+            const Pair2* pd = pairs + (size_t)dl * M * M;  // symmetric: [i][m] == [m][i]
+            const int* c1 = cnt1 + (size_t)d * M * 2;
+            const int ecol0 = e0 + kColsPerWarp * h;
+            const int ncols = min(kColsPerWarp, M - ecol0);
+            // column context of this warp's columns: pair (b, e) and single e
+            __syncwarp();
+            for (int cidx = lane; cidx < kColsPerWarp; cidx += 32) {
+                const int e = ecol0 + cidx;
+                ColCtx x{0, 0, 0, 0, 0};
+                if (cidx < ncols) {
+                    const Pair2 p = pd[(size_t)b * M + e];
+                    x.n0 = p.n0;
+                    x.n1 = p.n1;
+                    x.sh = fx_narrow(p.sh, fbits);
+                    x.ne0 = c1[2 * e];
+                    x.ne1 = c1[2 * e + 1];
                 }
-                const unsigned long long m = warp_max_key(k_e);
-                if (lane == 0 && m) atomicMax(&s_ke[col], m);
+                cc[cidx] = x;
             }
+            __syncwarp();
+            // row context: pair (a, b), single a, and per-row constants
+            const int a = a0 + row;
+            const bool arow = a < b;
+            const bool warp_rows = (a0 + 32 * q) < b;  // some row of this warp is valid
+            int pab0 = 0, pab1 = 0, shab = 0, na0 = 0, na1 = 0;
+            if (arow) {
+                const Pair2 p = pd[(size_t)b * M + a];
+                pab0 = p.n0;
+                pab1 = p.n1;
+                shab = fx_narrow(p.sh, fbits);
+                na0 = c1[2 * a];
+                na1 = c1[2 * a + 1];
+            }
+            const int nb0 = c1[2 * b], nb1 = c1[2 * b + 1];
+            const int kab0 = N0 - na0 - nb0 + pab0, kab1 = N1 - na1 - nb1 + pab1;
+            const uint32_t dM = (uint32_t)d * (uint32_t)M;
+            const uint32_t idx_a = (dM + (uint32_t)b) * (uint32_t)M;   // role a: partners (b, e)
+            const uint32_t idx_be = (dM + (uint32_t)a) * (uint32_t)M;  // roles b: (a, e) and e: (a, b)
+
+            if (!tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort)) break;
+            tc::tc_fence_after();
+            unsigned long long ka = 0ull, kbest = 0ull;
+            if (warp_rows && ncols > 0) {
+                const uint32_t taddr =
+                    tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kAccCols + (uint32_t)(kColsPerWarp * h);
+#pragma unroll 1
+                for (int c0 = 0; c0 < ncols; c0 += 8) {
+                    uint32_t r0[8], r1[8];
+                    tc::tmem_ld8(taddr + (uint32_t)c0, r0);
+                    tc::tmem_ld8(taddr + (uint32_t)(kTile + c0), r1);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int col = c0 + j;
+                        const int e = ecol0 + col;
+                        unsigned long long k_e = 0ull;
+                        if (arow && col < ncols) {
+                            const ColCtx cx = cc[col];
+                            const Pair2 pae = pd[(size_t)e * M + a];
+                            const int shae = fx_narrow(pae.sh, fbits);
+                            int sh3, t0, t1, t2, t3, t4, t5, t6, t7;
+                            {
+                                const int x = (int)__uint_as_float(r0[j]);
+                                const int c011 = cx.n0 - x, c101 = pae.n0 - x, c110 = pab0 - x;
+                                const int c001 = cx.ne0 - pae.n0 - c011;
+                                const int c010 = nb0 - pab0 - c011;
+                                const int c100 = na0 - pab0 - c101;
+                                const int c000 = kab0 - cx.ne0 + pae.n0 + c011;
+                                sh3 = -(tab32(sT0, x, N0) + tab32(sT0, c011, N0) + tab32(sT0, c101, N0) +
+                                        tab32(sT0, c110, N0) + tab32(sT0, c001, N0) + tab32(sT0, c010, N0) +
+                                        tab32(sT0, c100, N0) + tab32(sT0, c000, N0));
+                                t7 = x;
+                                t3 = c011;
+                                t5 = c101;
+                                t6 = c110;
+                                t1 = c001;
+                                t2 = c010;
+                                t4 = c100;
+                                t0 = c000;
+                            }
+                            {
+                                const int x = (int)__uint_as_float(r1[j]);
+                                const int c011 = cx.n1 - x, c101 = pae.n1 - x, c110 = pab1 - x;
+                                const int c001 = cx.ne1 - pae.n1 - c011;
+                                const int c010 = nb1 - pab1 - c011;
+                                const int c100 = na1 - pab1 - c101;
+                                const int c000 = kab1 - cx.ne1 + pae.n1 + c011;
+                                sh3 -= tab32(sT1, x, N1) + tab32(sT1, c011, N1) + tab32(sT1, c101, N1) +
+                                       tab32(sT1, c110, N1) + tab32(sT1, c001, N1) + tab32(sT1, c010, N1) +
+                                       tab32(sT1, c100, N1) + tab32(sT1, c000, N1);
+                                t7 += x;
+                                t3 += c011;
+                                t5 += c101;
+                                t6 += c110;
+                                t1 += c001;
+                                t2 += c010;
+                                t4 += c100;
+                                t0 += c000;
+                            }
+                            sh3 += tab32(sTB, t0, N) + tab32(sTB, t1, N) + tab32(sTB, t2, N) + tab32(sTB, t3, N) +
+                                   tab32(sTB, t4, N) + tab32(sTB, t5, N) + tab32(sTB, t6, N) + tab32(sTB, t7, N);
+                            // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around differences
+                            const float ig_a = (float)(cx.sh - sh3) * inv_scale;
+                            const float ig_b = (float)(shae - sh3) * inv_scale;
+                            const float ig_e = (float)(shab - sh3) * inv_scale;
+                            ka = umax64(ka, pack_key(ig_a, idx_a + (uint32_t)e));
+                            kbest = umax64(kbest, pack_key(ig_b, idx_be + (uint32_t)e));
+                            k_e = pack_key(ig_e, idx_be + (uint32_t)b);
+                        }
+                        const unsigned long long m = warp_max_key(k_e);
+                        if (lane == 0 && m) atomicMax(keys + e, m);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&bar_tempty[buf]);
+            if (ka) atomicMax(keys + a, ka);
+            const unsigned long long mb = warp_max_key(kbest);
+            if (lane == 0 && mb) atomicMax(keys + b, mb);
         }
-        if (ka) atomicMax(&s_ka[row], ka);
-        const unsigned long long mb = warp_max_key(kbest);
-        if (lane == 0 && mb) atomicMax(&s_kb, mb);
     }
-    __syncthreads();
-    if (!*abort && s_committed) {
-        if (tid == 0 && s_kb) atomicMax(keys + b, s_kb);
-        for (int r = tid; r < kTile; r += kThreads) {
-            if (s_ka[r]) atomicMax(keys + a0 + r, s_ka[r]);
-            if (s_ke[r]) atomicMax(keys + e0 + r, s_ke[r]);
-        }
-    }
-    // ---------------- teardown ----------------------------------------------
+
+    // ---------------- teardown ------------------------------------------------
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 1) tc::tmem_dealloc(tmem, kTmemCols);
     if (tid == 0 && *abort) atomicOr(err, *abort);  // 1: bounded wait gave up, 2: shared layout too small
 }
 
@@ -316,9 +405,18 @@ void build_k3tc_items(int M, std::vector<int2>& items) {
     }
 }
 
-// stages + tables T0[0..N0], T1[0..N1], TB[0..N0+N1] + alignment slack
+// stages + int32 tables T0[0..N0], T1[0..N1], TB[0..N0+N1] + alignment slack
 size_t k3tc_smem_bytes(int N0, int N1) {
-    return kTabOffset + (size_t)(2 * (N0 + N1) + 3) * sizeof(long long) + 1024;
+    return kTabOffset + (size_t)(2 * (N0 + N1) + 3) * sizeof(int) + 1024;
+}
+
+// Largest fraction bits s <= 20 with |IG| 2^s < 2^31 for N samples
+// (|IG| <= N ln 2 plus pseudocount terms, bounded here by N ln 2 + 64).
+int k3tc_fraction_bits(int N) {
+    const double bound = (double)N * 0.6931471805599453 + 64.0;
+    int s = 20;
+    while (s > 1 && bound * (double)(1 << s) >= 2147483647.0) --s;
+    return s;
 }
 
 TcGeom make_tc_geom(int N0, int N1) {
@@ -337,7 +435,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     if (!fn) {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
         else
@@ -369,8 +468,14 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
     cudaError_t e = cudaFuncSetAttribute(k3tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(n_items, nd);
-    k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, items, tab, cnt1, pairs, keys, err);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long n_tiles = (long long)n_items * nd;
+    if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
+    k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab,
+                                              k3tc_fraction_bits(tg.N0 + tg.N1), cnt1, pairs, keys, err);
     return cudaGetLastError();
 }
 
