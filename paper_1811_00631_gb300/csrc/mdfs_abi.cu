@@ -435,10 +435,11 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
     bool check_err = false;
     if (k == 2) {
-        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, st));
+        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st));
     } else if (use_tc3) {
-        // two classes: symmetric Pair2 records and the tcgen05 triple kernel
-        const size_t per_disc = (size_t)M * M * sizeof(Pair2);
+        // two classes: symmetric 8-byte pair records and the tcgen05 triple kernel
+        const size_t per_disc = (size_t)M * M * sizeof(PairC);
+        const int fbits = k3tc_fraction_bits(N);
         size_t budget = (size_t)4 << 30;
         if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
         int nd = (int)(budget / per_disc);
@@ -462,9 +463,10 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
-                                                   nullptr, (Pair2*)ws->pairs2.p, st));
+                                                   nullptr, (PairC*)ws->pairs2.p, fbits, st));
             MDFS_LAUNCH("k3", st, launch_k3tc(map, onehot, tg, M, d0, nn, (const int2*)ws->items2.p, ws->n_items2,
-                                              tab, cnt1, (const Pair2*)ws->pairs2.p, keys, (int*)ws->err.p, st));
+                                              tab, fbits, cnt1, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p,
+                                              st));
         }
         check_err = true;
     } else if (k == 3) {
@@ -490,7 +492,7 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
-                                                   (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, st));
+                                                   (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
             MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p, ws->n_items, tab, cnt1,
                                         (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
         }

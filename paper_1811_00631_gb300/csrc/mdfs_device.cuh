@@ -53,6 +53,12 @@ __device__ __forceinline__ float fx_to_float(long long v) {
     return __ll2float_rn(v) * 2.3283064365386963e-10f;  // exact scaling by 2^-32
 }
 
+// int64 multiple of 2^-32  ->  int32 multiple of 2^-s (round to nearest, mod 2^32)
+__device__ __forceinline__ int fx_narrow(long long v, int s) {
+    const int shift = 32 - s;
+    return (int)((v + (1ll << (shift - 1))) >> shift);
+}
+
 // Counts index the [0, n] tables; a count outside that range cannot arise from
 // consistent inputs, and clamping keeps every table read inside its buffer.
 __device__ __forceinline__ int clamp_count(int v, int n) { return min(max(v, 0), n); }

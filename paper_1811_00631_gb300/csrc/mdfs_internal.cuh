@@ -45,11 +45,12 @@ struct TcGeom {
     int N0, N1, K0p, Kp, nkb0, nkb;
 };
 
-// Pair record of the two-class (c = 2) k = 3 path: class counts of the voxel
-// (1, 1) of the pair and its regularised entropy SH (fixed point).
-struct __align__(16) Pair2 {
-    int n0, n1;
-    long long sh;
+// Pair record of the two-class (c = 2) k = 3 path, 8 bytes: class counts of
+// the voxel (1, 1) of the pair (n0 | n1 << 16; counts <= 32768) and its
+// regularised entropy SH as an int32 multiple of 2^-fbits (wrap-around).
+struct __align__(8) PairC {
+    uint32_t cnt;
+    int sh;
 };
 
 // ---- launchers (all asynchronous on `st`) -----------------------------------
@@ -79,11 +80,12 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 // Pair pass over discretisations [d0, d0 + nd).  keys != NULL: fold the two IG
 // roles of every pair into keys (k = 2).  sh2/cnt2 != NULL: store the pair
 // tables (k = 3): sh2 [nd][M][M] i64, cnt2 [nd][M][M][(c-1)^2][2] i32 (i < m only).
-// pairs2 != NULL (c = 2 only): store Pair2 records [nd][M][M] instead, at
-// both [i][m] and [m][i].
+// pairs2 != NULL (c = 2 only): store PairC records [nd][M][M] instead, at
+// both [i][m] and [m][i], with the entropy in fbits fraction bits.
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd,
                       const long long* tab, const int* cnt1, const long long* sh1,
-                      unsigned long long* keys, long long* sh2, int* cnt2, Pair2* pairs2, cudaStream_t st);
+                      unsigned long long* keys, long long* sh2, int* cnt2, PairC* pairs2, int fbits,
+                      cudaStream_t st);
 
 // Triple pass over discretisations [d0, d0 + nd), using the pair tables of the
 // same chunk.  Folds the three IG roles of every triple into keys.  items[j] =
@@ -95,15 +97,6 @@ cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, i
                             int n_items, const long long* tab, const int* cnt1, const long long* sh2,
                             const int* cnt2, unsigned long long* keys, cudaStream_t st);
 
-// Two-class k = 3 kernel (middle-variable tiles, Harley-Seal counting, tables
-// in shared memory).  items from build_k3c2_items; needs k3c2_smem_bytes(N) of
-// dynamic shared memory.
-void build_k3c2_items(int M, std::vector<int2>& items);
-size_t k3c2_smem_bytes(int N);
-cudaError_t launch_k3c2(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
-                        const long long* tab, const int* cnt1, const Pair2* pairs, unsigned long long* keys,
-                        cudaStream_t st);
-
 // Two-class k = 3 kernel on the tensor cores (tcgen05 kind::f8f6f4): one-hot
 // operands through TMA, counts in TMEM, fused entropy epilogue.  pairs must be
 // symmetric ([i][m] and [m][i] both written).  err: device flag set on a
@@ -111,10 +104,11 @@ cudaError_t launch_k3c2(const uint32_t* planes, PlaneGeom g, int M, int d0, int 
 TcGeom make_tc_geom(int N0, int N1);
 void build_k3tc_items(int M, std::vector<int2>& items);
 size_t k3tc_smem_bytes(int N0, int N1);
+int k3tc_fraction_bits(int N);
 cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D, int Kp);
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
-                        const int2* items, int n_items, const long long* tab, const int* cnt1, const Pair2* pairs,
-                        unsigned long long* keys, int* err, cudaStream_t st);
+                        const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1,
+                        const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st);
 
 // keys [M] -> ig [M] f32, tuples [M][k-1] i32 (NULL ok), disc [M] i32 (NULL ok).
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,

@@ -68,12 +68,6 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-// int64 multiple of 2^-32  ->  int32 multiple of 2^-s (round to nearest, mod 2^32)
-__device__ __forceinline__ int fx_narrow(long long v, int s) {
-    const int shift = 32 - s;
-    return (int)((v + (1ll << (shift - 1))) >> shift);
-}
-
 __device__ __forceinline__ int tab32(const int* t, int n, int nmax) { return t[min((unsigned)n, (unsigned)nmax)]; }
 
 struct ColCtx {
@@ -87,7 +81,7 @@ struct ColCtx {
 __global__ void __launch_bounds__(kThreads, 1)
     k3tc_kernel(const __grid_constant__ CUtensorMap map_oh, const uint8_t* __restrict__ oh, TcGeom tg, int M, int d0,
                 int nd, const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
-                const int* __restrict__ cnt1, const Pair2* __restrict__ pairs, unsigned long long* __restrict__ keys,
+                const int* __restrict__ cnt1, const PairC* __restrict__ pairs, unsigned long long* __restrict__ keys,
                 int* __restrict__ err) {
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
@@ -266,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int2 item = items[t % n_items];
             const int dl = t / n_items, d = d0 + dl;
             const int b = item.x, a0 = (item.y >> 16) * kTile, e0 = b + 1 + (item.y & 0xFFFF) * kTile;
-            const Pair2* pd = pairs + (size_t)dl * M * M;  // symmetric: [i][m] == [m][i]
+            const PairC* pd = pairs + (size_t)dl * M * M;  // symmetric: [i][m] == [m][i]
             const int* c1 = cnt1 + (size_t)d * M * 2;
             const int ecol0 = e0 + kColsPerWarp * h;
             const int ncols = min(kColsPerWarp, M - ecol0);
@@ -276,10 +270,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int e = ecol0 + cidx;
                 ColCtx x{0, 0, 0, 0, 0};
                 if (cidx < ncols) {
-                    const Pair2 p = pd[(size_t)b * M + e];
-                    x.n0 = p.n0;
-                    x.n1 = p.n1;
-                    x.sh = fx_narrow(p.sh, fbits);
+                    const PairC p = pd[(size_t)b * M + e];
+                    x.n0 = (int)(p.cnt & 0xFFFFu);
+                    x.n1 = (int)(p.cnt >> 16);
+                    x.sh = p.sh;
                     x.ne0 = c1[2 * e];
                     x.ne1 = c1[2 * e + 1];
                 }
@@ -292,10 +286,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool warp_rows = (a0 + 32 * q) < b;  // some row of this warp is valid
             int pab0 = 0, pab1 = 0, shab = 0, na0 = 0, na1 = 0;
             if (arow) {
-                const Pair2 p = pd[(size_t)b * M + a];
-                pab0 = p.n0;
-                pab1 = p.n1;
-                shab = fx_narrow(p.sh, fbits);
+                const PairC p = pd[(size_t)b * M + a];
+                pab0 = (int)(p.cnt & 0xFFFFu);
+                pab1 = (int)(p.cnt >> 16);
+                shab = p.sh;
                 na0 = c1[2 * a];
                 na1 = c1[2 * a + 1];
             }
@@ -304,6 +298,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
             const uint32_t idx_a = (dM + (uint32_t)b) * (uint32_t)M;   // role a: partners (b, e)
             const uint32_t idx_be = (dM + (uint32_t)a) * (uint32_t)M;  // roles b: (a, e) and e: (a, b)
+            // pair (a, e) records of the first 8 columns, fetched before the accumulators are ready
+            const PairC* prow = pd + (size_t)ecol0 * M + (arow ? a : 0);  // column e -> prow[(e - ecol0) * M]
+            PairC pnext[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) pnext[j] = (arow && j < ncols) ? prow[(size_t)j * M] : PairC{0u, 0};
 
             if (!tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort)) break;
             tc::tc_fence_after();
@@ -316,6 +315,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint32_t r0[8], r1[8];
                     tc::tmem_ld8(taddr + (uint32_t)c0, r0);
                     tc::tmem_ld8(taddr + (uint32_t)(kTile + c0), r1);
+                    PairC pcur[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        pcur[j] = pnext[j];
+                        const int cn = c0 + 8 + j;
+                        pnext[j] = (arow && cn < ncols) ? prow[(size_t)cn * M] : PairC{0u, 0};
+                    }
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -324,16 +330,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         unsigned long long k_e = 0ull;
                         if (arow && col < ncols) {
                             const ColCtx cx = cc[col];
-                            const Pair2 pae = pd[(size_t)e * M + a];
-                            const int shae = fx_narrow(pae.sh, fbits);
+                            const int pae0 = (int)(pcur[j].cnt & 0xFFFFu), pae1 = (int)(pcur[j].cnt >> 16);
                             int sh3, t0, t1, t2, t3, t4, t5, t6, t7;
                             {
                                 const int x = (int)__uint_as_float(r0[j]);
-                                const int c011 = cx.n0 - x, c101 = pae.n0 - x, c110 = pab0 - x;
-                                const int c001 = cx.ne0 - pae.n0 - c011;
+                                const int c011 = cx.n0 - x, c101 = pae0 - x, c110 = pab0 - x;
+                                const int c001 = cx.ne0 - pae0 - c011;
                                 const int c010 = nb0 - pab0 - c011;
                                 const int c100 = na0 - pab0 - c101;
-                                const int c000 = kab0 - cx.ne0 + pae.n0 + c011;
+                                const int c000 = kab0 - cx.ne0 + pae0 + c011;
                                 sh3 = -(tab32(sT0, x, N0) + tab32(sT0, c011, N0) + tab32(sT0, c101, N0) +
                                         tab32(sT0, c110, N0) + tab32(sT0, c001, N0) + tab32(sT0, c010, N0) +
                                         tab32(sT0, c100, N0) + tab32(sT0, c000, N0));
@@ -348,11 +353,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                             {
                                 const int x = (int)__uint_as_float(r1[j]);
-                                const int c011 = cx.n1 - x, c101 = pae.n1 - x, c110 = pab1 - x;
-                                const int c001 = cx.ne1 - pae.n1 - c011;
+                                const int c011 = cx.n1 - x, c101 = pae1 - x, c110 = pab1 - x;
+                                const int c001 = cx.ne1 - pae1 - c011;
                                 const int c010 = nb1 - pab1 - c011;
                                 const int c100 = na1 - pab1 - c101;
-                                const int c000 = kab1 - cx.ne1 + pae.n1 + c011;
+                                const int c000 = kab1 - cx.ne1 + pae1 + c011;
                                 sh3 -= tab32(sT1, x, N1) + tab32(sT1, c011, N1) + tab32(sT1, c101, N1) +
                                        tab32(sT1, c110, N1) + tab32(sT1, c001, N1) + tab32(sT1, c010, N1) +
                                        tab32(sT1, c100, N1) + tab32(sT1, c000, N1);
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                    tab32(sTB, t4, N) + tab32(sTB, t5, N) + tab32(sTB, t6, N) + tab32(sTB, t7, N);
                             // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around differences
                             const float ig_a = (float)(cx.sh - sh3) * inv_scale;
-                            const float ig_b = (float)(shae - sh3) * inv_scale;
+                            const float ig_b = (float)(pcur[j].sh - sh3) * inv_scale;
                             const float ig_e = (float)(shab - sh3) * inv_scale;
                             ka = umax64(ka, pack_key(ig_a, idx_a + (uint32_t)e));
                             kbest = umax64(kbest, pack_key(ig_b, idx_be + (uint32_t)e));
@@ -462,8 +467,8 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 }
 
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
-                        const int2* items, int n_items, const long long* tab, const int* cnt1, const Pair2* pairs,
-                        unsigned long long* keys, int* err, cudaStream_t st) {
+                        const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1,
+                        const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
     cudaError_t e = cudaFuncSetAttribute(k3tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -474,8 +479,8 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     const long long n_tiles = (long long)n_items * nd;
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
-    k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab,
-                                              k3tc_fraction_bits(tg.N0 + tg.N1), cnt1, pairs, keys, err);
+    k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, pairs, keys,
+                                              err);
     return cudaGetLastError();
 }
 

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k2_kernel(const uint32_t* __restrict__ pl
                                                  int ntile, const long long* __restrict__ tab,
                                                  const int* __restrict__ cnt1, const long long* __restrict__ sh1,
                                                  unsigned long long* __restrict__ keys, long long* __restrict__ sh2,
-                                                 int* __restrict__ cnt2, Pair2* __restrict__ pairs2) {
+                                                 int* __restrict__ cnt2, PairC* __restrict__ pairs2, int fbits) {
     constexpr int P = C - 1, TI = 32, WC = 32, LD = WC + 1;
     __shared__ uint32_t si[P][TI][LD];
     __shared__ uint32_t sm[P][TI][LD];
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k2_kernel(const uint32_t* __restrict__ pl
                 atomicMax(&kmax[TI + tx], pack_key(ig_m, (uint32_t)(d * M + i)));
             }
             if (pairs2) {
-                const Pair2 rec{X0[0][0], X1[0][0], sh};
+                const PairC rec{(uint32_t)X0[0][0] | ((uint32_t)X1[0][0] << 16), fx_narrow(sh, fbits)};
                 pairs2[((size_t)dl * M + i) * M + m] = rec;
                 pairs2[((size_t)dl * M + m) * M + i] = rec;
             }
@@ -585,15 +585,15 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd, const long long* tab,
                       const int* cnt1, const long long* sh1, unsigned long long* keys, long long* sh2, int* cnt2,
-                      Pair2* pairs2, cudaStream_t st) {
+                      PairC* pairs2, int fbits, cudaStream_t st) {
     if (pairs2 && c != 2) return cudaErrorInvalidValue;
     (void)D;
     const int ntile = (M + 31) / 32;
     dim3 grid(ntile * (ntile + 1) / 2, nd);
     switch (c) {
-        case 2: k2_kernel<2><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2); break;
-        case 3: k2_kernel<3><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2); break;
-        case 4: k2_kernel<4><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2); break;
+        case 2: k2_kernel<2><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits); break;
+        case 3: k2_kernel<3><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits); break;
+        case 4: k2_kernel<4><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
