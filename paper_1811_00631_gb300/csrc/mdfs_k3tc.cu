@@ -11,13 +11,16 @@
 // the counts are exact integers.  Class-0 and class-1 samples occupy separate
 // K ranges and accumulate into two TMEM accumulators.
 //
-// Persistent, warp-specialised kernel (one CTA per SM, 384 threads):
+// Persistent, warp-specialised kernel (one CTA per SM, 640 threads):
 //   warp 0       TMA producer: A (a rows), B (e rows), OH[b] row per K block,
 //   warp 1       TMEM owner and MMA issuer (4 MMAs of K = 32 per K block),
 //   warps 2-3    AND the A tile with OH[b] in shared memory (128B swizzle),
-//   warps 4-11   epilogue: tcgen05.ld of both class accumulators, the 8-voxel
+//   warps 4-19   epilogue: tcgen05.ld of both class accumulators, the 8-voxel
 //                tables by inclusion-exclusion, SH3 from fixed-point tables
 //                in shared memory, three IG roles, packed max keys.
+// Registers: launched at kRegsLaunch per thread; the first warpgroup gives
+// back to kRegsProducer, the four epilogue warpgroups take kRegsEpilogue
+// (128 kRegsProducer + 512 kRegsEpilogue == 640 kRegsLaunch).
 // Four shared-memory stages and two TMEM accumulator buffers (2 x 256
 // columns) let the epilogue of one tile overlap the MMAs of the next.
 //
@@ -45,10 +48,13 @@ constexpr int kStages = 4;
 constexpr uint32_t kTileBytes = kTile * kBK;  // 16 KB
 constexpr uint32_t kAccCols = 2 * kTile;      // class 0 and class 1 accumulators
 constexpr uint32_t kTmemCols = 2 * kAccCols;  // double buffer
-constexpr int kThreads = 384;
+constexpr int kThreads = 640;
 constexpr int kMaskWarp0 = 2, kMaskThreads = 64;
-constexpr int kEpiWarp0 = 4, kEpiThreads = 256;
-constexpr int kColsPerWarp = 64;
+constexpr int kEpiWarp0 = 4, kEpiThreads = 512;
+constexpr int kColsPerWarp = 32;
+constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
+static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
+              "register split must add up to the launch allocation");
 constexpr size_t kTabOffset = 2 * kStages * kTileBytes + kStages * kBK;  // after A, B, OH[b] rows
 
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
@@ -136,8 +142,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = s_tmem;
     const int n_tiles = n_items * nd;
     const int nkb = tg.nkb;
-
-    if (warp == 0) {
+    if (warp < kEpiWarp0) {
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsProducer));
+      if (warp == 0) {
         // ------------------------------ TMA producer ------------------------------
         if (lane == 0 && !*abort) {
             uint32_t g = 0;  // running K-block counter across this CTA's tiles
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int s = 0; s < kStages; ++s)
                 if (pend_mask & (1 << s)) mbar_drain(&bar_full[s], pend_use[s] & 1);
         }
-    } else if (warp == 1) {
+      } else if (warp == 1) {
         // ------------------------------ MMA issuer --------------------------------
         if (lane == 0 && !*abort) {
             const uint32_t idesc = tc::idesc_e4m3_f32(kTile, kTile);
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_drain(&bar_drain, 0);
             }
         }
-    } else if (warp < kEpiWarp0) {
+      } else {
         // ------------------------------ A-tile maskers ----------------------------
         const int mt = tid - kMaskWarp0 * 32;
         uint32_t g = 0;
@@ -246,10 +253,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
         }
+      }
     } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpilogue));
         // ------------------------------ epilogue ----------------------------------
-        const int ew = warp - kEpiWarp0;      // 0..7
-        const int q = warp & 3, h = ew >> 2;  // TMEM lane quarter (warp % 4), column half
+        const int ew = warp - kEpiWarp0;      // 0..15
+        const int q = warp & 3, h = ew >> 2;  // TMEM lane quarter (warp % 4), column quarter
         const int row = 32 * q + lane;
         const float inv_scale = __int_as_float((127 - fbits) << 23);  // 2^-fbits
         ColCtx* cc = s_col[ew];
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t idx_a = (dM + (uint32_t)b) * (uint32_t)M;   // role a: partners (b, e)
             const uint32_t idx_be = (dM + (uint32_t)a) * (uint32_t)M;  // roles b: (a, e) and e: (a, b)
             // pair (a, e) records of the first 8 columns, fetched before the accumulators are ready
-            const PairC* prow = pd + (size_t)ecol0 * M + (arow ? a : 0);  // column e -> prow[(e - ecol0) * M]
+            const PairC* prow = pd + (size_t)min(ecol0, M - 1) * M + (arow ? a : 0);  // prow[(e - ecol0) * M]
             PairC pnext[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) pnext[j] = (arow && j < ncols) ? prow[(size_t)j * M] : PairC{0u, 0};
@@ -478,6 +487,10 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const long long n_tiles = (long long)n_items * nd;
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+    // the register split inside the kernel needs exactly kRegsLaunch registers per thread
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k3tc_kernel)) != cudaSuccess) return e;
+    if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
     k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, pairs, keys,
                                               err);
