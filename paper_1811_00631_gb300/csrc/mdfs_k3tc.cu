@@ -222,9 +222,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       } else {
         // ------------------------------ A-tile maskers ----------------------------
+        // Thread mt owns 16-byte slot (mt & 7) of rows (mt >> 3) + 8 i; since 8
+        // divides the row step, its swizzled chunk j = slot ^ (row & 7) and hence
+        // its mask chunk are the same for every row it touches.  Rows a >= b
+        // are left as loaded: their counts are never used.
         const int mt = tid - kMaskWarp0 * 32;
+        const int slot = mt & 7, r0 = mt >> 3;
+        const int jchunk = slot ^ (r0 & 7);
         uint32_t g = 0;
         for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
+            const int2 item = items[t % n_items];
+            const int a0 = (item.y >> 16) * kTile;
+            const int rows = min(kTile, item.x - a0);  // valid rows: a < b
             bool ok = true;
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int s = (int)(g % kStages);
@@ -233,14 +242,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = false;
                     break;
                 }
-                uint8_t* A = sA + s * kTileBytes;
-                const uint8_t* mrow = sOHb + s * kBK;
+                uint8_t* A = sA + s * kTileBytes + slot * 16;
+                const uint4 m = *reinterpret_cast<const uint4*>(sOHb + s * kBK + jchunk * 16);
 #pragma unroll 4
-                for (int idx = mt; idx < kTile * 8; idx += kMaskThreads) {
-                    const int r = idx >> 3, slot = idx & 7;
-                    const int j = slot ^ (r & 7);  // 128-byte swizzle: chunk slot = chunk ^ (row % 8)
-                    uint4* p = reinterpret_cast<uint4*>(A + r * kBK + slot * 16);
-                    const uint4 m = *reinterpret_cast<const uint4*>(mrow + j * 16);
+                for (int r = r0; r < rows; r += kMaskThreads / 8) {
+                    uint4* p = reinterpret_cast<uint4*>(A + r * kBK);
                     uint4 v = *p;
                     v.x &= m.x;
                     v.y &= m.y;
