@@ -125,6 +125,37 @@ int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretization
                 const uint8_t* irrelevant_mask, double alpha, double* p_values, double* ig_lim,
                 double* n_eff, void* stream);
 
+/*
+ * mdfs_max_ig without any device allocation (the paper has no counterpart:
+ * this is a deployment variant).
+ *
+ * Some callers cannot let a library allocate device memory: a serving process
+ * whose allocator owns the device budget, a host application that only lets
+ * plug-ins use memory it handed out, or a latency-bound loop that cannot pay
+ * for cudaMalloc/cudaFree and the synchronisation they imply.  This entry point
+ * computes the same result as mdfs_max_ig for k = 1 or 2, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch (bit planes,
+ * tables, counts, keys) lives in one file-scope device array of
+ * MDFS_NOALLOC_SCRATCH_BYTES, which every GPU that loads that part of the
+ * library holds until the process exits.
+ *
+ * x, y, ig, tuples and best_disc must be device pointers of the current device
+ * (MDFS_EINVAL otherwise).  Problems whose scratch does not fit the array are
+ * rejected with MDFS_EINVAL and a message giving the bytes needed; roughly
+ * discretizations * M * (divisions * (N/8 + 20) + 16) bytes must stay below
+ * the array size.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array: two calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race and must not be
+ * issued; serialise them.  The call waits once for a 16-byte validation read
+ * of the inputs; with a non-NULL stream the rest is stream-ordered.
+ */
+#define MDFS_NOALLOC_SCRATCH_BYTES (32u << 20)
+int mdfs_max_ig_noalloc(const mdfs_data* data, int k, int divisions, int discretizations, double range,
+                        double pc_xi, uint64_t seed, float* ig, int32_t* tuples, int32_t* best_disc,
+                        void* stream);
+
 /* Thread-local description of the last failure of this thread ("" if none). */
 const char* mdfs_last_error(void);
 

@@ -275,6 +275,10 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
 
 }  // namespace
 
+namespace mdfs {
+void record_error(const char* msg) { g_err = msg; }
+}  // namespace mdfs
+
 extern "C" {
 
 int mdfs_abi_version(void) { return 1; }

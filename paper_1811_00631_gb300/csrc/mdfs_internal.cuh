@@ -119,4 +119,7 @@ cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float*
 cudaError_t launch_ig_lim(const float* ig, int M, int df, const uint8_t* mask, double alpha,
                           double* p_values, double* res, cudaStream_t st);
 
+// Sets the thread-local message that mdfs_last_error() returns.
+void record_error(const char* msg);
+
 }  // namespace mdfs

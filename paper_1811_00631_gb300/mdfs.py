@@ -31,7 +31,8 @@ _ERRORS = {
 }
 
 EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
-            "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report")
+            "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
+            "mdfs_max_ig_noalloc")
 
 
 class MdfsError(RuntimeError):
@@ -65,6 +66,9 @@ def load(path: str = LIB_PATH):
         lib.mdfs_max_ig.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
         lib.mdfs_max_ig.restype = ctypes.c_int
+        lib.mdfs_max_ig_noalloc.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
+        lib.mdfs_max_ig_noalloc.restype = ctypes.c_int
         lib.mdfs_ig_lim.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                     ctypes.c_double, P, P, P, P]
         lib.mdfs_ig_lim.restype = ctypes.c_int
@@ -194,6 +198,34 @@ def max_ig(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range
     rc = lib.mdfs_max_ig(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
                          int(seed) & (2**64 - 1), ctypes.c_void_p(ptrs[0]),
                          ctypes.c_void_p(ptrs[1]) if k > 1 else None, ctypes.c_void_p(ptrs[2]), stream)
+    _check(rc)
+    del keep
+    return ig, tu[:, : k - 1], di
+
+
+def max_ig_noalloc(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range_: float = 0.0,
+                   pc_xi: float = 0.25, seed: int = 0, out=None):
+    """mdfs_max_ig_noalloc: k = 1 or 2 with all scratch in the library's fixed device array.
+
+    x, y and the outputs must be CUDA tensors; outputs are allocated here (by
+    torch) unless ``out`` passes (ig, tuples, disc).  Returns them like max_ig.
+    """
+    import torch
+    lib = load()
+    if not (_is_cuda(x) and _is_cuda(y)):
+        raise TypeError("max_ig_noalloc needs CUDA tensors")
+    data, keep = _data(x, y)
+    M = data.M
+    if out is None:
+        ig = torch.empty(M, dtype=torch.float32, device=x.device)
+        tu = torch.empty((M, 1), dtype=torch.int32, device=x.device)
+        di = torch.empty(M, dtype=torch.int32, device=x.device)
+    else:
+        ig, tu, di = out
+    rc = lib.mdfs_max_ig_noalloc(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
+                                 int(seed) & (2**64 - 1), ctypes.c_void_p(ig.data_ptr()),
+                                 ctypes.c_void_p(tu.data_ptr()) if k > 1 else None, ctypes.c_void_p(di.data_ptr()),
+                                 _stream_of(x))
     _check(rc)
     del keep
     return ig, tu[:, : k - 1], di

@@ -1,0 +1,85 @@
+"""The allocation-free entry point against the allocating one.
+
+mdfs_max_ig_noalloc serves callers that cannot let a library allocate device
+memory (an allocator that owns the device budget, a host that hands plug-ins
+their memory, a loop that cannot pay for cudaMalloc). It keeps its scratch in
+a fixed device array shared by every call, so these tests make two calls in a
+row with different inputs and compare each with mdfs_max_ig. This file is
+named to run last.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ATOL, RTOL = 1e-4, 1e-5
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_00631_gb300 import build
+    build.build()
+    return torch
+
+
+def _compare(torch, got, want, k):
+    g_ig, g_tu, g_di = (t.cpu().numpy() for t in got)
+    w_ig, w_tu, w_di = (t.cpu().numpy() for t in want)
+    assert np.all(np.abs(g_ig.astype(np.float64) - w_ig) <= ATOL + RTOL * np.abs(w_ig))
+    assert np.array_equal(g_di, w_di)
+    if k == 2:
+        assert np.array_equal(g_tu, w_tu)
+
+
+def test_two_calls_in_a_row_match_the_allocating_entry_point(cuda):
+    torch = cuda
+    from paper_1811_00631_gb300 import mdfs, synth
+    cases = [
+        (synth.madelon_like(N=1500, M=300, seed=21), 2, 2, 6, 0.5, 0.25, 31),
+        (synth.xor_small(N=777, M=120, seed=4), 2, 1, 9, 0.3, 0.1, 7),
+        (synth.madelon_like(N=999, M=64, seed=5), 1, 3, 4, 0.8, 0.5, 3),
+    ]
+    for ds, k, div, D, r, xi, seed in cases:
+        x = torch.from_numpy(ds.x).cuda()
+        y = torch.from_numpy(ds.y).cuda()
+        want = mdfs.max_ig(x, y, k, div, D, r, xi, seed)
+        got = mdfs.max_ig_noalloc(x, y, k, div, D, r, xi, seed)
+        torch.cuda.synchronize()
+        _compare(torch, got, want, k)
+
+
+def test_int8_input_and_side_stream(cuda):
+    torch = cuda
+    from paper_1811_00631_gb300 import mdfs, synth
+    rng = np.random.default_rng(3)
+    x8 = torch.from_numpy(synth.to_int8(rng.standard_normal((90, 640)), scale=5.0)).cuda()
+    y = torch.from_numpy((rng.random(640) < 0.3).astype(np.uint8)).cuda()
+    want = mdfs.max_ig(x8, y, 2, 2, 5, 0.6, 0.25, 11)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        got = mdfs.max_ig_noalloc(x8, y, 2, 2, 5, 0.6, 0.25, 11)
+    s.synchronize()
+    _compare(torch, got, want, 2)
+
+
+def test_rejects_oversize_and_host_pointers(cuda):
+    torch = cuda
+    from paper_1811_00631_gb300 import mdfs
+    x = torch.randn(4000, 2000, device="cuda")
+    y = (torch.arange(2000, device="cuda") % 2).to(torch.uint8)
+    with pytest.raises(mdfs.MdfsError) as e:
+        mdfs.max_ig_noalloc(x, y, 2, 3, 30, 0.5, 0.25, 1)  # needs far more than the fixed array
+    assert e.value.code == -1 and "scratch" in str(e.value)
+    lib = mdfs.load()
+    import ctypes
+    xh = np.zeros((4, 10), dtype=np.float32)
+    yh = (np.arange(10) % 2).astype(np.uint8)
+    ig = torch.empty(4, device="cuda")
+    d = mdfs._Data(0, xh.ctypes.data, yh.ctypes.data, 10, 4)
+    rc = lib.mdfs_max_ig_noalloc(ctypes.byref(d), 2, 1, 1, 0.0, 0.25, 1, ctypes.c_void_p(ig.data_ptr()), None, None,
+                                 None)
+    assert rc == -1 and b"device pointers" in lib.mdfs_last_error()
