@@ -291,6 +291,8 @@ def run_gpu(args, rank, world, local_rank):
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "kernels": shares}
+    if args.serving_jobs > 0:
+        line["serving"] = serving_run(args.serving_jobs, local_rank)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -302,6 +304,47 @@ def run_gpu(args, rank, world, local_rank):
                                           f"{DISC} discretisations, {dt:.1f} s"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def serving_run(n_jobs: int, device: int):
+    """Serving-mix measurement: a closed-loop pass measures capacity (jobs/s),
+    then a Poisson stream at 70% of that capacity gives the job latencies."""
+    from paper_1811_00631_gb300 import serve, synth
+    specs = synth.serving_mix(n_jobs=n_jobs, seed=17, rate_hz=1.0, n_range=(100, 5000), m_range=(100, 5000),
+                              max_work=2e10)
+    jobs = []
+    evals = 0.0
+    for sp in specs:
+        x, y = synth.serving_data(sp)
+        jobs.append(serve.Job(x=x, y=y, k=sp["k"], divisions=sp["divisions"], discretizations=sp["discretizations"],
+                              range_=0.5, pc_xi=0.25, seed=sp["seed"], alpha=0.05, tag=sp["job"]))
+        evals += serve.job_evals(sp["M"], sp["k"], sp["discretizations"])
+    with serve.Server(n_slots=4, device=device) as srv:  # warm-up: workspaces and modules
+        for f in [srv.submit(j) for j in jobs[:8]]:
+            f.result()
+        t0 = time.perf_counter()
+        for f in [srv.submit(j) for j in jobs]:
+            f.result()
+        closed_s = time.perf_counter() - t0
+        capacity = n_jobs / closed_s
+        rate = 0.7 * capacity
+        rng = np.random.default_rng(3)
+        gaps = rng.exponential(1.0 / rate, size=n_jobs)
+        t0 = time.perf_counter()
+        futs = []
+        for j, g in zip(jobs, np.cumsum(gaps)):
+            delay = g - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(j))
+        results = [f.result() for f in futs]
+        open_s = time.perf_counter() - t0
+    st = serve.latency_stats(results)
+    return {"jobs": n_jobs, "slots": 4, "capacity_jobs_per_s": capacity, "arrival_rate_jobs_per_s": rate,
+            "p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"], "mean_ms": 1e3 * st["mean_s"],
+            "evals_per_s_closed_loop": evals / closed_s, "evals_per_s_poisson": evals / open_s,
+            "mix": "k in 1..3, N U[100,5000], M log-U[100,5000] capped at C(M,k)*D*N <= 2e10, f32/i8, "
+                   "divisions 1-3, 5-30 discretisations, each scan followed by the IG_lim fit"}
 
 
 def main():
@@ -316,9 +359,11 @@ def main():
     ap.add_argument("--k3-traffic", type=float, default=None,
                     help="DRAM bytes per k=3 launch from an ncu capture of the current kernel")
     ap.add_argument("--small", action="store_true", help="reduced profiling case (M=160, D=4)")
+    ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving-mix run (0: skip)")
     args = ap.parse_args()
     if args.small:
         _use_small_case()
+        args.serving_jobs = 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -1,0 +1,220 @@
+"""Continuous-batching request loop for MDFS scans on one GPU.
+
+A ``Server`` owns ``n_slots`` worker threads, each bound to its own CUDA
+stream.  The C library keeps one workspace per stream, so a slot's device
+buffers stay resident across the jobs it runs.  Jobs are admitted in arrival
+order as soon as a slot is free and the job's estimated device footprint fits
+the remaining memory budget.  Jobs that arrive while others are on the GPU
+join as slots and memory free up, and their work overlaps on the device
+(different streams).  A job is one ``mdfs_max_ig`` scan (IG^k_max, Eq. 1 of
+arXiv 1811.00631) followed by the chi^2 / extreme-value fit ``mdfs_ig_lim``
+(section "Theory").  The scan is deterministic, so a job's result is the same
+alone or in a mix.
+
+The scheduler is independent of the GPU: ``Server`` takes an ``executor``
+callable, and the default one runs the job through the C ABI on the slot's
+stream.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import threading
+import time
+from concurrent.futures import Future
+from typing import Callable, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Job:
+    x: object                 # (M, N) float32 or int8, host array or CUDA tensor
+    y: object                 # (N,) uint8
+    k: int = 2
+    divisions: int = 1
+    discretizations: int = 1
+    range_: float = 0.0
+    pc_xi: float = 0.25
+    seed: int = 0
+    alpha: float = 0.05       # level of the IG_lim fit (None: skip the fit)
+    tag: object = None
+
+
+@dataclasses.dataclass
+class Result:
+    ig: np.ndarray
+    tuples: np.ndarray
+    disc: np.ndarray
+    p_values: Optional[np.ndarray]
+    ig_lim: Optional[float]
+    n_eff: Optional[float]
+    submit_t: float
+    start_t: float
+    end_t: float
+    slot: int
+    tag: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.end_t - self.submit_t
+
+
+def job_device_bytes(M: int, N: int, k: int, divisions: int, discretizations: int, x_itemsize: int = 4) -> int:
+    """Upper estimate of the device memory one job holds in its slot's workspace
+    (inputs, bit planes, one-hot operand and pair records for k = 3, tables)."""
+    c = divisions + 1
+    P = c - 1
+    D = discretizations
+    words = (N + 31) // 32 + 5
+    kp = ((N + 127) // 128 + 1) * 128
+    b = M * N * x_itemsize + N * 5 + 3 * (N + 1) * 8
+    b += D * M * P * words * 4 + D * M * (P * 8 + 8) + M * 8
+    if k == 3:
+        if c == 2:
+            b += D * M * kp + D * M * M * 8
+        else:
+            b += D * M * M * (8 + P * P * 8)
+    return int(b * 1.15) + (1 << 20)
+
+
+class Server:
+    """Admits jobs into ``n_slots`` concurrent slots under a device-memory budget."""
+
+    def __init__(self, n_slots: int = 4, memory_budget: Optional[int] = None, device: int = 0,
+                 executor: Optional[Callable] = None, estimate: Callable = job_device_bytes):
+        self.n_slots = n_slots
+        self.device = device
+        self.estimate = estimate
+        if memory_budget is None:
+            memory_budget = self._default_budget(device) if executor is None else 1 << 40
+        self.budget = int(memory_budget)
+        self._executor = executor
+        self._queue = collections.deque()
+        self._cv = threading.Condition()
+        self._in_use = 0
+        self._running = 0
+        self._closed = False
+        self.peak_in_use = 0
+        self.peak_running = 0
+        self._threads = [threading.Thread(target=self._worker, args=(s,), daemon=True) for s in range(n_slots)]
+        for t in self._threads:
+            t.start()
+
+    @staticmethod
+    def _default_budget(device: int) -> int:
+        import torch
+        free, _total = torch.cuda.mem_get_info(device)
+        return int(free * 0.8)
+
+    # ------------------------------------------------------------------
+    def submit(self, job: Job) -> Future:
+        fut: Future = Future()
+        M, N = int(job.x.shape[0]), int(job.x.shape[1])
+        itemsize = 1 if str(getattr(job.x, "dtype", "")).endswith("int8") else 4
+        need = self.estimate(M, N, job.k, job.divisions, job.discretizations, itemsize)
+        if need > self.budget:
+            fut.set_exception(MemoryError(f"job needs ~{need} device bytes, budget is {self.budget}"))
+            return fut
+        with self._cv:
+            if self._closed:
+                raise RuntimeError("server closed")
+            self._queue.append((job, fut, need, time.perf_counter()))
+            self._cv.notify_all()
+        return fut
+
+    def close(self, wait: bool = True):
+        with self._cv:
+            self._closed = True
+            self._cv.notify_all()
+        if wait:
+            for t in self._threads:
+                t.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------
+    def _next(self):
+        """Head-of-line admission: the oldest job runs as soon as it fits."""
+        with self._cv:
+            while True:
+                if self._queue:
+                    job, fut, need, t_sub = self._queue[0]
+                    if self._in_use + need <= self.budget:
+                        self._queue.popleft()
+                        self._in_use += need
+                        self._running += 1
+                        self.peak_in_use = max(self.peak_in_use, self._in_use)
+                        self.peak_running = max(self.peak_running, self._running)
+                        return job, fut, need, t_sub
+                elif self._closed:
+                    return None
+                self._cv.wait()
+
+    def _release(self, need: int):
+        with self._cv:
+            self._in_use -= need
+            self._running -= 1
+            self._cv.notify_all()
+
+    def _worker(self, slot: int):
+        ctx = None
+        if self._executor is None:
+            import torch
+            torch.cuda.set_device(self.device)
+            ctx = torch.cuda.Stream(self.device)
+        while True:
+            item = self._next()
+            if item is None:
+                return
+            job, fut, need, t_sub = item
+            t0 = time.perf_counter()
+            try:
+                if self._executor is not None:
+                    out = self._executor(job, slot)
+                else:
+                    out = _run_on_gpu(job, ctx, self.device)
+                t1 = time.perf_counter()
+                fut.set_result(Result(*out, submit_t=t_sub, start_t=t0, end_t=t1, slot=slot, tag=job.tag))
+            except BaseException as e:  # the job failed; the slot keeps serving
+                fut.set_exception(e)
+            finally:
+                self._release(need)
+
+
+def _run_on_gpu(job: Job, stream, device: int):
+    import torch
+
+    from . import mdfs
+    with torch.cuda.device(device), torch.cuda.stream(stream):
+        x = job.x if getattr(job.x, "is_cuda", False) else torch.as_tensor(np.asarray(job.x)).to(
+            f"cuda:{device}", non_blocking=False)
+        y = job.y if getattr(job.y, "is_cuda", False) else torch.as_tensor(np.asarray(job.y, dtype=np.uint8)).to(
+            f"cuda:{device}", non_blocking=False)
+        ig, tu, di = mdfs.max_ig(x, y, job.k, job.divisions, job.discretizations, job.range_, job.pc_xi, job.seed)
+        p = lim = neff = None
+        if job.alpha is not None:
+            try:
+                p_t, lim, neff = mdfs.ig_lim(ig, job.k, job.divisions, job.discretizations, None, job.alpha)
+                p = p_t.cpu().numpy()
+            except mdfs.MdfsError as e:
+                if e.code != -2:  # no variable with IG > 0: no fit for this job
+                    raise
+        stream.synchronize()
+        return ig.cpu().numpy(), tu.cpu().numpy(), di.cpu().numpy(), p, lim, neff
+
+
+def latency_stats(results):
+    lat = np.array([r.latency for r in results])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "n": int(len(lat))}
+
+
+def job_evals(M: int, k: int, discretizations: int) -> float:
+    """Unordered k-tuple x discretisation evaluations of one job."""
+    return float(math.comb(M, k)) * discretizations

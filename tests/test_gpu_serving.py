@@ -1,0 +1,53 @@
+"""The serving loop on the GPU: a Poisson stream of mixed jobs (k = 1..3, mixed
+N, M, divisions, float32 and int8), admitted into concurrent slots; every
+result equals the same job run alone, bit for bit, and jobs overlap."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1811_00631_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_00631_gb300 import build
+    build.build()
+    return torch
+
+
+def test_mix_equals_alone_and_overlaps(cuda):
+    from paper_1811_00631_gb300 import mdfs, serve
+    specs = synth.serving_mix(n_jobs=24, seed=11, rate_hz=200.0, n_range=(100, 1500), m_range=(40, 300),
+                              max_work=2e9)
+    jobs = []
+    for sp in specs:
+        x, y = synth.serving_data(sp)
+        jobs.append(serve.Job(x=x, y=y, k=sp["k"], divisions=sp["divisions"], discretizations=sp["discretizations"],
+                              range_=0.5, pc_xi=0.25, seed=sp["seed"], alpha=0.05, tag=sp["job"]))
+    with serve.Server(n_slots=4) as srv:
+        t0 = time.perf_counter()
+        futs = []
+        for sp, job in zip(specs, jobs):
+            delay = sp["arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(job))
+        results = [f.result(timeout=120) for f in futs]
+    assert srv.peak_running >= 2
+    assert srv.peak_in_use <= srv.budget
+    for job, r in zip(jobs, results):
+        ig, tu, di = mdfs.max_ig(job.x, job.y, job.k, job.divisions, job.discretizations, job.range_, job.pc_xi,
+                                 job.seed)
+        assert np.array_equal(r.ig, ig), f"job {job.tag}"
+        assert np.array_equal(r.disc, di)
+        if job.k > 1:
+            assert np.array_equal(r.tuples, tu)
+        assert r.latency > 0
+    st = serve.latency_stats(results)
+    assert st["p99_s"] >= st["p50_s"] > 0

@@ -1,0 +1,99 @@
+"""Host logic of the continuous-batching request loop, with a fake executor
+(no GPU): admission under the memory budget, slot limits, arrival order,
+failure isolation and latency bookkeeping."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1811_00631_gb300 import serve
+
+
+class FakeJob:
+    def __init__(self, need, dur, tag, fail=False):
+        self.x = np.zeros((need, 1), dtype=np.float32)  # M encodes the memory need below
+        self.y = np.zeros(1, dtype=np.uint8)
+        self.k, self.divisions, self.discretizations = 1, 1, 1
+        self.dur, self.tag, self.fail = dur, tag, fail
+
+
+def _estimate(M, N, k, div, D, itemsize):
+    return M
+
+
+def _run(jobs, n_slots, budget):
+    active = []
+    lock = threading.Lock()
+    log = []
+
+    def executor(job, slot):
+        with lock:
+            active.append(job.tag)
+            log.append(("start", job.tag, slot, list(active)))
+        time.sleep(job.dur)
+        with lock:
+            active.remove(job.tag)
+        if job.fail:
+            raise ValueError(f"job {job.tag} failed")
+        return (np.array([job.tag]), None, None, None, None, None)
+
+    srv = serve.Server(n_slots=n_slots, memory_budget=budget, executor=executor, estimate=_estimate)
+    futs = [srv.submit(j) for j in jobs]
+    res = []
+    for f in futs:
+        try:
+            res.append(f.result(timeout=20))
+        except ValueError as e:
+            res.append(e)
+    srv.close()
+    return srv, res, log
+
+
+def test_slots_and_budget_bound_concurrency():
+    jobs = [FakeJob(need=40, dur=0.05, tag=i) for i in range(12)]
+    srv, res, log = _run(jobs, n_slots=4, budget=100)
+    # at most two 40-byte jobs fit in 100 bytes even though 4 slots exist
+    assert srv.peak_in_use <= 100
+    assert srv.peak_running == 2
+    assert max(len(a) for _, _, _, a in log) <= 2
+    assert [r.ig[0] for r in res] == list(range(12))
+
+
+def test_arrival_order_is_kept_and_big_jobs_are_not_starved():
+    jobs = [FakeJob(need=10, dur=0.03, tag=0), FakeJob(need=90, dur=0.03, tag=1)] + \
+           [FakeJob(need=10, dur=0.03, tag=i) for i in range(2, 8)]
+    srv, res, log = _run(jobs, n_slots=4, budget=100)
+    starts = [t for kind, t, _, _ in log if kind == "start"]
+    assert starts == sorted(starts)  # head-of-line admission: start order == arrival order
+    assert srv.peak_in_use <= 100
+
+
+def test_failure_is_isolated_and_oversize_is_rejected():
+    jobs = [FakeJob(need=10, dur=0.01, tag=0), FakeJob(need=10, dur=0.01, tag=1, fail=True),
+            FakeJob(need=10, dur=0.01, tag=2)]
+    srv, res, _ = _run(jobs, n_slots=2, budget=100)
+    assert isinstance(res[1], ValueError)
+    assert res[0].ig[0] == 0 and res[2].ig[0] == 2
+    srv2 = serve.Server(n_slots=1, memory_budget=5, executor=lambda j, s: None, estimate=_estimate)
+    with pytest.raises(MemoryError):
+        srv2.submit(FakeJob(need=10, dur=0, tag=9)).result(timeout=5)
+    srv2.close()
+
+
+def test_latency_bookkeeping():
+    jobs = [FakeJob(need=1, dur=0.02, tag=i) for i in range(6)]
+    _, res, _ = _run(jobs, n_slots=1, budget=10)
+    lat = [r.latency for r in res]
+    assert all(l >= 0.02 for l in lat)
+    assert lat == sorted(lat)  # one slot: later arrivals wait longer
+    st = serve.latency_stats(res)
+    assert st["p50_s"] <= st["p99_s"] and st["n"] == 6
+
+
+def test_device_byte_estimate_grows_with_the_work():
+    a = serve.job_device_bytes(500, 2000, 2, 1, 30)
+    b = serve.job_device_bytes(500, 2000, 3, 1, 30)
+    c = serve.job_device_bytes(1000, 2000, 3, 1, 30)
+    assert a < b < c
+    assert b > 30 * 500 * 500 * 8  # pair records of the k = 3 path
