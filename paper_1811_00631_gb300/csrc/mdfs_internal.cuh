@@ -119,6 +119,11 @@ cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float*
 cudaError_t launch_ig_lim(const float* ig, int M, int df, const uint8_t* mask, double alpha,
                           double* p_values, double* res, cudaStream_t st);
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit on the current
+// device to at least `bytes`.  Thread-safe: concurrent calls on other streams
+// can only see the limit grow, so a launch sized below it stays valid.
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
+
 // Sets the thread-local message that mdfs_last_error() returns.
 void record_error(const char* msg);
 

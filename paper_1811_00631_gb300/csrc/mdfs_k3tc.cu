@@ -451,17 +451,17 @@ TcGeom make_tc_geom(int N0, int N1) {
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // resolved once (thread-safe static initialisation)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-        else
-            cudaGetLastError();
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -486,7 +486,7 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
                         const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
-    cudaError_t e = cudaFuncSetAttribute(k3tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)k3tc_kernel, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

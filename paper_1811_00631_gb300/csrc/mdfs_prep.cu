@@ -262,12 +262,12 @@ cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int
     const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
     cudaError_t e;
     if (dtype == 0) {
-        e = cudaFuncSetAttribute(discretize_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_dynamic_smem((const void*)discretize_kernel<float>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<float><<<M, 512, smem, st>>>((const float*)x, N, M, c, D, R, k0, k1, npad, perm, g,
                                                        planes, codes, thr, onehot, tg);
     } else {
-        e = cudaFuncSetAttribute(discretize_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_dynamic_smem((const void*)discretize_kernel<int8_t>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<int8_t><<<M, 512, smem, st>>>((const int8_t*)x, N, M, c, D, R, k0, k1, npad, perm, g,
                                                         planes, codes, thr, onehot, tg);
