@@ -105,6 +105,25 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
                 void* stream);
 
 /*
+ * Batched scan: n_jobs independent mdfs_max_ig jobs over resamples of one
+ * dataset, e.g. bootstrap or cross-validation folds and y-permutation nulls
+ * (the null distribution the significance test of section "Theory" is fitted
+ * to).  Job j is exactly mdfs_max_ig on
+ *     x_j[v][t] = x[v][idx_j[t]],   y_j[t] = y[perm_j[idx_j[t]]],   t = 0..N-1,
+ * with idx_j = sample_idx + j N and perm_j = y_perm + j N (either may be NULL =
+ * identity), the same k, divisions, discretizations, range, pc_xi and seed.
+ *
+ * sample_idx, y_perm:  [n_jobs][N] int32, host or device; entries in [0, N).
+ * ig:                  [n_jobs][M] float; tuples [n_jobs][M][k-1] or NULL;
+ *                      best_disc [n_jobs][M] or NULL (host or device).
+ * A job whose decision has one class fails the call with MDFS_EDEGENERATE
+ * (the message names the job).  Returns after all jobs are complete.
+ */
+int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_idx, const int32_t* y_perm, int k,
+                      int divisions, int discretizations, double range, double pc_xi, uint64_t seed, float* ig,
+                      int32_t* tuples, int32_t* best_disc, void* stream);
+
+/*
  * Significance of IG^k_max (section "Theory"): a single tuple's 2 IG is
  * chi^2 with df = (c-1) c^(k-1) degrees of freedom; the maximum over T
  * effective tests has CDF F_df(2 g)^T.  T is fitted by maximum likelihood on

@@ -44,6 +44,7 @@ struct Workspace {
     cudaStream_t stream = nullptr;
     Buffer x, y, stats, perm, tab, planes, cnt1, sh1, keys, sh2, cnt2, items, ig, tuples, disc, codes, mask, pv, res;
     Buffer pairs2, items2, onehot, err;
+    Buffer bx, by, bidx, bperm;  // batch: gathered job data and the job index maps
     int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
     double* host_res = nullptr; // pinned, 4 doubles
@@ -52,7 +53,7 @@ struct Workspace {
     ~Workspace() {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
-                         &onehot, &err};
+                         &onehot, &err, &bx,   &by,  &bidx, &bperm};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -273,6 +274,111 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
     }
 }
 
+// The scan of one job whose x and y are on the device and validated (ws->perm
+// holds the class-stable order, n1 the class-1 count): entropy tables,
+// discretisation and the counting kernels.  Leaves the packed max keys in ws->keys.
+int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, int k, int divisions, int D, double range,
+              double pc_xi, uint64_t seed, bool* check_err) {
+    cudaStream_t st = ws->stream;
+    const int c = divisions + 1;
+    *check_err = false;
+    const int n0 = N - n1;
+    const double mn = (double)(n0 < n1 ? n0 : n1);
+    const double b0 = pc_xi * n0 / mn, b1 = pc_xi * n1 / mn;
+    const PlaneGeom g = make_geom(N, n0);
+    const int P = c - 1;
+
+    MDFS_ENSURE(ws, tab, (size_t)3 * (N + 1) * sizeof(long long));
+    MDFS_ENSURE(ws, planes, (size_t)D * M * P * g.Ws * sizeof(uint32_t));
+    MDFS_ENSURE(ws, cnt1, (size_t)D * M * P * 2 * sizeof(int));
+    MDFS_ENSURE(ws, sh1, (size_t)D * M * sizeof(long long));
+    MDFS_ENSURE(ws, keys, (size_t)M * sizeof(unsigned long long));
+    long long* tab = (long long*)ws->tab.p;
+    uint32_t* planes = (uint32_t*)ws->planes.p;
+    int* cnt1 = (int*)ws->cnt1.p;
+    long long* sh1 = (long long*)ws->sh1.p;
+    unsigned long long* keys = (unsigned long long*)ws->keys.p;
+
+    MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
+    // tensor-core triple path: two classes and tables that fit in shared memory
+    const bool use_tc3 = (k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
+    TcGeom tg = make_tc_geom(n0, n1);
+    uint8_t* onehot = nullptr;
+    if (use_tc3) {
+        MDFS_ENSURE(ws, onehot, (size_t)D * M * tg.Kp);
+        onehot = (uint8_t*)ws->onehot.p;
+    }
+    MDFS_LAUNCH("discretize", st, launch_discretize(xd, dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g,
+                                                    planes, nullptr, nullptr, onehot, tg, st));
+    MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
+    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
+    if (k == 2) {
+        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st));
+    } else if (use_tc3) {
+        // two classes: symmetric 8-byte pair records and the tcgen05 triple kernel
+        const size_t per_disc = (size_t)M * M * sizeof(PairC);
+        const int fbits = k3tc_fraction_bits(N);
+        size_t budget = (size_t)4 << 30;
+        if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
+        int nd = (int)(budget / per_disc);
+        if (nd < 1) nd = 1;
+        if (nd > D) nd = D;
+        MDFS_ENSURE(ws, pairs2, (size_t)nd * per_disc);
+        MDFS_ENSURE(ws, err, sizeof(int));
+        MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
+        if (ws->items2_M != M) {
+            std::vector<int2> items;
+            build_k3tc_items(M, items);
+            MDFS_ENSURE(ws, items2, items.size() * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items2.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items2_M = M;
+            ws->n_items2 = (int)items.size();
+        }
+        CUtensorMap map;
+        MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M, D, tg.Kp));
+        for (int d0 = 0; d0 < D; d0 += nd) {
+            const int nn = std::min(nd, D - d0);
+            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
+                                                   nullptr, (PairC*)ws->pairs2.p, fbits, st));
+            MDFS_LAUNCH("k3", st, launch_k3tc(map, onehot, tg, M, d0, nn, (const int2*)ws->items2.p, ws->n_items2,
+                                              tab, fbits, cnt1, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p,
+                                              st));
+        }
+        *check_err = true;
+    } else if (k == 3) {
+        const size_t per_disc = (size_t)M * M * (sizeof(long long) + (size_t)P * P * 2 * sizeof(int));
+        size_t budget = (size_t)4 << 30;
+        if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
+        int nd = (int)(budget / per_disc);
+        if (nd < 1) nd = 1;
+        if (nd > D) nd = D;
+        MDFS_ENSURE(ws, sh2, (size_t)nd * M * M * sizeof(long long));
+        MDFS_ENSURE(ws, cnt2, (size_t)nd * M * M * P * P * 2 * sizeof(int));
+        if (ws->items_M != M || ws->items_c != c) {
+            std::vector<int2> items;
+            build_k3_items(M, c, items);
+            MDFS_ENSURE(ws, items, items.size() * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items_M = M;
+            ws->items_c = c;
+            ws->n_items = (int)items.size();
+        }
+        for (int d0 = 0; d0 < D; d0 += nd) {
+            const int nn = std::min(nd, D - d0);
+            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
+                                                   (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
+            MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p, ws->n_items, tab, cnt1,
+                                        (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
+        }
+    }
+
+    return MDFS_OK;
+}
+
 }  // namespace
 
 namespace mdfs {
@@ -421,100 +527,10 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     int n1 = 0;
     rc = stage_inputs(ws, data, true, &xd, &yd, &n1);
     if (rc) return rc;
-    const int n0 = N - n1;
-    const double mn = (double)(n0 < n1 ? n0 : n1);
-    const double b0 = pc_xi * n0 / mn, b1 = pc_xi * n1 / mn;
-    const PlaneGeom g = make_geom(N, n0);
-    const int P = c - 1;
-
-    MDFS_ENSURE(ws, tab, (size_t)3 * (N + 1) * sizeof(long long));
-    MDFS_ENSURE(ws, planes, (size_t)D * M * P * g.Ws * sizeof(uint32_t));
-    MDFS_ENSURE(ws, cnt1, (size_t)D * M * P * 2 * sizeof(int));
-    MDFS_ENSURE(ws, sh1, (size_t)D * M * sizeof(long long));
-    MDFS_ENSURE(ws, keys, (size_t)M * sizeof(unsigned long long));
-    long long* tab = (long long*)ws->tab.p;
-    uint32_t* planes = (uint32_t*)ws->planes.p;
-    int* cnt1 = (int*)ws->cnt1.p;
-    long long* sh1 = (long long*)ws->sh1.p;
-    unsigned long long* keys = (unsigned long long*)ws->keys.p;
-
-    MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
-    // tensor-core triple path: two classes and tables that fit in shared memory
-    const bool use_tc3 = (k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
-    TcGeom tg = make_tc_geom(n0, n1);
-    uint8_t* onehot = nullptr;
-    if (use_tc3) {
-        MDFS_ENSURE(ws, onehot, (size_t)D * M * tg.Kp);
-        onehot = (uint8_t*)ws->onehot.p;
-    }
-    MDFS_LAUNCH("discretize", st, launch_discretize(xd, data->dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g,
-                                                    planes, nullptr, nullptr, onehot, tg, st));
-    MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
-    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
     bool check_err = false;
-    if (k == 2) {
-        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st));
-    } else if (use_tc3) {
-        // two classes: symmetric 8-byte pair records and the tcgen05 triple kernel
-        const size_t per_disc = (size_t)M * M * sizeof(PairC);
-        const int fbits = k3tc_fraction_bits(N);
-        size_t budget = (size_t)4 << 30;
-        if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
-        int nd = (int)(budget / per_disc);
-        if (nd < 1) nd = 1;
-        if (nd > D) nd = D;
-        MDFS_ENSURE(ws, pairs2, (size_t)nd * per_disc);
-        MDFS_ENSURE(ws, err, sizeof(int));
-        MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
-        if (ws->items2_M != M) {
-            std::vector<int2> items;
-            build_k3tc_items(M, items);
-            MDFS_ENSURE(ws, items2, items.size() * sizeof(int2));
-            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items2.p, items.data(), items.size() * sizeof(int2),
-                                          cudaMemcpyHostToDevice, st));
-            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
-            ws->items2_M = M;
-            ws->n_items2 = (int)items.size();
-        }
-        CUtensorMap map;
-        MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M, D, tg.Kp));
-        for (int d0 = 0; d0 < D; d0 += nd) {
-            const int nn = std::min(nd, D - d0);
-            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
-                                                   nullptr, (PairC*)ws->pairs2.p, fbits, st));
-            MDFS_LAUNCH("k3", st, launch_k3tc(map, onehot, tg, M, d0, nn, (const int2*)ws->items2.p, ws->n_items2,
-                                              tab, fbits, cnt1, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p,
-                                              st));
-        }
-        check_err = true;
-    } else if (k == 3) {
-        const size_t per_disc = (size_t)M * M * (sizeof(long long) + (size_t)P * P * 2 * sizeof(int));
-        size_t budget = (size_t)4 << 30;
-        if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
-        int nd = (int)(budget / per_disc);
-        if (nd < 1) nd = 1;
-        if (nd > D) nd = D;
-        MDFS_ENSURE(ws, sh2, (size_t)nd * M * M * sizeof(long long));
-        MDFS_ENSURE(ws, cnt2, (size_t)nd * M * M * P * P * 2 * sizeof(int));
-        if (ws->items_M != M || ws->items_c != c) {
-            std::vector<int2> items;
-            build_k3_items(M, c, items);
-            MDFS_ENSURE(ws, items, items.size() * sizeof(int2));
-            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items.p, items.data(), items.size() * sizeof(int2),
-                                          cudaMemcpyHostToDevice, st));
-            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
-            ws->items_M = M;
-            ws->items_c = c;
-            ws->n_items = (int)items.size();
-        }
-        for (int d0 = 0; d0 < D; d0 += nd) {
-            const int nn = std::min(nd, D - d0);
-            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
-                                                   (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
-            MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p, ws->n_items, tab, cnt1,
-                                        (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
-        }
-    }
+    rc = scan_core(ws, xd, data->dtype, N, M, n1, k, divisions, D, range, pc_xi, seed, &check_err);
+    if (rc) return rc;
+    unsigned long long* keys = (unsigned long long*)ws->keys.p;
 
     Out<float> oig;
     Out<int32_t> otu, odi;
@@ -536,6 +552,93 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     } else if (oig.staged || otu.staged || odi.staged || st == nullptr) {
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    return MDFS_OK;
+}
+
+int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_idx, const int32_t* y_perm, int k,
+                      int divisions, int discretizations, double range, double pc_xi, uint64_t seed, float* ig,
+                      int32_t* tuples, int32_t* best_disc, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, true);
+    if (rc) return rc;
+    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    if (n_jobs < 1) return fail(MDFS_EINVAL, "n_jobs = %d < 1", n_jobs);
+    if (k < 1 || k > 3) return fail(MDFS_EINVAL, "k = %d outside [1, 3]", k);
+    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
+    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
+    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
+    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if (!ig) return fail(MDFS_EINVAL, "ig is NULL");
+    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
+    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1_all = 0;
+    // validates x (finite) and the labels of y; a y with one class stays one class in every job
+    rc = stage_inputs(ws, data, true, &xd, &yd, &n1_all);
+    if (rc) return rc;
+    const size_t nidx = (size_t)n_jobs * N * sizeof(int32_t);
+    const int32_t* idxd = sample_idx;
+    if (sample_idx && !is_device_ptr(sample_idx)) {
+        MDFS_ENSURE(ws, bidx, nidx);
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->bidx.p, sample_idx, nidx, cudaMemcpyHostToDevice, st));
+        idxd = (const int32_t*)ws->bidx.p;
+    }
+    const int32_t* permd = y_perm;
+    if (y_perm && !is_device_ptr(y_perm)) {
+        MDFS_ENSURE(ws, bperm, nidx);
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->bperm.p, y_perm, nidx, cudaMemcpyHostToDevice, st));
+        permd = (const int32_t*)ws->bperm.p;
+    }
+    const size_t xbytes = (size_t)M * N * (data->dtype == MDFS_F32 ? 4 : 1);
+    MDFS_ENSURE(ws, bx, xbytes);
+    MDFS_ENSURE(ws, by, (size_t)N);
+    Out<float> oig;
+    Out<int32_t> otu, odi;
+    const int kk = k > 1 ? k - 1 : 1;
+    rc = bind_out(ws, ws->ig, ig, (size_t)n_jobs * M, &oig);
+    if (rc) return rc;
+    rc = bind_out(ws, ws->tuples, k > 1 ? tuples : (int32_t*)nullptr, (size_t)n_jobs * M * kk, &otu);
+    if (rc) return rc;
+    rc = bind_out(ws, ws->disc, best_disc, (size_t)n_jobs * M, &odi);
+    if (rc) return rc;
+    int* stats = (int*)ws->stats.p;
+    for (int j = 0; j < n_jobs; ++j) {
+        MDFS_CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * sizeof(int), st));
+        MDFS_LAUNCH("gather", st, launch_gather_job(xd, data->dtype, yd, N, M, idxd ? idxd + (size_t)j * N : nullptr,
+                                                    permd ? permd + (size_t)j * N : nullptr, ws->bx.p,
+                                                    (uint8_t*)ws->by.p, stats + 3, st));
+        MDFS_LAUNCH("stats", st, launch_stats((const uint8_t*)ws->by.p, N, stats, (int*)ws->perm.p, st));
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats, stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (ws->host_stats[3] != 0) return fail(MDFS_EINVAL, "job %d: sample or permutation index outside [0, N)", j);
+        const int n1 = ws->host_stats[0];
+        if (n1 == 0 || n1 == N) return fail(MDFS_EDEGENERATE, "job %d: decision has a single class", j);
+        bool check_err = false;
+        rc = scan_core(ws, ws->bx.p, data->dtype, N, M, n1, k, divisions, D, range, pc_xi, seed, &check_err);
+        if (rc) return rc;
+        MDFS_LAUNCH("finalize", st,
+                    launch_finalize((const unsigned long long*)ws->keys.p, M, k, oig.dev + (size_t)j * M,
+                                    otu.dev ? otu.dev + (size_t)j * M * kk : nullptr,
+                                    odi.dev ? odi.dev + (size_t)j * M : nullptr, st));
+        if (check_err) {
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+            const int flag = ws->host_stats[8];
+            if (flag & 2) return fail(MDFS_ECUDA, "triple kernel: dynamic shared memory smaller than its table layout");
+            if (flag != 0) return fail(MDFS_ETIMEOUT, "job %d: a device-side wait timed out in the triple kernel", j);
+        }
+    }
+    if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     return MDFS_OK;
 }
 

@@ -59,6 +59,11 @@ struct __align__(8) PairC {
 cudaError_t launch_stats(const uint8_t* y, int N, int* stats, int* perm, cudaStream_t st);
 cudaError_t launch_check_finite(const float* x, long long count, int* flag, cudaStream_t st);
 
+// Batch job j: x_j[v][t] = x[v][idx[t]], y_j[t] = y[yperm[idx[t]]] (NULL = identity);
+// out-of-range indices increment *flag.
+cudaError_t launch_gather_job(const void* x, int dtype, const uint8_t* y, int N, int M, const int* idx,
+                              const int* yperm, void* xo, uint8_t* yo, int* flag, cudaStream_t st);
+
 // int64 fixed-point tables T0[n] = f(n + b0), T1[n] = f(n + b1), TB[n] = f(n + b0 + b1),
 // n = 0..N, f(t) = t ln t; laid out as [3][N + 1].
 cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStream_t st);

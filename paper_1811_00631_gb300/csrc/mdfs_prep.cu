@@ -105,6 +105,57 @@ cudaError_t launch_check_finite(const float* x, long long count, int* flag, cuda
 }
 
 // ---------------------------------------------------------------------------
+// One job of a batch: x_j[v][t] = x[v][idx[t]], y_j[t] = y[yperm[idx[t]]]
+// (idx / yperm NULL = identity).  Indices outside [0, N) count in *flag and
+// read sample 0 instead.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void gather_job_kernel(const T* __restrict__ x, const uint8_t* __restrict__ y, int N, int M,
+                                  const int* __restrict__ idx, const int* __restrict__ yperm, T* __restrict__ xo,
+                                  uint8_t* __restrict__ yo, int* __restrict__ flag) {
+    const long long total = (long long)M * N;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int v = (int)(i / N), t = (int)(i - (long long)v * N);
+        int s = idx ? idx[t] : t;
+        if (s < 0 || s >= N) {
+            bad = 1;
+            s = 0;
+        }
+        xo[i] = x[(size_t)v * N + s];
+    }
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += stride) {
+        int s = idx ? idx[t] : (int)t;
+        if (s < 0 || s >= N) {
+            bad = 1;
+            s = 0;
+        }
+        int s2 = yperm ? yperm[s] : s;
+        if (s2 < 0 || s2 >= N) {
+            bad = 1;
+            s2 = 0;
+        }
+        yo[t] = y[s2];
+    }
+    if (bad) atomicAdd(flag, 1);
+}
+
+cudaError_t launch_gather_job(const void* x, int dtype, const uint8_t* y, int N, int M, const int* idx,
+                              const int* yperm, void* xo, uint8_t* yo, int* flag, cudaStream_t st) {
+    long long blocks = ((long long)M * N + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    if (dtype == 0)
+        gather_job_kernel<float><<<(int)blocks, 256, 0, st>>>((const float*)x, y, N, M, idx, yperm, (float*)xo, yo,
+                                                              flag);
+    else
+        gather_job_kernel<int8_t><<<(int)blocks, 256, 0, st>>>((const int8_t*)x, y, N, M, idx, yperm, (int8_t*)xo,
+                                                               yo, flag);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Entropy tables (Eqs. H, p, beta).  f(t) = t ln t in FP64, stored as int64
 // multiples of 2^-32 (round to nearest).
 // ---------------------------------------------------------------------------

@@ -32,7 +32,7 @@ _ERRORS = {
 
 EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
-            "mdfs_max_ig_noalloc")
+            "mdfs_max_ig_noalloc", "mdfs_max_ig_batch")
 
 
 class MdfsError(RuntimeError):
@@ -69,6 +69,9 @@ def load(path: str = LIB_PATH):
         lib.mdfs_max_ig_noalloc.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
         lib.mdfs_max_ig_noalloc.restype = ctypes.c_int
+        lib.mdfs_max_ig_batch.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
+        lib.mdfs_max_ig_batch.restype = ctypes.c_int
         lib.mdfs_ig_lim.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                     ctypes.c_double, P, P, P, P]
         lib.mdfs_ig_lim.restype = ctypes.c_int
@@ -201,6 +204,52 @@ def max_ig(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range
     _check(rc)
     del keep
     return ig, tu[:, : k - 1], di
+
+
+def max_ig_batch(x, y, sample_idx=None, y_perm=None, n_jobs=None, k: int = 2, divisions: int = 1,
+                 discretizations: int = 1, range_: float = 0.0, pc_xi: float = 0.25, seed: int = 0):
+    """mdfs_max_ig_batch: independent scans of resampled / label-permuted copies of (x, y).
+
+    Job j scans x[:, idx_j] with labels y[perm_j[idx_j]] (idx_j = sample_idx[j],
+    perm_j = y_perm[j]; None = identity).  Returns (ig [J, M], tuples [J, M, k-1],
+    disc [J, M]) on the device of x (CUDA tensors) or as numpy arrays.
+    """
+    lib = load()
+    data, keep = _data(x, y)
+    M, N = data.M, data.N
+    J = n_jobs if n_jobs is not None else (len(sample_idx) if sample_idx is not None else len(y_perm))
+    kk = max(k - 1, 1)
+
+    def index_ptr(a):
+        if a is None:
+            return None, None
+        if _is_cuda(a):
+            import torch
+            t = a.contiguous().to(torch.int32)
+            return ctypes.c_void_p(t.data_ptr()), t
+        h = _host(a, np.int32)
+        return ctypes.c_void_p(h.ctypes.data), h
+    ip, ik = index_ptr(sample_idx)
+    pp, pk = index_ptr(y_perm)
+    if _is_cuda(x):
+        import torch
+        ig = torch.empty((J, M), dtype=torch.float32, device=x.device)
+        tu = torch.empty((J, M, kk), dtype=torch.int32, device=x.device)
+        di = torch.empty((J, M), dtype=torch.int32, device=x.device)
+        ptrs = (ig.data_ptr(), tu.data_ptr(), di.data_ptr())
+        stream = _stream_of(x)
+    else:
+        ig = np.empty((J, M), np.float32)
+        tu = np.empty((J, M, kk), np.int32)
+        di = np.empty((J, M), np.int32)
+        ptrs = (ig.ctypes.data, tu.ctypes.data, di.ctypes.data)
+        stream = None
+    rc = lib.mdfs_max_ig_batch(ctypes.byref(data), J, ip, pp, k, divisions, discretizations, float(range_),
+                               float(pc_xi), int(seed) & (2**64 - 1), ctypes.c_void_p(ptrs[0]),
+                               ctypes.c_void_p(ptrs[1]) if k > 1 else None, ctypes.c_void_p(ptrs[2]), stream)
+    _check(rc)
+    del keep, ik, pk
+    return ig, tu[:, :, : k - 1], di
 
 
 def max_ig_noalloc(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range_: float = 0.0,
