@@ -45,6 +45,8 @@ struct Workspace {
     Buffer x, y, stats, perm, tab, planes, cnt1, sh1, keys, sh2, cnt2, items, ig, tuples, disc, codes, mask, pv, res;
     Buffer pairs2, items2, onehot, err;
     Buffer bx, by, bidx, bperm;  // batch: gathered job data and the job index maps
+    Buffer items3;               // k = 2 tensor-core tile list
+    int items3_M = -1, items3_c = -1, n_items3 = 0;
     int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
     double* host_res = nullptr; // pinned, 4 doubles
@@ -53,7 +55,7 @@ struct Workspace {
     ~Workspace() {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
-                         &onehot, &err, &bx,   &by,  &bidx, &bperm};
+                         &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -300,19 +302,40 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     unsigned long long* keys = (unsigned long long*)ws->keys.p;
 
     MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
-    // tensor-core triple path: two classes and tables that fit in shared memory
+    // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
+    // when their fixed-point tables fit in shared memory
+    const bool use_tc2 = (k == 2 && k2tc_supported(c) && k2tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     const bool use_tc3 = (k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     TcGeom tg = make_tc_geom(n0, n1);
     uint8_t* onehot = nullptr;
-    if (use_tc3) {
-        MDFS_ENSURE(ws, onehot, (size_t)D * M * tg.Kp);
+    if (use_tc2 || use_tc3) {
+        MDFS_ENSURE(ws, onehot, (size_t)D * M * P * tg.Kp);
         onehot = (uint8_t*)ws->onehot.p;
     }
     MDFS_LAUNCH("discretize", st, launch_discretize(xd, dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g,
                                                     planes, nullptr, nullptr, onehot, tg, st));
     MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
     MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
-    if (k == 2) {
+    if (use_tc2) {
+        MDFS_ENSURE(ws, err, sizeof(int));
+        MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
+        if (ws->items3_M != M || ws->items3_c != c) {
+            std::vector<int2> items;
+            build_k2tc_items(M, c, items);
+            MDFS_ENSURE(ws, items3, items.size() * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items3.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items3_M = M;
+            ws->items3_c = c;
+            ws->n_items3 = (int)items.size();
+        }
+        CUtensorMap map;
+        MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M * P, D, tg.Kp));
+        MDFS_LAUNCH("k2", st, launch_k2tc(map, tg, M, c, 0, D, (const int2*)ws->items3.p, ws->n_items3, tab,
+                                          k3tc_fraction_bits(N), cnt1, sh1, keys, (int*)ws->err.p, st));
+        *check_err = true;
+    } else if (k == 2) {
         MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st));
     } else if (use_tc3) {
         // two classes: symmetric 8-byte pair records and the tcgen05 triple kernel
@@ -547,8 +570,8 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
         const int flag = ws->host_stats[8];
-        if (flag & 2) return fail(MDFS_ECUDA, "triple kernel: dynamic shared memory smaller than its table layout");
-        if (flag != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in the triple kernel");
+        if (flag & 2) return fail(MDFS_ECUDA, "tensor-core kernel: dynamic shared memory smaller than its table layout");
+        if (flag != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in a tensor-core kernel");
     } else if (oig.staged || otu.staged || odi.staged || st == nullptr) {
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     }
@@ -633,7 +656,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
             MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
             MDFS_CUDA_TRY(cudaStreamSynchronize(st));
             const int flag = ws->host_stats[8];
-            if (flag & 2) return fail(MDFS_ECUDA, "triple kernel: dynamic shared memory smaller than its table layout");
+            if (flag & 2) return fail(MDFS_ECUDA, "tensor-core kernel: dynamic shared memory smaller than its table layout");
             if (flag != 0) return fail(MDFS_ETIMEOUT, "job %d: a device-side wait timed out in the triple kernel", j);
         }
     }

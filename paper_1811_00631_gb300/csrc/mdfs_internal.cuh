@@ -115,6 +115,15 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1,
                         const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st);
 
+// k = 2 on the tensor cores for c = 2, 3: one-hot rows M (c-1) through TMA
+// (map over [D][M (c-1)][Kp]), symmetric tiles (it <= mt) from build_k2tc_items.
+bool k2tc_supported(int c);
+void build_k2tc_items(int M, int c, std::vector<int2>& items);
+size_t k2tc_smem_bytes(int N0, int N1);
+cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
+                        int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
+                        unsigned long long* keys, int* err, cudaStream_t st);
+
 // keys [M] -> ig [M] f32, tuples [M][k-1] i32 (NULL ok), disc [M] i32 (NULL ok).
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,
                             int* disc, cudaStream_t st);

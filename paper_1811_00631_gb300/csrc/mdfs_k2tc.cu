@@ -1,0 +1,409 @@
+// k = 2 scan on the 5th-generation tensor cores (tcgen05, kind::f8f6f4) for
+// c = 2 or 3 classes per variable.  Voxel counters of section "Algorithm and
+// implementation"; the two IG roles of Eq. 1 with |S| = 1.
+//
+// Every (variable, bin >= 1) is one E4M3 one-hot row over the class-sorted
+// samples (rows v P + p, P = c - 1).  The pair counts of the voxels with both
+// coordinates >= 1 are the symmetric GEMM C = OH OH^T; class-0 and class-1
+// samples occupy separate K ranges and accumulate into two TMEM accumulators.
+// Tiles of 128 x 128 rows/columns on and above the diagonal; no operand needs
+// masking.  Counts are exact (0/1 products, FP32 sums below 2^24).
+//
+// Persistent kernel, one CTA per SM, 640 threads:
+//   warp 0       TMA producer (A rows, B rows; 128B swizzle),
+//   warp 1       TMEM owner and MMA issuer,
+//   warps 4-19   epilogue: tcgen05.ld, c x c tables per class by
+//                inclusion-exclusion, SH2 from int32 fixed-point tables in
+//                shared memory, IG(i | m) = SH1(m) - SH2 and IG(m | i), keys.
+// With c = 3 a variable spans two adjacent rows (TMEM lanes); the two lanes
+// exchange their counts with shuffles and split the 27 table lookups.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "mdfs_device.cuh"
+#include "mdfs_internal.cuh"
+#include "mdfs_tc.cuh"
+
+namespace mdfs {
+
+namespace {
+
+constexpr int kTile = 128;
+constexpr int kBK = 128;
+constexpr int kStages = 4;
+constexpr uint32_t kTileBytes = kTile * kBK;
+constexpr uint32_t kAccCols = 2 * kTile;
+constexpr uint32_t kTmemCols = 2 * kAccCols;
+constexpr int kThreads = 640;
+constexpr int kEpiWarp0 = 4, kEpiThreads = 512;
+constexpr int kColsPerWarp = 32;
+constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
+static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
+              "register split must add up to the launch allocation");
+constexpr size_t kTabOffset = 2 * kStages * kTileBytes;
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = tc::global_ns();
+    while (!tc::mbar_try_wait(bar, parity))
+        if (tc::global_ns() - t0 > tc::kWaitLimitNs) return;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k) {
+    const uint32_t hi = (uint32_t)(k >> 32);
+    const uint32_t hmax = __reduce_max_sync(0xffffffffu, hi);
+    const uint32_t lo = (hi == hmax) ? (uint32_t)k : 0u;
+    const uint32_t lmax = __reduce_max_sync(0xffffffffu, lo);
+    return ((unsigned long long)hmax << 32) | lmax;
+}
+
+__device__ __forceinline__ int tab32(const int* t, int n, int nmax) { return t[min((unsigned)n, (unsigned)nmax)]; }
+
+// c x c voxel counts of one channel from the all->=1 block X (P x P) and the
+// marginals of the row variable (ni[0..P-1]) and column variable (nm[..]).
+template <int P>
+__device__ __forceinline__ void complete2(const int (&X)[P][P], const int (&ni)[P], const int (&nm)[P], int ntot,
+                                          int (&T)[P + 1][P + 1]) {
+    int all = 0;
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+#pragma unroll
+        for (int b = 0; b < P; ++b) T[a + 1][b + 1] = X[a][b];
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        int s = 0;
+#pragma unroll
+        for (int b = 0; b < P; ++b) s += X[a][b];
+        T[a + 1][0] = ni[a] - s;
+        all += ni[a];
+    }
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        int s = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) s += X[a][b];
+        T[0][b + 1] = nm[b] - s;
+        all += T[0][b + 1];
+    }
+    T[0][0] = ntot - all;
+}
+
+}  // namespace
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+    k2tc_kernel(const __grid_constant__ CUtensorMap map_oh, TcGeom tg, int M, int d0, int nd,
+                const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
+                const int* __restrict__ cnt1, const long long* __restrict__ sh1, unsigned long long* __restrict__ keys,
+                int* __restrict__ err) {
+    constexpr int C = P + 1;
+    constexpr int VT = kTile / P;  // variables per tile
+    extern __shared__ uint8_t dsmem_raw[];
+    __shared__ uint64_t bar_full[kStages], bar_empty[kStages];
+    __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* base = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
+    uint8_t* sA = base;
+    uint8_t* sB = base + kStages * kTileBytes;
+    const int N0 = tg.N0, N1 = tg.N1, N = N0 + N1, np1 = N + 1;
+    int* sT0 = reinterpret_cast<int*>(base + kTabOffset);
+    int* sT1 = sT0 + (N0 + 1);
+    int* sTB = sT1 + (N1 + 1);
+    volatile int* abort = &s_abort;
+
+    uint32_t dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    const bool fits = (size_t)(base - dsmem_raw) + kTabOffset + (size_t)(2 * N + 3) * sizeof(int) <= dyn_bytes;
+
+    if (tid == 0) {
+        s_abort = (*(volatile int*)err ? 1 : 0) | (fits ? 0 : 2);
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&bar_full[s], 1);
+            tc::mbar_init(&bar_empty[s], 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            tc::mbar_init(&bar_tfull[j], 1);
+            tc::mbar_init(&bar_tempty[j], kEpiThreads);
+        }
+        tc::mbar_init(&bar_drain, 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&s_tmem, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    if (fits) {
+        for (int i = tid; i <= N0; i += kThreads) sT0[i] = fx_narrow(tab[i], fbits);
+        for (int i = tid; i <= N1; i += kThreads) sT1[i] = fx_narrow(tab[np1 + i], fbits);
+        for (int i = tid; i <= N; i += kThreads) sTB[i] = fx_narrow(tab[2 * np1 + i], fbits);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const int n_tiles = n_items * nd;
+    const int nkb = tg.nkb;
+
+    if (warp < kEpiWarp0) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsProducer));
+        if (warp == 0) {
+            // ------------------------------ TMA producer --------------------------
+            if (lane == 0 && !*abort) {
+                uint32_t g = 0;
+                int pend_mask = 0;
+                uint32_t pend_use[kStages] = {};
+                for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
+                    const int2 item = items[t % n_items];
+                    const int d = d0 + t / n_items;
+                    const int r0 = item.x * kTile, c0 = item.y * kTile;
+                    bool ok = true;
+                    for (int kb = 0; kb < nkb; ++kb, ++g) {
+                        const int s = (int)(g % kStages);
+                        const uint32_t use = g / kStages;
+                        if (use > 0 && !tc::mbar_wait(&bar_empty[s], (use - 1) & 1, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(&bar_full[s], 2 * kTileBytes);
+                        tc::tma_load_3d(sA + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, r0, d);
+                        tc::tma_load_3d(sB + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, c0, d);
+                        pend_mask |= 1 << s;
+                        pend_use[s] = use;
+                    }
+                    if (!ok) break;
+                }
+                for (int s = 0; s < kStages; ++s)
+                    if (pend_mask & (1 << s)) mbar_drain(&bar_full[s], pend_use[s] & 1);
+            }
+        } else if (warp == 1) {
+            // ------------------------------ MMA issuer ----------------------------
+            if (lane == 0 && !*abort) {
+                const uint32_t idesc = tc::idesc_e4m3_f32(kTile, kTile);
+                uint32_t g = 0;
+                int i = 0;
+                bool issued = false;
+                for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
+                    const int buf = i & 1;
+                    const uint32_t tuse = (uint32_t)(i >> 1);
+                    if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort)) break;
+                    tc::tc_fence_after();
+                    const uint32_t dbase = tmem + (uint32_t)buf * kAccCols;
+                    bool ok = true;
+                    for (int kb = 0; kb < nkb; ++kb, ++g) {
+                        const int s = (int)(g % kStages);
+                        const uint32_t use = g / kStages;
+                        if (!tc::mbar_wait(&bar_full[s], use & 1, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t d_tmem = dbase + (kb >= tg.nkb0 ? (uint32_t)kTile : 0u);
+                        const uint32_t a_addr = tc::smem_u32(sA + s * kTileBytes);
+                        const uint32_t b_addr = tc::smem_u32(sB + s * kTileBytes);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 32; ++kk) {
+                            const uint32_t acc = (kb != 0 && kb != tg.nkb0) || kk > 0;
+                            tc::mma_f8(d_tmem, tc::sw128_kmajor_desc(a_addr + 32 * kk),
+                                       tc::sw128_kmajor_desc(b_addr + 32 * kk), idesc, acc);
+                        }
+                        tc::mma_commit(&bar_empty[s]);
+                        issued = true;
+                    }
+                    if (!ok) break;
+                    tc::mma_commit(&bar_tfull[buf]);
+                }
+                if (issued) {
+                    tc::mma_commit(&bar_drain);
+                    mbar_drain(&bar_drain, 0);
+                }
+            }
+        }
+        // warps 2-3 have no role in this kernel
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpilogue));
+        // ------------------------------ epilogue ----------------------------------
+        const int ew = warp - kEpiWarp0;
+        const int q = warp & 3, h = ew >> 2;  // TMEM lane quarter, column quarter
+        const int row = 32 * q + lane;
+        const int alpha = row % P;            // bin index (0-based) of this row
+        const float inv_scale = __int_as_float((127 - fbits) << 23);
+        int i = 0;
+        for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            const uint32_t tuse = (uint32_t)(i >> 1);
+            const int2 item = items[t % n_items];
+            const int dl = t / n_items, d = d0 + dl;
+            const int vi = item.x * VT + row / P;       // row variable
+            const int vm0 = item.y * VT + (kColsPerWarp / P) * h;  // first column variable of this warp
+            const bool diag = item.x == item.y;
+            const int* c1 = cnt1 + (size_t)d * M * P * 2;
+            const long long* s1 = sh1 + (size_t)d * M;
+            const bool irow = vi < M;
+            // row-variable context
+            int ni0[P], ni1[P], nit[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                ni0[p] = irow ? c1[((size_t)vi * P + p) * 2] : 0;
+                ni1[p] = irow ? c1[((size_t)vi * P + p) * 2 + 1] : 0;
+                nit[p] = ni0[p] + ni1[p];
+            }
+            const int shi = irow ? fx_narrow(s1[vi], fbits) : 0;
+            const uint32_t dM = (uint32_t)d * (uint32_t)M;
+
+            if (!tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort)) break;
+            tc::tc_fence_after();
+            unsigned long long ki = 0ull;
+            const bool warp_rows = (item.x * VT + (32 * q) / P) < M;
+            if (warp_rows && vm0 < M) {
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kAccCols +
+                                       (uint32_t)(kColsPerWarp * h);
+                uint32_t r0[kColsPerWarp], r1[kColsPerWarp];
+                tc::tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(&r0[0]));
+                tc::tmem_ld16(taddr + 16, *reinterpret_cast<uint32_t(*)[16]>(&r0[16]));
+                tc::tmem_ld16(taddr + kTile, *reinterpret_cast<uint32_t(*)[16]>(&r1[0]));
+                tc::tmem_ld16(taddr + kTile + 16, *reinterpret_cast<uint32_t(*)[16]>(&r1[16]));
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int jm = 0; jm < kColsPerWarp / P; ++jm) {
+                    const int vm = vm0 + jm;
+                    const bool ok = irow && vm < M && (!diag || vi < vm);
+                    // counts of the all->=1 block, both classes: X?[alpha][beta] here,
+                    // the other row(s) of the block from the neighbouring lane
+                    int X0[P][P], X1[P][P];
+#pragma unroll
+                    for (int b = 0; b < P; ++b) {
+                        const int v0 = (int)__uint_as_float(r0[jm * P + b]);
+                        const int v1 = (int)__uint_as_float(r1[jm * P + b]);
+                        if (P == 1) {
+                            X0[0][b] = v0;
+                            X1[0][b] = v1;
+                        } else {
+                            const int o0 = __shfl_xor_sync(0xffffffffu, v0, 1);
+                            const int o1 = __shfl_xor_sync(0xffffffffu, v1, 1);
+                            X0[0][b] = alpha ? o0 : v0;
+                            X0[P - 1][b] = alpha ? v0 : o0;
+                            X1[0][b] = alpha ? o1 : v1;
+                            X1[P - 1][b] = alpha ? v1 : o1;
+                        }
+                    }
+                    // column-variable context
+                    int nm0[P], nm1[P], nmt[P];
+                    const int vmc = ok ? vm : 0;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        nm0[p] = c1[((size_t)vmc * P + p) * 2];
+                        nm1[p] = c1[((size_t)vmc * P + p) * 2 + 1];
+                        nmt[p] = nm0[p] + nm1[p];
+                    }
+                    int XT[P][P];
+#pragma unroll
+                    for (int a = 0; a < P; ++a)
+#pragma unroll
+                        for (int b = 0; b < P; ++b) XT[a][b] = X0[a][b] + X1[a][b];
+                    int T0v[C][C], T1v[C][C], TTv[C][C];
+                    complete2<P>(X0, ni0, nm0, N0, T0v);
+                    complete2<P>(X1, ni1, nm1, N1, T1v);
+                    complete2<P>(XT, nit, nmt, N, TTv);
+                    int part = 0;
+                    if (P == 1) {
+#pragma unroll
+                        for (int a = 0; a < C; ++a)
+#pragma unroll
+                            for (int b = 0; b < C; ++b)
+                                part += tab32(sTB, TTv[a][b], N) - tab32(sT0, T0v[a][b], N0) -
+                                        tab32(sT1, T1v[a][b], N1);
+                    } else {
+                        // the two lanes of a variable split the lookups without diverging:
+                        // lane alpha = 0 takes class 0 and total voxels 0..4, alpha = 1
+                        // takes class 1 and total voxels 5..8
+                        const int* tcls = alpha ? sT1 : sT0;
+                        const int ncls = alpha ? N1 : N0;
+#pragma unroll
+                        for (int a = 0; a < C; ++a)
+#pragma unroll
+                            for (int b = 0; b < C; ++b) part -= tab32(tcls, alpha ? T1v[a][b] : T0v[a][b], ncls);
+#pragma unroll
+                        for (int u = 0; u < 5; ++u) {
+                            const int lo = TTv[u / C][u % C];
+                            const int hi = u + 5 < C * C ? TTv[(u + 5) / C][(u + 5) % C] : 0;
+                            const int v = tab32(sTB, alpha ? hi : lo, N);
+                            part += (alpha && u + 5 >= C * C) ? 0 : v;
+                        }
+                        part += __shfl_xor_sync(0xffffffffu, part, 1);
+                    }
+                    const int sh2 = part;
+                    unsigned long long k_m = 0ull;
+                    if (ok) {
+                        if (P == 1 || alpha == 0) {
+                            // IG(i | m) = SH1(m) - SH2
+                            const float g = (float)(fx_narrow(s1[vm], fbits) - sh2) * inv_scale;
+                            ki = umax64(ki, pack_key(g, dM + (uint32_t)vm));
+                        }
+                        if (P == 1 || alpha == 1) {
+                            // IG(m | i) = SH1(i) - SH2
+                            const float g = (float)(shi - sh2) * inv_scale;
+                            k_m = pack_key(g, dM + (uint32_t)vi);
+                        }
+                    }
+                    const unsigned long long mk = warp_max_key(k_m);
+                    if (lane == 0 && mk) atomicMax(keys + vm, mk);
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&bar_tempty[buf]);
+            if (ki) atomicMax(keys + vi, ki);
+        }
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, kTmemCols);
+    if (tid == 0 && *abort) atomicOr(err, *abort);
+}
+
+void build_k2tc_items(int M, int c, std::vector<int2>& items) {
+    const int P = c - 1;
+    const int nt = (M * P + kTile - 1) / kTile;
+    items.clear();
+    for (int it = 0; it < nt; ++it)
+        for (int mt = it; mt < nt; ++mt) items.push_back(make_int2(it, mt));
+}
+
+size_t k2tc_smem_bytes(int N0, int N1) {
+    return kTabOffset + (size_t)(2 * (N0 + N1) + 3) * sizeof(int) + 1024;
+}
+
+bool k2tc_supported(int c) { return c == 2 || c == 3; }
+
+cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
+                        int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
+                        unsigned long long* keys, int* err, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    const size_t smem = k2tc_smem_bytes(tg.N0, tg.N1);
+    const void* fn = c == 2 ? (const void*)k2tc_kernel<1> : (const void*)k2tc_kernel<2>;
+    if (c != 2 && c != 3) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_dynamic_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+    if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long n_tiles = (long long)n_items * nd;
+    if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
+    if (c == 2)
+        k2tc_kernel<1><<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys,
+                                                     err);
+    else
+        k2tc_kernel<2><<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys,
+                                                     err);
+    return cudaGetLastError();
+}
+
+}  // namespace mdfs

@@ -25,13 +25,28 @@ def cuda():
     return torch
 
 
-def _compare(torch, got, want, k):
+def _compare(torch, got, want, k, x=None, y=None, div=None, D=None, r=None, xi=None, seed=None):
+    """IG within the tolerance of the parity tests.  The two entry points may
+    sum the entropies in different fixed-point widths, so where their argmax
+    (discretisation, partner) differ both must be maximisers within that
+    tolerance (checked with the FP64 oracle)."""
     g_ig, g_tu, g_di = (t.cpu().numpy() for t in got)
     w_ig, w_tu, w_di = (t.cpu().numpy() for t in want)
-    assert np.all(np.abs(g_ig.astype(np.float64) - w_ig) <= ATOL + RTOL * np.abs(w_ig))
-    assert np.array_equal(g_di, w_di)
+    tol = ATOL + RTOL * np.abs(w_ig)
+    assert np.all(np.abs(g_ig.astype(np.float64) - w_ig) <= tol)
+    diff = g_di != w_di
     if k == 2:
-        assert np.array_equal(g_tu, w_tu)
+        diff |= g_tu[:, 0] != w_tu[:, 0]
+    if diff.any():
+        import oracle
+        codes = oracle.discretize(x, div, D, r, seed)
+        c = div + 1
+        for i in np.nonzero(diff)[0]:
+            S = [int(g_tu[i, 0])] if k == 2 else []
+            Sw = [int(w_tu[i, 0])] if k == 2 else []
+            a = oracle.ig_one(codes, y, c, xi, int(g_di[i]), int(i), S)
+            b = oracle.ig_one(codes, y, c, xi, int(w_di[i]), int(i), Sw)
+            assert abs(a - b) <= 2 * tol[i], f"variable {i}: argmax differ by more than the tolerance"
 
 
 def test_two_calls_in_a_row_match_the_allocating_entry_point(cuda):
@@ -48,7 +63,7 @@ def test_two_calls_in_a_row_match_the_allocating_entry_point(cuda):
         want = mdfs.max_ig(x, y, k, div, D, r, xi, seed)
         got = mdfs.max_ig_noalloc(x, y, k, div, D, r, xi, seed)
         torch.cuda.synchronize()
-        _compare(torch, got, want, k)
+        _compare(torch, got, want, k, ds.x, ds.y, div, D, r, xi, seed)
 
 
 def test_int8_input_and_side_stream(cuda):
@@ -63,7 +78,7 @@ def test_int8_input_and_side_stream(cuda):
     with torch.cuda.stream(s):
         got = mdfs.max_ig_noalloc(x8, y, 2, 2, 5, 0.6, 0.25, 11)
     s.synchronize()
-    _compare(torch, got, want, 2)
+    _compare(torch, got, want, 2, x8.cpu().numpy().astype(np.float32), y.cpu().numpy(), 2, 5, 0.6, 0.25, 11)
 
 
 def test_rejects_oversize_and_host_pointers(cuda):
