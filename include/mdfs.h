@@ -124,6 +124,28 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
                       int32_t* tuples, int32_t* best_disc, void* stream);
 
 /*
+ * Sharded scan of one job over several processes or GPUs (the tuple space of
+ * Eq. 1 is embarrassingly parallel).  Shard `shard` of `n_shards` scans its
+ * contiguous share of the tuple tiles (the pair path without tensor cores and
+ * k = 1 run whole on shard 0) and writes the packed max keys:
+ *     key = (order-preserving bits of float IG) << 32 | ~(tie-break index),
+ *     index = d M + m (k = 2), (d M + m1) M + m2 (k = 3), d (k = 1),
+ * so that a larger key is a larger IG and, on a tie, the lower (d, S).  The
+ * element-wise UNSIGNED maximum of all shards' keys equals the keys of the
+ * unsharded scan exactly (for a signed all-reduce, flip bit 63 before and
+ * after).  keys_out: [M] uint64, host or device.  Returns after completion.
+ */
+int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretizations, double range, double pc_xi,
+                      uint64_t seed, int shard, int n_shards, uint64_t* keys_out, void* stream);
+
+/*
+ * Decodes merged keys into the outputs of mdfs_max_ig (same meaning):
+ * ig [M] float, tuples [M][k-1] or NULL, best_disc [M] or NULL; keys of 0
+ * (no candidate) give NaN and discretisation -1.  Host or device pointers.
+ */
+int mdfs_keys_decode(const uint64_t* keys, int M, int k, float* ig, int32_t* tuples, int32_t* best_disc, void* stream);
+
+/*
  * Significance of IG^k_max (section "Theory"): a single tuple's 2 IG is
  * chi^2 with df = (c-1) c^(k-1) degrees of freedom; the maximum over T
  * effective tests has CDF F_df(2 g)^T.  T is fitted by maximum likelihood on

@@ -279,9 +279,17 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
 // The scan of one job whose x and y are on the device and validated (ws->perm
 // holds the class-stable order, n1 the class-1 count): entropy tables,
 // discretisation and the counting kernels.  Leaves the packed max keys in ws->keys.
+// shard / n_shards: this call folds only its share of the tuple tiles into the
+// keys (tensor-core and generic triple paths); the popcount pair path and k = 1
+// run whole on shard 0.  Merging the keys of all shards by maximum gives the
+// keys of the unsharded scan.
 int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, int k, int divisions, int D, double range,
-              double pc_xi, uint64_t seed, bool* check_err) {
+              double pc_xi, uint64_t seed, bool* check_err, int shard = 0, int n_shards = 1) {
     cudaStream_t st = ws->stream;
+    auto share = [&](int n, int* lo) {
+        *lo = (int)((long long)n * shard / n_shards);
+        return (int)((long long)n * (shard + 1) / n_shards) - *lo;
+    };
     const int c = divisions + 1;
     *check_err = false;
     const int n0 = N - n1;
@@ -315,7 +323,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     MDFS_LAUNCH("discretize", st, launch_discretize(xd, dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g,
                                                     planes, nullptr, nullptr, onehot, tg, st));
     MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
-    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, k == 1 ? keys : nullptr, st));
+    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, (k == 1 && shard == 0) ? keys : nullptr, st));
     if (use_tc2) {
         MDFS_ENSURE(ws, err, sizeof(int));
         MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
@@ -332,11 +340,14 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         }
         CUtensorMap map;
         MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M * P, D, tg.Kp));
-        MDFS_LAUNCH("k2", st, launch_k2tc(map, tg, M, c, 0, D, (const int2*)ws->items3.p, ws->n_items3, tab,
+        int lo = 0;
+        const int cnt = share(ws->n_items3, &lo);
+        MDFS_LAUNCH("k2", st, launch_k2tc(map, tg, M, c, 0, D, (const int2*)ws->items3.p + lo, cnt, tab,
                                           k3tc_fraction_bits(N), cnt1, sh1, keys, (int*)ws->err.p, st));
         *check_err = true;
     } else if (k == 2) {
-        MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st));
+        if (shard == 0)
+            MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st));
     } else if (use_tc3) {
         // two classes: symmetric 8-byte pair records and the tcgen05 triple kernel
         const size_t per_disc = (size_t)M * M * sizeof(PairC);
@@ -365,9 +376,10 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
                                                    nullptr, (PairC*)ws->pairs2.p, fbits, st));
-            MDFS_LAUNCH("k3", st, launch_k3tc(map, onehot, tg, M, d0, nn, (const int2*)ws->items2.p, ws->n_items2,
-                                              tab, fbits, cnt1, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p,
-                                              st));
+            int lo = 0;
+            const int cnt = share(ws->n_items2, &lo);
+            MDFS_LAUNCH("k3", st, launch_k3tc(map, onehot, tg, M, d0, nn, (const int2*)ws->items2.p + lo, cnt, tab,
+                                              fbits, cnt1, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, st));
         }
         *check_err = true;
     } else if (k == 3) {
@@ -394,8 +406,10 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
                                                    (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
-            MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p, ws->n_items, tab, cnt1,
-                                        (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
+            int lo = 0;
+            const int cnt = share(ws->n_items, &lo);
+            MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p + lo, cnt, tab,
+                                                  cnt1, (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
         }
     }
 
@@ -660,6 +674,77 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
             if (flag != 0) return fail(MDFS_ETIMEOUT, "job %d: a device-side wait timed out in the triple kernel", j);
         }
     }
+    if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretizations, double range, double pc_xi,
+                      uint64_t seed, int shard, int n_shards, uint64_t* keys_out, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, true);
+    if (rc) return rc;
+    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    if (n_shards < 1 || shard < 0 || shard >= n_shards) return fail(MDFS_EINVAL, "shard %d of %d", shard, n_shards);
+    if (k < 1 || k > 3) return fail(MDFS_EINVAL, "k = %d outside [1, 3]", k);
+    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
+    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
+    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
+    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if (!keys_out) return fail(MDFS_EINVAL, "keys is NULL");
+    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
+    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    rc = stage_inputs(ws, data, true, &xd, &yd, &n1);
+    if (rc) return rc;
+    bool check_err = false;
+    rc = scan_core(ws, xd, data->dtype, N, M, n1, k, divisions, D, range, pc_xi, seed, &check_err, shard, n_shards);
+    if (rc) return rc;
+    MDFS_CUDA_TRY(cudaMemcpyAsync(keys_out, ws->keys.p, (size_t)M * sizeof(uint64_t), cudaMemcpyDefault, st));
+    if (check_err) {
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+        const int flag = ws->host_stats[8];
+        if (flag & 2) return fail(MDFS_ECUDA, "tensor-core kernel: dynamic shared memory smaller than its table layout");
+        if (flag != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in a tensor-core kernel");
+    }
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_keys_decode(const uint64_t* keys, int M, int k, float* ig, int32_t* tuples, int32_t* best_disc, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    if (!keys || !ig) return fail(MDFS_EINVAL, "keys and ig must not be NULL");
+    if (M < 1 || M > 65535 || k < 1 || k > 3) return fail(MDFS_EINVAL, "M or k out of range");
+    int rc = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const unsigned long long* kd = (const unsigned long long*)keys;
+    if (!is_device_ptr(keys)) {
+        MDFS_ENSURE(ws, keys, (size_t)M * sizeof(uint64_t));
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->keys.p, keys, (size_t)M * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        kd = (const unsigned long long*)ws->keys.p;
+    }
+    Out<float> oig;
+    Out<int32_t> otu, odi;
+    rc = bind_out(ws, ws->ig, ig, (size_t)M, &oig);
+    if (rc) return rc;
+    rc = bind_out(ws, ws->tuples, k > 1 ? tuples : (int32_t*)nullptr, (size_t)M * (k > 1 ? k - 1 : 1), &otu);
+    if (rc) return rc;
+    rc = bind_out(ws, ws->disc, best_disc, (size_t)M, &odi);
+    if (rc) return rc;
+    MDFS_LAUNCH("finalize", st, launch_finalize(kd, M, k, oig.dev, otu.dev, odi.dev, st));
     if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     return MDFS_OK;

@@ -32,7 +32,7 @@ _ERRORS = {
 
 EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
-            "mdfs_max_ig_noalloc", "mdfs_max_ig_batch")
+            "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode")
 
 
 class MdfsError(RuntimeError):
@@ -72,6 +72,12 @@ def load(path: str = LIB_PATH):
         lib.mdfs_max_ig_batch.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
         lib.mdfs_max_ig_batch.restype = ctypes.c_int
+        lib.mdfs_max_ig_shard.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                          P, P]
+        lib.mdfs_max_ig_shard.restype = ctypes.c_int
+        lib.mdfs_keys_decode.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P]
+        lib.mdfs_keys_decode.restype = ctypes.c_int
         lib.mdfs_ig_lim.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                     ctypes.c_double, P, P, P, P]
         lib.mdfs_ig_lim.restype = ctypes.c_int
@@ -250,6 +256,35 @@ def max_ig_batch(x, y, sample_idx=None, y_perm=None, n_jobs=None, k: int = 2, di
     _check(rc)
     del keep, ik, pk
     return ig, tu[:, :, : k - 1], di
+
+
+def max_ig_shard(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range_: float = 0.0,
+                 pc_xi: float = 0.25, seed: int = 0, shard: int = 0, n_shards: int = 1) -> np.ndarray:
+    """Packed max keys (uint64 [M], host) of shard `shard` of `n_shards` of the scan."""
+    lib = load()
+    data, keep = _data(x, y)
+    keys = np.zeros(data.M, dtype=np.uint64)
+    stream = _stream_of(x) if _is_cuda(x) else None
+    rc = lib.mdfs_max_ig_shard(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
+                               int(seed) & (2**64 - 1), shard, n_shards, ctypes.c_void_p(keys.ctypes.data), stream)
+    _check(rc)
+    del keep
+    return keys
+
+
+def decode_keys(keys: np.ndarray, k: int):
+    """(ig, tuples, disc) numpy arrays of merged keys, as max_ig returns them."""
+    lib = load()
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    M = len(keys)
+    ig = np.empty(M, np.float32)
+    tu = np.empty((M, max(k - 1, 1)), np.int32)
+    di = np.empty(M, np.int32)
+    rc = lib.mdfs_keys_decode(ctypes.c_void_p(keys.ctypes.data), M, k, ctypes.c_void_p(ig.ctypes.data),
+                              ctypes.c_void_p(tu.ctypes.data) if k > 1 else None, ctypes.c_void_p(di.ctypes.data),
+                              None)
+    _check(rc)
+    return ig, tu[:, : k - 1], di
 
 
 def max_ig_noalloc(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range_: float = 0.0,

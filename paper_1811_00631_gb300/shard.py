@@ -1,0 +1,62 @@
+"""Merging the packed max keys of a scan sharded over processes or GPUs.
+
+The scan's per-variable result is a 64-bit key: the order-preserving bits of
+the float IG in the high word and the complement of the tie-break index
+(discretisation and partner set) in the low word, so that the element-wise
+unsigned maximum over shards is the result of the unsharded scan.  torch has
+no unsigned 64-bit all-reduce, so keys travel as int64 with bit 63 flipped,
+which maps unsigned order onto signed order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_FLIP = np.uint64(1) << np.uint64(63)
+
+
+def to_signed_order(keys_u64: np.ndarray) -> np.ndarray:
+    """uint64 keys -> int64 values with the same order under signed comparison."""
+    return (np.asarray(keys_u64, dtype=np.uint64) ^ _FLIP).view(np.int64)
+
+
+def from_signed_order(vals_i64: np.ndarray) -> np.ndarray:
+    return (np.asarray(vals_i64, dtype=np.int64).view(np.uint64) ^ _FLIP)
+
+
+def merge(keys_per_shard) -> np.ndarray:
+    """Element-wise unsigned maximum of the shards' keys (host)."""
+    out = None
+    for k in keys_per_shard:
+        k = np.asarray(k, dtype=np.uint64)
+        out = k.copy() if out is None else np.maximum(out, k)
+    return out
+
+
+def allreduce_max(keys_u64: np.ndarray, group=None) -> np.ndarray:
+    """All-reduce MAX of uint64 keys across a torch.distributed group (any backend)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(to_signed_order(keys_u64).copy())
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return from_signed_order(t.numpy())
+
+
+# --- key format (mirrors the device packing; used to build test candidates) ---
+def pack(ig: np.ndarray, index: np.ndarray) -> np.ndarray:
+    """Keys of float32 IG values and uint32 tie-break indices."""
+    b = np.asarray(ig, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    neg = (b & np.uint64(0x80000000)) != 0
+    ordered = np.where(neg, (~b) & np.uint64(0xFFFFFFFF), b | np.uint64(0x80000000))
+    return (ordered << np.uint64(32)) | ((~np.asarray(index, dtype=np.uint64)) & np.uint64(0xFFFFFFFF))
+
+
+def unpack(keys: np.ndarray):
+    """(IG float32, index uint32) of keys (keys of 0 give NaN, index 2^32-1)."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    ordered = keys >> np.uint64(32)
+    pos = (ordered & np.uint64(0x80000000)) != 0
+    bits = np.where(pos, ordered & np.uint64(0x7FFFFFFF), (~ordered) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    ig = bits.view(np.float32).copy()
+    ig[keys == 0] = np.nan
+    index = ((~keys) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    return ig, index

@@ -72,3 +72,17 @@ def test_batch_rejects_bad_indices(cuda):
     with pytest.raises(mdfs.MdfsError) as e:
         mdfs.max_ig_batch(ds.x, ds.y, si, None, k=2)
     assert e.value.code in (-1, -2)
+
+
+@pytest.mark.parametrize("k,div,M,N", [(2, 1, 300, 500), (2, 2, 90, 400), (3, 1, 160, 300), (3, 2, 40, 200),
+                                      (1, 1, 50, 200)])
+def test_sharded_scan_merges_to_the_unsharded_result(cuda, k, div, M, N):
+    """Three shards scanned one after another on one GPU, merged by unsigned
+    maximum, decode to exactly the result of the unsharded scan."""
+    from paper_1811_00631_gb300 import mdfs, shard
+    ds = synth.xor_pairs(N=N, M=M, n_pairs=4, seed=M)
+    want = mdfs.max_ig(ds.x, ds.y, k, div, 3, 0.5, 0.25, 21)
+    keys = shard.merge([mdfs.max_ig_shard(ds.x, ds.y, k, div, 3, 0.5, 0.25, 21, s, 3) for s in range(3)])
+    got = mdfs.decode_keys(keys, k)
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)

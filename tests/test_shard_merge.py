@@ -1,0 +1,99 @@
+"""Host logic of the sharded scan: the key format and the MAX merge across
+ranks (torch.distributed, gloo, world size 2, on CPU)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1811_00631_gb300 import shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _candidates(seed, M=37, n=4000):
+    """Random candidate (variable, IG, index) triples with exact ties."""
+    rng = np.random.default_rng(seed)
+    var = rng.integers(0, M, n)
+    ig = np.round(rng.normal(0, 3, n), 1).astype(np.float32)  # many exact ties, both signs
+    idx = rng.integers(0, 2**31, n).astype(np.uint64)
+    return var, ig, idx
+
+
+def _reference(var, ig, idx, M):
+    """Max IG per variable, ties to the lowest index (plain loops)."""
+    best = [None] * M
+    for v, g, i in zip(var, ig, idx):
+        if best[v] is None or g > best[v][0] or (g == best[v][0] and i < best[v][1]):
+            best[v] = (g, i)
+    return best
+
+
+def _keys_of(var, ig, idx, M):
+    keys = np.zeros(M, np.uint64)
+    packed = shard.pack(ig, idx)
+    for v, k in zip(var, packed):
+        keys[v] = max(keys[v], k)
+    return keys
+
+
+def test_key_order_is_ig_then_lowest_index():
+    ig = np.array([-5.5, -0.0, 0.0, 1e-30, 2.0, 2.0, np.float32(3e38)], np.float32)
+    idx = np.array([1, 2, 3, 4, 9, 5, 0], np.uint64)
+    keys = shard.pack(ig, idx)
+    order = np.argsort(keys)
+    assert list(order[-2:]) == [5, 6]               # 2.0 with index 5 beats 2.0 with index 9
+    assert keys[5] > keys[4] and keys[0] < keys[1] < keys[3]
+    g, i = shard.unpack(keys)
+    assert np.array_equal(g, ig) and np.array_equal(i.astype(np.uint64), idx)
+    # flipping bit 63 maps unsigned order onto signed order
+    assert np.array_equal(np.argsort(shard.to_signed_order(keys), kind="stable"), np.argsort(keys, kind="stable"))
+    assert np.array_equal(shard.from_signed_order(shard.to_signed_order(keys)), keys)
+
+
+def test_merge_of_shards_equals_global_max():
+    M = 37
+    var, ig, idx = _candidates(1, M)
+    parts = np.array_split(np.arange(len(var)), 5)
+    keys = shard.merge([_keys_of(var[p], ig[p], idx[p], M) for p in parts])
+    ref = _reference(var, ig, idx, M)
+    g, i = shard.unpack(keys)
+    for v in range(M):
+        assert (g[v], i[v]) == (ref[v][0], ref[v][1])
+
+
+def _rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    M = 37
+    var, ig, idx = _candidates(2, M)
+    mine = np.arange(len(var))[rank::world]  # disjoint shares of the tuple space
+    merged = shard.allreduce_max(_keys_of(var[mine], ig[mine], idx[mine], M))
+    np.save(out_path + f".{rank}.npy", merged)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_allreduce_merge(tmp_path):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    port = _free_port()
+    out = str(tmp_path / "keys")
+    mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
+    k0 = np.load(out + ".0.npy")
+    k1 = np.load(out + ".1.npy")
+    assert np.array_equal(k0, k1)
+    M = 37
+    var, ig, idx = _candidates(2, M)
+    ref = _reference(var, ig, idx, M)
+    g, i = shard.unpack(k0)
+    for v in range(M):
+        assert (g[v], i[v]) == (ref[v][0], ref[v][1])
