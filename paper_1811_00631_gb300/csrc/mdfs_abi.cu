@@ -46,6 +46,7 @@ struct Workspace {
     Buffer pairs2, items2, onehot, err;
     Buffer bx, by, bidx, bperm;  // batch: gathered job data and the job index maps
     Buffer items3;               // k = 2 tensor-core tile list
+    Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
     int items3_M = -1, items3_c = -1, n_items3 = 0;
     int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
@@ -55,7 +56,8 @@ struct Workspace {
     ~Workspace() {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
-                         &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3};
+                         &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
+                         &onehot2};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -370,16 +372,27 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             ws->items2_M = M;
             ws->n_items2 = (int)items.size();
         }
+        // relabel the variables of every discretisation by bin-1 count and
+        // store the one-hot rows in that order
+        MDFS_ENSURE(ws, lperm, (size_t)D * M * sizeof(int));
+        MDFS_ENSURE(ws, lrank, (size_t)D * M * sizeof(int));
+        MDFS_ENSURE(ws, cnt1s, (size_t)D * M * 2 * sizeof(int));
+        MDFS_ENSURE(ws, onehot2, (size_t)D * M * tg.Kp);
+        const int* lperm = (const int*)ws->lperm.p;
+        MDFS_LAUNCH("k3_order", st, launch_k3tc_order(cnt1, M, D, (int*)ws->lperm.p, (int*)ws->lrank.p,
+                                                      (int*)ws->cnt1s.p, st));
+        MDFS_LAUNCH("k3_permute", st, launch_permute_rows(onehot, (uint8_t*)ws->onehot2.p, lperm, M, D, tg.Kp, st));
         CUtensorMap map;
-        MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M, D, tg.Kp));
+        MDFS_CUDA_TRY(make_onehot_map(&map, (const uint8_t*)ws->onehot2.p, M, D, tg.Kp));
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
-                                                   nullptr, (PairC*)ws->pairs2.p, fbits, st));
+                                                   nullptr, (PairC*)ws->pairs2.p, fbits, st, (const int*)ws->lrank.p));
             int lo = 0;
             const int cnt = share(ws->n_items2, &lo);
-            MDFS_LAUNCH("k3", st, launch_k3tc(map, onehot, tg, M, d0, nn, (const int2*)ws->items2.p + lo, cnt, tab,
-                                              fbits, cnt1, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, st));
+            MDFS_LAUNCH("k3", st, launch_k3tc(map, (const uint8_t*)ws->onehot2.p, tg, M, d0, nn,
+                                              (const int2*)ws->items2.p + lo, cnt, tab, fbits, (const int*)ws->cnt1s.p,
+                                              lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, st));
         }
         *check_err = true;
     } else if (k == 3) {

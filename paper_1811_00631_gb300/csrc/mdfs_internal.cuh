@@ -46,7 +46,7 @@ struct TcGeom {
 };
 
 // Pair record of the two-class (c = 2) k = 3 path, 8 bytes: class counts of
-// the voxel (1, 1) of the pair (n0 | n1 << 16; counts <= 32768) and its
+// the voxel (1, 1) of the pair times 4 (4 n0 | 4 n1 << 16; n < 16384) and its
 // regularised entropy SH as an int32 multiple of 2^-fbits (wrap-around).
 struct __align__(8) PairC {
     uint32_t cnt;
@@ -86,11 +86,12 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 // roles of every pair into keys (k = 2).  sh2/cnt2 != NULL: store the pair
 // tables (k = 3): sh2 [nd][M][M] i64, cnt2 [nd][M][M][(c-1)^2][2] i32 (i < m only).
 // pairs2 != NULL (c = 2 only): store PairC records [nd][M][M] instead, at
-// both [i][m] and [m][i], with the entropy in fbits fraction bits.
+// both [ri][rm] and [rm][ri], with the entropy in fbits fraction bits; ri =
+// rank[d][i] (rank [D][M], NULL = identity).
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd,
                       const long long* tab, const int* cnt1, const long long* sh1,
                       unsigned long long* keys, long long* sh2, int* cnt2, PairC* pairs2, int fbits,
-                      cudaStream_t st);
+                      cudaStream_t st, const int* rank = nullptr);
 
 // Triple pass over discretisations [d0, d0 + nd), using the pair tables of the
 // same chunk.  Folds the three IG roles of every triple into keys.  items[j] =
@@ -111,9 +112,19 @@ void build_k3tc_items(int M, std::vector<int2>& items);
 size_t k3tc_smem_bytes(int N0, int N1);
 int k3tc_fraction_bits(int N);
 cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D, int Kp);
+// perm [D][M]: new label -> original variable; cnt1s [D][M][2], the one-hot
+// rows of `map` and the pair records are in the new labels (see launch_k3tc_order).
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
-                        const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1,
-                        const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st);
+                        const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
+                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st);
+// Relabelling of the k = 3 tensor path, per discretisation: new labels in
+// ascending order of the bin-1 count (ties by index) for M <= 8192, else the
+// identity.  perm [D][M] new -> original, rank [D][M] original -> new,
+// cnt1s [D][M][2] = cnt1 rows in the new order (c = 2 layout).
+cudaError_t launch_k3tc_order(const int* cnt1, int M, int D, int* perm, int* rank, int* cnt1s, cudaStream_t st);
+// dst [D][M][Kp] row r of disc d = src row perm[d][r]; Kp a multiple of 16.
+cudaError_t launch_permute_rows(const uint8_t* src, uint8_t* dst, const int* perm, int M, int D, int Kp,
+                                cudaStream_t st);
 
 // k = 2 on the tensor cores for c = 2, 3: one-hot rows M (c-1) through TMA
 // (map over [D][M (c-1)][Kp]), symmetric tiles (it <= mt) from build_k2tc_items.

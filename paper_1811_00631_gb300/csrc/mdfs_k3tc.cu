@@ -11,6 +11,15 @@
 // the counts are exact integers.  Class-0 and class-1 samples occupy separate
 // K ranges and accumulate into two TMEM accumulators.
 //
+// Variables are relabelled per discretisation in ascending order of their
+// bin-1 count before the scan (k3tc_order_kernel).  The kernel enumerates the
+// triples a < b < e of the new labels, which covers every unordered triple
+// once; in that order the 32 rows a of a warp have similar marginal counts, so
+// the voxel counts they look up fall in a narrow window of the entropy tables
+// and the shared-memory loads see fewer bank conflicts.  The one-hot rows,
+// pair records and single counts are stored in the new order; keys are
+// written for the original variables with sorted original partner indices.
+//
 // Persistent, warp-specialised kernel (one CTA per SM, 640 threads):
 //   warp 0       TMA producer: A (a rows), B (e rows), OH[b] row per K block,
 //   warp 1       TMEM owner and MMA issuer (4 MMAs of K = 32 per K block),
@@ -33,6 +42,7 @@
 // drains its copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <climits>
 
 #include "mdfs_device.cuh"
 #include "mdfs_internal.cuh"
@@ -55,9 +65,12 @@ constexpr int kColsPerWarp = 32;
 constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
 static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
               "register split must add up to the launch allocation");
-constexpr size_t kTabOffset = 2 * kStages * kTileBytes + kStages * kBK;  // after A, B, OH[b] rows
-
-__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+// Entropy tables sit first in dynamic shared memory at fixed byte offsets, so a
+// lookup is one load with an immediate base: T0 [0, 4096), T1 [4096, 8192),
+// TB [8192, 16384) int32 entries.  The stages follow, 1024-byte aligned.
+constexpr int kT0Cap = 4096, kT1Cap = 4096, kTBCap = 8192;
+constexpr size_t kTabBytes = (size_t)(kT0Cap + kT1Cap + kTBCap) * sizeof(int);
+constexpr size_t kStageBytes = 2 * kStages * kTileBytes + kStages * kBK;  // A, B, OH[b] rows
 
 // Waits for completion regardless of an abort (draining in-flight work); bounded.
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
@@ -74,20 +87,33 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-__device__ __forceinline__ int tab32(const int* t, int n, int nmax) { return t[min((unsigned)n, (unsigned)nmax)]; }
+// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4), clamped to the table
+__device__ __forceinline__ int tab4(const int* t, int n4, int nmax4) {
+    return *reinterpret_cast<const int*>(reinterpret_cast<const char*>(t) + min((unsigned)n4, (unsigned)nmax4));
+}
+
+// exact integer value of an FP32 count, times 4
+__device__ __forceinline__ int count4(uint32_t f) { return __float2int_rn(__uint_as_float(f)) << 2; }
 
 struct ColCtx {
-    int n0, n1;    // pair (b, e): class counts of voxel (1, 1)
+    int n0, n1;    // pair (b, e): class counts of voxel (1, 1), times 4
     int sh;        // pair (b, e): entropy, int32 fixed point
-    int ne0, ne1;  // single e: class counts of bin 1
+    int ne0, ne1;  // single e: class counts of bin 1, times 4
+    int eo;        // original index of e
 };
+
+// partner index of a key: (d M + lo) M + hi with the two partners sorted
+__device__ __forceinline__ uint32_t partner_index(uint32_t dM, int M, uint32_t p, uint32_t q) {
+    return (dM + min(p, q)) * (uint32_t)M + max(p, q);
+}
 
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1)
     k3tc_kernel(const __grid_constant__ CUtensorMap map_oh, const uint8_t* __restrict__ oh, TcGeom tg, int M, int d0,
                 int nd, const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
-                const int* __restrict__ cnt1, const PairC* __restrict__ pairs, unsigned long long* __restrict__ keys,
+                const int* __restrict__ cnt1s, const int* __restrict__ perm, const PairC* __restrict__ pairs,
+                unsigned long long* __restrict__ keys,
                 int* __restrict__ err) {
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
@@ -97,20 +123,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ ColCtx s_col[kEpiThreads / 32][kColsPerWarp];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint8_t* base = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
+    int* sT0 = reinterpret_cast<int*>(dsmem_raw);
+    int* sT1 = sT0 + kT0Cap;
+    int* sTB = sT1 + kT1Cap;
+    uint8_t* stage0 = dsmem_raw + kTabBytes;
+    uint8_t* base = stage0 + ((1024 - (tc::smem_u32(stage0) & 1023)) & 1023);
     uint8_t* sA = base;
     uint8_t* sB = base + kStages * kTileBytes;
     uint8_t* sOHb = base + 2 * kStages * kTileBytes;
     const int N0 = tg.N0, N1 = tg.N1, N = N0 + N1, np1 = N + 1;
-    int* sT0 = reinterpret_cast<int*>(base + kTabOffset);
-    int* sT1 = sT0 + (N0 + 1);
-    int* sTB = sT1 + (N1 + 1);
     volatile int* abort = &s_abort;
 
     // the layout above must fit the dynamic shared memory this launch received
     uint32_t dyn_bytes;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
-    const bool fits = (size_t)(base - dsmem_raw) + kTabOffset + (size_t)(2 * N + 3) * sizeof(int) <= dyn_bytes;
+    const bool fits = N0 < kT0Cap && N1 < kT1Cap && N < kTBCap &&
+                      (size_t)(base - dsmem_raw) + kStageBytes <= dyn_bytes;
 
     if (tid == 0) {
         // an earlier launch failed (skip the work), or the layout has no room (reason 2)
@@ -136,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = tid; i <= N1; i += kThreads) sT1[i] = fx_narrow(tab[np1 + i], fbits);
         for (int i = tid; i <= N; i += kThreads) sTB[i] = fx_narrow(tab[2 * np1 + i], fbits);
     }
+    const int N0x4 = 4 * N0, N1x4 = 4 * N1, Nx4 = 4 * N;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -276,43 +305,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int dl = t / n_items, d = d0 + dl;
             const int b = item.x, a0 = (item.y >> 16) * kTile, e0 = b + 1 + (item.y & 0xFFFF) * kTile;
             const PairC* pd = pairs + (size_t)dl * M * M;  // symmetric: [i][m] == [m][i]
-            const int* c1 = cnt1 + (size_t)d * M * 2;
+            const int* c1 = cnt1s + (size_t)d * M * 2;
+            const int* pm = perm + (size_t)d * M;        // new label -> original variable
             const int ecol0 = e0 + kColsPerWarp * h;
             const int ncols = min(kColsPerWarp, M - ecol0);
             // column context of this warp's columns: pair (b, e) and single e
             __syncwarp();
             for (int cidx = lane; cidx < kColsPerWarp; cidx += 32) {
                 const int e = ecol0 + cidx;
-                ColCtx x{0, 0, 0, 0, 0};
+                ColCtx x{0, 0, 0, 0, 0, 0};
                 if (cidx < ncols) {
                     const PairC p = pd[(size_t)b * M + e];
                     x.n0 = (int)(p.cnt & 0xFFFFu);
                     x.n1 = (int)(p.cnt >> 16);
                     x.sh = p.sh;
-                    x.ne0 = c1[2 * e];
-                    x.ne1 = c1[2 * e + 1];
+                    x.ne0 = 4 * c1[2 * e];
+                    x.ne1 = 4 * c1[2 * e + 1];
+                    x.eo = pm[e];
                 }
                 cc[cidx] = x;
             }
             __syncwarp();
-            // row context: pair (a, b), single a, and per-row constants
+            // row context: pair (a, b), single a, and per-row constants (counts times 4)
             const int a = a0 + row;
             const bool arow = a < b;
             const bool warp_rows = (a0 + 32 * q) < b;  // some row of this warp is valid
-            int pab0 = 0, pab1 = 0, shab = 0, na0 = 0, na1 = 0;
+            int pab0 = 0, pab1 = 0, shab = 0, na0 = 0, na1 = 0, ao = 0;
             if (arow) {
                 const PairC p = pd[(size_t)b * M + a];
                 pab0 = (int)(p.cnt & 0xFFFFu);
                 pab1 = (int)(p.cnt >> 16);
                 shab = p.sh;
-                na0 = c1[2 * a];
-                na1 = c1[2 * a + 1];
+                na0 = 4 * c1[2 * a];
+                na1 = 4 * c1[2 * a + 1];
+                ao = pm[a];
             }
-            const int nb0 = c1[2 * b], nb1 = c1[2 * b + 1];
-            const int kab0 = N0 - na0 - nb0 + pab0, kab1 = N1 - na1 - nb1 + pab1;
+            const uint32_t bo = (uint32_t)pm[b];
+            const int nb0 = 4 * c1[2 * b], nb1 = 4 * c1[2 * b + 1];
+            const int kab0 = N0x4 - na0 - nb0 + pab0, kab1 = N1x4 - na1 - nb1 + pab1;
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
-            const uint32_t idx_a = (dM + (uint32_t)b) * (uint32_t)M;   // role a: partners (b, e)
-            const uint32_t idx_be = (dM + (uint32_t)a) * (uint32_t)M;  // roles b: (a, e) and e: (a, b)
             // pair (a, e) records of the first 8 columns, fetched before the accumulators are ready
             const PairC* prow = pd + (size_t)min(ecol0, M - 1) * M + (arow ? a : 0);  // prow[(e - ecol0) * M]
             PairC pnext[8];
@@ -321,7 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
             if (!tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort)) break;
             tc::tc_fence_after();
-            unsigned long long ka = 0ull, kbest = 0ull;
+            // running maxima of the roles a (over e) and b (over this thread's (a, e));
+            // the column loop visits e in ascending order, so ">" keeps the lowest e on ties
+            int best_a = INT_MIN, best_a_col = -1, best_b = INT_MIN, best_b_col = -1;
             if (warp_rows && ncols > 0) {
                 const uint32_t taddr =
                     tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kAccCols + (uint32_t)(kColsPerWarp * h);
@@ -341,22 +374,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int col = c0 + j;
-                        const int e = ecol0 + col;
-                        unsigned long long k_e = 0ull;
-                        if (arow && col < ncols) {
+                        const bool ok = arow && col < ncols;
+                        int ig_e = INT_MIN;
+                        if (ok) {
                             const ColCtx cx = cc[col];
                             const int pae0 = (int)(pcur[j].cnt & 0xFFFFu), pae1 = (int)(pcur[j].cnt >> 16);
                             int sh3, t0, t1, t2, t3, t4, t5, t6, t7;
                             {
-                                const int x = (int)__uint_as_float(r0[j]);
+                                const int x = count4(r0[j]);
                                 const int c011 = cx.n0 - x, c101 = pae0 - x, c110 = pab0 - x;
                                 const int c001 = cx.ne0 - pae0 - c011;
                                 const int c010 = nb0 - pab0 - c011;
                                 const int c100 = na0 - pab0 - c101;
                                 const int c000 = kab0 - cx.ne0 + pae0 + c011;
-                                sh3 = -(tab32(sT0, x, N0) + tab32(sT0, c011, N0) + tab32(sT0, c101, N0) +
-                                        tab32(sT0, c110, N0) + tab32(sT0, c001, N0) + tab32(sT0, c010, N0) +
-                                        tab32(sT0, c100, N0) + tab32(sT0, c000, N0));
+                                sh3 = -(tab4(sT0, x, N0x4) + tab4(sT0, c011, N0x4) + tab4(sT0, c101, N0x4) +
+                                        tab4(sT0, c110, N0x4) + tab4(sT0, c001, N0x4) + tab4(sT0, c010, N0x4) +
+                                        tab4(sT0, c100, N0x4) + tab4(sT0, c000, N0x4));
                                 t7 = x;
                                 t3 = c011;
                                 t5 = c101;
@@ -367,15 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 t0 = c000;
                             }
                             {
-                                const int x = (int)__uint_as_float(r1[j]);
+                                const int x = count4(r1[j]);
                                 const int c011 = cx.n1 - x, c101 = pae1 - x, c110 = pab1 - x;
                                 const int c001 = cx.ne1 - pae1 - c011;
                                 const int c010 = nb1 - pab1 - c011;
                                 const int c100 = na1 - pab1 - c101;
                                 const int c000 = kab1 - cx.ne1 + pae1 + c011;
-                                sh3 -= tab32(sT1, x, N1) + tab32(sT1, c011, N1) + tab32(sT1, c101, N1) +
-                                       tab32(sT1, c110, N1) + tab32(sT1, c001, N1) + tab32(sT1, c010, N1) +
-                                       tab32(sT1, c100, N1) + tab32(sT1, c000, N1);
+                                sh3 -= tab4(sT1, x, N1x4) + tab4(sT1, c011, N1x4) + tab4(sT1, c101, N1x4) +
+                                       tab4(sT1, c110, N1x4) + tab4(sT1, c001, N1x4) + tab4(sT1, c010, N1x4) +
+                                       tab4(sT1, c100, N1x4) + tab4(sT1, c000, N1x4);
                                 t7 += x;
                                 t3 += c011;
                                 t5 += c101;
@@ -385,26 +418,44 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 t4 += c100;
                                 t0 += c000;
                             }
-                            sh3 += tab32(sTB, t0, N) + tab32(sTB, t1, N) + tab32(sTB, t2, N) + tab32(sTB, t3, N) +
-                                   tab32(sTB, t4, N) + tab32(sTB, t5, N) + tab32(sTB, t6, N) + tab32(sTB, t7, N);
-                            // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around differences
-                            const float ig_a = (float)(cx.sh - sh3) * inv_scale;
-                            const float ig_b = (float)(pcur[j].sh - sh3) * inv_scale;
-                            const float ig_e = (float)(shab - sh3) * inv_scale;
-                            ka = umax64(ka, pack_key(ig_a, idx_a + (uint32_t)e));
-                            kbest = umax64(kbest, pack_key(ig_b, idx_be + (uint32_t)e));
-                            k_e = pack_key(ig_e, idx_be + (uint32_t)b);
+                            sh3 += tab4(sTB, t0, Nx4) + tab4(sTB, t1, Nx4) + tab4(sTB, t2, Nx4) + tab4(sTB, t3, Nx4) +
+                                   tab4(sTB, t4, Nx4) + tab4(sTB, t5, Nx4) + tab4(sTB, t6, Nx4) + tab4(sTB, t7, Nx4);
+                            // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around int32 differences
+                            const int ig_a = cx.sh - sh3;
+                            const int ig_b = pcur[j].sh - sh3;
+                            ig_e = shab - sh3;
+                            if (ig_a > best_a) {
+                                best_a = ig_a;
+                                best_a_col = col;
+                            }
+                            if (ig_b > best_b) {
+                                best_b = ig_b;
+                                best_b_col = col;
+                            }
                         }
-                        const unsigned long long m = warp_max_key(k_e);
-                        if (lane == 0 && m) atomicMax(keys + e, m);
+                        // role e: the column's maximum over the rows (lowest new label a on ties)
+                        const int emax = __reduce_max_sync(0xffffffffu, ig_e);
+                        if (emax != INT_MIN) {
+                            const unsigned src = __reduce_min_sync(0xffffffffu, ig_e == emax ? (unsigned)lane : 32u);
+                            const int am = __shfl_sync(0xffffffffu, ao, (int)src);
+                            if (lane == 0)
+                                atomicMax(keys + cc[col].eo,
+                                          pack_key((float)emax * inv_scale, partner_index(dM, M, (uint32_t)am, bo)));
+                        }
                     }
                 }
             }
             tc::tc_fence_before();
             tc::mbar_arrive(&bar_tempty[buf]);
-            if (ka) atomicMax(keys + a, ka);
-            const unsigned long long mb = warp_max_key(kbest);
-            if (lane == 0 && mb) atomicMax(keys + b, mb);
+            if (best_a_col >= 0)  // IG(a | b, e): partners (b, e)
+                atomicMax(keys + ao, pack_key((float)best_a * inv_scale,
+                                              partner_index(dM, M, bo, (uint32_t)cc[best_a_col].eo)));
+            const unsigned long long kb_key =
+                best_b_col >= 0 ? pack_key((float)best_b * inv_scale,
+                                           partner_index(dM, M, (uint32_t)ao, (uint32_t)cc[best_b_col].eo))
+                                : 0ull;
+            const unsigned long long mb = warp_max_key(kb_key);  // IG(b | a, e): partners (a, e)
+            if (lane == 0 && mb) atomicMax(keys + bo, mb);
         }
     }
 
@@ -413,6 +464,76 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 1) tc::tmem_dealloc(tmem, kTmemCols);
     if (tid == 0 && *abort) atomicOr(err, *abort);  // 1: bounded wait gave up, 2: shared layout too small
+}
+
+namespace {
+
+// One CTA per discretisation: new labels in ascending order of the bin-1 count
+// n0 + n1 (ties by original index), sorted as 32-bit keys (count << 16 | m) by
+// a bitonic network in shared memory.  M above kOrderMax keeps the identity.
+constexpr int kOrderMax = 8192;
+
+__global__ void __launch_bounds__(1024) k3tc_order_kernel(const int* __restrict__ cnt1, int M, int* __restrict__ perm,
+                                                          int* __restrict__ rank, int* __restrict__ cnt1s) {
+    extern __shared__ uint32_t skey[];
+    const int d = blockIdx.x, tid = threadIdx.x;
+    const int* c1 = cnt1 + (size_t)d * M * 2;
+    if (M <= kOrderMax) {
+        int P2 = 1;
+        while (P2 < M) P2 <<= 1;
+        for (int i = tid; i < P2; i += blockDim.x)
+            skey[i] = i < M ? ((uint32_t)(c1[2 * i] + c1[2 * i + 1]) << 16) | (uint32_t)i : 0xFFFFFFFFu;
+        __syncthreads();
+        for (int k = 2; k <= P2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < P2; i += blockDim.x) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint32_t x = skey[i], y = skey[ixj];
+                        if ((x > y) == ((i & k) == 0)) {
+                            skey[i] = y;
+                            skey[ixj] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    for (int r = tid; r < M; r += blockDim.x) {
+        const int m = M <= kOrderMax ? (int)(skey[r] & 0xFFFFu) : r;
+        perm[(size_t)d * M + r] = m;
+        rank[(size_t)d * M + m] = r;
+        cnt1s[((size_t)d * M + r) * 2] = c1[2 * m];
+        cnt1s[((size_t)d * M + r) * 2 + 1] = c1[2 * m + 1];
+    }
+}
+
+// dst row (d, r) = src row (d, perm[d][r]); rows of Kp bytes, Kp a multiple of 16
+__global__ void __launch_bounds__(128) permute_rows_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
+                                                           const int* __restrict__ perm, int M, int Kp) {
+    const int r = blockIdx.x, d = blockIdx.y;
+    const int m = perm[(size_t)d * M + r];
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + ((size_t)d * M + m) * Kp);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + ((size_t)d * M + r) * Kp);
+    for (int i = threadIdx.x; i < Kp / 16; i += blockDim.x) d4[i] = s4[i];
+}
+
+}  // namespace
+
+cudaError_t launch_k3tc_order(const int* cnt1, int M, int D, int* perm, int* rank, int* cnt1s, cudaStream_t st) {
+    if (M > 65535) return cudaErrorInvalidValue;
+    int P2 = 1;
+    while (P2 < M) P2 <<= 1;
+    const size_t smem = M <= kOrderMax ? (size_t)P2 * sizeof(uint32_t) : 0;
+    k3tc_order_kernel<<<D, 1024, smem, st>>>(cnt1, M, perm, rank, cnt1s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_rows(const uint8_t* src, uint8_t* dst, const int* perm, int M, int D, int Kp,
+                                cudaStream_t st) {
+    if (Kp % 16 != 0 || ((uintptr_t)src & 15) || ((uintptr_t)dst & 15)) return cudaErrorInvalidValue;
+    permute_rows_kernel<<<dim3(M, D), 128, 0, st>>>(src, dst, perm, M, Kp);
+    return cudaGetLastError();
 }
 
 void build_k3tc_items(int M, std::vector<int2>& items) {
@@ -425,9 +546,10 @@ void build_k3tc_items(int M, std::vector<int2>& items) {
     }
 }
 
-// stages + int32 tables T0[0..N0], T1[0..N1], TB[0..N0+N1] + alignment slack
+// fixed-capacity tables + stages + alignment slack; 0 if the tables exceed their capacity
 size_t k3tc_smem_bytes(int N0, int N1) {
-    return kTabOffset + (size_t)(2 * (N0 + N1) + 3) * sizeof(int) + 1024;
+    if (N0 >= kT0Cap || N1 >= kT1Cap || N0 + N1 >= kTBCap) return (size_t)-1;
+    return kTabBytes + 1024 + kStageBytes;
 }
 
 // Largest fraction bits s <= 20 with |IG| 2^s < 2^31 for N samples
@@ -482,8 +604,8 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 }
 
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
-                        const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1,
-                        const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st) {
+                        const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
+                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
     cudaError_t e = ensure_dynamic_smem((const void*)k3tc_kernel, smem);
@@ -498,8 +620,8 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if ((e = cudaFuncGetAttributes(&fa, k3tc_kernel)) != cudaSuccess) return e;
     if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
-    k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, pairs, keys,
-                                              err);
+    k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm, pairs,
+                                              keys, err);
     return cudaGetLastError();
 }
 

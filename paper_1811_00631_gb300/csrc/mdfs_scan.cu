@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(256) k2_kernel(const uint32_t* __restrict__ pl
                                                  int ntile, const long long* __restrict__ tab,
                                                  const int* __restrict__ cnt1, const long long* __restrict__ sh1,
                                                  unsigned long long* __restrict__ keys, long long* __restrict__ sh2,
-                                                 int* __restrict__ cnt2, PairC* __restrict__ pairs2, int fbits) {
+                                                 int* __restrict__ cnt2, PairC* __restrict__ pairs2, int fbits,
+                                                 const int* __restrict__ rank) {
     constexpr int P = C - 1, TI = 32, WC = 32, LD = WC + 1;
     __shared__ uint32_t si[P][TI][LD];
     __shared__ uint32_t sm[P][TI][LD];
@@ -304,9 +305,12 @@ __global__ void __launch_bounds__(256) k2_kernel(const uint32_t* __restrict__ pl
                 atomicMax(&kmax[TI + tx], pack_key(ig_m, (uint32_t)(d * M + i)));
             }
             if (pairs2) {
-                const PairC rec{(uint32_t)X0[0][0] | ((uint32_t)X1[0][0] << 16), fx_narrow(sh, fbits)};
-                pairs2[((size_t)dl * M + i) * M + m] = rec;
-                pairs2[((size_t)dl * M + m) * M + i] = rec;
+                // counts times 4 (byte offsets of the consuming table lookups)
+                const PairC rec{(uint32_t)(4 * X0[0][0]) | ((uint32_t)(4 * X1[0][0]) << 16), fx_narrow(sh, fbits)};
+                const int ri = rank ? __ldg(rank + (size_t)d * M + i) : i;
+                const int rm = rank ? __ldg(rank + (size_t)d * M + m) : m;
+                pairs2[((size_t)dl * M + ri) * M + rm] = rec;
+                pairs2[((size_t)dl * M + rm) * M + ri] = rec;
             }
             if (sh2) {
                 const size_t pidx = ((size_t)dl * M + i) * M + m;
@@ -585,15 +589,18 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd, const long long* tab,
                       const int* cnt1, const long long* sh1, unsigned long long* keys, long long* sh2, int* cnt2,
-                      PairC* pairs2, int fbits, cudaStream_t st) {
+                      PairC* pairs2, int fbits, cudaStream_t st, const int* rank) {
     if (pairs2 && c != 2) return cudaErrorInvalidValue;
     (void)D;
     const int ntile = (M + 31) / 32;
     dim3 grid(ntile * (ntile + 1) / 2, nd);
     switch (c) {
-        case 2: k2_kernel<2><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits); break;
-        case 3: k2_kernel<3><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits); break;
-        case 4: k2_kernel<4><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits); break;
+        case 2: k2_kernel<2><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits,
+                                                    rank); break;
+        case 3: k2_kernel<3><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits,
+                                                    rank); break;
+        case 4: k2_kernel<4><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits,
+                                                    rank); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
