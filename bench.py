@@ -43,10 +43,10 @@ def _units():
 
 
 def _use_small_case():
-    """A reduced case of the same kernels for profiler captures (M = 160, 4 discretisations)."""
+    """A reduced case of the same kernels for profiler captures (M = 500, 2 discretisations)."""
     global M_VAR, DISC, WORKLOAD
-    M_VAR, DISC = 160, 4
-    WORKLOAD = "mdfs_scan_parity_N2000_M160_k2+k3_D4_c2 (profiling case)"
+    M_VAR, DISC = 500, 2
+    WORKLOAD = "mdfs_scan_parity_N2000_M500_k2+k3_D2_c2 (profiling case)"
 
 
 def _config(extra=None):
@@ -401,7 +401,7 @@ def main():
                     help="shared-memory lookup peak, 10^12 4-byte lookups/s")
     ap.add_argument("--k3-traffic", type=float, default=None,
                     help="DRAM bytes per k=3 launch from an ncu capture of the current kernel")
-    ap.add_argument("--small", action="store_true", help="reduced profiling case (M=160, D=4)")
+    ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=2)")
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving-mix run (0: skip)")
     ap.add_argument("--batched", action="store_true", help="run the batched k=2 workload instead")
     ap.add_argument("--batch-folds", type=int, default=16)

@@ -88,6 +88,17 @@ struct Workspace {
 std::mutex g_mu;
 std::map<std::pair<int, cudaStream_t>, std::unique_ptr<Workspace>> g_ws;
 
+// Error flag of the tensor-core kernels: 1 a bounded wait gave up, 2 dynamic
+// shared memory smaller than the table layout, 4 voxel counts outside the
+// entropy tables (inconsistent pair records).  job >= 0 names a batch job.
+int kernel_flag_error(int flag, int job = -1) {
+    char where[32] = "";
+    if (job >= 0) snprintf(where, sizeof where, "job %d: ", job);
+    if (flag & 2) return fail(MDFS_ECUDA, "%stensor-core kernel: dynamic shared memory smaller than its table layout", where);
+    if (flag & 4) return fail(MDFS_ECUDA, "%stensor-core kernel: voxel counts outside the entropy tables", where);
+    return fail(MDFS_ETIMEOUT, "%sa device-side wait timed out in a tensor-core kernel", where);
+}
+
 Workspace* get_ws(cudaStream_t st, int* err) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -373,7 +384,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             ws->n_items2 = (int)items.size();
         }
         // relabel the variables of every discretisation by bin-1 count and
-        // store the one-hot rows in that order
+        // store the one-hot rows in that order (class-1 samples weighted 64)
         MDFS_ENSURE(ws, lperm, (size_t)D * M * sizeof(int));
         MDFS_ENSURE(ws, lrank, (size_t)D * M * sizeof(int));
         MDFS_ENSURE(ws, cnt1s, (size_t)D * M * 2 * sizeof(int));
@@ -381,7 +392,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         const int* lperm = (const int*)ws->lperm.p;
         MDFS_LAUNCH("k3_order", st, launch_k3tc_order(cnt1, M, D, (int*)ws->lperm.p, (int*)ws->lrank.p,
                                                       (int*)ws->cnt1s.p, st));
-        MDFS_LAUNCH("k3_permute", st, launch_permute_rows(onehot, (uint8_t*)ws->onehot2.p, lperm, M, D, tg.Kp, st));
+        MDFS_LAUNCH("k3_operand", st, launch_k3tc_operand(onehot, (uint8_t*)ws->onehot2.p, lperm, M, D, tg, st));
         CUtensorMap map;
         MDFS_CUDA_TRY(make_onehot_map(&map, (const uint8_t*)ws->onehot2.p, M, D, tg.Kp));
         for (int d0 = 0; d0 < D; d0 += nd) {
@@ -597,8 +608,7 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
         const int flag = ws->host_stats[8];
-        if (flag & 2) return fail(MDFS_ECUDA, "tensor-core kernel: dynamic shared memory smaller than its table layout");
-        if (flag != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in a tensor-core kernel");
+        if (flag) return kernel_flag_error(flag);
     } else if (oig.staged || otu.staged || odi.staged || st == nullptr) {
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     }
@@ -683,8 +693,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
             MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
             MDFS_CUDA_TRY(cudaStreamSynchronize(st));
             const int flag = ws->host_stats[8];
-            if (flag & 2) return fail(MDFS_ECUDA, "tensor-core kernel: dynamic shared memory smaller than its table layout");
-            if (flag != 0) return fail(MDFS_ETIMEOUT, "job %d: a device-side wait timed out in the triple kernel", j);
+            if (flag) return kernel_flag_error(flag, j);
         }
     }
     if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
@@ -727,8 +736,7 @@ int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretiz
         MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
         const int flag = ws->host_stats[8];
-        if (flag & 2) return fail(MDFS_ECUDA, "tensor-core kernel: dynamic shared memory smaller than its table layout");
-        if (flag != 0) return fail(MDFS_ETIMEOUT, "a device-side wait timed out in a tensor-core kernel");
+        if (flag) return kernel_flag_error(flag);
     }
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     return MDFS_OK;

@@ -122,8 +122,10 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
 // identity.  perm [D][M] new -> original, rank [D][M] original -> new,
 // cnt1s [D][M][2] = cnt1 rows in the new order (c = 2 layout).
 cudaError_t launch_k3tc_order(const int* cnt1, int M, int D, int* perm, int* rank, int* cnt1s, cudaStream_t st);
-// dst [D][M][Kp] row r of disc d = src row perm[d][r]; Kp a multiple of 16.
-cudaError_t launch_permute_rows(const uint8_t* src, uint8_t* dst, const int* perm, int M, int D, int Kp,
+// The k = 3 tensor operand: dst [D][M][Kp] row r of disc d = src row
+// perm[d][r] (one-hot rows of launch_discretize), class-1 samples (K range
+// [K0p, Kp)) recoded from E4M3 1.0 to 64.0.
+cudaError_t launch_k3tc_operand(const uint8_t* src, uint8_t* dst, const int* perm, int M, int D, TcGeom tg,
                                 cudaStream_t st);
 
 // k = 2 on the tensor cores for c = 2, 3: one-hot rows M (c-1) through TMA

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int shi = irow ? fx_narrow(s1[vi], fbits) : 0;
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
 
-            if (!tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort)) break;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort))) break;  // warp-uniform
             tc::tc_fence_after();
             unsigned long long ki = 0ull;
             const bool warp_rows = (item.x * VT + (32 * q) / P) < M;

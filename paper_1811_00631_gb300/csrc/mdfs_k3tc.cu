@@ -3,13 +3,13 @@
 // implementation"; IG roles of Eq. 1 with |S| = 2.
 //
 // Each variable's bin-1 indicator over the class-sorted samples is stored as
-// one-hot E4M3 bytes (1.0 or 0).  For a middle variable b, the count of the
-// all-ones voxel of every triple (a, b, e) is
-//     X[a][e] = sum_s OH[a][s] * OH[b][s] * OH[e][s],
+// one-hot E4M3 bytes: 1.0 for a class-0 sample, 64.0 for a class-1 sample, 0
+// outside bin 1.  For a middle variable b, the all-ones voxel of every triple
+// (a, b, e) is counted by
+//     X[a][e] = sum_s OH[a][s] * OH[b][s] * OH[e][s] = n0 + 4096 n1,
 // a GEMM with A = OH[a-tile] masked by OH[b] and B = OH[e-tile], both K-major.
-// Products of 0/1 are exact and the FP32 accumulator is exact below 2^24, so
-// the counts are exact integers.  Class-0 and class-1 samples occupy separate
-// K ranges and accumulate into two TMEM accumulators.
+// Products are 0, 1 or 4096, and with n0, n1 < 4096 every partial sum is an
+// integer below 2^24, so the FP32 accumulator holds both class counts exactly.
 //
 // Variables are relabelled per discretisation in ascending order of their
 // bin-1 count before the scan (k3tc_order_kernel).  The kernel enumerates the
@@ -20,18 +20,22 @@
 // pair records and single counts are stored in the new order; keys are
 // written for the original variables with sorted original partner indices.
 //
+// Work item: (b, a tile of 128 rows, e group of up to 256 columns); one MMA
+// of N = 256 (or 128 for a narrow last group) per 32 samples reuses the
+// masked A tile across both halves of the group.
+//
 // Persistent, warp-specialised kernel (one CTA per SM, 640 threads):
 //   warp 0       TMA producer: A (a rows), B (e rows), OH[b] row per K block,
 //   warp 1       TMEM owner and MMA issuer (4 MMAs of K = 32 per K block),
 //   warps 2-3    AND the A tile with OH[b] in shared memory (128B swizzle),
-//   warps 4-19   epilogue: tcgen05.ld of both class accumulators, the 8-voxel
-//                tables by inclusion-exclusion, SH3 from fixed-point tables
-//                in shared memory, three IG roles, packed max keys.
+//   warps 4-19   epilogue: tcgen05.ld of the accumulator, the 8-voxel tables
+//                by inclusion-exclusion, SH3 from fixed-point tables in shared
+//                memory, three IG roles, packed max keys.
 // Registers: launched at kRegsLaunch per thread; the first warpgroup gives
 // back to kRegsProducer, the four epilogue warpgroups take kRegsEpilogue
 // (128 kRegsProducer + 512 kRegsEpilogue == 640 kRegsLaunch).
-// Four shared-memory stages and two TMEM accumulator buffers (2 x 256
-// columns) let the epilogue of one tile overlap the MMAs of the next.
+// Three shared-memory stages and two TMEM accumulator buffers (2 x 256
+// columns) let the epilogue of one item overlap the MMAs of the next.
 //
 // Entropy arithmetic: the FP64-built int64 tables (multiples of 2^-32) are
 // rounded to int32 multiples of 2^-s and summed with wrap-around; the IG
@@ -52,17 +56,20 @@ namespace mdfs {
 
 namespace {
 
-constexpr int kTile = 128;                    // a rows, e columns
-constexpr int kBK = 128;                      // K bytes (samples) per stage
-constexpr int kStages = 4;
-constexpr uint32_t kTileBytes = kTile * kBK;  // 16 KB
-constexpr uint32_t kAccCols = 2 * kTile;      // class 0 and class 1 accumulators
-constexpr uint32_t kTmemCols = 2 * kAccCols;  // double buffer
+constexpr int kTile = 128;                     // a rows
+constexpr int kTileE = 256;                    // e columns of a wide group
+constexpr int kBK = 128;                       // K bytes (samples) per stage
+constexpr int kStages = 3;
+constexpr uint32_t kTileBytes = kTile * kBK;   // 16 KB: A, or one 128-row half of B
+constexpr uint32_t kBBytes = 2 * kTileBytes;   // B stage: up to 256 rows
+constexpr uint32_t kAccCols = kTileE;          // one FP32 accumulator column per e
+constexpr uint32_t kTmemCols = 2 * kAccCols;   // double buffer
 constexpr int kThreads = 640;
 constexpr int kMaskWarp0 = 2, kMaskThreads = 64;
 constexpr int kEpiWarp0 = 4, kEpiThreads = 512;
-constexpr int kColsPerWarp = 32;
+constexpr int kChunk = 32;                     // e columns per epilogue pass of a warp
 constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
+constexpr uint8_t kClass1Byte = 0x68;          // E4M3 64.0
 static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
               "register split must add up to the launch allocation");
 // Entropy tables sit first in dynamic shared memory at fixed byte offsets, so a
@@ -70,7 +77,7 @@ static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kR
 // TB [8192, 16384) int32 entries.  The stages follow, 1024-byte aligned.
 constexpr int kT0Cap = 4096, kT1Cap = 4096, kTBCap = 8192;
 constexpr size_t kTabBytes = (size_t)(kT0Cap + kT1Cap + kTBCap) * sizeof(int);
-constexpr size_t kStageBytes = 2 * kStages * kTileBytes + kStages * kBK;  // A, B, OH[b] rows
+constexpr size_t kStageBytes = kStages * (kTileBytes + kBBytes + kBK);  // A, B, OH[b] rows
 
 // Waits for completion regardless of an abort (draining in-flight work); bounded.
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
@@ -87,20 +94,42 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4), clamped to the table
-__device__ __forceinline__ int tab4(const int* t, int n4, int nmax4) {
-    return *reinterpret_cast<const int*>(reinterpret_cast<const char*>(t) + min((unsigned)n4, (unsigned)nmax4));
+// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4),
+// clamped to the table's region of cap4 bytes (consistent counts never reach it)
+__device__ __forceinline__ int tab4(const int* t, int n4, unsigned cap4) {
+    return *reinterpret_cast<const int*>(reinterpret_cast<const char*>(t) + min((unsigned)n4, cap4));
+}
+constexpr unsigned kCap01 = 4 * (kT0Cap - 1), kCapB = 4 * (kTBCap - 1);  // T0/T1 and TB regions
+
+// Per-column constants of an item, counts times 4 (n_x: class count of bin 1
+// of x, n_xy: class count of the voxel (1, 1) of the pair (x, y)).
+struct ColCtx {
+    int n0, n1;    // n_be per class
+    int u0, u1;    // n_e - n_be per class
+    int sh;        // SH(b, e), int32 fixed point
+    int eo;        // original index of e
+    int thr;       // role-e pre-filter: IG(e | a, b) below thr cannot raise e's key
+};
+
+// Lower bound, in int32 fixed point with fbits fraction bits, of the IG values
+// that can still raise a key whose current value is `key` (0: no value yet).
+// Converting an int to float moves it by at most 128 for |v| < 2^31, so any v
+// whose float value reaches the key's IG is >= the bound.
+__device__ __forceinline__ int key_threshold(unsigned long long key, int fbits) {
+    if (key == 0ull) return INT_MIN;
+    const float t = order_bits_float((uint32_t)(key >> 32)) * __int_as_float((127 + fbits) << 23);
+    if (!(t < 2.0e9f)) return INT_MAX;
+    if (t < -2.0e9f) return INT_MIN;
+    return __float2int_rd(t) - 256;
 }
 
-// exact integer value of an FP32 count, times 4
-__device__ __forceinline__ int count4(uint32_t f) { return __float2int_rn(__uint_as_float(f)) << 2; }
-
-struct ColCtx {
-    int n0, n1;    // pair (b, e): class counts of voxel (1, 1), times 4
-    int sh;        // pair (b, e): entropy, int32 fixed point
-    int ne0, ne1;  // single e: class counts of bin 1, times 4
-    int eo;        // original index of e
-};
+// First a row of a-tile ta of middle variable b.  The a range [0, b) is tiled
+// from 0 upward for even b and from b downward for odd b (a0 may then be
+// negative: TMA fills those rows with zeros and the epilogue skips them).
+// TMEM lane quarter q, the rows 32 q .. 32 q + 31 of the accumulator, is read
+// by the warps of one SM sub-partition; alternating the alignment spreads the
+// partial tiles' valid rows evenly over the four quarters.
+__device__ __forceinline__ int tile_a0(int b, int ta) { return (b & 1) ? b - kTile * (ta + 1) : kTile * ta; }
 
 // partner index of a key: (d M + lo) M + hi with the two partners sorted
 __device__ __forceinline__ uint32_t partner_index(uint32_t dM, int M, uint32_t p, uint32_t q) {
@@ -120,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    __shared__ ColCtx s_col[kEpiThreads / 32][kColsPerWarp];
+    __shared__ ColCtx s_col[kEpiThreads / 32][kChunk];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int* sT0 = reinterpret_cast<int*>(dsmem_raw);
@@ -130,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* base = stage0 + ((1024 - (tc::smem_u32(stage0) & 1023)) & 1023);
     uint8_t* sA = base;
     uint8_t* sB = base + kStages * kTileBytes;
-    uint8_t* sOHb = base + 2 * kStages * kTileBytes;
+    uint8_t* sOHb = sB + kStages * kBBytes;
     const int N0 = tg.N0, N1 = tg.N1, N = N0 + N1, np1 = N + 1;
     volatile int* abort = &s_abort;
 
@@ -159,12 +188,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tmem_alloc(&s_tmem, kTmemCols);
         tc::tmem_relinquish();
     }
-    if (fits) {
-        for (int i = tid; i <= N0; i += kThreads) sT0[i] = fx_narrow(tab[i], fbits);
-        for (int i = tid; i <= N1; i += kThreads) sT1[i] = fx_narrow(tab[np1 + i], fbits);
-        for (int i = tid; i <= N; i += kThreads) sTB[i] = fx_narrow(tab[2 * np1 + i], fbits);
+    if (fits) {  // whole regions: entries past N_c are zero
+        for (int i = tid; i < kT0Cap; i += kThreads) sT0[i] = i <= N0 ? fx_narrow(tab[i], fbits) : 0;
+        for (int i = tid; i < kT1Cap; i += kThreads) sT1[i] = i <= N1 ? fx_narrow(tab[np1 + i], fbits) : 0;
+        for (int i = tid; i < kTBCap; i += kThreads) sTB[i] = i <= N ? fx_narrow(tab[2 * np1 + i], fbits) : 0;
     }
-    const int N0x4 = 4 * N0, N1x4 = 4 * N1, Nx4 = 4 * N;
+    const int N0x4 = 4 * N0, N1x4 = 4 * N1;  // class sizes, times 4
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -178,11 +207,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0 && !*abort) {
             uint32_t g = 0;  // running K-block counter across this CTA's tiles
             int pend_mask = 0;
-            uint32_t pend_use[kStages] = {0, 0, 0, 0};
+            uint32_t pend_use[kStages] = {};
             for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
                 const int2 item = items[t % n_items];
                 const int d = d0 + t / n_items;
-                const int b = item.x, a0 = (item.y >> 16) * kTile, e0 = b + 1 + (item.y & 0xFFFF) * kTile;
+                const int b = item.x, a0 = tile_a0(b, item.y >> 16), e0 = b + 1 + (item.y & 0xFFFF) * kTileE;
+                const bool wide = M - e0 > kTile;  // second 128-row half of B needed
                 const uint8_t* ohb = oh + ((size_t)d * M + b) * tg.Kp;
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
@@ -192,9 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(&bar_full[s], 2 * kTileBytes + kBK);
+                    tc::mbar_arrive_expect_tx(&bar_full[s], (wide ? 3 : 2) * kTileBytes + kBK);
                     tc::tma_load_3d(sA + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, a0, d);
-                    tc::tma_load_3d(sB + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, e0, d);
+                    tc::tma_load_3d(sB + s * kBBytes, &map_oh, &bar_full[s], kb * kBK, e0, d);
+                    if (wide) tc::tma_load_3d(sB + s * kBBytes + kTileBytes, &map_oh, &bar_full[s], kb * kBK, e0 + kTile, d);
                     tc::bulk_load(sOHb + s * kBK, ohb + (size_t)kb * kBK, kBK, &bar_full[s]);
                     pend_mask |= 1 << s;
                     pend_use[s] = use;
@@ -209,16 +240,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       } else if (warp == 1) {
         // ------------------------------ MMA issuer --------------------------------
         if (lane == 0 && !*abort) {
-            const uint32_t idesc = tc::idesc_e4m3_f32(kTile, kTile);
+            const uint32_t idesc_n128 = tc::idesc_e4m3_f32(kTile, kTile);
+            const uint32_t idesc_n256 = tc::idesc_e4m3_f32(kTile, kTileE);
             uint32_t g = 0;
             int i = 0;
             bool issued = false;
             for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
                 const int buf = i & 1;
                 const uint32_t tuse = (uint32_t)(i >> 1);
+                const int2 item = items[t % n_items];
+                const int e0 = item.x + 1 + (item.y & 0xFFFF) * kTileE;
+                const uint32_t idesc = M - e0 > kTile ? idesc_n256 : idesc_n128;
                 if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort)) break;
                 tc::tc_fence_after();
-                const uint32_t dbase = tmem + (uint32_t)buf * kAccCols;
+                const uint32_t d_tmem = tmem + (uint32_t)buf * kAccCols;
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int s = (int)(g % kStages);
@@ -228,12 +263,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t d_tmem = dbase + (kb >= tg.nkb0 ? (uint32_t)kTile : 0u);
                     const uint32_t a_addr = tc::smem_u32(sA + s * kTileBytes);
-                    const uint32_t b_addr = tc::smem_u32(sB + s * kTileBytes);
+                    const uint32_t b_addr = tc::smem_u32(sB + s * kBBytes);
 #pragma unroll
                     for (int kk = 0; kk < kBK / 32; ++kk) {
-                        const uint32_t acc = (kb != 0 && kb != tg.nkb0) || kk > 0;
+                        const uint32_t acc = kb > 0 || kk > 0;
                         tc::mma_f8(d_tmem, tc::sw128_kmajor_desc(a_addr + 32 * kk),
                                    tc::sw128_kmajor_desc(b_addr + 32 * kk), idesc, acc);
                     }
@@ -261,8 +295,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t g = 0;
         for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
             const int2 item = items[t % n_items];
-            const int a0 = (item.y >> 16) * kTile;
-            const int rows = min(kTile, item.x - a0);  // valid rows: a < b
+            const int a0 = tile_a0(item.x, item.y >> 16);
+            const int rows = min(kTile, item.x - a0);  // rows with a < b (rows with a < 0 hold zeros)
             bool ok = true;
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int s = (int)(g % kStages);
@@ -292,8 +326,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpilogue));
         // ------------------------------ epilogue ----------------------------------
+        // Warp (q, h): TMEM lane quarter q = warp % 4 (rows 32 q ..), column
+        // chunks h and h + 4 of 32 columns each.
         const int ew = warp - kEpiWarp0;      // 0..15
-        const int q = warp & 3, h = ew >> 2;  // TMEM lane quarter (warp % 4), column quarter
+        const int q = warp & 3, h = ew >> 2;
         const int row = 32 * q + lane;
         const float inv_scale = __int_as_float((127 - fbits) << 23);  // 2^-fbits
         ColCtx* cc = s_col[ew];
@@ -303,33 +339,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t tuse = (uint32_t)(i >> 1);
             const int2 item = items[t % n_items];
             const int dl = t / n_items, d = d0 + dl;
-            const int b = item.x, a0 = (item.y >> 16) * kTile, e0 = b + 1 + (item.y & 0xFFFF) * kTile;
+            const int b = item.x, a0 = tile_a0(b, item.y >> 16), e0 = b + 1 + (item.y & 0xFFFF) * kTileE;
             const PairC* pd = pairs + (size_t)dl * M * M;  // symmetric: [i][m] == [m][i]
             const int* c1 = cnt1s + (size_t)d * M * 2;
             const int* pm = perm + (size_t)d * M;        // new label -> original variable
-            const int ecol0 = e0 + kColsPerWarp * h;
-            const int ncols = min(kColsPerWarp, M - ecol0);
-            // column context of this warp's columns: pair (b, e) and single e
-            __syncwarp();
-            for (int cidx = lane; cidx < kColsPerWarp; cidx += 32) {
-                const int e = ecol0 + cidx;
-                ColCtx x{0, 0, 0, 0, 0, 0};
-                if (cidx < ncols) {
-                    const PairC p = pd[(size_t)b * M + e];
-                    x.n0 = (int)(p.cnt & 0xFFFFu);
-                    x.n1 = (int)(p.cnt >> 16);
-                    x.sh = p.sh;
-                    x.ne0 = 4 * c1[2 * e];
-                    x.ne1 = 4 * c1[2 * e + 1];
-                    x.eo = pm[e];
-                }
-                cc[cidx] = x;
-            }
-            __syncwarp();
-            // row context: pair (a, b), single a, and per-row constants (counts times 4)
+            // row constants (counts times 4): n_ab, n_b - n_ab, n_a - n_ab, N - n_a - n_b + n_ab
             const int a = a0 + row;
-            const bool arow = a < b;
-            const bool warp_rows = (a0 + 32 * q) < b;  // some row of this warp is valid
+            const bool arow = a >= 0 && a < b;
+            const bool warp_rows = (a0 + 32 * q) < b && (a0 + 32 * q + 31) >= 0;  // some row of this warp is valid
             int pab0 = 0, pab1 = 0, shab = 0, na0 = 0, na1 = 0, ao = 0;
             if (arow) {
                 const PairC p = pd[(size_t)b * M + a];
@@ -342,27 +359,61 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const uint32_t bo = (uint32_t)pm[b];
             const int nb0 = 4 * c1[2 * b], nb1 = 4 * c1[2 * b + 1];
+            const int r2_0 = nb0 - pab0, r2_1 = nb1 - pab1;
+            const int r3_0 = na0 - pab0, r3_1 = na1 - pab1;
             const int kab0 = N0x4 - na0 - nb0 + pab0, kab1 = N1x4 - na1 - nb1 + pab1;
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
-            // pair (a, e) records of the first 8 columns, fetched before the accumulators are ready
-            const PairC* prow = pd + (size_t)min(ecol0, M - 1) * M + (arow ? a : 0);  // prow[(e - ecol0) * M]
-            PairC pnext[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) pnext[j] = (arow && j < ncols) ? prow[(size_t)j * M] : PairC{0u, 0};
-
-            if (!tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort)) break;
-            tc::tc_fence_after();
             // running maxima of the roles a (over e) and b (over this thread's (a, e));
-            // the column loop visits e in ascending order, so ">" keeps the lowest e on ties
-            int best_a = INT_MIN, best_a_col = -1, best_b = INT_MIN, best_b_col = -1;
-            if (warp_rows && ncols > 0) {
+            // columns are visited in ascending e, so ">" keeps the first maximum
+            int best_a = INT_MIN, best_b = INT_MIN;
+            int best_a_eo = 0, best_b_eo = 0;
+            bool waited = false;
+#pragma unroll 1
+            for (int ch = h;; ch += 4) {
+                const int ecol0 = e0 + kChunk * ch;
+                const int ncols = ch < kTileE / kChunk ? min(kChunk, M - ecol0) : 0;
+                const PairC* prow = pd + (size_t)min(ecol0, M - 1) * M + (arow ? a : 0);  // prow[(e - ecol0) * M]
+                PairC pnext[8];
+                if (ncols > 0) {
+                    // column constants of this chunk
+                    __syncwarp();
+                    const int e = ecol0 + lane;
+                    ColCtx x{0, 0, 0, 0, 0, 0, INT_MAX};
+                    if (lane < ncols) {
+                        const PairC p = pd[(size_t)b * M + e];
+                        x.n0 = (int)(p.cnt & 0xFFFFu);
+                        x.n1 = (int)(p.cnt >> 16);
+                        x.u0 = 4 * c1[2 * e] - x.n0;
+                        x.u1 = 4 * c1[2 * e + 1] - x.n1;
+                        x.sh = p.sh;
+                        x.eo = pm[e];
+                        // keys only grow during the scan: a stale value is a valid lower bound
+                        x.thr = key_threshold(__ldcg(keys + x.eo), fbits);
+                    }
+                    cc[lane] = x;
+                    __syncwarp();
+                    // pair (a, e) records of the first 8 columns, fetched before the accumulator is read
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        pnext[j] = (arow && j < ncols) ? prow[(size_t)j * M] : PairC{0u, 0};
+                }
+                // every epilogue warp waits for the accumulator of every item, with
+                // or without columns, before it releases the buffer
+                if (!waited) {
+                    // warp-uniform outcome: the warp-wide reductions below need every lane
+                    if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort))) break;
+                    tc::tc_fence_after();
+                    waited = true;
+                }
+                if (ncols <= 0) break;
+                if (!warp_rows) continue;
+                int ca = -1, cb = -1;  // columns of this chunk that raised best_a, best_b
                 const uint32_t taddr =
-                    tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kAccCols + (uint32_t)(kColsPerWarp * h);
+                    tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kAccCols + (uint32_t)(kChunk * ch);
 #pragma unroll 1
                 for (int c0 = 0; c0 < ncols; c0 += 8) {
-                    uint32_t r0[8], r1[8];
-                    tc::tmem_ld8(taddr + (uint32_t)c0, r0);
-                    tc::tmem_ld8(taddr + (uint32_t)(kTile + c0), r1);
+                    uint32_t r[8];
+                    tc::tmem_ld8(taddr + (uint32_t)c0, r);
                     PairC pcur[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -374,86 +425,71 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int col = c0 + j;
-                        const bool ok = arow && col < ncols;
                         int ig_e = INT_MIN;
-                        if (ok) {
+                        bool cand = false;
+                        if (arow && col < ncols) {
                             const ColCtx cx = cc[col];
                             const int pae0 = (int)(pcur[j].cnt & 0xFFFFu), pae1 = (int)(pcur[j].cnt >> 16);
-                            int sh3, t0, t1, t2, t3, t4, t5, t6, t7;
-                            {
-                                const int x = count4(r0[j]);
-                                const int c011 = cx.n0 - x, c101 = pae0 - x, c110 = pab0 - x;
-                                const int c001 = cx.ne0 - pae0 - c011;
-                                const int c010 = nb0 - pab0 - c011;
-                                const int c100 = na0 - pab0 - c101;
-                                const int c000 = kab0 - cx.ne0 + pae0 + c011;
-                                sh3 = -(tab4(sT0, x, N0x4) + tab4(sT0, c011, N0x4) + tab4(sT0, c101, N0x4) +
-                                        tab4(sT0, c110, N0x4) + tab4(sT0, c001, N0x4) + tab4(sT0, c010, N0x4) +
-                                        tab4(sT0, c100, N0x4) + tab4(sT0, c000, N0x4));
-                                t7 = x;
-                                t3 = c011;
-                                t5 = c101;
-                                t6 = c110;
-                                t1 = c001;
-                                t2 = c010;
-                                t4 = c100;
-                                t0 = c000;
-                            }
-                            {
-                                const int x = count4(r1[j]);
-                                const int c011 = cx.n1 - x, c101 = pae1 - x, c110 = pab1 - x;
-                                const int c001 = cx.ne1 - pae1 - c011;
-                                const int c010 = nb1 - pab1 - c011;
-                                const int c100 = na1 - pab1 - c101;
-                                const int c000 = kab1 - cx.ne1 + pae1 + c011;
-                                sh3 -= tab4(sT1, x, N1x4) + tab4(sT1, c011, N1x4) + tab4(sT1, c101, N1x4) +
-                                       tab4(sT1, c110, N1x4) + tab4(sT1, c001, N1x4) + tab4(sT1, c010, N1x4) +
-                                       tab4(sT1, c100, N1x4) + tab4(sT1, c000, N1x4);
-                                t7 += x;
-                                t3 += c011;
-                                t5 += c101;
-                                t6 += c110;
-                                t1 += c001;
-                                t2 += c010;
-                                t4 += c100;
-                                t0 += c000;
-                            }
-                            sh3 += tab4(sTB, t0, Nx4) + tab4(sTB, t1, Nx4) + tab4(sTB, t2, Nx4) + tab4(sTB, t3, Nx4) +
-                                   tab4(sTB, t4, Nx4) + tab4(sTB, t5, Nx4) + tab4(sTB, t6, Nx4) + tab4(sTB, t7, Nx4);
+                            // X = n0 + 4096 n1, exact in FP32
+                            const int xv = __float2int_rn(__uint_as_float(r[j]));
+                            // voxel counts (times 4) by inclusion-exclusion, voxel (v_a v_b v_e)
+                            const int x0 = (xv << 2) & 0x3FFC;
+                            const int p011 = cx.n0 - x0, p101 = pae0 - x0, p110 = pab0 - x0;
+                            const int p001 = cx.u0 - pae0 + x0, p010 = r2_0 - cx.n0 + x0, p100 = r3_0 - pae0 + x0;
+                            const int p000 = kab0 - cx.u0 + pae0 - x0;
+                            const int x1 = (xv >> 10) & ~3;
+                            const int q011 = cx.n1 - x1, q101 = pae1 - x1, q110 = pab1 - x1;
+                            const int q001 = cx.u1 - pae1 + x1, q010 = r2_1 - cx.n1 + x1, q100 = r3_1 - pae1 + x1;
+                            const int q000 = kab1 - cx.u1 + pae1 - x1;
+                            const int sh3 =
+                                tab4(sTB, x0 + x1, kCapB) + tab4(sTB, p011 + q011, kCapB) + tab4(sTB, p101 + q101, kCapB) +
+                                tab4(sTB, p110 + q110, kCapB) + tab4(sTB, p001 + q001, kCapB) +
+                                tab4(sTB, p010 + q010, kCapB) + tab4(sTB, p100 + q100, kCapB) +
+                                tab4(sTB, p000 + q000, kCapB) -
+                                (tab4(sT0, x0, kCap01) + tab4(sT0, p011, kCap01) + tab4(sT0, p101, kCap01) +
+                                 tab4(sT0, p110, kCap01) + tab4(sT0, p001, kCap01) + tab4(sT0, p010, kCap01) +
+                                 tab4(sT0, p100, kCap01) + tab4(sT0, p000, kCap01)) -
+                                (tab4(sT1, x1, kCap01) + tab4(sT1, q011, kCap01) + tab4(sT1, q101, kCap01) +
+                                 tab4(sT1, q110, kCap01) + tab4(sT1, q001, kCap01) + tab4(sT1, q010, kCap01) +
+                                 tab4(sT1, q100, kCap01) + tab4(sT1, q000, kCap01));
                             // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around int32 differences
                             const int ig_a = cx.sh - sh3;
                             const int ig_b = pcur[j].sh - sh3;
                             ig_e = shab - sh3;
+                            cand = ig_e >= cx.thr;
                             if (ig_a > best_a) {
                                 best_a = ig_a;
-                                best_a_col = col;
+                                ca = col;
                             }
                             if (ig_b > best_b) {
                                 best_b = ig_b;
-                                best_b_col = col;
+                                cb = col;
                             }
                         }
-                        // role e: the column's maximum over the rows (lowest new label a on ties)
-                        const int emax = __reduce_max_sync(0xffffffffu, ig_e);
-                        if (emax != INT_MIN) {
-                            const unsigned src = __reduce_min_sync(0xffffffffu, ig_e == emax ? (unsigned)lane : 32u);
-                            const int am = __shfl_sync(0xffffffffu, ao, (int)src);
-                            if (lane == 0)
+                        // role e: the column's maximum over the warp's rows, written by the
+                        // lowest lane (lowest new label a) holding it; skipped when no lane
+                        // reaches the column's pre-filter bound
+                        if (__any_sync(0xffffffffu, cand)) {
+                            const int emax = __reduce_max_sync(0xffffffffu, ig_e);
+                            const unsigned hit = __ballot_sync(0xffffffffu, ig_e == emax);
+                            if (lane == __ffs(hit) - 1)
                                 atomicMax(keys + cc[col].eo,
-                                          pack_key((float)emax * inv_scale, partner_index(dM, M, (uint32_t)am, bo)));
+                                          pack_key((float)emax * inv_scale, partner_index(dM, M, (uint32_t)ao, bo)));
                         }
                     }
                 }
+                if (ca >= 0) best_a_eo = cc[ca].eo;
+                if (cb >= 0) best_b_eo = cc[cb].eo;
             }
+            if (!waited) break;  // the accumulator wait gave up
             tc::tc_fence_before();
             tc::mbar_arrive(&bar_tempty[buf]);
-            if (best_a_col >= 0)  // IG(a | b, e): partners (b, e)
-                atomicMax(keys + ao, pack_key((float)best_a * inv_scale,
-                                              partner_index(dM, M, bo, (uint32_t)cc[best_a_col].eo)));
+            if (best_a != INT_MIN)  // IG(a | b, e): partners (b, e)
+                atomicMax(keys + ao, pack_key((float)best_a * inv_scale, partner_index(dM, M, bo, (uint32_t)best_a_eo)));
             const unsigned long long kb_key =
-                best_b_col >= 0 ? pack_key((float)best_b * inv_scale,
-                                           partner_index(dM, M, (uint32_t)ao, (uint32_t)cc[best_b_col].eo))
-                                : 0ull;
+                best_b != INT_MIN
+                    ? pack_key((float)best_b * inv_scale, partner_index(dM, M, (uint32_t)ao, (uint32_t)best_b_eo))
+                    : 0ull;
             const unsigned long long mb = warp_max_key(kb_key);  // IG(b | a, e): partners (a, e)
             if (lane == 0 && mb) atomicMax(keys + bo, mb);
         }
@@ -508,14 +544,32 @@ __global__ void __launch_bounds__(1024) k3tc_order_kernel(const int* __restrict_
     }
 }
 
-// dst row (d, r) = src row (d, perm[d][r]); rows of Kp bytes, Kp a multiple of 16
+// nonzero bytes of w -> kClass1Byte, zero bytes stay zero
+__device__ __forceinline__ uint32_t recode_class1(uint32_t w) {
+    uint32_t nz = w | (w >> 4);
+    nz |= nz >> 2;
+    nz |= nz >> 1;
+    return (nz & 0x01010101u) * kClass1Byte;
+}
+
+// dst row (d, r) = src row (d, perm[d][r]); rows of Kp bytes, Kp a multiple of
+// 16.  Bytes from K0p on (class-1 samples, K0p a multiple of 16) become 64.0.
 __global__ void __launch_bounds__(128) permute_rows_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
-                                                           const int* __restrict__ perm, int M, int Kp) {
+                                                           const int* __restrict__ perm, int M, int Kp, int K0p) {
     const int r = blockIdx.x, d = blockIdx.y;
     const int m = perm[(size_t)d * M + r];
     const uint4* s4 = reinterpret_cast<const uint4*>(src + ((size_t)d * M + m) * Kp);
     uint4* d4 = reinterpret_cast<uint4*>(dst + ((size_t)d * M + r) * Kp);
-    for (int i = threadIdx.x; i < Kp / 16; i += blockDim.x) d4[i] = s4[i];
+    for (int i = threadIdx.x; i < Kp / 16; i += blockDim.x) {
+        uint4 v = s4[i];
+        if (i >= K0p / 16) {
+            v.x = recode_class1(v.x);
+            v.y = recode_class1(v.y);
+            v.z = recode_class1(v.z);
+            v.w = recode_class1(v.w);
+        }
+        d4[i] = v;
+    }
 }
 
 }  // namespace
@@ -529,10 +583,11 @@ cudaError_t launch_k3tc_order(const int* cnt1, int M, int D, int* perm, int* ran
     return cudaGetLastError();
 }
 
-cudaError_t launch_permute_rows(const uint8_t* src, uint8_t* dst, const int* perm, int M, int D, int Kp,
+cudaError_t launch_k3tc_operand(const uint8_t* src, uint8_t* dst, const int* perm, int M, int D, TcGeom tg,
                                 cudaStream_t st) {
-    if (Kp % 16 != 0 || ((uintptr_t)src & 15) || ((uintptr_t)dst & 15)) return cudaErrorInvalidValue;
-    permute_rows_kernel<<<dim3(M, D), 128, 0, st>>>(src, dst, perm, M, Kp);
+    if (tg.Kp % 16 != 0 || tg.K0p % 16 != 0 || ((uintptr_t)src & 15) || ((uintptr_t)dst & 15))
+        return cudaErrorInvalidValue;
+    permute_rows_kernel<<<dim3(M, D), 128, 0, st>>>(src, dst, perm, M, tg.Kp, tg.K0p);
     return cudaGetLastError();
 }
 
@@ -540,7 +595,7 @@ void build_k3tc_items(int M, std::vector<int2>& items) {
     items.clear();
     for (int b = 1; b + 1 < M; ++b) {
         const int nta = (b + kTile - 1) / kTile;
-        const int nte = (M - 1 - b + kTile - 1) / kTile;
+        const int nte = (M - 1 - b + kTileE - 1) / kTileE;
         for (int ta = 0; ta < nta; ++ta)
             for (int te = 0; te < nte; ++te) items.push_back(make_int2(b, (ta << 16) | te));
     }
