@@ -72,12 +72,26 @@ constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
 constexpr uint8_t kClass1Byte = 0x68;          // E4M3 64.0
 static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
               "register split must add up to the launch allocation");
-// Entropy tables sit first in dynamic shared memory at fixed byte offsets, so a
-// lookup is one load with an immediate base: T0 [0, 4096), T1 [4096, 8192),
-// TB [8192, 16384) int32 entries.  The stages follow, 1024-byte aligned.
+// Dynamic shared memory layout (byte offsets from its start):
+//   [align1024(0), +48 KB)        A stages
+//   [kT0Off, +16 KB)              T0: int32 entries 0..4095 (class 0)
+//   [kT1Off, +16 KB)              T1: class 1
+//   [kTBOff, +32 KB)              TB: entries 0..8191 (both classes)
+//   [align1024(kTabEnd), +96 KB)  B stages, then the OH[b] rows
+// The tables sit at fixed offsets, so a lookup is one load with an immediate
+// base.  Every table offset the epilogue forms from counts in [0, 4096) lies in
+// [-32 KB, +32 KB) of T0/T1 and in [-64 KB, +64 KB) of TB; those windows lie
+// inside the layout, so lookups need no clamp: inconsistent counts can only
+// read wrong values, never leave shared memory.
 constexpr int kT0Cap = 4096, kT1Cap = 4096, kTBCap = 8192;
-constexpr size_t kTabBytes = (size_t)(kT0Cap + kT1Cap + kTBCap) * sizeof(int);
-constexpr size_t kStageBytes = kStages * (kTileBytes + kBBytes + kBK);  // A, B, OH[b] rows
+constexpr uint32_t kAStageBytes = kStages * kTileBytes;                // 48 KB
+constexpr uint32_t kT0Off = kAStageBytes + 1024;                       // after A and its alignment slack
+constexpr uint32_t kT1Off = kT0Off + kT0Cap * 4;
+constexpr uint32_t kTBOff = kT1Off + kT1Cap * 4;
+constexpr uint32_t kTabEnd = kTBOff + kTBCap * 4;
+static_assert(kT0Off >= 32768 && kTBOff >= 65536, "guard windows below the tables");
+static_assert(kTBOff + 65536 <= kTabEnd + kStages * 2 * kTileBytes, "guard window above TB");
+constexpr size_t kDynBytes = kTabEnd + 1024 + kStages * (kBBytes + kBK);  // + B stages, OH[b] rows
 
 // Waits for completion regardless of an abort (draining in-flight work); bounded.
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
@@ -94,21 +108,24 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4),
-// clamped to the table's region of cap4 bytes (consistent counts never reach it)
-__device__ __forceinline__ int tab4(const int* t, int n4, unsigned cap4) {
-    return *reinterpret_cast<const int*>(reinterpret_cast<const char*>(t) + min((unsigned)n4, cap4));
+// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4)
+__device__ __forceinline__ int tab4(const int* t, int n4) {
+    return *reinterpret_cast<const int*>(reinterpret_cast<const char*>(t) + n4);
 }
-constexpr unsigned kCap01 = 4 * (kT0Cap - 1), kCapB = 4 * (kTBCap - 1);  // T0/T1 and TB regions
+
+// every count (times 4) in [0, 16380] and a multiple of 4: the range the
+// guard windows of the table layout are sized for
+__device__ __forceinline__ bool counts_ok(int any_or) { return (any_or & (int)0xFFFFC003u) == 0; }
 
 // Per-column constants of an item, counts times 4 (n_x: class count of bin 1
 // of x, n_xy: class count of the voxel (1, 1) of the pair (x, y)).
-struct ColCtx {
+struct __align__(16) ColCtx {
     int n0, n1;    // n_be per class
     int u0, u1;    // n_e - n_be per class
     int sh;        // SH(b, e), int32 fixed point
-    int eo;        // original index of e
     int thr;       // role-e pre-filter: IG(e | a, b) below thr cannot raise e's key
+    int eo;        // original index of e
+    int pad;
 };
 
 // Lower bound, in int32 fixed point with fbits fraction bits, of the IG values
@@ -152,13 +169,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ ColCtx s_col[kEpiThreads / 32][kChunk];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int* sT0 = reinterpret_cast<int*>(dsmem_raw);
-    int* sT1 = sT0 + kT0Cap;
-    int* sTB = sT1 + kT1Cap;
-    uint8_t* stage0 = dsmem_raw + kTabBytes;
-    uint8_t* base = stage0 + ((1024 - (tc::smem_u32(stage0) & 1023)) & 1023);
-    uint8_t* sA = base;
-    uint8_t* sB = base + kStages * kTileBytes;
+    int* sT0 = reinterpret_cast<int*>(dsmem_raw + kT0Off);
+    int* sT1 = reinterpret_cast<int*>(dsmem_raw + kT1Off);
+    int* sTB = reinterpret_cast<int*>(dsmem_raw + kTBOff);
+    uint8_t* sA = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
+    uint8_t* sB = dsmem_raw + kTabEnd + ((1024 - (tc::smem_u32(dsmem_raw + kTabEnd) & 1023)) & 1023);
     uint8_t* sOHb = sB + kStages * kBBytes;
     const int N0 = tg.N0, N1 = tg.N1, N = N0 + N1, np1 = N + 1;
     volatile int* abort = &s_abort;
@@ -167,7 +182,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t dyn_bytes;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
     const bool fits = N0 < kT0Cap && N1 < kT1Cap && N < kTBCap &&
-                      (size_t)(base - dsmem_raw) + kStageBytes <= dyn_bytes;
+                      (size_t)(sOHb - dsmem_raw) + kStages * kBK <= dyn_bytes &&
+                      (size_t)(sA - dsmem_raw) + kAStageBytes <= kT0Off;
 
     if (tid == 0) {
         // an earlier launch failed (skip the work), or the layout has no room (reason 2)
@@ -333,6 +349,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int row = 32 * q + lane;
         const float inv_scale = __int_as_float((127 - fbits) << 23);  // 2^-fbits
         ColCtx* cc = s_col[ew];
+        bool bad = false;       // inconsistent row or column constants
+        uint32_t badbits = 0;   // OR of the pair records' count fields (checked at the end)
         int i = 0;
         for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
             const int buf = i & 1;
@@ -359,9 +377,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const uint32_t bo = (uint32_t)pm[b];
             const int nb0 = 4 * c1[2 * b], nb1 = 4 * c1[2 * b + 1];
-            const int r2_0 = nb0 - pab0, r2_1 = nb1 - pab1;
-            const int r3_0 = na0 - pab0, r3_1 = na1 - pab1;
-            const int kab0 = N0x4 - na0 - nb0 + pab0, kab1 = N1x4 - na1 - nb1 + pab1;
+            int r2_0 = nb0 - pab0, r2_1 = nb1 - pab1;
+            int r3_0 = na0 - pab0, r3_1 = na1 - pab1;
+            int kab0 = N0x4 - na0 - nb0 + pab0, kab1 = N1x4 - na1 - nb1 + pab1;
+            if (!counts_ok(pab0 | pab1 | na0 | na1 | r2_0 | r2_1 | r3_0 | r3_1 | kab0 | kab1)) {
+                // inconsistent inputs: reported through the error flag; the
+                // zeroed constants keep every table offset inside its window
+                bad = true;
+                pab0 = pab1 = r2_0 = r2_1 = r3_0 = r3_1 = kab0 = kab1 = 0;
+            }
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
             // running maxima of the roles a (over e) and b (over this thread's (a, e));
             // columns are visited in ascending e, so ">" keeps the first maximum
@@ -378,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // column constants of this chunk
                     __syncwarp();
                     const int e = ecol0 + lane;
-                    ColCtx x{0, 0, 0, 0, 0, 0, INT_MAX};
+                    ColCtx x{0, 0, 0, 0, 0, INT_MAX, 0, 0};
                     if (lane < ncols) {
                         const PairC p = pd[(size_t)b * M + e];
                         x.n0 = (int)(p.cnt & 0xFFFFu);
@@ -389,6 +413,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         x.eo = pm[e];
                         // keys only grow during the scan: a stale value is a valid lower bound
                         x.thr = key_threshold(__ldcg(keys + x.eo), fbits);
+                        if (!counts_ok(x.n0 | x.n1 | x.u0 | x.u1)) {
+                            bad = true;
+                            x.n0 = x.n1 = x.u0 = x.u1 = 0;
+                        }
                     }
                     cc[lane] = x;
                     __syncwarp();
@@ -425,46 +453,42 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int col = c0 + j;
-                        int ig_e = INT_MIN;
-                        bool cand = false;
-                        if (arow && col < ncols) {
-                            const ColCtx cx = cc[col];
-                            const int pae0 = (int)(pcur[j].cnt & 0xFFFFu), pae1 = (int)(pcur[j].cnt >> 16);
-                            // X = n0 + 4096 n1, exact in FP32
-                            const int xv = __float2int_rn(__uint_as_float(r[j]));
-                            // voxel counts (times 4) by inclusion-exclusion, voxel (v_a v_b v_e)
-                            const int x0 = (xv << 2) & 0x3FFC;
-                            const int p011 = cx.n0 - x0, p101 = pae0 - x0, p110 = pab0 - x0;
-                            const int p001 = cx.u0 - pae0 + x0, p010 = r2_0 - cx.n0 + x0, p100 = r3_0 - pae0 + x0;
-                            const int p000 = kab0 - cx.u0 + pae0 - x0;
-                            const int x1 = (xv >> 10) & ~3;
-                            const int q011 = cx.n1 - x1, q101 = pae1 - x1, q110 = pab1 - x1;
-                            const int q001 = cx.u1 - pae1 + x1, q010 = r2_1 - cx.n1 + x1, q100 = r3_1 - pae1 + x1;
-                            const int q000 = kab1 - cx.u1 + pae1 - x1;
-                            const int sh3 =
-                                tab4(sTB, x0 + x1, kCapB) + tab4(sTB, p011 + q011, kCapB) + tab4(sTB, p101 + q101, kCapB) +
-                                tab4(sTB, p110 + q110, kCapB) + tab4(sTB, p001 + q001, kCapB) +
-                                tab4(sTB, p010 + q010, kCapB) + tab4(sTB, p100 + q100, kCapB) +
-                                tab4(sTB, p000 + q000, kCapB) -
-                                (tab4(sT0, x0, kCap01) + tab4(sT0, p011, kCap01) + tab4(sT0, p101, kCap01) +
-                                 tab4(sT0, p110, kCap01) + tab4(sT0, p001, kCap01) + tab4(sT0, p010, kCap01) +
-                                 tab4(sT0, p100, kCap01) + tab4(sT0, p000, kCap01)) -
-                                (tab4(sT1, x1, kCap01) + tab4(sT1, q011, kCap01) + tab4(sT1, q101, kCap01) +
-                                 tab4(sT1, q110, kCap01) + tab4(sT1, q001, kCap01) + tab4(sT1, q010, kCap01) +
-                                 tab4(sT1, q100, kCap01) + tab4(sT1, q000, kCap01));
-                            // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around int32 differences
-                            const int ig_a = cx.sh - sh3;
-                            const int ig_b = pcur[j].sh - sh3;
-                            ig_e = shab - sh3;
-                            cand = ig_e >= cx.thr;
-                            if (ig_a > best_a) {
-                                best_a = ig_a;
-                                ca = col;
-                            }
-                            if (ig_b > best_b) {
-                                best_b = ig_b;
-                                cb = col;
-                            }
+                        // straight-line for every lane and column: rows and columns outside
+                        // the item compute in-window garbage that is masked out below
+                        const bool valid = arow && col < ncols;
+                        const ColCtx cx = cc[col];
+                        badbits |= pcur[j].cnt;
+                        const int pae0 = (int)(pcur[j].cnt & 0x3FFCu), pae1 = (int)((pcur[j].cnt >> 16) & 0x3FFCu);
+                        // X = n0 + 4096 n1, exact in FP32
+                        const uint32_t xv = (uint32_t)__float2int_rn(__uint_as_float(r[j]));
+                        // voxel counts (times 4) by inclusion-exclusion, voxel (v_a v_b v_e)
+                        const int x0 = (int)((xv << 2) & 0x3FFCu);
+                        const int p011 = cx.n0 - x0, p101 = pae0 - x0, p110 = pab0 - x0;
+                        const int p001 = cx.u0 - pae0 + x0, p010 = r2_0 - cx.n0 + x0, p100 = r3_0 - pae0 + x0;
+                        const int p000 = kab0 - cx.u0 + pae0 - x0;
+                        const int x1 = (int)((xv >> 10) & 0x3FFCu);
+                        const int q011 = cx.n1 - x1, q101 = pae1 - x1, q110 = pab1 - x1;
+                        const int q001 = cx.u1 - pae1 + x1, q010 = r2_1 - cx.n1 + x1, q100 = r3_1 - pae1 + x1;
+                        const int q000 = kab1 - cx.u1 + pae1 - x1;
+                        const int sh3 = tab4(sTB, x0 + x1) + tab4(sTB, p011 + q011) + tab4(sTB, p101 + q101) +
+                                        tab4(sTB, p110 + q110) + tab4(sTB, p001 + q001) + tab4(sTB, p010 + q010) +
+                                        tab4(sTB, p100 + q100) + tab4(sTB, p000 + q000) -
+                                        (tab4(sT0, x0) + tab4(sT0, p011) + tab4(sT0, p101) + tab4(sT0, p110) +
+                                         tab4(sT0, p001) + tab4(sT0, p010) + tab4(sT0, p100) + tab4(sT0, p000)) -
+                                        (tab4(sT1, x1) + tab4(sT1, q011) + tab4(sT1, q101) + tab4(sT1, q110) +
+                                         tab4(sT1, q001) + tab4(sT1, q010) + tab4(sT1, q100) + tab4(sT1, q000));
+                        // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around int32 differences
+                        const int ig_a = cx.sh - sh3;
+                        const int ig_b = pcur[j].sh - sh3;
+                        const int ig_e = valid ? shab - sh3 : INT_MIN;
+                        const bool cand = valid && ig_e >= cx.thr;
+                        if (valid && ig_a > best_a) {
+                            best_a = ig_a;
+                            ca = col;
+                        }
+                        if (valid && ig_b > best_b) {
+                            best_b = ig_b;
+                            cb = col;
                         }
                         // role e: the column's maximum over the warp's rows, written by the
                         // lowest lane (lowest new label a) holding it; skipped when no lane
@@ -493,6 +517,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const unsigned long long mb = warp_max_key(kb_key);  // IG(b | a, e): partners (a, e)
             if (lane == 0 && mb) atomicMax(keys + bo, mb);
         }
+        // a pair count outside [0, 4096) was masked into range above: report it
+        if ((badbits & 0xC003C003u) != 0) bad = true;
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, 4);
     }
 
     // ---------------- teardown ------------------------------------------------
@@ -601,10 +628,10 @@ void build_k3tc_items(int M, std::vector<int2>& items) {
     }
 }
 
-// fixed-capacity tables + stages + alignment slack; 0 if the tables exceed their capacity
+// the fixed layout above; (size_t)-1 if the tables exceed their capacity
 size_t k3tc_smem_bytes(int N0, int N1) {
     if (N0 >= kT0Cap || N1 >= kT1Cap || N0 + N1 >= kTBCap) return (size_t)-1;
-    return kTabBytes + 1024 + kStageBytes;
+    return kDynBytes;
 }
 
 // Largest fraction bits s <= 20 with |IG| 2^s < 2^31 for N samples

@@ -203,6 +203,44 @@ def test_k3_tensor_core_tiles(cuda, M, N):
     _check(codes, y, 2, 3, 0.25, *g, ref, range(M))
 
 
+def test_k3_tensor_core_large_class_counts(cuda):
+    """Class sizes close to 4096: the single FP32 accumulator holds
+    n0 + 4096 n1 with both counts near their limit (wide e groups, many K
+    blocks in both classes)."""
+    rng = np.random.default_rng(77)
+    M, N = 40, 8150
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = np.zeros(N, dtype=np.uint8)
+    y[rng.permutation(N)[:4080]] = 1  # N0 = 4070, N1 = 4080
+    codes = oracle.discretize(x, 1, 1, 0.2, 31)
+    ref = oracle.max_ig(codes, y, 2, 3, 0.25)
+    g = _gpu_max_ig(cuda, x, y, 3, 1, 1, 0.2, 0.25, 31)
+    _check(codes, y, 2, 3, 0.25, *g, ref, range(M))
+
+
+def test_k3_permuted_variable_order_and_repeatability(cuda):
+    """The triple kernel relabels variables by marginal count and prunes role-e
+    updates with the keys found so far.  The same data in two variable orders
+    (two different relabellings) must both match the oracle, and repeated
+    calls must return identical IG, tuples and discretisations whatever the
+    order in which CTAs raised the keys."""
+    rng = np.random.default_rng(5)
+    M, N = 300, 700
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[3] > 0) ^ (x[150] > 0) ^ (x[299] > 0.3)).astype(np.uint8)
+    perm = rng.permutation(M)
+    rows = np.arange(0, M, 37)
+    for xx in (x, np.ascontiguousarray(x[perm])):
+        g = _gpu_max_ig(cuda, xx, y, 3, 1, 2, 0.5, 0.25, 13)
+        codes = oracle.discretize(xx, 1, 2, 0.5, 13)
+        ref = oracle.max_ig(codes, y, 2, 3, 0.25, variables=rows)
+        _check(codes, y, 2, 3, 0.25, *g, ref, rows)
+        for _ in range(2):
+            again = _gpu_max_ig(cuda, xx, y, 3, 1, 2, 0.5, 0.25, 13)
+            for u, v in zip(g, again):
+                assert np.array_equal(u, v)
+
+
 def test_unbalanced_classes_and_int8(cuda):
     rng = np.random.default_rng(9)
     M, N = 40, 777
