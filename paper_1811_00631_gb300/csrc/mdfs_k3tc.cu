@@ -68,6 +68,7 @@ constexpr int kThreads = 640;
 constexpr int kMaskWarp0 = 2, kMaskThreads = 64;
 constexpr int kEpiWarp0 = 4, kEpiThreads = 512;
 constexpr int kChunk = 32;                     // e columns per epilogue pass of a warp
+constexpr int kGroup = 4;                      // columns per TMEM load; pair records prefetched one group ahead
 constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
 constexpr uint8_t kClass1Byte = 0x68;          // E4M3 64.0
 static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
@@ -108,9 +109,12 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4)
-__device__ __forceinline__ int tab4(const int* t, int n4) {
-    return *reinterpret_cast<const int*>(reinterpret_cast<const char*>(t) + n4);
+// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4) of
+// the table starting at shared-window address `base`
+__device__ __forceinline__ int tab4(uint32_t base, int n4) {
+    int v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(base + (uint32_t)n4));
+    return v;
 }
 
 // every count (times 4) in [0, 16380] and a multiple of 4: the range the
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int* sT0 = reinterpret_cast<int*>(dsmem_raw + kT0Off);
     int* sT1 = reinterpret_cast<int*>(dsmem_raw + kT1Off);
     int* sTB = reinterpret_cast<int*>(dsmem_raw + kTBOff);
+    const uint32_t uT0 = tc::smem_u32(sT0), uT1 = tc::smem_u32(sT1), uTB = tc::smem_u32(sTB);
     uint8_t* sA = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
     uint8_t* sB = dsmem_raw + kTabEnd + ((1024 - (tc::smem_u32(dsmem_raw + kTabEnd) & 1023)) & 1023);
     uint8_t* sOHb = sB + kStages * kBBytes;
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ecol0 = e0 + kChunk * ch;
                 const int ncols = ch < kTileE / kChunk ? min(kChunk, M - ecol0) : 0;
                 const PairC* prow = pd + (size_t)min(ecol0, M - 1) * M + (arow ? a : 0);  // prow[(e - ecol0) * M]
-                PairC pnext[8];
+                PairC pnext[kGroup];
                 if (ncols > 0) {
                     // column constants of this chunk
                     __syncwarp();
@@ -420,9 +425,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     cc[lane] = x;
                     __syncwarp();
-                    // pair (a, e) records of the first 8 columns, fetched before the accumulator is read
+                    // pair (a, e) records of the first group, fetched before the accumulator is read
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
+                    for (int j = 0; j < kGroup; ++j)
                         pnext[j] = (arow && j < ncols) ? prow[(size_t)j * M] : PairC{0u, 0};
                 }
                 // every epilogue warp waits for the accumulator of every item, with
@@ -439,19 +444,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t taddr =
                     tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kAccCols + (uint32_t)(kChunk * ch);
 #pragma unroll 1
-                for (int c0 = 0; c0 < ncols; c0 += 8) {
-                    uint32_t r[8];
-                    tc::tmem_ld8(taddr + (uint32_t)c0, r);
-                    PairC pcur[8];
+                for (int c0 = 0; c0 < ncols; c0 += kGroup) {
+                    uint32_t r[kGroup];
+                    tc::tmem_ld(taddr + (uint32_t)c0, r);
+                    PairC pcur[kGroup];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < kGroup; ++j) {
                         pcur[j] = pnext[j];
-                        const int cn = c0 + 8 + j;
+                        const int cn = c0 + kGroup + j;
                         pnext[j] = (arow && cn < ncols) ? prow[(size_t)cn * M] : PairC{0u, 0};
                     }
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < kGroup; ++j) {
                         const int col = c0 + j;
                         // straight-line for every lane and column: rows and columns outside
                         // the item compute in-window garbage that is masked out below
@@ -470,13 +475,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int q011 = cx.n1 - x1, q101 = pae1 - x1, q110 = pab1 - x1;
                         const int q001 = cx.u1 - pae1 + x1, q010 = r2_1 - cx.n1 + x1, q100 = r3_1 - pae1 + x1;
                         const int q000 = kab1 - cx.u1 + pae1 - x1;
-                        const int sh3 = tab4(sTB, x0 + x1) + tab4(sTB, p011 + q011) + tab4(sTB, p101 + q101) +
-                                        tab4(sTB, p110 + q110) + tab4(sTB, p001 + q001) + tab4(sTB, p010 + q010) +
-                                        tab4(sTB, p100 + q100) + tab4(sTB, p000 + q000) -
-                                        (tab4(sT0, x0) + tab4(sT0, p011) + tab4(sT0, p101) + tab4(sT0, p110) +
-                                         tab4(sT0, p001) + tab4(sT0, p010) + tab4(sT0, p100) + tab4(sT0, p000)) -
-                                        (tab4(sT1, x1) + tab4(sT1, q011) + tab4(sT1, q101) + tab4(sT1, q110) +
-                                         tab4(sT1, q001) + tab4(sT1, q010) + tab4(sT1, q100) + tab4(sT1, q000));
+                        const int sh3 = tab4(uTB, x0 + x1) + tab4(uTB, p011 + q011) + tab4(uTB, p101 + q101) +
+                                        tab4(uTB, p110 + q110) + tab4(uTB, p001 + q001) + tab4(uTB, p010 + q010) +
+                                        tab4(uTB, p100 + q100) + tab4(uTB, p000 + q000) -
+                                        (tab4(uT0, x0) + tab4(uT0, p011) + tab4(uT0, p101) + tab4(uT0, p110) +
+                                         tab4(uT0, p001) + tab4(uT0, p010) + tab4(uT0, p100) + tab4(uT0, p000)) -
+                                        (tab4(uT1, x1) + tab4(uT1, q011) + tab4(uT1, q101) + tab4(uT1, q110) +
+                                         tab4(uT1, q001) + tab4(uT1, q010) + tab4(uT1, q100) + tab4(uT1, q000));
                         // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around int32 differences
                         const int ig_a = cx.sh - sh3;
                         const int ig_b = pcur[j].sh - sh3;
