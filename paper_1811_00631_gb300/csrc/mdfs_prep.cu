@@ -3,6 +3,8 @@
 // randomised rank-based discretiser (section "Algorithm and implementation").
 #include <math.h>
 
+#include <algorithm>
+
 #include "mdfs_device.cuh"
 #include "mdfs_internal.cuh"
 
@@ -193,10 +195,10 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
                                                          const int* __restrict__ perm, PlaneGeom g,
                                                          uint32_t* __restrict__ planes, uint8_t* __restrict__ codes,
                                                          float* __restrict__ thr_out, uint8_t* __restrict__ onehot,
-                                                         TcGeom tg) {
-    extern __shared__ float smem[];
-    float* s = smem;           // [npad] sorted column
-    float* thr = smem + npad;  // [D][c-1] thresholds
+                                                         TcGeom tg, int scol) {
+    extern __shared__ __align__(16) float smem[];
+    float* s = smem;           // [scol]: sorted column, then the class-sorted one-hot staging
+    float* thr = smem + scol;  // [D][c-1] thresholds
     const int v = blockIdx.x;
     const int tid = threadIdx.x;
     const T* xv = x + (size_t)v * N;
@@ -261,6 +263,9 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
     }
 
     if (onehot) {
+        // the sorted column is no longer needed: stage x in the class-sorted
+        // one-hot order (NaN in the padding, which compares false)
+        __syncthreads();
         for (int pos = tid; pos < tg.Kp; pos += blockDim.x) {
             int sidx = -1;
             if (pos < tg.K0p) {
@@ -268,13 +273,39 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
             } else if (pos - tg.K0p < g.N1) {
                 sidx = perm[g.N0 + pos - tg.K0p];
             }
-            const float xs = sidx >= 0 ? (float)xv[sidx] : 0.0f;
-            for (int d = 0; d < D; ++d) {
-                int code = 0;
-                for (int j = 0; j < cm1; ++j) code += (xs >= thr[d * cm1 + j]);
-                for (int a = 1; a <= cm1; ++a)
-                    onehot[(((size_t)d * M + v) * cm1 + (a - 1)) * tg.Kp + pos] =
-                        (sidx >= 0 && code == a) ? (uint8_t)0x38 : (uint8_t)0;
+            s[pos] = sidx >= 0 ? (float)xv[sidx] : __int_as_float(0x7fc00000);
+        }
+        __syncthreads();
+        // one 16-byte store per (16 positions, discretisation, bin)
+        const int nchunk = tg.Kp >> 4;
+        for (int w = tid; w < nchunk * D; w += blockDim.x) {
+            const int ch = w % nchunk, d = w / nchunk;
+            float xs[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = reinterpret_cast<const float4*>(s)[ch * 4 + q];
+                xs[4 * q] = f.x;
+                xs[4 * q + 1] = f.y;
+                xs[4 * q + 2] = f.z;
+                xs[4 * q + 3] = f.w;
+            }
+            for (int a = 1; a <= cm1; ++a) {
+                const float lo = thr[d * cm1 + a - 1];
+                const float hi = a < cm1 ? thr[d * cm1 + a] : INFINITY;
+                uint32_t wd[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t b = 0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float xv_ = xs[4 * q + k];
+                        // code == a  <=>  x >= thr[a-1] and not x >= thr[a] (thresholds ascending)
+                        if (xv_ >= lo && !(xv_ >= hi)) b |= 0x38u << (8 * k);
+                    }
+                    wd[q] = b;
+                }
+                reinterpret_cast<uint4*>(onehot + (((size_t)d * M + v) * cm1 + (a - 1)) * tg.Kp)[ch] =
+                    make_uint4(wd[0], wd[1], wd[2], wd[3]);
             }
         }
     }
@@ -308,7 +339,9 @@ cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int
                               uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st) {
     int npad = 1;
     while (npad < N) npad <<= 1;
-    const size_t smem = sizeof(float) * ((size_t)npad + (size_t)D * (c - 1));
+    // sorted column, reused for the class-sorted one-hot staging (Kp may exceed npad)
+    const size_t scol = (size_t)std::max(npad, tg.Kp);
+    const size_t smem = sizeof(float) * (scol + (size_t)D * (c - 1));
     const uint32_t R = (uint32_t)floor(range * 1048576.0 + 0.5);
     const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
     cudaError_t e;
@@ -316,12 +349,12 @@ cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int
         e = ensure_dynamic_smem((const void*)discretize_kernel<float>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<float><<<M, 512, smem, st>>>((const float*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                       planes, codes, thr, onehot, tg);
+                                                       planes, codes, thr, onehot, tg, (int)scol);
     } else {
         e = ensure_dynamic_smem((const void*)discretize_kernel<int8_t>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<int8_t><<<M, 512, smem, st>>>((const int8_t*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                        planes, codes, thr, onehot, tg);
+                                                        planes, codes, thr, onehot, tg, (int)scol);
     }
     return cudaGetLastError();
 }
