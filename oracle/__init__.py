@@ -9,7 +9,11 @@ no code.  Every function restates the paper (arXiv 1811.00631):
   "Algorithm and implementation";
 * ``sh`` / ``ig_one`` / ``max_ig`` -- Eq. (1), Eq. (3), Eqs. H, p and beta;
 * ``chi2_cdf`` / ``ig_lim`` -- the chi^2 / extreme-value significance fit of
-  section "Theory".
+  section "Theory";
+* ``shuffle_index`` / ``contrast`` / ``p_adjust`` / ``select`` -- contrast
+  variables and the canonical selection pipeline of section "Canonical
+  package usage" (contrasts, IG, fit on the contrasts, adjusted p-values,
+  relevant set).
 
 The readings taken where the paper is silent are listed in the C file header.
 """
@@ -77,6 +81,10 @@ def _load():
     lib.oracle_ig_lim.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_double,
                                   P, P, P]
     lib.oracle_ig_lim.restype = ctypes.c_int
+    lib.oracle_shuffle_index.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64]
+    lib.oracle_shuffle_index.restype = ctypes.c_uint32
+    lib.oracle_contrast.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, P]
+    lib.oracle_contrast.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = ctypes.c_int
     lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
@@ -202,6 +210,95 @@ def ig_lim(ig: np.ndarray, k: int, divisions: int, irrelevant_mask=None, alpha: 
     if rc != 0:
         raise ValueError(f"oracle_ig_lim failed ({rc})")
     return p, lim.value, neff.value
+
+
+def shuffle_index(i: int, n: int, stream: int, seed: int) -> int:
+    """Image of i under the counter-based pseudo-random permutation of [0, n)
+    (10-round Feistel network with Philox round functions, cycle walking)."""
+    return int(_load().oracle_shuffle_index(int(i), int(n), int(stream) & 0xFFFFFFFF, int(seed) & (2**64 - 1)))
+
+
+def contrast(x: np.ndarray, n_contrast: int, seed: int):
+    """Contrast variables (section "Canonical package usage"): returns
+    (x_ext f32[M + n_contrast][N], src i32[n_contrast]); row M + j is
+    variable src[j] with its samples shuffled."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    M, N = x.shape
+    out = np.zeros((M + n_contrast, N), dtype=np.float32)
+    src = np.zeros(max(n_contrast, 1), dtype=np.int32)
+    rc = lib.oracle_contrast(_ptr(x), N, M, int(n_contrast), int(seed) & (2**64 - 1), _ptr(out), _ptr(src))
+    if rc != 0:
+        raise ValueError(f"oracle_contrast failed ({rc})")
+    return out, src[:n_contrast]
+
+
+P_ADJUST_METHODS = ("none", "bonferroni", "holm", "hochberg", "BH", "BY")
+
+
+def p_adjust(p: np.ndarray, method: str = "holm") -> np.ndarray:
+    """Multiple-testing adjustment of p-values, written from the definitions
+    (p_(1) <= ... <= p_(m) the sorted values, results capped at 1):
+    Bonferroni m p; Holm's step-down max_{k<=i} (m-k+1) p_(k); Hochberg's
+    step-up min_{k>=i} (m-k+1) p_(k); Benjamini-Hochberg min_{k>=i} m/k p_(k);
+    Benjamini-Yekutieli the same times sum_{k=1..m} 1/k."""
+    p = np.asarray(p, dtype=np.float64)
+    m = len(p)
+    if m == 0 or method == "none":
+        return p.copy()
+    order = np.argsort(p, kind="stable")
+    ps = p[order]
+    adj = np.empty(m)
+    if method == "bonferroni":
+        adj = np.minimum(1.0, m * ps)
+    elif method == "holm":
+        run = 0.0
+        for i in range(m):
+            run = max(run, (m - i) * ps[i])
+            adj[i] = min(1.0, run)
+    elif method in ("hochberg", "BH", "BY"):
+        q = sum(1.0 / k for k in range(1, m + 1)) if method == "BY" else 1.0
+        run = np.inf
+        for i in range(m - 1, -1, -1):
+            f = (m - i) if method == "hochberg" else q * m / (i + 1)
+            run = min(run, f * ps[i])
+            adj[i] = min(1.0, run)
+    else:
+        raise ValueError(f"unknown method {method!r}")
+    out = np.empty(m)
+    out[order] = adj
+    return out
+
+
+def select(x: np.ndarray, y: np.ndarray, n_contrast: int, k: int, divisions: int, discretizations: int,
+           range_: float, pc_xi: float, seed: int, method: str = "holm", level: float = 0.05, variables=None):
+    """The canonical pipeline of section "Canonical package usage": contrast
+    variables, IG^k_max over the extended set, the chi^2 / extreme-value fit on
+    the contrast variables only, p-values of the original variables, their
+    adjustment and the relevant set (adjusted p < level).  Returns a dict with
+    ig / tuples / disc / p / adjusted / relevant for the M original variables
+    and ig_lim, n_eff, src.  ``variables`` (optional) restricts the IG scan to
+    those original rows plus all contrasts (the fit needs every contrast)."""
+    M = x.shape[0]
+    x_ext, src = contrast(x, n_contrast, seed)
+    c = divisions + 1
+    codes = discretize(x_ext, divisions, discretizations, range_, seed)
+    Mx = M + n_contrast
+    rows = np.arange(Mx, dtype=np.int32) if variables is None else \
+        np.concatenate([np.asarray(variables, dtype=np.int32), np.arange(M, Mx, dtype=np.int32)])
+    r = max_ig(codes, y, c, k, pc_xi, variables=rows)
+    ig = np.full(Mx, np.nan)
+    ig[rows] = r["ig"]
+    mask = np.zeros(Mx, dtype=np.uint8)
+    mask[M:] = 1
+    p_ext, lim, neff = ig_lim(ig[M:], k, divisions)  # fitted on the contrasts only
+    # p-values of the original variables under the fitted T
+    df = (c - 1) * c ** (k - 1)
+    p = np.array([1.0 - chi2_cdf(2.0 * g, df) ** neff if g > 0 else 1.0 for g in ig[:M]])
+    adj = p_adjust(p, method)
+    out = {"ig": ig[:M], "tuples": None, "disc": None, "p": p, "adjusted": adj, "relevant": adj < level,
+           "ig_lim": lim, "n_eff": neff, "src": src, "rows": rows, "max_ig": r}
+    return out
 
 
 def num_threads() -> int:

@@ -36,6 +36,13 @@
  *   - argmax ties go to the lowest (discretisation, lexicographic tuple).
  *   - the chi^2 extreme-value fit: CDF F_df(2x)^T, T fitted by maximum
  *     likelihood on the irrelevant variables (closed form).
+ *   - contrast variables (section "Canonical package usage"): copies of
+ *     original variables with their samples shuffled.  The shuffle is our
+ *     choice of a counter-based pseudo-random permutation (a 10-round Feistel
+ *     network with Philox round functions, restricted to [0, n) by cycle
+ *     walking); the sources are the same permutation of [0, M) at j mod M.
+ *   - p-value adjustment: the step-down / step-up definitions of Holm,
+ *     Hochberg, Bonferroni, Benjamini-Hochberg and Benjamini-Yekutieli.
  */
 #include <math.h>
 #include <stdint.h>
@@ -400,3 +407,66 @@ void oracle_set_num_threads(int n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Contrast variables (section "Canonical package usage").                   */
+/*                                                                            */
+/* Pseudo-random permutation of [0, n): the Luby-Rackoff (Feistel) network    */
+/* on 2h-bit words, h = ceil(ceil(log2 n) / 2), 10 rounds (fewer rounds leave */
+/* measurable bias on small domains; 10 is the count of NIST's FF1)          */
+/*     (L, R) -> (R, L xor F_r(R)),   F_r(R) = Philox4x32-10 word 0 of        */
+/*     counter (R, r, stream, 0x43545253), key (seed_lo, seed_hi), masked to h */
+/*     bits,                                                                  */
+/* is a bijection of [0, 2^(2h)); cycle walking (Black and Rogaway, "Ciphers  */
+/* with arbitrary finite domains", CT-RSA 2002) applies it until the value    */
+/* falls below n, which restricts it to a bijection of [0, n).  The orbit of  */
+/* i returns to i within 2^(2h) steps, so the walk ends.                      */
+/* ------------------------------------------------------------------------ */
+static const uint32_t kContrastTag = 0x43545253u;  /* "CTRS" */
+
+static uint32_t feistel10(uint32_t v, int h, uint32_t stream, const uint32_t key[2])
+{
+    const uint32_t mask = (h >= 32) ? 0xFFFFFFFFu : ((1u << h) - 1u);
+    uint32_t L = v >> h, R = v & mask;
+    for (uint32_t r = 0; r < 10; ++r) {
+        uint32_t ctr[4] = {R, r, stream, kContrastTag}, out[4];
+        oracle_philox4x32_10(ctr, key, out);
+        uint32_t nl = R, nr = (L ^ out[0]) & mask;
+        L = nl;
+        R = nr;
+    }
+    return (L << h) | R;
+}
+
+uint32_t oracle_shuffle_index(uint32_t i, uint32_t n, uint32_t stream, uint64_t seed)
+{
+    if (n <= 1) return 0;
+    int b = 0;
+    while ((1ull << b) < (unsigned long long)n) ++b;   /* 2^b >= n */
+    int h = (b + 1) / 2;
+    if (h < 1) h = 1;
+    const uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t v = i;
+    do {
+        v = feistel10(v, h, stream, key);
+    } while (v >= n);
+    return v;
+}
+
+/* x_out [(M + n_contrast)][N]: rows 0..M-1 are x; row M + j is variable
+ * src[j] = shuffle_M(j mod M) (stream 0xFFFFFFFF) with sample i taken from
+ * sample shuffle_N(i) (stream j). */
+int oracle_contrast(const float* x, int N, int M, int n_contrast, uint64_t seed, float* x_out, int32_t* src)
+{
+    if (N < 1 || M < 1 || n_contrast < 0) return -1;
+    memcpy(x_out, x, sizeof(float) * (size_t)N * (size_t)M);
+    for (int j = 0; j < n_contrast; ++j) {
+        const uint32_t s = oracle_shuffle_index((uint32_t)(j % M), (uint32_t)M, 0xFFFFFFFFu, seed);
+        if (src) src[j] = (int32_t)s;
+        float* row = x_out + (size_t)(M + j) * N;
+        for (int i = 0; i < N; ++i)
+            row[i] = x[(size_t)s * N + oracle_shuffle_index((uint32_t)i, (uint32_t)N, (uint32_t)j, seed)];
+    }
+    return 0;
+}
+
