@@ -167,6 +167,73 @@ int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretization
                 double* n_eff, void* stream);
 
 /*
+ * Contrast variables (section "Canonical package usage"): copies of original
+ * variables with their samples shuffled, appended to the data so that the
+ * significance fit sees variables known to be irrelevant.
+ *
+ * Row M + j of x_ext (j < n_contrast) is variable src[j] = P_M(j mod M) with
+ * sample i taken from sample P_N^(j)(i), where P_n^(s) is a pseudo-random
+ * permutation of [0, n): a 10-round Feistel network on 2h-bit words
+ * (h = ceil(ceil(log2 n) / 2)) with round function word 0 of Philox4x32-10
+ * (counter (R, round, s, 0x43545253), key = seed), restricted to [0, n) by
+ * cycle walking; P_M uses stream s = 0xFFFFFFFF.  Sources are drawn without
+ * replacement while j < M.  Rows 0 .. M-1 of x_ext are x.
+ *
+ * data:       x (dtype, [M][N] variable-major), y unused; host or device.
+ * n_contrast: 0 .. 65535 - M.
+ * x_ext:      [(M + n_contrast)][N] of x's dtype, caller-owned, host or device.
+ * src:        [n_contrast] int32 or NULL, host or device.
+ * Errors: MDFS_EINVAL (arguments), MDFS_ENOMEM, MDFS_ECUDA.
+ */
+int mdfs_contrast(const mdfs_data* data, int n_contrast, uint64_t seed, void* x_ext, int32_t* src, void* stream);
+
+/* Multiple-testing adjustments of p-values (the selection step of section
+ * "Canonical package usage"). */
+#define MDFS_ADJUST_NONE 0
+#define MDFS_ADJUST_BONFERRONI 1
+#define MDFS_ADJUST_HOLM 2
+#define MDFS_ADJUST_HOCHBERG 3
+#define MDFS_ADJUST_BH 4
+#define MDFS_ADJUST_BY 5
+
+/*
+ * Adjusts m p-values (p_(1) <= ... <= p_(m) sorted, ties by index, results
+ * capped at 1): Bonferroni m p; Holm max_{s<=r} (m-s+1) p_(s); Hochberg
+ * min_{s>=r} (m-s+1) p_(s); Benjamini-Hochberg min_{s>=r} m/s p_(s);
+ * Benjamini-Yekutieli the same times sum_{s=1..m} 1/s.  NaN inputs are not
+ * counted in m and stay NaN.  Runs as one CTA on the device.
+ *
+ * p, adjusted: [m] double, host or device; m in 1 .. 65536.
+ * Errors: MDFS_EINVAL (arguments, unknown method), MDFS_ENOMEM, MDFS_ECUDA.
+ */
+int mdfs_p_adjust(const double* p, int m, int method, double* adjusted, void* stream);
+
+/*
+ * The canonical selection pipeline (section "Canonical package usage"):
+ *   1. n_contrast contrast variables (mdfs_contrast, same seed);
+ *   2. IG^k_max over the M + n_contrast variables (mdfs_max_ig, same seed);
+ *   3. the chi^2 / extreme-value fit (mdfs_ig_lim) on the contrast variables
+ *      only, at alpha = level, and p-values for every variable;
+ *   4. the adjustment (mdfs_p_adjust) of the p-values of the M original
+ *      variables (contrast variables do not enter the adjustment);
+ *   5. relevant[i] = adjusted[i] < level.
+ *
+ * Outputs are for the M original variables (host or device, caller-owned):
+ * ig [M] float; tuples [M][k-1] int32 or NULL (partner indices in
+ * [0, M + n_contrast): M + j is contrast j); best_disc [M] int32 or NULL;
+ * p_values, adjusted [M] double; relevant [M] uint8; ig_lim, n_eff one
+ * double each or NULL; contrast_src [n_contrast] int32 or NULL.
+ * Limits: n_contrast >= 1 and M + n_contrast <= 65535, plus the limits of
+ * mdfs_max_ig on the extended set.
+ * Errors: those of mdfs_max_ig and mdfs_ig_lim (MDFS_EDEGENERATE when no
+ * contrast variable has IG > 0).
+ */
+int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int discretizations, double range,
+                double pc_xi, uint64_t seed, int p_adjust_method, double level, float* ig, int32_t* tuples,
+                int32_t* best_disc, double* p_values, double* adjusted, uint8_t* relevant, double* ig_lim,
+                double* n_eff, int32_t* contrast_src, void* stream);
+
+/*
  * mdfs_max_ig without any device allocation (the paper has no counterpart:
  * this is a deployment variant).
  *

@@ -47,6 +47,7 @@ struct Workspace {
     Buffer bx, by, bidx, bperm;  // batch: gathered job data and the job index maps
     Buffer items3;               // k = 2 tensor-core tile list
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
+    Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
     int items3_M = -1, items3_c = -1, n_items3 = 0;
     int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
@@ -57,7 +58,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2};
+                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -266,6 +267,15 @@ int bind_out(Workspace* ws, Buffer& buf, T* user, size_t count, Out<T>* o) {
 template <typename T>
 int copy_back(Workspace* ws, const Out<T>& o) {
     if (o.staged) MDFS_CUDA_TRY(cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, ws->stream));
+    return MDFS_OK;
+}
+
+// Copies `count` elements of a device array to a caller pointer (host or device).
+template <typename T>
+int emit(Workspace* ws, const T* dev, T* user, size_t count) {
+    if (!user || count == 0) return MDFS_OK;
+    MDFS_CUDA_TRY(cudaMemcpyAsync(user, dev, count * sizeof(T),
+                                  is_device_ptr(user) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ws->stream));
     return MDFS_OK;
 }
 
@@ -821,6 +831,156 @@ int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretization
         if (is_device_ptr(n_eff)) MDFS_CUDA_TRY(cudaMemcpyAsync(n_eff, res + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
         else *n_eff = ws->host_res[1];
     }
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_contrast(const mdfs_data* data, int n_contrast, uint64_t seed, void* x_ext, int32_t* src, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, false);
+    if (rc) return rc;
+    const int N = data->N, M = data->M;
+    if (n_contrast < 0 || M + n_contrast > 65535)
+        return fail(MDFS_EINVAL, "n_contrast = %d: M + n_contrast must lie in [M, 65535]", n_contrast);
+    if (!x_ext) return fail(MDFS_EINVAL, "x_ext is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    rc = stage_inputs(ws, data, false, &xd, &yd, &n1);
+    if (rc) return rc;
+    const size_t elem = data->dtype == MDFS_F32 ? 4 : 1;
+    Out<uint8_t> ox;
+    Out<int32_t> os;
+    rc = bind_out(ws, ws->xe, (uint8_t*)x_ext, (size_t)(M + n_contrast) * N * elem, &ox);
+    if (rc) return rc;
+    rc = bind_out(ws, ws->srcb, src, (size_t)n_contrast, &os);
+    if (rc) return rc;
+    MDFS_CUDA_TRY(cudaMemcpyAsync(ox.dev, xd, (size_t)M * N * elem, cudaMemcpyDeviceToDevice, st));
+    MDFS_LAUNCH("contrast", st, launch_contrast(xd, data->dtype, N, M, n_contrast, seed, ox.dev, os.dev, st));
+    if ((rc = copy_back(ws, ox)) || (rc = copy_back(ws, os))) return rc;
+    if (ox.staged || os.staged || st == nullptr) MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_p_adjust(const double* p, int m, int method, double* adjusted, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    if (!p || !adjusted) return fail(MDFS_EINVAL, "p and adjusted must not be NULL");
+    if (m < 1 || m > 65536) return fail(MDFS_EINVAL, "m = %d outside [1, 65536]", m);
+    if (method < MDFS_ADJUST_NONE || method > MDFS_ADJUST_BY) return fail(MDFS_EINVAL, "unknown method %d", method);
+    int rc = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const double* pd = p;
+    if (!is_device_ptr(p)) {
+        MDFS_ENSURE(ws, pext, (size_t)m * sizeof(double));
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->pext.p, p, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st));
+        pd = (const double*)ws->pext.p;
+    }
+    Out<double> oa;
+    rc = bind_out(ws, ws->adjb, adjusted, (size_t)m, &oa);
+    if (rc) return rc;
+    MDFS_ENSURE(ws, padj, p_adjust_scratch_bytes(m));
+    MDFS_LAUNCH("p_adjust", st, launch_p_adjust(pd, m, method, 1.0, ws->padj.p, oa.dev, nullptr, st));
+    rc = copy_back(ws, oa);
+    if (rc) return rc;
+    if (oa.staged || st == nullptr) MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int discretizations, double range,
+                double pc_xi, uint64_t seed, int p_adjust_method, double level, float* ig, int32_t* tuples,
+                int32_t* best_disc, double* p_values, double* adjusted, uint8_t* relevant, double* ig_lim,
+                double* n_eff, int32_t* contrast_src, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, true);
+    if (rc) return rc;
+    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    const int Mx = M + n_contrast;
+    if (n_contrast < 1 || Mx > 65535)
+        return fail(MDFS_EINVAL, "n_contrast = %d: need n_contrast >= 1 and M + n_contrast <= 65535", n_contrast);
+    if (k < 1 || k > 3) return fail(MDFS_EINVAL, "k = %d outside [1, 3]", k);
+    if (Mx < k) return fail(MDFS_EINVAL, "M + n_contrast = %d smaller than k = %d", Mx, k);
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
+    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
+    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
+    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if (!(level > 0.0 && level < 1.0)) return fail(MDFS_EINVAL, "level must lie in (0, 1)");
+    if (p_adjust_method < MDFS_ADJUST_NONE || p_adjust_method > MDFS_ADJUST_BY)
+        return fail(MDFS_EINVAL, "unknown p_adjust_method %d", p_adjust_method);
+    if (!ig || !p_values || !adjusted || !relevant)
+        return fail(MDFS_EINVAL, "ig, p_values, adjusted and relevant must not be NULL");
+    if (k == 2 && (unsigned long long)D * Mx >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
+    if (k == 3 && (unsigned long long)D * Mx * Mx >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * (M + n_contrast)^2 must stay below 2^32 for k = 3");
+    int df = c - 1;
+    for (int j = 1; j < k; ++j) df *= c;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    rc = stage_inputs(ws, data, true, &xd, &yd, &n1);
+    if (rc) return rc;
+    // 1. the extended variable set
+    const size_t elem = data->dtype == MDFS_F32 ? 4 : 1;
+    MDFS_ENSURE(ws, xe, (size_t)Mx * N * elem);
+    MDFS_ENSURE(ws, srcb, (size_t)n_contrast * sizeof(int));
+    MDFS_CUDA_TRY(cudaMemcpyAsync(ws->xe.p, xd, (size_t)M * N * elem, cudaMemcpyDeviceToDevice, st));
+    MDFS_LAUNCH("contrast", st,
+                launch_contrast(xd, data->dtype, N, M, n_contrast, seed, ws->xe.p, (int*)ws->srcb.p, st));
+    // 2. IG^k_max over it
+    bool check_err = false;
+    rc = scan_core(ws, ws->xe.p, data->dtype, N, Mx, n1, k, divisions, D, range, pc_xi, seed, &check_err);
+    if (rc) return rc;
+    const int kk = k > 1 ? k - 1 : 1;
+    MDFS_ENSURE(ws, igx, (size_t)Mx * sizeof(float));
+    MDFS_ENSURE(ws, tux, (size_t)Mx * kk * sizeof(int));
+    MDFS_ENSURE(ws, dix, (size_t)Mx * sizeof(int));
+    float* igx = (float*)ws->igx.p;
+    MDFS_LAUNCH("finalize", st, launch_finalize((const unsigned long long*)ws->keys.p, Mx, k, igx,
+                                                k > 1 ? (int*)ws->tux.p : nullptr, (int*)ws->dix.p, st));
+    if (check_err) {
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (ws->host_stats[8]) return kernel_flag_error(ws->host_stats[8]);
+    }
+    // 3. the fit on the contrast variables, p-values of every variable
+    MDFS_ENSURE(ws, mask, (size_t)Mx);
+    MDFS_CUDA_TRY(cudaMemsetAsync(ws->mask.p, 0, (size_t)M, st));
+    MDFS_CUDA_TRY(cudaMemsetAsync((uint8_t*)ws->mask.p + M, 1, (size_t)n_contrast, st));
+    MDFS_ENSURE(ws, pext, (size_t)Mx * sizeof(double));
+    MDFS_ENSURE(ws, res, 4 * sizeof(double));
+    double* pext = (double*)ws->pext.p;
+    double* res = (double*)ws->res.p;
+    MDFS_CUDA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(double), st));
+    MDFS_LAUNCH("ig_lim", st, launch_ig_lim(igx, Mx, df, (const uint8_t*)ws->mask.p, level, pext, res, st));
+    // 4-5. adjustment over the original variables and the relevant set
+    MDFS_ENSURE(ws, adjb, (size_t)M * sizeof(double));
+    MDFS_ENSURE(ws, relb, (size_t)M);
+    MDFS_ENSURE(ws, padj, p_adjust_scratch_bytes(M));
+    MDFS_LAUNCH("p_adjust", st, launch_p_adjust(pext, M, p_adjust_method, level, ws->padj.p, (double*)ws->adjb.p,
+                                                (uint8_t*)ws->relb.p, st));
+    MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_res, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(ws->host_res[2] > 0.0) || !(ws->host_res[1] > 0.0))
+        return fail(MDFS_EDEGENERATE, "no contrast variable with IG > 0");
+    if ((rc = emit(ws, igx, ig, (size_t)M)) || (rc = emit(ws, (const int*)ws->tux.p, tuples, (size_t)M * (k - 1))) ||
+        (rc = emit(ws, (const int*)ws->dix.p, best_disc, (size_t)M)) || (rc = emit(ws, (const double*)pext, p_values, (size_t)M)) ||
+        (rc = emit(ws, (const double*)ws->adjb.p, adjusted, (size_t)M)) ||
+        (rc = emit(ws, (const uint8_t*)ws->relb.p, relevant, (size_t)M)) ||
+        (rc = emit(ws, (const int*)ws->srcb.p, contrast_src, (size_t)n_contrast)) ||
+        (rc = emit(ws, (const double*)res, ig_lim, 1)) || (rc = emit(ws, (const double*)res + 1, n_eff, 1)))
+        return rc;
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     return MDFS_OK;
 }

@@ -137,6 +137,16 @@ cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0,
                         int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
                         unsigned long long* keys, int* err, cudaStream_t st);
 
+// Contrast rows M .. M + n_contrast - 1 of x_ext (dtype 0 f32, 1 i8); rows
+// 0 .. M-1 are not written.  src [n_contrast] or NULL.
+cudaError_t launch_contrast(const void* x, int dtype, int N, int M, int n_contrast, uint64_t seed, void* x_ext,
+                            int* src, cudaStream_t st);
+// p-value adjustment (MDFS_ADJUST_*), one CTA; scratch of p_adjust_scratch_bytes(m);
+// relevant [m] (adjusted < level) or NULL.
+size_t p_adjust_scratch_bytes(int m);
+cudaError_t launch_p_adjust(const double* p, int m, int method, double level, void* scratch, double* adjusted,
+                            uint8_t* relevant, cudaStream_t st);
+
 // keys [M] -> ig [M] f32, tuples [M][k-1] i32 (NULL ok), disc [M] i32 (NULL ok).
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,
                             int* disc, cudaStream_t st);

@@ -32,7 +32,11 @@ _ERRORS = {
 
 EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
-            "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode")
+            "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
+            "mdfs_contrast", "mdfs_p_adjust", "mdfs_select")
+
+# p-value adjustment methods (MDFS_ADJUST_* of include/mdfs.h)
+P_ADJUST = {"none": 0, "bonferroni": 1, "holm": 2, "hochberg": 3, "BH": 4, "BY": 5}
 
 
 class MdfsError(RuntimeError):
@@ -81,6 +85,14 @@ def load(path: str = LIB_PATH):
         lib.mdfs_ig_lim.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                     ctypes.c_double, P, P, P, P]
         lib.mdfs_ig_lim.restype = ctypes.c_int
+        lib.mdfs_contrast.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_uint64, P, P, P]
+        lib.mdfs_contrast.restype = ctypes.c_int
+        lib.mdfs_p_adjust.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+        lib.mdfs_p_adjust.restype = ctypes.c_int
+        lib.mdfs_select.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
+                                    P, P, P, P, P, P, P, P, P, P]
+        lib.mdfs_select.restype = ctypes.c_int
         lib.mdfs_last_error.argtypes = []
         lib.mdfs_last_error.restype = ctypes.c_char_p
         lib.mdfs_release.argtypes = []
@@ -353,6 +365,99 @@ def ig_lim(ig, k: int, divisions: int, discretizations: int = 1, irrelevant_mask
                              ctypes.c_void_p(p.ctypes.data), ctypes.byref(lim), ctypes.byref(neff), None)
     _check(rc)
     return p, lim.value, neff.value
+
+
+def contrast(x, n_contrast: int, seed: int = 0):
+    """Contrast variables (section "Canonical package usage"): returns
+    (x_ext [(M + n_contrast), N] of x's dtype, src i32[n_contrast]) on the
+    device of x (torch) or the host (numpy).  Row M + j is variable src[j] with
+    its samples shuffled by a counter-based permutation (include/mdfs.h)."""
+    lib = load()
+    data, keep = _data(x, None)
+    M, N = data.M, data.N
+    if _is_cuda(x):
+        import torch
+        xe = torch.empty((M + n_contrast, N), dtype=x.dtype, device=x.device)
+        src = torch.empty(max(n_contrast, 1), dtype=torch.int32, device=x.device)
+        rc = lib.mdfs_contrast(ctypes.byref(data), int(n_contrast), int(seed) & (2**64 - 1),
+                               ctypes.c_void_p(xe.data_ptr()), ctypes.c_void_p(src.data_ptr()), _stream_of(x))
+    else:
+        xe = np.empty((M + n_contrast, N), dtype=np.int8 if data.dtype == MDFS_I8 else np.float32)
+        src = np.empty(max(n_contrast, 1), dtype=np.int32)
+        rc = lib.mdfs_contrast(ctypes.byref(data), int(n_contrast), int(seed) & (2**64 - 1),
+                               ctypes.c_void_p(xe.ctypes.data), ctypes.c_void_p(src.ctypes.data), None)
+    _check(rc)
+    del keep
+    return xe, src[:n_contrast]
+
+
+def p_adjust(p, method: str = "holm"):
+    """Multiple-testing adjustment of p-values (Holm, Hochberg, Bonferroni, BH,
+    BY, none) on the device; returns an array of the same kind as p."""
+    lib = load()
+    m = int(p.shape[0])
+    if _is_cuda(p):
+        import torch
+        pc = p.contiguous().double()
+        out = torch.empty(m, dtype=torch.float64, device=p.device)
+        rc = lib.mdfs_p_adjust(ctypes.c_void_p(pc.data_ptr()), m, P_ADJUST[method], ctypes.c_void_p(out.data_ptr()),
+                               _stream_of(p))
+    else:
+        pc = _host(p, np.float64)
+        out = np.empty(m, dtype=np.float64)
+        rc = lib.mdfs_p_adjust(ctypes.c_void_p(pc.ctypes.data), m, P_ADJUST[method], ctypes.c_void_p(out.ctypes.data),
+                               None)
+    _check(rc)
+    return out
+
+
+def select(x, y, n_contrast: int = None, k: int = 1, divisions: int = 1, discretizations: int = 1,
+           range_: float = 0.0, pc_xi: float = 0.25, seed: int = 0, p_adjust_method: str = "holm",
+           level: float = 0.05):
+    """The canonical selection pipeline (section "Canonical package usage"):
+    contrast variables, IG^k_max over the extended set, the chi^2 /
+    extreme-value fit on the contrasts, adjusted p-values and the relevant set,
+    all on the device.  n_contrast defaults to max(M, 30).  Returns a dict of
+    arrays for the M original variables (torch on x's device, or numpy):
+    ig, tuples, disc, p_value, adjusted_p_value, relevant (bool), plus ig_lim,
+    n_eff and contrast_src."""
+    lib = load()
+    data, keep = _data(x, y)
+    M = data.M
+    nc = max(M, 30) if n_contrast is None else int(n_contrast)
+    kk = max(k - 1, 1)
+    lim = ctypes.c_double()
+    neff = ctypes.c_double()
+    if _is_cuda(x):
+        import torch
+        dev = x.device
+        ig = torch.empty(M, dtype=torch.float32, device=dev)
+        tu = torch.empty((M, kk), dtype=torch.int32, device=dev)
+        di = torch.empty(M, dtype=torch.int32, device=dev)
+        pv = torch.empty(M, dtype=torch.float64, device=dev)
+        adj = torch.empty(M, dtype=torch.float64, device=dev)
+        rel = torch.empty(M, dtype=torch.uint8, device=dev)
+        src = torch.empty(nc, dtype=torch.int32, device=dev)
+        ptr = lambda a: ctypes.c_void_p(a.data_ptr())
+        stream = _stream_of(x)
+    else:
+        ig = np.empty(M, dtype=np.float32)
+        tu = np.empty((M, kk), dtype=np.int32)
+        di = np.empty(M, dtype=np.int32)
+        pv = np.empty(M, dtype=np.float64)
+        adj = np.empty(M, dtype=np.float64)
+        rel = np.empty(M, dtype=np.uint8)
+        src = np.empty(nc, dtype=np.int32)
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+        stream = None
+    rc = lib.mdfs_select(ctypes.byref(data), nc, k, divisions, discretizations, float(range_), float(pc_xi),
+                         int(seed) & (2**64 - 1), P_ADJUST[p_adjust_method], float(level), ptr(ig),
+                         ptr(tu) if k > 1 else None, ptr(di), ptr(pv), ptr(adj), ptr(rel), ctypes.byref(lim),
+                         ctypes.byref(neff), ptr(src), stream)
+    _check(rc)
+    del keep
+    return {"ig": ig, "tuples": tu[:, : k - 1], "disc": di, "p_value": pv, "adjusted_p_value": adj,
+            "relevant": rel != 0, "ig_lim": lim.value, "n_eff": neff.value, "contrast_src": src}
 
 
 def last_launch_count() -> int:
