@@ -293,6 +293,8 @@ def run_gpu(args, rank, world, local_rank):
             "kernels": shares}
     if args.serving_jobs > 0:
         line["serving"] = serving_run(args.serving_jobs, local_rank)
+    if args.select_reps > 0:
+        line["select"] = select_run(args.select_reps, local_rank)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -304,6 +306,44 @@ def run_gpu(args, rank, world, local_rank):
                                           f"{DISC} discretisations, {dt:.1f} s"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def select_run(reps: int, device: int):
+    """The canonical selection pipeline (contrasts, IG scan over the extended
+    set, fit on the contrasts, Holm-adjusted p-values, relevant set) on 2000 x
+    500 data with 5 planted XOR pairs (10% label flips; a pair is invisible to
+    single-variable tests) and n_contrast = M = 500, for k = 2 and k = 3.
+    Timed with CUDA events on the current stream around whole mdfs_select
+    calls (device-resident inputs; the call returns after the result is on the
+    device).  evals counts unordered tuples of the extended set x
+    discretisations."""
+    import torch
+    from paper_1811_00631_gb300 import mdfs, synth
+    dev = torch.device("cuda", device)
+    ds = synth.xor_pairs(N=N_OBJ, M=M_VAR, n_pairs=5, flip=0.1, seed=4)
+    x = torch.from_numpy(ds.x).to(dev)
+    y = torch.from_numpy(ds.y).to(dev)
+    nc = M_VAR
+    out = {"workload": f"xor-pairs data N={N_OBJ} M={M_VAR} (5 planted pairs) + {nc} contrast variables, "
+                       f"D={DISC}, c={DIV + 1}, Holm at 0.05"}
+    for k in (2, 3):
+        r = mdfs.select(x, y, nc, k, DIV, DISC, RANGE, XI, seed=5)  # warm-up
+        stream = torch.cuda.current_stream(dev)
+        ts = []
+        for i in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = mdfs.select(x, y, nc, k, DIV, DISC, RANGE, XI, seed=5 + i)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        evals = math.comb(M_VAR + nc, k) * DISC
+        rel = r["relevant"].cpu().numpy()
+        out[f"k{k}"] = {"ms": ms, "evals_per_s": evals / (ms / 1e3), "selected": int(rel.sum()),
+                        "informative_selected": int(rel[ds.informative].sum()),
+                        "informative": int(len(ds.informative)), "ig_lim": r["ig_lim"], "n_eff": r["n_eff"]}
+    return out
 
 
 def serving_run(n_jobs: int, device: int):
@@ -404,6 +444,8 @@ def main():
                          "current kernel (profiles/launches_mdfs_scan_parity_N2000_M500_k2k3_D30.md)")
     ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=2)")
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving-mix run (0: skip)")
+    ap.add_argument("--select-reps", type=int, default=3,
+                    help="timed calls of the selection pipeline per k (0: skip)")
     ap.add_argument("--batched", action="store_true", help="run the batched k=2 workload instead")
     ap.add_argument("--batch-folds", type=int, default=16)
     ap.add_argument("--batch-perms", type=int, default=4)
@@ -412,6 +454,7 @@ def main():
     if args.small:
         _use_small_case()
         args.serving_jobs = 0
+        args.select_reps = 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
