@@ -211,7 +211,7 @@ def _cmi_sklearn(y, cols_s, col_i, c):
     return mi_si - mi_s
 
 
-@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("k", [2, 3, 4])
 def test_ig_limit_is_n_times_conditional_mutual_information(k):
     """xi -> 0: IG(i | S) -> N * I(y; x_i | S) = N [I(y; S, x_i) - I(y; S)]
     (scikit-learn's plug-in mutual information, nats)."""
@@ -226,20 +226,20 @@ def test_ig_limit_is_n_times_conditional_mutual_information(k):
         assert got == pytest.approx(want, abs=1e-6)
 
 
-@pytest.mark.parametrize("k,c,xi", [(2, 2, 0.25), (2, 3, 0.5), (3, 2, 0.25), (3, 4, 0.1)])
+@pytest.mark.parametrize("k,c,xi", [(2, 2, 0.25), (2, 3, 0.5), (3, 2, 0.25), (3, 4, 0.1), (4, 2, 0.25), (4, 3, 0.3)])
 def test_duplicate_variable_closed_form(k, c, xi):
     """If x_i duplicates a member of S, the extra voxels are all empty:
     IG(i|S) = -c^(k-1) (c-1) [f(b0+b1) - f(b0) - f(b1)],  f(x) = x ln x."""
     rng = np.random.default_rng(7)
-    N, M = 64, 4
+    N, M = 64, 5
     codes = rng.integers(0, c, (1, M, N)).astype(np.uint8)
-    codes[0, 3] = codes[0, 1]
+    codes[0, 4] = codes[0, 1]
     y = (rng.random(N) < 0.4).astype(np.uint8)
     b0, b1 = oracle.pseudocounts(y, xi)
     f = lambda t: t * math.log(t)
     want = -(c ** (k - 1)) * (c - 1) * (f(b0 + b1) - f(b0) - f(b1))
-    S = [1] if k == 2 else [1, 2]
-    assert oracle.ig_one(codes, y, c, xi, 0, 3, S) == pytest.approx(want, abs=1e-9)
+    S = [1, 2, 3][: k - 1]
+    assert oracle.ig_one(codes, y, c, xi, 0, 4, S) == pytest.approx(want, abs=1e-9)
 
 
 def test_null_scale_is_chi2():
@@ -255,6 +255,20 @@ def test_null_scale_is_chi2():
         vals.append(2 * oracle.ig_one(xs[r].reshape(1, 1, N), ys[r], c, 1e-9, 0, 0, []))
     vals = np.array(vals)
     df = 1
+    assert abs(vals.mean() - df) < 3 * math.sqrt(2 * df / reps)
+
+
+def test_null_scale_k4_c2():
+    """k = 4, c = 2: 2 IG of a null single tuple has mean df = (c-1) c^3 = 8."""
+    rng = np.random.default_rng(14)
+    N, c, reps = 5000, 2, 600
+    vals = []
+    for r in range(reps):
+        y = (rng.random(N) < 0.5).astype(np.uint8)
+        codes = rng.integers(0, c, (1, 4, N)).astype(np.uint8)
+        vals.append(2 * oracle.ig_one(codes, y, c, 1e-9, 0, 0, [1, 2, 3]))
+    df = (c - 1) * c ** 3
+    vals = np.array(vals)
     assert abs(vals.mean() - df) < 3 * math.sqrt(2 * df / reps)
 
 
@@ -274,7 +288,7 @@ def test_null_scale_k2_c3():
 # --------------------------------------------------------------------------
 # max / argmax over tuples and discretisations
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_max_ig_brute_force(k):
     """Exhaustive Python enumeration (sklearn CMI, xi -> 0) of the max over
     (discretisation, tuple) with the lowest-(d, S) tie-break."""
