@@ -6,7 +6,7 @@
  * where S runs over all (k-1)-subsets of the other variables and, in
  * addition, over several random discretisations of the data (section
  * "Algorithm and implementation").  This library computes that scan on one
- * GPU (sm_103a) for k = 1..3 and fits the chi^2 / extreme-value null that
+ * GPU (sm_103a) for k = 1..4 and fits the chi^2 / extreme-value null that
  * turns the result into p-values (section "Theory").
  *
  * Conventions shared by every entry point
@@ -32,7 +32,8 @@
  *   section "Algorithm and implementation": the same c for all variables);
  *   2 <= c <= N <= 32768; 1 <= discretizations <= 1024; k <= M <= 65535;
  *   for k = 2, discretizations * M < 2^32; for k = 3,
- *   discretizations * M * M < 2^32.
+ *   discretizations * M * M < 2^32; k = 4 needs divisions = 1 and
+ *   discretizations * M^3 < 2^32.
  */
 #ifndef MDFS_H
 #define MDFS_H
@@ -90,7 +91,7 @@ int mdfs_discretize(const mdfs_data* data, int divisions, int discretizations, d
  *     f(t) = t ln t,  b^d = pc_xi * N^d / min(N^0, N^1),
  * summed over all c^|S| voxels v, and IG(i | S) = SH(S) - SH(S + {i}).
  *
- * k:          1, 2 or 3.
+ * k:          1, 2, 3 or 4 (k = 4: divisions = 1).
  * pc_xi:      the pseudocount parameter xi, 0 < pc_xi < 1.
  * ig:         [M] float, the maximum per variable (may be slightly negative
  *             when the pseudocounts dominate).

@@ -103,6 +103,14 @@ cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, i
                             int n_items, const long long* tab, const int* cnt1, const long long* sh2,
                             const int* cnt2, unsigned long long* keys, cudaStream_t st);
 
+// Quadruple pass (k = 4, c = 2) over discretisations [d0, d0 + nd), using the
+// pair counts cnt2 of the same chunk.  items from build_k4_items:
+// (a | b << 16, c-tile << 16 | e-tile).
+void build_k4_items(int M, std::vector<int2>& items);
+cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
+                      const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
+                      cudaStream_t st);
+
 // Two-class k = 3 kernel on the tensor cores (tcgen05 kind::f8f6f4): one-hot
 // operands through TMA, counts in TMEM, fused entropy epilogue.  pairs must be
 // symmetric ([i][m] and [m][i] both written).  err: device flag set on a

@@ -559,13 +559,23 @@ __global__ void finalize_kernel(const unsigned long long* __restrict__ keys, int
     } else if (k == 2) {
         d = (int)(index / (uint32_t)M);
         if (tuples) tuples[v] = (int)(index % (uint32_t)M);
-    } else {
+    } else if (k == 3) {
         const uint32_t mm = (uint32_t)M * (uint32_t)M;
         d = (int)(index / mm);
         const uint32_t rem = index % mm;
         if (tuples) {
             tuples[2 * v] = (int)(rem / (uint32_t)M);
             tuples[2 * v + 1] = (int)(rem % (uint32_t)M);
+        }
+    } else {  // k = 4: ((d M + p1) M + p2) M + p3
+        const uint32_t p3 = index % (uint32_t)M, r2 = index / (uint32_t)M;
+        const uint32_t p2 = r2 % (uint32_t)M, r1 = r2 / (uint32_t)M;
+        const uint32_t p1 = r1 % (uint32_t)M;
+        d = (int)(r1 / (uint32_t)M);
+        if (tuples) {
+            tuples[3 * v] = (int)p1;
+            tuples[3 * v + 1] = (int)p2;
+            tuples[3 * v + 2] = (int)p3;
         }
     }
     if (disc) disc[v] = key ? d : -1;

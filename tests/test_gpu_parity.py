@@ -309,3 +309,58 @@ def test_repeatable_and_stream_ordered(cuda):
     s.synchronize()
     for u, v in zip(a, b):
         assert torch.equal(u, v)
+
+
+@pytest.mark.parametrize("M,N,D", [(4, 97, 1), (5, 300, 2), (14, 300, 2), (9, 2100, 1)])
+def test_k4_matches_oracle(cuda, M, N, D):
+    """k = 4 (two classes): every variable against the brute-force oracle; N up
+    to 2100 spans several 32-word chunks per class; M = 4 is one quadruple."""
+    rng = np.random.default_rng(M * 100 + N)
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[1] > 0) ^ (x[M - 1] > 0.2) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, D, 0.5, 17)
+    ref = oracle.max_ig(codes, y, 2, 4, 0.25)
+    g = _gpu_max_ig(cuda, x, y, 4, 1, D, 0.5, 0.25, 17)
+    _check(codes, y, 2, 4, 0.25, *g, ref, range(M))
+
+
+def test_k4_several_tiles_sampled(cuda):
+    """M = 70 spans three 32-wide c and e tiles; a sample of variables is checked
+    (each oracle row scans all C(69, 3) partner triples)."""
+    rng = np.random.default_rng(70)
+    M, N, D = 70, 200, 1
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[5] > 0) ^ (x[33] > 0) ^ (x[69] > 0)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, D, 0.5, 3)
+    rows = np.array([0, 5, 31, 32, 33, 40, 63, 64, 69], dtype=np.int32)
+    ref = oracle.max_ig(codes, y, 2, 4, 0.25, variables=rows)
+    g = _gpu_max_ig(cuda, x, y, 4, 1, D, 0.5, 0.25, 3)
+    _check(codes, y, 2, 4, 0.25, *g, ref, rows)
+
+
+def test_k4_four_way_parity_found(cuda):
+    """y = parity of four variables: each member's best partner triple is the
+    other three, and the four are the top four at k = 4."""
+    rng = np.random.default_rng(404)
+    M, N = 12, 3000
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    mem = [1, 4, 6, 10]
+    y = np.zeros(N, dtype=np.uint8)
+    for m in mem:
+        y ^= (x[m] > 0).astype(np.uint8)
+    ig, tu, di = _gpu_max_ig(cuda, x, y, 4, 1, 1, 0.0, 0.25, 9)
+    assert set(np.argsort(-ig)[:4].tolist()) == set(mem)
+    for m in mem:
+        assert sorted(tu[m].tolist()) == sorted(v for v in mem if v != m)
+
+
+def test_k4_errors(cuda):
+    from paper_1811_00631_gb300 import mdfs
+    x = np.random.default_rng(0).standard_normal((6, 50)).astype(np.float32)
+    y = (np.arange(50) % 2).astype(np.uint8)
+    with pytest.raises(mdfs.MdfsError):
+        mdfs.max_ig(x, y, 4, 2, 1)  # three classes: not supported at k = 4
+    xl = np.random.default_rng(1).standard_normal((1700, 8)).astype(np.float32)
+    yl = (np.arange(8) % 2).astype(np.uint8)
+    with pytest.raises(mdfs.MdfsError):
+        mdfs.max_ig(xl, yl, 4, 1, 1)  # 1700^3 >= 2^32: keys cannot index the triple
