@@ -295,6 +295,8 @@ def run_gpu(args, rank, world, local_rank):
         line["serving"] = serving_run(args.serving_jobs, local_rank)
     if args.select_reps > 0:
         line["select"] = select_run(args.select_reps, local_rank)
+    if args.k4 and DIV == 1 and math.comb(M_VAR, 3) * DISC * M_VAR < 2**32:
+        line["k4"] = k4_run(local_rank)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -344,6 +346,30 @@ def select_run(reps: int, device: int):
                         "informative_selected": int(rel[ds.informative].sum()),
                         "informative": int(len(ds.informative)), "ig_lim": r["ig_lim"], "n_eff": r["n_eff"]}
     return out
+
+
+def k4_run(device: int):
+    """One k = 4 scan of the bench data (2000 x 500, 30 discretisations, 2
+    classes): C(500, 4) x 30 = 7.7e10 quadruple x discretisation evaluations,
+    timed with CUDA events after a one-discretisation warm-up."""
+    import torch
+    from paper_1811_00631_gb300 import mdfs, synth
+    dev = torch.device("cuda", device)
+    ds = synth.madelon_like(M=M_VAR, seed=2)
+    x = torch.from_numpy(ds.x).to(dev)
+    y = torch.from_numpy(ds.y).to(dev)
+    mdfs.max_ig(x, y, 4, DIV, 1, RANGE, XI, 1)
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    mdfs.max_ig(x, y, 4, DIV, DISC, RANGE, XI, 5)
+    b.record(stream)
+    b.synchronize()
+    s = a.elapsed_time(b) / 1e3
+    evals = math.comb(M_VAR, 4) * DISC
+    return {"workload": f"madelon-shaped parity data N={N_OBJ} M={M_VAR}, k=4, D={DISC}, c={DIV + 1}",
+            "s": s, "evals_per_s": evals / s,
+            "paper_context": "Table 2 of the paper: 4D, 30 discretisations, Madelon 2000 x 500 on a Tesla K80: 456 s"}
 
 
 def serving_run(n_jobs: int, device: int):
@@ -444,6 +470,7 @@ def main():
                          "current kernel (profiles/launches_mdfs_scan_parity_N2000_M500_k2k3_D30.md)")
     ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=2)")
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving-mix run (0: skip)")
+    ap.add_argument("--k4", type=int, default=1, help="time one k = 4 scan of the bench data (0: skip)")
     ap.add_argument("--select-reps", type=int, default=3,
                     help="timed calls of the selection pipeline per k (0: skip)")
     ap.add_argument("--batched", action="store_true", help="run the batched k=2 workload instead")
@@ -455,6 +482,7 @@ def main():
         _use_small_case()
         args.serving_jobs = 0
         args.select_reps = 0
+        args.k4 = 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -29,7 +29,8 @@ namespace mdfs {
 
 namespace {
 
-constexpr int kRC = 2, kRE = 2, kTC = 16 * kRC, kTE = 16 * kRE, kWC = 32, kLD = kWC + 1;
+constexpr int kRC = 2, kRE = 2, kTC = 16 * kRC, kTE = 16 * kRE, kWC = 32;
+constexpr int kLD = kWC + 2;  // even row stride: 8-byte word-pair loads, rows 2 banks apart
 
 // In-place Moebius inversion over supersets of L bits: on entry n[T] is the
 // all-ones count of subset T, on exit n[O] the count of the voxel whose ones
@@ -60,8 +61,8 @@ __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__
                                                  const int2* __restrict__ items, const long long* __restrict__ tab,
                                                  const int* __restrict__ cnt1, const int* __restrict__ cnt2,
                                                  unsigned long long* __restrict__ keys) {
-    __shared__ uint32_t sa[kWC], sb[kWC], sab[kWC];
-    __shared__ uint32_t sabc[kTC][kLD], sac[kTC][kLD], sbc[kTC][kLD], se[kTE][kLD];
+    __shared__ __align__(8) uint32_t sa[kWC], sb[kWC], sab[kWC];
+    __shared__ __align__(8) uint32_t sabc[kTC][kLD], sac[kTC][kLD], sbc[kTC][kLD], se[kTE][kLD];
     __shared__ unsigned long long kc[kTC], ke[kTE], ka, kb;
 
     const int2 it = items[blockIdx.x];
@@ -114,23 +115,26 @@ __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__
                 se[r][w] = (w < nw && ve < M) ? pbase[(size_t)ve * g.Ws + w0 + w] : 0u;
             }
             __syncthreads();
-            for (int w = 0; w < nw; ++w) {
-                const uint32_t ab = sab[w];
-                uint32_t ev[kRE];
+            // two words per step (entries past nw are zero)
+            for (int w = 0; w < nw; w += 2) {
+                const uint2 ab = *reinterpret_cast<const uint2*>(&sab[w]);
+                uint2 ev[kRE];
 #pragma unroll
                 for (int re = 0; re < kRE; ++re) {
-                    ev[re] = se[te + 16 * re][w];
-                    xabe[cls][re] += __popc(ab & ev[re]);
+                    ev[re] = *reinterpret_cast<const uint2*>(&se[te + 16 * re][w]);
+                    xabe[cls][re] += __popc(ab.x & ev[re].x) + __popc(ab.y & ev[re].y);
                 }
 #pragma unroll
                 for (int rc = 0; rc < kRC; ++rc) {
-                    const uint32_t v3 = sabc[tc + 16 * rc][w], vac = sac[tc + 16 * rc][w], vbc = sbc[tc + 16 * rc][w];
-                    xabc[cls][rc] += __popc(v3);
+                    const uint2 v3 = *reinterpret_cast<const uint2*>(&sabc[tc + 16 * rc][w]);
+                    const uint2 vac = *reinterpret_cast<const uint2*>(&sac[tc + 16 * rc][w]);
+                    const uint2 vbc = *reinterpret_cast<const uint2*>(&sbc[tc + 16 * rc][w]);
+                    xabc[cls][rc] += __popc(v3.x) + __popc(v3.y);
 #pragma unroll
                     for (int re = 0; re < kRE; ++re) {
-                        x4[cls][rc][re] += __popc(v3 & ev[re]);
-                        xace[cls][rc][re] += __popc(vac & ev[re]);
-                        xbce[cls][rc][re] += __popc(vbc & ev[re]);
+                        x4[cls][rc][re] += __popc(v3.x & ev[re].x) + __popc(v3.y & ev[re].y);
+                        xace[cls][rc][re] += __popc(vac.x & ev[re].x) + __popc(vac.y & ev[re].y);
+                        xbce[cls][rc][re] += __popc(vbc.x & ev[re].x) + __popc(vbc.y & ev[re].y);
                     }
                 }
             }
