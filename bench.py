@@ -295,7 +295,7 @@ def run_gpu(args, rank, world, local_rank):
         line["serving"] = serving_run(args.serving_jobs, local_rank)
     if args.select_reps > 0:
         line["select"] = select_run(args.select_reps, local_rank)
-    if args.k4 and DIV == 1 and math.comb(M_VAR, 3) * DISC * M_VAR < 2**32:
+    if args.k4 and DIV == 1 and DISC * M_VAR ** 3 < 2**32:
         line["k4"] = k4_run(local_rank)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
