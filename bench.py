@@ -23,6 +23,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -69,7 +70,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples go to MDFS_BENCH_LOG_DIR when set, else to the system temp directory
+        log_dir = os.environ.get("MDFS_BENCH_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(log_dir, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
