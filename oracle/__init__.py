@@ -10,6 +10,8 @@ no code.  Every function restates the paper (arXiv 1811.00631):
 * ``sh`` / ``ig_one`` / ``max_ig`` -- Eq. (1), Eq. (3), Eqs. H, p and beta;
 * ``chi2_cdf`` / ``ig_lim`` -- the chi^2 / extreme-value significance fit of
   section "Theory";
+* ``interesting_tuples`` -- every (variable, tuple) reaching an IG threshold
+  (section "Examples");
 * ``shuffle_index`` / ``contrast`` / ``p_adjust`` / ``select`` -- contrast
   variables and the canonical selection pipeline of section "Canonical
   package usage" (contrasts, IG, fit on the contrasts, adjusted p-values,
@@ -210,6 +212,28 @@ def ig_lim(ig: np.ndarray, k: int, divisions: int, irrelevant_mask=None, alpha: 
     if rc != 0:
         raise ValueError(f"oracle_ig_lim failed ({rc})")
     return p, lim.value, neff.value
+
+
+def interesting_tuples(codes: np.ndarray, y: np.ndarray, c: int, k: int, xi: float, threshold: float):
+    """ComputeInterestingTuples (section "Examples"): every (variable v, partner
+    set S, |S| = k-1, v not in S) whose IG(v | S), maximised over the
+    discretisations, reaches ``threshold``; brute force in FP64 through
+    ``ig_one``.  Returns a list of (v, S tuple ascending, ig, d) sorted by
+    (v, S); d is the lowest discretisation reaching the maximum."""
+    import itertools
+    D, M, N = codes.shape
+    out = []
+    for v in range(M):
+        others = [m for m in range(M) if m != v]
+        for S in itertools.combinations(others, k - 1):
+            best, bd = -np.inf, -1
+            for d in range(D):
+                g = ig_one(codes, y, c, xi, d, v, list(S))
+                if g > best:
+                    best, bd = g, d
+            if best >= threshold:
+                out.append((v, tuple(S), best, bd))
+    return out
 
 
 def shuffle_index(i: int, n: int, stream: int, seed: int) -> int:

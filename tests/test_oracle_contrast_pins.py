@@ -143,3 +143,27 @@ def test_select_null_and_planted_signal():
     r = oracle.select(x, y, 24, 2, 1, 1, 0.0, 0.25, seed=7)
     assert r["relevant"][2] and r["relevant"][7]
     assert r["relevant"].sum() <= 3
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_interesting_tuples_agree_with_the_max(k):
+    """Every variable's IG^k_max record is interesting at a threshold just below
+    it, nothing is interesting above the global max, and the records at
+    threshold -inf are all (variable, tuple) pairs."""
+    rng = np.random.default_rng(50 + k)
+    M, N, D = 7, 150, 2
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[3] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, D, 0.5, seed=9)
+    ref = oracle.max_ig(codes, y, 2, k, 0.25)
+    allrec = oracle.interesting_tuples(codes, y, 2, k, 0.25, -np.inf)
+    assert len(allrec) == M * math.comb(M - 1, k - 1)
+    assert [r[:2] for r in allrec] == sorted(r[:2] for r in allrec)
+    for v in range(M):
+        mine = [r for r in allrec if r[0] == v]
+        best = max(mine, key=lambda r: r[2])
+        assert best[2] == pytest.approx(ref["ig"][v], abs=1e-12)
+    top = float(np.max(ref["ig"]))
+    assert oracle.interesting_tuples(codes, y, 2, k, 0.25, top + 1e-9) == []
+    recs = oracle.interesting_tuples(codes, y, 2, k, 0.25, top - 1e-9)
+    assert len(recs) >= 1 and all(r[2] >= top - 1e-9 for r in recs)
