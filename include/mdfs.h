@@ -52,6 +52,7 @@ extern "C" {
 #define MDFS_ENOMEM (-4)      /* device workspace allocation failed                   */
 #define MDFS_ECUDA (-5)       /* a CUDA runtime call or kernel launch failed          */
 #define MDFS_ETIMEOUT (-6)    /* reserved for bounded device-side waits               */
+#define MDFS_ETRUNCATED (-7)  /* more output records than the caller's capacity        */
 
 /* x element types */
 #define MDFS_F32 0
@@ -208,6 +209,27 @@ int mdfs_contrast(const mdfs_data* data, int n_contrast, uint64_t seed, void* x_
  * Errors: MDFS_EINVAL (arguments, unknown method), MDFS_ENOMEM, MDFS_ECUDA.
  */
 int mdfs_p_adjust(const double* p, int m, int method, double* adjusted, void* stream);
+
+/*
+ * Interesting tuples (section "Examples": the package's third entry point
+ * beside the max scan and the selection pipeline): every (variable v,
+ * partner set S) with |S| = k - 1, v not in S, whose IG(v | S) maximised
+ * over the discretisations reaches ig_threshold (nats).  Same data, k,
+ * divisions, discretizations, range, pc_xi and seed as mdfs_max_ig (k = 1..4;
+ * k = 4 with divisions = 1); the scan runs on the popcount kernels.
+ *
+ * Records are sorted by (v, S) ascending: var [n], tuples [n][k-1] (S
+ * ascending; NULL allowed for k = 1), ig [n] float, best_disc [n] (the lowest
+ * discretisation reaching the maximum; NULL allowed), all of at least
+ * `capacity` entries, host or device.  *count (host) receives n.
+ * capacity: 1 .. 2^22.
+ * Errors: those of mdfs_max_ig; MDFS_ETRUNCATED when more than capacity
+ * records reach the threshold (*count then holds their number, or a lower
+ * bound when the message says "at least"; no record is written).
+ */
+int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int discretizations, double range,
+                            double pc_xi, uint64_t seed, double ig_threshold, int capacity, int32_t* var,
+                            int32_t* tuples, float* ig, int32_t* best_disc, int64_t* count, void* stream);
 
 /*
  * The canonical selection pipeline (section "Canonical package usage"):

@@ -2,6 +2,8 @@
 // per-(device, stream) workspaces and the launch sequence of the scan.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -49,6 +51,7 @@ struct Workspace {
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
     Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
     Buffer items4;                                           // k = 4 work items
+    Buffer ekeys, evals, ecnt, erk, erv;                     // interesting-tuple table and its records
     int items4_M = -1, n_items4 = 0;
     int items3_M = -1, items3_c = -1, n_items3 = 0;
     int items2_M = -1, n_items2 = 0;
@@ -60,7 +63,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4};
+                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &ekeys, &evals, &ecnt, &erk, &erv};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -308,8 +311,11 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
 // keys (tensor-core and generic triple paths); the popcount pair path and k = 1
 // run whole on shard 0.  Merging the keys of all shards by maximum gives the
 // keys of the unsharded scan.
+// emit != NULL: interesting-tuple emission into that table; the scan then runs on
+// the popcount kernels (the tensor-core kernels do not emit).
 int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, int k, int divisions, int D, double range,
-              double pc_xi, uint64_t seed, bool* check_err, int shard = 0, int n_shards = 1) {
+              double pc_xi, uint64_t seed, bool* check_err, int shard = 0, int n_shards = 1,
+              const EmitTable* emit = nullptr) {
     cudaStream_t st = ws->stream;
     auto share = [&](int n, int* lo) {
         *lo = (int)((long long)n * shard / n_shards);
@@ -337,8 +343,9 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
-    const bool use_tc2 = (k == 2 && k2tc_supported(c) && k2tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
-    const bool use_tc3 = (k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
+    const EmitTable em = emit ? *emit : EmitTable();
+    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
+    const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     TcGeom tg = make_tc_geom(n0, n1);
     uint8_t* onehot = nullptr;
     if (use_tc2 || use_tc3) {
@@ -348,7 +355,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     MDFS_LAUNCH("discretize", st, launch_discretize(xd, dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g,
                                                     planes, nullptr, nullptr, onehot, tg, st));
     MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
-    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, (k == 1 && shard == 0) ? keys : nullptr, st));
+    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, (k == 1 && shard == 0) ? keys : nullptr, st,
+                                    k == 1 ? em : EmitTable()));
     if (use_tc2) {
         MDFS_ENSURE(ws, err, sizeof(int));
         MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
@@ -372,7 +380,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         *check_err = true;
     } else if (k == 2) {
         if (shard == 0)
-            MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st));
+            MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st,
+                                            nullptr, em));
     } else if (use_tc3) {
         // two classes: symmetric 8-byte pair records and the tcgen05 triple kernel
         const size_t per_disc = (size_t)M * M * sizeof(PairC);
@@ -445,7 +454,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             int lo = 0;
             const int cnt = share(ws->n_items, &lo);
             MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p + lo, cnt, tab,
-                                                  cnt1, (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st));
+                                                  cnt1, (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st,
+                                                  em));
         }
     } else if (k == 4) {
         // two classes: pair counts from the pair pass, then the quadruple kernel
@@ -475,7 +485,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             int lo = 0;
             const int cnt = share(ws->n_items4, &lo);
             MDFS_LAUNCH("k4", st, launch_k4(planes, g, M, d0, nn, (const int2*)ws->items4.p + lo, cnt, tab, cnt1,
-                                            (const int*)ws->cnt2.p, keys, st));
+                                            (const int*)ws->cnt2.p, keys, st, em));
         }
     }
 
@@ -1025,6 +1035,97 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
         (rc = emit(ws, (const int*)ws->srcb.p, contrast_src, (size_t)n_contrast)) ||
         (rc = emit(ws, (const double*)res, ig_lim, 1)) || (rc = emit(ws, (const double*)res + 1, n_eff, 1)))
         return rc;
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int discretizations, double range,
+                            double pc_xi, uint64_t seed, double ig_threshold, int capacity, int32_t* var,
+                            int32_t* tuples, float* ig, int32_t* best_disc, int64_t* count, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, true);
+    if (rc) return rc;
+    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    if (k < 1 || k > 4) return fail(MDFS_EINVAL, "k = %d outside [1, 4]", k);
+    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
+    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
+    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
+    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if (!(ig_threshold > -1e9 && ig_threshold < 1e9)) return fail(MDFS_EINVAL, "ig_threshold must be finite");
+    if (capacity < 1 || capacity > (1 << 22)) return fail(MDFS_EINVAL, "capacity = %d outside [1, 2^22]", capacity);
+    if (!var || !ig || !count || (k > 1 && !tuples))
+        return fail(MDFS_EINVAL, "var, ig, tuples (k > 1) and count must not be NULL");
+    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
+    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
+    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
+    if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    rc = stage_inputs(ws, data, true, &xd, &yd, &n1);
+    if (rc) return rc;
+    // room for twice the capacity: more records than capacity are detected, not lost silently
+    size_t tsize = 1024;
+    while (tsize < 2 * (size_t)capacity + 1) tsize <<= 1;
+    MDFS_ENSURE(ws, ekeys, tsize * sizeof(unsigned long long));
+    MDFS_ENSURE(ws, evals, tsize * sizeof(unsigned long long));
+    MDFS_ENSURE(ws, ecnt, 4 * sizeof(int));
+    MDFS_CUDA_TRY(cudaMemsetAsync(ws->ekeys.p, 0xFF, tsize * sizeof(unsigned long long), st));
+    MDFS_CUDA_TRY(cudaMemsetAsync(ws->evals.p, 0, tsize * sizeof(unsigned long long), st));
+    MDFS_CUDA_TRY(cudaMemsetAsync(ws->ecnt.p, 0, 4 * sizeof(int), st));
+    EmitTable em;
+    em.keys = (unsigned long long*)ws->ekeys.p;
+    em.vals = (unsigned long long*)ws->evals.p;
+    em.mask = (unsigned int)(tsize - 1);
+    em.thr_fx = llround(ig_threshold * kFxScale);
+    em.n_keys = (int*)ws->ecnt.p;
+    em.full = (int*)ws->ecnt.p + 1;
+    bool check_err = false;
+    rc = scan_core(ws, xd, data->dtype, N, M, n1, k, divisions, D, range, pc_xi, seed, &check_err, 0, 1, &em);
+    if (rc) return rc;
+    MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->ecnt.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    const int n = ws->host_stats[8], full = ws->host_stats[9];
+    *count = n;
+    if (full || n > capacity)
+        return fail(MDFS_ETRUNCATED, "%s%d records reach the threshold; capacity is %d", full ? "at least " : "", n,
+                    capacity);
+    int npad = 1;
+    while (npad < n) npad <<= 1;
+    MDFS_ENSURE(ws, erk, (size_t)npad * sizeof(unsigned long long));
+    MDFS_ENSURE(ws, erv, (size_t)npad * sizeof(unsigned long long));
+    const size_t nn = (size_t)std::max(n, 1);
+    Out<int32_t> ov, otu, odi;
+    Out<float> oig;
+    if ((rc = bind_out(ws, ws->tux, var, nn, &ov)) ||
+        (rc = bind_out(ws, ws->dix, k > 1 ? tuples : (int32_t*)nullptr, nn * (k > 1 ? k - 1 : 1), &otu)) ||
+        (rc = bind_out(ws, ws->relb, best_disc, nn, &odi)) || (rc = bind_out(ws, ws->igx, ig, nn, &oig)))
+        return rc;
+    int* disc_dev = odi.dev;  // the decoder always writes a discretisation
+    if (!disc_dev) {
+        MDFS_ENSURE(ws, adjb, nn * sizeof(int));
+        disc_dev = (int*)ws->adjb.p;
+    }
+    MDFS_LAUNCH("emit_collect", st,
+                launch_emit_collect(em, k, (unsigned long long*)ws->erk.p, (unsigned long long*)ws->erv.p,
+                                    (int*)ws->ecnt.p + 2, npad, ov.dev, otu.dev, oig.dev, disc_dev, n, st));
+    if (n > 0) {
+        ov.bytes = (size_t)n * sizeof(int32_t);
+        otu.bytes = (size_t)n * (k > 1 ? k - 1 : 1) * sizeof(int32_t);
+        odi.bytes = (size_t)n * sizeof(int32_t);
+        oig.bytes = (size_t)n * sizeof(float);
+        if ((rc = copy_back(ws, ov)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi)) ||
+            (rc = copy_back(ws, oig)))
+            return rc;
+    }
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     return MDFS_OK;
 }

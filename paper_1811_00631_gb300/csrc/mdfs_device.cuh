@@ -48,6 +48,40 @@ __device__ __forceinline__ unsigned long long pack_key(float ig, uint32_t index)
     return ((unsigned long long)float_order_bits(ig) << 32) | (unsigned long long)(~index);
 }
 
+// Hash-table key of an interesting (variable, partners) record; unused partners 0xFFFF.
+__device__ __forceinline__ unsigned long long emit_key(int v, int p1, int p2, int p3) {
+    return (unsigned long long)(uint16_t)v | ((unsigned long long)(uint16_t)p1 << 16) |
+           ((unsigned long long)(uint16_t)p2 << 32) | ((unsigned long long)(uint16_t)p3 << 48);
+}
+
+// SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014): a bijective
+// 64-bit mixer, used to spread record keys over the hash table.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Inserts (key, packed value) into an emission table (EmitTable of
+// mdfs_internal.cuh): linear probing from mix64(key), the slot claimed by
+// compare-and-swap, the value max-reduced.  The probe count is bounded by the
+// table size; a table with no free slot raises t.full.
+constexpr unsigned long long kEmptyEmitKey = ~0ull;
+template <class Table>
+__device__ __forceinline__ void emit_insert(const Table& t, unsigned long long key, unsigned long long val) {
+    unsigned int slot = (unsigned int)mix64(key) & t.mask;
+    for (unsigned int probe = 0; probe <= t.mask; ++probe) {
+        const unsigned long long prev = atomicCAS(t.keys + slot, kEmptyEmitKey, key);
+        if (prev == kEmptyEmitKey || prev == key) {
+            if (prev == kEmptyEmitKey) atomicAdd(t.n_keys, 1);
+            atomicMax(t.vals + slot, val);
+            return;
+        }
+        slot = (slot + 1) & t.mask;
+    }
+    atomicOr(t.full, 1);
+}
+
 // Fixed-point IG (multiples of 2^-32) to float with a single rounding.
 __device__ __forceinline__ float fx_to_float(long long v) {
     return __ll2float_rn(v) * 2.3283064365386963e-10f;  // exact scaling by 2^-32

@@ -53,6 +53,20 @@ struct __align__(8) PairC {
     int sh;
 };
 
+// Interesting-tuple emission (section "Examples"): every (variable, partner
+// set) whose IG reaches a threshold is inserted into an open-addressing hash
+// table keyed by v | p1 << 16 | p2 << 32 | p3 << 48 (unused partners 0xFFFF;
+// an all-ones key marks an empty slot), with the maximum over discretisations
+// kept as a packed key (IG, discretisation).  keys == NULL disables emission.
+struct EmitTable {
+    unsigned long long* keys = nullptr;  // [mask + 1]
+    unsigned long long* vals = nullptr;  // [mask + 1], 0 = none
+    unsigned int mask = 0;               // table size - 1, a power of two minus one
+    long long thr_fx = 0;                // threshold in multiples of 2^-32 (the IG fixed point)
+    int* n_keys = nullptr;               // distinct keys inserted
+    int* full = nullptr;                 // set when an insert found no free slot
+};
+
 // ---- launchers (all asynchronous on `st`) -----------------------------------
 // stats[0] = N1 (count of y == 1), stats[1] = number of y not in {0,1},
 // stats[2] = number of non-finite x.  perm = class-stable sample order.
@@ -80,7 +94,8 @@ cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int
 // Per (disc, variable): class counts of bins 1..c-1 -> cnt1 [D][M][c-1][2] i32,
 // SH1 [D][M] i64.  If keys != NULL also folds IG^1 = SH0 - SH1 into keys.
 cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, const long long* tab,
-                      int* cnt1, long long* sh1, unsigned long long* keys, cudaStream_t st);
+                      int* cnt1, long long* sh1, unsigned long long* keys, cudaStream_t st,
+                      EmitTable emit = EmitTable());
 
 // Pair pass over discretisations [d0, d0 + nd).  keys != NULL: fold the two IG
 // roles of every pair into keys (k = 2).  sh2/cnt2 != NULL: store the pair
@@ -91,7 +106,7 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd,
                       const long long* tab, const int* cnt1, const long long* sh1,
                       unsigned long long* keys, long long* sh2, int* cnt2, PairC* pairs2, int fbits,
-                      cudaStream_t st, const int* rank = nullptr);
+                      cudaStream_t st, const int* rank = nullptr, EmitTable emit = EmitTable());
 
 // Triple pass over discretisations [d0, d0 + nd), using the pair tables of the
 // same chunk.  Folds the three IG roles of every triple into keys.  items[j] =
@@ -101,7 +116,8 @@ int k3_tile_b(int c);
 int k3_tile_e(int c);
 cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, int d0, int nd, const int2* items,
                             int n_items, const long long* tab, const int* cnt1, const long long* sh2,
-                            const int* cnt2, unsigned long long* keys, cudaStream_t st);
+                            const int* cnt2, unsigned long long* keys, cudaStream_t st,
+                            EmitTable emit = EmitTable());
 
 // Quadruple pass (k = 4, c = 2) over discretisations [d0, d0 + nd), using the
 // pair counts cnt2 of the same chunk.  items from build_k4_items:
@@ -109,7 +125,14 @@ cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, i
 void build_k4_items(int M, std::vector<int2>& items);
 cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
-                      cudaStream_t st);
+                      cudaStream_t st, EmitTable emit = EmitTable());
+// Interesting tuples: gather the occupied slots of the table into recs_key /
+// recs_val (npad >= n entries, a power of two), sort them by (variable,
+// partners) in one CTA and decode into var [n], tuples [n][k-1] (NULL ok),
+// ig [n], disc [n].
+cudaError_t launch_emit_collect(EmitTable t, int k, unsigned long long* recs_key, unsigned long long* recs_val,
+                                int* counter, int npad, int* var, int* tuples, float* ig, int* disc, int n,
+                                cudaStream_t st);
 
 // Two-class k = 3 kernel on the tensor cores (tcgen05 kind::f8f6f4): one-hot
 // operands through TMA, counts in TMEM, fused entropy epilogue.  pairs must be

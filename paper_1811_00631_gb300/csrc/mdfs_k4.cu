@@ -60,7 +60,7 @@ __device__ __forceinline__ unsigned long long kmax(unsigned long long a, unsigne
 __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M, int d0,
                                                  const int2* __restrict__ items, const long long* __restrict__ tab,
                                                  const int* __restrict__ cnt1, const int* __restrict__ cnt2,
-                                                 unsigned long long* __restrict__ keys) {
+                                                 unsigned long long* __restrict__ keys, EmitTable emit) {
     __shared__ __align__(8) uint32_t sa[kWC], sb[kWC], sab[kWC];
     __shared__ __align__(8) uint32_t sabc[kTC][kLD], sac[kTC][kLD], sbc[kTC][kLD], se[kTE][kLD];
     __shared__ unsigned long long kc[kTC], ke[kTE], ka, kb;
@@ -249,6 +249,14 @@ __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__
             my_kb = kmax(my_kb, k_b);
             my_kc = kmax(my_kc, k_c);
             atomicMax(&ke[te + 16 * re], k_e);
+            if (emit.keys) {  // the four roles, partners ascending
+                const long long g4[4] = {sh_bce - sh4, sh_ace - sh4, sh_abe - sh4, sh_abc - sh4};
+                const unsigned long long ek[4] = {emit_key(a, b, c, e), emit_key(b, a, c, e), emit_key(c, a, b, e),
+                                                  emit_key(e, a, b, c)};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (g4[r] >= emit.thr_fx) emit_insert(emit, ek[r], pack_key(fx_to_float(g4[r]), (uint32_t)d));
+            }
         }
         if (my_kc) atomicMax(&kc[tc + 16 * rc], my_kc);
     }
@@ -292,10 +300,10 @@ void build_k4_items(int M, std::vector<int2>& items) {
 
 cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
-                      cudaStream_t st) {
+                      cudaStream_t st, EmitTable emit) {
     if (n_items == 0 || nd == 0) return cudaSuccess;
     if (nd > 65535) return cudaErrorInvalidValue;
-    k4_kernel<<<dim3(n_items, nd), 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, keys);
+    k4_kernel<<<dim3(n_items, nd), 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, keys, emit);
     return cudaGetLastError();
 }
 

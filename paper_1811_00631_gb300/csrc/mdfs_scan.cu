@@ -19,7 +19,8 @@ namespace mdfs {
 template <int C>
 __global__ void __launch_bounds__(256) k1_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M, int D,
                                                  const long long* __restrict__ tab, int* __restrict__ cnt1,
-                                                 long long* __restrict__ sh1, unsigned long long* __restrict__ keys) {
+                                                 long long* __restrict__ sh1, unsigned long long* __restrict__ keys,
+                                                 EmitTable emit) {
     constexpr int P = C - 1;
     const int lane = threadIdx.x & 31;
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -56,10 +57,12 @@ __global__ void __launch_bounds__(256) k1_kernel(const uint32_t* __restrict__ pl
         cnt1[((size_t)item * P + (a - 1)) * 2 + 0] = n0[a];
         cnt1[((size_t)item * P + (a - 1)) * 2 + 1] = n1[a];
     }
-    if (keys) {
+    if (keys || emit.keys) {
         const int d = item / M, v = item - d * M;
-        const long long sh0 = voxel_h(tab, np1, g.N0, g.N1);
-        atomicMax(keys + v, pack_key(fx_to_float(sh0 - sh), (uint32_t)d));
+        const long long ig = voxel_h(tab, np1, g.N0, g.N1) - sh;
+        if (keys) atomicMax(keys + v, pack_key(fx_to_float(ig), (uint32_t)d));
+        if (emit.keys && ig >= emit.thr_fx)
+            emit_insert(emit, emit_key(v, -1, -1, -1), pack_key(fx_to_float(ig), (uint32_t)d));
     }
 }
 
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(256) k2_kernel(const uint32_t* __restrict__ pl
                                                  const int* __restrict__ cnt1, const long long* __restrict__ sh1,
                                                  unsigned long long* __restrict__ keys, long long* __restrict__ sh2,
                                                  int* __restrict__ cnt2, PairC* __restrict__ pairs2, int fbits,
-                                                 const int* __restrict__ rank) {
+                                                 const int* __restrict__ rank, EmitTable emit) {
     constexpr int P = C - 1, TI = 32, WC = 32, LD = WC + 1;
     __shared__ uint32_t si[P][TI][LD];
     __shared__ uint32_t sm[P][TI][LD];
@@ -304,6 +307,11 @@ __global__ void __launch_bounds__(256) k2_kernel(const uint32_t* __restrict__ pl
                 atomicMax(&kmax[ty * 4 + r], pack_key(ig_i, (uint32_t)(d * M + m)));
                 atomicMax(&kmax[TI + tx], pack_key(ig_m, (uint32_t)(d * M + i)));
             }
+            if (emit.keys) {  // IG(i | m), IG(m | i)
+                const long long gi = __ldg(sh1 + (size_t)d * M + m) - sh, gm = __ldg(sh1 + (size_t)d * M + i) - sh;
+                if (gi >= emit.thr_fx) emit_insert(emit, emit_key(i, m, -1, -1), pack_key(fx_to_float(gi), (uint32_t)d));
+                if (gm >= emit.thr_fx) emit_insert(emit, emit_key(m, i, -1, -1), pack_key(fx_to_float(gm), (uint32_t)d));
+            }
             if (pairs2) {
                 // counts times 4 (byte offsets of the consuming table lookups)
                 const PairC rec{(uint32_t)(4 * X0[0][0]) | ((uint32_t)(4 * X1[0][0]) << 16), fx_narrow(sh, fbits)};
@@ -354,7 +362,8 @@ template <int C>
 __global__ void __launch_bounds__(256) k3_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M, int d0,
                                                  const int2* __restrict__ items, const long long* __restrict__ tab,
                                                  const int* __restrict__ cnt1, const long long* __restrict__ sh2,
-                                                 const int* __restrict__ cnt2, unsigned long long* __restrict__ keys) {
+                                                 const int* __restrict__ cnt2, unsigned long long* __restrict__ keys,
+                                                 EmitTable emit) {
     constexpr int P = C - 1, RB = K3Shape<C>::RB, RE = K3Shape<C>::RE;
     constexpr int TB = 16 * RB, TE = 16 * RE, WC = 32, LD = WC + 1;
     __shared__ uint32_t sa[P][WC];
@@ -527,6 +536,12 @@ __global__ void __launch_bounds__(256) k3_kernel(const uint32_t* __restrict__ pl
             my_ka = k_a > my_ka ? k_a : my_ka;
             my_kb = k_b > my_kb ? k_b : my_kb;
             atomicMax(&ke[te + 16 * re], k_e);
+            if (emit.keys) {  // IG(a | b,e), IG(b | a,e), IG(e | a,b)
+                const long long ga = __ldg(sh2 + pbe) - sh3, gb = __ldg(sh2 + pae) - sh3, ge = sh_ab - sh3;
+                if (ga >= emit.thr_fx) emit_insert(emit, emit_key(a, b, e, -1), pack_key(fx_to_float(ga), (uint32_t)d));
+                if (gb >= emit.thr_fx) emit_insert(emit, emit_key(b, a, e, -1), pack_key(fx_to_float(gb), (uint32_t)d));
+                if (ge >= emit.thr_fx) emit_insert(emit, emit_key(e, a, b, -1), pack_key(fx_to_float(ge), (uint32_t)d));
+            }
         }
         if (my_kb) atomicMax(&kb[tb + 16 * rb], my_kb);
     }
@@ -585,13 +600,13 @@ __global__ void finalize_kernel(const unsigned long long* __restrict__ keys, int
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, const long long* tab, int* cnt1,
-                      long long* sh1, unsigned long long* keys, cudaStream_t st) {
+                      long long* sh1, unsigned long long* keys, cudaStream_t st, EmitTable emit) {
     const int items = D * M;
     const int blocks = (items + 7) / 8;
     switch (c) {
-        case 2: k1_kernel<2><<<blocks, 256, 0, st>>>(planes, g, M, D, tab, cnt1, sh1, keys); break;
-        case 3: k1_kernel<3><<<blocks, 256, 0, st>>>(planes, g, M, D, tab, cnt1, sh1, keys); break;
-        case 4: k1_kernel<4><<<blocks, 256, 0, st>>>(planes, g, M, D, tab, cnt1, sh1, keys); break;
+        case 2: k1_kernel<2><<<blocks, 256, 0, st>>>(planes, g, M, D, tab, cnt1, sh1, keys, emit); break;
+        case 3: k1_kernel<3><<<blocks, 256, 0, st>>>(planes, g, M, D, tab, cnt1, sh1, keys, emit); break;
+        case 4: k1_kernel<4><<<blocks, 256, 0, st>>>(planes, g, M, D, tab, cnt1, sh1, keys, emit); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -599,18 +614,18 @@ cudaError_t launch_k1(const uint32_t* planes, PlaneGeom g, int M, int c, int D, 
 
 cudaError_t launch_k2(const uint32_t* planes, PlaneGeom g, int M, int c, int D, int d0, int nd, const long long* tab,
                       const int* cnt1, const long long* sh1, unsigned long long* keys, long long* sh2, int* cnt2,
-                      PairC* pairs2, int fbits, cudaStream_t st, const int* rank) {
+                      PairC* pairs2, int fbits, cudaStream_t st, const int* rank, EmitTable emit) {
     if (pairs2 && c != 2) return cudaErrorInvalidValue;
     (void)D;
     const int ntile = (M + 31) / 32;
     dim3 grid(ntile * (ntile + 1) / 2, nd);
     switch (c) {
         case 2: k2_kernel<2><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits,
-                                                    rank); break;
+                                                    rank, emit); break;
         case 3: k2_kernel<3><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits,
-                                                    rank); break;
+                                                    rank, emit); break;
         case 4: k2_kernel<4><<<grid, 256, 0, st>>>(planes, g, M, d0, ntile, tab, cnt1, sh1, keys, sh2, cnt2, pairs2, fbits,
-                                                    rank); break;
+                                                    rank, emit); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -621,13 +636,13 @@ int k3_tile_e(int c) { return c == 2 ? 64 : 32; }
 
 cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, int d0, int nd, const int2* items,
                             int n_items, const long long* tab, const int* cnt1, const long long* sh2, const int* cnt2,
-                            unsigned long long* keys, cudaStream_t st) {
+                            unsigned long long* keys, cudaStream_t st, EmitTable emit) {
     if (n_items == 0) return cudaSuccess;
     dim3 grid(n_items, nd);
     switch (c) {
-        case 2: k3_kernel<2><<<grid, 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, sh2, cnt2, keys); break;
-        case 3: k3_kernel<3><<<grid, 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, sh2, cnt2, keys); break;
-        case 4: k3_kernel<4><<<grid, 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, sh2, cnt2, keys); break;
+        case 2: k3_kernel<2><<<grid, 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, sh2, cnt2, keys, emit); break;
+        case 3: k3_kernel<3><<<grid, 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, sh2, cnt2, keys, emit); break;
+        case 4: k3_kernel<4><<<grid, 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, sh2, cnt2, keys, emit); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -28,12 +28,13 @@ _ERRORS = {
     -4: "MDFS_ENOMEM",
     -5: "MDFS_ECUDA",
     -6: "MDFS_ETIMEOUT",
+    -7: "MDFS_ETRUNCATED",
 }
 
 EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
             "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
-            "mdfs_contrast", "mdfs_p_adjust", "mdfs_select")
+            "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples")
 
 # p-value adjustment methods (MDFS_ADJUST_* of include/mdfs.h)
 P_ADJUST = {"none": 0, "bonferroni": 1, "holm": 2, "hochberg": 3, "BH": 4, "BY": 5}
@@ -93,6 +94,10 @@ def load(path: str = LIB_PATH):
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
                                     P, P, P, P, P, P, P, P, P, P]
         lib.mdfs_select.restype = ctypes.c_int
+        lib.mdfs_interesting_tuples.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_double,
+                                                ctypes.c_int, P, P, P, P, P, P]
+        lib.mdfs_interesting_tuples.restype = ctypes.c_int
         lib.mdfs_last_error.argtypes = []
         lib.mdfs_last_error.restype = ctypes.c_char_p
         lib.mdfs_release.argtypes = []
@@ -458,6 +463,43 @@ def select(x, y, n_contrast: int = None, k: int = 1, divisions: int = 1, discret
     del keep
     return {"ig": ig, "tuples": tu[:, : k - 1], "disc": di, "p_value": pv, "adjusted_p_value": adj,
             "relevant": rel != 0, "ig_lim": lim.value, "n_eff": neff.value, "contrast_src": src}
+
+
+def interesting_tuples(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range_: float = 0.0,
+                       pc_xi: float = 0.25, seed: int = 0, threshold: float = 0.0, capacity: int = 1 << 20):
+    """Every (variable, partner tuple) whose IG, maximised over discretisations,
+    reaches ``threshold`` (ComputeInterestingTuples, section "Examples").
+
+    Returns (var i32[n], tuples i32[n, k-1], ig f32[n], disc i32[n]) sorted by
+    (var, tuple), on the device of x (torch) or the host (numpy).  Raises
+    MdfsError MDFS_ETRUNCATED when more than ``capacity`` records qualify."""
+    lib = load()
+    data, keep = _data(x, y)
+    kk = max(k - 1, 1)
+    count = ctypes.c_int64(0)
+    if _is_cuda(x):
+        import torch
+        dev = x.device
+        var = torch.empty(capacity, dtype=torch.int32, device=dev)
+        tu = torch.empty((capacity, kk), dtype=torch.int32, device=dev)
+        ig = torch.empty(capacity, dtype=torch.float32, device=dev)
+        di = torch.empty(capacity, dtype=torch.int32, device=dev)
+        ptr = lambda a: ctypes.c_void_p(a.data_ptr())
+        stream = _stream_of(x)
+    else:
+        var = np.empty(capacity, dtype=np.int32)
+        tu = np.empty((capacity, kk), dtype=np.int32)
+        ig = np.empty(capacity, dtype=np.float32)
+        di = np.empty(capacity, dtype=np.int32)
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+        stream = None
+    rc = lib.mdfs_interesting_tuples(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
+                                     int(seed) & (2**64 - 1), float(threshold), int(capacity), ptr(var),
+                                     ptr(tu) if k > 1 else None, ptr(ig), ptr(di), ctypes.byref(count), stream)
+    _check(rc)
+    del keep
+    n = count.value
+    return var[:n], tu[:n, : k - 1], ig[:n], di[:n]
 
 
 def last_launch_count() -> int:

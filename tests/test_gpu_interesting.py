@@ -1,0 +1,103 @@
+"""GPU (sm_103a) parity of interesting tuples (ComputeInterestingTuples,
+section "Examples" of arXiv 1811.00631) against the FP64 CPU oracle, through
+the C ABI.
+
+Bars: every oracle record farther than the IG tolerance (1e-4 + 1e-5 |IG|)
+above the threshold is found, every GPU record not within that tolerance of
+the threshold is an oracle record, IG within the tolerance, and the
+discretisation equal unless another one reaches the maximum within it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+ATOL, RTOL = 1e-4, 1e-5
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_00631_gb300 import build
+    build.build()
+    return torch
+
+
+def _compare(codes, y, c, k, xi, thr, got, ref):
+    var, tu, ig, di = (np.asarray(a.cpu() if hasattr(a, "cpu") else a) for a in got)
+    g = {(int(v), tuple(int(p) for p in t)): (float(s), int(d)) for v, t, s, d in zip(var, tu, ig, di)}
+    o = {(v, S): (s, d) for v, S, s, d in ref}
+    # records sorted by (variable, tuple)
+    keys = [(int(v), tuple(int(p) for p in t)) for v, t in zip(var, tu)]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+    for key, (s, d) in o.items():
+        tol = ATOL + RTOL * abs(s)
+        if s >= thr + tol:
+            assert key in g, f"oracle record {key} ({s}) missing"
+    for key, (s, d) in g.items():
+        v, S = key
+        assert v not in S and list(S) == sorted(S) and len(S) == k - 1
+        if key in o:
+            so, do = o[key]
+            assert abs(s - so) <= ATOL + RTOL * abs(so), (key, s, so)
+            if d != do:  # another discretisation reaches the maximum within the tolerance
+                alt = oracle.ig_one(codes, y, c, xi, d, v, list(S))
+                assert abs(alt - so) <= 2 * (ATOL + RTOL * abs(so))
+        else:
+            assert s < thr + ATOL + RTOL * abs(s), f"GPU record {key} ({s}) not in the oracle"
+
+
+@pytest.mark.parametrize("k,div,M,N,D", [(1, 1, 40, 300, 3), (2, 1, 30, 400, 2), (2, 2, 20, 333, 2),
+                                         (3, 1, 14, 257, 2), (3, 2, 10, 200, 1), (4, 1, 10, 300, 2)])
+def test_interesting_tuples_match_oracle(cuda, k, div, M, N, D):
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(k * 100 + M)
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[1] > 0) ^ (x[M - 2] > 0.3) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    c = div + 1
+    codes = oracle.discretize(x, div, D, 0.5, 23)
+    # a threshold that keeps roughly the top tenth of all (variable, tuple) maxima
+    allrec = oracle.interesting_tuples(codes, y, c, k, 0.25, -np.inf)
+    thr = float(np.quantile([r[2] for r in allrec], 0.9))
+    ref = [r for r in allrec if r[2] >= thr]
+    got = mdfs.interesting_tuples(cuda.from_numpy(x).cuda(), cuda.from_numpy(y).cuda(), k, div, D, 0.5, 0.25, 23,
+                                  thr, capacity=4096)
+    _compare(codes, y, c, k, 0.25, thr, got, ref)
+    got_h = mdfs.interesting_tuples(x, y, k, div, D, 0.5, 0.25, 23, thr, capacity=4096)  # host pointers
+    for a, b in zip(got, got_h):
+        assert np.array_equal(np.asarray(a.cpu()), b)
+
+
+def test_interesting_tuples_all_records_and_max_agree(cuda):
+    """At a threshold below every IG, the records are all M * C(M-1, k-1)
+    (variable, tuple) pairs, and each variable's best record is its IG^k_max."""
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(5)
+    M, N, k = 12, 300, 3
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[5] > 0)).astype(np.uint8)
+    var, tu, ig, di = mdfs.interesting_tuples(x, y, k, 1, 2, 0.5, 0.25, 4, -1e6, capacity=M * math.comb(M - 1, k - 1))
+    assert len(var) == M * math.comb(M - 1, k - 1)
+    best, _, _ = mdfs.max_ig(x, y, k, 1, 2, 0.5, 0.25, 4)
+    for v in range(M):
+        mine = ig[var == v]
+        assert abs(float(mine.max()) - float(best[v])) <= ATOL + RTOL * abs(float(best[v]))
+
+
+def test_interesting_tuples_capacity(cuda):
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(6)
+    M, N = 20, 200
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = (rng.random(N) < 0.5).astype(np.uint8)
+    with pytest.raises(mdfs.MdfsError) as e:
+        mdfs.interesting_tuples(x, y, 2, 1, 1, 0.0, 0.25, 1, -1e6, capacity=10)  # 380 records qualify
+    assert e.value.code == -7 and "380" in str(e.value)
+    var, tu, ig, di = mdfs.interesting_tuples(x, y, 2, 1, 1, 0.0, 0.25, 1, 1e6, capacity=10)
+    assert len(var) == 0
