@@ -189,6 +189,91 @@ cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStrea
 // key = seed).  Positions p_j = floor(N S_j / S_c) with S_j = w_0 + .. + w_{j-1},
 // clamped to [j, N-c+j] and made strictly increasing.
 // ---------------------------------------------------------------------------
+// Ascending bitonic sort of s[0 .. npad) (npad a power of two) by the whole block,
+// every stage through shared memory.
+__device__ void bitonic_sort_smem(float* s, int npad, int tid, int nthreads) {
+    for (int k = 2; k <= npad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < npad; i += nthreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const float a = s[i], b = s[ixj];
+                    const bool ascending = (i & k) == 0;
+                    if ((a > b) == ascending) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The same network with 512 threads holding E = npad / 512 consecutive elements
+// each (indices E t + r): compare-exchange distances j < E stay in registers,
+// E <= j < 32 E pair lanes of one warp (shuffles), and only j >= 32 E goes
+// through shared memory with block barriers.  Leaves the sorted values in s.
+template <int E>
+__device__ void bitonic_sort_regs(float* s, int npad, int tid) {
+    float v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) v[r] = s[E * tid + r];
+    for (int k = 2; k <= npad; k <<= 1) {
+        int j = k >> 1;
+        if (j >= 32 * E) {  // long distances: shared memory
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < E; ++r) s[E * tid + r] = v[r];
+            __syncthreads();
+            for (; j >= 32 * E; j >>= 1) {
+                for (int i = tid; i < npad; i += 512) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const float a = s[i], b = s[ixj];
+                        if ((a > b) == ((i & k) == 0)) {
+                            s[i] = b;
+                            s[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < E; ++r) v[r] = s[E * tid + r];
+        }
+        for (; j >= E; j >>= 1) {  // partner in lane tid ^ (j / E), same r
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int i = E * tid + r;
+                const float p = __shfl_xor_sync(0xffffffffu, v[r], j / E);
+                const bool lower = (i & j) == 0, asc = (i & k) == 0;
+                v[r] = (lower == asc) ? fminf(v[r], p) : fmaxf(v[r], p);
+            }
+        }
+        // partner r ^ jj in this thread; jj runs over the compile-time distances
+        // below E that this k uses (jj <= j), so v stays in registers
+#pragma unroll
+        for (int jj = E / 2; jj > 0; jj >>= 1) {
+            if (jj > j) continue;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int rp = r ^ jj;
+                if (rp > r) {
+                    const bool asc = ((E * tid + r) & k) == 0;
+                    const float a = v[r], b = v[rp];
+                    v[r] = asc ? fminf(a, b) : fmaxf(a, b);
+                    v[rp] = asc ? fmaxf(a, b) : fminf(a, b);
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < E; ++r) s[E * tid + r] = v[r];
+    __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x, int N, int M, int c, int D,
                                                          uint32_t R, uint32_t key0, uint32_t key1, int npad,
@@ -205,21 +290,12 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
 
     for (int i = tid; i < npad; i += blockDim.x) s[i] = (i < N) ? (float)xv[i] : INFINITY;
     __syncthreads();
-    for (int k = 2; k <= npad; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < npad; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const float a = s[i], b = s[ixj];
-                    const bool ascending = (i & k) == 0;
-                    if ((a > b) == ascending) {
-                        s[i] = b;
-                        s[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+    switch (blockDim.x == 512 ? npad : 0) {
+        case 1024: bitonic_sort_regs<2>(s, npad, tid); break;
+        case 2048: bitonic_sort_regs<4>(s, npad, tid); break;
+        case 4096: bitonic_sort_regs<8>(s, npad, tid); break;
+        case 8192: bitonic_sort_regs<16>(s, npad, tid); break;
+        default: bitonic_sort_smem(s, npad, tid, blockDim.x); break;
     }
 
     const int cm1 = c - 1;

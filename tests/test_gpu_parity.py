@@ -72,6 +72,20 @@ def test_discretize_bit_exact(cuda):
         assert np.array_equal(got_h, want)
 
 
+@pytest.mark.parametrize("N", [600, 1000, 1025, 3000, 4096, 8000])
+def test_discretize_bit_exact_sort_sizes(cuda, N):
+    """Codes bit-exact for column lengths that use each in-register sort width
+    (padded lengths 1024 .. 8192) and its boundaries."""
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal((5, N)).astype(np.float32)
+    x[1] = np.round(x[1] * 4) / 4  # ties
+    for div in (1, 3):
+        want = oracle.discretize(x, div, 3, 0.7, seed=99)
+        got = mdfs.discretize(cuda.from_numpy(x).cuda(), div, 3, 0.7, seed=99).cpu().numpy()
+        assert np.array_equal(got, want)
+
+
 def test_discretize_int8_and_ties(cuda):
     from paper_1811_00631_gb300 import mdfs
     torch = cuda
