@@ -468,7 +468,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--smem-peak", type=float, default=32 * 152 * 2.07e9 / 1e12,
                     help="shared-memory lookup peak, 10^12 4-byte lookups/s")
-    ap.add_argument("--k3-traffic", type=float, default=91215616.0,
+    ap.add_argument("--k3-traffic", type=float, default=93863424.0,
                     help="DRAM bytes (read + write) per full-size k=3 launch from an ncu capture of the "
                          "current kernel (profiles/launches_mdfs_scan_parity_N2000_M500_k2k3_D30.md)")
     ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=2)")
