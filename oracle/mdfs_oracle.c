@@ -217,7 +217,7 @@ double oracle_ig_one(const uint8_t* codes, const uint8_t* y, int N, int M, int c
 
 /*
  * IG^k_max (Eq. 1) maximised over discretisations as well, for the variables
- * listed in vars (all M if vars == NULL), k = 1..4.
+ * listed in vars (all M if vars == NULL), k = 1..5.
  *   ig[n_vars]           FP64 maximum,
  *   tuples[n_vars][k-1]  partner set of the maximum (ascending), k >= 2,
  *   best_disc[n_vars]    discretisation of the maximum,
@@ -230,7 +230,7 @@ int oracle_max_ig(const uint8_t* codes, const uint8_t* y, int N, int M, int D, i
                   const int32_t* vars, int n_vars, double* ig, int32_t* tuples, int32_t* best_disc,
                   double* second)
 {
-    if (k < 1 || k > 4 || M < k) return -1;
+    if (k < 1 || k > 5 || M < k) return -1;
     if (vars == NULL) n_vars = M;
     double b0, b1;
     oracle_pseudocounts(y, N, xi, &b0, &b1);
@@ -238,7 +238,7 @@ int oracle_max_ig(const uint8_t* codes, const uint8_t* y, int N, int M, int D, i
     for (int t = 0; t < n_vars; ++t) {
         const int i = vars ? vars[t] : t;
         double best = -INFINITY, runner = -INFINITY;
-        int32_t bs[3] = {-1, -1, -1};
+        int32_t bs[4] = {-1, -1, -1, -1};
         int32_t bd = -1;
         for (int d = 0; d < D; ++d) {
             const uint8_t* ci = codes + ((size_t)d * M + i) * N;
@@ -271,7 +271,7 @@ int oracle_max_ig(const uint8_t* codes, const uint8_t* y, int N, int M, int D, i
                         else if (g > runner) runner = g;
                     }
                 }
-            } else {
+            } else if (k == 4) {
                 for (int m1 = 0; m1 < M; ++m1) {
                     if (m1 == i) continue;
                     const uint8_t* c1 = codes + ((size_t)d * M + m1) * N;
@@ -286,6 +286,30 @@ int oracle_max_ig(const uint8_t* codes, const uint8_t* y, int N, int M, int D, i
                             double g = oracle_sh(cs, 3, y, N, c, b0, b1) - oracle_sh(csi, 4, y, N, c, b0, b1);
                             if (g > best) { runner = best; best = g; bd = d; bs[0] = m1; bs[1] = m2; bs[2] = m3; }
                             else if (g > runner) runner = g;
+                        }
+                    }
+                }
+            } else {
+                for (int m1 = 0; m1 < M; ++m1) {
+                    if (m1 == i) continue;
+                    const uint8_t* c1 = codes + ((size_t)d * M + m1) * N;
+                    for (int m2 = m1 + 1; m2 < M; ++m2) {
+                        if (m2 == i) continue;
+                        const uint8_t* c2 = codes + ((size_t)d * M + m2) * N;
+                        for (int m3 = m2 + 1; m3 < M; ++m3) {
+                            if (m3 == i) continue;
+                            const uint8_t* c3 = codes + ((size_t)d * M + m3) * N;
+                            for (int m4 = m3 + 1; m4 < M; ++m4) {
+                                if (m4 == i) continue;
+                                const uint8_t* c4 = codes + ((size_t)d * M + m4) * N;
+                                const uint8_t* cs[4] = {c1, c2, c3, c4};
+                                const uint8_t* csi[5] = {c1, c2, c3, c4, ci};
+                                double g = oracle_sh(cs, 4, y, N, c, b0, b1) - oracle_sh(csi, 5, y, N, c, b0, b1);
+                                if (g > best) {
+                                    runner = best; best = g; bd = d;
+                                    bs[0] = m1; bs[1] = m2; bs[2] = m3; bs[3] = m4;
+                                } else if (g > runner) runner = g;
+                            }
                         }
                     }
                 }

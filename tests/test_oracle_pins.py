@@ -211,7 +211,7 @@ def _cmi_sklearn(y, cols_s, col_i, c):
     return mi_si - mi_s
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_ig_limit_is_n_times_conditional_mutual_information(k):
     """xi -> 0: IG(i | S) -> N * I(y; x_i | S) = N [I(y; S, x_i) - I(y; S)]
     (scikit-learn's plug-in mutual information, nats)."""
@@ -226,19 +226,20 @@ def test_ig_limit_is_n_times_conditional_mutual_information(k):
         assert got == pytest.approx(want, abs=1e-6)
 
 
-@pytest.mark.parametrize("k,c,xi", [(2, 2, 0.25), (2, 3, 0.5), (3, 2, 0.25), (3, 4, 0.1), (4, 2, 0.25), (4, 3, 0.3)])
+@pytest.mark.parametrize("k,c,xi", [(2, 2, 0.25), (2, 3, 0.5), (3, 2, 0.25), (3, 4, 0.1), (4, 2, 0.25), (4, 3, 0.3),
+                                    (5, 2, 0.25), (5, 3, 0.2)])
 def test_duplicate_variable_closed_form(k, c, xi):
     """If x_i duplicates a member of S, the extra voxels are all empty:
     IG(i|S) = -c^(k-1) (c-1) [f(b0+b1) - f(b0) - f(b1)],  f(x) = x ln x."""
     rng = np.random.default_rng(7)
-    N, M = 64, 5
+    N, M = 64, 6
     codes = rng.integers(0, c, (1, M, N)).astype(np.uint8)
     codes[0, 4] = codes[0, 1]
     y = (rng.random(N) < 0.4).astype(np.uint8)
     b0, b1 = oracle.pseudocounts(y, xi)
     f = lambda t: t * math.log(t)
     want = -(c ** (k - 1)) * (c - 1) * (f(b0 + b1) - f(b0) - f(b1))
-    S = [1, 2, 3][: k - 1]
+    S = [1, 2, 3, 5][: k - 1]
     assert oracle.ig_one(codes, y, c, xi, 0, 4, S) == pytest.approx(want, abs=1e-9)
 
 
@@ -272,6 +273,20 @@ def test_null_scale_k4_c2():
     assert abs(vals.mean() - df) < 3 * math.sqrt(2 * df / reps)
 
 
+def test_null_scale_k5_c2():
+    """k = 5, c = 2: 2 IG of a null single tuple has mean df = (c-1) c^4 = 16."""
+    rng = np.random.default_rng(15)
+    N, c, reps = 5000, 2, 400
+    vals = []
+    for r in range(reps):
+        y = (rng.random(N) < 0.5).astype(np.uint8)
+        codes = rng.integers(0, c, (1, 5, N)).astype(np.uint8)
+        vals.append(2 * oracle.ig_one(codes, y, c, 1e-9, 0, 0, [1, 2, 3, 4]))
+    df = (c - 1) * c ** 4
+    vals = np.array(vals)
+    assert abs(vals.mean() - df) < 3 * math.sqrt(2 * df / reps)
+
+
 def test_null_scale_k2_c3():
     rng = np.random.default_rng(13)
     N, c, reps = 5000, 3, 600
@@ -288,7 +303,7 @@ def test_null_scale_k2_c3():
 # --------------------------------------------------------------------------
 # max / argmax over tuples and discretisations
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_max_ig_brute_force(k):
     """Exhaustive Python enumeration (sklearn CMI, xi -> 0) of the max over
     (discretisation, tuple) with the lowest-(d, S) tie-break."""
@@ -327,6 +342,24 @@ def test_xor_pair_invisible_in_1d_found_in_2d():
     rank1 = np.argsort(np.argsort(-r1["ig"]))
     assert rank1[0] > 5 and rank1[1] > 5
     assert r2["ig"][0] > 10 * np.median(r2["ig"])
+
+
+def test_five_way_parity_needs_k5():
+    """y is the parity of five variables: every proper subset of them is
+    independent of y, so IG stays at the noise level up to k = 4 and jumps
+    at k = 5, where each member's argmax partners are the other four."""
+    rng = np.random.default_rng(55)
+    N, M = 400, 7
+    codes = rng.integers(0, 2, (1, M, N)).astype(np.uint8)
+    members = [0, 2, 3, 5, 6]
+    y = (np.bitwise_xor.reduce(codes[0, members], axis=0) ^ (rng.random(N) < 0.05)).astype(np.uint8)
+    r4 = oracle.max_ig(codes, y, 2, 4, 0.25)
+    r5 = oracle.max_ig(codes, y, 2, 5, 0.25)
+    assert r4["ig"].max() < 20.0
+    for v in members:
+        assert r5["ig"][v] > 150.0
+        assert sorted(r5["tuples"][v].tolist()) == [m for m in members if m != v]
+    assert r5["ig"][1] < 20.0 and r5["ig"][4] < 20.0
 
 
 # --------------------------------------------------------------------------
