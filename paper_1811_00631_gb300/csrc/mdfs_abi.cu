@@ -51,8 +51,10 @@ struct Workspace {
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
     Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
     Buffer items4;                                           // k = 4 work items
+    Buffer items5;                                           // k = 5 work items
     Buffer ekeys, evals, ecnt, erk, erv;                     // interesting-tuple table and its records
     int items4_M = -1, n_items4 = 0;
+    int items5_M = -1, n_items5 = 0;
     int items3_M = -1, items3_c = -1, n_items3 = 0;
     int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
@@ -63,7 +65,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &ekeys, &evals, &ecnt, &erk, &erv};
+                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &ekeys, &evals, &ecnt, &erk, &erv};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -195,6 +197,18 @@ cudaEvent_t prof_event() {
         if (!(ws)->ensure((ws)->buf, (bytes)))                                                      \
             return fail(MDFS_ENOMEM, "device allocation of %zu bytes failed", (size_t)(bytes));      \
     } while (0)
+
+// k = 5 limits: two classes per variable, class sizes that fit the packed
+// 16-bit counters, and argmax indices d C(M,4) + rank that fit 32 bits.
+int check_k5(int M, int c, int D, int N) {
+    if (c != 2) return fail(MDFS_EINVAL, "k = 5 supports two classes per variable (divisions = 1)");
+    if (N > 65535) return fail(MDFS_EINVAL, "k = 5 supports N up to 65535 samples");
+    const unsigned long long m = (unsigned long long)M;
+    const unsigned long long k4 = m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4;
+    if ((unsigned long long)D * k4 >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * C(M, 4) must stay below 2^32 for k = 5");
+    return MDFS_OK;
+}
 
 int check_data(const mdfs_data* data, bool need_y) {
     if (!data) return fail(MDFS_EINVAL, "data is NULL");
@@ -487,6 +501,36 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             MDFS_LAUNCH("k4", st, launch_k4(planes, g, M, d0, nn, (const int2*)ws->items4.p + lo, cnt, tab, cnt1,
                                             (const int*)ws->cnt2.p, keys, st, em));
         }
+    } else if (k == 5) {
+        // two classes: pair counts from the pair pass, then the quintuple kernel
+        const size_t per_disc = (size_t)M * M * (sizeof(long long) + 2 * sizeof(int));
+        size_t budget = (size_t)4 << 30;
+        if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
+        int nd = (int)(budget / per_disc);
+        if (nd < 1) nd = 1;
+        if (nd > D) nd = D;
+        if (nd > 65535) nd = 65535;
+        MDFS_ENSURE(ws, sh2, (size_t)nd * M * M * sizeof(long long));
+        MDFS_ENSURE(ws, cnt2, (size_t)nd * M * M * 2 * sizeof(int));
+        if (ws->items5_M != M) {
+            std::vector<int2> items;
+            build_k5_items(M, items);
+            MDFS_ENSURE(ws, items5, std::max<size_t>(items.size(), 1) * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items5.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items5_M = M;
+            ws->n_items5 = (int)items.size();
+        }
+        for (int d0 = 0; d0 < D; d0 += nd) {
+            const int nn = std::min(nd, D - d0);
+            MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
+                                                   (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
+            int lo = 0;
+            const int cnt = share(ws->n_items5, &lo);
+            MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
+                                            (const int*)ws->cnt2.p, keys, st));
+        }
     }
 
     return MDFS_OK;
@@ -620,7 +664,7 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     int rc = check_data(data, true);
     if (rc) return rc;
     const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
-    if (k < 1 || k > 4) return fail(MDFS_EINVAL, "k = %d outside [1, 4]", k);
+    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
     if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
     if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
     if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
@@ -634,6 +678,7 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
     if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
+    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
 
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
@@ -679,7 +724,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     if (rc) return rc;
     const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
     if (n_jobs < 1) return fail(MDFS_EINVAL, "n_jobs = %d < 1", n_jobs);
-    if (k < 1 || k > 4) return fail(MDFS_EINVAL, "k = %d outside [1, 4]", k);
+    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
     if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
     if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
     if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
@@ -693,6 +738,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
     if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
+    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
 
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
@@ -767,7 +813,7 @@ int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretiz
     if (rc) return rc;
     const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
     if (n_shards < 1 || shard < 0 || shard >= n_shards) return fail(MDFS_EINVAL, "shard %d of %d", shard, n_shards);
-    if (k < 1 || k > 4) return fail(MDFS_EINVAL, "k = %d outside [1, 4]", k);
+    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
     if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
     if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
     if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
@@ -781,6 +827,7 @@ int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretiz
     if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
     if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
+    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -807,7 +854,7 @@ int mdfs_keys_decode(const uint64_t* keys, int M, int k, float* ig, int32_t* tup
     g_err.clear();
     g_launches = 0;
     if (!keys || !ig) return fail(MDFS_EINVAL, "keys and ig must not be NULL");
-    if (M < 1 || M > 65535 || k < 1 || k > 4) return fail(MDFS_EINVAL, "M or k out of range");
+    if (M < 1 || M > 65535 || k < 1 || k > 5) return fail(MDFS_EINVAL, "M or k out of range");
     int rc = 0;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
@@ -839,7 +886,7 @@ int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretization
     (void)discretizations;
     if (!ig || !p_values) return fail(MDFS_EINVAL, "ig and p_values must not be NULL");
     if (M < 1) return fail(MDFS_EINVAL, "M = %d < 1", M);
-    if (k < 1 || k > 4) return fail(MDFS_EINVAL, "k = %d outside [1, 4]", k);
+    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
     const int c = divisions + 1;
     if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(MDFS_EINVAL, "alpha must lie in (0, 1)");
@@ -956,7 +1003,7 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
     const int Mx = M + n_contrast;
     if (n_contrast < 1 || Mx > 65535)
         return fail(MDFS_EINVAL, "n_contrast = %d: need n_contrast >= 1 and M + n_contrast <= 65535", n_contrast);
-    if (k < 1 || k > 4) return fail(MDFS_EINVAL, "k = %d outside [1, 4]", k);
+    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
     if (Mx < k) return fail(MDFS_EINVAL, "M + n_contrast = %d smaller than k = %d", Mx, k);
     if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
     if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
@@ -974,6 +1021,7 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
     if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
     if (k == 4 && (unsigned long long)D * Mx * Mx * Mx >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * (M + n_contrast)^3 must stay below 2^32 for k = 4");
+    if (k == 5 && (rc = check_k5(Mx, c, D, N))) return rc;
     int df = c - 1;
     for (int j = 1; j < k; ++j) df *= c;
 
@@ -1047,7 +1095,7 @@ int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int dis
     int rc = check_data(data, true);
     if (rc) return rc;
     const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
-    if (k < 1 || k > 4) return fail(MDFS_EINVAL, "k = %d outside [1, 4]", k);
+    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
     if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
     if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
     if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
@@ -1064,6 +1112,7 @@ int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int dis
     if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
     if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
+    if (k == 5) return fail(MDFS_EINVAL, "interesting tuples support k up to 4");
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;

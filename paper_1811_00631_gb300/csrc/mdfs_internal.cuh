@@ -126,6 +126,14 @@ void build_k4_items(int M, std::vector<int2>& items);
 cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
                       cudaStream_t st, EmitTable emit = EmitTable());
+// Quintuple pass (k = 5, c = 2) over discretisations [d0, d0 + nd), using the
+// pair counts cnt2 of the same chunk.  items from build_k5_items:
+// (b | c << 16, e-tile << 16 | f-tile); keys index d C(M,4) + lexicographic
+// rank of the partner set.
+void build_k5_items(int M, std::vector<int2>& items);
+cudaError_t launch_k5(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
+                      const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
+                      cudaStream_t st);
 // Interesting tuples: gather the occupied slots of the table into recs_key /
 // recs_val (npad >= n entries, a power of two), sort them by (variable,
 // partners) in one CTA and decode into var [n], tuples [n][k-1] (NULL ok),

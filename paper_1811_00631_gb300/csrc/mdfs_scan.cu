@@ -582,6 +582,30 @@ __global__ void finalize_kernel(const unsigned long long* __restrict__ keys, int
             tuples[2 * v] = (int)(rem / (uint32_t)M);
             tuples[2 * v + 1] = (int)(rem % (uint32_t)M);
         }
+    } else if (k == 5) {
+        // index = d C(M,4) + rho, rho = C(M,4) - 1 - R and
+        // R = C(t1,4) + C(t2,3) + C(t3,2) + C(t4,1), t_j = M - 1 - p_j
+        const unsigned long long m = (unsigned long long)M;
+        const unsigned long long k4 = m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4;
+        d = (int)(index / k4);
+        unsigned long long R = k4 - 1ull - (index % k4);
+        int p[4];
+        unsigned long long t = m;  // t_j strictly decreasing
+        for (int j = 0; j < 4; ++j) {
+            const int r = 4 - j;  // C(t, r)
+            auto binom = [r](unsigned long long x) {
+                unsigned long long v = 1;
+                for (int i = 0; i < r; ++i) v = v * (x - i) / (i + 1);
+                return x < (unsigned long long)r ? 0ull : v;
+            };
+            unsigned long long x = t - 1;
+            while (binom(x) > R) --x;
+            R -= binom(x);
+            p[j] = (int)(m - 1 - x);
+            t = x;
+        }
+        if (tuples)
+            for (int j = 0; j < 4; ++j) tuples[4 * v + j] = p[j];
     } else {  // k = 4: ((d M + p1) M + p2) M + p3
         const uint32_t p3 = index % (uint32_t)M, r2 = index / (uint32_t)M;
         const uint32_t p2 = r2 % (uint32_t)M, r1 = r2 / (uint32_t)M;

@@ -55,8 +55,8 @@ def test_argument_errors_need_no_gpu(lib):
     y = np.zeros(10, dtype=np.uint8)
     d = mdfs._Data(0, x.ctypes.data, y.ctypes.data, 10, 4)
     ig = np.zeros(4, dtype=np.float32)
-    rc = lib.mdfs_max_ig(ctypes.byref(d), 5, 1, 1, 0.0, 0.25, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
-    assert rc == -1 and b"k = 5" in lib.mdfs_last_error()
+    rc = lib.mdfs_max_ig(ctypes.byref(d), 6, 1, 1, 0.0, 0.25, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
+    assert rc == -1 and b"k = 6" in lib.mdfs_last_error()
     rc = lib.mdfs_max_ig(ctypes.byref(d), 2, 1, 1, 0.0, 1.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
     assert rc == -1 and b"pc_xi" in lib.mdfs_last_error()
     rc = lib.mdfs_max_ig(ctypes.byref(d), 2, 9, 1, 0.0, 0.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)

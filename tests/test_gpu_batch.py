@@ -75,7 +75,7 @@ def test_batch_rejects_bad_indices(cuda):
 
 
 @pytest.mark.parametrize("k,div,M,N", [(2, 1, 300, 500), (2, 2, 90, 400), (3, 1, 160, 300), (3, 2, 40, 200),
-                                      (1, 1, 50, 200), (4, 1, 60, 300)])
+                                      (1, 1, 50, 200), (4, 1, 60, 300), (5, 1, 40, 300)])
 def test_sharded_scan_merges_to_the_unsharded_result(cuda, k, div, M, N):
     """Three shards scanned one after another on one GPU, merged by unsigned
     maximum, decode to exactly the result of the unsharded scan."""

@@ -1,0 +1,88 @@
+"""GPU (sm_103a) parity of the k = 5 scan (two classes per variable) against
+the FP64 CPU oracle, through the C ABI.  Same bars as the other scans: IG
+within 1e-4 absolute + 1e-5 relative, argmax partner quadruple and
+discretisation equal unless the GPU's choice is an equally good maximiser."""
+import numpy as np
+import pytest
+
+import oracle
+
+from test_gpu_parity import _check, _gpu_max_ig
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_00631_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.mark.parametrize("M,N,D", [(5, 97, 1), (7, 300, 2), (12, 300, 2), (9, 4500, 1), (6, 40, 3)])
+def test_k5_matches_oracle(cuda, M, N, D):
+    """Every variable against the brute-force oracle.  M = 5 is one quintuple;
+    N = 4500 needs two staged chunks of 128 words; N = 40 leaves most of a
+    32-sample word empty."""
+    rng = np.random.default_rng(M * 1000 + N)
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[2] > 0) ^ (x[M - 1] > 0.3) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, D, 0.5, 23)
+    ref = oracle.max_ig(codes, y, 2, 5, 0.25)
+    g = _gpu_max_ig(cuda, x, y, 5, 1, D, 0.5, 0.25, 23)
+    _check(codes, y, 2, 5, 0.25, *g, ref, range(M))
+    gh = _gpu_max_ig(cuda, x, y, 5, 1, D, 0.5, 0.25, 23, host=True)
+    for a, b in zip(g, gh):
+        assert np.array_equal(a, b)
+
+
+def test_k5_several_tiles_sampled(cuda):
+    """M = 72: e and f span several 32-wide tiles (and the f-tile boundary
+    above the diagonal tile); a sample of variables is checked against the
+    oracle, each row scanning all C(71, 4) partner quadruples."""
+    rng = np.random.default_rng(72)
+    M, N, D = 72, 96, 1
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[3] > 0) ^ (x[36] > 0) ^ (x[71] > 0) ^ (rng.random(N) < 0.05)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, D, 0.5, 5)
+    rows = np.array([0, 3, 34, 36, 67, 70, 71], dtype=np.int32)
+    ref = oracle.max_ig(codes, y, 2, 5, 0.25, variables=rows)
+    g = _gpu_max_ig(cuda, x, y, 5, 1, D, 0.5, 0.25, 5)
+    _check(codes, y, 2, 5, 0.25, *g, ref, rows)
+
+
+def test_k5_five_way_parity_found(cuda):
+    """y = parity of five variables: invisible to every proper subset, so the
+    five are the top five at k = 5 and each one's partners are the other four."""
+    rng = np.random.default_rng(505)
+    M, N = 14, 4000
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    mem = [0, 3, 7, 8, 13]
+    y = np.zeros(N, dtype=np.uint8)
+    for m in mem:
+        y ^= (x[m] > 0).astype(np.uint8)
+    ig, tu, di = _gpu_max_ig(cuda, x, y, 5, 1, 1, 0.0, 0.25, 9)
+    assert set(np.argsort(-ig)[:5].tolist()) == set(mem)
+    for m in mem:
+        assert tu[m].tolist() == [v for v in mem if v != m]
+    ig4, _, _ = _gpu_max_ig(cuda, x, y, 4, 1, 1, 0.0, 0.25, 9)
+    assert ig4.max() < 0.02 * ig[mem].min()
+
+
+def test_k5_errors(cuda):
+    from paper_1811_00631_gb300 import mdfs
+    x = np.random.default_rng(0).standard_normal((7, 50)).astype(np.float32)
+    y = (np.arange(50) % 2).astype(np.uint8)
+    with pytest.raises(mdfs.MdfsError):
+        mdfs.max_ig(x, y, 5, 2, 1)  # three classes: not supported at k = 5
+    with pytest.raises(mdfs.MdfsError):
+        mdfs.max_ig(x[:4], y, 5, 1, 1)  # fewer variables than k
+    with pytest.raises(mdfs.MdfsError):
+        mdfs.interesting_tuples(x, y, 5, 1, 1)  # no room for four partners in a record
+    xl = np.random.default_rng(1).standard_normal((600, 8)).astype(np.float32)
+    yl = (np.arange(8) % 2).astype(np.uint8)
+    with pytest.raises(mdfs.MdfsError):
+        mdfs.max_ig(xl, yl, 5, 1, 1)  # C(600, 4) >= 2^32: keys cannot index the quadruple
