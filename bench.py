@@ -300,6 +300,8 @@ def run_gpu(args, rank, world, local_rank):
         line["select"] = select_run(args.select_reps, local_rank)
     if args.k4 and DIV == 1 and DISC * M_VAR ** 3 < 2**32:
         line["k4"] = k4_run(local_rank)
+    if args.k5_m >= 5 and DIV == 1 and math.comb(args.k5_m, 4) < 2**32:
+        line["k5"] = k5_run(args.k5_m, local_rank)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -373,6 +375,31 @@ def k4_run(device: int):
     return {"workload": f"madelon-shaped parity data N={N_OBJ} M={M_VAR}, k=4, D={DISC}, c={DIV + 1}",
             "s": s, "evals_per_s": evals / s,
             "paper_context": "Table 2 of the paper: 4D, 30 discretisations, Madelon 2000 x 500 on a Tesla K80: 456 s"}
+
+
+def k5_run(m: int, device: int):
+    """One k = 5 scan, one discretisation, of the first m variables of the
+    bench data's generator (madelon-shaped, 2000 samples, 2 classes): C(m, 5)
+    quintuple evaluations, timed with CUDA events after a warm-up on a
+    40-variable subset."""
+    import torch
+    from paper_1811_00631_gb300 import mdfs, synth
+    dev = torch.device("cuda", device)
+    ds = synth.madelon_like(M=m, seed=2)
+    x = torch.from_numpy(ds.x).to(dev)
+    y = torch.from_numpy(ds.y).to(dev)
+    mdfs.max_ig(x[:40].contiguous(), y, 5, DIV, 1, RANGE, XI, 1)
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    mdfs.max_ig(x, y, 5, DIV, 1, RANGE, XI, 5)
+    b.record(stream)
+    b.synchronize()
+    s = a.elapsed_time(b) / 1e3
+    evals = math.comb(m, 5)
+    return {"workload": f"madelon-shaped parity data N={N_OBJ} M={m}, k=5, D=1, c={DIV + 1}",
+            "s": s, "evals_per_s": evals / s,
+            "paper_context": "Table 1 of the paper: 5D, 1 discretisation, Madelon 2000 x 500: 1 h on the GPU"}
 
 
 def serving_run(n_jobs: int, device: int):
@@ -474,6 +501,9 @@ def main():
     ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=2)")
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving-mix run (0: skip)")
     ap.add_argument("--k4", type=int, default=1, help="time one k = 4 scan of the bench data (0: skip)")
+    ap.add_argument("--k5-m", type=int, default=200,
+                    help="variables of the timed one-discretisation k = 5 scan (0: skip; 500 = the "
+                         "madelon-shaped 5D case, about 45 s)")
     ap.add_argument("--select-reps", type=int, default=3,
                     help="timed calls of the selection pipeline per k (0: skip)")
     ap.add_argument("--batched", action="store_true", help="run the batched k=2 workload instead")
@@ -486,6 +516,7 @@ def main():
         args.serving_jobs = 0
         args.select_reps = 0
         args.k4 = 0
+        args.k5_m = 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -6,7 +6,7 @@
  * where S runs over all (k-1)-subsets of the other variables and, in
  * addition, over several random discretisations of the data (section
  * "Algorithm and implementation").  This library computes that scan on one
- * GPU (sm_103a) for k = 1..4 and fits the chi^2 / extreme-value null that
+ * GPU (sm_103a) for k = 1..5 and fits the chi^2 / extreme-value null that
  * turns the result into p-values (section "Theory").
  *
  * Conventions shared by every entry point
@@ -33,7 +33,9 @@
  *   2 <= c <= N <= 32768; 1 <= discretizations <= 1024; k <= M <= 65535;
  *   for k = 2, discretizations * M < 2^32; for k = 3,
  *   discretizations * M * M < 2^32; k = 4 needs divisions = 1 and
- *   discretizations * M^3 < 2^32.
+ *   discretizations * M^3 < 2^32; k = 5 needs divisions = 1 and
+ *   discretizations * C(M, 4) < 2^32 (M = 500 allows one discretisation,
+ *   M = 200 up to 66).
  */
 #ifndef MDFS_H
 #define MDFS_H
@@ -92,7 +94,7 @@ int mdfs_discretize(const mdfs_data* data, int divisions, int discretizations, d
  *     f(t) = t ln t,  b^d = pc_xi * N^d / min(N^0, N^1),
  * summed over all c^|S| voxels v, and IG(i | S) = SH(S) - SH(S + {i}).
  *
- * k:          1, 2, 3 or 4 (k = 4: divisions = 1).
+ * k:          1 .. 5 (k = 4, 5: divisions = 1).
  * pc_xi:      the pseudocount parameter xi, 0 < pc_xi < 1.
  * ig:         [M] float, the maximum per variable (may be slightly negative
  *             when the pseudocounts dominate).
@@ -215,8 +217,8 @@ int mdfs_p_adjust(const double* p, int m, int method, double* adjusted, void* st
  * beside the max scan and the selection pipeline): every (variable v,
  * partner set S) with |S| = k - 1, v not in S, whose IG(v | S) maximised
  * over the discretisations reaches ig_threshold (nats).  Same data, k,
- * divisions, discretizations, range, pc_xi and seed as mdfs_max_ig (k = 1..4;
- * k = 4 with divisions = 1); the scan runs on the popcount kernels.
+ * divisions, discretizations, range, pc_xi and seed as mdfs_max_ig (k = 1..5;
+ * k = 4, 5 with divisions = 1); the scan runs on the popcount kernels.
  *
  * Records are sorted by (v, S) ascending: var [n], tuples [n][k-1] (S
  * ascending; NULL allowed for k = 1), ig [n] float, best_disc [n] (the lowest

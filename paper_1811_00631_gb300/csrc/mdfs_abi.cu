@@ -529,7 +529,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             int lo = 0;
             const int cnt = share(ws->n_items5, &lo);
             MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
-                                            (const int*)ws->cnt2.p, keys, st));
+                                            (const int*)ws->cnt2.p, keys, st, em));
         }
     }
 
@@ -1112,7 +1112,7 @@ int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int dis
     if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
     if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
-    if (k == 5) return fail(MDFS_EINVAL, "interesting tuples support k up to 4");
+    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;

@@ -62,6 +62,14 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// k = 5 record key: five 12-bit fields (variable, then partners ascending),
+// v in bits 0..11 and p4 in bits 48..59 (the k = 5 limit D C(M,4) < 2^32
+// keeps M below 569); never equal to the empty key.
+__device__ __forceinline__ unsigned long long emit_key5(int v, int p1, int p2, int p3, int p4) {
+    return (unsigned long long)v | ((unsigned long long)p1 << 12) | ((unsigned long long)p2 << 24) |
+           ((unsigned long long)p3 << 36) | ((unsigned long long)p4 << 48);
+}
+
 // Inserts (key, packed value) into an emission table (EmitTable of
 // mdfs_internal.cuh): linear probing from mix64(key), the slot claimed by
 // compare-and-swap, the value max-reduced.  The probe count is bounded by the

@@ -15,13 +15,17 @@ namespace {
 
 constexpr int kSortThreads = 1024;
 
-// (v, p1, p2, p3) lexicographic order: the 16-bit fields with v most significant
-__device__ __forceinline__ unsigned long long sort_key(unsigned long long key) {
+// (v, p1, p2, p3) lexicographic order: the 16-bit fields with v most
+// significant; k = 5: the five 12-bit fields (v, p1, .., p4) in that order.
+__device__ __forceinline__ unsigned long long sort_key(unsigned long long key, int k) {
+    if (k == 5)
+        return ((key & 0xFFFull) << 48) | (((key >> 12) & 0xFFFull) << 36) | (((key >> 24) & 0xFFFull) << 24) |
+               (((key >> 36) & 0xFFFull) << 12) | (key >> 48);
     return ((key & 0xFFFFull) << 48) | (((key >> 16) & 0xFFFFull) << 32) | (((key >> 32) & 0xFFFFull) << 16) |
            (key >> 48);
 }
 
-__global__ void emit_gather_kernel(EmitTable t, unsigned long long* __restrict__ rk,
+__global__ void emit_gather_kernel(EmitTable t, int k, unsigned long long* __restrict__ rk,
                                    unsigned long long* __restrict__ rv, int* __restrict__ counter, int n_max) {
     const unsigned int size = t.mask + 1u;
     for (unsigned int s = blockIdx.x * blockDim.x + threadIdx.x; s < size; s += gridDim.x * blockDim.x) {
@@ -29,7 +33,7 @@ __global__ void emit_gather_kernel(EmitTable t, unsigned long long* __restrict__
         if (key == kEmptyEmitKey) continue;
         const int pos = atomicAdd(counter, 1);
         if (pos < n_max) {
-            rk[pos] = sort_key(key);
+            rk[pos] = sort_key(key, k);
             rv[pos] = t.vals[s];
         }
     }
@@ -67,8 +71,14 @@ __global__ void __launch_bounds__(kSortThreads) emit_sort_decode_kernel(unsigned
         }
     for (int i = tid; i < n; i += kSortThreads) {
         const unsigned long long s = rk[i], v = rv[i];
-        var[i] = (int)(s >> 48);
-        const int p[3] = {(int)((s >> 32) & 0xFFFF), (int)((s >> 16) & 0xFFFF), (int)(s & 0xFFFF)};
+        int p[4];
+        if (k == 5) {
+            var[i] = (int)(s >> 48);
+            for (int j = 0; j < 4; ++j) p[j] = (int)((s >> (36 - 12 * j)) & 0xFFF);
+        } else {
+            var[i] = (int)(s >> 48);
+            for (int j = 0; j < 3; ++j) p[j] = (int)((s >> (32 - 16 * j)) & 0xFFFF);
+        }
         if (tuples)
             for (int j = 0; j < k - 1; ++j) tuples[(size_t)i * (k - 1) + j] = p[j];
         ig[i] = order_bits_float((uint32_t)(v >> 32));
@@ -85,7 +95,7 @@ cudaError_t launch_emit_collect(EmitTable t, int k, unsigned long long* recs_key
     if (e != cudaSuccess) return e;
     const unsigned int size = t.mask + 1u;
     const int blocks = (int)std::min<unsigned int>((size + 255u) / 256u, 4096u);
-    emit_gather_kernel<<<blocks, 256, 0, st>>>(t, recs_key, recs_val, counter, npad);
+    emit_gather_kernel<<<blocks, 256, 0, st>>>(t, k, recs_key, recs_val, counter, npad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
     emit_sort_decode_kernel<<<1, kSortThreads, 0, st>>>(recs_key, recs_val, n, npad, k, var, tuples, ig, disc);

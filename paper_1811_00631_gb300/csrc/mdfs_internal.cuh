@@ -133,7 +133,7 @@ cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd
 void build_k5_items(int M, std::vector<int2>& items);
 cudaError_t launch_k5(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
-                      cudaStream_t st);
+                      cudaStream_t st, EmitTable emit = EmitTable());
 // Interesting tuples: gather the occupied slots of the table into recs_key /
 // recs_val (npad >= n entries, a power of two), sort them by (variable,
 // partners) in one CTA and decode into var [n], tuples [n][k-1] (NULL ok),

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                                                         int d0, const int2* __restrict__ items,
                                                         const long long* __restrict__ tab,
                                                         const int* __restrict__ cnt1, const int* __restrict__ cnt2,
-                                                        unsigned long long* __restrict__ keys) {
+                                                        unsigned long long* __restrict__ keys, EmitTable emit) {
     __shared__ __align__(16) uint32_t sE[kTE * kLD], sF[kTF * kLD];
     __shared__ __align__(16) uint32_t sB[kWC], sC[kWC], sBC[kWC], sA[kWC], sAB[kWC], sAC[kWC], sABC[kWC];
     // per e / f row: item part (n_x, n_bx, n_cx, n_bcx), a part (n_ax, n_abx, n_acx, n_abcx)
@@ -437,6 +437,17 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                     pack_key(fx_to_float(shF[tx + 16 * rf] - sh5), base - (a4 + b3 + c2 + f1[rf]));
                 const unsigned long long k_f =
                     pack_key(fx_to_float(shE[2 * ty + re] - sh5), base - (a4 + b3 + c2 + e1[re]));
+                if (emit.keys) {  // the five roles, partners ascending
+                    const int e = ev[re], f = fv[rf];
+                    const long long g5[5] = {shI[re][rf] - sh5, sh_acef - sh5, sh_abef - sh5, shF[tx + 16 * rf] - sh5,
+                                             shE[2 * ty + re] - sh5};
+                    const unsigned long long ek[5] = {emit_key5(a, b, c, e, f), emit_key5(b, a, c, e, f),
+                                                      emit_key5(c, a, b, e, f), emit_key5(e, a, b, c, f),
+                                                      emit_key5(f, a, b, c, e)};
+#pragma unroll
+                    for (int r = 0; r < 5; ++r)
+                        if (g5[r] >= emit.thr_fx) emit_insert(emit, ek[r], pack_key(fx_to_float(g5[r]), (uint32_t)d));
+                }
                 kA = kmax(kA, k_a);
                 kB = kmax(kB, k_b);
                 kC = kmax(kC, k_c);
@@ -505,10 +516,10 @@ void build_k5_items(int M, std::vector<int2>& items) {
 
 cudaError_t launch_k5(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
-                      cudaStream_t st) {
+                      cudaStream_t st, EmitTable emit) {
     if (n_items == 0 || nd == 0) return cudaSuccess;
     if (nd > 65535) return cudaErrorInvalidValue;
-    k5_kernel<<<dim3(n_items, nd), kThreads, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, keys);
+    k5_kernel<<<dim3(n_items, nd), kThreads, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, keys, emit);
     return cudaGetLastError();
 }
 

@@ -54,7 +54,8 @@ def _compare(codes, y, c, k, xi, thr, got, ref):
 
 
 @pytest.mark.parametrize("k,div,M,N,D", [(1, 1, 40, 300, 3), (2, 1, 30, 400, 2), (2, 2, 20, 333, 2),
-                                         (3, 1, 14, 257, 2), (3, 2, 10, 200, 1), (4, 1, 10, 300, 2)])
+                                         (3, 1, 14, 257, 2), (3, 2, 10, 200, 1), (4, 1, 10, 300, 2),
+                                         (5, 1, 9, 300, 2)])
 def test_interesting_tuples_match_oracle(cuda, k, div, M, N, D):
     from paper_1811_00631_gb300 import mdfs
     rng = np.random.default_rng(k * 100 + M)

@@ -81,7 +81,7 @@ def test_k5_errors(cuda):
     with pytest.raises(mdfs.MdfsError):
         mdfs.max_ig(x[:4], y, 5, 1, 1)  # fewer variables than k
     with pytest.raises(mdfs.MdfsError):
-        mdfs.interesting_tuples(x, y, 5, 1, 1)  # no room for four partners in a record
+        mdfs.interesting_tuples(x, y, 5, 2, 1)  # three classes
     xl = np.random.default_rng(1).standard_normal((600, 8)).astype(np.float32)
     yl = (np.arange(8) % 2).astype(np.uint8)
     with pytest.raises(mdfs.MdfsError):
