@@ -122,6 +122,17 @@ __device__ __forceinline__ void pair_counts(const uint32_t* __restrict__ sE, con
     }
 }
 
+// Interesting-tuple records of the five roles of (a, b, c, e, f), partners
+// ascending; kept out of line (taken only when emitting).
+__device__ __noinline__ void emit_roles5(EmitTable t, int a, int b, int c, int e, int f, long long ga, long long gb,
+                                         long long gc, long long ge, long long gf, int d) {
+    if (ga >= t.thr_fx) emit_insert(t, emit_key5(a, b, c, e, f), pack_key(fx_to_float(ga), (uint32_t)d));
+    if (gb >= t.thr_fx) emit_insert(t, emit_key5(b, a, c, e, f), pack_key(fx_to_float(gb), (uint32_t)d));
+    if (gc >= t.thr_fx) emit_insert(t, emit_key5(c, a, b, e, f), pack_key(fx_to_float(gc), (uint32_t)d));
+    if (ge >= t.thr_fx) emit_insert(t, emit_key5(e, a, b, c, f), pack_key(fx_to_float(ge), (uint32_t)d));
+    if (gf >= t.thr_fx) emit_insert(t, emit_key5(f, a, b, c, e), pack_key(fx_to_float(gf), (uint32_t)d));
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M,
                                                         int d0, const int2* __restrict__ items,
                                                         const long long* __restrict__ tab,
@@ -298,24 +309,27 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
         }
     }
     __syncthreads();
+    // per-pair values in rotation slots p = 2 re + rf: the pair epilogue below
+    // is a rolled loop that always works on slot 0 and rotates the slots
+    uint32_t pIs[4][3], nefs[4];
+    long long shIs[4];
     // SH(b, c, e, f) per pair: bits b = 1, c = 2, e = 4, f = 8
-    long long shI[2][2];
-    uint32_t nef[2][2];
 #pragma unroll
-    for (int re = 0; re < 2; ++re)
+    for (int p = 0; p < 4; ++p) {
+        const int re = p >> 1, rf = p & 1;
 #pragma unroll
-        for (int rf = 0; rf < 2; ++rf) {
-            shI[re][rf] = 0;
-            nef[re][rf] = 0u;
-            if (!ok[re][rf]) continue;
-            const uint32_t* E = eI[2 * ty + re];
-            const uint32_t* F = fI[tx + 16 * rf];
-            nef[re][rf] = pair(ev[re], fv[rf]);
-            uint32_t q[16] = {NC,   nb,   nc,   nbc,  E[0],           E[1],           E[2],           E[3],
-                              F[0], F[1], F[2], F[3], nef[re][rf], pI[re][rf][0], pI[re][rf][1], pI[re][rf][2]};
-            moebius_packed<4>(q);
-            shI[re][rf] = sh_packed<4>(q, tb);
-        }
+        for (int k = 0; k < 3; ++k) pIs[p][k] = pI[re][rf][k];
+        shIs[p] = 0;
+        nefs[p] = 0u;
+        if (!ok[re][rf]) continue;
+        const uint32_t* E = eI[2 * ty + re];
+        const uint32_t* F = fI[tx + 16 * rf];
+        nefs[p] = pair(ev[re], fv[rf]);
+        uint32_t q[16] = {NC,   nb,   nc,   nbc,  E[0],     E[1],       E[2],       E[3],
+                          F[0], F[1], F[2], F[3], nefs[p], pIs[p][0], pIs[p][1], pIs[p][2]};
+        moebius_packed<4>(q);
+        shIs[p] = sh_packed<4>(q, tb);
+    }
 
     // rank parts: rho(S) = C(M,4) - 1 - [C(M-1-s1,4) + C(M-1-s2,3) + C(M-1-s3,2) + (M-1-s4)]
     const unsigned long long K4 = bin4((unsigned long long)M);
@@ -323,15 +337,8 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
     const unsigned long long Mm1 = (unsigned long long)(M - 1);
     const uint32_t b4 = (uint32_t)bin4(Mm1 - b), b3 = (uint32_t)bin3(Mm1 - b);
     const uint32_t c3 = (uint32_t)bin3(Mm1 - c), c2 = (uint32_t)bin2(Mm1 - c);
-    uint32_t e2[2], e1[2], f1[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        e2[r] = ev[r] < M ? (uint32_t)bin2(Mm1 - ev[r]) : 0u;
-        e1[r] = (uint32_t)(M - 1 - ev[r]);
-        f1[r] = (uint32_t)(M - 1 - fv[r]);
-    }
 
-    unsigned long long kB = 0ull, kC = 0ull, kE[2] = {0ull, 0ull}, kF[2] = {0ull, 0ull};
+    unsigned long long kB = 0ull, kC = 0ull, kE0 = 0ull, kE1 = 0ull, kF0 = 0ull, kF1 = 0ull;
 
     // ---------------- loop over a < b ----------------
     for (int a = 0; a < b; ++a) {
@@ -355,10 +362,11 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
             for (int rf = 0; rf < 2; ++rf)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc[re][rf][k] = 0u;
+        const uint32_t* const str[4] = {sA, sAB, sAC, sABC};
         for (int ch = 0; ch < nchunk; ++ch) {
             const int s0 = ch * kWC, len = min(kWC, z.Wst - s0);
             if (nchunk > 1) {
-                __syncthreads();
+                if (ch > 0) __syncthreads();  // the previous chunk's readers are done
                 stage_rows(ch);
             }
             for (int j = tid; j < kWC; j += kThreads) {
@@ -370,54 +378,76 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
             }
             __syncthreads();
             row_counts(ch, true);
-            if (warp_live) {
+            if (nchunk > 1 && warp_live) {
                 int lo[2], hi[2];
                 segments(ch, lo, hi);
-                const uint32_t* const str[4] = {sA, sAB, sAC, sABC};
 #pragma unroll
                 for (int cls = 0; cls < 2; ++cls)
                     pair_counts<4>(sE, sF, str, lo[cls], hi[cls], cls ? 65536u : 1u, ty, tx, acc);
             }
-            if (nchunk > 1) __syncthreads();  // sA.. and the rows are restaged next chunk
         }
-        __syncthreads();
+        __syncthreads();  // row counts complete
         const uint32_t na = sa4[0], nab = sa4[1], nac = sa4[2], nabc = sa4[3];
-        // SH(a, b, c, x) per e row and f row: bits a = 1, b = 2, c = 4, x = 8
-        if (tid < kTE + kTF) {
-            const int r = tid < kTE ? tid : tid - kTE;
-            const int v = tid < kTE ? e0 + r : f0 + r;
-            uint32_t* A = tid < kTE ? eA[r] : fA[r];
-            const uint32_t* I = tid < kTE ? eI[r] : fI[r];
+        // SH(a, b, c, x) per e row and f row (bits a = 1, b = 2, c = 4, x = 8),
+        // four threads per row, one quarter of the voxels each
+        {
+            const int r = tid >> 2, qq = tid & 3;
+            const bool isE = r < kTE;
+            const int rr = isE ? r : r - kTE;
+            const int v = isE ? e0 + rr : f0 + rr;
+            uint32_t* A = isE ? eA[rr] : fA[rr];
+            const uint32_t* I = isE ? eI[rr] : fI[rr];
             long long sh = 0;
             if (v < M) {
-                A[0] = pair(a, v);
-                uint32_t q[16] = {NC,   na,   nb,   nab,  nc,   nac,  nbc,  nabc,
-                                  I[0], A[0], I[1], A[1], I[2], A[2], I[3], A[3]};
+                const uint32_t nax = pair(a, v);
+                uint32_t q[16] = {NC, na, nb, nab, nc, nac, nbc, nabc, I[0], nax, I[1], A[1], I[2], A[2], I[3], A[3]};
                 moebius_packed<4>(q);
-                sh = sh_packed<4>(q, tb);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t w = qq == 0 ? q[4 * j] : (qq == 1 ? q[4 * j + 1] : (qq == 2 ? q[4 * j + 2] : q[4 * j + 3]));
+                    sh += voxel_sh(w, tb);
+                }
+                if (qq == 0) A[0] = nax;
             }
-            if (tid < kTE) shE[r] = sh;
-            else shF[r] = sh;
+            sh += __shfl_xor_sync(0xffffffffu, sh, 1);
+            sh += __shfl_xor_sync(0xffffffffu, sh, 2);
+            if (qq == 0) {
+                if (isE) shE[rr] = sh;
+                else shF[rr] = sh;
+            }
         }
-        __syncthreads();
+        if (nchunk == 1 && warp_live) {
+            int lo[2], hi[2];
+            segments(0, lo, hi);
+#pragma unroll
+            for (int cls = 0; cls < 2; ++cls)
+                pair_counts<4>(sE, sF, str, lo[cls], hi[cls], cls ? 65536u : 1u, ty, tx, acc);
+        }
+        __syncthreads();  // SH(a,b,c,x), n_ax and the pair counts complete
         if (!warp_live) continue;
         const uint32_t a4 = (uint32_t)bin4(Mm1 - a), a3 = (uint32_t)bin3(Mm1 - a);
+        uint32_t accs[4][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) accs[p][k] = acc[p >> 1][p & 1][k];
         unsigned long long kA = 0ull;
-#pragma unroll
-        for (int re = 0; re < 2; ++re)
-#pragma unroll
-            for (int rf = 0; rf < 2; ++rf) {
-                if (!ok[re][rf]) continue;
+#pragma unroll 1
+        for (int p = 0; p < 4; ++p) {
+            const int re = p >> 1, rf = p & 1;
+            const int e = e0 + 2 * ty + re, f = f0 + tx + 16 * rf;
+            if (e < M && f < M && f > e) {
                 const uint32_t* EI = eI[2 * ty + re];
                 const uint32_t* EA = eA[2 * ty + re];
                 const uint32_t* FI = fI[tx + 16 * rf];
                 const uint32_t* FA = fA[tx + 16 * rf];
                 // bits a = 1, b = 2, c = 4, e = 8, f = 16
-                uint32_t q[32] = {NC,     na,     nb,     nab,    nc,     nac,    nbc,    nabc,
-                                  EI[0],  EA[0],  EI[1],  EA[1],  EI[2],  EA[2],  EI[3],  EA[3],
-                                  FI[0],  FA[0],  FI[1],  FA[1],  FI[2],  FA[2],  FI[3],  FA[3],
-                                  nef[re][rf], acc[re][rf][0], pI[re][rf][0], acc[re][rf][1],
-                                  pI[re][rf][1], acc[re][rf][2], pI[re][rf][2], acc[re][rf][3]};
+                uint32_t q[32] = {NC,       na,          nb,          nab,         nc,          nac,
+                                  nbc,      nabc,        EI[0],       EA[0],       EI[1],       EA[1],
+                                  EI[2],    EA[2],       EI[3],       EA[3],       FI[0],       FA[0],
+                                  FI[1],    FA[1],       FI[2],       FA[2],       FI[3],       FA[3],
+                                  nefs[0],  accs[0][0],  pIs[0][0],   accs[0][1],  pIs[0][1],   accs[0][2],
+                                  pIs[0][2], accs[0][3]};
                 moebius_packed<5>(q);
                 const long long sh5 = sh_packed<5>(q, tb);
                 long long sh_acef = 0, sh_abef = 0;
@@ -428,32 +458,51 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                     sh_acef += voxel_sh(q[mb] + q[mb | 2], tb);
                     sh_abef += voxel_sh(q[mc] + q[mc | 4], tb);
                 }
-                const uint32_t tef = e2[re] + f1[rf];
-                const unsigned long long k_a =
-                    pack_key(fx_to_float(shI[re][rf] - sh5), base - (b4 + c3 + tef));
+                const long long she = shE[2 * ty + re], shf = shF[tx + 16 * rf];
+                const uint32_t e1 = (uint32_t)(M - 1 - e), f1 = (uint32_t)(M - 1 - f);
+                const uint32_t tef = (uint32_t)bin2((unsigned long long)e1) + f1;
+                const unsigned long long k_a = pack_key(fx_to_float(shIs[0] - sh5), base - (b4 + c3 + tef));
                 const unsigned long long k_b = pack_key(fx_to_float(sh_acef - sh5), base - (a4 + c3 + tef));
                 const unsigned long long k_c = pack_key(fx_to_float(sh_abef - sh5), base - (a4 + b3 + tef));
-                const unsigned long long k_e =
-                    pack_key(fx_to_float(shF[tx + 16 * rf] - sh5), base - (a4 + b3 + c2 + f1[rf]));
-                const unsigned long long k_f =
-                    pack_key(fx_to_float(shE[2 * ty + re] - sh5), base - (a4 + b3 + c2 + e1[re]));
-                if (emit.keys) {  // the five roles, partners ascending
-                    const int e = ev[re], f = fv[rf];
-                    const long long g5[5] = {shI[re][rf] - sh5, sh_acef - sh5, sh_abef - sh5, shF[tx + 16 * rf] - sh5,
-                                             shE[2 * ty + re] - sh5};
-                    const unsigned long long ek[5] = {emit_key5(a, b, c, e, f), emit_key5(b, a, c, e, f),
-                                                      emit_key5(c, a, b, e, f), emit_key5(e, a, b, c, f),
-                                                      emit_key5(f, a, b, c, e)};
-#pragma unroll
-                    for (int r = 0; r < 5; ++r)
-                        if (g5[r] >= emit.thr_fx) emit_insert(emit, ek[r], pack_key(fx_to_float(g5[r]), (uint32_t)d));
-                }
+                const unsigned long long k_e = pack_key(fx_to_float(shf - sh5), base - (a4 + b3 + c2 + f1));
+                const unsigned long long k_f = pack_key(fx_to_float(she - sh5), base - (a4 + b3 + c2 + e1));
+                if (emit.keys)
+                    emit_roles5(emit, a, b, c, e, f, shIs[0] - sh5, sh_acef - sh5, sh_abef - sh5, shf - sh5, she - sh5,
+                                d);
                 kA = kmax(kA, k_a);
                 kB = kmax(kB, k_b);
                 kC = kmax(kC, k_c);
-                kE[re] = kmax(kE[re], k_e);
-                kF[rf] = kmax(kF[rf], k_f);
+                if (re) kE1 = kmax(kE1, k_e);
+                else kE0 = kmax(kE0, k_e);
+                if (rf) kF1 = kmax(kF1, k_f);
+                else kF0 = kmax(kF0, k_f);
             }
+            // rotate the slots (four rotations restore the item constants)
+            {
+                const uint32_t n0 = nefs[0];
+                const long long s0 = shIs[0];
+                uint32_t t0[3], t1[4];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) t0[k] = pIs[0][k];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) t1[k] = accs[0][k];
+#pragma unroll
+                for (int q2 = 0; q2 < 3; ++q2) {
+                    nefs[q2] = nefs[q2 + 1];
+                    shIs[q2] = shIs[q2 + 1];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) pIs[q2][k] = pIs[q2 + 1][k];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) accs[q2][k] = accs[q2 + 1][k];
+                }
+                nefs[3] = n0;
+                shIs[3] = s0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) pIs[3][k] = t0[k];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) accs[3][k] = t1[k];
+            }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) kA = kmax(kA, __shfl_xor_sync(0xffffffffu, kA, o));
         if (lane == 0 && kA) atomicMax(&ka, kA);
@@ -467,24 +516,23 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
         kC = kmax(kC, __shfl_xor_sync(0xffffffffu, kC, o));
     }
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) kE[r] = kmax(kE[r], __shfl_xor_sync(0xffffffffu, kE[r], o));
-        kF[r] = kmax(kF[r], __shfl_xor_sync(0xffffffffu, kF[r], 16));
+    for (int o = 8; o > 0; o >>= 1) {
+        kE0 = kmax(kE0, __shfl_xor_sync(0xffffffffu, kE0, o));
+        kE1 = kmax(kE1, __shfl_xor_sync(0xffffffffu, kE1, o));
     }
+    kF0 = kmax(kF0, __shfl_xor_sync(0xffffffffu, kF0, 16));
+    kF1 = kmax(kF1, __shfl_xor_sync(0xffffffffu, kF1, 16));
     if (lane == 0) {
         if (kB) atomicMax(&kbc[0], kB);
         if (kC) atomicMax(&kbc[1], kC);
     }
     if (tx == 0) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-            if (kE[r]) atomicMax(keys + ev[r], kE[r]);
+        if (kE0) atomicMax(keys + ev[0], kE0);
+        if (kE1) atomicMax(keys + ev[1], kE1);
     }
     if (lane < 16) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-            if (kF[r]) atomicMax(&kf[tx + 16 * r], kF[r]);
+        if (kF0) atomicMax(&kf[tx], kF0);
+        if (kF1) atomicMax(&kf[tx + 16], kF1);
     }
     __syncthreads();
     if (tid == 0) {
