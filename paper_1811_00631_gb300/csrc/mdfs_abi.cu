@@ -52,9 +52,12 @@ struct Workspace {
     Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
     Buffer items4;                                           // k = 4 work items
     Buffer items5;                                           // k = 5 work items
+    Buffer items3t, t3c, t3s;                                // triple tables (k = 4, 5)
+    Buffer t4c, t4s;                                         // quadruple tables (k = 5)
     Buffer ekeys, evals, ecnt, erk, erv;                     // interesting-tuple table and its records
     int items4_M = -1, n_items4 = 0;
     int items5_M = -1, n_items5 = 0;
+    int items3t_M = -1, n_items3t = 0;
     int items3_M = -1, items3_c = -1, n_items3 = 0;
     int items2_M = -1, n_items2 = 0;
     int* host_stats = nullptr;  // pinned, 16 ints
@@ -65,7 +68,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &ekeys, &evals, &ecnt, &erk, &erv};
+                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &ekeys, &evals, &ecnt, &erk, &erv};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -472,8 +475,10 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                                                   em));
         }
     } else if (k == 4) {
-        // two classes: pair counts from the pair pass, then the quadruple kernel
-        const size_t per_disc = (size_t)M * M * (sizeof(long long) + 2 * sizeof(int));
+        // two classes: pair counts from the pair pass, triple tables, then the quadruple kernel
+        const size_t n3 = t3_entries(M);
+        const size_t per_disc = (size_t)M * M * (sizeof(long long) + 2 * sizeof(int)) +
+                                n3 * (sizeof(uint32_t) + sizeof(long long));
         size_t budget = (size_t)4 << 30;
         if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
         int nd = (int)(budget / per_disc);
@@ -482,6 +487,18 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         if (nd > 65535) nd = 65535;
         MDFS_ENSURE(ws, sh2, (size_t)nd * M * M * sizeof(long long));
         MDFS_ENSURE(ws, cnt2, (size_t)nd * M * M * 2 * sizeof(int));
+        MDFS_ENSURE(ws, t3c, std::max<size_t>((size_t)nd * n3, 1) * sizeof(uint32_t));
+        MDFS_ENSURE(ws, t3s, std::max<size_t>((size_t)nd * n3, 1) * sizeof(long long));
+        if (ws->items3t_M != M) {
+            std::vector<int2> items;
+            build_t3_items(M, items);
+            MDFS_ENSURE(ws, items3t, std::max<size_t>(items.size(), 1) * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items3t.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items3t_M = M;
+            ws->n_items3t = (int)items.size();
+        }
         if (ws->items4_M != M) {
             std::vector<int2> items;
             build_k4_items(M, items);
@@ -496,14 +513,21 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
                                                    (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
+            MDFS_LAUNCH("t3", st, launch_t3(planes, g, M, d0, nn, (const int2*)ws->items3t.p, ws->n_items3t, tab, cnt1,
+                                            (const int*)ws->cnt2.p, (uint32_t*)ws->t3c.p, (long long*)ws->t3s.p,
+                                            st));
             int lo = 0;
             const int cnt = share(ws->n_items4, &lo);
             MDFS_LAUNCH("k4", st, launch_k4(planes, g, M, d0, nn, (const int2*)ws->items4.p + lo, cnt, tab, cnt1,
-                                            (const int*)ws->cnt2.p, keys, st, em));
+                                            (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
+                                            (const long long*)ws->t3s.p, keys, st, em));
         }
     } else if (k == 5) {
-        // two classes: pair counts from the pair pass, then the quintuple kernel
-        const size_t per_disc = (size_t)M * M * (sizeof(long long) + 2 * sizeof(int));
+        // two classes: pair counts, triple tables, quadruple tables (counts and
+        // entropies of all C(M,4) quadruples), then the quintuple kernel
+        const size_t n3 = t3_entries(M), n4 = t4_entries(M);
+        const size_t per_disc = (size_t)M * M * (sizeof(long long) + 2 * sizeof(int)) +
+                                (n3 + n4) * (sizeof(uint32_t) + sizeof(long long));
         size_t budget = (size_t)4 << 30;
         if (const char* env = getenv("MDFS_PAIR_TABLE_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
         int nd = (int)(budget / per_disc);
@@ -512,24 +536,45 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         if (nd > 65535) nd = 65535;
         MDFS_ENSURE(ws, sh2, (size_t)nd * M * M * sizeof(long long));
         MDFS_ENSURE(ws, cnt2, (size_t)nd * M * M * 2 * sizeof(int));
-        if (ws->items5_M != M) {
+        MDFS_ENSURE(ws, t3c, std::max<size_t>((size_t)nd * n3, 1) * sizeof(uint32_t));
+        MDFS_ENSURE(ws, t3s, std::max<size_t>((size_t)nd * n3, 1) * sizeof(long long));
+        MDFS_ENSURE(ws, t4c, std::max<size_t>((size_t)nd * n4, 1) * sizeof(uint32_t));
+        MDFS_ENSURE(ws, t4s, std::max<size_t>((size_t)nd * n4, 1) * sizeof(long long));
+        const struct {
+            Buffer* buf;
+            int* m;
+            int* n;
+            void (*build)(int, std::vector<int2>&);
+        } lists[3] = {{&ws->items3t, &ws->items3t_M, &ws->n_items3t, build_t3_items},
+                      {&ws->items4, &ws->items4_M, &ws->n_items4, build_k4_items},
+                      {&ws->items5, &ws->items5_M, &ws->n_items5, build_k5_items}};
+        for (const auto& l : lists) {
+            if (*l.m == M) continue;
             std::vector<int2> items;
-            build_k5_items(M, items);
-            MDFS_ENSURE(ws, items5, std::max<size_t>(items.size(), 1) * sizeof(int2));
-            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items5.p, items.data(), items.size() * sizeof(int2),
-                                          cudaMemcpyHostToDevice, st));
+            l.build(M, items);
+            if (!ws->ensure(*l.buf, std::max<size_t>(items.size(), 1) * sizeof(int2)))
+                return fail(MDFS_ENOMEM, "device allocation of %zu bytes failed", items.size() * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(l.buf->p, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
             MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
-            ws->items5_M = M;
-            ws->n_items5 = (int)items.size();
+            *l.m = M;
+            *l.n = (int)items.size();
         }
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
                                                    (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
+            MDFS_LAUNCH("t3", st, launch_t3(planes, g, M, d0, nn, (const int2*)ws->items3t.p, ws->n_items3t, tab, cnt1,
+                                            (const int*)ws->cnt2.p, (uint32_t*)ws->t3c.p, (long long*)ws->t3s.p,
+                                            st));
+            MDFS_LAUNCH("t4", st, launch_t4(planes, g, M, d0, nn, (const int2*)ws->items4.p, ws->n_items4, tab, cnt1,
+                                            (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
+                                            (const long long*)ws->t3s.p, (uint32_t*)ws->t4c.p, (long long*)ws->t4s.p,
+                                            st));
             int lo = 0;
             const int cnt = share(ws->n_items5, &lo);
             MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
-                                            (const int*)ws->cnt2.p, keys, st, em));
+                                            (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
+                                            (const uint32_t*)ws->t4c.p, (const long long*)ws->t4s.p, keys, st, em));
         }
     }
 

@@ -119,21 +119,40 @@ cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, i
                             const int* cnt2, unsigned long long* keys, cudaStream_t st,
                             EmitTable emit = EmitTable());
 
+// Triple tables (c = 2) of discretisations [d0, d0 + nd): t3c [nd][C(M,3)]
+// packed all-ones counts (class 0 | class 1 << 16) and t3s [nd][C(M,3)] int64
+// fixed-point SH of every triple x < y < z at its lexicographic rank
+// C(M,3) - 1 - [C(M-1-x,3) + C(M-1-y,2) + (M-1-z)].  items from build_t3_items.
+void build_t3_items(int M, std::vector<int2>& items);
+size_t t3_entries(int M);
+cudaError_t launch_t3(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
+                      const long long* tab, const int* cnt1, const int* cnt2, uint32_t* t3c, long long* t3s,
+                      cudaStream_t st);
+
 // Quadruple pass (k = 4, c = 2) over discretisations [d0, d0 + nd), using the
-// pair counts cnt2 of the same chunk.  items from build_k4_items:
-// (a | b << 16, c-tile << 16 | e-tile).
+// pair counts cnt2 and the triple tables of the same chunk.  items from
+// build_k4_items: (a | b << 16, c-tile << 16 | e-tile).
 void build_k4_items(int M, std::vector<int2>& items);
 cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
-                      const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
-                      cudaStream_t st, EmitTable emit = EmitTable());
+                      const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
+                      const long long* t3s, unsigned long long* keys, cudaStream_t st, EmitTable emit = EmitTable());
+// Quadruple tables (c = 2, C(M,4) <= 2^32) of discretisations [d0, d0 + nd):
+// t4c / t4s [nd][C(M,4)] packed all-ones count and SH of every quadruple at
+// its lexicographic rank; same items and inputs as launch_k4.
+size_t t4_entries(int M);
+cudaError_t launch_t4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
+                      const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
+                      const long long* t3s, uint32_t* t4c, long long* t4s, cudaStream_t st);
 // Quintuple pass (k = 5, c = 2) over discretisations [d0, d0 + nd), using the
-// pair counts cnt2 of the same chunk.  items from build_k5_items:
+// pair counts cnt2, the triple counts t3c and the quadruple tables of the
+// same chunk.  items from build_k5_items:
 // (b | c << 16, e-tile << 16 | f-tile); keys index d C(M,4) + lexicographic
 // rank of the partner set.
 void build_k5_items(int M, std::vector<int2>& items);
 cudaError_t launch_k5(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
-                      const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
-                      cudaStream_t st, EmitTable emit = EmitTable());
+                      const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
+                      const uint32_t* t4c, const long long* t4s, unsigned long long* keys, cudaStream_t st,
+                      EmitTable emit = EmitTable());
 // Interesting tuples: gather the occupied slots of the table into recs_key /
 // recs_val (npad >= n entries, a power of two), sort them by (variable,
 // partners) in one CTA and decode into var [n], tuples [n][k-1] (NULL ok),

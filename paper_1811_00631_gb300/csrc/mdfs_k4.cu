@@ -3,16 +3,14 @@
 // implementation").
 //
 // For a quadruple a < b < c < e and one class, the 16 voxel counts follow
-// from the all-ones counts n_T of every subset T of {a, b, c, e} (n_{} = class
-// size) by Moebius inversion over supersets: count(ones exactly O) =
-// sum_{T >= O} (-1)^{|T \ O|} n_T.  Singles and pairs come from the k = 1 and
-// pair passes; the kernel counts, per 32 samples and class,
-//     n_abce = popc(A&B&C&E),  n_ace = popc(A&C&E),  n_bce = popc(B&C&E),
-//     n_abe = popc(A&B&E) (per e),  n_abc = popc(A&B&C) (per c).
-// SH over the 16 voxels gives IG(a|bce), IG(b|ace), IG(c|abe), IG(e|abc) from
-// the four triple entropies, which the kernel builds the same way from 8
-// voxels.  Entropies are exact int64 fixed-point sums of the f(n + beta)
-// tables.
+// from the all-ones counts n_T of every subset T of {a, b, c, e} by Moebius
+// inversion over supersets: count(ones exactly O) = sum_{T >= O}
+// (-1)^{|T \ O|} n_T.  Singles and pairs come from the k = 1 and pair passes,
+// the four triples' counts and entropies from the triple tables (t3_kernel);
+// the kernel counts only n_abce = popc(A&B&C&E) per 32 samples, both classes
+// packed in one word.  SH over the 16 voxels gives IG(a|bce), IG(b|ace),
+// IG(c|abe), IG(e|abc) against the tabled triple entropies.  Entropies are
+// exact int64 fixed-point sums of the f(n + beta) tables.
 //
 // Work item: a pair (a, b) with a tile of 32 c (c > b) and a tile of 32 e
 // (e > c); 16 x 16 threads, 2 x 2 (c, e) per thread.  Keys index the partner
@@ -24,45 +22,29 @@
 
 #include "mdfs_device.cuh"
 #include "mdfs_internal.cuh"
+#include "mdfs_packed.cuh"
 
 namespace mdfs {
 
 namespace {
 
-constexpr int kRC = 2, kRE = 2, kTC = 16 * kRC, kTE = 16 * kRE, kWC = 32;
-constexpr int kLD = kWC + 2;  // even row stride: 8-byte word-pair loads, rows 2 banks apart
-
-// In-place Moebius inversion over supersets of L bits: on entry n[T] is the
-// all-ones count of subset T, on exit n[O] the count of the voxel whose ones
-// are exactly O.
-template <int L>
-__device__ __forceinline__ void superset_moebius(int (&n)[1 << L]) {
-#pragma unroll
-    for (int j = 0; j < L; ++j)
-#pragma unroll
-        for (int m = 0; m < (1 << L); ++m)
-            if (!(m & (1 << j))) n[m] -= n[m | (1 << j)];
-}
-
-// SH = sum over voxels of f(n0+n1+b0+b1) - f(n0+b0) - f(n1+b1) (int64 tables)
-template <int L>
-__device__ __forceinline__ long long sh_voxels(const int (&n0)[1 << L], const int (&n1)[1 << L],
-                                               const long long* __restrict__ tab, int np1) {
-    long long s = 0;
-#pragma unroll
-    for (int m = 0; m < (1 << L); ++m)
-        s += __ldg(tab + 2 * np1 + n0[m] + n1[m]) - __ldg(tab + n0[m]) - __ldg(tab + np1 + n1[m]);
-    return s;
-}
+constexpr int kRC = 2, kRE = 2, kTC = 16 * kRC, kTE = 16 * kRE;
+constexpr int kWC = 128;      // staged words per chunk (even)
+constexpr int kLD = kWC + 2;  // row stride: uint2 loads, e rows two banks apart
 
 __device__ __forceinline__ unsigned long long kmax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 
+// kTable: instead of folding the four roles into keys, store n_abce and
+// SH(a,b,c,e) of every quadruple at its lexicographic rank (the quadruple
+// tables of the k = 5 scan; C(M,4) < 2^32).
+template <bool kTable>
 __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M, int d0,
                                                  const int2* __restrict__ items, const long long* __restrict__ tab,
                                                  const int* __restrict__ cnt1, const int* __restrict__ cnt2,
-                                                 unsigned long long* __restrict__ keys, EmitTable emit) {
-    __shared__ __align__(8) uint32_t sa[kWC], sb[kWC], sab[kWC];
-    __shared__ __align__(8) uint32_t sabc[kTC][kLD], sac[kTC][kLD], sbc[kTC][kLD], se[kTE][kLD];
+                                                 const uint32_t* __restrict__ t3c, const long long* __restrict__ t3s,
+                                                 unsigned long long* __restrict__ keys, EmitTable emit,
+                                                 uint32_t* __restrict__ t4c, long long* __restrict__ t4s) {
+    __shared__ __align__(16) uint32_t sABC[kTC * kLD], sE[kTE * kLD], sAB[kWC];
     __shared__ unsigned long long kc[kTC], ke[kTE], ka, kb;
 
     const int2 it = items[blockIdx.x];
@@ -72,71 +54,44 @@ __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__
     const int dl = blockIdx.y, d = d0 + dl;
     const int tid = threadIdx.x, tc = tid >> 4, te = tid & 15;
     const uint32_t* pbase = planes + (size_t)d * M * g.Ws;  // one plane per variable (c = 2)
+    const Staging z = make_staging(g.W0, g.W1);
 
-    // all-ones counts per class: [cls][rc][re] for abce, ace, bce; [cls][rc] abc; [cls][re] abe
-    int x4[2][kRC][kRE], xace[2][kRC][kRE], xbce[2][kRC][kRE], xabc[2][kRC], xabe[2][kRE];
-#pragma unroll
-    for (int cl = 0; cl < 2; ++cl) {
-#pragma unroll
-        for (int rc = 0; rc < kRC; ++rc) {
-            xabc[cl][rc] = 0;
-#pragma unroll
-            for (int re = 0; re < kRE; ++re) x4[cl][rc][re] = xace[cl][rc][re] = xbce[cl][rc][re] = 0;
+    // all-ones counts n_abce per (c, e), both classes packed
+    uint32_t x4[kRC][kRE] = {{0u, 0u}, {0u, 0u}};
+    for (int s0 = 0; s0 < z.Wst; s0 += kWC) {
+        const int len = min(kWC, z.Wst - s0);
+        __syncthreads();
+        for (int j = tid; j < kWC; j += 256) {
+            uint32_t w = 0u;
+            if (j < len)
+                w = staged_word(pbase + (size_t)a * g.Ws, s0 + j, z) & staged_word(pbase + (size_t)b * g.Ws, s0 + j, z);
+            sAB[j] = w;
         }
+        __syncthreads();
+        for (int idx = tid; idx < (kTC + kTE) * kWC; idx += 256) {
+            const int r = idx / kWC, j = idx % kWC;
+            const int v = r < kTC ? c0 + r : e0 + (r - kTC);
+            const uint32_t w = (j < len && v < M) ? staged_word(pbase + (size_t)v * g.Ws, s0 + j, z) : 0u;
+            if (r < kTC) sABC[r * kLD + j] = w & sAB[j];
+            else sE[(r - kTC) * kLD + j] = w;
+        }
+        __syncthreads();
+        int lo[2], hi[2];
+        class_segments(z, s0, kWC, lo, hi);
 #pragma unroll
-        for (int re = 0; re < kRE; ++re) xabe[cl][re] = 0;
-    }
-
+        for (int cls = 0; cls < 2; ++cls) {
+            const uint32_t mul = cls ? 65536u : 1u;
+            for (int j = lo[cls]; j < hi[cls]; j += 2) {
+                uint2 u[kRC], w[kRE];
 #pragma unroll
-    for (int cls = 0; cls < 2; ++cls) {
-        const int wb = cls == 0 ? 0 : g.W0, we = cls == 0 ? g.W0 : g.W;
-        for (int w0 = wb; w0 < we; w0 += kWC) {
-            const int nw = min(kWC, we - w0);
-            __syncthreads();
-            if (tid < kWC) {
-                const uint32_t pa = tid < nw ? pbase[(size_t)a * g.Ws + w0 + tid] : 0u;
-                const uint32_t pb = tid < nw ? pbase[(size_t)b * g.Ws + w0 + tid] : 0u;
-                sa[tid] = pa;
-                sb[tid] = pb;
-                sab[tid] = pa & pb;
-            }
-            __syncthreads();
-            for (int idx = tid; idx < kTC * kWC; idx += 256) {
-                const int w = idx % kWC, r = idx / kWC;
-                const int vc = c0 + r;
-                const uint32_t pc = (w < nw && vc < M) ? pbase[(size_t)vc * g.Ws + w0 + w] : 0u;
-                sabc[r][w] = sab[w] & pc;
-                sac[r][w] = sa[w] & pc;
-                sbc[r][w] = sb[w] & pc;
-            }
-            for (int idx = tid; idx < kTE * kWC; idx += 256) {
-                const int w = idx % kWC, r = idx / kWC;
-                const int ve = e0 + r;
-                se[r][w] = (w < nw && ve < M) ? pbase[(size_t)ve * g.Ws + w0 + w] : 0u;
-            }
-            __syncthreads();
-            // two words per step (entries past nw are zero)
-            for (int w = 0; w < nw; w += 2) {
-                const uint2 ab = *reinterpret_cast<const uint2*>(&sab[w]);
-                uint2 ev[kRE];
+                for (int r = 0; r < kRC; ++r) u[r] = *reinterpret_cast<const uint2*>(sABC + (tc + 16 * r) * kLD + j);
 #pragma unroll
-                for (int re = 0; re < kRE; ++re) {
-                    ev[re] = *reinterpret_cast<const uint2*>(&se[te + 16 * re][w]);
-                    xabe[cls][re] += __popc(ab.x & ev[re].x) + __popc(ab.y & ev[re].y);
-                }
+                for (int r = 0; r < kRE; ++r) w[r] = *reinterpret_cast<const uint2*>(sE + (te + 16 * r) * kLD + j);
 #pragma unroll
-                for (int rc = 0; rc < kRC; ++rc) {
-                    const uint2 v3 = *reinterpret_cast<const uint2*>(&sabc[tc + 16 * rc][w]);
-                    const uint2 vac = *reinterpret_cast<const uint2*>(&sac[tc + 16 * rc][w]);
-                    const uint2 vbc = *reinterpret_cast<const uint2*>(&sbc[tc + 16 * rc][w]);
-                    xabc[cls][rc] += __popc(v3.x) + __popc(v3.y);
+                for (int rc = 0; rc < kRC; ++rc)
 #pragma unroll
-                    for (int re = 0; re < kRE; ++re) {
-                        x4[cls][rc][re] += __popc(v3.x & ev[re].x) + __popc(v3.y & ev[re].y);
-                        xace[cls][rc][re] += __popc(vac.x & ev[re].x) + __popc(vac.y & ev[re].y);
-                        xbce[cls][rc][re] += __popc(vbc.x & ev[re].x) + __popc(vbc.y & ev[re].y);
-                    }
-                }
+                    for (int re = 0; re < kRE; ++re)
+                        x4[rc][re] += (uint32_t)(__popc(u[rc].x & w[re].x) + __popc(u[rc].y & w[re].y)) * mul;
             }
         }
     }
@@ -146,96 +101,58 @@ __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__
     if (tid == 0) ka = kb = 0ull;
     __syncthreads();
 
-    const int np1 = g.N + 1;
-    const int NC[2] = {g.N0, g.N1};
-    auto single = [&](int v, int cl) { return __ldg(cnt1 + ((size_t)d * M + v) * 2 + cl); };
-    auto pair = [&](int i, int m, int cl) {  // i < m
-        return __ldg(cnt2 + ((((size_t)dl * M + i) * M + m)) * 2 + cl);
+    Tabs tb;
+    tb.tab = tab;
+    tb.np1 = g.N + 1;
+    tb.N0 = g.N0;
+    tb.N1 = g.N1;
+    const uint32_t NC = pack2(g.N0, g.N1);
+    auto single = [&](int v) -> uint32_t {
+        const int* p = cnt1 + ((size_t)d * M + v) * 2;
+        return pack2(__ldg(p), __ldg(p + 1));
     };
-    int na[2], nb[2], nab[2];
-#pragma unroll
-    for (int cl = 0; cl < 2; ++cl) {
-        na[cl] = single(a, cl);
-        nb[cl] = single(b, cl);
-        nab[cl] = pair(a, b, cl);
-    }
+    auto pair = [&](int i, int m) -> uint32_t {  // i < m
+        const int* p = cnt2 + (((size_t)dl * M + i) * M + m) * 2;
+        return pack2(__ldg(p), __ldg(p + 1));
+    };
+    const Rank3 rk = make_rank3(M);
+    const uint32_t* T3c = t3c + (size_t)dl * ((size_t)rk.top + 1);
+    const long long* T3s = t3s + (size_t)dl * ((size_t)rk.top + 1);
+    const uint32_t na = single(a), nb = single(b), nab = pair(a, b);
+    const uint32_t ra = rk.part_x(a), rb = rk.part_x(b), rab = ra + rk.part_y(b);
     const uint32_t dM = (uint32_t)d * (uint32_t)M;
-    unsigned long long my_ka = 0ull, my_kb = 0ull;
+    unsigned long long my_ka = 0ull, my_kb = 0ull, my_ke[kRE] = {0ull, 0ull};
 #pragma unroll
     for (int rc = 0; rc < kRC; ++rc) {
         const int c = c0 + tc + 16 * rc;
         if (c >= M) continue;
-        int nc[2], nac[2], nbc[2];
-#pragma unroll
-        for (int cl = 0; cl < 2; ++cl) {
-            nc[cl] = single(c, cl);
-            nac[cl] = pair(a, c, cl);
-            nbc[cl] = pair(b, c, cl);
-        }
-        // SH(a, b, c): subsets of {a, b, c} as bits 0, 1, 2
-        long long sh_abc;
-        {
-            int t0[8], t1[8];
-#pragma unroll
-            for (int cl = 0; cl < 2; ++cl) {
-                int* t = cl ? t1 : t0;
-                t[0] = NC[cl]; t[1] = na[cl]; t[2] = nb[cl]; t[3] = nab[cl];
-                t[4] = nc[cl]; t[5] = nac[cl]; t[6] = nbc[cl]; t[7] = xabc[cl][rc];
-            }
-            superset_moebius<3>(t0);
-            superset_moebius<3>(t1);
-            sh_abc = sh_voxels<3>(t0, t1, tab, np1);
-        }
+        const uint32_t nc = single(c), nac = pair(a, c), nbc = pair(b, c);
+        const uint32_t i_abc = rk.top - (rab + (uint32_t)(rk.Mm1 - c));
+        const uint32_t n_abc = __ldg(T3c + i_abc);
+        const long long sh_abc = __ldg(T3s + i_abc);
+        const uint32_t rac = ra + rk.part_y(c), rbc = rb + rk.part_y(c);
         unsigned long long my_kc = 0ull;
 #pragma unroll
         for (int re = 0; re < kRE; ++re) {
             const int e = e0 + te + 16 * re;
             if (e >= M || e <= c) continue;
-            int ne[2], nae[2], nbe[2], nce[2];
-#pragma unroll
-            for (int cl = 0; cl < 2; ++cl) {
-                ne[cl] = single(e, cl);
-                nae[cl] = pair(a, e, cl);
-                nbe[cl] = pair(b, e, cl);
-                nce[cl] = pair(c, e, cl);
-            }
+            const uint32_t ne = single(e), nae = pair(a, e), nbe = pair(b, e), nce = pair(c, e);
+            const uint32_t t_e = (uint32_t)(rk.Mm1 - e);
+            const uint32_t i_abe = rk.top - (rab + t_e), i_ace = rk.top - (rac + t_e), i_bce = rk.top - (rbc + t_e);
             // the four-variable table: bits a = 1, b = 2, c = 4, e = 8
-            int q0[16], q1[16];
-#pragma unroll
-            for (int cl = 0; cl < 2; ++cl) {
-                int* q = cl ? q1 : q0;
-                q[0] = NC[cl]; q[1] = na[cl]; q[2] = nb[cl]; q[3] = nab[cl];
-                q[4] = nc[cl]; q[5] = nac[cl]; q[6] = nbc[cl]; q[7] = xabc[cl][rc];
-                q[8] = ne[cl]; q[9] = nae[cl]; q[10] = nbe[cl]; q[11] = xabe[cl][re];
-                q[12] = nce[cl]; q[13] = xace[cl][rc][re]; q[14] = xbce[cl][rc][re]; q[15] = x4[cl][rc][re];
+            uint32_t q[16] = {NC, na,  nb,  nab,           nc,  nac,           nbc,           n_abc,
+                              ne, nae, nbe, __ldg(T3c + i_abe), nce, __ldg(T3c + i_ace), __ldg(T3c + i_bce), x4[rc][re]};
+            moebius_packed<4>(q);
+            const long long sh4 = sh_packed<4>(q, tb);
+            if (kTable) {
+                const Rank4 r4 = make_rank4(M);
+                const size_t at = (size_t)dl * ((size_t)r4.top + 1) +
+                                  (r4.top - (r4.part_w(a) + r4.part_x(b) + r4.part_y(c) + (uint32_t)(r4.Mm1 - e)));
+                t4c[at] = x4[rc][re];
+                t4s[at] = sh4;
+                continue;
             }
-            // triples: (a, c, e), (b, c, e), (a, b, e) as 3-bit tables
-            int u0[8], u1[8], v0[8], v1[8], w0t[8], w1t[8];
-#pragma unroll
-            for (int cl = 0; cl < 2; ++cl) {
-                const int* q = cl ? q1 : q0;
-                int* u = cl ? u1 : u0;  // a c e -> bits 0 1 2 from q bits 1 4 8
-                int* v = cl ? v1 : v0;  // b c e from q bits 2 4 8
-                int* w = cl ? w1t : w0t;  // a b e from q bits 1 2 8
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    u[m] = q[((m & 1) ? 1 : 0) | ((m & 2) ? 4 : 0) | ((m & 4) ? 8 : 0)];
-                    v[m] = q[((m & 1) ? 2 : 0) | ((m & 2) ? 4 : 0) | ((m & 4) ? 8 : 0)];
-                    w[m] = q[((m & 1) ? 1 : 0) | ((m & 2) ? 2 : 0) | ((m & 4) ? 8 : 0)];
-                }
-            }
-            superset_moebius<4>(q0);
-            superset_moebius<4>(q1);
-            superset_moebius<3>(u0);
-            superset_moebius<3>(u1);
-            superset_moebius<3>(v0);
-            superset_moebius<3>(v1);
-            superset_moebius<3>(w0t);
-            superset_moebius<3>(w1t);
-            const long long sh4 = sh_voxels<4>(q0, q1, tab, np1);
-            const long long sh_ace = sh_voxels<3>(u0, u1, tab, np1);
-            const long long sh_bce = sh_voxels<3>(v0, v1, tab, np1);
-            const long long sh_abe = sh_voxels<3>(w0t, w1t, tab, np1);
+            const long long sh_abe = __ldg(T3s + i_abe), sh_ace = __ldg(T3s + i_ace), sh_bce = __ldg(T3s + i_bce);
             // IG(a | b,c,e), IG(b | a,c,e), IG(c | a,b,e), IG(e | a,b,c)
             const unsigned long long k_a =
                 pack_key(fx_to_float(sh_bce - sh4), ((dM + (uint32_t)b) * M + (uint32_t)c) * M + (uint32_t)e);
@@ -248,7 +165,7 @@ __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__
             my_ka = kmax(my_ka, k_a);
             my_kb = kmax(my_kb, k_b);
             my_kc = kmax(my_kc, k_c);
-            atomicMax(&ke[te + 16 * re], k_e);
+            my_ke[re] = kmax(my_ke[re], k_e);
             if (emit.keys) {  // the four roles, partners ascending
                 const long long g4[4] = {sh_bce - sh4, sh_ace - sh4, sh_abe - sh4, sh_abc - sh4};
                 const unsigned long long ek[4] = {emit_key(a, b, c, e), emit_key(b, a, c, e), emit_key(c, a, b, e),
@@ -264,6 +181,14 @@ __global__ void __launch_bounds__(256, 2) k4_kernel(const uint32_t* __restrict__
     for (int o = 16; o > 0; o >>= 1) {
         my_ka = kmax(my_ka, __shfl_xor_sync(0xffffffffu, my_ka, o));
         my_kb = kmax(my_kb, __shfl_xor_sync(0xffffffffu, my_kb, o));
+    }
+    // role e: the two c rows of a warp (lanes t and t + 16) share each e
+#pragma unroll
+    for (int re = 0; re < kRE; ++re) my_ke[re] = kmax(my_ke[re], __shfl_xor_sync(0xffffffffu, my_ke[re], 16));
+    if ((tid & 31) < 16) {
+#pragma unroll
+        for (int re = 0; re < kRE; ++re)
+            if (my_ke[re]) atomicMax(&ke[te + 16 * re], my_ke[re]);
     }
     if ((tid & 31) == 0) {
         if (my_ka) atomicMax(&ka, my_ka);
@@ -299,11 +224,27 @@ void build_k4_items(int M, std::vector<int2>& items) {
 }
 
 cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
-                      const long long* tab, const int* cnt1, const int* cnt2, unsigned long long* keys,
-                      cudaStream_t st, EmitTable emit) {
+                      const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
+                      const long long* t3s, unsigned long long* keys, cudaStream_t st, EmitTable emit) {
     if (n_items == 0 || nd == 0) return cudaSuccess;
     if (nd > 65535) return cudaErrorInvalidValue;
-    k4_kernel<<<dim3(n_items, nd), 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, keys, emit);
+    k4_kernel<false><<<dim3(n_items, nd), 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, t3c, t3s, keys, emit,
+                                                       nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+size_t t4_entries(int M) {
+    const size_t m = (size_t)M;
+    return M < 4 ? 0 : m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4;
+}
+
+cudaError_t launch_t4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
+                      const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
+                      const long long* t3s, uint32_t* t4c, long long* t4s, cudaStream_t st) {
+    if (n_items == 0 || nd == 0) return cudaSuccess;
+    if (nd > 65535 || t4_entries(M) > (1ull << 32)) return cudaErrorInvalidValue;
+    k4_kernel<true><<<dim3(n_items, nd), 256, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, t3c, t3s, nullptr,
+                                                      EmitTable(), t4c, t4s);
     return cudaGetLastError();
 }
 
