@@ -50,6 +50,42 @@ __device__ __noinline__ void emit_roles5(EmitTable t, int a, int b, int c, int e
     if (gf >= t.thr_fx) emit_insert(t, emit_key5(f, a, b, c, e), pack_key(fx_to_float(gf), (uint32_t)d));
 }
 
+// Asynchronous global -> shared copies of `bytes` (4 or 8); a copy with
+// valid == false writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// the a part of one e or f row: n_ax (two class counts), n_abx, n_acx, n_abcx, SH(a,b,c,x)
+struct RowA {
+    int2 ax;
+    uint32_t abx, acx, abcx, pad;
+    long long sh;
+};
+// the a part of the item: n_a, n_ab, n_ac (class counts), n_abc
+struct ScalA {
+    int2 a, ab, ac;
+    uint32_t abc, pad;
+};
+struct K5Smem {
+    uint32_t sE[kTE * kLD], sF[kTF * kLD];  // e and f rows (staged words)
+    uint32_t sBC[kWC], sABC[kWC];
+    uint32_t eI[kTE][4], fI[kTF][4];        // per row: n_x, n_bx, n_cx, n_bcx
+    RowA rows[2][kTE + kTF];                // a part, double-buffered by the parity of a
+    ScalA sa[2];
+    uint32_t pI[4][4][kThreads];            // per thread and pair slot: n_ef, n_bef, n_cef, n_bcef
+    long long shI[4][kThreads];             // SH(b, c, e, f)
+    uint32_t gA[2][3][4][kThreads];         // n_aef, n_abef, n_acef, double-buffered
+    unsigned long long ka, kbc[2], kf[kTF];
+};
+
 __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M,
                                                         int d0, const int2* __restrict__ items,
                                                         const long long* __restrict__ tab,
@@ -58,12 +94,8 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                                                         const uint32_t* __restrict__ t4c,
                                                         const long long* __restrict__ t4s,
                                                         unsigned long long* __restrict__ keys, EmitTable emit) {
-    __shared__ __align__(16) uint32_t sE[kTE * kLD], sF[kTF * kLD], sBC[kWC], sABC[kWC];
-    // per e / f row: item part (n_x, n_bx, n_cx, n_bcx), a part (n_ax, n_abx, n_acx, n_abcx)
-    __shared__ uint32_t eI[kTE][4], fI[kTF][4], eA[kTE][4], fA[kTF][4];
-    __shared__ long long shE[kTE], shF[kTF];  // SH(a,b,c,e), SH(a,b,c,f)
-    __shared__ uint32_t sa4[4];               // n_a, n_ab, n_ac, n_abc
-    __shared__ unsigned long long ka, kbc[2], kf[kTF];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K5Smem& sm = *reinterpret_cast<K5Smem*>(smem_raw);
 
     const int2 it = items[blockIdx.x];
     const int b = it.x & 0xFFFF, c = it.x >> 16;
@@ -86,17 +118,16 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
     const uint32_t* T3c = t3c + (size_t)dl * ((size_t)r3.top + 1);
     const uint32_t* T4c = t4c + (size_t)dl * ((size_t)r4.top + 1);
     const long long* T4s = t4s + (size_t)dl * ((size_t)r4.top + 1);
+    const int* C1 = cnt1 + (size_t)d * M * 2;
+    const int* C2 = cnt2 + (size_t)dl * M * M * 2;
 
-    auto single = [&](int v) -> uint32_t {
-        const int* p = cnt1 + ((size_t)d * M + v) * 2;
-        return pack2(__ldg(p), __ldg(p + 1));
-    };
+    auto single = [&](int v) -> uint32_t { return pack2(__ldg(C1 + 2 * v), __ldg(C1 + 2 * v + 1)); };
     auto pair = [&](int i, int m) -> uint32_t {  // i < m
-        const int* p = cnt2 + (((size_t)dl * M + i) * M + m) * 2;
+        const int* p = C2 + ((size_t)i * M + m) * 2;
         return pack2(__ldg(p), __ldg(p + 1));
     };
 
-    // this thread's e and f, and validity of its four pairs
+    // this thread's e and f
     int ev[2], fv[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -115,13 +146,13 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                 const int v = r < kTE ? e0 + r : f0 + (r - kTE);
                 if (v < M) w = staged_word(pbase + (size_t)v * g.Ws, s0 + j, z);
             }
-            if (r < kTE) sE[r * kLD + j] = w;
-            else sF[(r - kTE) * kLD + j] = w;
+            if (r < kTE) sm.sE[r * kLD + j] = w;
+            else sm.sF[(r - kTE) * kLD + j] = w;
         }
         for (int j = tid; j < kWC; j += kThreads)
-            sBC[j] = j < len ? staged_word(pbase + (size_t)b * g.Ws, s0 + j, z) &
-                                   staged_word(pbase + (size_t)c * g.Ws, s0 + j, z)
-                             : 0u;
+            sm.sBC[j] = j < len ? staged_word(pbase + (size_t)b * g.Ws, s0 + j, z) &
+                                      staged_word(pbase + (size_t)c * g.Ws, s0 + j, z)
+                                : 0u;
     };
 
     // rank parts: R(w,x,y,z) = C(M-1-w,4) + C(M-1-x,3) + C(M-1-y,2) + (M-1-z);
@@ -129,12 +160,49 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
     const uint32_t b4 = r4.part_w(b), b3 = r4.part_x(b), c3 = r4.part_x(c), c2 = r4.part_y(c);
     const uint32_t base = (uint32_t)((unsigned long long)d * ((unsigned long long)r4.top + 1ull)) + r4.top;
 
+    // asynchronous fetch of the a part into buffer `buf`
+    auto fetch_a = [&](int a, int buf) {
+        const uint32_t a4 = r4.part_w(a);
+        if (tid == 0) {
+            ScalA& S = sm.sa[buf];
+            cp_async8(&S.a, C1 + 2 * a, true);
+            cp_async8(&S.ab, C2 + ((size_t)a * M + b) * 2, true);
+            cp_async8(&S.ac, C2 + ((size_t)a * M + c) * 2, true);
+            cp_async4(&S.abc, T3c + r3.of(a, b, c), true);
+        }
+        if (tid < kTE + kTF) {
+            const int v = tid < kTE ? e0 + tid : f0 + (tid - kTE);
+            const bool ok = v < M;
+            const int vv = ok ? v : c + 1;  // any valid row for the address of a zero-filled copy
+            const uint32_t i4 = r4.top - (a4 + b3 + c2 + (uint32_t)(r4.Mm1 - vv));
+            RowA& R = sm.rows[buf][tid];
+            cp_async8(&R.ax, C2 + ((size_t)a * M + vv) * 2, ok);
+            cp_async4(&R.abx, T3c + r3.of(a, b, vv), ok);
+            cp_async4(&R.acx, T3c + r3.of(a, c, vv), ok);
+            cp_async4(&R.abcx, T4c + i4, ok);
+            cp_async8(&R.sh, T4s + i4, ok);
+        }
+        if (warp_live) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int e = ev[p >> 1], f = fv[p & 1];
+                const bool ok = e < M && f < M && f > e;
+                const int ee = ok ? e : c + 1, ff = ok ? f : c + 2;  // c + 2 < M: some (e, f) exists
+                const uint32_t ef = r4.part_y(ee) + (uint32_t)(r4.Mm1 - ff);
+                cp_async4(&sm.gA[buf][0][p][tid], T3c + r3.of(a, ee, ff), ok);
+                cp_async4(&sm.gA[buf][1][p][tid], T4c + (r4.top - (a4 + b3 + ef)), ok);
+                cp_async4(&sm.gA[buf][2][p][tid], T4c + (r4.top - (a4 + c3 + ef)), ok);
+            }
+        }
+        cp_async_commit();
+    };
+
     // ---------------- item part ----------------
     const uint32_t nb = single(b), nc = single(c), nbc = pair(b, c);
     if (tid < kTE + kTF) {
         const int r = tid < kTE ? tid : tid - kTE;
         const int v = tid < kTE ? e0 + r : f0 + r;
-        uint32_t* o = tid < kTE ? eI[r] : fI[r];
+        uint32_t* o = tid < kTE ? sm.eI[r] : sm.fI[r];
         if (v < M) {
             o[0] = single(v);
             o[1] = pair(b, v);
@@ -143,76 +211,51 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
         } else {
             o[0] = o[1] = o[2] = o[3] = 0u;
         }
-        if (tid < kTF) kf[tid] = 0ull;
+        if (tid < kTF) sm.kf[tid] = 0ull;
     }
     if (tid == 0) {
-        ka = 0ull;
-        kbc[0] = kbc[1] = 0ull;
+        sm.ka = 0ull;
+        sm.kbc[0] = sm.kbc[1] = 0ull;
     }
+    if (b > 0) fetch_a(0, 0);
     if (nchunk == 1) stage_rows(0);
-    // per-pair item values in rotation slots p = 2 re + rf: the pair epilogue
-    // below is a rolled loop that always works on slot 0 and rotates the slots
-    uint32_t nefs[4], pIs[4][3];  // n_ef; n_bef, n_cef, n_bcef
-    long long shIs[4];            // SH(b, c, e, f)
+    // per-pair item values, slot p = 2 re + rf
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int e = ev[p >> 1], f = fv[p & 1];
-        nefs[p] = pIs[p][0] = pIs[p][1] = pIs[p][2] = 0u;
-        shIs[p] = 0;
+        uint32_t v0 = 0u, v1 = 0u, v2 = 0u, v3 = 0u;
+        long long sh = 0;
         if (e < M && f < M && f > e) {
             const uint32_t ef = r4.part_y(e) + (uint32_t)(r4.Mm1 - f);
-            nefs[p] = pair(e, f);
-            pIs[p][0] = __ldg(T3c + r3.of(b, e, f));
-            pIs[p][1] = __ldg(T3c + r3.of(c, e, f));
             const uint32_t i_bcef = r4.top - (b4 + c3 + ef);
-            pIs[p][2] = __ldg(T4c + i_bcef);
-            shIs[p] = __ldg(T4s + i_bcef);
+            v0 = pair(e, f);
+            v1 = __ldg(T3c + r3.of(b, e, f));
+            v2 = __ldg(T3c + r3.of(c, e, f));
+            v3 = __ldg(T4c + i_bcef);
+            sh = __ldg(T4s + i_bcef);
         }
+        sm.pI[0][p][tid] = v0;
+        sm.pI[1][p][tid] = v1;
+        sm.pI[2][p][tid] = v2;
+        sm.pI[3][p][tid] = v3;
+        sm.shI[p][tid] = sh;
     }
 
     unsigned long long kB = 0ull, kC = 0ull, kE0 = 0ull, kE1 = 0ull, kF0 = 0ull, kF1 = 0ull;
 
     // ---------------- loop over a < b ----------------
+    // The table values of the a part arrive by asynchronous copies issued one
+    // iteration ahead, into the buffer of the parity of a.
     for (int a = 0; a < b; ++a) {
-        __syncthreads();  // previous iteration's readers of the a-part tables and sABC are done
+        const int buf = a & 1;
+        cp_async_wait_all();
+        __syncthreads();  // the a part has landed; the previous iteration's readers are done
         const uint32_t a4 = r4.part_w(a);
         if (tid == 0) {
-            if (ka) atomicMax(keys + (a - 1), ka);
-            ka = 0ull;
-            sa4[0] = single(a);
-            sa4[1] = pair(a, b);
-            sa4[2] = pair(a, c);
-            sa4[3] = __ldg(T3c + r3.of(a, b, c));
+            if (sm.ka) atomicMax(keys + (a - 1), sm.ka);
+            sm.ka = 0ull;
         }
-        if (tid < kTE + kTF) {  // the a part of every e and f row, and SH(a,b,c,x)
-            const int r = tid < kTE ? tid : tid - kTE;
-            const int v = tid < kTE ? e0 + r : f0 + r;
-            uint32_t* o = tid < kTE ? eA[r] : fA[r];
-            long long sh = 0;
-            if (v < M) {
-                const uint32_t i4 = r4.top - (a4 + b3 + c2 + (uint32_t)(r4.Mm1 - v));
-                o[0] = pair(a, v);
-                o[1] = __ldg(T3c + r3.of(a, b, v));
-                o[2] = __ldg(T3c + r3.of(a, c, v));
-                o[3] = __ldg(T4c + i4);
-                sh = __ldg(T4s + i4);
-            }
-            if (tid < kTE) shE[r] = sh;
-            else shF[r] = sh;
-        }
-        // counts of the triple and quadruples with a and the pair (e, f)
-        uint32_t gA[4][3];  // n_aef, n_abef, n_acef per slot
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int e = ev[p >> 1], f = fv[p & 1];
-            gA[p][0] = gA[p][1] = gA[p][2] = 0u;
-            if (warp_live && e < M && f < M && f > e) {
-                const uint32_t ef = r4.part_y(e) + (uint32_t)(r4.Mm1 - f);
-                gA[p][0] = __ldg(T3c + r3.of(a, e, f));
-                gA[p][1] = __ldg(T4c + (r4.top - (a4 + b3 + ef)));
-                gA[p][2] = __ldg(T4c + (r4.top - (a4 + c3 + ef)));
-            }
-        }
+        if (a + 1 < b) fetch_a(a + 1, buf ^ 1);
         // n_abcef per pair
         uint32_t acc[2][2] = {{0u, 0u}, {0u, 0u}};
         for (int ch = 0; ch < nchunk; ++ch) {
@@ -223,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                 __syncthreads();  // sBC of this chunk staged
             }
             for (int j = tid; j < kWC; j += kThreads)
-                sABC[j] = j < len ? staged_word(pbase + (size_t)a * g.Ws, s0 + j, z) & sBC[j] : 0u;
+                sm.sABC[j] = j < len ? staged_word(pbase + (size_t)a * g.Ws, s0 + j, z) & sm.sBC[j] : 0u;
             __syncthreads();
             if (warp_live) {
                 int lo[2], hi[2];
@@ -232,12 +275,12 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                 for (int cls = 0; cls < 2; ++cls) {
                     const uint32_t mul = cls ? 65536u : 1u;
                     for (int j = lo[cls]; j < hi[cls]; j += 2) {
-                        const uint2 s = *reinterpret_cast<const uint2*>(sABC + j);
+                        const uint2 s = *reinterpret_cast<const uint2*>(sm.sABC + j);
                         uint2 e[2], f[2];
 #pragma unroll
                         for (int r = 0; r < 2; ++r) {
-                            e[r] = *reinterpret_cast<const uint2*>(sE + (2 * ty + r) * kLD + j);
-                            f[r] = *reinterpret_cast<const uint2*>(sF + (tx + 16 * r) * kLD + j);
+                            e[r] = *reinterpret_cast<const uint2*>(sm.sE + (2 * ty + r) * kLD + j);
+                            f[r] = *reinterpret_cast<const uint2*>(sm.sF + (tx + 16 * r) * kLD + j);
                         }
 #pragma unroll
                         for (int re = 0; re < 2; ++re) {
@@ -251,10 +294,9 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
             }
         }
         if (!warp_live) continue;
-        const uint32_t na = sa4[0], nab = sa4[1], nac = sa4[2], nabc = sa4[3];
-        uint32_t accs[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) accs[p] = acc[p >> 1][p & 1];
+        const ScalA& S = sm.sa[buf];
+        const uint32_t na = pack2(S.a.x, S.a.y), nab = pack2(S.ab.x, S.ab.y), nac = pack2(S.ac.x, S.ac.y), nabc = S.abc;
+        uint32_t accs[4] = {acc[0][0], acc[0][1], acc[1][0], acc[1][1]};
         unsigned long long kA = 0ull;
 #pragma unroll 1
         for (int p = 0; p < 4; ++p) {
@@ -265,26 +307,54 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                 const uint32_t ef = r4.part_y(e) + f1;
                 const uint32_t R_acef = a4 + c3 + ef, R_abef = a4 + b3 + ef;
                 const long long sh_acef = __ldg(T4s + (r4.top - R_acef)), sh_abef = __ldg(T4s + (r4.top - R_abef));
-                const uint32_t* EI = eI[2 * ty + re];
-                const uint32_t* EA = eA[2 * ty + re];
-                const uint32_t* FI = fI[tx + 16 * rf];
-                const uint32_t* FA = fA[tx + 16 * rf];
+                const uint32_t* EI = sm.eI[2 * ty + re];
+                const uint32_t* FI = sm.fI[tx + 16 * rf];
+                const RowA& EA = sm.rows[buf][2 * ty + re];
+                const RowA& FA = sm.rows[buf][kTE + tx + 16 * rf];
                 // bits a = 1, b = 2, c = 4, e = 8, f = 16
-                uint32_t q[32] = {NC,       na,       nb,       nab,       nc,       nac,       nbc,       nabc,
-                                  EI[0],    EA[0],    EI[1],    EA[1],     EI[2],    EA[2],     EI[3],     EA[3],
-                                  FI[0],    FA[0],    FI[1],    FA[1],     FI[2],    FA[2],     FI[3],     FA[3],
-                                  nefs[0],  gA[0][0], pIs[0][0], gA[0][1], pIs[0][1], gA[0][2], pIs[0][2], accs[0]};
+                uint32_t q[32] = {NC,
+                                  na,
+                                  nb,
+                                  nab,
+                                  nc,
+                                  nac,
+                                  nbc,
+                                  nabc,
+                                  EI[0],
+                                  pack2(EA.ax.x, EA.ax.y),
+                                  EI[1],
+                                  EA.abx,
+                                  EI[2],
+                                  EA.acx,
+                                  EI[3],
+                                  EA.abcx,
+                                  FI[0],
+                                  pack2(FA.ax.x, FA.ax.y),
+                                  FI[1],
+                                  FA.abx,
+                                  FI[2],
+                                  FA.acx,
+                                  FI[3],
+                                  FA.abcx,
+                                  sm.pI[0][p][tid],
+                                  sm.gA[buf][0][p][tid],
+                                  sm.pI[1][p][tid],
+                                  sm.gA[buf][1][p][tid],
+                                  sm.pI[2][p][tid],
+                                  sm.gA[buf][2][p][tid],
+                                  sm.pI[3][p][tid],
+                                  accs[0]};
                 moebius_packed<5>(q);
                 const long long sh5 = sh_packed<5>(q, tb);
-                const long long she = shE[2 * ty + re], shf = shF[tx + 16 * rf];
-                const unsigned long long k_a = pack_key(fx_to_float(shIs[0] - sh5), base - (b4 + c3 + ef));
+                const long long shI = sm.shI[p][tid];
+                const long long she = EA.sh, shf = FA.sh;
+                const unsigned long long k_a = pack_key(fx_to_float(shI - sh5), base - (b4 + c3 + ef));
                 const unsigned long long k_b = pack_key(fx_to_float(sh_acef - sh5), base - R_acef);
                 const unsigned long long k_c = pack_key(fx_to_float(sh_abef - sh5), base - R_abef);
                 const unsigned long long k_e = pack_key(fx_to_float(shf - sh5), base - (a4 + b3 + c2 + f1));
                 const unsigned long long k_f = pack_key(fx_to_float(she - sh5), base - (a4 + b3 + c2 + e1));
                 if (emit.keys)
-                    emit_roles5(emit, a, b, c, e, f, shIs[0] - sh5, sh_acef - sh5, sh_abef - sh5, shf - sh5, she - sh5,
-                                d);
+                    emit_roles5(emit, a, b, c, e, f, shI - sh5, sh_acef - sh5, sh_abef - sh5, shf - sh5, she - sh5, d);
                 kA = kmax(kA, k_a);
                 kB = kmax(kB, k_b);
                 kC = kmax(kC, k_c);
@@ -293,43 +363,19 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                 if (rf) kF1 = kmax(kF1, k_f);
                 else kF0 = kmax(kF0, k_f);
             }
-            // rotate the slots (four rotations restore the item values)
-            {
-                const uint32_t n0 = nefs[0], t1 = accs[0];
-                const long long s0 = shIs[0];
-                uint32_t t0[3], t2[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    t0[k] = pIs[0][k];
-                    t2[k] = gA[0][k];
-                }
-#pragma unroll
-                for (int q2 = 0; q2 < 3; ++q2) {
-                    nefs[q2] = nefs[q2 + 1];
-                    shIs[q2] = shIs[q2 + 1];
-                    accs[q2] = accs[q2 + 1];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        pIs[q2][k] = pIs[q2 + 1][k];
-                        gA[q2][k] = gA[q2 + 1][k];
-                    }
-                }
-                nefs[3] = n0;
-                shIs[3] = s0;
-                accs[3] = t1;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    pIs[3][k] = t0[k];
-                    gA[3][k] = t2[k];
-                }
-            }
+            const uint32_t t = accs[0];  // rotate the counts: slot p + 1 comes next
+            accs[0] = accs[1];
+            accs[1] = accs[2];
+            accs[2] = accs[3];
+            accs[3] = t;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) kA = kmax(kA, __shfl_xor_sync(0xffffffffu, kA, o));
-        if (lane == 0 && kA) atomicMax(&ka, kA);
+        if (lane == 0 && kA) atomicMax(&sm.ka, kA);
     }
+    cp_async_wait_all();
     __syncthreads();
-    if (tid == 0 && ka) atomicMax(keys + (b - 1), ka);
+    if (tid == 0 && sm.ka) atomicMax(keys + (b - 1), sm.ka);
     // roles b, c (one variable each), e (per e row), f (per f row)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -344,23 +390,23 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
     kF0 = kmax(kF0, __shfl_xor_sync(0xffffffffu, kF0, 16));
     kF1 = kmax(kF1, __shfl_xor_sync(0xffffffffu, kF1, 16));
     if (lane == 0) {
-        if (kB) atomicMax(&kbc[0], kB);
-        if (kC) atomicMax(&kbc[1], kC);
+        if (kB) atomicMax(&sm.kbc[0], kB);
+        if (kC) atomicMax(&sm.kbc[1], kC);
     }
     if (tx == 0) {
         if (kE0) atomicMax(keys + ev[0], kE0);
         if (kE1) atomicMax(keys + ev[1], kE1);
     }
     if (lane < 16) {
-        if (kF0) atomicMax(&kf[tx], kF0);
-        if (kF1) atomicMax(&kf[tx + 16], kF1);
+        if (kF0) atomicMax(&sm.kf[tx], kF0);
+        if (kF1) atomicMax(&sm.kf[tx + 16], kF1);
     }
     __syncthreads();
     if (tid == 0) {
-        if (kbc[0]) atomicMax(keys + b, kbc[0]);
-        if (kbc[1]) atomicMax(keys + c, kbc[1]);
+        if (sm.kbc[0]) atomicMax(keys + b, sm.kbc[0]);
+        if (sm.kbc[1]) atomicMax(keys + c, sm.kbc[1]);
     }
-    if (tid < kTF && kf[tid]) atomicMax(keys + f0 + tid, kf[tid]);
+    if (tid < kTF && sm.kf[tid]) atomicMax(keys + f0 + tid, sm.kf[tid]);
 }
 
 }  // namespace
@@ -389,8 +435,11 @@ cudaError_t launch_k5(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd
                       EmitTable emit) {
     if (n_items == 0 || nd == 0) return cudaSuccess;
     if (nd > 65535) return cudaErrorInvalidValue;
-    k5_kernel<<<dim3(n_items, nd), kThreads, 0, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, t3c, t4c, t4s, keys,
-                                                      emit);
+    const size_t smem = sizeof(K5Smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)k5_kernel, smem);
+    if (e != cudaSuccess) return e;
+    k5_kernel<<<dim3(n_items, nd), kThreads, smem, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, t3c, t4c, t4s,
+                                                         keys, emit);
     return cudaGetLastError();
 }
 
