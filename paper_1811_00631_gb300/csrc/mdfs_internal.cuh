@@ -131,7 +131,7 @@ cudaError_t launch_t3(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd
 
 // Quadruple pass (k = 4, c = 2) over discretisations [d0, d0 + nd), using the
 // pair counts cnt2 and the triple tables of the same chunk.  items from
-// build_k4_items: (a | b << 16, c-tile << 16 | e-tile).
+// build_k4_items: (b, c-tile << 16 | e-tile); the kernel loops over a < b.
 void build_k4_items(int M, std::vector<int2>& items);
 cudaError_t launch_k4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
