@@ -34,8 +34,8 @@
  *   for k = 2, discretizations * M < 2^32; for k = 3,
  *   discretizations * M * M < 2^32; k = 4 needs divisions = 1 and
  *   discretizations * M^3 < 2^32; k = 5 needs divisions = 1 and
- *   discretizations * C(M, 4) < 2^32 (M = 500 allows one discretisation,
- *   M = 200 up to 66).
+ *   C(M, 4) < 2^32 (M <= 568), and for mdfs_max_ig_shard also
+ *   discretizations * C(M, 4) < 2^32.
  */
 #ifndef MDFS_H
 #define MDFS_H

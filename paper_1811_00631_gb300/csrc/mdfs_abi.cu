@@ -54,6 +54,8 @@ struct Workspace {
     Buffer items5;                                           // k = 5 work items
     Buffer items3t, t3c, t3s;                                // triple tables (k = 4, 5)
     Buffer t4c, t4s;                                         // quadruple tables (k = 5)
+    Buffer keys5, kdisc;                                     // k = 5 per-discretisation keys, best discretisation
+    bool k5_wide = false;                                    // keys hold (IG, rank) and kdisc the discretisation
     Buffer ekeys, evals, ecnt, erk, erv;                     // interesting-tuple table and its records
     int items4_M = -1, n_items4 = 0;
     int items5_M = -1, n_items5 = 0;
@@ -68,7 +70,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &ekeys, &evals, &ecnt, &erk, &erv};
+                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -202,16 +204,23 @@ cudaEvent_t prof_event() {
     } while (0)
 
 // k = 5 limits: two classes per variable, class sizes that fit the packed
-// 16-bit counters, and argmax indices d C(M,4) + rank that fit 32 bits.
-int check_k5(int M, int c, int D, int N) {
+// 16-bit counters, partner ranks below 2^32 (C(M,4) < 2^32), and for the
+// single-word keys of the sharded scan d C(M,4) + rank below 2^32.
+unsigned long long binom4(int M) {
+    const unsigned long long m = (unsigned long long)M;
+    return M < 4 ? 0ull : m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4;
+}
+int check_k5(int M, int c, int D, int N, bool single_key = false) {
     if (c != 2) return fail(MDFS_EINVAL, "k = 5 supports two classes per variable (divisions = 1)");
     if (N > 65535) return fail(MDFS_EINVAL, "k = 5 supports N up to 65535 samples");
-    const unsigned long long m = (unsigned long long)M;
-    const unsigned long long k4 = m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4;
-    if ((unsigned long long)D * k4 >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * C(M, 4) must stay below 2^32 for k = 5");
+    if (binom4(M) >= (1ull << 32)) return fail(MDFS_EINVAL, "C(M, 4) must stay below 2^32 for k = 5");
+    if (single_key && (unsigned long long)D * binom4(M) >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * C(M, 4) must stay below 2^32 for the keys of a k = 5 shard");
     return MDFS_OK;
 }
+
+// discretisation of each key when the k = 5 scan kept per-discretisation keys
+const int* wide_disc(const Workspace* ws) { return ws->k5_wide ? (const int*)ws->kdisc.p : nullptr; }
 
 int check_data(const mdfs_data* data, bool need_y) {
     if (!data) return fail(MDFS_EINVAL, "data is NULL");
@@ -357,6 +366,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     long long* sh1 = (long long*)ws->sh1.p;
     unsigned long long* keys = (unsigned long long*)ws->keys.p;
 
+    ws->k5_wide = false;
     MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
@@ -540,6 +550,14 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         MDFS_ENSURE(ws, t3s, std::max<size_t>((size_t)nd * n3, 1) * sizeof(long long));
         MDFS_ENSURE(ws, t4c, std::max<size_t>((size_t)nd * n4, 1) * sizeof(uint32_t));
         MDFS_ENSURE(ws, t4s, std::max<size_t>((size_t)nd * n4, 1) * sizeof(long long));
+        // one 64-bit key cannot hold d C(M,4) + rank: per-discretisation keys
+        const bool wide = (unsigned long long)D * n4 >= (1ull << 32) || getenv("MDFS_K5_DISC_KEYS") != nullptr;
+        ws->k5_wide = wide;
+        if (wide) {
+            MDFS_ENSURE(ws, keys5, (size_t)nd * M * sizeof(unsigned long long));
+            MDFS_ENSURE(ws, kdisc, (size_t)M * sizeof(int));
+            MDFS_CUDA_TRY(cudaMemsetAsync(ws->kdisc.p, 0, (size_t)M * sizeof(int), st));
+        }
         const struct {
             Buffer* buf;
             int* m;
@@ -572,9 +590,22 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                                             st));
             int lo = 0;
             const int cnt = share(ws->n_items5, &lo);
-            MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
-                                            (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
-                                            (const uint32_t*)ws->t4c.p, (const long long*)ws->t4s.p, keys, st, em));
+            if (!wide) {
+                MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
+                                                (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
+                                                (const uint32_t*)ws->t4c.p, (const long long*)ws->t4s.p, keys, 0,
+                                                true, st, em));
+            } else {
+                // keys of this chunk per discretisation (IG, partner rank), folded
+                // into (keys, kdisc) in discretisation order
+                unsigned long long* k5 = (unsigned long long*)ws->keys5.p;
+                MDFS_CUDA_TRY(cudaMemsetAsync(k5, 0, (size_t)nn * M * sizeof(unsigned long long), st));
+                MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
+                                                (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
+                                                (const uint32_t*)ws->t4c.p, (const long long*)ws->t4s.p, k5, M,
+                                                false, st, em));
+                MDFS_LAUNCH("k5_merge", st, launch_k5_merge(k5, nn, M, d0, keys, (int*)ws->kdisc.p, st));
+            }
         }
     }
 
@@ -746,7 +777,7 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     if (rc) return rc;
     rc = bind_out(ws, ws->disc, best_disc, (size_t)M, &odi);
     if (rc) return rc;
-    MDFS_LAUNCH("finalize", st, launch_finalize(keys, M, k, oig.dev, otu.dev, odi.dev, st));
+    MDFS_LAUNCH("finalize", st, launch_finalize(keys, M, k, oig.dev, otu.dev, odi.dev, st, wide_disc(ws)));
     if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
     if (check_err) {
         // the tensor-core kernel reports bounded-wait timeouts through this flag
@@ -837,7 +868,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
         MDFS_LAUNCH("finalize", st,
                     launch_finalize((const unsigned long long*)ws->keys.p, M, k, oig.dev + (size_t)j * M,
                                     otu.dev ? otu.dev + (size_t)j * M * kk : nullptr,
-                                    odi.dev ? odi.dev + (size_t)j * M : nullptr, st));
+                                    odi.dev ? odi.dev + (size_t)j * M : nullptr, st, wide_disc(ws)));
         if (check_err) {
             MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
             MDFS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -872,7 +903,7 @@ int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretiz
     if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
     if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
-    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
+    if (k == 5 && (rc = check_k5(M, c, D, N, true))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -1095,7 +1126,8 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
     MDFS_ENSURE(ws, dix, (size_t)Mx * sizeof(int));
     float* igx = (float*)ws->igx.p;
     MDFS_LAUNCH("finalize", st, launch_finalize((const unsigned long long*)ws->keys.p, Mx, k, igx,
-                                                k > 1 ? (int*)ws->tux.p : nullptr, (int*)ws->dix.p, st));
+                                                k > 1 ? (int*)ws->tux.p : nullptr, (int*)ws->dix.p, st,
+                                                wide_disc(ws)));
     if (check_err) {
         MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));

@@ -149,10 +149,16 @@ cudaError_t launch_t4(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd
 // (b | c << 16, e-tile << 16 | f-tile); keys index d C(M,4) + lexicographic
 // rank of the partner set.
 void build_k5_items(int M, std::vector<int2>& items);
+// keys_stride = 0 and disc_in_index: keys [M], index d C(M,4) + rank;
+// keys_stride = M and !disc_in_index: keys [nd][M] of this chunk, index = rank.
 cudaError_t launch_k5(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
-                      const uint32_t* t4c, const long long* t4s, unsigned long long* keys, cudaStream_t st,
-                      EmitTable emit = EmitTable());
+                      const uint32_t* t4c, const long long* t4s, unsigned long long* keys, int keys_stride,
+                      bool disc_in_index, cudaStream_t st, EmitTable emit = EmitTable());
+// Folds per-discretisation keys [nd][M] of discretisations d0.. into (best [M],
+// best_d [M]): a strictly larger IG replaces, so ties keep the lowest d.
+cudaError_t launch_k5_merge(const unsigned long long* keys5, int nd, int M, int d0, unsigned long long* best,
+                            int* best_d, cudaStream_t st);
 // Interesting tuples: gather the occupied slots of the table into recs_key /
 // recs_val (npad >= n entries, a power of two), sort them by (variable,
 // partners) in one CTA and decode into var [n], tuples [n][k-1] (NULL ok),
@@ -206,8 +212,10 @@ cudaError_t launch_p_adjust(const double* p, int m, int method, double level, vo
                             uint8_t* relevant, cudaStream_t st);
 
 // keys [M] -> ig [M] f32, tuples [M][k-1] i32 (NULL ok), disc [M] i32 (NULL ok).
+// kdisc != NULL (k = 5 with per-discretisation keys): the keys index the
+// partner rank only and kdisc [M] holds the discretisation.
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,
-                            int* disc, cudaStream_t st);
+                            int* disc, cudaStream_t st, const int* kdisc = nullptr);
 
 // chi^2 / extreme-value fit in FP64 (one CTA).  res[0] = IG_lim, res[1] = T,
 // res[2] = number of variables in the fit.

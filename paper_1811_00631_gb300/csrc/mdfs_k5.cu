@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
                                                         const uint32_t* __restrict__ t3c,
                                                         const uint32_t* __restrict__ t4c,
                                                         const long long* __restrict__ t4s,
-                                                        unsigned long long* __restrict__ keys, EmitTable emit) {
+                                                        unsigned long long* __restrict__ keys, int keys_stride,
+                                                        uint32_t disc_mul, EmitTable emit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K5Smem& sm = *reinterpret_cast<K5Smem*>(smem_raw);
 
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
     const uint32_t* pbase = planes + (size_t)d * M * g.Ws;
     const Staging z = make_staging(g.W0, g.W1);
     const int nchunk = (z.Wst + kWC - 1) / kWC;
+    keys += (size_t)dl * keys_stride;
     Tabs tb;
     tb.tab = tab;
     tb.np1 = g.N + 1;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
     // rank parts: R(w,x,y,z) = C(M-1-w,4) + C(M-1-x,3) + C(M-1-y,2) + (M-1-z);
     // table rank = C(M,4) - 1 - R, key index = d C(M,4) + table rank
     const uint32_t b4 = r4.part_w(b), b3 = r4.part_x(b), c3 = r4.part_x(c), c2 = r4.part_y(c);
-    const uint32_t base = (uint32_t)((unsigned long long)d * ((unsigned long long)r4.top + 1ull)) + r4.top;
+    const uint32_t base = (uint32_t)d * disc_mul + r4.top;
 
     // asynchronous fetch of the a part into buffer `buf`
     auto fetch_a = [&](int a, int buf) {
@@ -431,15 +433,42 @@ void build_k5_items(int M, std::vector<int2>& items) {
 
 cudaError_t launch_k5(const uint32_t* planes, PlaneGeom g, int M, int d0, int nd, const int2* items, int n_items,
                       const long long* tab, const int* cnt1, const int* cnt2, const uint32_t* t3c,
-                      const uint32_t* t4c, const long long* t4s, unsigned long long* keys, cudaStream_t st,
-                      EmitTable emit) {
+                      const uint32_t* t4c, const long long* t4s, unsigned long long* keys, int keys_stride,
+                      bool disc_in_index, cudaStream_t st, EmitTable emit) {
     if (n_items == 0 || nd == 0) return cudaSuccess;
     if (nd > 65535) return cudaErrorInvalidValue;
     const size_t smem = sizeof(K5Smem);
     cudaError_t e = ensure_dynamic_smem((const void*)k5_kernel, smem);
     if (e != cudaSuccess) return e;
+    const unsigned long long m = (unsigned long long)M;
+    const uint32_t disc_mul = disc_in_index ? (uint32_t)(m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4) : 0u;
     k5_kernel<<<dim3(n_items, nd), kThreads, smem, st>>>(planes, g, M, d0, items, tab, cnt1, cnt2, t3c, t4c, t4s,
-                                                         keys, emit);
+                                                         keys, keys_stride, disc_mul, emit);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k5_merge_kernel(const unsigned long long* __restrict__ keys5, int nd, int M, int d0,
+                                unsigned long long* __restrict__ best, int* __restrict__ best_d) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= M) return;
+    unsigned long long b = best[v];
+    int bd = best_d[v];
+    for (int dl = 0; dl < nd; ++dl) {
+        const unsigned long long k = keys5[(size_t)dl * M + v];
+        if (k && (!b || (k >> 32) > (b >> 32))) {
+            b = k;
+            bd = d0 + dl;
+        }
+    }
+    best[v] = b;
+    best_d[v] = bd;
+}
+}  // namespace
+
+cudaError_t launch_k5_merge(const unsigned long long* keys5, int nd, int M, int d0, unsigned long long* best,
+                            int* best_d, cudaStream_t st) {
+    k5_merge_kernel<<<(M + 255) / 256, 256, 0, st>>>(keys5, nd, M, d0, best, best_d);
     return cudaGetLastError();
 }
 

@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(256) k3_kernel(const uint32_t* __restrict__ pl
 
 // ---------------------------------------------------------------------------
 __global__ void finalize_kernel(const unsigned long long* __restrict__ keys, int M, int k, float* __restrict__ ig,
-                                int* __restrict__ tuples, int* __restrict__ disc) {
+                                int* __restrict__ tuples, int* __restrict__ disc, const int* __restrict__ kdisc) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= M) return;
     const unsigned long long key = keys[v];
@@ -587,8 +587,8 @@ __global__ void finalize_kernel(const unsigned long long* __restrict__ keys, int
         // R = C(t1,4) + C(t2,3) + C(t3,2) + C(t4,1), t_j = M - 1 - p_j
         const unsigned long long m = (unsigned long long)M;
         const unsigned long long k4 = m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4;
-        d = (int)(index / k4);
-        unsigned long long R = k4 - 1ull - (index % k4);
+        d = kdisc ? kdisc[v] : (int)(index / k4);
+        unsigned long long R = k4 - 1ull - (kdisc ? (unsigned long long)index : index % k4);
         int p[4];
         unsigned long long t = m;  // t_j strictly decreasing
         for (int j = 0; j < 4; ++j) {
@@ -673,8 +673,8 @@ cudaError_t launch_k3_items(const uint32_t* planes, PlaneGeom g, int M, int c, i
 }
 
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples, int* disc,
-                            cudaStream_t st) {
-    finalize_kernel<<<(M + 255) / 256, 256, 0, st>>>(keys, M, k, ig, tuples, disc);
+                            cudaStream_t st, const int* kdisc) {
+    finalize_kernel<<<(M + 255) / 256, 256, 0, st>>>(keys, M, k, ig, tuples, disc, k == 5 ? kdisc : nullptr);
     return cudaGetLastError();
 }
 

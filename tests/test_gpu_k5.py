@@ -86,3 +86,43 @@ def test_k5_errors(cuda):
     yl = (np.arange(8) % 2).astype(np.uint8)
     with pytest.raises(mdfs.MdfsError):
         mdfs.max_ig(xl, yl, 5, 1, 1)  # C(600, 4) >= 2^32: keys cannot index the quadruple
+
+
+def test_k5_per_discretisation_keys(cuda, monkeypatch):
+    """Per-discretisation keys (used when D C(M,4) >= 2^32, forced here with
+    MDFS_K5_DISC_KEYS) give exactly the single-key result.  With range 0 every
+    discretisation is the same equipotent split, so each maximum is tied
+    across all D discretisations and must report the lowest one."""
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(77)
+    M, N = 11, 600
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[1] > 0) ^ (x[4] > 0) ^ (x[9] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    for D, r in ((4, 0.5), (3, 0.0)):
+        want = _gpu_max_ig(cuda, x, y, 5, 1, D, r, 0.25, 31)
+        monkeypatch.setenv("MDFS_K5_DISC_KEYS", "1")
+        got = _gpu_max_ig(cuda, x, y, 5, 1, D, r, 0.25, 31)
+        monkeypatch.delenv("MDFS_K5_DISC_KEYS")
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+        if r == 0.0:
+            assert np.all(got[2] == 0)
+        codes = oracle.discretize(x, 1, D, r, 31)
+        ref = oracle.max_ig(codes, y, 2, 5, 0.25)
+        _check(codes, y, 2, 5, 0.25, *got, ref, range(M))
+
+
+def test_k5_select_pipeline(cuda):
+    """The selection pipeline at k = 5 (contrast variables, fit, Holm)
+    against the oracle's."""
+    from paper_1811_00631_gb300 import mdfs
+    from test_gpu_select import _check_select
+    rng = np.random.default_rng(55)
+    M, N, nc = 7, 500, 6
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = np.zeros(N, dtype=np.uint8)
+    for m in (0, 2, 3, 5, 6):
+        y ^= (x[m] > 0).astype(np.uint8)
+    ref = oracle.select(x, y, nc, 5, 1, 1, 0.0, 0.25, seed=3)
+    g = mdfs.select(x, y, nc, 5, 1, 1, 0.0, 0.25, seed=3)
+    _check_select(g, ref, M, 5, 1, 0.05)
