@@ -301,7 +301,7 @@ def run_gpu(args, rank, world, local_rank):
     if args.k4 and DIV == 1 and DISC * M_VAR ** 3 < 2**32:
         line["k4"] = k4_run(local_rank)
     if args.k5_m >= 5 and DIV == 1 and math.comb(args.k5_m, 4) < 2**32:
-        line["k5"] = k5_run(args.k5_m, local_rank)
+        line["k5"] = k5_run(args.k5_m, args.k5_disc, local_rank)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -377,11 +377,11 @@ def k4_run(device: int):
             "paper_context": "Table 2 of the paper: 4D, 30 discretisations, Madelon 2000 x 500 on a Tesla K80: 456 s"}
 
 
-def k5_run(m: int, device: int):
-    """One k = 5 scan, one discretisation, of the first m variables of the
-    bench data's generator (madelon-shaped, 2000 samples, 2 classes): C(m, 5)
-    quintuple evaluations, timed with CUDA events after a warm-up on a
-    40-variable subset."""
+def k5_run(m: int, n_disc: int, device: int):
+    """One k = 5 scan with n_disc discretisations of the bench data's
+    generator with m variables (madelon-shaped, 2000 samples, 2 classes):
+    C(m, 5) x n_disc quintuple evaluations, timed with CUDA events after a
+    warm-up on a 40-variable subset."""
     import torch
     from paper_1811_00631_gb300 import mdfs, synth
     dev = torch.device("cuda", device)
@@ -392,14 +392,15 @@ def k5_run(m: int, device: int):
     stream = torch.cuda.current_stream(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    mdfs.max_ig(x, y, 5, DIV, 1, RANGE, XI, 5)
+    mdfs.max_ig(x, y, 5, DIV, n_disc, RANGE, XI, 5)
     b.record(stream)
     b.synchronize()
     s = a.elapsed_time(b) / 1e3
-    evals = math.comb(m, 5)
-    return {"workload": f"madelon-shaped parity data N={N_OBJ} M={m}, k=5, D=1, c={DIV + 1}",
+    evals = math.comb(m, 5) * n_disc
+    return {"workload": f"madelon-shaped parity data N={N_OBJ} M={m}, k=5, D={n_disc}, c={DIV + 1}",
             "s": s, "evals_per_s": evals / s,
-            "paper_context": "Table 1 of the paper: 5D, 1 discretisation, Madelon 2000 x 500: 1 h on the GPU"}
+            "paper_context": "Madelon 2000 x 500 at 5D on the paper's GPU: 1 h with 1 discretisation (Table 1), "
+                             "42 h with 30 (Table 2)"}
 
 
 def serving_run(n_jobs: int, device: int):
@@ -503,7 +504,8 @@ def main():
     ap.add_argument("--k4", type=int, default=1, help="time one k = 4 scan of the bench data (0: skip)")
     ap.add_argument("--k5-m", type=int, default=200,
                     help="variables of the timed one-discretisation k = 5 scan (0: skip; 500 = the "
-                         "madelon-shaped 5D case, about 45 s)")
+                         "madelon-shaped 5D case, about 19 s per discretisation)")
+    ap.add_argument("--k5-disc", type=int, default=1, help="discretisations of the timed k = 5 scan")
     ap.add_argument("--select-reps", type=int, default=3,
                     help="timed calls of the selection pipeline per k (0: skip)")
     ap.add_argument("--batched", action="store_true", help="run the batched k=2 workload instead")
