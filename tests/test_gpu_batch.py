@@ -28,7 +28,8 @@ def _jobs(N, n_folds, n_perms, seed):
 
 
 @pytest.mark.parametrize("k,div,M,N,D", [(1, 2, 40, 300, 3), (2, 1, 70, 256, 2), (2, 2, 45, 333, 2),
-                                        (3, 1, 140, 200, 2), (3, 2, 24, 150, 1)])
+                                        (3, 1, 140, 200, 2), (3, 2, 24, 150, 1), (4, 1, 40, 300, 2),
+                                        (5, 1, 24, 200, 2)])
 def test_batch_equals_jobs_one_by_one(cuda, k, div, M, N, D):
     torch = cuda
     from paper_1811_00631_gb300 import mdfs
