@@ -54,6 +54,7 @@ struct Workspace {
     Buffer items5;                                           // k = 5 work items
     Buffer items3t, t3c, t3s;                                // triple tables (k = 4, 5)
     Buffer t4c, t4s;                                         // quadruple tables (k = 5)
+    Buffer tabw;                                             // wide-layout f tables (k = 4, 5)
     Buffer keys5, kdisc;                                     // k = 5 per-discretisation keys, best discretisation
     bool k5_wide = false;                                    // keys hold (IG, rank) and kdisc the discretisation
     Buffer ekeys, evals, ecnt, erk, erv;                     // interesting-tuple table and its records
@@ -70,7 +71,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv};
+                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -368,6 +369,12 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
 
     ws->k5_wide = false;
     MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
+    const long long* tabw = nullptr;  // wide-layout tables of the packed-count kernels (k = 4, 5)
+    if (k >= 4) {
+        MDFS_ENSURE(ws, tabw, (size_t)kWideTab * sizeof(long long));
+        MDFS_LAUNCH("ftable_wide", st, launch_ftable_wide(b0, b1, (long long*)ws->tabw.p, st));
+        tabw = (const long long*)ws->tabw.p;
+    }
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
     const EmitTable em = emit ? *emit : EmitTable();
@@ -523,12 +530,12 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
                                                    (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
-            MDFS_LAUNCH("t3", st, launch_t3(planes, g, M, d0, nn, (const int2*)ws->items3t.p, ws->n_items3t, tab, cnt1,
+            MDFS_LAUNCH("t3", st, launch_t3(planes, g, M, d0, nn, (const int2*)ws->items3t.p, ws->n_items3t, tabw, cnt1,
                                             (const int*)ws->cnt2.p, (uint32_t*)ws->t3c.p, (long long*)ws->t3s.p,
                                             st));
             int lo = 0;
             const int cnt = share(ws->n_items4, &lo);
-            MDFS_LAUNCH("k4", st, launch_k4(planes, g, M, d0, nn, (const int2*)ws->items4.p + lo, cnt, tab, cnt1,
+            MDFS_LAUNCH("k4", st, launch_k4(planes, g, M, d0, nn, (const int2*)ws->items4.p + lo, cnt, tabw, cnt1,
                                             (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
                                             (const long long*)ws->t3s.p, keys, st, em));
         }
@@ -581,17 +588,17 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr,
                                                    (long long*)ws->sh2.p, (int*)ws->cnt2.p, nullptr, 0, st));
-            MDFS_LAUNCH("t3", st, launch_t3(planes, g, M, d0, nn, (const int2*)ws->items3t.p, ws->n_items3t, tab, cnt1,
+            MDFS_LAUNCH("t3", st, launch_t3(planes, g, M, d0, nn, (const int2*)ws->items3t.p, ws->n_items3t, tabw, cnt1,
                                             (const int*)ws->cnt2.p, (uint32_t*)ws->t3c.p, (long long*)ws->t3s.p,
                                             st));
-            MDFS_LAUNCH("t4", st, launch_t4(planes, g, M, d0, nn, (const int2*)ws->items4.p, ws->n_items4, tab, cnt1,
+            MDFS_LAUNCH("t4", st, launch_t4(planes, g, M, d0, nn, (const int2*)ws->items4.p, ws->n_items4, tabw, cnt1,
                                             (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
                                             (const long long*)ws->t3s.p, (uint32_t*)ws->t4c.p, (long long*)ws->t4s.p,
                                             st));
             int lo = 0;
             const int cnt = share(ws->n_items5, &lo);
             if (!wide) {
-                MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
+                MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tabw, cnt1,
                                                 (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
                                                 (const uint32_t*)ws->t4c.p, (const long long*)ws->t4s.p, keys, 0,
                                                 true, st, em));
@@ -600,7 +607,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                 // into (keys, kdisc) in discretisation order
                 unsigned long long* k5 = (unsigned long long*)ws->keys5.p;
                 MDFS_CUDA_TRY(cudaMemsetAsync(k5, 0, (size_t)nn * M * sizeof(unsigned long long), st));
-                MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tab, cnt1,
+                MDFS_LAUNCH("k5", st, launch_k5(planes, g, M, d0, nn, (const int2*)ws->items5.p + lo, cnt, tabw, cnt1,
                                                 (const int*)ws->cnt2.p, (const uint32_t*)ws->t3c.p,
                                                 (const uint32_t*)ws->t4c.p, (const long long*)ws->t4s.p, k5, M,
                                                 false, st, em));

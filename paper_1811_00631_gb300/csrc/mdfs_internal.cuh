@@ -81,6 +81,11 @@ cudaError_t launch_gather_job(const void* x, int dtype, const uint8_t* y, int N,
 // int64 fixed-point tables T0[n] = f(n + b0), T1[n] = f(n + b1), TB[n] = f(n + b0 + b1),
 // n = 0..N, f(t) = t ln t; laid out as [3][N + 1].
 cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStream_t st);
+// f tables of the packed-count kernels (t3, k4, k5): f(n + b0) at [0, 2^16),
+// f(n + b1) at [2^16, 2^17), f(n + b0 + b1) at [2^17, 2^18), so that any two
+// 16-bit class counts index inside the table.
+constexpr int kWideTab = 1 << 18;
+cudaError_t launch_ftable_wide(double b0, double b1, long long* tab, cudaStream_t st);
 
 // One CTA per variable: sort, thresholds, and codes and/or class-sorted bit planes.
 // planes: [D][M][c-1][Ws] u32 (NULL = skip); codes: [D][M][N] u8 (NULL = skip);

@@ -93,10 +93,7 @@ __global__ void __launch_bounds__(kThreads, 2) k4_kernel(const uint32_t* __restr
     const Staging z = make_staging(g.W0, g.W1);
     const int nchunk = (z.Wst + kWC - 1) / kWC;
     Tabs tb;
-    tb.tab = tab;
-    tb.np1 = g.N + 1;
-    tb.N0 = g.N0;
-    tb.N1 = g.N1;
+    tb.tab = tab;  // wide layout
     const uint32_t NC = pack2(g.N0, g.N1);
     const Rank3 r3 = make_rank3(M);
     const uint32_t* T3c = t3c + (size_t)dl * ((size_t)r3.top + 1);

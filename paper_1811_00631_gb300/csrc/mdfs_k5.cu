@@ -110,10 +110,7 @@ __global__ void __launch_bounds__(kThreads, 2) k5_kernel(const uint32_t* __restr
     const int nchunk = (z.Wst + kWC - 1) / kWC;
     keys += (size_t)dl * keys_stride;
     Tabs tb;
-    tb.tab = tab;
-    tb.np1 = g.N + 1;
-    tb.N0 = g.N0;
-    tb.N1 = g.N1;
+    tb.tab = tab;  // wide layout
     const uint32_t NC = pack2(g.N0, g.N1);
     const Rank3 r3 = make_rank3(M);
     const Rank4 r4 = make_rank4(M);

@@ -28,17 +28,16 @@ __device__ __forceinline__ void moebius_packed(uint32_t (&n)[1 << L]) {
             if (!(m & (1 << j))) n[m] -= n[m | (1 << j)];
 }
 
-// Lookup geometry of the f(n + beta) tables: T0 at [0, N], T1 at [N+1, 2N+1],
-// TB at [2N+2, 3N+2]; class sizes clamp the indices (a count never exceeds its
-// class size, so the clamp only keeps every read inside the tables).
+// The f(n + beta) tables in the wide layout (launch_ftable_wide): f(n + b0) at
+// [0, 2^16), f(n + b1) at [2^16, 2^17), f(n + b0 + b1) at [2^17, 2^18), so
+// that every packed word indexes inside the tables.
 struct Tabs {
     const long long* tab;
-    int np1, N0, N1;
 };
 // one voxel's f(n0+n1+b0+b1) - f(n0+b0) - f(n1+b1)
 __device__ __forceinline__ long long voxel_sh(uint32_t v, const Tabs& t) {
-    const int n0 = min((int)(v & kPackLo), t.N0), n1 = min((int)(v >> 16), t.N1);
-    return __ldg(t.tab + 2 * t.np1 + n0 + n1) - __ldg(t.tab + n0) - __ldg(t.tab + t.np1 + n1);
+    const uint32_t n0 = v & kPackLo, n1 = v >> 16;
+    return __ldg(t.tab + (1u << 17) + n0 + n1) - __ldg(t.tab + n0) - __ldg(t.tab + (1u << 16) + n1);
 }
 template <int L>
 __device__ __forceinline__ long long sh_packed(const uint32_t (&n)[1 << L], const Tabs& t) {

@@ -178,6 +178,24 @@ cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStrea
     return cudaGetLastError();
 }
 
+// The same f(n + beta) values in the fixed layout of the packed-count kernels:
+// n + b0 at [0, 2^16), n + b1 at [2^16, 2^17), n + b0 + b1 at [2^17, 2^18).
+__global__ void ftable_wide_kernel(double b0, double b1, long long* __restrict__ tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (1 << 18)) return;
+    const int which = i < (1 << 16) ? 0 : (i < (1 << 17) ? 1 : 2);
+    const int n = which == 2 ? i - (1 << 17) : (which == 1 ? i - (1 << 16) : i);
+    const double beta = which == 0 ? b0 : (which == 1 ? b1 : b0 + b1);
+    const double t = (double)n + beta;
+    const double f = t > 0.0 ? t * log(t) : 0.0;
+    tab[i] = __double2ll_rn(f * kFxScale);
+}
+
+cudaError_t launch_ftable_wide(double b0, double b1, long long* tab, cudaStream_t st) {
+    ftable_wide_kernel<<<(1 << 18) / 256, 256, 0, st>>>(b0, b1, tab);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Discretiser: one CTA per variable.
 //   1. bitonic sort of the column in shared memory (padded with +inf),

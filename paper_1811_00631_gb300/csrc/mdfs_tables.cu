@@ -77,10 +77,7 @@ __global__ void __launch_bounds__(kThreads) t3_kernel(const uint32_t* __restrict
     }
 
     Tabs tb;
-    tb.tab = tab;
-    tb.np1 = g.N + 1;
-    tb.N0 = g.N0;
-    tb.N1 = g.N1;
+    tb.tab = tab;  // wide layout
     const uint32_t NC = pack2(g.N0, g.N1);
     auto single = [&](int v) -> uint32_t {
         const int* p = cnt1 + ((size_t)d * M + v) * 2;
