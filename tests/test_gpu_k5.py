@@ -39,6 +39,20 @@ def test_k5_matches_oracle(cuda, M, N, D):
         assert np.array_equal(a, b)
 
 
+def test_k5_int8_input(cuda):
+    """int8 variables (ties at the cut points go to the upper class) give the
+    oracle's result on the same int8 values."""
+    from paper_1811_00631_gb300 import synth
+    rng = np.random.default_rng(8)
+    M, N, D = 8, 700, 2
+    x8 = synth.to_int8(rng.standard_normal((M, N)), scale=6.0)
+    y = ((x8[1] > 0) ^ (x8[4] > 2) ^ (x8[6] > -1) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x8.astype(np.float32), 1, D, 0.5, 41)
+    ref = oracle.max_ig(codes, y, 2, 5, 0.25)
+    g = _gpu_max_ig(cuda, x8, y, 5, 1, D, 0.5, 0.25, 41)
+    _check(codes, y, 2, 5, 0.25, *g, ref, range(M))
+
+
 def test_k5_several_tiles_sampled(cuda):
     """M = 72: e and f span several 32-wide tiles (and the f-tile boundary
     above the diagonal tile); a sample of variables is checked against the

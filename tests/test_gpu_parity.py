@@ -325,10 +325,11 @@ def test_repeatable_and_stream_ordered(cuda):
         assert torch.equal(u, v)
 
 
-@pytest.mark.parametrize("M,N,D", [(4, 97, 1), (5, 300, 2), (14, 300, 2), (9, 2100, 1)])
+@pytest.mark.parametrize("M,N,D", [(4, 97, 1), (5, 300, 2), (14, 300, 2), (9, 2100, 1), (8, 4500, 1), (6, 40, 2)])
 def test_k4_matches_oracle(cuda, M, N, D):
-    """k = 4 (two classes): every variable against the brute-force oracle; N up
-    to 2100 spans several 32-word chunks per class; M = 4 is one quadruple."""
+    """k = 4 (two classes): every variable against the brute-force oracle.
+    M = 4 is one quadruple; N = 4500 needs two staged chunks of 128 words;
+    N = 40 leaves most of a 32-sample word empty."""
     rng = np.random.default_rng(M * 100 + N)
     x = rng.standard_normal((M, N)).astype(np.float32)
     y = ((x[0] > 0) ^ (x[1] > 0) ^ (x[M - 1] > 0.2) ^ (rng.random(N) < 0.1)).astype(np.uint8)
