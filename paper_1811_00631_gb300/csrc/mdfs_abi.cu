@@ -220,6 +220,30 @@ int check_k5(int M, int c, int D, int N, bool single_key = false) {
     return MDFS_OK;
 }
 
+// Arguments shared by every scan entry point (k, M variables, divisions, N,
+// discretizations, range, pc_xi) and the index limits of each k's argmax key;
+// shard_keys: the single-word keys of mdfs_max_ig_shard (k = 5 limit).
+int check_scan_args(int k, int M, int divisions, int N, int D, double range, double pc_xi, bool shard_keys = false) {
+    const int c = divisions + 1;
+    int rc = 0;
+    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
+    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
+    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
+    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
+    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
+    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
+    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    const unsigned long long m = (unsigned long long)M, d = (unsigned long long)D;
+    if (k == 2 && d * m >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
+    if (k == 3 && d * m * m >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
+    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
+    if (k == 4 && d * m * m * m >= (1ull << 32))
+        return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
+    if (k == 5 && (rc = check_k5(M, c, D, N, shard_keys))) return rc;
+    return MDFS_OK;
+}
+
 // discretisation of each key when the k = 5 scan kept per-discretisation keys
 const int* wide_disc(const Workspace* ws) { return ws->k5_wide ? (const int*)ws->kdisc.p : nullptr; }
 
@@ -746,22 +770,9 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     g_launches = 0;
     int rc = check_data(data, true);
     if (rc) return rc;
-    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
-    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
-    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
-    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
-    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
-    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
-    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
-    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    const int N = data->N, M = data->M, D = discretizations;
+    if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi))) return rc;
     if (!ig) return fail(MDFS_EINVAL, "ig is NULL");
-    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
-    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
-    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
-    if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
-    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
 
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
@@ -805,23 +816,10 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     g_launches = 0;
     int rc = check_data(data, true);
     if (rc) return rc;
-    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    const int N = data->N, M = data->M, D = discretizations;
     if (n_jobs < 1) return fail(MDFS_EINVAL, "n_jobs = %d < 1", n_jobs);
-    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
-    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
-    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
-    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
-    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
-    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
-    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi))) return rc;
     if (!ig) return fail(MDFS_EINVAL, "ig is NULL");
-    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
-    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
-    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
-    if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
-    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
 
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
@@ -894,23 +892,10 @@ int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretiz
     g_launches = 0;
     int rc = check_data(data, true);
     if (rc) return rc;
-    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    const int N = data->N, M = data->M, D = discretizations;
     if (n_shards < 1 || shard < 0 || shard >= n_shards) return fail(MDFS_EINVAL, "shard %d of %d", shard, n_shards);
-    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
-    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
-    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
-    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
-    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
-    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
-    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi, true))) return rc;
     if (!keys_out) return fail(MDFS_EINVAL, "keys is NULL");
-    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
-    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
-    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
-    if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
-    if (k == 5 && (rc = check_k5(M, c, D, N, true))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -1086,25 +1071,12 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
     const int Mx = M + n_contrast;
     if (n_contrast < 1 || Mx > 65535)
         return fail(MDFS_EINVAL, "n_contrast = %d: need n_contrast >= 1 and M + n_contrast <= 65535", n_contrast);
-    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
-    if (Mx < k) return fail(MDFS_EINVAL, "M + n_contrast = %d smaller than k = %d", Mx, k);
-    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
-    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
-    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
-    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
-    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    if ((rc = check_scan_args(k, Mx, divisions, N, D, range, pc_xi))) return rc;
     if (!(level > 0.0 && level < 1.0)) return fail(MDFS_EINVAL, "level must lie in (0, 1)");
     if (p_adjust_method < MDFS_ADJUST_NONE || p_adjust_method > MDFS_ADJUST_BY)
         return fail(MDFS_EINVAL, "unknown p_adjust_method %d", p_adjust_method);
     if (!ig || !p_values || !adjusted || !relevant)
         return fail(MDFS_EINVAL, "ig, p_values, adjusted and relevant must not be NULL");
-    if (k == 2 && (unsigned long long)D * Mx >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
-    if (k == 3 && (unsigned long long)D * Mx * Mx >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * (M + n_contrast)^2 must stay below 2^32 for k = 3");
-    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
-    if (k == 4 && (unsigned long long)D * Mx * Mx * Mx >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * (M + n_contrast)^3 must stay below 2^32 for k = 4");
-    if (k == 5 && (rc = check_k5(Mx, c, D, N))) return rc;
     int df = c - 1;
     for (int j = 1; j < k; ++j) df *= c;
 
@@ -1178,25 +1150,12 @@ int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int dis
     g_launches = 0;
     int rc = check_data(data, true);
     if (rc) return rc;
-    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
-    if (k < 1 || k > 5) return fail(MDFS_EINVAL, "k = %d outside [1, 5]", k);
-    if (M < k) return fail(MDFS_EINVAL, "M = %d smaller than k = %d", M, k);
-    if (divisions < 1 || c > kMaxC) return fail(MDFS_EINVAL, "divisions = %d outside [1, %d]", divisions, kMaxC - 1);
-    if (N < c) return fail(MDFS_EINVAL, "N = %d smaller than the number of classes %d", N, c);
-    if (D < 1 || D > kMaxD) return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", D, kMaxD);
-    if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
-    if (!(pc_xi > 0.0 && pc_xi < 1.0)) return fail(MDFS_EINVAL, "pc_xi must lie in (0, 1)");
+    const int N = data->N, M = data->M, D = discretizations;
+    if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi))) return rc;
     if (!(ig_threshold > -1e9 && ig_threshold < 1e9)) return fail(MDFS_EINVAL, "ig_threshold must be finite");
     if (capacity < 1 || capacity > (1 << 22)) return fail(MDFS_EINVAL, "capacity = %d outside [1, 2^22]", capacity);
     if (!var || !ig || !count || (k > 1 && !tuples))
         return fail(MDFS_EINVAL, "var, ig, tuples (k > 1) and count must not be NULL");
-    if (k == 2 && (unsigned long long)D * M >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
-    if (k == 3 && (unsigned long long)D * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
-    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
-    if (k == 4 && (unsigned long long)D * M * M * M >= (1ull << 32))
-        return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
-    if (k == 5 && (rc = check_k5(M, c, D, N))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;

@@ -50,18 +50,6 @@ __device__ __noinline__ void emit_roles5(EmitTable t, int a, int b, int c, int e
     if (gf >= t.thr_fx) emit_insert(t, emit_key5(f, a, b, c, e), pack_key(fx_to_float(gf), (uint32_t)d));
 }
 
-// Asynchronous global -> shared copies of `bytes` (4 or 8); a copy with
-// valid == false writes zeros and reads nothing.
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // the a part of one e or f row: n_ax (two class counts), n_abx, n_acx, n_abcx, SH(a,b,c,x)
 struct RowA {
