@@ -61,3 +61,27 @@ def test_argument_errors_need_no_gpu(lib):
     assert rc == -1 and b"pc_xi" in lib.mdfs_last_error()
     rc = lib.mdfs_max_ig(ctypes.byref(d), 2, 9, 1, 0.0, 0.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
     assert rc == -1 and b"divisions" in lib.mdfs_last_error()
+
+
+def test_k5_limits_need_no_gpu(lib):
+    """k = 5 argument limits: two classes per variable, C(M, 4) < 2^32, and for
+    the single-word keys of a shard also discretizations * C(M, 4) < 2^32."""
+    import ctypes
+    from paper_1811_00631_gb300 import mdfs
+    import numpy as np
+
+    def call(M, divisions, D, shard=False):
+        x = np.zeros((M, 10), dtype=np.float32)
+        y = (np.arange(10) % 2).astype(np.uint8)
+        d = mdfs._Data(0, x.ctypes.data, y.ctypes.data, 10, M)
+        out = np.zeros(M, dtype=np.uint64 if shard else np.float32)
+        if shard:
+            return lib.mdfs_max_ig_shard(ctypes.byref(d), 5, divisions, D, 0.0, 0.25, 1, 0, 1,
+                                         ctypes.c_void_p(out.ctypes.data), None)
+        return lib.mdfs_max_ig(ctypes.byref(d), 5, divisions, D, 0.0, 0.25, 1, ctypes.c_void_p(out.ctypes.data),
+                               None, None, None)
+
+    assert call(20, 2, 1) == -1 and b"two classes" in lib.mdfs_last_error()
+    assert call(569, 1, 1) == -1 and b"C(M, 4)" in lib.mdfs_last_error()  # C(569, 4) > 2^32
+    assert call(500, 1, 2, shard=True) == -1 and b"shard" in lib.mdfs_last_error()  # 2 C(500, 4) > 2^32
+    assert call(4, 1, 1) == -1 and b"smaller than k" in lib.mdfs_last_error()
