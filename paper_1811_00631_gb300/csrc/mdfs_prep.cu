@@ -370,6 +370,61 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
             s[pos] = sidx >= 0 ? (float)xv[sidx] : __int_as_float(0x7fc00000);
         }
         __syncthreads();
+        if (planes) {
+            // one pass for both outputs: per (32 positions, discretisation, bin)
+            // two 16-byte one-hot stores and the bit-plane word of the same 32
+            // class-sorted samples (class 0 at word g, class 1 from word W0)
+            const int ngroup = tg.Kp >> 5;
+            for (int w = tid; w < ngroup * D; w += blockDim.x) {
+                const int gi = w % ngroup, d = w / ngroup;
+                const int pos0 = gi * 32;
+                int pw = -1;  // plane word of this group, if any
+                if (pos0 < tg.K0p) {
+                    if (gi < g.W0) pw = gi;
+                } else if (((pos0 - tg.K0p) >> 5) < g.W1) {
+                    pw = g.W0 + ((pos0 - tg.K0p) >> 5);
+                }
+                float xs[32];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 f = reinterpret_cast<const float4*>(s)[gi * 8 + q];
+                    xs[4 * q] = f.x;
+                    xs[4 * q + 1] = f.y;
+                    xs[4 * q + 2] = f.z;
+                    xs[4 * q + 3] = f.w;
+                }
+                for (int a = 1; a <= cm1; ++a) {
+                    const float lo = thr[d * cm1 + a - 1];
+                    const float hi = a < cm1 ? thr[d * cm1 + a] : INFINITY;
+                    uint32_t wd[8], bits = 0u;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        uint32_t b = 0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float xv_ = xs[4 * q + k];
+                            // code == a  <=>  x >= thr[a-1] and not x >= thr[a] (thresholds ascending)
+                            const bool in = xv_ >= lo && !(xv_ >= hi);
+                            b |= in ? 0x38u << (8 * k) : 0u;
+                            bits |= in ? 1u << (4 * q + k) : 0u;
+                        }
+                        wd[q] = b;
+                    }
+                    uint4* row = reinterpret_cast<uint4*>(onehot + (((size_t)d * M + v) * cm1 + (a - 1)) * tg.Kp);
+                    row[2 * gi] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                    row[2 * gi + 1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+                    if (pw >= 0) planes[(((size_t)d * M + v) * cm1 + (a - 1)) * g.Ws + pw] = bits;
+                }
+            }
+            // the padding words [W, Ws) of every plane
+            const int npad = g.Ws - g.W;
+            for (int w = tid; w < npad * D * cm1; w += blockDim.x) {
+                const int pwd = w % npad, row = w / npad;  // row = d * cm1 + (a - 1)
+                const int d = row / cm1, a1 = row % cm1;
+                planes[(((size_t)d * M + v) * cm1 + a1) * g.Ws + g.W + pwd] = 0u;
+            }
+            return;
+        }
         // one 16-byte store per (16 positions, discretisation, bin)
         const int nchunk = tg.Kp >> 4;
         for (int w = tid; w < nchunk * D; w += blockDim.x) {
