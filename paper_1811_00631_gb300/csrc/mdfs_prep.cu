@@ -200,8 +200,10 @@ cudaError_t launch_ftable_wide(double b0, double b1, long long* tab, cudaStream_
 // Discretiser: one CTA per variable.
 //   1. bitonic sort of the column in shared memory (padded with +inf),
 //   2. per discretisation: c Philox shares -> c-1 cut positions -> thresholds,
-//   3. codes (original sample order) and/or bit planes of bins 1..c-1 in the
-//      class-sorted sample order (one ballot per 32 samples).
+//   3. codes (original sample order), and bit planes of bins 1..c-1 in the
+//      class-sorted sample order: with the E4M3 one-hot rows, one pass per 32
+//      class-sorted samples writes both (the plane word from the same
+//      compares); alone, one ballot per 32 samples.
 // Share j of (v, d): w_j = W - R + floor(u_j * 2R / 2^32), W = 2^20,
 // R = round(range * 2^20), u_j = word j%4 of Philox(counter (j/4, v, d, tag),
 // key = seed).  Positions p_j = floor(N S_j / S_c) with S_j = w_0 + .. + w_{j-1},
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
             s[pos] = sidx >= 0 ? (float)xv[sidx] : __int_as_float(0x7fc00000);
         }
         __syncthreads();
-        if (planes) {
+        {
             // one pass for both outputs: per (32 positions, discretisation, bin)
             // two 16-byte one-hot stores and the bit-plane word of the same 32
             // class-sorted samples (class 0 at word g, class 1 from word W0)
@@ -413,53 +415,20 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
                     uint4* row = reinterpret_cast<uint4*>(onehot + (((size_t)d * M + v) * cm1 + (a - 1)) * tg.Kp);
                     row[2 * gi] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
                     row[2 * gi + 1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
-                    if (pw >= 0) planes[(((size_t)d * M + v) * cm1 + (a - 1)) * g.Ws + pw] = bits;
+                    if (planes && pw >= 0) planes[(((size_t)d * M + v) * cm1 + (a - 1)) * g.Ws + pw] = bits;
                 }
             }
             // the padding words [W, Ws) of every plane
-            const int npad = g.Ws - g.W;
+            const int npad = planes ? g.Ws - g.W : 0;
             for (int w = tid; w < npad * D * cm1; w += blockDim.x) {
                 const int pwd = w % npad, row = w / npad;  // row = d * cm1 + (a - 1)
                 const int d = row / cm1, a1 = row % cm1;
                 planes[(((size_t)d * M + v) * cm1 + a1) * g.Ws + g.W + pwd] = 0u;
             }
-            return;
-        }
-        // one 16-byte store per (16 positions, discretisation, bin)
-        const int nchunk = tg.Kp >> 4;
-        for (int w = tid; w < nchunk * D; w += blockDim.x) {
-            const int ch = w % nchunk, d = w / nchunk;
-            float xs[16];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 f = reinterpret_cast<const float4*>(s)[ch * 4 + q];
-                xs[4 * q] = f.x;
-                xs[4 * q + 1] = f.y;
-                xs[4 * q + 2] = f.z;
-                xs[4 * q + 3] = f.w;
-            }
-            for (int a = 1; a <= cm1; ++a) {
-                const float lo = thr[d * cm1 + a - 1];
-                const float hi = a < cm1 ? thr[d * cm1 + a] : INFINITY;
-                uint32_t wd[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t b = 0;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float xv_ = xs[4 * q + k];
-                        // code == a  <=>  x >= thr[a-1] and not x >= thr[a] (thresholds ascending)
-                        if (xv_ >= lo && !(xv_ >= hi)) b |= 0x38u << (8 * k);
-                    }
-                    wd[q] = b;
-                }
-                reinterpret_cast<uint4*>(onehot + (((size_t)d * M + v) * cm1 + (a - 1)) * tg.Kp)[ch] =
-                    make_uint4(wd[0], wd[1], wd[2], wd[3]);
-            }
         }
     }
 
-    if (planes) {
+    if (planes && !onehot) {  // planes alone: one ballot per (32 samples, discretisation, bin)
         const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
         for (int w = warp; w < g.Ws; w += nwarps) {
             int sidx = -1;
