@@ -140,3 +140,20 @@ def test_k5_select_pipeline(cuda):
     ref = oracle.select(x, y, nc, 5, 1, 1, 0.0, 0.25, seed=3)
     g = mdfs.select(x, y, nc, 5, 1, 1, 0.0, 0.25, seed=3)
     _check_select(g, ref, M, 5, 1, 0.05)
+
+
+@pytest.mark.parametrize("k,M,c", [(3, 40, 3), (4, 20, 2), (5, 12, 2)])
+def test_discretisation_chunks_give_the_same_result(cuda, monkeypatch, k, M, c):
+    """Table passes over chunks of discretisations (forced to one per chunk
+    with MDFS_PAIR_TABLE_BYTES) give exactly the single-chunk result: the
+    chunk offsets of the pair, triple and quadruple tables and of the keys."""
+    rng = np.random.default_rng(k * 10 + M)
+    N, D = 300, 4
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[0] > 0) ^ (x[M // 2] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    want = _gpu_max_ig(cuda, x, y, k, c - 1, D, 0.5, 0.25, 19)
+    monkeypatch.setenv("MDFS_PAIR_TABLE_BYTES", "1")
+    got = _gpu_max_ig(cuda, x, y, k, c - 1, D, 0.5, 0.25, 19)
+    monkeypatch.delenv("MDFS_PAIR_TABLE_BYTES")
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
