@@ -18,7 +18,9 @@
 //
 // Argmax key: index = d C(M,4) + rho(S), rho the lexicographic rank of the
 // partner set S among the 4-subsets of [0, M) (the same rank indexes the
-// quadruple tables).  The caller guarantees D C(M,4) < 2^32.
+// quadruple tables; C(M,4) < 2^32).  When D C(M,4) does not fit 32 bits the
+// caller passes per-discretisation keys [nd][M] and the index is rho alone;
+// a separate fold keeps the lowest discretisation on ties.
 #include <cuda_runtime.h>
 
 #include <algorithm>
