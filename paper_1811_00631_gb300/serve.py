@@ -62,8 +62,12 @@ class Result:
 
 
 def job_device_bytes(M: int, N: int, k: int, divisions: int, discretizations: int, x_itemsize: int = 4) -> int:
-    """Upper estimate of the device memory one job holds in its slot's workspace
-    (inputs, bit planes, one-hot operand and pair records for k = 3, tables)."""
+    """Upper estimate of the device memory one job holds in its slot's workspace,
+    following the library's allocations: inputs, entropy tables, bit planes,
+    single counts and keys; the one-hot operands of the tensor-core paths
+    (k = 2 with c <= 3, k = 3 with c = 2); and the pair, triple and quadruple
+    tables of k = 3..5, processed in chunks of discretisations that fit a 4 GB
+    table budget (at least one discretisation per chunk)."""
     c = divisions + 1
     P = c - 1
     D = discretizations
@@ -71,11 +75,22 @@ def job_device_bytes(M: int, N: int, k: int, divisions: int, discretizations: in
     kp = ((N + 127) // 128 + 1) * 128
     b = M * N * x_itemsize + N * 5 + 3 * (N + 1) * 8
     b += D * M * P * words * 4 + D * M * (P * 8 + 8) + M * 8
-    if k == 3:
-        if c == 2:
-            b += D * M * kp + D * M * M * 8
-        else:
-            b += D * M * M * (8 + P * P * 8)
+
+    def chunked(per_disc: int) -> int:
+        nd = max(1, min(D, (4 << 30) // max(per_disc, 1)))
+        return nd * per_disc
+
+    if k == 2 and c <= 3:
+        b += D * M * P * kp
+    elif k == 3 and c == 2:
+        b += 2 * D * M * kp + D * M * 16 + chunked(M * M * 8)
+    elif k == 3:
+        b += chunked(M * M * (8 + P * P * 8))
+    elif k in (4, 5):
+        per_disc = M * M * 16 + math.comb(M, 3) * 12
+        if k == 5:
+            per_disc += math.comb(M, 4) * 12 + M * 8
+        b += chunked(per_disc) + (1 << 21)
     return int(b * 1.15) + (1 << 20)
 
 

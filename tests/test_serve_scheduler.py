@@ -97,3 +97,16 @@ def test_device_byte_estimate_grows_with_the_work():
     c = serve.job_device_bytes(1000, 2000, 3, 1, 30)
     assert a < b < c
     assert b > 30 * 500 * 500 * 8  # pair records of the k = 3 path
+
+
+def test_device_byte_estimate_covers_the_higher_order_tables():
+    """k = 4 holds the triple tables of a chunk of discretisations (chunks fit
+    4 GB, at least one discretisation); k = 5 also the quadruple tables, which
+    alone are 12 C(M,4) bytes per discretisation."""
+    import math
+    k4 = serve.job_device_bytes(500, 2000, 4, 1, 30)
+    k5 = serve.job_device_bytes(500, 2000, 5, 1, 1)
+    assert k4 > 12 * math.comb(500, 3) * 10  # at least ten discretisations of triple tables
+    assert k4 < 8 << 30                      # but chunked, not all thirty at once
+    assert k5 > 12 * math.comb(500, 4)       # one discretisation of quadruple tables
+    assert serve.job_device_bytes(200, 2000, 2, 1, 30) > 30 * 200 * 2048  # the k = 2 one-hot operand
