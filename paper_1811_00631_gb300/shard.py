@@ -60,3 +60,68 @@ def unpack(keys: np.ndarray):
     ig[keys == 0] = np.nan
     index = ((~keys) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     return ig, index
+
+
+# --- checkpointed (resumable) sharded scan ------------------------------------
+def _fingerprint(params: dict) -> str:
+    import hashlib
+    import json
+    return hashlib.sha256(json.dumps(params, sort_keys=True).encode()).hexdigest()
+
+
+def run_resumable(scan_shard, n_shards: int, checkpoint_dir: str, params: dict) -> np.ndarray:
+    """Merged keys of a scan split into `n_shards` shards, resumable.
+
+    ``scan_shard(s)`` returns the uint64 keys of shard s (e.g. a closure over
+    ``mdfs.max_ig_shard``).  Each finished shard's keys are written to
+    ``checkpoint_dir/shard_<s>.npy`` (written to a temporary name, then
+    renamed, so a file that exists is complete) next to a fingerprint of
+    ``params`` (the scan's arguments and a digest of its data); a rerun with
+    the same fingerprint scans only the shards without a file, and one with a
+    different fingerprint refuses to mix results.  Because the merge is an
+    element-wise maximum, the order in which shards finish does not matter.
+    """
+    import json
+    import os
+    os.makedirs(checkpoint_dir, exist_ok=True)
+    fp = _fingerprint(dict(params, n_shards=n_shards))
+    meta = os.path.join(checkpoint_dir, "scan.json")
+    if os.path.exists(meta):
+        with open(meta) as f:
+            old = json.load(f)
+        if old.get("fingerprint") != fp:
+            raise ValueError(f"{checkpoint_dir} holds shards of a different scan")
+    else:
+        tmp = meta + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump({"fingerprint": fp, "params": params, "n_shards": n_shards}, f)
+        os.replace(tmp, meta)
+    keys = []
+    for s in range(n_shards):
+        path = os.path.join(checkpoint_dir, f"shard_{s}.npy")
+        if os.path.exists(path):
+            keys.append(np.load(path))
+            continue
+        k = np.asarray(scan_shard(s), dtype=np.uint64)
+        tmp = path + ".tmp.npy"
+        np.save(tmp, k)
+        os.replace(tmp, path)
+        keys.append(k)
+    return merge(keys)
+
+
+def max_ig_resumable(x, y, k: int, divisions: int, discretizations: int, range_: float, pc_xi: float, seed: int,
+                     n_shards: int, checkpoint_dir: str):
+    """``mdfs.max_ig`` computed shard by shard with the shards' keys kept in
+    ``checkpoint_dir`` (see ``run_resumable``); returns (ig, tuples, disc) as
+    numpy arrays, identical to the unsharded scan."""
+    import hashlib
+    from . import mdfs
+    xh = x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)
+    yh = y.detach().cpu().numpy() if hasattr(y, "detach") else np.asarray(y)
+    digest = hashlib.sha256(np.ascontiguousarray(xh).tobytes() + np.ascontiguousarray(yh).tobytes()).hexdigest()
+    params = dict(k=k, divisions=divisions, discretizations=discretizations, range=range_, pc_xi=pc_xi, seed=seed,
+                  shape=list(xh.shape), dtype=str(xh.dtype), data=digest)
+    keys = run_resumable(lambda s: mdfs.max_ig_shard(x, y, k, divisions, discretizations, range_, pc_xi, seed, s,
+                                                     n_shards), n_shards, checkpoint_dir, params)
+    return mdfs.decode_keys(keys, k)

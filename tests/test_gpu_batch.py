@@ -87,3 +87,16 @@ def test_sharded_scan_merges_to_the_unsharded_result(cuda, k, div, M, N):
     got = mdfs.decode_keys(keys, k)
     for a, b in zip(got, want):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_resumable_scan_equals_the_unsharded_scan(cuda, tmp_path, k):
+    """The checkpointed sharded scan, first run and a resumed run that finds
+    every shard on disk, decode to exactly the unsharded result."""
+    from paper_1811_00631_gb300 import mdfs, shard
+    ds = synth.xor_pairs(N=300, M=30 if k == 5 else 120, n_pairs=3, seed=k)
+    want = mdfs.max_ig(ds.x, ds.y, k, 1, 2, 0.5, 0.25, 8)
+    for _ in range(2):
+        got = shard.max_ig_resumable(ds.x, ds.y, k, 1, 2, 0.5, 0.25, 8, 4, str(tmp_path))
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)

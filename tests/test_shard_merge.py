@@ -97,3 +97,31 @@ def test_gloo_allreduce_merge(tmp_path):
     g, i = shard.unpack(k0)
     for v in range(M):
         assert (g[v], i[v]) == (ref[v][0], ref[v][1])
+
+
+def test_resumable_scan_skips_finished_shards_and_refuses_other_scans(tmp_path):
+    """An interrupted checkpointed scan resumes with the missing shards only,
+    and its merge equals the merge of a run without interruption."""
+    rng = np.random.default_rng(3)
+    n_shards, M = 5, 40
+    per_shard = [shard.pack(rng.standard_normal(M).astype(np.float32), rng.integers(0, 2**31, M)) for _ in range(n_shards)]
+    want = shard.merge(per_shard)
+    calls = []
+
+    def flaky(s):
+        calls.append(s)
+        if s == 3 and calls.count(3) == 1:
+            raise RuntimeError("interrupted")
+        return per_shard[s]
+
+    params = {"k": 2, "seed": 1}
+    with pytest.raises(RuntimeError):
+        shard.run_resumable(flaky, n_shards, str(tmp_path), params)
+    assert calls == [0, 1, 2, 3]
+    got = shard.run_resumable(flaky, n_shards, str(tmp_path), params)
+    assert calls == [0, 1, 2, 3, 3, 4]  # only the unfinished shards ran again
+    assert np.array_equal(got, want)
+    again = shard.run_resumable(lambda s: pytest.fail("nothing left to scan"), n_shards, str(tmp_path), params)
+    assert np.array_equal(again, want)
+    with pytest.raises(ValueError):
+        shard.run_resumable(flaky, n_shards, str(tmp_path), {"k": 3, "seed": 1})
