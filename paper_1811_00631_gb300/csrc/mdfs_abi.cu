@@ -1,5 +1,6 @@
 // Host side of the MDFS C ABI (include/mdfs.h): argument checks, input staging,
 // per-(device, stream) workspaces and the launch sequence of the scan.
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -189,7 +190,9 @@ cudaEvent_t prof_event() {
             }                                                                                       \
         }                                                                                           \
         if (_prof) cudaEventRecord(_e0, (stream));                                                  \
+        nvtxRangePushA(name); /* host-side range per stage, seen by NVTX-aware profilers */       \
         cudaError_t _e = (expr);                                                                    \
+        nvtxRangePop();                                                                             \
         if (_prof) {                                                                                \
             cudaEventRecord(_e1, (stream));                                                         \
             std::lock_guard<std::mutex> _l(g_prof_mu);                                              \
