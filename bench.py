@@ -500,7 +500,7 @@ def main():
                     help="DRAM bytes (read + write) per full-size k=3 launch from an ncu capture of the "
                          "current kernel (profiles/launches_mdfs_scan_parity_N2000_M500_k2k3_D30.md)")
     ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=2)")
-    ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving-mix run (0: skip)")
+    ap.add_argument("--serving-jobs", type=int, default=512, help="jobs of the serving-mix run (0: skip)")
     ap.add_argument("--k4", type=int, default=1, help="time one k = 4 scan of the bench data (0: skip)")
     ap.add_argument("--k5-m", type=int, default=200,
                     help="variables of the timed one-discretisation k = 5 scan (0: skip; 500 = the "
