@@ -1,11 +1,15 @@
 """The serving loop on the GPU: a Poisson stream of mixed jobs (k = 1..3, mixed
 N, M, divisions, float32 and int8), admitted into concurrent slots; every
-result equals the same job run alone, bit for bit, and jobs overlap."""
+result equals the same job run alone, bit for bit, jobs overlap, and the jobs
+small enough for the FP64 oracle match it (IG within 1e-4 + 1e-5 |IG|; the
+fit's p-values equal the oracle fit of the same IG)."""
+import math
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1811_00631_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -51,3 +55,18 @@ def test_mix_equals_alone_and_overlaps(cuda):
         assert r.latency > 0
     st = serve.latency_stats(results)
     assert st["p99_s"] >= st["p50_s"] > 0
+    checked = 0
+    for sp, job, r in zip(specs, jobs, results):
+        M, N = job.x.shape
+        if math.comb(M, job.k) * job.discretizations * N > 3e8:
+            continue
+        c = job.divisions + 1
+        codes = oracle.discretize(np.asarray(job.x, dtype=np.float32), job.divisions, job.discretizations, job.range_,
+                                  job.seed)
+        ref = oracle.max_ig(codes, job.y, c, job.k, job.pc_xi)
+        assert np.all(np.abs(r.ig - ref["ig"]) <= 1e-4 + 1e-5 * np.abs(ref["ig"])), f"job {job.tag}"
+        if r.p_values is not None:
+            p_ref, _, _ = oracle.ig_lim(r.ig.astype(np.float64), job.k, job.divisions, alpha=job.alpha)
+            assert np.allclose(r.p_values, p_ref, rtol=1e-9, atol=1e-12), f"job {job.tag}"
+        checked += 1
+    assert checked >= 5
