@@ -61,6 +61,14 @@ def test_argument_errors_need_no_gpu(lib):
     assert rc == -1 and b"pc_xi" in lib.mdfs_last_error()
     rc = lib.mdfs_max_ig(ctypes.byref(d), 2, 9, 1, 0.0, 0.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
     assert rc == -1 and b"divisions" in lib.mdfs_last_error()
+    rc = lib.mdfs_max_ig(ctypes.byref(d), 2, 1, 1025, 0.0, 0.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None, None)
+    assert rc == -1 and b"discretizations" in lib.mdfs_last_error()
+    # N beyond the discretiser's limit (32768) and below 2; M = 0
+    for n, m in [(32769, 4), (1, 4), (10, 0)]:
+        dd = mdfs._Data(0, x.ctypes.data, y.ctypes.data, n, m)
+        rc = lib.mdfs_max_ig(ctypes.byref(dd), 2, 1, 1, 0.0, 0.5, 1, ctypes.c_void_p(ig.ctypes.data), None, None,
+                             None)
+        assert rc == -1 and (b"N = " in lib.mdfs_last_error() or b"M = " in lib.mdfs_last_error())
 
 
 def test_k5_limits_need_no_gpu(lib):

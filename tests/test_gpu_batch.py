@@ -100,3 +100,55 @@ def test_resumable_scan_equals_the_unsharded_scan(cuda, tmp_path, k):
         got = shard.max_ig_resumable(ds.x, ds.y, k, 1, 2, 0.5, 0.25, 8, 4, str(tmp_path))
         for a, b in zip(got, want):
             assert np.array_equal(a, b)
+
+
+def test_batched_full_size_sampled(cuda):
+    """The batched workload at full size, in the launch that bench.py --batched
+    times: N = 1000 x M = 20000 (100 planted XOR pairs), 3 classes, 10
+    discretisations, 16 bootstrap folds x 4 label permutations = 64 jobs in one
+    call.  Sampled jobs and variables are compared with the FP64 oracle (IG
+    within 1e-4 + 1e-5 |o|; an argmax that differs must be an equally good
+    maximiser), one job with the single-job scan bit for bit, and job 0 (the
+    unpermuted labels) must name the planted partner of every XOR member."""
+    torch = cuda
+    from paper_1811_00631_gb300 import mdfs
+    N, M, D, div, r, xi, seed = 1000, 20000, 10, 2, 0.5, 0.25, 1
+    c = div + 1
+    ds = synth.xor_pairs(N=N, M=M, n_pairs=100, seed=4)
+    si, yp = _jobs(N, 16, 4, seed=5)
+    xt, yt = torch.from_numpy(ds.x).cuda(), torch.from_numpy(ds.y).cuda()
+    ig, tu, di = mdfs.max_ig_batch(xt, yt, torch.from_numpy(si).cuda(), torch.from_numpy(yp).cuda(), k=2,
+                                   divisions=div, discretizations=D, range_=r, pc_xi=xi, seed=seed)
+    torch.cuda.synchronize()
+    ig, tu, di = ig.cpu().numpy(), tu.cpu().numpy(), di.cpu().numpy()
+    assert ig.shape == (64, M) and tu.shape == (64, M, 1) and di.shape == (64, M)
+
+    pairs = ds.info["pairs"]
+    found = sum(int(tu[0, a, 0] == b) + int(tu[0, b, 0] == a) for a, b in pairs)
+    assert found == 2 * len(pairs), f"job 0 names {found} of {2 * len(pairs)} planted partners"
+
+    rng = np.random.default_rng(17)
+    for j in (0, 29, 63):
+        xj = np.ascontiguousarray(ds.x[:, si[j]])
+        yj = ds.y[yp[j][si[j]]]
+        codes = oracle.discretize(xj, div, D, r, seed)
+        a, b = pairs[rng.integers(len(pairs))]
+        variables = np.array(sorted({int(a), int(b), *rng.choice(M, 6, replace=False).tolist()}), np.int32)
+        ref = oracle.max_ig(codes, yj, c, 2, xi, variables=variables)
+        for row, i in enumerate(variables):
+            o = ref["ig"][row]
+            tol = 1e-4 + 1e-5 * abs(o)
+            assert abs(float(ig[j, i]) - o) <= tol, f"job {j} var {i}: gpu {ig[j, i]!r} oracle {o!r}"
+            if di[j, i] != ref["disc"][row] or tu[j, i, 0] != ref["tuples"][row, 0]:
+                m = int(tu[j, i, 0])
+                assert 0 <= m < M and m != i and 0 <= di[j, i] < D
+                alt = oracle.ig_one(codes, yj, c, xi, int(di[j, i]), int(i), [m])
+                assert abs(alt - o) <= 2 * tol, f"job {j} var {i}: gpu argmax gives {alt}, oracle max {o}"
+
+    j = 63
+    w_ig, w_tu, w_di = mdfs.max_ig(torch.from_numpy(np.ascontiguousarray(ds.x[:, si[j]])).cuda(),
+                                   torch.from_numpy(ds.y[yp[j][si[j]]]).cuda(), 2, div, D, r, xi, seed)
+    torch.cuda.synchronize()
+    assert np.array_equal(ig[j], w_ig.cpu().numpy())
+    assert np.array_equal(tu[j], w_tu.cpu().numpy())
+    assert np.array_equal(di[j], w_di.cpu().numpy())

@@ -72,10 +72,11 @@ def test_discretize_bit_exact(cuda):
         assert np.array_equal(got_h, want)
 
 
-@pytest.mark.parametrize("N", [600, 1000, 1025, 3000, 4096, 8000])
+@pytest.mark.parametrize("N", [600, 1000, 1025, 3000, 4096, 8000, 16385, 32768])
 def test_discretize_bit_exact_sort_sizes(cuda, N):
     """Codes bit-exact for column lengths that use each in-register sort width
-    (padded lengths 1024 .. 8192) and its boundaries."""
+    (padded lengths 1024 .. 8192) and its boundaries, the shared-memory sort of
+    longer columns, and the largest N the discretiser takes (32768)."""
     from paper_1811_00631_gb300 import mdfs
     rng = np.random.default_rng(N)
     x = rng.standard_normal((5, N)).astype(np.float32)
@@ -173,6 +174,21 @@ def test_edge_minimal_sizes(cuda):
         ref = oracle.max_ig(codes, y, div + 1, k, 0.5)
         g = _gpu_max_ig(cuda, x, y, k, div, 2, 0.3, 0.5, 3)
         _check(codes, y, div + 1, k, 0.5, *g, ref, range(M))
+
+
+def test_edge_maximum_sizes(cuda):
+    """The largest sample count (N = 32768, the discretiser's in-CTA sort
+    limit) with the most classes per variable (divisions = 3) and with two
+    classes, for k = 1..3; every variable against the oracle."""
+    rng = np.random.default_rng(41)
+    M, N, D = 6, 32768, 2
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[1] > 0) ^ (x[4] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    for k, div in [(1, 3), (2, 1), (2, 3), (3, 1), (3, 3)]:
+        codes = oracle.discretize(x, div, D, 0.5, 17)
+        ref = oracle.max_ig(codes, y, div + 1, k, 0.25)
+        g = _gpu_max_ig(cuda, x, y, k, div, D, 0.5, 0.25, 17)
+        _check(codes, y, div + 1, k, 0.25, *g, ref, range(M))
 
 
 def test_k3_large_n_uses_global_tables(cuda):
