@@ -51,10 +51,13 @@ def build(force: bool = False) -> str:
 
 
 def _load():
+    """Loads the oracle library.  MDFS_ORACLE_LIB names another build of the
+    oracle source to load instead; the mutation test uses it to run the pins
+    against copies of the oracle with planted mistakes."""
     global _lib
     if _lib is not None:
         return _lib
-    path = build()
+    path = os.environ.get("MDFS_ORACLE_LIB") or build()
     lib = ctypes.CDLL(path)
     P = ctypes.c_void_p
     lib.oracle_philox4x32_10.argtypes = [P, P, P]

@@ -328,6 +328,82 @@ def test_max_ig_brute_force(k):
         assert res["second"][i] <= res["ig"][i]
 
 
+def _brute_max(codes, y, c, k, xi, i):
+    """Max of IG(i | S) over discretisations d ascending and partner sets S of
+    k - 1 distinct variables other than i in lexicographic order (Eq. 1), the
+    first maximum kept, with SH in the paper's -sum (n+b) ln p form."""
+    D, M, _ = codes.shape
+    best, arg = -np.inf, None
+    for d in range(D):
+        for S in itertools.combinations([m for m in range(M) if m != i], k - 1):
+            cols = [codes[d, s] for s in S]
+            g = _sh_from_probabilities(cols, y, c, xi) - _sh_from_probabilities(cols + [codes[d, i]], y, c, xi)
+            if g > best:
+                best, arg = g, (d, S)
+    return best, arg
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_max_ig_brute_force_negative_gains(k):
+    """Few samples, three classes and a large xi: the pseudocounts make most
+    gains negative.  The maximum still ranges only over sets of k - 1 distinct
+    variables other than i (Eq. 1), even where every such gain is below zero
+    (a set holding i itself, or one variable twice, would score 0 or a
+    lower-order gain instead)."""
+    rng = np.random.default_rng(40 + k)
+    N, M, c, D, xi = 10, 5, 3, 2, 0.9
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = (rng.random(N) < 0.5).astype(np.uint8)
+    y[0], y[1] = 0, 1
+    codes = oracle.discretize(x, c - 1, D, 0.5, seed=5)
+    res = oracle.max_ig(codes, y, c, k, xi)
+    negative = 0
+    for i in range(M):
+        best, arg = _brute_max(codes, y, c, k, xi, i)
+        negative += best < 0
+        assert res["ig"][i] == pytest.approx(best, abs=1e-9)
+        assert (int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])) == arg
+    assert negative >= 2, "the case must hold variables whose every gain is negative"
+
+
+def test_max_ig_excludes_the_variable_itself():
+    """Eq. 1 takes S within V minus {i}.  In this 4-sample, 2-variable case
+    (xi = 0.3) the only admissible partner scores below what pairing x0 with
+    itself would score (every off-diagonal voxel empty: -2 h(beta)), so a scan
+    that let i into S would report the wrong maximum and partner."""
+    codes = np.array([[[1, 1, 1, 0], [0, 1, 0, 0]]], dtype=np.uint8)
+    y = np.array([1, 0, 1, 1], dtype=np.uint8)
+    c, xi = 2, 0.3
+    want = _sh_from_probabilities([codes[0, 1]], y, c, xi) - _sh_from_probabilities([codes[0, 1], codes[0, 0]], y, c, xi)
+    self_pair = (_sh_from_probabilities([codes[0, 0]], y, c, xi)
+                 - _sh_from_probabilities([codes[0, 0], codes[0, 0]], y, c, xi))
+    assert want < self_pair
+    res = oracle.max_ig(codes, y, c, 2, xi)
+    assert res["ig"][0] == pytest.approx(want, abs=1e-12)
+    assert int(res["tuples"][0][0]) == 1
+
+
+def test_max_ig_ties_go_to_lowest_disc_and_tuple():
+    """Reading of Eq. 1's argmax: ties go to the lowest (discretisation,
+    lexicographic S).  With range = 0 every discretisation is the same
+    equipotent split, and variables 1, 2 and 3 are copies of one column, so
+    each maximum is reached by several (d, S) with bit-identical counts."""
+    rng = np.random.default_rng(7)
+    N, c, D, xi = 60, 2, 3, 0.25
+    base = rng.standard_normal((3, N)).astype(np.float32)
+    x = np.stack([base[0], base[1], base[1], base[1], base[2]])
+    y = ((x[0] > 0) ^ (x[1] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x, c - 1, D, 0.0, seed=1)
+    assert all(np.array_equal(codes[0], codes[d]) for d in range(D))
+    for k in (2, 3):
+        res = oracle.max_ig(codes, y, c, k, xi)
+        for i in range(5):
+            best, arg = _brute_max(codes, y, c, k, xi, i)
+            assert res["ig"][i] == pytest.approx(best, abs=1e-9)
+            assert (int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])) == arg
+        assert res["disc"][0] == 0 and tuple(res["tuples"][0])[0] == 1  # partner 1 of the three copies
+
+
 def test_xor_pair_invisible_in_1d_found_in_2d():
     """Synergy (section "Introduction"/"Theory"): x0, x1 set y by XOR, so each
     is uninformative alone but the top pair at k = 2, each the other's partner."""
