@@ -985,7 +985,9 @@ int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretization
     MDFS_ENSURE(ws, res, 4 * sizeof(double));
     double* res = (double*)ws->res.p;
     MDFS_CUDA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(double), st));
-    MDFS_LAUNCH("ig_lim", st, launch_ig_lim(igd, M, df, maskd, alpha, op.dev, res, st));
+    MDFS_LAUNCH("ig_lim_cdf", st, launch_ig_lim_cdf(igd, M, df, op.dev, st));
+    MDFS_LAUNCH("ig_lim_fit", st, launch_ig_lim_fit(op.dev, M, df, maskd, alpha, res, st));
+    MDFS_LAUNCH("ig_lim_p", st, launch_ig_lim_p(M, res, op.dev, st));
     MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_res, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     if (!(ws->host_res[2] > 0.0) || !(ws->host_res[1] > 0.0))
@@ -1124,7 +1126,9 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
     double* pext = (double*)ws->pext.p;
     double* res = (double*)ws->res.p;
     MDFS_CUDA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(double), st));
-    MDFS_LAUNCH("ig_lim", st, launch_ig_lim(igx, Mx, df, (const uint8_t*)ws->mask.p, level, pext, res, st));
+    MDFS_LAUNCH("ig_lim_cdf", st, launch_ig_lim_cdf(igx, Mx, df, pext, st));
+    MDFS_LAUNCH("ig_lim_fit", st, launch_ig_lim_fit(pext, Mx, df, (const uint8_t*)ws->mask.p, level, res, st));
+    MDFS_LAUNCH("ig_lim_p", st, launch_ig_lim_p(Mx, res, pext, st));
     // 4-5. adjustment over the original variables and the relevant set
     MDFS_ENSURE(ws, adjb, (size_t)M * sizeof(double));
     MDFS_ENSURE(ws, relb, (size_t)M);

@@ -10,6 +10,7 @@
 // evaluated with the power series (Abramowitz & Stegun 6.5.29) below a + 1
 // and with the Legendre continued fraction for the upper tail (A&S 6.5.31),
 // summed by the modified Lentz method, above it.
+#include <climits>
 #include <math.h>
 
 #include "mdfs_internal.cuh"
@@ -57,21 +58,36 @@ __device__ double chi2_cdf(double x, int df) {
     return 1.0 - gamma_q_fraction(a, z);
 }
 
-__global__ void __launch_bounds__(256) ig_lim_kernel(const float* __restrict__ ig, int M, int df,
-                                                     const uint8_t* __restrict__ mask, double alpha,
-                                                     double* __restrict__ p_values, double* __restrict__ res) {
+// Pass 1, one thread per variable: u_i = F_df(2 IG_i), written where the
+// p-values will go (pass 3 turns them into p-values in place).
+__global__ void __launch_bounds__(256) fit_cdf_kernel(const float* __restrict__ ig, int M, int df,
+                                                      double* __restrict__ u) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) u[i] = chi2_cdf(2.0 * (double)ig[i], df);
+}
+
+// Pass 2, one CTA of 256 threads: T by maximum likelihood, then IG_lim.
+// The sum of ln u_i runs in a fixed order (strided by thread, then a fixed
+// reduction tree), so T is the same on every call.  IG_lim solves
+// F_df(x) = (1 - alpha)^(1/T): the smallest power of two at or above the root
+// comes from 256 points 2^0 .. 2^255 evaluated at once, then 12 rounds of
+// 256-way multisection shrink the bracket [lo, hi] (F(lo) < target <= F(hi))
+// by 257 each, far below the FP64 spacing of the root.
+__global__ void __launch_bounds__(256) fit_t_kernel(const double* __restrict__ u, int M, int df,
+                                                    const uint8_t* __restrict__ mask, double alpha,
+                                                    double* __restrict__ res) {
     __shared__ double s_sum[8];
     __shared__ int s_n[8];
-    __shared__ double s_T;
-    __shared__ int s_ok;
+    __shared__ double s_T, s_lo, s_hi;
+    __shared__ int s_ok, s_first;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double sum = 0.0;
     int n = 0;
     for (int i = tid; i < M; i += blockDim.x) {
         if (mask && !mask[i]) continue;
-        const double u = chi2_cdf(2.0 * (double)ig[i], df);
-        if (u > 0.0) {
-            sum += log(u);
+        const double ui = u[i];
+        if (ui > 0.0) {
+            sum += log(ui);
             ++n;
         }
     }
@@ -95,30 +111,65 @@ __global__ void __launch_bounds__(256) ig_lim_kernel(const float* __restrict__ i
         s_T = s_ok ? -(double)nn / t : 0.0;
         res[2] = (double)nn;
         res[1] = s_T;
+        s_first = INT_MAX;
     }
     __syncthreads();
     if (!s_ok) return;
-    const double T = s_T;
-    for (int i = tid; i < M; i += blockDim.x) {
-        const double u = chi2_cdf(2.0 * (double)ig[i], df);
-        p_values[i] = u > 0.0 ? -expm1(T * log(u)) : 1.0;
-    }
+    const double target = pow(1.0 - alpha, 1.0 / s_T);
+    // bracket: the first 2^t (t = 0 .. 255) whose CDF reaches the target
+    if (chi2_cdf(ldexp(1.0, tid), df) >= target) atomicMin(&s_first, tid);
+    __syncthreads();
     if (tid == 0) {
-        const double target = pow(1.0 - alpha, 1.0 / T);
-        double lo = 0.0, hi = 1.0;
-        for (int it = 0; it < 1100 && chi2_cdf(hi, df) < target; ++it) hi *= 2.0;
-        for (int it = 0; it < 200; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (chi2_cdf(mid, df) < target) lo = mid;
-            else hi = mid;
+        if (s_first == INT_MAX) {  // beyond 2^255: report that bound
+            s_lo = s_hi = ldexp(1.0, (int)blockDim.x - 1);
+        } else {
+            s_hi = ldexp(1.0, s_first);
+            s_lo = s_first > 0 ? ldexp(1.0, s_first - 1) : 0.0;
         }
-        res[0] = 0.25 * (lo + hi);
     }
+    __syncthreads();
+    for (int round = 0; round < 12; ++round) {
+        const double lo = s_lo, hi = s_hi;
+        const double x = lo + (hi - lo) * ((double)(tid + 1) / (double)(blockDim.x + 1));
+        const bool reached = chi2_cdf(x, df) >= target;
+        __syncthreads();  // every thread has read the bracket
+        if (tid == 0) s_first = INT_MAX;
+        __syncthreads();
+        if (reached) atomicMin(&s_first, tid);
+        __syncthreads();
+        const int first = s_first;
+        if (first == tid) s_hi = x;                                        // first point at or above
+        if (first == tid + 1) s_lo = x;                                    // the point before it
+        if (first == INT_MAX && tid == (int)blockDim.x - 1) s_lo = x;      // every point below
+        __syncthreads();
+    }
+    if (tid == 0) res[0] = 0.25 * (s_lo + s_hi);
 }
 
-cudaError_t launch_ig_lim(const float* ig, int M, int df, const uint8_t* mask, double alpha, double* p_values,
-                          double* res, cudaStream_t st) {
-    ig_lim_kernel<<<1, 256, 0, st>>>(ig, M, df, mask, alpha, p_values, res);
+// Pass 3, one thread per variable: p_i = 1 - u_i^T (as -expm1(T ln u_i),
+// accurate for small p), 1 where u_i = 0.  Nothing is written if the fit failed.
+__global__ void __launch_bounds__(256) fit_p_kernel(int M, const double* __restrict__ res, double* __restrict__ p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double T = res[1];
+    if (!(res[2] > 0.0) || !(T > 0.0)) return;
+    const double ui = p[i];
+    p[i] = ui > 0.0 ? -expm1(T * log(ui)) : 1.0;
+}
+
+cudaError_t launch_ig_lim_cdf(const float* ig, int M, int df, double* p_values, cudaStream_t st) {
+    fit_cdf_kernel<<<(M + 255) / 256, 256, 0, st>>>(ig, M, df, p_values);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ig_lim_fit(const double* p_values, int M, int df, const uint8_t* mask, double alpha, double* res,
+                              cudaStream_t st) {
+    fit_t_kernel<<<1, 256, 0, st>>>(p_values, M, df, mask, alpha, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ig_lim_p(int M, const double* res, double* p_values, cudaStream_t st) {
+    fit_p_kernel<<<(M + 255) / 256, 256, 0, st>>>(M, res, p_values);
     return cudaGetLastError();
 }
 

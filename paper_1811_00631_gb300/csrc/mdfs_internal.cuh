@@ -222,10 +222,15 @@ cudaError_t launch_p_adjust(const double* p, int m, int method, double level, vo
 cudaError_t launch_finalize(const unsigned long long* keys, int M, int k, float* ig, int* tuples,
                             int* disc, cudaStream_t st, const int* kdisc = nullptr);
 
-// chi^2 / extreme-value fit in FP64 (one CTA).  res[0] = IG_lim, res[1] = T,
-// res[2] = number of variables in the fit.
-cudaError_t launch_ig_lim(const float* ig, int M, int df, const uint8_t* mask, double alpha,
-                          double* p_values, double* res, cudaStream_t st);
+// chi^2 / extreme-value fit in FP64, three launches on one stream:
+//   cdf: p_values[i] = F_df(2 ig[i]) (one thread per variable);
+//   fit: res[0] = IG_lim, res[1] = T, res[2] = number of variables in the fit
+//        (one CTA; reads the CDF values left in p_values);
+//   p:   p_values[i] = 1 - F^T in place (skipped when the fit failed).
+cudaError_t launch_ig_lim_cdf(const float* ig, int M, int df, double* p_values, cudaStream_t st);
+cudaError_t launch_ig_lim_fit(const double* p_values, int M, int df, const uint8_t* mask, double alpha, double* res,
+                              cudaStream_t st);
+cudaError_t launch_ig_lim_p(int M, const double* res, double* p_values, cudaStream_t st);
 
 // Raises (never lowers) a kernel's dynamic shared-memory limit on the current
 // device to at least `bytes`.  Thread-safe: concurrent calls on other streams
