@@ -157,12 +157,15 @@ int mdfs_keys_decode(const uint64_t* keys, int M, int k, float* ig, int32_t* tup
  * IG <= 0 carry no likelihood term), then
  *     p_i    = 1 - F_df(2 IG_i)^T,
  *     IG_lim = F_df^{-1}((1 - alpha)^(1/T)) / 2.
- * Runs in FP64 on the device.
+ * Runs in FP64 on the device: the CDF of every variable in parallel, then T
+ * and IG_lim (a parallel root search) in one CTA, then the p-values.
  *
  * ig:               [M] float, host or device (an mdfs_max_ig result).
  * discretizations:  recorded only; the fit absorbs it into T.
  * irrelevant_mask:  [M] uint8 or NULL (NULL = every variable is used).
- * p_values:         [M] double, host or device.
+ * p_values:         [M] double, host or device.  A device array also holds
+ *                   the CDF values during the call; after MDFS_EDEGENERATE
+ *                   its contents are unspecified.
  * ig_lim, n_eff:    one double each, host or device (n_eff = fitted T).
  * Returns MDFS_EDEGENERATE when no variable contributes to the fit.
  */
