@@ -167,3 +167,20 @@ def test_interesting_tuples_agree_with_the_max(k):
     assert oracle.interesting_tuples(codes, y, 2, k, 0.25, top + 1e-9) == []
     recs = oracle.interesting_tuples(codes, y, 2, k, 0.25, top - 1e-9)
     assert len(recs) >= 1 and all(r[2] >= top - 1e-9 for r in recs)
+
+
+def test_interesting_tuples_threshold_reached_and_lowest_discretisation():
+    """A (variable, tuple) is interesting when its IG reaches the threshold,
+    equality included; and with range = 0 every discretisation is the same
+    equipotent split, so each record's maximum is reached at every d and the
+    lowest, d = 0, is the one reported."""
+    rng = np.random.default_rng(61)
+    M, N, D = 6, 120, 3
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[1] > 0) ^ (x[4] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+    codes = oracle.discretize(x, 1, D, 0.0, seed=3)
+    allrec = oracle.interesting_tuples(codes, y, 2, 2, 0.25, -np.inf)
+    assert all(r[3] == 0 for r in allrec)
+    top = max(r[2] for r in allrec)
+    at_top = oracle.interesting_tuples(codes, y, 2, 2, 0.25, top)
+    assert at_top == [r for r in allrec if r[2] >= top] and len(at_top) >= 1

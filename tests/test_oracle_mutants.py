@@ -14,6 +14,7 @@ it; the bit-exact GPU parity of the discretised codes does.
 """
 import concurrent.futures
 import os
+import shutil
 import subprocess
 import sys
 
@@ -100,13 +101,18 @@ def _build(src_text: str, path: str):
                    check=True, capture_output=True)
 
 
-def _pins_pass(lib_path: str) -> bool:
-    env = dict(os.environ, MDFS_ORACLE_LIB=lib_path, OMP_NUM_THREADS="2",
-               PYTHONPATH=ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
+def _pins_pass(lib_path: str = None, first_path: str = ROOT) -> bool:
+    """Runs the CPU pins in a child process against the oracle library at
+    lib_path, or against the oracle package found first on the path."""
+    env = dict(os.environ, OMP_NUM_THREADS="2",
+               PYTHONPATH=first_path + os.pathsep + ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    env.pop("MDFS_ORACLE_LIB", None)
+    if lib_path:
+        env["MDFS_ORACLE_LIB"] = lib_path
     r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_contrast_pins.py"),
                         "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+                       cwd=first_path, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode == 0
 
 
@@ -123,6 +129,51 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
         lib = str(tmp_path / f"mutant{i}.so")
         _build(text, lib)
         return what, _pins_pass(lib)
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=4) as ex:
+        results = list(ex.map(run, enumerate(jobs)))
+    assert results[0] == ("unchanged", True), "the unchanged oracle must pass its pins"
+    survivors = [what for what, passed in results[1:] if passed]
+    assert not survivors, f"planted mistakes that no pin catches: {survivors}"
+
+
+# mistakes in the Python side of the oracle (p-value adjustment, interesting
+# tuples, the selection pipeline)
+PY_MUTANTS = [
+    ("Holm multiplier one too small", "run = max(run, (m - i) * ps[i])", "run = max(run, (m - i - 1) * ps[i])"),
+    ("Holm without the running maximum", "run = max(run, (m - i) * ps[i])", "run = (m - i) * ps[i]"),
+    ("step-up adjustments taken from the smallest p-value",
+     "for i in range(m - 1, -1, -1):", "for i in range(m):"),
+    ("Benjamini-Hochberg rank off by one", "q * m / (i + 1)", "q * m / (i + 2)"),
+    ("Benjamini-Yekutieli harmonic sum one term short",
+     "sum(1.0 / k for k in range(1, m + 1))", "sum(1.0 / k for k in range(1, m))"),
+    ("Bonferroni not capped at 1", "adj = np.minimum(1.0, m * ps)", "adj = m * ps"),
+    ("adjusted values left in sorted order", "out[order] = adj", "out[:] = adj"),
+    ("interesting only strictly above the threshold", "if best >= threshold:", "if best > threshold:"),
+    ("interesting tuple keeps the last discretisation of a tie", "                if g > best:\n                    best, bd = g, d",
+     "                if g >= best:\n                    best, bd = g, d"),
+    ("selection p-values as F^T", "p = np.array([1.0 - chi2_cdf(2.0 * g, df) ** neff if g > 0 else 1.0 for g in ig[:M]])",
+     "p = np.array([chi2_cdf(2.0 * g, df) ** neff if g > 0 else 1.0 for g in ig[:M]])"),
+]
+
+
+def test_every_planted_mistake_in_the_python_oracle_fails_a_pin(tmp_path):
+    src_dir = os.path.join(ROOT, "oracle")
+    with open(os.path.join(src_dir, "__init__.py")) as f:
+        init = f.read()
+    jobs = [("unchanged", init)]
+    for what, old, new in PY_MUTANTS:
+        assert init.count(old) == 1, f"mutation site not unique: {what}"
+        jobs.append((what, init.replace(old, new)))
+
+    def run(i_job):
+        i, (what, text) = i_job
+        root = tmp_path / f"m{i}"
+        pkg = root / "oracle"
+        pkg.mkdir(parents=True)
+        shutil.copy(os.path.join(src_dir, "mdfs_oracle.c"), pkg / "mdfs_oracle.c")
+        (pkg / "__init__.py").write_text(text)
+        return what, _pins_pass(first_path=str(root))
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=4) as ex:
         results = list(ex.map(run, enumerate(jobs)))
