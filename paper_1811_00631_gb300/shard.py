@@ -69,6 +69,39 @@ def _fingerprint(params: dict) -> str:
     return hashlib.sha256(json.dumps(params, sort_keys=True).encode()).hexdigest()
 
 
+def _open_checkpoint(checkpoint_dir: str, n_shards: int, params: dict) -> str:
+    """Creates or checks the checkpoint directory of one scan; returns its fingerprint."""
+    import json
+    import os
+    os.makedirs(checkpoint_dir, exist_ok=True)
+    fp = _fingerprint(dict(params, n_shards=n_shards))
+    meta = os.path.join(checkpoint_dir, "scan.json")
+    if not os.path.exists(meta):
+        tmp = meta + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump({"fingerprint": fp, "params": params, "n_shards": n_shards}, f)
+        os.replace(tmp, meta)
+    with open(meta) as f:
+        old = json.load(f)
+    if old.get("fingerprint") != fp:
+        raise ValueError(f"{checkpoint_dir} holds shards of a different scan")
+    return fp
+
+
+def _shard_keys(s: int, scan_shard, checkpoint_dir: str) -> np.ndarray:
+    """Keys of shard s: read from its checkpoint file, or scanned and saved
+    (temporary name, then rename: a file that exists is complete)."""
+    import os
+    path = os.path.join(checkpoint_dir, f"shard_{s}.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    k = np.asarray(scan_shard(s), dtype=np.uint64)
+    tmp = path + f".tmp{os.getpid()}.npy"
+    np.save(tmp, k)
+    os.replace(tmp, path)
+    return k
+
+
 def run_resumable(scan_shard, n_shards: int, checkpoint_dir: str, params: dict) -> np.ndarray:
     """Merged keys of a scan split into `n_shards` shards, resumable.
 
@@ -81,33 +114,40 @@ def run_resumable(scan_shard, n_shards: int, checkpoint_dir: str, params: dict) 
     different fingerprint refuses to mix results.  Because the merge is an
     element-wise maximum, the order in which shards finish does not matter.
     """
-    import json
-    import os
-    os.makedirs(checkpoint_dir, exist_ok=True)
-    fp = _fingerprint(dict(params, n_shards=n_shards))
-    meta = os.path.join(checkpoint_dir, "scan.json")
-    if os.path.exists(meta):
-        with open(meta) as f:
-            old = json.load(f)
-        if old.get("fingerprint") != fp:
-            raise ValueError(f"{checkpoint_dir} holds shards of a different scan")
-    else:
-        tmp = meta + ".tmp"
-        with open(tmp, "w") as f:
-            json.dump({"fingerprint": fp, "params": params, "n_shards": n_shards}, f)
-        os.replace(tmp, meta)
-    keys = []
-    for s in range(n_shards):
-        path = os.path.join(checkpoint_dir, f"shard_{s}.npy")
-        if os.path.exists(path):
-            keys.append(np.load(path))
-            continue
-        k = np.asarray(scan_shard(s), dtype=np.uint64)
-        tmp = path + ".tmp.npy"
-        np.save(tmp, k)
-        os.replace(tmp, path)
-        keys.append(k)
-    return merge(keys)
+    _open_checkpoint(checkpoint_dir, n_shards, params)
+    return merge([_shard_keys(s, scan_shard, checkpoint_dir) for s in range(n_shards)])
+
+
+def run_ranks_with_recovery(scan_shard, n_shards: int, checkpoint_dir: str, params: dict, rank: int, world: int,
+                            store, timeout_s: float = 30.0, poll_s: float = 0.05):
+    """A scan sharded over ``world`` host processes that survives a failed rank.
+
+    Rank r scans shards r, r + world, ... through the checkpoint directory
+    (shared by all ranks), then posts a done flag in the c10d ``store`` (e.g. a
+    ``torch.distributed.TCPStore``).  It then waits at most ``timeout_s`` for
+    the other ranks' flags.  A rank whose flag has not appeared by then is
+    taken as failed, and the waiting rank scans whatever shards have no
+    checkpoint file itself.  No step waits on a peer without a bound, and the
+    merge needs no collective, so a dead rank cannot hang the others.  Shards
+    are deterministic, so a shard scanned twice (a slow rank taken for dead)
+    gives the same keys.  Returns (merged keys, sorted ranks taken as failed);
+    the keys equal those of the unsharded scan.
+    """
+    import time
+    fp = _open_checkpoint(checkpoint_dir, n_shards, params)
+    for s in range(rank, n_shards, world):
+        _shard_keys(s, scan_shard, checkpoint_dir)
+    flag = f"mdfs/{fp[:16]}/done/"
+    store.set(flag + str(rank), "1")
+    pending = [r for r in range(world) if r != rank]
+    deadline = time.monotonic() + timeout_s
+    while pending:
+        pending = [r for r in pending if not store.check([flag + str(r)])]
+        if not pending or time.monotonic() >= deadline:
+            break
+        time.sleep(poll_s)
+    keys = merge([_shard_keys(s, scan_shard, checkpoint_dir) for s in range(n_shards)])
+    return keys, sorted(pending)
 
 
 def max_ig_resumable(x, y, k: int, divisions: int, discretizations: int, range_: float, pc_xi: float, seed: int,

@@ -2,6 +2,7 @@
 ranks (torch.distributed, gloo, world size 2, on CPU)."""
 import os
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -125,3 +126,60 @@ def test_resumable_scan_skips_finished_shards_and_refuses_other_scans(tmp_path):
     assert np.array_equal(again, want)
     with pytest.raises(ValueError):
         shard.run_resumable(flaky, n_shards, str(tmp_path), {"k": 3, "seed": 1})
+
+
+def _recovery_rank(rank, world, port, ckpt, out_path, fail_rank):
+    """One host rank of a sharded scan; ``fail_rank`` dies after its first shard."""
+    from datetime import timedelta
+
+    import torch.distributed as dist
+    store = dist.TCPStore("127.0.0.1", port, world, is_master=(rank == 0), timeout=timedelta(seconds=30))
+    per_shard = _recovery_shards()
+    done = []
+
+    def scan(s):
+        if rank == fail_rank and done:
+            os._exit(0)  # the process ends in the middle of its share, without a word to the others
+        done.append(s)
+        time.sleep(0.05)
+        return per_shard[s]
+
+    keys, failed = shard.run_ranks_with_recovery(scan, len(per_shard), ckpt, {"k": 2, "seed": 9}, rank, world, store,
+                                                 timeout_s=2.0)
+    np.save(out_path + f".{rank}.npy", keys)
+    with open(out_path + f".{rank}.failed", "w") as f:
+        f.write(",".join(map(str, failed)))
+    store.set(f"exit/{rank}", "1")
+    if rank == 0:  # the store lives in rank 0: keep it up until the live ranks are through
+        deadline = time.monotonic() + 20
+        while time.monotonic() < deadline and not all(
+                store.check([f"exit/{r}"]) for r in range(world) if r != fail_rank):
+            time.sleep(0.05)
+
+
+def _recovery_shards():
+    rng = np.random.default_rng(17)
+    return [shard.pack(rng.standard_normal(30).astype(np.float32), rng.integers(0, 2**31, 30)) for _ in range(6)]
+
+
+@pytest.mark.parametrize("fail_rank", [None, 1])
+def test_sharded_scan_survives_a_failed_rank(tmp_path, fail_rank):
+    """Two host ranks share six shards.  With no failure both return the
+    merged keys and name no failed rank.  When rank 1 dies after its first
+    shard, rank 0 stops waiting for it after the bounded wait, names it, scans
+    its unfinished shards from the shared checkpoint directory, and still
+    returns the keys of the whole scan."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    port = _free_port()
+    out = str(tmp_path / "res")
+    mp.spawn(_recovery_rank, args=(2, port, str(tmp_path / "ckpt"), out, fail_rank if fail_rank is not None else -1),
+             nprocs=2, join=True)
+    want = shard.merge(_recovery_shards())
+    live = [0, 1] if fail_rank is None else [0]
+    for r in live:
+        assert np.array_equal(np.load(out + f".{r}.npy"), want)
+        with open(out + f".{r}.failed") as f:
+            assert f.read() == ("" if fail_rank is None else str(fail_rank))
+    if fail_rank is not None:
+        assert not os.path.exists(out + f".{fail_rank}.npy")
