@@ -40,6 +40,7 @@ class Job:
     seed: int = 0
     alpha: float = 0.05       # level of the IG_lim fit (None: skip the fit)
     tag: object = None
+    deadline_s: Optional[float] = None  # latest start, in seconds after submission (None: no deadline)
 
 
 @dataclasses.dataclass
@@ -111,6 +112,8 @@ class Server:
         self._in_use = 0
         self._running = 0
         self._closed = False
+        self.expired = 0
+        self._n_deadline = 0  # queued jobs that carry a deadline
         self.peak_in_use = 0
         self.peak_running = 0
         self._threads = [threading.Thread(target=self._worker, args=(s,), daemon=True) for s in range(n_slots)]
@@ -135,7 +138,9 @@ class Server:
         with self._cv:
             if self._closed:
                 raise RuntimeError("server closed")
+            self._purge_expired()
             self._queue.append((job, fut, need, time.perf_counter()))
+            self._n_deadline += getattr(job, "deadline_s", None) is not None
             self._cv.notify_all()
         return fut
 
@@ -154,14 +159,45 @@ class Server:
         self.close()
 
     # ------------------------------------------------------------------
+    def _purge_expired(self):
+        """Drops queued jobs whose start deadline has passed; their futures get
+        TimeoutError.  Runs whenever the scheduler looks at the queue (a job
+        arrives, a slot asks for work, or an idle slot's timed wait ends).
+        Caller holds the lock."""
+        if not self._n_deadline:
+            return
+        now = time.perf_counter()
+        keep = collections.deque()
+        for item in self._queue:
+            job, fut, _need, t_sub = item
+            dl = getattr(job, "deadline_s", None)
+            if dl is not None and now - t_sub > dl:
+                fut.set_exception(TimeoutError(f"job {job.tag!r} not started within its deadline of {dl} s"))
+                self.expired += 1
+                self._n_deadline -= 1
+            else:
+                keep.append(item)
+        self._queue = keep
+
+    def _deadline_wait(self):
+        """Seconds until the earliest queued start deadline (None: no deadline)."""
+        if not self._n_deadline:
+            return None
+        now = time.perf_counter()
+        waits = [getattr(j, "deadline_s") - (now - t) for j, _f, _n, t in self._queue
+                 if getattr(j, "deadline_s", None) is not None]
+        return max(1e-3, min(waits)) if waits else None
+
     def _next(self):
         """Head-of-line admission: the oldest job runs as soon as it fits."""
         with self._cv:
             while True:
+                self._purge_expired()
                 if self._queue:
                     job, fut, need, t_sub = self._queue[0]
                     if self._in_use + need <= self.budget:
                         self._queue.popleft()
+                        self._n_deadline -= getattr(job, "deadline_s", None) is not None
                         self._in_use += need
                         self._running += 1
                         self.peak_in_use = max(self.peak_in_use, self._in_use)
@@ -169,7 +205,7 @@ class Server:
                         return job, fut, need, t_sub
                 elif self._closed:
                     return None
-                self._cv.wait()
+                self._cv.wait(self._deadline_wait())
 
     def _release(self, need: int):
         with self._cv:

@@ -110,3 +110,49 @@ def test_device_byte_estimate_covers_the_higher_order_tables():
     assert k4 < 8 << 30                      # but chunked, not all thirty at once
     assert k5 > 12 * math.comb(500, 4)       # one discretisation of quadruple tables
     assert serve.job_device_bytes(200, 2000, 2, 1, 30) > 30 * 200 * 2048  # the k = 2 one-hot operand
+
+
+def test_jobs_past_their_start_deadline_are_dropped():
+    """A queued job that cannot start within its deadline fails with
+    TimeoutError and never runs; jobs without a deadline, or with a deadline
+    they meet, run as usual."""
+    ran = []
+
+    def executor(job, slot):
+        ran.append(job.tag)
+        time.sleep(job.dur)
+        return (np.array([job.tag]), None, None, None, None, None)
+
+    slow = FakeJob(need=1, dur=0.3, tag=0)
+    late = FakeJob(need=1, dur=0.01, tag=1)
+    late.deadline_s = 0.05
+    patient = FakeJob(need=1, dur=0.01, tag=2)
+    patient.deadline_s = 10.0
+    plain = FakeJob(need=1, dur=0.01, tag=3)
+    srv = serve.Server(n_slots=1, memory_budget=10, executor=executor, estimate=_estimate)
+    futs = [srv.submit(j) for j in (slow, late, patient, plain)]
+    with pytest.raises(TimeoutError):
+        futs[1].result(timeout=5)
+    assert [f.result(timeout=5).ig[0] for f in (futs[0], futs[2], futs[3])] == [0, 2, 3]
+    srv.close()
+    assert srv.expired == 1 and ran == [0, 2, 3]
+
+
+def test_deadline_drops_a_job_blocked_behind_the_memory_budget():
+    """An idle slot wakes up for the earliest deadline: a job that waits
+    behind a memory-bound head-of-line job expires while the budget is held."""
+    def executor(job, slot):
+        time.sleep(job.dur)
+        return (np.array([job.tag]), None, None, None, None, None)
+
+    big = FakeJob(need=8, dur=0.4, tag=0)
+    waiting = FakeJob(need=8, dur=0.01, tag=1)
+    waiting.deadline_s = 0.1
+    srv = serve.Server(n_slots=2, memory_budget=10, executor=executor, estimate=_estimate)
+    t0 = time.perf_counter()
+    f_big, f_wait = srv.submit(big), srv.submit(waiting)
+    with pytest.raises(TimeoutError):
+        f_wait.result(timeout=5)
+    assert time.perf_counter() - t0 < 0.35  # dropped before the big job released the budget
+    assert f_big.result(timeout=5).ig[0] == 0
+    srv.close()
