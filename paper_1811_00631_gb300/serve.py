@@ -99,8 +99,11 @@ class Server:
     """Admits jobs into ``n_slots`` concurrent slots under a device-memory budget."""
 
     def __init__(self, n_slots: int = 4, memory_budget: Optional[int] = None, device: int = 0,
-                 executor: Optional[Callable] = None, estimate: Callable = job_device_bytes):
+                 executor: Optional[Callable] = None, estimate: Callable = job_device_bytes,
+                 log_path: Optional[str] = None):
         self.n_slots = n_slots
+        self._log_path = log_path  # JSON line per finished, failed or expired job
+        self._log_lock = threading.Lock()
         self.device = device
         self.estimate = estimate
         if memory_budget is None:
@@ -173,6 +176,7 @@ class Server:
             dl = getattr(job, "deadline_s", None)
             if dl is not None and now - t_sub > dl:
                 fut.set_exception(TimeoutError(f"job {job.tag!r} not started within its deadline of {dl} s"))
+                self._log(job, "expired", t_sub, None, now, None)
                 self.expired += 1
                 self._n_deadline -= 1
             else:
@@ -232,10 +236,29 @@ class Server:
                     out = _run_on_gpu(job, ctx, self.device)
                 t1 = time.perf_counter()
                 fut.set_result(Result(*out, submit_t=t_sub, start_t=t0, end_t=t1, slot=slot, tag=job.tag))
+                self._log(job, "ok", t_sub, t0, t1, slot)
             except BaseException as e:  # the job failed; the slot keeps serving
                 fut.set_exception(e)
+                self._log(job, f"error: {type(e).__name__}: {e}", t_sub, t0, time.perf_counter(), slot)
             finally:
                 self._release(need)
+
+    def _log(self, job, status: str, t_sub: float, t_start, t_end: float, slot):
+        """Appends one JSON line per job to log_path: shape, work, queue wait,
+        run time, latency, evaluation rate and status."""
+        if not self._log_path:
+            return
+        import json
+        M, N = int(job.x.shape[0]), int(job.x.shape[1])
+        evals = job_evals(M, job.k, job.discretizations) if M >= job.k else 0.0
+        run_s = (t_end - t_start) if t_start is not None else None
+        rec = {"tag": job.tag if isinstance(job.tag, (int, float, str)) or job.tag is None else str(job.tag),
+               "N": N, "M": M, "k": job.k, "classes": job.divisions + 1, "discretizations": job.discretizations,
+               "evals": evals, "queue_s": (t_start if t_start is not None else t_end) - t_sub, "run_s": run_s,
+               "latency_s": t_end - t_sub, "evals_per_s": evals / run_s if run_s else None, "slot": slot,
+               "status": status}
+        with self._log_lock, open(self._log_path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
 
 
 def _run_on_gpu(job: Job, stream, device: int):

@@ -156,3 +156,34 @@ def test_deadline_drops_a_job_blocked_behind_the_memory_budget():
     assert time.perf_counter() - t0 < 0.35  # dropped before the big job released the budget
     assert f_big.result(timeout=5).ig[0] == 0
     srv.close()
+
+
+def test_per_job_records(tmp_path):
+    """With log_path set, every job leaves one JSON line: its shape and work,
+    queue wait, run time, latency and status (ok, the error, or expired)."""
+    import json
+
+    def executor(job, slot):
+        time.sleep(job.dur)
+        if job.fail:
+            raise ValueError("bad job")
+        return (np.array([job.tag]), None, None, None, None, None)
+
+    log = tmp_path / "jobs.jsonl"
+    jobs = [FakeJob(need=2, dur=0.05, tag=0), FakeJob(need=2, dur=0.01, tag=1, fail=True),
+            FakeJob(need=2, dur=0.01, tag=2)]
+    jobs[2].deadline_s = 0.01
+    srv = serve.Server(n_slots=1, memory_budget=10, executor=executor, estimate=_estimate, log_path=str(log))
+    futs = [srv.submit(j) for j in jobs]
+    for f in futs:
+        try:
+            f.result(timeout=5)
+        except (ValueError, TimeoutError):
+            pass
+    srv.close()
+    recs = {r["tag"]: r for r in map(json.loads, log.read_text().splitlines())}
+    assert set(recs) == {0, 1, 2}
+    assert recs[0]["status"] == "ok" and recs[0]["run_s"] >= 0.05 and recs[0]["M"] == 2 and recs[0]["evals"] == 2.0
+    assert recs[0]["latency_s"] >= recs[0]["run_s"] and recs[0]["queue_s"] >= 0
+    assert recs[1]["status"].startswith("error: ValueError")
+    assert recs[2]["status"] == "expired" and recs[2]["run_s"] is None
