@@ -134,7 +134,7 @@ def oracle_sample(n2: int, n3: int, seed: int = 11, n_disc: int = None):
     ds = synth.madelon_like()
     nd = DISC if n_disc is None else max(1, min(DISC, n_disc))
     t0 = time.perf_counter()
-    codes = np.ascontiguousarray(oracle.discretize(ds.x, DIV, DISC, RANGE, seed)[:nd])
+    codes = oracle.discretize(ds.x, DIV, nd, RANGE, seed)  # the first nd discretisations
     if n2:
         oracle.max_ig(codes, ds.y, DIV + 1, 2, XI, variables=np.arange(n2, dtype=np.int32))
     if n3:
