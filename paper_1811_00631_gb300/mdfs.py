@@ -171,6 +171,25 @@ def _data(x, y):
     return _Data(dt, xp, yp, N, M), (xk, yk)
 
 
+def _check_out(arrs, shapes, dtypes, like):
+    """Preallocated outputs must match the kind of ``like`` (CUDA tensors on its
+    device, else numpy arrays), be C-contiguous and have the exact dtype and
+    shape the library writes; anything else is refused before the call, since
+    the library trusts the sizes it is given."""
+    for a, shape, dt in zip(arrs, shapes, dtypes):
+        if _is_cuda(like):
+            import torch
+            tdt = {np.float32: torch.float32, np.int32: torch.int32}[dt]
+            ok = (_is_cuda(a) and a.device == like.device and a.dtype == tdt and a.is_contiguous()
+                  and tuple(a.shape) == shape)
+        else:
+            ok = (isinstance(a, np.ndarray) and a.dtype == dt and a.flags.c_contiguous and a.shape == shape
+                  and a.flags.writeable)
+        if not ok:
+            raise ValueError(f"out: expected a contiguous {np.dtype(dt).name} array of shape {shape} "
+                             f"{'on ' + str(like.device) if _is_cuda(like) else 'in host memory'}")
+
+
 def discretize(x, divisions: int = 1, discretizations: int = 1, range_: float = 0.0, seed: int = 0):
     """Codes u8[D][M][N] (section "Algorithm and implementation" of arXiv 1811.00631)."""
     lib = load()
@@ -210,6 +229,7 @@ def max_ig(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range
             di = torch.empty(M, dtype=torch.int32, device=x.device)
         else:
             ig, tu, di = out
+            _check_out(out, ((M,), (M, kk), (M,)), (np.float32, np.int32, np.int32), x)
         ptrs = (ig.data_ptr(), tu.data_ptr(), di.data_ptr())
         stream = _stream_of(x)
     else:
@@ -219,6 +239,7 @@ def max_ig(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range
             di = np.empty(M, dtype=np.int32)
         else:
             ig, tu, di = out
+            _check_out(out, ((M,), (M, kk), (M,)), (np.float32, np.int32, np.int32), x)
         ptrs = (ig.ctypes.data, tu.ctypes.data, di.ctypes.data)
         stream = None
     rc = lib.mdfs_max_ig(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
