@@ -265,13 +265,18 @@ def max_ig_batch(x, y, sample_idx=None, y_perm=None, n_jobs=None, k: int = 2, di
     kk = max(k - 1, 1)
 
     def index_ptr(a):
+        # the library reads J x N indices from each map
         if a is None:
             return None, None
         if _is_cuda(a):
             import torch
             t = a.contiguous().to(torch.int32)
+            if t.numel() < J * N:
+                raise ValueError(f"index map holds {t.numel()} entries; {J} jobs x N = {N} need {J * N}")
             return ctypes.c_void_p(t.data_ptr()), t
         h = _host(a, np.int32)
+        if h.size < J * N:
+            raise ValueError(f"index map holds {h.size} entries; {J} jobs x N = {N} need {J * N}")
         return ctypes.c_void_p(h.ctypes.data), h
     ip, ik = index_ptr(sample_idx)
     pp, pk = index_ptr(y_perm)
@@ -344,6 +349,7 @@ def max_ig_noalloc(x, y, k: int = 2, divisions: int = 1, discretizations: int = 
         di = torch.empty(M, dtype=torch.int32, device=x.device)
     else:
         ig, tu, di = out
+        _check_out(out, ((M,), (M, 1), (M,)), (np.float32, np.int32, np.int32), x)
     rc = lib.mdfs_max_ig_noalloc(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
                                  int(seed) & (2**64 - 1), ctypes.c_void_p(ig.data_ptr()),
                                  ctypes.c_void_p(tu.data_ptr()) if k > 1 else None, ctypes.c_void_p(di.data_ptr()),
@@ -379,6 +385,8 @@ def ig_lim(ig, k: int, divisions: int, discretizations: int = 1, irrelevant_mask
         mk = None
         if irrelevant_mask is not None:
             mk = torch.as_tensor(irrelevant_mask, device=ig.device).to(torch.uint8).contiguous()
+            if mk.numel() != M:
+                raise ValueError(f"irrelevant_mask holds {mk.numel()} entries, ig {M}")
         rc = lib.mdfs_ig_lim(ctypes.c_void_p(igc.data_ptr()), M, k, divisions, discretizations,
                              ctypes.c_void_p(mk.data_ptr()) if mk is not None else None, float(alpha),
                              ctypes.c_void_p(p.data_ptr()), ctypes.byref(lim), ctypes.byref(neff), _stream_of(ig))
@@ -386,6 +394,8 @@ def ig_lim(ig, k: int, divisions: int, discretizations: int = 1, irrelevant_mask
         igc = _host(ig, np.float32)
         p = np.empty(M, dtype=np.float64)
         mk = _host(irrelevant_mask, np.uint8) if irrelevant_mask is not None else None
+        if mk is not None and mk.size != M:
+            raise ValueError(f"irrelevant_mask holds {mk.size} entries, ig {M}")
         rc = lib.mdfs_ig_lim(ctypes.c_void_p(igc.ctypes.data), M, k, divisions, discretizations,
                              ctypes.c_void_p(mk.ctypes.data) if mk is not None else None, float(alpha),
                              ctypes.c_void_p(p.ctypes.data), ctypes.byref(lim), ctypes.byref(neff), None)

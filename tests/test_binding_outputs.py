@@ -81,3 +81,23 @@ def test_bad_cuda_outputs_are_refused(bad):
         outs[0] = FakeCuda((M,), torch.float32, contiguous=False)
     with pytest.raises(ValueError):
         mdfs._check_out(outs, ((M,), (M, kk), (M,)), (np.float32, np.int32, np.int32), x)
+
+
+def test_short_batch_index_maps_are_refused():
+    """mdfs_max_ig_batch reads n_jobs x N indices from each map: shorter maps
+    are refused in the binding, before the library is called."""
+    x = np.zeros((5, 20), np.float32)
+    y = (np.arange(20) % 2).astype(np.uint8)
+    good = np.zeros((3, 20), np.int32)
+    with pytest.raises(ValueError, match="index map"):
+        mdfs.max_ig_batch(x, y, good[:, :19], None, n_jobs=3)
+    with pytest.raises(ValueError, match="index map"):
+        mdfs.max_ig_batch(x, y, good, good[:2], n_jobs=3)
+    with pytest.raises(ValueError, match="index map"):
+        mdfs.max_ig_batch(x, y, good, None, n_jobs=4)
+
+
+def test_fit_mask_of_the_wrong_length_is_refused():
+    ig = np.ones(10, np.float32)
+    with pytest.raises(ValueError, match="irrelevant_mask"):
+        mdfs.ig_lim(ig, 1, 1, 1, np.ones(9, np.uint8))
