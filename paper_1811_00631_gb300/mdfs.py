@@ -62,7 +62,7 @@ def load(path: str = LIB_PATH):
         if _lib is not None:
             return _lib
         if not os.path.exists(path):
-            raise RuntimeError(f"MDFS CUDA library not built ({path} missing); run __graft_entry__.build()")
+            raise RuntimeError(f"MDFS CUDA library not built ({path} missing); run python -m paper_1811_00631_gb300.build")
         lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         lib.mdfs_discretize.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_double,

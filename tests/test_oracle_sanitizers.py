@@ -1,6 +1,6 @@
 """The C oracle under AddressSanitizer and UndefinedBehaviorSanitizer.
 
-A small driver (written here, test infrastructure) calls every oracle entry
+A small harness program (written here, test infrastructure) calls every oracle entry
 point on tiny seeded inputs: all class counts, k = 1..5, ragged N, the
 chi^2 fit with and without a mask, the contrast shuffle.  It is compiled with
 -fsanitize=address,undefined and no recovery, so any out-of-bounds access,
@@ -14,7 +14,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-DRIVER = r"""
+HARNESS = r"""
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -74,9 +74,9 @@ def test_oracle_under_address_and_undefined_behaviour_sanitizers(tmp_path):
     gcc = shutil.which("gcc")
     if gcc is None:
         pytest.skip("no gcc")
-    drv = tmp_path / "driver.c"
-    drv.write_text(DRIVER)
-    exe = tmp_path / "driver"
+    drv = tmp_path / "harness.c"
+    drv.write_text(HARNESS)
+    exe = tmp_path / "harness"
     cmd = [gcc, "-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
            os.path.join(ROOT, "oracle", "mdfs_oracle.c"), str(drv), "-lm", "-o", str(exe)]
     built = subprocess.run(cmd, capture_output=True, text=True)
