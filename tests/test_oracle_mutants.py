@@ -87,6 +87,25 @@ MUTANTS = [
      "for (uint32_t r = 0; r < 10; ++r) {", "for (uint32_t r = 0; r < 4; ++r) {"),
     ("contrast Feistel round that drops the left half",
      "uint32_t nl = R, nr = (L ^ out[0]) & mask;", "uint32_t nl = R, nr = out[0] & mask;"),
+    ("cut positions without the lower clamp",
+     "if (p < j) p = j;", "if (0) p = j;"),
+    ("cut positions without the upper clamp",
+     "if (p > N - c + j) p = N - c + j;", "if (0) p = N - c + j;"),
+    ("threshold read one position low",
+     "if (xs >= sorted[pos[j]]) code++;", "if (xs >= sorted[pos[j] - 1]) code++;"),
+    ("shares that do not depend on the discretisation",
+     "uint32_t ctr[4] = {(uint32_t)(j / 4), (uint32_t)v, (uint32_t)d, 0x4D444653u};",
+     "uint32_t ctr[4] = {(uint32_t)(j / 4), (uint32_t)v, 0u, 0x4D444653u};"),
+    ("shares that do not depend on the variable",
+     "uint32_t ctr[4] = {(uint32_t)(j / 4), (uint32_t)v, (uint32_t)d, 0x4D444653u};",
+     "uint32_t ctr[4] = {(uint32_t)(j / 4), 0u, (uint32_t)d, 0x4D444653u};"),
+    ("class-1 pseudocount from the class-0 size",
+     "*beta1 = xi * (double)n1 / mn;", "*beta1 = xi * (double)n0 / mn;"),
+    ("k = 3 joint set with the first partner twice",
+     "const uint8_t* csi[3] = {c1, c2, ci};", "const uint8_t* csi[3] = {c1, c1, ci};"),
+    ("k = 2 runner-up not tracked",
+     "if (g > best) { runner = best; best = g; bd = d; bs[0] = m; }\n                    else if (g > runner) runner = g;",
+     "if (g > best) { runner = best; best = g; bd = d; bs[0] = m; }\n                    else if (0) runner = g;"),
     ("contrast sources with replacement",
      "oracle_shuffle_index((uint32_t)(j % M), (uint32_t)M, 0xFFFFFFFFu, seed);",
      "oracle_shuffle_index((uint32_t)(j % M), (uint32_t)M, (uint32_t)j, seed);"),

@@ -102,6 +102,17 @@ def test_share_distribution():
     assert fr.std() > 0.05
 
 
+def test_each_discretisation_draws_its_own_thresholds():
+    """The discretisation is repeated with fresh random thresholds (section
+    "Algorithm and implementation"): with range > 0 the cut positions of one
+    variable differ between discretisations, and so do those of different
+    variables within one discretisation."""
+    N, div = 2000, 2
+    per_disc = {tuple(oracle.cut_positions(N, div, 0, d, 0.5, seed=4)) for d in range(20)}
+    per_var = {tuple(oracle.cut_positions(N, div, v, 0, 0.5, seed=4)) for v in range(20)}
+    assert len(per_disc) >= 18 and len(per_var) >= 18
+
+
 def test_ties_go_to_upper_class():
     x = np.array([[0, 1, 1, 1, 2, 3]], dtype=np.float32)
     codes = oracle.discretize(x, 1, 1, 0.0, seed=1)  # position 3 -> threshold 1.0
@@ -333,14 +344,16 @@ def _brute_max(codes, y, c, k, xi, i):
     k - 1 distinct variables other than i in lexicographic order (Eq. 1), the
     first maximum kept, with SH in the paper's -sum (n+b) ln p form."""
     D, M, _ = codes.shape
-    best, arg = -np.inf, None
+    vals = []
     for d in range(D):
         for S in itertools.combinations([m for m in range(M) if m != i], k - 1):
             cols = [codes[d, s] for s in S]
             g = _sh_from_probabilities(cols, y, c, xi) - _sh_from_probabilities(cols + [codes[d, i]], y, c, xi)
-            if g > best:
-                best, arg = g, (d, S)
-    return best, arg
+            vals.append((g, (d, S)))
+    best = max(g for g, _ in vals)
+    pos = next(j for j, (g, _) in enumerate(vals) if g == best)  # the first maximum
+    second = max((g for j, (g, _) in enumerate(vals) if j != pos), default=-np.inf)
+    return best, vals[pos][1], second
 
 
 @pytest.mark.parametrize("k", [2, 3])
@@ -359,10 +372,11 @@ def test_max_ig_brute_force_negative_gains(k):
     res = oracle.max_ig(codes, y, c, k, xi)
     negative = 0
     for i in range(M):
-        best, arg = _brute_max(codes, y, c, k, xi, i)
+        best, arg, second = _brute_max(codes, y, c, k, xi, i)
         negative += best < 0
         assert res["ig"][i] == pytest.approx(best, abs=1e-9)
         assert (int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])) == arg
+        assert res["second"][i] == pytest.approx(second, abs=1e-9)  # best over every other (d, S)
     assert negative >= 2, "the case must hold variables whose every gain is negative"
 
 
@@ -398,9 +412,10 @@ def test_max_ig_ties_go_to_lowest_disc_and_tuple():
     for k in (2, 3):
         res = oracle.max_ig(codes, y, c, k, xi)
         for i in range(5):
-            best, arg = _brute_max(codes, y, c, k, xi, i)
+            best, arg, second = _brute_max(codes, y, c, k, xi, i)
             assert res["ig"][i] == pytest.approx(best, abs=1e-9)
             assert (int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])) == arg
+            assert res["second"][i] == pytest.approx(second, abs=1e-9)
         assert res["disc"][0] == 0 and tuple(res["tuples"][0])[0] == 1  # partner 1 of the three copies
 
 
