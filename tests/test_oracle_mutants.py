@@ -106,6 +106,25 @@ MUTANTS = [
     ("k = 2 runner-up not tracked",
      "if (g > best) { runner = best; best = g; bd = d; bs[0] = m; }\n                    else if (g > runner) runner = g;",
      "if (g > best) { runner = best; best = g; bd = d; bs[0] = m; }\n                    else if (0) runner = g;"),
+    ("k = 1 argmax keeps the last of equal maxima",
+     "if (g > best) { runner = best; best = g; bd = d; }", "if (g >= best) { runner = best; best = g; bd = d; }"),
+    ("k = 3 runner-up not tracked",
+     "bs[0] = m1; bs[1] = m2; }\n                        else if (g > runner) runner = g;",
+     "bs[0] = m1; bs[1] = m2; }\n                        else if (0) runner = g;"),
+    ("k = 4 runner-up not tracked",
+     "bs[2] = m3; }\n                            else if (g > runner) runner = g;",
+     "bs[2] = m3; }\n                            else if (0) runner = g;"),
+    ("k = 5 runner-up not tracked",
+     "} else if (g > runner) runner = g;\n                            }", "} else if (0) runner = g;\n                            }"),
+    ("k = 4 third partner may repeat the second",
+     "for (int m3 = m2 + 1; m3 < M; ++m3) {\n                            if (m3 == i) continue;\n"
+     "                            const uint8_t* c3 = codes + ((size_t)d * M + m3) * N;\n"
+     "                            const uint8_t* cs[3]",
+     "for (int m3 = m2; m3 < M; ++m3) {\n                            if (m3 == i) continue;\n"
+     "                            const uint8_t* c3 = codes + ((size_t)d * M + m3) * N;\n"
+     "                            const uint8_t* cs[3]"),
+    ("k = 5 fourth partner may repeat the third",
+     "for (int m4 = m3 + 1; m4 < M; ++m4)", "for (int m4 = m3; m4 < M; ++m4)"),
     ("contrast sources with replacement",
      "oracle_shuffle_index((uint32_t)(j % M), (uint32_t)M, 0xFFFFFFFFu, seed);",
      "oracle_shuffle_index((uint32_t)(j % M), (uint32_t)M, (uint32_t)j, seed);"),

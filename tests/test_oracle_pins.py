@@ -340,31 +340,32 @@ def test_max_ig_brute_force(k):
 
 
 def _brute_max(codes, y, c, k, xi, i):
-    """Max of IG(i | S) over discretisations d ascending and partner sets S of
-    k - 1 distinct variables other than i in lexicographic order (Eq. 1), the
-    first maximum kept, with SH in the paper's -sum (n+b) ln p form."""
+    """IG(i | S) for every discretisation d and every set S of k - 1 distinct
+    variables other than i (Eq. 1), in the order (d ascending, S
+    lexicographic), with SH in the paper's -sum (n+b) ln p form.  Returns
+    (max, runner-up over every other (d, S), {(d, S): IG} in that order)."""
     D, M, _ = codes.shape
-    vals = []
+    table = {}
     for d in range(D):
         for S in itertools.combinations([m for m in range(M) if m != i], k - 1):
             cols = [codes[d, s] for s in S]
-            g = _sh_from_probabilities(cols, y, c, xi) - _sh_from_probabilities(cols + [codes[d, i]], y, c, xi)
-            vals.append((g, (d, S)))
-    best = max(g for g, _ in vals)
-    pos = next(j for j, (g, _) in enumerate(vals) if g == best)  # the first maximum
-    second = max((g for j, (g, _) in enumerate(vals) if j != pos), default=-np.inf)
-    return best, vals[pos][1], second
+            table[(d, S)] = (_sh_from_probabilities(cols, y, c, xi)
+                             - _sh_from_probabilities(cols + [codes[d, i]], y, c, xi))
+    vals = sorted(table.values(), reverse=True)
+    return vals[0], (vals[1] if len(vals) > 1 else -np.inf), table
 
 
-@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_max_ig_brute_force_negative_gains(k):
     """Few samples, three classes and a large xi: the pseudocounts make most
     gains negative.  The maximum still ranges only over sets of k - 1 distinct
     variables other than i (Eq. 1), even where every such gain is below zero
     (a set holding i itself, or one variable twice, would score 0 or a
-    lower-order gain instead)."""
+    lower-order gain instead).  Many (d, S) tie here in exact arithmetic, so
+    the reported (d, S) must be a maximiser within rounding, and the runner-up
+    must be the best of the other candidates."""
     rng = np.random.default_rng(40 + k)
-    N, M, c, D, xi = 10, 5, 3, 2, 0.9
+    N, M, c, D, xi = 10, 6, 3, 2, 0.9
     x = rng.standard_normal((M, N)).astype(np.float32)
     y = (rng.random(N) < 0.5).astype(np.uint8)
     y[0], y[1] = 0, 1
@@ -372,11 +373,13 @@ def test_max_ig_brute_force_negative_gains(k):
     res = oracle.max_ig(codes, y, c, k, xi)
     negative = 0
     for i in range(M):
-        best, arg, second = _brute_max(codes, y, c, k, xi, i)
+        best, second, table = _brute_max(codes, y, c, k, xi, i)
         negative += best < 0
+        d, S = int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])
+        assert len(set(S)) == k - 1 and i not in S and list(S) == sorted(S)
         assert res["ig"][i] == pytest.approx(best, abs=1e-9)
-        assert (int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])) == arg
-        assert res["second"][i] == pytest.approx(second, abs=1e-9)  # best over every other (d, S)
+        assert table[(d, S)] == pytest.approx(best, abs=1e-9)
+        assert res["second"][i] == pytest.approx(second, abs=1e-9)
     assert negative >= 2, "the case must hold variables whose every gain is negative"
 
 
@@ -409,14 +412,17 @@ def test_max_ig_ties_go_to_lowest_disc_and_tuple():
     y = ((x[0] > 0) ^ (x[1] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
     codes = oracle.discretize(x, c - 1, D, 0.0, seed=1)
     assert all(np.array_equal(codes[0], codes[d]) for d in range(D))
-    for k in (2, 3):
+    for k in (1, 2, 3):
         res = oracle.max_ig(codes, y, c, k, xi)
         for i in range(5):
-            best, arg, second = _brute_max(codes, y, c, k, xi, i)
+            best, second, table = _brute_max(codes, y, c, k, xi, i)
+            first = next(key for key, g in table.items() if g >= best - 1e-9)  # lowest (d, S) of the tie
             assert res["ig"][i] == pytest.approx(best, abs=1e-9)
-            assert (int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])) == arg
+            assert (int(res["disc"][i]), tuple(int(t) for t in res["tuples"][i])) == first
             assert res["second"][i] == pytest.approx(second, abs=1e-9)
-        assert res["disc"][0] == 0 and tuple(res["tuples"][0])[0] == 1  # partner 1 of the three copies
+        assert res["disc"][0] == 0
+        if k > 1:
+            assert tuple(res["tuples"][0])[0] == 1  # partner 1 of the three copies
 
 
 def test_xor_pair_invisible_in_1d_found_in_2d():
