@@ -38,7 +38,13 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_abi_version_and_error_string(lib):
     assert lib.mdfs_abi_version() == 1
-    assert lib.mdfs_last_error() == b""
+    # the message is thread-local: a thread that has made no call sees ""
+    import threading
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(lib.mdfs_last_error()))
+    t.start()
+    t.join()
+    assert seen == [b""]
 
 
 def test_binding_names_match_header():
