@@ -21,10 +21,12 @@
  *   (an N x M column-major matrix with leading dimension N).
  * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  A
  *   call with device outputs is stream-ordered on `stream` but waits once for
- *   the 16-byte validation result of its inputs; a call with host outputs, or
- *   with stream == NULL, returns after its results are complete.  Calls on
- *   different streams may run concurrently; calls sharing one stream from
- *   several host threads must be serialised by the caller.
+ *   the 16-byte validation result of its inputs; scans that run a tensor-core
+ *   kernel (k = 2 with 2 or 3 classes, k = 3 with 2 classes) also wait for
+ *   their kernels, to read the kernel's error flag.  A call with host
+ *   outputs, or with stream == NULL, returns after its results are complete.
+ *   Calls on different streams may run concurrently; calls sharing one stream
+ *   from several host threads must be serialised by the caller.
  * Errors: 0 on success, a negative MDFS_E* code otherwise; mdfs_last_error()
  *   then describes the failure (thread-local string).  On error no output is
  *   guaranteed to have been written.
@@ -53,7 +55,7 @@ extern "C" {
 #define MDFS_ENONFINITE (-3)  /* x holds NaN or +-Inf                                 */
 #define MDFS_ENOMEM (-4)      /* device workspace allocation failed                   */
 #define MDFS_ECUDA (-5)       /* a CUDA runtime call or kernel launch failed          */
-#define MDFS_ETIMEOUT (-6)    /* reserved for bounded device-side waits               */
+#define MDFS_ETIMEOUT (-6)    /* a bounded device-side wait gave up (tensor cores)    */
 #define MDFS_ETRUNCATED (-7)  /* more output records than the caller's capacity        */
 
 /* x element types */
