@@ -104,6 +104,7 @@ class Server:
         self.n_slots = n_slots
         self._log_path = log_path  # JSON line per finished, failed or expired job
         self._log_lock = threading.Lock()
+        self.log_errors = 0
         self.device = device
         self.estimate = estimate
         if memory_budget is None:
@@ -257,8 +258,11 @@ class Server:
                "evals": evals, "queue_s": (t_start if t_start is not None else t_end) - t_sub, "run_s": run_s,
                "latency_s": t_end - t_sub, "evals_per_s": evals / run_s if run_s else None, "slot": slot,
                "status": status}
-        with self._log_lock, open(self._log_path, "a") as f:
-            f.write(json.dumps(rec) + "\n")
+        try:  # a record that cannot be written must not take down the slot
+            with self._log_lock, open(self._log_path, "a") as f:
+                f.write(json.dumps(rec) + "\n")
+        except (OSError, TypeError, ValueError):
+            self.log_errors += 1
 
 
 def _run_on_gpu(job: Job, stream, device: int):

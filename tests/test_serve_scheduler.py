@@ -187,3 +187,16 @@ def test_per_job_records(tmp_path):
     assert recs[0]["latency_s"] >= recs[0]["run_s"] and recs[0]["queue_s"] >= 0
     assert recs[1]["status"].startswith("error: ValueError")
     assert recs[2]["status"] == "expired" and recs[2]["run_s"] is None
+
+
+def test_unwritable_record_does_not_stop_the_slot(tmp_path):
+    """A log path that cannot be written (here a directory) only counts the
+    lost records; every job still completes on the one slot."""
+    def executor(job, slot):
+        return (np.array([job.tag]), None, None, None, None, None)
+
+    srv = serve.Server(n_slots=1, memory_budget=10, executor=executor, estimate=_estimate, log_path=str(tmp_path))
+    futs = [srv.submit(FakeJob(need=1, dur=0, tag=i)) for i in range(3)]
+    assert [f.result(timeout=5).ig[0] for f in futs] == [0, 1, 2]
+    srv.close()
+    assert srv.log_errors == 3
