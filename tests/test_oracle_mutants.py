@@ -125,6 +125,21 @@ MUTANTS = [
      "                            const uint8_t* cs[3]"),
     ("k = 5 fourth partner may repeat the third",
      "for (int m4 = m3 + 1; m4 < M; ++m4)", "for (int m4 = m3; m4 < M; ++m4)"),
+    ("class sizes counted with the labels swapped",
+     "for (int s = 0; s < N; ++s) n1 += y[s] ? 1 : 0;", "for (int s = 0; s < N; ++s) n1 += y[s] ? 0 : 1;"),
+    ("voxel counts with the labels swapped",
+     "if (y[s]) n1[vox]++; else n0[vox]++;", "if (y[s]) n0[vox]++; else n1[vox]++;"),
+    ("single-set gain with the sign flipped", "return sh_s - sh_si;", "return sh_si - sh_s;"),
+    ("even-df chi^2 tail series one term long",
+     "for (int j = 0; j < df / 2; ++j) {", "for (int j = 0; j <= df / 2; ++j) {"),
+    ("fit takes variables with F = 0 into the likelihood",
+     "if (u <= 0.0) continue;", "if (u < 0.0) continue;"),
+    ("IG_lim bisection moving the wrong end",
+     "if (oracle_chi2_cdf(mid, df) < target) lo = mid; else hi = mid;",
+     "if (oracle_chi2_cdf(mid, df) < target) hi = mid; else lo = mid;"),
+    ("contrast samples left unshuffled",
+     "row[i] = x[(size_t)s * N + oracle_shuffle_index((uint32_t)i, (uint32_t)N, (uint32_t)j, seed)];",
+     "row[i] = x[(size_t)s * N + i];"),
     ("contrast sources with replacement",
      "oracle_shuffle_index((uint32_t)(j % M), (uint32_t)M, 0xFFFFFFFFu, seed);",
      "oracle_shuffle_index((uint32_t)(j % M), (uint32_t)M, (uint32_t)j, seed);"),
