@@ -441,6 +441,26 @@ def test_xor_pair_invisible_in_1d_found_in_2d():
     assert r2["ig"][0] > 10 * np.median(r2["ig"])
 
 
+def test_three_way_parity_needs_k3():
+    """Synergy of three variables (section "Introduction"): y is the parity of
+    x0, x3, x5, so no single member and no pair carries information about y;
+    IG stays at the noise level for k = 1 and 2 and jumps at k = 3, where
+    each member's argmax partners are the other two."""
+    rng = np.random.default_rng(33)
+    N, M = 400, 7
+    codes = rng.integers(0, 2, (1, M, N)).astype(np.uint8)
+    members = [0, 3, 5]
+    y = (np.bitwise_xor.reduce(codes[0, members], axis=0) ^ (rng.random(N) < 0.05)).astype(np.uint8)
+    r1 = oracle.max_ig(codes, y, 2, 1, 0.25)
+    r2 = oracle.max_ig(codes, y, 2, 2, 0.25)
+    r3 = oracle.max_ig(codes, y, 2, 3, 0.25)
+    assert r1["ig"].max() < 10.0 and r2["ig"].max() < 15.0
+    for v in members:
+        assert r3["ig"][v] > 150.0
+        assert sorted(r3["tuples"][v].tolist()) == [m for m in members if m != v]
+    assert max(r3["ig"][v] for v in range(M) if v not in members) < 20.0
+
+
 def test_five_way_parity_needs_k5():
     """y is the parity of five variables: every proper subset of them is
     independent of y, so IG stays at the noise level up to k = 4 and jumps
