@@ -145,7 +145,7 @@ def test_deadline_drops_a_job_blocked_behind_the_memory_budget():
         time.sleep(job.dur)
         return (np.array([job.tag]), None, None, None, None, None)
 
-    big = FakeJob(need=8, dur=0.4, tag=0)
+    big = FakeJob(need=8, dur=1.5, tag=0)
     waiting = FakeJob(need=8, dur=0.01, tag=1)
     waiting.deadline_s = 0.1
     srv = serve.Server(n_slots=2, memory_budget=10, executor=executor, estimate=_estimate)
@@ -153,7 +153,7 @@ def test_deadline_drops_a_job_blocked_behind_the_memory_budget():
     f_big, f_wait = srv.submit(big), srv.submit(waiting)
     with pytest.raises(TimeoutError):
         f_wait.result(timeout=5)
-    assert time.perf_counter() - t0 < 0.35  # dropped before the big job released the budget
+    assert time.perf_counter() - t0 < 1.2  # dropped before the big job released the budget
     assert f_big.result(timeout=5).ig[0] == 0
     srv.close()
 

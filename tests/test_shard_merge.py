@@ -144,8 +144,10 @@ def _recovery_rank(rank, world, port, ckpt, out_path, fail_rank):
         time.sleep(0.05)
         return per_shard[s]
 
+    # a dead rank is given up on after 2 s; without a failure the wait is long,
+    # so a slow but live rank is never taken for dead on a loaded machine
     keys, failed = shard.run_ranks_with_recovery(scan, len(per_shard), ckpt, {"k": 2, "seed": 9}, rank, world, store,
-                                                 timeout_s=2.0)
+                                                 timeout_s=2.0 if fail_rank >= 0 else 60.0)
     np.save(out_path + f".{rank}.npy", keys)
     with open(out_path + f".{rank}.failed", "w") as f:
         f.write(",".join(map(str, failed)))
