@@ -99,3 +99,15 @@ def test_k5_limits_need_no_gpu(lib):
     assert call(569, 1, 1) == -1 and b"C(M, 4)" in lib.mdfs_last_error()  # C(569, 4) > 2^32
     assert call(500, 1, 2, shard=True) == -1 and b"shard" in lib.mdfs_last_error()  # 2 C(500, 4) > 2^32
     assert call(4, 1, 1) == -1 and b"smaller than k" in lib.mdfs_last_error()
+
+
+def test_profile_report_and_release_without_work(lib):
+    """Tracing switches and an empty report need no GPU: nothing recorded
+    gives an empty report; releasing with no workspace succeeds."""
+    import ctypes
+    assert lib.mdfs_profile(1) == 0
+    buf = ctypes.create_string_buffer(64)
+    assert lib.mdfs_profile_report(buf, 64) == 0
+    assert buf.value == b""
+    assert lib.mdfs_profile(0) == 0
+    assert lib.mdfs_release() == 0
