@@ -4,6 +4,7 @@ job against the FP64 oracle."""
 import numpy as np
 import pytest
 
+import argmax_rule
 import oracle
 from paper_1811_00631_gb300 import synth
 
@@ -107,8 +108,8 @@ def test_batched_full_size_sampled(cuda):
     times: N = 1000 x M = 20000 (100 planted XOR pairs), 3 classes, 10
     discretisations, 16 bootstrap folds x 4 label permutations = 64 jobs in one
     call.  Sampled jobs and variables are compared with the FP64 oracle (IG
-    within 1e-4 + 1e-5 |o|; an argmax that differs must be an equally good
-    maximiser), one job with the single-job scan bit for bit, and job 0 (the
+    within 1e-4 + 1e-5 |o|; an argmax that differs only where the oracle's
+    top two lie within that tolerance), one job with the single-job scan bit for bit, and job 0 (the
     unpermuted labels) must name the planted partner of every XOR member."""
     torch = cuda
     from paper_1811_00631_gb300 import mdfs
@@ -137,13 +138,12 @@ def test_batched_full_size_sampled(cuda):
         ref = oracle.max_ig(codes, yj, c, 2, xi, variables=variables)
         for row, i in enumerate(variables):
             o = ref["ig"][row]
-            tol = 1e-4 + 1e-5 * abs(o)
-            assert abs(float(ig[j, i]) - o) <= tol, f"job {j} var {i}: gpu {ig[j, i]!r} oracle {o!r}"
+            assert abs(float(ig[j, i]) - o) <= argmax_rule.tol(o), f"job {j} var {i}: gpu {ig[j, i]!r} oracle {o!r}"
             if di[j, i] != ref["disc"][row] or tu[j, i, 0] != ref["tuples"][row, 0]:
                 m = int(tu[j, i, 0])
                 assert 0 <= m < M and m != i and 0 <= di[j, i] < D
                 alt = oracle.ig_one(codes, yj, c, xi, int(di[j, i]), int(i), [m])
-                assert abs(alt - o) <= 2 * tol, f"job {j} var {i}: gpu argmax gives {alt}, oracle max {o}"
+                argmax_rule.check_alternative(o, ref["second"][row], alt, f"job {j} var {i}")
 
     j = 63
     w_ig, w_tu, w_di = mdfs.max_ig(torch.from_numpy(np.ascontiguousarray(ds.x[:, si[j]])).cuda(),
