@@ -13,7 +13,8 @@
  * ---------------------------------------
  * Pointers: every array argument may be a host pointer or a device pointer of
  *   the current CUDA device; the library tells them apart with
- *   cudaPointerGetAttributes.  Host inputs are copied to the device inside the
+ *   cudaPointerGetAttributes, and refuses device memory of another GPU with
+ *   MDFS_EINVAL.  Host inputs are copied to the device inside the
  *   call; host outputs are written before the call returns.  All outputs are
  *   owned by the caller.  The library keeps only a cached device workspace per
  *   (device, stream), which mdfs_release() frees.
@@ -284,10 +285,13 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
  * the array size.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  All calls share the array: two calls whose work overlaps on the
- * GPU (different streams, or different host threads) race and must not be
- * issued; serialise them.  The call waits once for a 16-byte validation read
- * of the inputs; with a non-NULL stream the rest is stream-ordered.
+ * capture begins.  The address is kept until mdfs_release(), which a caller
+ * must call after a cudaDeviceReset before the next call.  All calls share the
+ * array and it keeps the last call's contents: two calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and must not
+ * be issued; serialise them.  Every call copies a 16-byte validation result of
+ * its inputs to a host buffer and synchronises its stream before the scan
+ * kernels are enqueued; with a non-NULL stream the rest is stream-ordered.
  */
 #define MDFS_NOALLOC_SCRATCH_BYTES (32u << 20)
 int mdfs_max_ig_noalloc(const mdfs_data* data, int k, int divisions, int discretizations, double range,
@@ -300,6 +304,12 @@ const char* mdfs_last_error(void);
 /* Frees every cached device workspace of this process.  No call may be in
  * flight.  Returns 0. */
 int mdfs_release(void);
+
+/* Frees the cached device workspace of one (current device, stream) pair,
+ * e.g. when a long-lived stream that ran a large job goes on with small ones.
+ * No call may be in flight on that stream.  Returns 0 (also when the stream
+ * has no workspace). */
+int mdfs_release_stream(void* stream);
 
 /* ABI version, currently 1. */
 int mdfs_abi_version(void);

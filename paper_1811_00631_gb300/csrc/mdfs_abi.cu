@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "../../include/mdfs.h"
+#include "../../include/mdfs_testing.h"
 #include "mdfs_internal.cuh"
 
 using namespace mdfs;
@@ -114,6 +116,17 @@ int kernel_flag_error(int flag, int job = -1) {
     return fail(MDFS_ETIMEOUT, "%sa device-side wait timed out in a tensor-core kernel", where);
 }
 
+// Test hooks of the triple kernel set by mdfs_testing_k3_wait_fault, taken
+// (and cleared) by the next k = 3 tensor-core scan of any thread.
+std::mutex g_hooks_mu;
+TcTestHooks g_hooks;
+TcTestHooks take_test_hooks() {
+    std::lock_guard<std::mutex> lock(g_hooks_mu);
+    TcTestHooks h = g_hooks;
+    g_hooks = TcTestHooks();
+    return h;
+}
+
 Workspace* get_ws(cudaStream_t st, int* err) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -137,6 +150,34 @@ Workspace* get_ws(cudaStream_t st, int* err) {
     Workspace* raw = ws.get();
     g_ws[key] = std::move(ws);
     return raw;
+}
+
+// Device index of p when it is device memory of a GPU other than the current
+// one (the library would hand it to the current device's kernels); -1 for
+// host memory, managed memory, device memory of the current GPU or NULL.
+int foreign_device(const void* p) {
+    if (!p) return -1;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (a.type != cudaMemoryTypeDevice) return -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return a.device == dev ? -1 : a.device;
+}
+
+// MDFS_EINVAL naming the first argument that lives on another GPU.
+int check_devices(std::initializer_list<std::pair<const void*, const char*>> ptrs) {
+    for (const auto& pr : ptrs) {
+        const int d = foreign_device(pr.first);
+        if (d >= 0) return fail(MDFS_EINVAL, "%s is device memory of GPU %d, not of the current device", pr.second, d);
+    }
+    return MDFS_OK;
 }
 
 bool is_device_ptr(const void* p) {
@@ -367,9 +408,11 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
 // keys of the unsharded scan.
 // emit != NULL: interesting-tuple emission into that table; the scan then runs on
 // the popcount kernels (the tensor-core kernels do not emit).
+// dump != NULL (test hook, mdfs_testing_counts): the tensor-core kernel also
+// writes its class counts there; the call fails if that kernel does not apply.
 int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, int k, int divisions, int D, double range,
               double pc_xi, uint64_t seed, bool* check_err, int shard = 0, int n_shards = 1,
-              const EmitTable* emit = nullptr) {
+              const EmitTable* emit = nullptr, uint32_t* dump = nullptr) {
     cudaStream_t st = ws->stream;
     auto share = [&](int n, int* lo) {
         *lo = (int)((long long)n * shard / n_shards);
@@ -408,6 +451,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     TcGeom tg = make_tc_geom(n0, n1);
+    if (dump && !use_tc2 && !use_tc3)
+        return fail(MDFS_EINVAL, "no tensor-core kernel serves k = %d, %d classes, N0 = %d, N1 = %d", k, c, n0, n1);
     uint8_t* onehot = nullptr;
     if (use_tc2 || use_tc3) {
         MDFS_ENSURE(ws, onehot, (size_t)D * M * P * tg.Kp);
@@ -437,7 +482,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         int lo = 0;
         const int cnt = share(ws->n_items3, &lo);
         MDFS_LAUNCH("k2", st, launch_k2tc(map, tg, M, c, 0, D, (const int2*)ws->items3.p + lo, cnt, tab,
-                                          k3tc_fraction_bits(N), cnt1, sh1, keys, (int*)ws->err.p, st));
+                                          k3tc_fraction_bits(N), cnt1, sh1, keys, (int*)ws->err.p, st, dump));
         *check_err = true;
     } else if (k == 2) {
         if (shard == 0)
@@ -477,6 +522,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         MDFS_LAUNCH("k3_operand", st, launch_k3tc_operand(onehot, (uint8_t*)ws->onehot2.p, lperm, M, D, tg, st));
         CUtensorMap map;
         MDFS_CUDA_TRY(make_onehot_map(&map, (const uint8_t*)ws->onehot2.p, M, D, tg.Kp));
+        const TcTestHooks hooks = take_test_hooks();
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
@@ -485,7 +531,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             const int cnt = share(ws->n_items2, &lo);
             MDFS_LAUNCH("k3", st, launch_k3tc(map, (const uint8_t*)ws->onehot2.p, tg, M, d0, nn,
                                               (const int2*)ws->items2.p + lo, cnt, tab, fbits, (const int*)ws->cnt1s.p,
-                                              lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, st));
+                                              lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, st, dump,
+                                              hooks));
         }
         *check_err = true;
     } else if (k == 3) {
@@ -728,9 +775,31 @@ int mdfs_profile_report(char* buf, int len) {
     return rc;
 }
 
+int mdfs_release_stream(void* stream) {
+    g_err.clear();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MDFS_ECUDA, "no CUDA device is available");
+    }
+    std::unique_ptr<Workspace> ws;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = g_ws.find(std::make_pair(dev, (cudaStream_t)stream));
+        if (it == g_ws.end()) return MDFS_OK;
+        ws = std::move(it->second);
+        g_ws.erase(it);
+    }
+    // the workspace's buffers are freed here, outside the lock
+    return MDFS_OK;
+}
+
 int mdfs_release(void) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    g_ws.clear();
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        g_ws.clear();
+    }
+    noalloc_forget_devices();
     return MDFS_OK;
 }
 
@@ -747,6 +816,7 @@ int mdfs_discretize(const mdfs_data* data, int divisions, int discretizations, d
         return fail(MDFS_EINVAL, "discretizations = %d outside [1, %d]", discretizations, kMaxD);
     if (!(range >= 0.0 && range <= 1.0)) return fail(MDFS_EINVAL, "range must lie in [0, 1]");
     if (!codes) return fail(MDFS_EINVAL, "codes is NULL");
+    if ((rc = check_devices({{data->x, "x"}, {codes, "codes"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -777,6 +847,7 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
     if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi))) return rc;
     if (!ig) return fail(MDFS_EINVAL, "ig is NULL");
 
+    if ((rc = check_devices({{data->x, "x"}, {data->y, "y"}, {ig, "ig"}, {tuples, "tuples"}, {best_disc, "best_disc"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -824,6 +895,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi))) return rc;
     if (!ig) return fail(MDFS_EINVAL, "ig is NULL");
 
+    if ((rc = check_devices({{data->x, "x"}, {data->y, "y"}, {sample_idx, "sample_idx"}, {y_perm, "y_perm"}, {ig, "ig"}, {tuples, "tuples"}, {best_disc, "best_disc"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -899,6 +971,7 @@ int mdfs_max_ig_shard(const mdfs_data* data, int k, int divisions, int discretiz
     if (n_shards < 1 || shard < 0 || shard >= n_shards) return fail(MDFS_EINVAL, "shard %d of %d", shard, n_shards);
     if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi, true))) return rc;
     if (!keys_out) return fail(MDFS_EINVAL, "keys is NULL");
+    if ((rc = check_devices({{data->x, "x"}, {data->y, "y"}, {keys_out, "keys"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -927,6 +1000,7 @@ int mdfs_keys_decode(const uint64_t* keys, int M, int k, float* ig, int32_t* tup
     if (!keys || !ig) return fail(MDFS_EINVAL, "keys and ig must not be NULL");
     if (M < 1 || M > 65535 || k < 1 || k > 5) return fail(MDFS_EINVAL, "M or k out of range");
     int rc = 0;
+    if ((rc = check_devices({{keys, "keys"}, {ig, "ig"}, {tuples, "tuples"}, {best_disc, "best_disc"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -964,6 +1038,7 @@ int mdfs_ig_lim(const float* ig, int M, int k, int divisions, int discretization
     int df = c - 1;
     for (int j = 1; j < k; ++j) df *= c;
     int rc = 0;
+    if ((rc = check_devices({{ig, "ig"}, {irrelevant_mask, "irrelevant_mask"}, {p_values, "p_values"}, {ig_lim, "ig_lim"}, {n_eff, "n_eff"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -1015,6 +1090,7 @@ int mdfs_contrast(const mdfs_data* data, int n_contrast, uint64_t seed, void* x_
     if (n_contrast < 0 || M + n_contrast > 65535)
         return fail(MDFS_EINVAL, "n_contrast = %d: M + n_contrast must lie in [M, 65535]", n_contrast);
     if (!x_ext) return fail(MDFS_EINVAL, "x_ext is NULL");
+    if ((rc = check_devices({{data->x, "x"}, {x_ext, "x_ext"}, {src, "src"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -1044,6 +1120,7 @@ int mdfs_p_adjust(const double* p, int m, int method, double* adjusted, void* st
     if (m < 1 || m > 65536) return fail(MDFS_EINVAL, "m = %d outside [1, 65536]", m);
     if (method < MDFS_ADJUST_NONE || method > MDFS_ADJUST_BY) return fail(MDFS_EINVAL, "unknown method %d", method);
     int rc = 0;
+    if ((rc = check_devices({{p, "p"}, {adjusted, "adjusted"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -1085,6 +1162,7 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
     int df = c - 1;
     for (int j = 1; j < k; ++j) df *= c;
 
+    if ((rc = check_devices({{data->x, "x"}, {data->y, "y"}, {ig, "ig"}, {tuples, "tuples"}, {best_disc, "best_disc"}, {p_values, "p_values"}, {adjusted, "adjusted"}, {relevant, "relevant"}, {ig_lim, "ig_lim"}, {n_eff, "n_eff"}, {contrast_src, "contrast_src"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -1163,6 +1241,7 @@ int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int dis
     if (capacity < 1 || capacity > (1 << 22)) return fail(MDFS_EINVAL, "capacity = %d outside [1, 2^22]", capacity);
     if (!var || !ig || !count || (k > 1 && !tuples))
         return fail(MDFS_EINVAL, "var, ig, tuples (k > 1) and count must not be NULL");
+    if ((rc = check_devices({{data->x, "x"}, {data->y, "y"}, {var, "var"}, {tuples, "tuples"}, {ig, "ig"}, {best_disc, "best_disc"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
     if (!ws) return rc;
@@ -1226,6 +1305,47 @@ int mdfs_interesting_tuples(const mdfs_data* data, int k, int divisions, int dis
             return rc;
     }
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return MDFS_OK;
+}
+
+// ---- test-only entry points (include/mdfs_testing.h) -------------------------
+
+int mdfs_testing_counts(const mdfs_data* data, int k, int divisions, int discretizations, double range, uint64_t seed,
+                        uint32_t* counts, void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, true);
+    if (rc) return rc;
+    const int N = data->N, M = data->M, D = discretizations;
+    if (k != 2 && k != 3) return fail(MDFS_EINVAL, "k = %d: the count hook serves k = 2 and k = 3", k);
+    if ((rc = check_scan_args(k, M, divisions, N, D, range, 0.25))) return rc;
+    if (!counts) return fail(MDFS_EINVAL, "counts is NULL");
+    if (!is_device_ptr(counts) || foreign_device(counts) >= 0)
+        return fail(MDFS_EINVAL, "counts must be device memory of the current device");
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    if ((rc = stage_inputs(ws, data, true, &xd, &yd, &n1))) return rc;
+    bool check_err = false;
+    rc = scan_core(ws, xd, data->dtype, N, M, n1, k, divisions, D, range, 0.25, seed, &check_err, 0, 1, nullptr,
+                   counts);
+    if (rc) return rc;
+    MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ws->host_stats[8]) return kernel_flag_error(ws->host_stats[8]);
+    return MDFS_OK;
+}
+
+int mdfs_testing_k3_wait_fault(int withhold_kb, long long wait_ns) {
+    g_err.clear();
+    if (withhold_kb < -1) return fail(MDFS_EINVAL, "withhold_kb = %d < -1", withhold_kb);
+    if (wait_ns < 0 || wait_ns > 10000000000ll) return fail(MDFS_EINVAL, "wait_ns outside [0, 10 s]");
+    std::lock_guard<std::mutex> lock(g_hooks_mu);
+    g_hooks.withhold_kb = withhold_kb;
+    g_hooks.wait_ns = (unsigned long long)wait_ns;
     return MDFS_OK;
 }
 

@@ -183,9 +183,21 @@ int k3tc_fraction_bits(int N);
 cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D, int Kp);
 // perm [D][M]: new label -> original variable; cnt1s [D][M][2], the one-hot
 // rows of `map` and the pair records are in the new labels (see launch_k3tc_order).
+// Test hooks of the triple kernel (defaults: off).  wait_ns: limit of every
+// bounded mbarrier wait (0 = the library's 1 s); withhold_kb >= 0: the TMA
+// producer of CTA 0 never fills the stage of that K block of its running
+// count, so the consumers' wait runs out and the call reports MDFS_ETIMEOUT.
+struct TcTestHooks {
+    unsigned long long wait_ns = 0;
+    int withhold_kb = -1;
+};
+// dump != NULL (test hook): also writes the 8-voxel class counts of every
+// triple, [D][C(M,3)][8] uint32 n0 | n1 << 16, lexicographic triple rank of the
+// original variables, voxel 4 v_lo + 2 v_mid + v_hi.
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
-                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st);
+                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st,
+                        uint32_t* dump = nullptr, TcTestHooks hooks = TcTestHooks());
 // Relabelling of the k = 3 tensor path, per discretisation: new labels in
 // ascending order of the bin-1 count (ties by index) for M <= 8192, else the
 // identity.  perm [D][M] new -> original, rank [D][M] original -> new,
@@ -202,9 +214,12 @@ cudaError_t launch_k3tc_operand(const uint8_t* src, uint8_t* dst, const int* per
 bool k2tc_supported(int c);
 void build_k2tc_items(int M, int c, std::vector<int2>& items);
 size_t k2tc_smem_bytes(int N0, int N1);
+// dump != NULL (test hook): also writes the c x c class counts of every pair
+// i < m, [D][C(M,2)][c c] uint32 n0 | n1 << 16 at the pair's rank in the upper
+// triangle, voxel code_i c + code_m.
 cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
                         int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
-                        unsigned long long* keys, int* err, cudaStream_t st);
+                        unsigned long long* keys, int* err, cudaStream_t st, uint32_t* dump = nullptr);
 
 // Contrast rows M .. M + n_contrast - 1 of x_ext (dtype 0 f32, 1 i8); rows
 // 0 .. M-1 are not written.  src [n_contrast] or NULL.
@@ -239,5 +254,9 @@ cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
 
 // Sets the thread-local message that mdfs_last_error() returns.
 void record_error(const char* msg);
+
+// Drops the cached device addresses of the allocation-free entry point's
+// scratch array (mdfs_release; they are looked up again on the next call).
+void noalloc_forget_devices();
 
 }  // namespace mdfs

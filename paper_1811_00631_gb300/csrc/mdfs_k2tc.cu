@@ -91,12 +91,14 @@ __device__ __forceinline__ void complete2(const int (&X)[P][P], const int (&ni)[
 
 }  // namespace
 
-template <int P>
+// kDump: also write the c x c class counts of every pair to `dump` (test hook;
+// the scan itself is unchanged).
+template <int P, bool kDump>
 __global__ void __launch_bounds__(kThreads, 1)
     k2tc_kernel(const __grid_constant__ CUtensorMap map_oh, TcGeom tg, int M, int d0, int nd,
                 const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
                 const int* __restrict__ cnt1, const long long* __restrict__ sh1, unsigned long long* __restrict__ keys,
-                int* __restrict__ err) {
+                int* __restrict__ err, uint32_t* __restrict__ dump) {
     constexpr int C = P + 1;
     constexpr int VT = kTile / P;  // variables per tile
     extern __shared__ uint8_t dsmem_raw[];
@@ -308,6 +310,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     complete2<P>(X0, ni0, nm0, N0, T0v);
                     complete2<P>(X1, ni1, nm1, N1, T1v);
                     complete2<P>(XT, nit, nmt, N, TTv);
+                    if constexpr (kDump) {
+                        if (ok && (P == 1 || alpha == 0)) {
+                            const unsigned long long np = (unsigned long long)M * (M - 1) / 2;
+                            const unsigned long long rank =
+                                (unsigned long long)vi * (2ull * M - vi - 1) / 2 + (unsigned long long)(vm - vi - 1);
+                            uint32_t* o = dump + ((unsigned long long)d * np + rank) * (C * C);
+#pragma unroll
+                            for (int a = 0; a < C; ++a)
+#pragma unroll
+                                for (int b = 0; b < C; ++b)
+                                    o[a * C + b] = (uint32_t)T0v[a][b] | ((uint32_t)T1v[a][b] << 16);
+                        }
+                    }
                     int part = 0;
                     if (P == 1) {
 #pragma unroll
@@ -381,10 +396,11 @@ bool k2tc_supported(int c) { return c == 2 || c == 3; }
 
 cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
                         int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
-                        unsigned long long* keys, int* err, cudaStream_t st) {
+                        unsigned long long* keys, int* err, cudaStream_t st, uint32_t* dump) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = k2tc_smem_bytes(tg.N0, tg.N1);
-    const void* fn = c == 2 ? (const void*)k2tc_kernel<1> : (const void*)k2tc_kernel<2>;
+    const void* fn = c == 2 ? (dump ? (const void*)k2tc_kernel<1, true> : (const void*)k2tc_kernel<1, false>)
+                            : (dump ? (const void*)k2tc_kernel<2, true> : (const void*)k2tc_kernel<2, false>);
     if (c != 2 && c != 3) return cudaErrorInvalidValue;
     cudaError_t e = ensure_dynamic_smem(fn, smem);
     if (e != cudaSuccess) return e;
@@ -397,12 +413,16 @@ cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0,
     const long long n_tiles = (long long)n_items * nd;
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
-    if (c == 2)
-        k2tc_kernel<1><<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys,
-                                                     err);
-    else
-        k2tc_kernel<2><<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys,
-                                                     err);
+    auto launch = [&](auto kern) {
+        kern<<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys, err, dump);
+    };
+    if (c == 2) {
+        if (dump) launch(k2tc_kernel<1, true>);
+        else launch(k2tc_kernel<1, false>);
+    } else {
+        if (dump) launch(k2tc_kernel<2, true>);
+        else launch(k2tc_kernel<2, false>);
+    }
     return cudaGetLastError();
 }
 

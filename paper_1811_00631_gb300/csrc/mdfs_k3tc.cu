@@ -157,14 +157,44 @@ __device__ __forceinline__ uint32_t partner_index(uint32_t dM, int M, uint32_t p
     return (dM + min(p, q)) * (uint32_t)M + max(p, q);
 }
 
+// lexicographic rank of x < y < z among the C(M, 3) triples of [0, M)
+__device__ __forceinline__ unsigned long long triple_rank(int M, int x, int y, int z) {
+    auto c2 = [](long long n) { return n < 2 ? 0ll : n * (n - 1) / 2; };
+    auto c3 = [](long long n) { return n < 3 ? 0ll : n * (n - 1) * (n - 2) / 6; };
+    return (unsigned long long)(c3(M) - c3(M - x) + c2(M - x - 1) - c2(M - y) + (z - y - 1));
+}
+
+// Test hook: the 8 voxel counts (times 4) of the triple (a, b, e) of original
+// variables, kernel voxel order (v_a v_b v_e) = 111, 011, 101, 110, 001, 010,
+// 100, 000, written as n0 | n1 << 16 at dump[(d C(M,3) + rank) 8 + v] with v =
+// 4 v_lo + 2 v_mid + v_hi in the sorted order lo < mid < hi.
+struct Vox8 {
+    int v[8];
+};
+__device__ __noinline__ void dump_triple(uint32_t* dump, int M, int d, int a, int b, int e, Vox8 n0, Vox8 n1) {
+    const int lo = min(a, min(b, e)), hi = max(a, max(b, e)), mid = a + b + e - lo - hi;
+    const int wa = 4 >> ((a > b) + (a > e)), wb = 4 >> ((b > a) + (b > e)), we = 4 >> ((e > a) + (e > b));
+    const unsigned long long c3 = (unsigned long long)M * (M - 1) * (M - 2) / 6;
+    uint32_t* o = dump + ((unsigned long long)d * c3 + triple_rank(M, lo, mid, hi)) * 8;
+    const int va[8] = {1, 0, 1, 1, 0, 0, 1, 0}, vb[8] = {1, 1, 0, 1, 0, 1, 0, 0}, ve[8] = {1, 1, 1, 0, 1, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        o[va[j] * wa + vb[j] * wb + ve[j] * we] = (uint32_t)(n0.v[j] >> 2) | ((uint32_t)(n1.v[j] >> 2) << 16);
+}
+
 }  // namespace
 
+// kDump: also write the 8-voxel class counts of every triple to `dump` (test
+// hook; the scan itself is unchanged).  wait_ns bounds every mbarrier wait;
+// withhold_kb >= 0 makes the producer of CTA 0 skip the copies of that K block
+// of its running count (test hook: the consumers' bounded wait then runs out).
+template <bool kDump>
 __global__ void __launch_bounds__(kThreads, 1)
     k3tc_kernel(const __grid_constant__ CUtensorMap map_oh, const uint8_t* __restrict__ oh, TcGeom tg, int M, int d0,
                 int nd, const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
                 const int* __restrict__ cnt1s, const int* __restrict__ perm, const PairC* __restrict__ pairs,
-                unsigned long long* __restrict__ keys,
-                int* __restrict__ err) {
+                unsigned long long* __restrict__ keys, int* __restrict__ err, uint32_t* __restrict__ dump,
+                unsigned long long wait_ns, int withhold_kb) {
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
@@ -226,6 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (warp == 0) {
         // ------------------------------ TMA producer ------------------------------
         if (lane == 0 && !*abort) {
+            const int withhold = blockIdx.x == 0 ? withhold_kb : -1;
             uint32_t g = 0;  // running K-block counter across this CTA's tiles
             int pend_mask = 0;
             uint32_t pend_use[kStages] = {};
@@ -239,10 +270,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int s = (int)(g % kStages);
                     const uint32_t use = g / kStages;
-                    if (use > 0 && !tc::mbar_wait(&bar_empty[s], (use - 1) & 1, abort)) {
+                    if (use > 0 && !tc::mbar_wait(&bar_empty[s], (use - 1) & 1, abort, wait_ns)) {
                         ok = false;
                         break;
                     }
+                    if ((int)g == withhold) continue;  // test hook: this stage is never filled
                     tc::mbar_arrive_expect_tx(&bar_full[s], (wide ? 3 : 2) * kTileBytes + kBK);
                     tc::tma_load_3d(sA + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, a0, d);
                     tc::tma_load_3d(sB + s * kBBytes, &map_oh, &bar_full[s], kb * kBK, e0, d);
@@ -272,14 +304,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int2 item = items[t % n_items];
                 const int e0 = item.x + 1 + (item.y & 0xFFFF) * kTileE;
                 const uint32_t idesc = M - e0 > kTile ? idesc_n256 : idesc_n128;
-                if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort)) break;
+                if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort, wait_ns)) break;
                 tc::tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)buf * kAccCols;
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int s = (int)(g % kStages);
                     const uint32_t use = g / kStages;
-                    if (!tc::mbar_wait(&bar_ready[s], use & 1, abort)) {
+                    if (!tc::mbar_wait(&bar_ready[s], use & 1, abort, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -322,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t use = g / kStages;
-                if (!tc::mbar_wait(&bar_full[s], use & 1, abort)) {
+                if (!tc::mbar_wait(&bar_full[s], use & 1, abort, wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -434,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // or without columns, before it releases the buffer
                 if (!waited) {
                     // warp-uniform outcome: the warp-wide reductions below need every lane
-                    if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort))) break;
+                    if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort, wait_ns))) break;
                     tc::tc_fence_after();
                     waited = true;
                 }
@@ -494,6 +526,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (valid && ig_b > best_b) {
                             best_b = ig_b;
                             cb = col;
+                        }
+                        if constexpr (kDump) {
+                            if (valid)
+                                dump_triple(dump, M, d, ao, (int)bo, cc[col].eo,
+                                            {x0, p011, p101, p110, p001, p010, p100, p000},
+                                            {x1, q011, q101, q110, q001, q010, q100, q000});
                         }
                         // role e: the column's maximum over the warp's rows, written by the
                         // lowest lane (lowest new label a) holding it; skipped when no lane
@@ -692,10 +730,12 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
-                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st) {
+                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st,
+                        uint32_t* dump, TcTestHooks hooks) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
-    cudaError_t e = ensure_dynamic_smem((const void*)k3tc_kernel, smem);
+    const void* fn = dump ? (const void*)k3tc_kernel<true> : (const void*)k3tc_kernel<false>;
+    cudaError_t e = ensure_dynamic_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -704,11 +744,16 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
     // the register split inside the kernel needs exactly kRegsLaunch registers per thread
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, k3tc_kernel)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
     if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
-    k3tc_kernel<<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm, pairs,
-                                              keys, err);
+    const unsigned long long wait_ns = hooks.wait_ns ? hooks.wait_ns : tc::kWaitLimitNs;
+    if (dump)
+        k3tc_kernel<true><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s,
+                                                        perm, pairs, keys, err, dump, wait_ns, hooks.withhold_kb);
+    else
+        k3tc_kernel<false><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s,
+                                                         perm, pairs, keys, err, nullptr, wait_ns, hooks.withhold_kb);
     return cudaGetLastError();
 }
 

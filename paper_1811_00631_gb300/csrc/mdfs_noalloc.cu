@@ -31,6 +31,8 @@ int fail(int code, const char* msg) {
 
 // Device address of g_noalloc_scratch, looked up once per device with that
 // device current (host code only sees a host-side stand-in under that name).
+// The address belongs to the device's current context: mdfs_release() drops
+// the cache, which a caller must do after a cudaDeviceReset.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -56,6 +58,7 @@ int scratch_for_current_device(void** out) {
     return MDFS_OK;
 }
 
+// Device memory of the current device, or managed memory.
 bool on_device(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -63,7 +66,13 @@ bool on_device(const void* p) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Carves 256-byte-aligned pieces off the scratch array; `used` is the running total.
@@ -79,6 +88,13 @@ struct Carver {
 };
 
 }  // namespace
+
+namespace mdfs {
+void noalloc_forget_devices() {
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (void*& p : g_scratch_ptr) p = nullptr;
+}
+}  // namespace mdfs
 
 extern "C" int mdfs_max_ig_noalloc(const mdfs_data* data, int k, int divisions, int discretizations, double range,
                                    double pc_xi, uint64_t seed, float* ig, int32_t* tuples, int32_t* best_disc,
@@ -96,7 +112,8 @@ extern "C" int mdfs_max_ig_noalloc(const mdfs_data* data, int k, int divisions, 
         return fail(MDFS_EINVAL, "mdfs_max_ig_noalloc: range must lie in [0, 1] and pc_xi in (0, 1)");
     if (!on_device(data->x) || !on_device(data->y) || !on_device(ig) || (tuples && !on_device(tuples)) ||
         (best_disc && !on_device(best_disc)))
-        return fail(MDFS_EINVAL, "mdfs_max_ig_noalloc: x, y and every output must be device pointers");
+        return fail(MDFS_EINVAL,
+                    "mdfs_max_ig_noalloc: x, y and every output must be device pointers of the current device");
 
     // scratch layout; planes sized for the worst class split (Ws <= round_up(ceil(N/32) + 1, 4))
     const int P = c - 1;

@@ -60,14 +60,16 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t pa
 constexpr uint32_t kSuspendHintNs = 100000;  // 0.1 ms per suspended try, far below kWaitLimitNs
 
 // Bounded wait on the phase with the given parity.  Returns false (and sets
-// *abort) on timeout or when another thread has already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// *abort) after limit_ns without completion or when another thread has
+// already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
         if (mbar_try_wait_suspend(bar, parity, kSuspendHintNs)) return true;
         if (*abort) return false;
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit_ns) {
             *abort = 1;
             return false;
         }

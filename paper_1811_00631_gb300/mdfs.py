@@ -34,7 +34,8 @@ _ERRORS = {
 EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
             "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
-            "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples")
+            "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples",
+            "mdfs_release_stream", "mdfs_testing_counts", "mdfs_testing_k3_wait_fault")
 
 # p-value adjustment methods (MDFS_ADJUST_* of include/mdfs.h)
 P_ADJUST = {"none": 0, "bonferroni": 1, "holm": 2, "hochberg": 3, "BH": 4, "BY": 5}
@@ -102,6 +103,8 @@ def load(path: str = LIB_PATH):
         lib.mdfs_last_error.restype = ctypes.c_char_p
         lib.mdfs_release.argtypes = []
         lib.mdfs_release.restype = ctypes.c_int
+        lib.mdfs_release_stream.argtypes = [P]
+        lib.mdfs_release_stream.restype = ctypes.c_int
         lib.mdfs_abi_version.argtypes = []
         lib.mdfs_abi_version.restype = ctypes.c_int
         lib.mdfs_last_launch_count.argtypes = []
@@ -110,6 +113,12 @@ def load(path: str = LIB_PATH):
         lib.mdfs_profile.restype = ctypes.c_int
         lib.mdfs_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int]
         lib.mdfs_profile_report.restype = ctypes.c_int
+        # test-only entry points (include/mdfs_testing.h)
+        lib.mdfs_testing_counts.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_uint64, P, P]
+        lib.mdfs_testing_counts.restype = ctypes.c_int
+        lib.mdfs_testing_k3_wait_fault.argtypes = [ctypes.c_int, ctypes.c_longlong]
+        lib.mdfs_testing_k3_wait_fault.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -557,5 +566,37 @@ def release() -> None:
     _check(load().mdfs_release())
 
 
+def release_stream(stream) -> None:
+    """Frees the library's workspace of one torch CUDA stream (no call in flight on it)."""
+    _check(load().mdfs_release_stream(ctypes.c_void_p(stream.cuda_stream)))
+
+
 def abi_version() -> int:
     return load().mdfs_abi_version()
+
+
+# ---- test-only entry points (include/mdfs_testing.h) -------------------------
+def testing_counts(x, y, k: int, divisions: int = 1, discretizations: int = 1, range_: float = 0.0, seed: int = 0):
+    """The voxel class counts of the tensor-core k = 2 / k = 3 kernels, as an
+    int32 CUDA tensor [D, C(M, k), c^k] of n0 | n1 << 16 (x, y CUDA tensors)."""
+    import math
+
+    import torch
+    lib = load()
+    if not (_is_cuda(x) and _is_cuda(y)):
+        raise ValueError("testing_counts takes CUDA tensors")
+    data, keep = _data(x, y)
+    c = divisions + 1
+    # -1 marks entries the kernel did not write
+    out = torch.full((discretizations, math.comb(data.M, k), c ** k), -1, dtype=torch.int32, device=x.device)
+    rc = lib.mdfs_testing_counts(ctypes.byref(data), k, divisions, discretizations, float(range_),
+                                 int(seed) & (2**64 - 1), ctypes.c_void_p(out.data_ptr()), _stream_of(x))
+    _check(rc)
+    del keep
+    return out
+
+
+def testing_k3_wait_fault(withhold_kb: int = -1, wait_ns: int = 0) -> None:
+    """Arms (or, with the defaults, disarms) the one-shot bounded-wait hook of
+    the next k = 3 tensor-core scan."""
+    _check(load().mdfs_testing_k3_wait_fault(int(withhold_kb), int(wait_ns)))

@@ -2,9 +2,15 @@
 
 A ``Server`` owns ``n_slots`` worker threads, each bound to its own CUDA
 stream.  The C library keeps one workspace per stream, so a slot's device
-buffers stay resident across the jobs it runs.  Jobs are admitted in arrival
-order as soon as a slot is free and the job's estimated device footprint fits
-the remaining memory budget.  Jobs that arrive while others are on the GPU
+buffers stay resident across the jobs it runs; the library grows a buffer when
+a job needs more and keeps it afterwards.  The scheduler therefore charges
+each slot what it retains, per buffer group: the largest estimate of that
+group over the jobs the slot has run since its workspace was last freed.  Jobs
+are admitted in arrival order as soon as a slot is free and the retained
+bytes of all slots, with the job's groups merged into its slot's, fit the
+memory budget.  When they do not, the slot frees its own workspace if that
+makes the job fit, and otherwise asks idle slots to free theirs
+(``mdfs_release_stream``).  Jobs that arrive while others are on the GPU
 join as slots and memory free up, and their work overlaps on the device
 (different streams).  A job is one ``mdfs_max_ig`` scan (IG^k_max, Eq. 1 of
 arXiv 1811.00631) followed by the chi^2 / extreme-value fit ``mdfs_ig_lim``
@@ -62,45 +68,68 @@ class Result:
         return self.end_t - self.submit_t
 
 
-def job_device_bytes(M: int, N: int, k: int, divisions: int, discretizations: int, x_itemsize: int = 4) -> int:
-    """Upper estimate of the device memory one job holds in its slot's workspace,
-    following the library's allocations: inputs, entropy tables, bit planes,
-    single counts and keys; the one-hot operands of the tensor-core paths
-    (k = 2 with c <= 3, k = 3 with c = 2); and the pair, triple and quadruple
-    tables of k = 3..5, processed in chunks of discretisations that fit a 4 GB
-    table budget (at least one discretisation per chunk)."""
+def job_device_parts(M: int, N: int, k: int, divisions: int, discretizations: int, x_itemsize: int = 4) -> dict:
+    """Upper estimate of the device memory one job holds in its slot's
+    workspace, per group of library buffers: "inputs" (staged x and y, the
+    class order, entropy tables), "planes" (bit planes, single counts, keys),
+    "onehot" (the tensor-core operand of k = 2 with c <= 3 and k = 3 with
+    c = 2), "k3tc" (the relabelled operand and the pair records of the k = 3
+    tensor path), "pairs" (pair tables of the generic k = 3 path) and "tables"
+    (pair, triple and quadruple tables of k = 4, 5).  Tables are processed in
+    chunks of discretisations that fit a 4 GB budget (at least one
+    discretisation per chunk)."""
     c = divisions + 1
     P = c - 1
     D = discretizations
     words = (N + 31) // 32 + 5
     kp = ((N + 127) // 128 + 1) * 128
-    b = M * N * x_itemsize + N * 5 + 3 * (N + 1) * 8
-    b += D * M * P * words * 4 + D * M * (P * 8 + 8) + M * 8
 
     def chunked(per_disc: int) -> int:
         nd = max(1, min(D, (4 << 30) // max(per_disc, 1)))
         return nd * per_disc
 
+    parts = {"inputs": M * N * x_itemsize + N * 5 + 3 * (N + 1) * 8 + (1 << 20),
+             "planes": D * M * P * words * 4 + D * M * (P * 8 + 8) + M * 8}
     if k == 2 and c <= 3:
-        b += D * M * P * kp
+        parts["onehot"] = D * M * P * kp
     elif k == 3 and c == 2:
-        b += 2 * D * M * kp + D * M * 16 + chunked(M * M * 8)
+        parts["onehot"] = D * M * kp
+        parts["k3tc"] = D * M * kp + D * M * 16 + chunked(M * M * 8)
     elif k == 3:
-        b += chunked(M * M * (8 + P * P * 8))
+        parts["pairs"] = chunked(M * M * (8 + P * P * 8))
     elif k in (4, 5):
         per_disc = M * M * 16 + math.comb(M, 3) * 12
         if k == 5:
             per_disc += math.comb(M, 4) * 12 + M * 8
-        b += chunked(per_disc) + (1 << 21)
-    return int(b * 1.15) + (1 << 20)
+        parts["tables"] = chunked(per_disc) + (1 << 21)
+    return {g: int(b * 1.15) for g, b in parts.items()}
+
+
+def job_device_bytes(M: int, N: int, k: int, divisions: int, discretizations: int, x_itemsize: int = 4) -> int:
+    """Total of job_device_parts: the device bytes one job needs in an empty slot."""
+    return sum(job_device_parts(M, N, k, divisions, discretizations, x_itemsize).values())
+
+
+def _parts(need) -> dict:
+    """An estimate as buffer groups (a plain byte count is one group)."""
+    return dict(need) if isinstance(need, dict) else {"all": int(need)}
+
+
+def _merged(held: dict, need: dict) -> dict:
+    return {g: max(held.get(g, 0), need.get(g, 0)) for g in set(held) | set(need)}
 
 
 class Server:
     """Admits jobs into ``n_slots`` concurrent slots under a device-memory budget."""
 
     def __init__(self, n_slots: int = 4, memory_budget: Optional[int] = None, device: int = 0,
-                 executor: Optional[Callable] = None, estimate: Callable = job_device_bytes,
-                 log_path: Optional[str] = None):
+                 executor: Optional[Callable] = None, estimate: Callable = job_device_parts,
+                 log_path: Optional[str] = None, release_workspace: Optional[Callable] = None):
+        """estimate(M, N, k, divisions, discretizations, itemsize) gives a job's
+        device bytes, as a dict of buffer groups or one number; release_workspace(slot)
+        frees a slot's library workspace (default: mdfs_release_stream on the
+        slot's stream; with a custom executor and no callback it only resets the
+        bookkeeping)."""
         self.n_slots = n_slots
         self._log_path = log_path  # JSON line per finished, failed or expired job
         self._log_lock = threading.Lock()
@@ -111,9 +140,14 @@ class Server:
             memory_budget = self._default_budget(device) if executor is None else 1 << 40
         self.budget = int(memory_budget)
         self._executor = executor
+        self._release_cb = release_workspace
+        self._streams = [None] * n_slots
         self._queue = collections.deque()
         self._cv = threading.Condition()
-        self._in_use = 0
+        self._held = [dict() for _ in range(n_slots)]  # bytes retained per buffer group, per slot
+        self._busy = [False] * n_slots
+        self._shrink = False  # the head job waits for idle slots to free their workspaces
+        self.workspace_releases = 0
         self._running = 0
         self._closed = False
         self.expired = 0
@@ -135,9 +169,9 @@ class Server:
         fut: Future = Future()
         M, N = int(job.x.shape[0]), int(job.x.shape[1])
         itemsize = 1 if str(getattr(job.x, "dtype", "")).endswith("int8") else 4
-        need = self.estimate(M, N, job.k, job.divisions, job.discretizations, itemsize)
-        if need > self.budget:
-            fut.set_exception(MemoryError(f"job needs ~{need} device bytes, budget is {self.budget}"))
+        need = _parts(self.estimate(M, N, job.k, job.divisions, job.discretizations, itemsize))
+        if sum(need.values()) > self.budget:
+            fut.set_exception(MemoryError(f"job needs ~{sum(need.values())} device bytes, budget is {self.budget}"))
             return fut
         with self._cv:
             if self._closed:
@@ -193,28 +227,64 @@ class Server:
                  if getattr(j, "deadline_s", None) is not None]
         return max(1e-3, min(waits)) if waits else None
 
-    def _next(self):
-        """Head-of-line admission: the oldest job runs as soon as it fits."""
+    @property
+    def in_use(self) -> int:
+        """Device bytes the slots retain (estimate), running or idle."""
         with self._cv:
-            while True:
-                self._purge_expired()
-                if self._queue:
-                    job, fut, need, t_sub = self._queue[0]
-                    if self._in_use + need <= self.budget:
-                        self._queue.popleft()
-                        self._n_deadline -= getattr(job, "deadline_s", None) is not None
-                        self._in_use += need
-                        self._running += 1
-                        self.peak_in_use = max(self.peak_in_use, self._in_use)
-                        self.peak_running = max(self.peak_running, self._running)
-                        return job, fut, need, t_sub
-                elif self._closed:
-                    return None
-                self._cv.wait(self._deadline_wait())
+            return self._held_total()
 
-    def _release(self, need: int):
+    def _held_total(self, skip: int = -1) -> int:
+        return sum(sum(h.values()) for s, h in enumerate(self._held) if s != skip)
+
+    def _next(self, slot: int):
+        """Head-of-line admission: the oldest job runs as soon as it fits."""
+        while True:
+            with self._cv:
+                while True:
+                    self._purge_expired()
+                    mine = sum(self._held[slot].values())
+                    if self._shrink and mine > 0:
+                        break  # idle: free this slot's workspace for the waiting head job
+                    if self._queue:
+                        job, fut, need, t_sub = self._queue[0]
+                        others = self._held_total(skip=slot)
+                        merged = _merged(self._held[slot], need)
+                        if others + sum(merged.values()) <= self.budget:
+                            self._queue.popleft()
+                            self._n_deadline -= getattr(job, "deadline_s", None) is not None
+                            self._held[slot] = merged
+                            self._busy[slot] = True
+                            self._shrink = False
+                            self._running += 1
+                            self.peak_in_use = max(self.peak_in_use, self._held_total())
+                            self.peak_running = max(self.peak_running, self._running)
+                            return job, fut, need, t_sub
+                        if mine > 0 and others + sum(need.values()) <= self.budget:
+                            break  # fits once this slot's retained buffers are freed
+                        if any(not self._busy[s] and self._held[s] for s in range(self.n_slots) if s != slot):
+                            self._shrink = True
+                            self._cv.notify_all()
+                    elif self._closed:
+                        return None
+                    self._cv.wait(self._deadline_wait())
+            # outside the lock: the slot's workspace is freed before its bytes are
+            # returned to the budget
+            self._free_workspace(slot)
+            with self._cv:
+                self._held[slot] = {}
+                self.workspace_releases += 1
+                self._cv.notify_all()
+
+    def _free_workspace(self, slot: int):
+        if self._release_cb is not None:
+            self._release_cb(slot)
+        elif self._executor is None and self._streams[slot] is not None:
+            from . import mdfs
+            mdfs.release_stream(self._streams[slot])
+
+    def _release(self, slot: int):
         with self._cv:
-            self._in_use -= need
+            self._busy[slot] = False
             self._running -= 1
             self._cv.notify_all()
 
@@ -224,8 +294,9 @@ class Server:
             import torch
             torch.cuda.set_device(self.device)
             ctx = torch.cuda.Stream(self.device)
+            self._streams[slot] = ctx
         while True:
-            item = self._next()
+            item = self._next(slot)
             if item is None:
                 return
             job, fut, need, t_sub = item
@@ -242,7 +313,7 @@ class Server:
                 fut.set_exception(e)
                 self._log(job, f"error: {type(e).__name__}: {e}", t_sub, t0, time.perf_counter(), slot)
             finally:
-                self._release(need)
+                self._release(slot)
 
     def _log(self, job, status: str, t_sub: float, t_start, t_end: float, slot):
         """Appends one JSON line per job to log_path: shape, work, queue wait,

@@ -114,6 +114,16 @@ CASES = [
      lambda lib: lib.mdfs_max_ig_noalloc(_data(), 3, 1, 1, 0.5, 0.25, 1, P, P, P, None), "k must be 1 or 2"),
     ("noalloc: divisions = 4",
      lambda lib: lib.mdfs_max_ig_noalloc(_data(), 2, 4, 1, 0.5, 0.25, 1, P, P, P, None), "divisions"),
+    ("testing counts: k = 1",
+     lambda lib: lib.mdfs_testing_counts(_data(), 1, 1, 1, 0.5, 1, P, None), "k = 1"),
+    ("testing counts: divisions = 4",
+     lambda lib: lib.mdfs_testing_counts(_data(), 2, 4, 1, 0.5, 1, P, None), "divisions"),
+    ("testing counts: counts NULL",
+     lambda lib: lib.mdfs_testing_counts(_data(), 2, 1, 1, 0.5, 1, None, None), "counts is NULL"),
+    ("testing wait fault: stage below -1", lambda lib: lib.mdfs_testing_k3_wait_fault(-2, 0), "withhold_kb"),
+    ("testing wait fault: limit above 10 s",
+     lambda lib: lib.mdfs_testing_k3_wait_fault(0, 20_000_000_000), "wait_ns"),
+    ("testing wait fault: negative limit", lambda lib: lib.mdfs_testing_k3_wait_fault(0, -1), "wait_ns"),
 ]
 
 

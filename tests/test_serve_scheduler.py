@@ -200,3 +200,52 @@ def test_unwritable_record_does_not_stop_the_slot(tmp_path):
     assert [f.result(timeout=5).ig[0] for f in futs] == [0, 1, 2]
     srv.close()
     assert srv.log_errors == 3
+
+
+def test_retained_workspaces_are_charged_and_freed_when_needed():
+    """The library keeps a slot's buffers after its job.  A slot that ran a job
+    using one group of buffers and then takes a job using another holds both;
+    the scheduler charges what every slot retains, frees a slot's workspace
+    when the merged bytes would pass the budget, and has idle slots free
+    theirs when the head job does not fit beside them."""
+    def est(M, N, k, div, D, itemsize):
+        return {f"group{k}": M}
+
+    def executor(job, slot):
+        time.sleep(job.dur)
+        return (np.array([job.tag]), None, None, None, None, None)
+
+    def job(need, group, tag):
+        j = FakeJob(need=need, dur=0.02, tag=tag)
+        j.k = group
+        return j
+
+    # merged groups that fit: both stay resident, nothing is freed
+    released = []
+    srv = serve.Server(n_slots=1, memory_budget=100, executor=executor, estimate=est,
+                       release_workspace=released.append)
+    for f in [srv.submit(job(30, 1, 0)), srv.submit(job(30, 2, 1))]:
+        f.result(timeout=5)
+    assert srv.in_use == 60 and released == []
+    # merged groups past the budget: the slot frees its workspace first
+    for f in [srv.submit(job(50, 3, 2))]:
+        f.result(timeout=5)
+    assert released == [0] and srv.in_use == 50 and srv.peak_in_use <= 100
+    srv.close()
+
+    # two slots: the idle slot that retains 60 bytes frees them for a 50-byte job
+    for _ in range(3):
+        released = []
+        srv = serve.Server(n_slots=2, memory_budget=100, executor=executor, estimate=est,
+                           release_workspace=released.append)
+        srv.submit(job(60, 1, 0)).result(timeout=5)
+        assert srv.in_use == 60
+        srv.submit(job(50, 2, 1)).result(timeout=5)
+        srv.close()
+        assert len(released) == 1 and srv.in_use == 50 and srv.peak_in_use <= 100
+
+
+def test_estimate_parts_add_up():
+    parts = serve.job_device_parts(500, 2000, 3, 1, 30)
+    assert {"inputs", "planes", "onehot", "k3tc"} <= set(parts)
+    assert sum(parts.values()) == serve.job_device_bytes(500, 2000, 3, 1, 30)
