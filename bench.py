@@ -52,11 +52,11 @@ def _bf16_burst_peak():
         return 1900.0, "fallback"
 
 
-def _use_small_case():
-    """A reduced case of the same kernels for profiler captures (M = 500, 2 discretisations)."""
+def _use_small_case(n_disc: int = 2):
+    """A reduced case of the same kernels for profiler captures (M = 500, n_disc discretisations)."""
     global M_VAR, DISC, WORKLOAD
-    M_VAR, DISC = 500, 2
-    WORKLOAD = "mdfs_scan_parity_N2000_M500_k2+k3_D2_c2 (profiling case)"
+    M_VAR, DISC = 500, n_disc
+    WORKLOAD = f"mdfs_scan_parity_N2000_M500_k2+k3_D{n_disc}_c2 (profiling case)"
 
 
 def _config(extra=None):
@@ -517,7 +517,8 @@ def main():
     ap.add_argument("--k3-traffic", type=float, default=93863424.0,
                     help="DRAM bytes (read + write) per full-size k=3 launch from an ncu capture of the "
                          "current kernel (profiles/launches_mdfs_scan_parity_N2000_M500_k2k3_D30.md)")
-    ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=2)")
+    ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=--small-disc)")
+    ap.add_argument("--small-disc", type=int, default=2, help="discretisations of the --small case")
     ap.add_argument("--serving-jobs", type=int, default=512, help="jobs of the serving-mix run (0: skip)")
     ap.add_argument("--k4", type=int, default=1, help="time one k = 4 scan of the bench data (0: skip)")
     ap.add_argument("--k5-m", type=int, default=200,
@@ -532,7 +533,7 @@ def main():
     ap.add_argument("--batch-m", type=int, default=20000)
     args = ap.parse_args()
     if args.small:
-        _use_small_case()
+        _use_small_case(args.small_disc)
         args.serving_jobs = 0
         args.select_reps = 0
         args.k4 = 0

@@ -531,8 +531,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             const int cnt = share(ws->n_items2, &lo);
             MDFS_LAUNCH("k3", st, launch_k3tc(map, (const uint8_t*)ws->onehot2.p, tg, M, d0, nn,
                                               (const int2*)ws->items2.p + lo, cnt, tab, fbits, (const int*)ws->cnt1s.p,
-                                              lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, st, dump,
-                                              hooks));
+                                              lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, b0, b1, st,
+                                              dump, hooks));
         }
         *check_err = true;
     } else if (k == 3) {
@@ -1336,6 +1336,13 @@ int mdfs_testing_counts(const mdfs_data* data, int k, int divisions, int discret
     MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     if (ws->host_stats[8]) return kernel_flag_error(ws->host_stats[8]);
+    return MDFS_OK;
+}
+
+int mdfs_testing_k3_exact(void) {
+    g_err.clear();
+    std::lock_guard<std::mutex> lock(g_hooks_mu);
+    g_hooks.exact = true;
     return MDFS_OK;
 }
 

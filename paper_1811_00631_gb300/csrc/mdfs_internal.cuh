@@ -186,18 +186,22 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 // Test hooks of the triple kernel (defaults: off).  wait_ns: limit of every
 // bounded mbarrier wait (0 = the library's 1 s); withhold_kb >= 0: the TMA
 // producer of CTA 0 never fills the stage of that K block of its running
-// count, so the consumers' wait runs out and the call reports MDFS_ETIMEOUT.
+// count, so the consumers' wait runs out and the call reports MDFS_ETIMEOUT;
+// exact: no triple is skipped by the SH3 lower bound.
 struct TcTestHooks {
     unsigned long long wait_ns = 0;
     int withhold_kb = -1;
+    bool exact = false;  // evaluate every triple exactly (no SH3 bound)
 };
 // dump != NULL (test hook): also writes the 8-voxel class counts of every
 // triple, [D][C(M,3)][8] uint32 n0 | n1 << 16, lexicographic triple rank of the
 // original variables, voxel 4 v_lo + 2 v_mid + v_hi.
+// b0, b1: the pseudocounts of the two decision classes (they enter a lower
+// bound of SH3 that lets the epilogue skip triples that cannot change a key).
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
-                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st,
-                        uint32_t* dump = nullptr, TcTestHooks hooks = TcTestHooks());
+                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, double b0, double b1,
+                        cudaStream_t st, uint32_t* dump = nullptr, TcTestHooks hooks = TcTestHooks());
 // Relabelling of the k = 3 tensor path, per discretisation: new labels in
 // ascending order of the bin-1 count (ties by index) for M <= 8192, else the
 // identity.  perm [D][M] new -> original, rank [D][M] original -> new,

@@ -47,6 +47,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <climits>
+#include <cmath>
 
 #include "mdfs_device.cuh"
 #include "mdfs_internal.cuh"
@@ -109,11 +110,12 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
     return ((unsigned long long)hmax << 32) | lmax;
 }
 
-// table entry at byte offset n4 = 4 n (counts are carried multiplied by 4) of
-// the table starting at shared-window address `base`
-__device__ __forceinline__ int tab4(uint32_t base, int n4) {
+// table entry at shared-window byte address `addr`.  Not volatile: the tables
+// are read-only once built, so the compiler may reorder and overlap the loads
+// of several voxels and columns.
+__device__ __forceinline__ int lds(uint32_t addr) {
     int v;
-    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(base + (uint32_t)n4));
+    asm("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
 
@@ -121,16 +123,47 @@ __device__ __forceinline__ int tab4(uint32_t base, int n4) {
 // guard windows of the table layout are sized for
 __device__ __forceinline__ bool counts_ok(int any_or) { return (any_or & (int)0xFFFFC003u) == 0; }
 
-// Per-column constants of an item, counts times 4 (n_x: class count of bin 1
-// of x, n_xy: class count of the voxel (1, 1) of the pair (x, y)).
+// Per-column constants of an item (n_x: class count of bin 1 of x, n_xy: class
+// count of the voxel (1, 1) of the pair (x, y)).
 struct __align__(16) ColCtx {
-    int n0, n1;    // n_be per class
-    int u0, u1;    // n_e - n_be per class
-    int sh;        // SH(b, e), int32 fixed point
-    int thr;       // role-e pre-filter: IG(e | a, b) below thr cannot raise e's key
-    int eo;        // original index of e
-    int pad;
+    float2 nu0, nu1;  // per class: (n_be, n_e - n_be) + beta of the class (smoothed counts)
+    float sh_c;       // SH(b, e) in LB units (K3Prune)
+    float thr_c;      // role-e key threshold in LB units (see key_threshold)
+    int sh;           // SH(b, e), int32 fixed point
+    int eo;           // original index of e
 };
+
+// Bound that lets the epilogue skip the exact SH3 of most triples.  Each
+// voxel's term of SH is E(m0, m1) = f(m0 + m1) - f(m0) - f(m1) with the
+// smoothed class counts m_d = n_d + beta_d; E = (m0 + m1) H(m0 / (m0 + m1)) with
+// H the binary entropy in nats, and H(p) >= 4 ln 2 p (1 - p) gives
+//     SH3 >= 4 ln 2 sum_v m0_v m1_v / (m0_v + m1_v) = 4 ln 2 LB.
+// IG(x | S) = SH(S) - SH3 can raise x's key only if SH3 <= SH(S) - thr_x, so a
+// triple with LB above (SH(S) - thr_x) / (4 ln 2 2^s) for all three roles
+// cannot change any result and its 24 table lookups are skipped.  SH values
+// are compared as their int32 fixed-point values, which equal the true values
+// when (N + 8 (beta0 + beta1)) ln 2 2^s < 2^31 (on = 0 otherwise).  Float
+// rounding of LB (relative < 1e-5) and of the thresholds (absolute < 1e-3)
+// lies far inside the margins kBoundRel |hi| + kBoundAbs.
+struct K3Prune {
+    int on;
+    float beta0, beta1;  // pseudocounts of the two decision classes
+    float fx_to_count;   // 1 / (4 ln 2 2^s): int32 fixed point -> LB units
+    float count_to_fx;   // 4 ln 2 2^s
+};
+constexpr float kBoundRel = 1.0f / 4096.0f, kBoundAbs = 0.05f;
+
+// packed FP32 pairs (two lanes per instruction)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Two fractions per lane pair: (pa / sa) + (pb / sb) as num / den in each lane (sa, sb > 0).
+__device__ __forceinline__ void frac_add2(float2 pa, float2 sa, float2 pb, float2 sb, float2& num, float2& den) {
+    num = fma2(pa, sb, mul2(pb, sa));
+    den = mul2(sa, sb);
+}
 
 // Lower bound, in int32 fixed point with fbits fraction bits, of the IG values
 // that can still raise a key whose current value is `key` (0: no value yet).
@@ -193,8 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k3tc_kernel(const __grid_constant__ CUtensorMap map_oh, const uint8_t* __restrict__ oh, TcGeom tg, int M, int d0,
                 int nd, const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
                 const int* __restrict__ cnt1s, const int* __restrict__ perm, const PairC* __restrict__ pairs,
-                unsigned long long* __restrict__ keys, int* __restrict__ err, uint32_t* __restrict__ dump,
-                unsigned long long wait_ns, int withhold_kb) {
+                unsigned long long* __restrict__ keys, int* __restrict__ err, K3Prune prune,
+                uint32_t* __restrict__ dump, unsigned long long wait_ns, int withhold_kb) {
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
@@ -207,6 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int* sT1 = reinterpret_cast<int*>(dsmem_raw + kT1Off);
     int* sTB = reinterpret_cast<int*>(dsmem_raw + kTBOff);
     const uint32_t uT0 = tc::smem_u32(sT0), uT1 = tc::smem_u32(sT1), uTB = tc::smem_u32(sTB);
+    const uint32_t tb_off = uTB - uT0 - uT1;  // TB address of a voxel = T0 address + T1 address + tb_off
     uint8_t* sA = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
     uint8_t* sB = dsmem_raw + kTabEnd + ((1024 - (tc::smem_u32(dsmem_raw + kTabEnd) & 1023)) & 1023);
     uint8_t* sOHb = sB + kStages * kBBytes;
@@ -423,6 +457,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bad = true;
                 pab0 = pab1 = r2_0 = r2_1 = r3_0 = r3_1 = kab0 = kab1 = 0;
             }
+            // The constants carry the table base addresses (once, or twice where a
+            // voxel count subtracts another biased constant), so each voxel's byte
+            // address in T0 / T1 is one add or subtract away, and its address in TB
+            // is the sum of the two plus tb_off.
+            const uint32_t A110 = uT0 + pab0, A010 = 2 * uT0 + r2_0, A100 = 2 * uT0 + r3_0, A000 = 2 * uT0 + kab0;
+            const uint32_t B110 = uT1 + pab1, B010 = 2 * uT1 + r2_1, B100 = 2 * uT1 + r3_1, B000 = 2 * uT1 + kab1;
+            // The same row constants as smoothed class counts for the SH3 bound,
+            // paired per class as the voxel pairs below need them: (n_ab + beta,
+            // n_a - n_ab + beta) and (n_b - n_ab + 2 beta, N - n_a - n_b + n_ab + 2 beta).
+            const float fb0 = prune.beta0, fb1 = prune.beta1;
+            const float2 beta0 = make_float2(fb0, fb0), beta1 = make_float2(fb1, fb1);
+            const float2 rpr3_0 = make_float2(fmaf((float)pab0, 0.25f, fb0), fmaf((float)r3_0, 0.25f, fb0));
+            const float2 rpr3_1 = make_float2(fmaf((float)pab1, 0.25f, fb1), fmaf((float)r3_1, 0.25f, fb1));
+            const float2 r2k_0 = make_float2(fmaf((float)r2_0, 0.25f, 2.0f * fb0), fmaf((float)kab0, 0.25f, 2.0f * fb0));
+            const float2 r2k_1 = make_float2(fmaf((float)r2_1, 0.25f, 2.0f * fb1), fmaf((float)kab1, 0.25f, 2.0f * fb1));
+            // role thresholds in LB units: IG(e | a,b) can raise e's key only if
+            // SH3 <= SH(a,b) - thr_e, IG(a | b,e) only if SH3 <= SH(b,e) - thr_a,
+            // IG(b | a,e) only if SH3 <= SH(a,e) - thr_b
+            const float shab_c = (float)shab * prune.fx_to_count;
+            const float thra_c = arow ? (float)key_threshold(__ldcg(keys + ao), fbits) * prune.fx_to_count : 0.0f;
+            const float thrb_c = (float)key_threshold(__ldcg(keys + bo), fbits) * prune.fx_to_count;
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
             // running maxima of the roles a (over e) and b (over this thread's (a, e));
             // columns are visited in ascending e, so ">" keeps the first maximum
@@ -439,22 +494,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // column constants of this chunk
                     __syncwarp();
                     const int e = ecol0 + lane;
-                    ColCtx x{0, 0, 0, 0, 0, INT_MAX, 0, 0};
+                    int n0 = 0, n1 = 0, u0 = 0, u1 = 0, thr = INT_MAX;
+                    ColCtx x{};
                     if (lane < ncols) {
                         const PairC p = pd[(size_t)b * M + e];
-                        x.n0 = (int)(p.cnt & 0xFFFFu);
-                        x.n1 = (int)(p.cnt >> 16);
-                        x.u0 = 4 * c1[2 * e] - x.n0;
-                        x.u1 = 4 * c1[2 * e + 1] - x.n1;
+                        n0 = (int)(p.cnt & 0xFFFFu);
+                        n1 = (int)(p.cnt >> 16);
+                        u0 = 4 * c1[2 * e] - n0;
+                        u1 = 4 * c1[2 * e + 1] - n1;
                         x.sh = p.sh;
                         x.eo = pm[e];
                         // keys only grow during the scan: a stale value is a valid lower bound
-                        x.thr = key_threshold(__ldcg(keys + x.eo), fbits);
-                        if (!counts_ok(x.n0 | x.n1 | x.u0 | x.u1)) {
+                        thr = key_threshold(__ldcg(keys + x.eo), fbits);
+                        if (!counts_ok(n0 | n1 | u0 | u1)) {
                             bad = true;
-                            x.n0 = x.n1 = x.u0 = x.u1 = 0;
+                            n0 = n1 = u0 = u1 = 0;
                         }
                     }
+                    x.nu0 = make_float2(fmaf((float)n0, 0.25f, fb0), fmaf((float)u0, 0.25f, fb0));
+                    x.nu1 = make_float2(fmaf((float)n1, 0.25f, fb1), fmaf((float)u1, 0.25f, fb1));
+                    x.sh_c = (float)x.sh * prune.fx_to_count;
+                    x.thr_c = (float)thr * prune.fx_to_count;
                     cc[lane] = x;
                     __syncwarp();
                     // pair (a, e) records of the first group, fetched before the accumulator is read
@@ -487,38 +547,101 @@ __global__ void __launch_bounds__(kThreads, 1)
                         pnext[j] = (arow && cn < ncols) ? prow[(size_t)cn * M] : PairC{0u, 0};
                     }
                     tc::tmem_ld_wait();
+                    // Which (a, e) of the group need the exact SH3: those where the
+                    // lower bound of SH3 does not already rule out all three roles.
+                    unsigned need = 0;
 #pragma unroll
                     for (int j = 0; j < kGroup; ++j) {
+                        badbits |= pcur[j].cnt;
+                        const bool valid = arow && c0 + j < ncols;
+                        if (kDump || !prune.on) {
+                            need |= valid ? 1u << j : 0u;
+                            continue;
+                        }
+                        const float4 nu = *reinterpret_cast<const float4*>(&cc[c0 + j].nu0);
+                        const float2 sht = *reinterpret_cast<const float2*>(&cc[c0 + j].sh_c);
+                        const float2 nu0 = make_float2(nu.x, nu.y), nu1 = make_float2(nu.z, nu.w);
+                        // class counts of the voxel (1,1,1): X = n0 + 4096 n1, exact in FP32
+                        const float X = __uint_as_float(r[j]);
+                        const float x1 = floorf(X * (1.0f / 4096.0f)), x0 = fmaf(x1, -4096.0f, X);
+                        // pair (a, e) class counts: 4 n in 16-bit fields, read as floats
+                        const float q0 = fmaf(__uint_as_float((pcur[j].cnt & 0xFFFFu) | 0x4B000000u), 0.25f,
+                                              -2097152.0f);
+                        const float q1 = fmaf(__uint_as_float((pcur[j].cnt >> 16) | 0x4B000000u), 0.25f,
+                                              -2097152.0f);
+                        // per class, (x, t) with t = n_ae - x, and the smoothed class counts
+                        // of four voxel pairs (v_a v_b v_e):
+                        //   va = (011, 001) = (n_be, n_e - n_be) - (x, t)
+                        //   vb = (110, 100) = (n_ab, n_a - n_ab) - (x, t)
+                        //   vc = (111, 101) = (x, t) + beta
+                        //   vd = (010, 000) = (n_b - n_ab, N - n_a - n_b + n_ab) - (n_be, n_e - n_be) + (x, t)
+                        // (each constant carries its beta, twice where one is subtracted)
+                        const float2 xt0 = make_float2(x0, q0 - x0), xt1 = make_float2(x1, q1 - x1);
+                        const float2 va0 = sub2(nu0, xt0), va1 = sub2(nu1, xt1);
+                        const float2 vb0 = sub2(rpr3_0, xt0), vb1 = sub2(rpr3_1, xt1);
+                        const float2 vc0 = add2(xt0, beta0), vc1 = add2(xt1, beta1);
+                        const float2 vd0 = add2(sub2(r2k_0, nu0), xt0), vd1 = add2(sub2(r2k_1, nu1), xt1);
+                        // sum over the voxels of m w / (m + w) (m, w the two classes' smoothed
+                        // counts), accumulated as one fraction per lane of the pairs
+                        float2 nab, dab, ncd, dcd, num2, den2;
+                        frac_add2(mul2(va0, va1), add2(va0, va1), mul2(vb0, vb1), add2(vb0, vb1), nab, dab);
+                        frac_add2(mul2(vc0, vc1), add2(vc0, vc1), mul2(vd0, vd1), add2(vd0, vd1), ncd, dcd);
+                        frac_add2(nab, dab, ncd, dcd, num2, den2);
+                        const float num = fmaf(num2.x, den2.y, num2.y * den2.x), den = den2.x * den2.y;
+                        // largest SH3 (LB units) that still lets one role reach its bound
+                        const float sh_ae = (float)pcur[j].sh * prune.fx_to_count;
+                        const float hi = fmaxf(fmaxf(sht.x - thra_c, sh_ae - thrb_c), shab_c - sht.y);
+                        const float lim = fmaf(fabsf(hi), kBoundRel, hi + kBoundAbs);
+                        need |= (valid && num <= lim * den) ? 1u << j : 0u;
+                    }
+                    if (!__any_sync(0xffffffffu, need != 0)) continue;
+#pragma unroll
+                    for (int j = 0; j < kGroup; ++j) {
+                        if (!__any_sync(0xffffffffu, (need >> j) & 1u)) continue;
                         const int col = c0 + j;
-                        // straight-line for every lane and column: rows and columns outside
-                        // the item compute in-window garbage that is masked out below
                         const bool valid = arow && col < ncols;
                         const ColCtx cx = cc[col];
-                        badbits |= pcur[j].cnt;
-                        const int pae0 = (int)(pcur[j].cnt & 0x3FFCu), pae1 = (int)((pcur[j].cnt >> 16) & 0x3FFCu);
+                        // exact column counts (times 4), recovered from the smoothed floats
+                        const uint32_t cn0 = 4u * (uint32_t)__float2int_rn(cx.nu0.x - fb0);
+                        const uint32_t cu0 = 4u * (uint32_t)__float2int_rn(cx.nu0.y - fb0);
+                        const uint32_t cn1 = 4u * (uint32_t)__float2int_rn(cx.nu1.x - fb1);
+                        const uint32_t cu1 = 4u * (uint32_t)__float2int_rn(cx.nu1.y - fb1);
+                        const uint32_t n0b = uT0 + cn0, n1b = uT1 + cn1, u0b = 2 * uT0 + cu0, u1b = 2 * uT1 + cu1;
+                        const uint32_t pae0 = pcur[j].cnt & 0x3FFCu, pae1 = (pcur[j].cnt >> 16) & 0x3FFCu;
                         // X = n0 + 4096 n1, exact in FP32
                         const uint32_t xv = (uint32_t)__float2int_rn(__uint_as_float(r[j]));
-                        // voxel counts (times 4) by inclusion-exclusion, voxel (v_a v_b v_e)
-                        const int x0 = (int)((xv << 2) & 0x3FFCu);
-                        const int p011 = cx.n0 - x0, p101 = pae0 - x0, p110 = pab0 - x0;
-                        const int p001 = cx.u0 - pae0 + x0, p010 = r2_0 - cx.n0 + x0, p100 = r3_0 - pae0 + x0;
-                        const int p000 = kab0 - cx.u0 + pae0 - x0;
-                        const int x1 = (int)((xv >> 10) & 0x3FFCu);
-                        const int q011 = cx.n1 - x1, q101 = pae1 - x1, q110 = pab1 - x1;
-                        const int q001 = cx.u1 - pae1 + x1, q010 = r2_1 - cx.n1 + x1, q100 = r3_1 - pae1 + x1;
-                        const int q000 = kab1 - cx.u1 + pae1 - x1;
-                        const int sh3 = tab4(uTB, x0 + x1) + tab4(uTB, p011 + q011) + tab4(uTB, p101 + q101) +
-                                        tab4(uTB, p110 + q110) + tab4(uTB, p001 + q001) + tab4(uTB, p010 + q010) +
-                                        tab4(uTB, p100 + q100) + tab4(uTB, p000 + q000) -
-                                        (tab4(uT0, x0) + tab4(uT0, p011) + tab4(uT0, p101) + tab4(uT0, p110) +
-                                         tab4(uT0, p001) + tab4(uT0, p010) + tab4(uT0, p100) + tab4(uT0, p000)) -
-                                        (tab4(uT1, x1) + tab4(uT1, q011) + tab4(uT1, q101) + tab4(uT1, q110) +
-                                         tab4(uT1, q001) + tab4(uT1, q010) + tab4(uT1, q100) + tab4(uT1, q000));
+                        const uint32_t x0 = (xv << 2) & 0x3FFCu, x1 = (xv >> 10) & 0x3FFCu;
+                        // byte addresses of the voxels (v_a v_b v_e) by inclusion-exclusion
+                        const uint32_t a111 = uT0 + x0, a011 = n0b - x0, a110 = A110 - x0, a101 = uT0 + pae0 - x0;
+                        const uint32_t a001 = u0b - a101, a010 = A010 - n0b + x0, a100 = A100 - a101;
+                        const uint32_t a000 = A000 - u0b + a101;
+                        const uint32_t b111 = uT1 + x1, b011 = n1b - x1, b110 = B110 - x1, b101 = uT1 + pae1 - x1;
+                        const uint32_t b001 = u1b - b101, b010 = B010 - n1b + x1, b100 = B100 - b101;
+                        const uint32_t b000 = B000 - u1b + b101;
+                        // straight-line for every lane: rows and columns outside the item
+                        // compute in-window garbage that is masked out below
+                        const int sh3 = (lds(a111 + b111 + tb_off) + lds(a011 + b011 + tb_off) +
+                                         lds(a101 + b101 + tb_off) + lds(a110 + b110 + tb_off) +
+                                         lds(a001 + b001 + tb_off) + lds(a010 + b010 + tb_off) +
+                                         lds(a100 + b100 + tb_off) + lds(a000 + b000 + tb_off)) -
+                                        (lds(a111) + lds(a011) + lds(a101) + lds(a110) + lds(a001) + lds(a010) +
+                                         lds(a100) + lds(a000)) -
+                                        (lds(b111) + lds(b011) + lds(b101) + lds(b110) + lds(b001) + lds(b010) +
+                                         lds(b100) + lds(b000));
+                        if constexpr (kDump) {
+                            if (valid)
+                                dump_triple(dump, M, d, ao, (int)bo, cx.eo,
+                                            {(int)(a111 - uT0), (int)(a011 - uT0), (int)(a101 - uT0),
+                                             (int)(a110 - uT0), (int)(a001 - uT0), (int)(a010 - uT0),
+                                             (int)(a100 - uT0), (int)(a000 - uT0)},
+                                            {(int)(b111 - uT1), (int)(b011 - uT1), (int)(b101 - uT1),
+                                             (int)(b110 - uT1), (int)(b001 - uT1), (int)(b010 - uT1),
+                                             (int)(b100 - uT1), (int)(b000 - uT1)});
+                        }
                         // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around int32 differences
                         const int ig_a = cx.sh - sh3;
                         const int ig_b = pcur[j].sh - sh3;
                         const int ig_e = valid ? shab - sh3 : INT_MIN;
-                        const bool cand = valid && ig_e >= cx.thr;
                         if (valid && ig_a > best_a) {
                             best_a = ig_a;
                             ca = col;
@@ -527,20 +650,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                             best_b = ig_b;
                             cb = col;
                         }
-                        if constexpr (kDump) {
-                            if (valid)
-                                dump_triple(dump, M, d, ao, (int)bo, cc[col].eo,
-                                            {x0, p011, p101, p110, p001, p010, p100, p000},
-                                            {x1, q011, q101, q110, q001, q010, q100, q000});
-                        }
                         // role e: the column's maximum over the warp's rows, written by the
                         // lowest lane (lowest new label a) holding it; skipped when no lane
-                        // reaches the column's pre-filter bound
-                        if (__any_sync(0xffffffffu, cand)) {
+                        // reaches the column's key threshold (taken 1024 units low: the
+                        // float form of the threshold is not exact)
+                        const float thr_fx = fmaf(cx.thr_c, prune.count_to_fx, -1024.0f);
+                        if (__any_sync(0xffffffffu, valid && (float)ig_e >= thr_fx)) {
                             const int emax = __reduce_max_sync(0xffffffffu, ig_e);
                             const unsigned hit = __ballot_sync(0xffffffffu, ig_e == emax);
                             if (lane == __ffs(hit) - 1)
-                                atomicMax(keys + cc[col].eo,
+                                atomicMax(keys + cx.eo,
                                           pack_key((float)emax * inv_scale, partner_index(dM, M, (uint32_t)ao, bo)));
                         }
                     }
@@ -730,8 +849,8 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
-                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, cudaStream_t st,
-                        uint32_t* dump, TcTestHooks hooks) {
+                        const int* perm, const PairC* pairs, unsigned long long* keys, int* err, double b0, double b1,
+                        cudaStream_t st, uint32_t* dump, TcTestHooks hooks) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
     const void* fn = dump ? (const void*)k3tc_kernel<true> : (const void*)k3tc_kernel<false>;
@@ -748,12 +867,23 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
     const unsigned long long wait_ns = hooks.wait_ns ? hooks.wait_ns : tc::kWaitLimitNs;
+    K3Prune prune;
+    const double scale = 4.0 * 0.6931471805599453 * std::ldexp(1.0, fbits);
+    prune.on = !hooks.exact && !dump && b0 >= 1e-3 && b1 >= 1e-3 &&
+               ((double)(tg.N0 + tg.N1) + 8.0 * (b0 + b1)) * 0.6931471805599453 * std::ldexp(1.0, fbits) <
+                   2147483647.0;
+    prune.beta0 = (float)b0;
+    prune.beta1 = (float)b1;
+    prune.fx_to_count = (float)(1.0 / scale);
+    prune.count_to_fx = (float)scale;
     if (dump)
         k3tc_kernel<true><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s,
-                                                        perm, pairs, keys, err, dump, wait_ns, hooks.withhold_kb);
+                                                        perm, pairs, keys, err, prune, dump, wait_ns,
+                                                        hooks.withhold_kb);
     else
         k3tc_kernel<false><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s,
-                                                         perm, pairs, keys, err, nullptr, wait_ns, hooks.withhold_kb);
+                                                         perm, pairs, keys, err, prune, nullptr, wait_ns,
+                                                         hooks.withhold_kb);
     return cudaGetLastError();
 }
 

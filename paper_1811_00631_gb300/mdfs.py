@@ -35,7 +35,8 @@ EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", 
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
             "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
             "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples",
-            "mdfs_release_stream", "mdfs_testing_counts", "mdfs_testing_k3_wait_fault")
+            "mdfs_release_stream", "mdfs_testing_counts", "mdfs_testing_k3_wait_fault",
+            "mdfs_testing_k3_exact")
 
 # p-value adjustment methods (MDFS_ADJUST_* of include/mdfs.h)
 P_ADJUST = {"none": 0, "bonferroni": 1, "holm": 2, "hochberg": 3, "BH": 4, "BY": 5}
@@ -119,6 +120,8 @@ def load(path: str = LIB_PATH):
         lib.mdfs_testing_counts.restype = ctypes.c_int
         lib.mdfs_testing_k3_wait_fault.argtypes = [ctypes.c_int, ctypes.c_longlong]
         lib.mdfs_testing_k3_wait_fault.restype = ctypes.c_int
+        lib.mdfs_testing_k3_exact.argtypes = []
+        lib.mdfs_testing_k3_exact.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -600,3 +603,9 @@ def testing_k3_wait_fault(withhold_kb: int = -1, wait_ns: int = 0) -> None:
     """Arms (or, with the defaults, disarms) the one-shot bounded-wait hook of
     the next k = 3 tensor-core scan."""
     _check(load().mdfs_testing_k3_wait_fault(int(withhold_kb), int(wait_ns)))
+
+
+def testing_k3_exact() -> None:
+    """Arms the one-shot hook under which the next k = 3 tensor-core scan
+    evaluates every triple exactly (no SH3 lower-bound skipping)."""
+    _check(load().mdfs_testing_k3_exact())
