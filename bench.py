@@ -9,7 +9,12 @@ tuple x discretisation evaluations per second:
 
 Default arm: inputs resident in HBM, each step timed with CUDA events on the
 launching stream, L2 flushed (512 MB write) between steps.  ``e2e`` repeats
-the steps through the C ABI with pinned host inputs and host outputs.
+the steps through the C ABI with pinned host inputs and host outputs.  The
+same JSON line also carries the measured tensor-core and shared-memory rates
+of the GPU (``peaks``), the roofline of the k = 3 kernel against the measured
+E4M3 rate, and the other configurations (``configs``: the 200 x 50 XOR case,
+k = 1 and k = 2 on the parity data, the batched 64-job workload), each timed
+and compared with the FP64 oracle on sampled variables.
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload (the method has no other reference implementation here).
 
@@ -272,27 +277,31 @@ def run_gpu(args, rank, world, local_rank):
         return 0
 
     # ---- roofline of the dominant kernel (k = 3 triple kernel) ----
-    # Counting runs on the tensor cores (one-hot E4M3 GEMM); the binding unit is
-    # the entropy epilogue's shared-memory table lookups: 24 per (triple,
-    # discretisation) for two classes (8 voxels x {class 0, class 1, total}).
+    # Counting runs on the tensor cores as a one-hot E4M3 GEMM: the useful work
+    # is one multiply-add per (triple, discretisation, sample) for the all-ones
+    # voxel, 2 C(M,3) D N flops per launch.  The entropy epilogue skips the
+    # table lookups of every triple that its SH3 lower bound rules out, so its
+    # lookups are data-dependent and not the bound.  The peak is this GPU's
+    # dense E4M3 rate measured in this run by the tcgen05 microbenchmark.
+    peaks = peaks_run(local_rank) if not args.no_peaks else None
     roof = None
     k3 = prof.get("k3", None)
     if k3 and k3["count"]:
         avg_s = k3["ms"] / k3["count"] / 1e3
         evals = math.comb(M, 3) * DISC
-        lookups = evals * 24
-        achieved = lookups / avg_s / 1e12
-        peak = float(args.smem_peak)
-        macs = evals * N_OBJ  # useful one-hot MACs (counts of the all-ones voxel)
-        bf16, bf16_src = _bf16_burst_peak()
-        roof = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "Tlookup/s", "frac": achieved / peak,
-                "traffic": args.k3_traffic, "kernel": "k3tc_kernel", "launch_ms": 1e3 * avg_s,
-                "per_launch": {"evals": evals, "lookups": lookups, "useful_fp8_flop": 2 * macs},
-                "peak_note": "32 banks x 4 B per clock per SM x 152 SMs x 2.07 GHz (unit count x max clock); "
-                             "random 4-byte lookups measured at 3.68 Tlookup/s on this GPU (bank conflicts)",
-                "tensor": {"achieved_tflops": 2 * macs / avg_s / 1e12,
-                           "peak_tflops": 2 * bf16, "frac": 2 * macs / avg_s / 1e12 / (2 * bf16),
-                           "peak_note": f"fp8 dense = 2 x {bf16_src} bf16 burst ({bf16} TF/s), of {bf16_src}"}}
+        flops = 2.0 * evals * N_OBJ
+        achieved = flops / avg_s / 1e12
+        if peaks:
+            peak, peak_src = peaks["fp8_mma_tflops"], "of measured (tcgen05 kind::f8f6f4 microbenchmark, this run)"
+        else:
+            bf16, bf16_src = _bf16_burst_peak()
+            peak, peak_src = 2 * bf16, f"2 x {bf16_src} bf16 burst ({bf16} TF/s), of {bf16_src}"
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k3tc_kernel", "launch_ms": 1e3 * avg_s,
+                "per_launch": {"evals": evals, "useful_fp8_flop": flops},
+                "peak_note": f"dense E4M3 {peak_src}",
+                "traffic_note": "not measured in this run; DRAM bytes per launch from the ncu capture are in "
+                                "profiles/ (the operand and pair records are read once: about 91 MB per launch)"}
     shares = {}
     tot = sum(v["ms"] for v in prof.values()) or 1.0
     for kname, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
@@ -319,6 +328,10 @@ def run_gpu(args, rank, world, local_rank):
         line["k4"] = k4_run(local_rank)
     if args.k5_m >= 5 and DIV == 1 and math.comb(args.k5_m, 4) < 2**32:
         line["k5"] = k5_run(args.k5_m, args.k5_disc, local_rank)
+    if peaks:
+        line["peaks"] = peaks
+    if args.configs and not args.small:
+        line["configs"] = configs_run(local_rank, args)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -331,6 +344,170 @@ def run_gpu(args, rank, world, local_rank):
                                           f"{nd} of the {DISC} discretisations, {dt:.1f} s"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def peaks_run(device: int):
+    """Measured rates of this GPU (library microbenchmarks): dense E4M3
+    tcgen05 MMA throughput and random 4-byte shared-memory loads."""
+    import torch
+    from paper_1811_00631_gb300 import mdfs
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mma = mdfs.bench_mma_f8(40000)
+    rnd = mdfs.bench_smem_lookup(4000, 0)
+    win = mdfs.bench_smem_lookup(4000, 64)
+    ghz = 2.07
+    return {"fp8_mma_tflops": mma["tflops"], "fp8_mma_s": mma["seconds"],
+            "smem_lookups_random_per_s": rnd["lookups_per_s"],
+            "smem_lookups_window64_per_s": win["lookups_per_s"],
+            "smem_lookups_random_per_sm_clock_at_2070mhz": rnd["lookups_per_s"] / sms / (ghz * 1e9),
+            "smem_lookups_window64_per_sm_clock_at_2070mhz": win["lookups_per_s"] / sms / (ghz * 1e9),
+            "how": "mdfs_bench_mma_f8 (one CTA per SM issuing tcgen05.mma kind::f8f6f4 128x256x32 on shared-memory "
+                   "operands) and mdfs_bench_smem_lookup (8 xorshift index streams per thread over a 64 KB table, "
+                   "whole table or 64-entry windows), CUDA events after a warm-up launch"}
+
+
+def _parity(codes, y, c, k, xi, g_ig, g_tu, g_di, ref, variables):
+    """Largest |IG - oracle| over the variables and how the argmax compares:
+    equal, a different (d, S) that the tolerance rule allows (oracle's top two
+    within 1e-4 + 1e-5 |o| and the GPU's choice within it of the maximum), or
+    bad."""
+    import oracle
+    err, equal, allowed, bad = 0.0, 0, 0, 0
+    for row, i in enumerate(variables):
+        o = float(ref["ig"][row])
+        tol = 1e-4 + 1e-5 * abs(o)
+        err = max(err, abs(float(g_ig[i]) - o))
+        S = [int(v) for v in g_tu[i]] if k > 1 else []
+        if int(g_di[i]) == int(ref["disc"][row]) and (k == 1 or tuple(S) == tuple(int(v) for v in ref["tuples"][row])):
+            equal += 1
+            continue
+        alt = oracle.ig_one(codes, y, c, xi, int(g_di[i]), int(i), S)
+        if o - float(ref["second"][row]) <= tol and o - alt <= tol:
+            allowed += 1
+        else:
+            bad += 1
+    return {"max_abs_err": err, "argmax_equal": equal, "argmax_other_within_tol": allowed, "argmax_bad": bad,
+            "variables": len(variables)}
+
+
+def _time_scan(torch, fn, reps: int):
+    """Median milliseconds of fn() over reps calls, CUDA events on the current stream."""
+    stream = torch.cuda.current_stream()
+    fn()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def configs_run(device: int, args):
+    """The other workloads of the method's configurations, each timed on the
+    device and compared with the FP64 oracle on sampled variables (all of them
+    for the small case):
+      xor_N200_M50_k2:  200 x 50 XOR data, 2 classes, 1 discretisation;
+      parity_N2000_M500_k1 / k2 (2 and 3 classes), 30 discretisations;
+      parity_N2000_M500_k3: the bench step's k = 3 scan (two variables);
+      batched_N1000_M20000_k2: 16 bootstrap folds x 4 label permutations in one
+        call, 3 classes, 10 discretisations (spot check of three jobs, one job
+        bit for bit against the single-job scan)."""
+    import torch
+
+    import oracle
+    from paper_1811_00631_gb300 import mdfs, synth
+    oracle.build()
+    dev = torch.device("cuda", device)
+    out = {}
+    # XOR 200 x 50, k = 2 (latency-bound: one call is a few launches)
+    ds = synth.xor_small()
+    x, y = torch.from_numpy(ds.x).to(dev), torch.from_numpy(ds.y).to(dev)
+    ms = _time_scan(torch, lambda: mdfs.max_ig(x, y, 2, 1, 1, 0.25, 0.25, 1), 20)
+    g = [t.cpu().numpy() for t in mdfs.max_ig(x, y, 2, 1, 1, 0.25, 0.25, 1)]
+    codes = oracle.discretize(ds.x, 1, 1, 0.25, 1)
+    ref = oracle.max_ig(codes, ds.y, 2, 2, 0.25)
+    out["xor_N200_M50_k2"] = {"ms_per_call": ms, "evals_per_s": math.comb(50, 2) / (ms / 1e3),
+                              **_parity(codes, ds.y, 2, 2, 0.25, *g, ref, range(50))}
+    # parity data 2000 x 500: k = 1, k = 2 with 2 and 3 classes, 30 discretisations
+    ds = synth.madelon_like()
+    x, y = torch.from_numpy(ds.x).to(dev), torch.from_numpy(ds.y).to(dev)
+    rng = np.random.default_rng(3)
+    noise = np.setdiff1d(np.arange(500), ds.informative)
+    variables = np.concatenate([ds.informative, rng.choice(noise, 10, replace=False)]).astype(np.int32)
+    for k, div in ((1, 1), (2, 1), (2, 2)):
+        ms = _time_scan(torch, lambda: mdfs.max_ig(x, y, k, div, 30, 0.5, 0.25, 11), 5)
+        g = [t.cpu().numpy() for t in mdfs.max_ig(x, y, k, div, 30, 0.5, 0.25, 11)]
+        codes = oracle.discretize(ds.x, div, 30, 0.5, 11)
+        ref = oracle.max_ig(codes, ds.y, div + 1, k, 0.25, variables=variables)
+        out[f"parity_N2000_M500_k{k}_c{div + 1}"] = {
+            "ms_per_call": ms, "evals_per_s": math.comb(500, k) * 30 / (ms / 1e3),
+            **_parity(codes, ds.y, div + 1, k, 0.25, *g, ref, variables)}
+    # k = 3 of the bench step: two variables, full partner scans over 30 discretisations
+    g = [t.cpu().numpy() for t in mdfs.max_ig(x, y, 3, 1, 30, 0.5, 0.25, 11)]
+    codes = oracle.discretize(ds.x, 1, 30, 0.5, 11)
+    v3 = np.array([ds.info["base"][0], int(noise[0])], dtype=np.int32)
+    ref = oracle.max_ig(codes, ds.y, 2, 3, 0.25, variables=v3)
+    out["parity_N2000_M500_k3_c2"] = {"timing": "the bench step's k = 3 launch (roofline)",
+                                      **_parity(codes, ds.y, 2, 3, 0.25, *g, ref, v3)}
+    if args.batch_configs:
+        out["batched_N1000_M20000_k2_c3"] = batched_check(device, args.batch_folds, args.batch_perms, args.batch_m)
+    return out
+
+
+def batched_check(device: int, n_folds: int, n_perms: int, M: int):
+    """The batched workload in one mdfs_max_ig_batch call, timed with CUDA
+    events; three jobs spot-checked against the oracle and one job bit for bit
+    against the single-job scan of its resampled data."""
+    import torch
+
+    import oracle
+    from paper_1811_00631_gb300 import mdfs, synth
+    dev = torch.device("cuda", device)
+    N, D, div, r, xi, seed = 1000, 10, 2, 0.5, 0.25, 1
+    ds = synth.xor_pairs(N=N, M=M, n_pairs=100, seed=4)
+    idx, yperm = synth.bootstrap_jobs(N, n_folds=n_folds, n_perms=n_perms, seed=5)
+    si = np.repeat(idx, n_perms, axis=0).astype(np.int32)
+    yp = np.tile(yperm, (n_folds, 1)).astype(np.int32)
+    x, y = torch.from_numpy(ds.x).to(dev), torch.from_numpy(ds.y).to(dev)
+    sid, ypd = torch.from_numpy(si).to(dev), torch.from_numpy(yp).to(dev)
+    J = n_folds * n_perms
+    mdfs.max_ig_batch(x, y, sid[:1], ypd[:1], n_jobs=1, k=2, divisions=div, discretizations=D, range_=r, seed=seed)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ig, tu, di = mdfs.max_ig_batch(x, y, sid, ypd, n_jobs=J, k=2, divisions=div, discretizations=D, range_=r,
+                                   pc_xi=xi, seed=seed)
+    b.record()
+    b.synchronize()
+    secs = a.elapsed_time(b) / 1e3
+    ig, tu, di = ig.cpu().numpy(), tu.cpu().numpy(), di.cpu().numpy()
+    pairs = ds.info["pairs"]
+    found = sum(int(tu[0, p, 0] == q) + int(tu[0, q, 0] == p) for p, q in pairs)
+    rng = np.random.default_rng(17)
+    checks = []
+    for j in (0, J // 2, J - 1):
+        xj = np.ascontiguousarray(ds.x[:, si[j]])
+        yj = ds.y[yp[j][si[j]]]
+        codes = oracle.discretize(xj, div, D, r, seed)
+        p, q = pairs[rng.integers(len(pairs))]
+        variables = np.array(sorted({int(p), int(q), *rng.choice(M, 2, replace=False).tolist()}), np.int32)
+        ref = oracle.max_ig(codes, yj, div + 1, 2, xi, variables=variables)
+        checks.append(_parity(codes, yj, div + 1, 2, xi, ig[j], tu[j], di[j], ref, variables))
+    j = J - 1
+    w = mdfs.max_ig(torch.from_numpy(np.ascontiguousarray(ds.x[:, si[j]])).to(dev),
+                    torch.from_numpy(ds.y[yp[j][si[j]]]).to(dev), 2, div, D, r, xi, seed)
+    single_equal = all(np.array_equal(u, v.cpu().numpy()) for u, v in zip((ig[j], tu[j], di[j]), w))
+    return {"jobs": J, "seconds": secs, "evals_per_s": J * math.comb(M, 2) * D / secs,
+            "max_abs_err": max(c["max_abs_err"] for c in checks),
+            "argmax_bad": sum(c["argmax_bad"] for c in checks),
+            "argmax_equal": sum(c["argmax_equal"] for c in checks),
+            "argmax_other_within_tol": sum(c["argmax_other_within_tol"] for c in checks),
+            "variables_checked": sum(c["variables"] for c in checks),
+            "job_equals_single_job_scan": bool(single_equal),
+            "xor_partners_recovered_job0": f"{found}/{2 * len(pairs)}"}
 
 
 def select_run(reps: int, device: int):
@@ -512,11 +689,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--smem-peak", type=float, default=32 * 152 * 2.07e9 / 1e12,
-                    help="shared-memory lookup peak, 10^12 4-byte lookups/s")
-    ap.add_argument("--k3-traffic", type=float, default=93863424.0,
-                    help="DRAM bytes (read + write) per full-size k=3 launch from an ncu capture of the "
-                         "current kernel (profiles/launches_mdfs_scan_parity_N2000_M500_k2k3_D30.md)")
     ap.add_argument("--small", action="store_true", help="reduced profiling case (M=500, D=--small-disc)")
     ap.add_argument("--small-disc", type=int, default=2, help="discretisations of the --small case")
     ap.add_argument("--serving-jobs", type=int, default=512, help="jobs of the serving-mix run (0: skip)")
@@ -527,6 +699,10 @@ def main():
     ap.add_argument("--k5-disc", type=int, default=1, help="discretisations of the timed k = 5 scan")
     ap.add_argument("--select-reps", type=int, default=3,
                     help="timed calls of the selection pipeline per k (0: skip)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the tensor-core and shared-memory microbenchmarks")
+    ap.add_argument("--configs", type=int, default=1, help="time the other configurations with oracle checks (0: skip)")
+    ap.add_argument("--batch-configs", type=int, default=1,
+                    help="include the batched 64-job workload among the configurations (0: skip)")
     ap.add_argument("--batched", action="store_true", help="run the batched k=2 workload instead")
     ap.add_argument("--batch-folds", type=int, default=16)
     ap.add_argument("--batch-perms", type=int, default=4)
@@ -534,6 +710,7 @@ def main():
     args = ap.parse_args()
     if args.small:
         _use_small_case(args.small_disc)
+        args.configs = 0
         args.serving_jobs = 0
         args.select_reps = 0
         args.k4 = 0

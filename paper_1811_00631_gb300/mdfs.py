@@ -35,7 +35,7 @@ EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", 
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
             "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
             "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples",
-            "mdfs_release_stream", "mdfs_testing_counts", "mdfs_testing_k3_wait_fault",
+            "mdfs_release_stream", "mdfs_bench_mma_f8", "mdfs_bench_smem_lookup", "mdfs_testing_counts", "mdfs_testing_k3_wait_fault",
             "mdfs_testing_k3_exact")
 
 # p-value adjustment methods (MDFS_ADJUST_* of include/mdfs.h)
@@ -114,6 +114,11 @@ def load(path: str = LIB_PATH):
         lib.mdfs_profile.restype = ctypes.c_int
         lib.mdfs_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int]
         lib.mdfs_profile_report.restype = ctypes.c_int
+        # hardware microbenchmarks (include/mdfs_bench.h)
+        lib.mdfs_bench_mma_f8.argtypes = [ctypes.c_int, P, P]
+        lib.mdfs_bench_mma_f8.restype = ctypes.c_int
+        lib.mdfs_bench_smem_lookup.argtypes = [ctypes.c_int, ctypes.c_int, P, P]
+        lib.mdfs_bench_smem_lookup.restype = ctypes.c_int
         # test-only entry points (include/mdfs_testing.h)
         lib.mdfs_testing_counts.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_uint64, P, P]
@@ -576,6 +581,23 @@ def release_stream(stream) -> None:
 
 def abi_version() -> int:
     return load().mdfs_abi_version()
+
+
+# ---- hardware microbenchmarks (include/mdfs_bench.h) --------------------------
+def bench_mma_f8(iters: int = 40000) -> dict:
+    """Dense E4M3 tensor-core throughput of the current device (tcgen05.mma
+    128 x 256 x 32 on shared-memory operands, one CTA per SM)."""
+    tf, sec = ctypes.c_double(), ctypes.c_double()
+    _check(load().mdfs_bench_mma_f8(int(iters), ctypes.byref(tf), ctypes.byref(sec)))
+    return {"tflops": tf.value, "seconds": sec.value, "iters": int(iters)}
+
+
+def bench_smem_lookup(iters: int = 4000, window: int = 0) -> dict:
+    """Random 4-byte shared-memory loads per second (window 0: the whole 64 KB
+    table; else that many consecutive entries at a warp-wide offset)."""
+    rate, sec = ctypes.c_double(), ctypes.c_double()
+    _check(load().mdfs_bench_smem_lookup(int(iters), int(window), ctypes.byref(rate), ctypes.byref(sec)))
+    return {"lookups_per_s": rate.value, "seconds": sec.value, "iters": int(iters), "window": int(window)}
 
 
 # ---- test-only entry points (include/mdfs_testing.h) -------------------------
