@@ -52,13 +52,13 @@ int mdfs_testing_counts(const mdfs_data* data, int k, int divisions, int discret
 int mdfs_testing_k3_wait_fault(int withhold_kb, long long wait_ns);
 
 /*
- * Arms a one-shot hook that the next k = 3 tensor-core scan of any thread
- * takes and clears: that scan evaluates the regularised entropy of every
- * triple exactly, without skipping the triples that a lower bound of SH3
- * rules out.  Its results must equal those of the normal scan bit for bit.
- * Returns 0.
+ * Arms a one-shot hook that the next tensor-core scan (k = 2 or k = 3) of any
+ * thread takes and clears: that scan evaluates the regularised entropy of
+ * every tuple exactly, without skipping the tuples that a lower bound of the
+ * entropy rules out.  Its results must equal those of the normal scan bit for
+ * bit.  Returns 0.
  */
-int mdfs_testing_k3_exact(void);
+int mdfs_testing_exact(void);
 
 #ifdef __cplusplus
 }

@@ -116,14 +116,21 @@ int kernel_flag_error(int flag, int job = -1) {
     return fail(MDFS_ETIMEOUT, "%sa device-side wait timed out in a tensor-core kernel", where);
 }
 
-// Test hooks of the triple kernel set by mdfs_testing_k3_wait_fault, taken
-// (and cleared) by the next k = 3 tensor-core scan of any thread.
+// Test hooks of the tensor-core kernels: the wait fault (mdfs_testing_k3_wait_fault)
+// is taken by the next k = 3 tensor-core scan, the exact evaluation
+// (mdfs_testing_exact) by the next k = 2 or k = 3 one, each then cleared.
 std::mutex g_hooks_mu;
 TcTestHooks g_hooks;
-TcTestHooks take_test_hooks() {
+TcTestHooks take_test_hooks(bool k3) {
     std::lock_guard<std::mutex> lock(g_hooks_mu);
     TcTestHooks h = g_hooks;
-    g_hooks = TcTestHooks();
+    if (k3) {
+        g_hooks = TcTestHooks();
+    } else {
+        h.wait_ns = 0;
+        h.withhold_kb = -1;
+        g_hooks.exact = false;
+    }
     return h;
 }
 
@@ -481,8 +488,10 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M * P, D, tg.Kp));
         int lo = 0;
         const int cnt = share(ws->n_items3, &lo);
+        const bool exact = take_test_hooks(false).exact;
         MDFS_LAUNCH("k2", st, launch_k2tc(map, tg, M, c, 0, D, (const int2*)ws->items3.p + lo, cnt, tab,
-                                          k3tc_fraction_bits(N), cnt1, sh1, keys, (int*)ws->err.p, st, dump));
+                                          k3tc_fraction_bits(N), cnt1, sh1, keys, (int*)ws->err.p, b0, b1,
+                                          !exact, st, dump));
         *check_err = true;
     } else if (k == 2) {
         if (shard == 0)
@@ -522,7 +531,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         MDFS_LAUNCH("k3_operand", st, launch_k3tc_operand(onehot, (uint8_t*)ws->onehot2.p, lperm, M, D, tg, st));
         CUtensorMap map;
         MDFS_CUDA_TRY(make_onehot_map(&map, (const uint8_t*)ws->onehot2.p, M, D, tg.Kp));
-        const TcTestHooks hooks = take_test_hooks();
+        const TcTestHooks hooks = take_test_hooks(true);
         for (int d0 = 0; d0 < D; d0 += nd) {
             const int nn = std::min(nd, D - d0);
             MDFS_LAUNCH("k2_tables", st, launch_k2(planes, g, M, c, D, d0, nn, tab, cnt1, sh1, nullptr, nullptr,
@@ -1339,7 +1348,7 @@ int mdfs_testing_counts(const mdfs_data* data, int k, int divisions, int discret
     return MDFS_OK;
 }
 
-int mdfs_testing_k3_exact(void) {
+int mdfs_testing_exact(void) {
     g_err.clear();
     std::lock_guard<std::mutex> lock(g_hooks_mu);
     g_hooks.exact = true;

@@ -221,9 +221,13 @@ size_t k2tc_smem_bytes(int N0, int N1);
 // dump != NULL (test hook): also writes the c x c class counts of every pair
 // i < m, [D][C(M,2)][c c] uint32 n0 | n1 << 16 at the pair's rank in the upper
 // triangle, voxel code_i c + code_m.
+// b0, b1: the pseudocounts of the two decision classes; with bound (and three
+// classes per variable) they enter a lower bound of SH2 that lets the epilogue
+// skip pairs that cannot change a key.
 cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
                         int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
-                        unsigned long long* keys, int* err, cudaStream_t st, uint32_t* dump = nullptr);
+                        unsigned long long* keys, int* err, double b0, double b1, bool bound, cudaStream_t st,
+                        uint32_t* dump = nullptr);
 
 // Contrast rows M .. M + n_contrast - 1 of x_ext (dtype 0 f32, 1 i8); rows
 // 0 .. M-1 are not written.  src [n_contrast] or NULL.

@@ -60,19 +60,53 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k)
 
 __device__ __forceinline__ int tab32(const int* t, int n, int nmax) { return t[min((unsigned)n, (unsigned)nmax)]; }
 
+// Bound that lets the epilogue skip the table lookups of most pairs (three
+// classes per variable).  Each voxel's term of SH is E(m0, m1) = f(m0 + m1) -
+// f(m0) - f(m1) = (m0 + m1) H(m0 / (m0 + m1)) with the smoothed class counts
+// m_d = n_d + beta_d, and H(p) >= 4 ln 2 p (1 - p) gives
+//     SH2 >= 4 ln 2 sum_v m0_v m1_v / (m0_v + m1_v) = 4 ln 2 LB.
+// IG(i | m) = SH1(m) - SH2 can raise i's key only if SH2 <= SH1(m) - IG_key(i),
+// and likewise for m, so a pair with LB above both limits (in units of 4 ln 2
+// nats, with the margins kBoundRel |hi| + kBoundAbs for float rounding) cannot
+// change any result and skips its 27 lookups.
+struct K2Prune {
+    int on;
+    float beta0, beta1;  // pseudocounts of the two decision classes
+};
+constexpr float kBoundRel = 1.0f / 4096.0f, kBoundAbs = 0.05f;
+constexpr float kInv4Ln2 = 0.36067376022224085f;            // 1 / (4 ln 2)
+constexpr float kFx32ToCount = 2.3283064365386963e-10f * kInv4Ln2;  // 2^-32 / (4 ln 2)
+
+// The IG of a key in units of 4 ln 2 nats; -inf for a key not yet set.
+__device__ __forceinline__ float key_ig_count(unsigned long long key) {
+    return key ? order_bits_float((uint32_t)(key >> 32)) * kInv4Ln2 : -INFINITY;
+}
+
+// a / b + c / d as one fraction num / den (b, d > 0)
+__device__ __forceinline__ void frac_add(float a, float b, float c, float d, float& num, float& den) {
+    num = fmaf(a, d, c * b);
+    den = b * d;
+}
+
+// Integers below 2^22 in magnitude between int and float, through the bits of
+// 1.5 2^23 + v (exact; no conversion instruction).
+__device__ __forceinline__ float i2f_exact(int v) { return __int_as_float(0x4B400000 + v) - 12582912.0f; }
+__device__ __forceinline__ int f2i_exact(float f) { return __float_as_int(f + 12582912.0f) - 0x4B400000; }
+
 // c x c voxel counts of one channel from the all->=1 block X (P x P) and the
-// marginals of the row variable (ni[0..P-1]) and column variable (nm[..]).
-template <int P>
-__device__ __forceinline__ void complete2(const int (&X)[P][P], const int (&ni)[P], const int (&nm)[P], int ntot,
-                                          int (&T)[P + 1][P + 1]) {
-    int all = 0;
+// marginals of the row variable (ni[0..P-1]) and column variable (nm[..]);
+// integer-valued floats (exact below 2^24).
+template <int P, typename V>
+__device__ __forceinline__ void complete2(const V (&X)[P][P], const V (&ni)[P], const V (&nm)[P], V ntot,
+                                          V (&T)[P + 1][P + 1]) {
+    V all = 0;
 #pragma unroll
     for (int a = 0; a < P; ++a)
 #pragma unroll
         for (int b = 0; b < P; ++b) T[a + 1][b + 1] = X[a][b];
 #pragma unroll
     for (int a = 0; a < P; ++a) {
-        int s = 0;
+        V s = 0;
 #pragma unroll
         for (int b = 0; b < P; ++b) s += X[a][b];
         T[a + 1][0] = ni[a] - s;
@@ -80,7 +114,7 @@ __device__ __forceinline__ void complete2(const int (&X)[P][P], const int (&ni)[
     }
 #pragma unroll
     for (int b = 0; b < P; ++b) {
-        int s = 0;
+        V s = 0;
 #pragma unroll
         for (int a = 0; a < P; ++a) s += X[a][b];
         T[0][b + 1] = nm[b] - s;
@@ -98,8 +132,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     k2tc_kernel(const __grid_constant__ CUtensorMap map_oh, TcGeom tg, int M, int d0, int nd,
                 const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
                 const int* __restrict__ cnt1, const long long* __restrict__ sh1, unsigned long long* __restrict__ keys,
-                int* __restrict__ err, uint32_t* __restrict__ dump) {
+                int* __restrict__ err, K2Prune prune, uint32_t* __restrict__ dump) {
     constexpr int C = P + 1;
+    // the bound pays for itself with three classes (27 lookups per pair)
+    const bool use_bound = P == 2 && !kDump && prune.on;
     constexpr int VT = kTile / P;  // variables per tile
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_empty[kStages];
@@ -245,15 +281,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int* c1 = cnt1 + (size_t)d * M * P * 2;
             const long long* s1 = sh1 + (size_t)d * M;
             const bool irow = vi < M;
-            // row-variable context
-            int ni0[P], ni1[P], nit[P];
+            // row-variable context (class counts of bins 1..P as exact floats)
+            float ni0[P], ni1[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                ni0[p] = irow ? c1[((size_t)vi * P + p) * 2] : 0;
-                ni1[p] = irow ? c1[((size_t)vi * P + p) * 2 + 1] : 0;
-                nit[p] = ni0[p] + ni1[p];
+                ni0[p] = i2f_exact(irow ? c1[((size_t)vi * P + p) * 2] : 0);
+                ni1[p] = i2f_exact(irow ? c1[((size_t)vi * P + p) * 2 + 1] : 0);
             }
             const int shi = irow ? fx_narrow(s1[vi], fbits) : 0;
+            // SH1(i) and the key of i in units of 4 ln 2 nats (the bound's units)
+            const float shi_c = irow ? (float)s1[vi] * kFx32ToCount : 0.0f;
+            const float keyi_c = irow ? key_ig_count(__ldcg(keys + vi)) : 0.0f;
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
 
             if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort))) break;  // warp-uniform
@@ -269,47 +307,97 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::tmem_ld16(taddr + kTile, *reinterpret_cast<uint32_t(*)[16]>(&r1[0]));
                 tc::tmem_ld16(taddr + kTile + 16, *reinterpret_cast<uint32_t(*)[16]>(&r1[16]));
                 tc::tmem_ld_wait();
+                // column-variable context: lane j holds column vm0 + j (j < columns of
+                // the warp), handed to every lane of the warp by shuffles per column
+                constexpr int kCols = kColsPerWarp / P;
+                const int vcol = vm0 + lane % kCols;
+                const bool colok = vcol < M;
+                float cn0[P], cn1[P];
 #pragma unroll
-                for (int jm = 0; jm < kColsPerWarp / P; ++jm) {
+                for (int p = 0; p < P; ++p) {
+                    cn0[p] = i2f_exact(colok ? c1[((size_t)vcol * P + p) * 2] : 0);
+                    cn1[p] = i2f_exact(colok ? c1[((size_t)vcol * P + p) * 2 + 1] : 0);
+                }
+                const int csh = colok ? fx_narrow(s1[vcol], fbits) : 0;
+                // SH1(m) and the key of m in units of 4 ln 2 nats (the bound's units)
+                const float cshc = (use_bound && colok) ? (float)s1[vcol] * kFx32ToCount : 0.0f;
+                const float ckey = (use_bound && colok) ? key_ig_count(__ldcg(keys + vcol)) : 0.0f;
+                const float fN0 = i2f_exact(N0), fN1 = i2f_exact(N1);
+#pragma unroll
+                for (int jm = 0; jm < kCols; ++jm) {
                     const int vm = vm0 + jm;
                     const bool ok = irow && vm < M && (!diag || vi < vm);
-                    // counts of the all->=1 block, both classes: X?[alpha][beta] here,
-                    // the other row(s) of the block from the neighbouring lane
-                    int X0[P][P], X1[P][P];
+                    // counts of the all->=1 block, both classes, exact in FP32: X?[alpha][beta]
+                    // here, the other row(s) of the block from the neighbouring lane
+                    float X0[P][P], X1[P][P];
 #pragma unroll
                     for (int b = 0; b < P; ++b) {
-                        const int v0 = (int)__uint_as_float(r0[jm * P + b]);
-                        const int v1 = (int)__uint_as_float(r1[jm * P + b]);
+                        const float v0 = __uint_as_float(r0[jm * P + b]);
+                        const float v1 = __uint_as_float(r1[jm * P + b]);
                         if (P == 1) {
                             X0[0][b] = v0;
                             X1[0][b] = v1;
                         } else {
-                            const int o0 = __shfl_xor_sync(0xffffffffu, v0, 1);
-                            const int o1 = __shfl_xor_sync(0xffffffffu, v1, 1);
+                            const float o0 = __shfl_xor_sync(0xffffffffu, v0, 1);
+                            const float o1 = __shfl_xor_sync(0xffffffffu, v1, 1);
                             X0[0][b] = alpha ? o0 : v0;
                             X0[P - 1][b] = alpha ? v0 : o0;
                             X1[0][b] = alpha ? o1 : v1;
                             X1[P - 1][b] = alpha ? v1 : o1;
                         }
                     }
-                    // column-variable context
-                    int nm0[P], nm1[P], nmt[P];
-                    const int vmc = ok ? vm : 0;
+                    float nm0[P], nm1[P];
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        nm0[p] = c1[((size_t)vmc * P + p) * 2];
-                        nm1[p] = c1[((size_t)vmc * P + p) * 2 + 1];
-                        nmt[p] = nm0[p] + nm1[p];
+                        nm0[p] = __shfl_sync(0xffffffffu, cn0[p], jm);
+                        nm1[p] = __shfl_sync(0xffffffffu, cn1[p], jm);
                     }
-                    int XT[P][P];
+                    float T0v[C][C], T1v[C][C];
+                    complete2<P>(X0, ni0, nm0, fN0, T0v);
+                    complete2<P>(X1, ni1, nm1, fN1, T1v);
+                    // pairs whose SH2 lower bound rules out both roles skip the lookups
+                    bool need = ok;
+                    if (use_bound) {
+                        const float shm_c = __shfl_sync(0xffffffffu, cshc, jm);
+                        const float keym_c = __shfl_sync(0xffffffffu, ckey, jm);
+                        // this lane's voxels: alpha 0 takes 0..4, alpha 1 takes 5..8 (row-major)
+                        float pn[5], ps[5];
 #pragma unroll
-                    for (int a = 0; a < P; ++a)
+                        for (int u = 0; u < 5; ++u) {
+                            const int va = u, vb = u + 5;
+                            const float n0 = alpha ? (vb < C * C ? T0v[vb / C][vb % C] : 0.0f) : T0v[va / C][va % C];
+                            const float n1 = alpha ? (vb < C * C ? T1v[vb / C][vb % C] : 0.0f) : T1v[va / C][va % C];
+                            const float m0 = n0 + prune.beta0, m1 = n1 + prune.beta1;
+                            const bool used = !alpha || vb < C * C;
+                            pn[u] = used ? m0 * m1 : 0.0f;  // an unused slot adds 0 / 1
+                            ps[u] = used ? m0 + m1 : 1.0f;
+                        }
+                        float n01, d01, n23, d23, n03, d03, nl, dl;
+                        frac_add(pn[0], ps[0], pn[1], ps[1], n01, d01);
+                        frac_add(pn[2], ps[2], pn[3], ps[3], n23, d23);
+                        frac_add(n01, d01, n23, d23, n03, d03);
+                        frac_add(n03, d03, pn[4], ps[4], nl, dl);
+                        // both lanes of the variable combine the two halves in the same order
+                        const float on = __shfl_xor_sync(0xffffffffu, nl, 1), od = __shfl_xor_sync(0xffffffffu, dl, 1);
+                        const float na = alpha ? on : nl, da = alpha ? od : dl, nb = alpha ? nl : on,
+                                    db = alpha ? dl : od;
+                        const float num = fmaf(na, db, nb * da), den = da * db;
+                        // largest SH2 (units of 4 ln 2 nats) that lets one role reach its key
+                        const float hi = fmaxf(shm_c - keyi_c, shi_c - keym_c);
+                        const float lim = fmaf(fabsf(hi), kBoundRel, hi + kBoundAbs);
+                        need = ok && num <= lim * den;
+                    }
+                    if (!__any_sync(0xffffffffu, need)) continue;
+                    // exact path: integer counts and the table lookups
+                    int T0i[C][C], T1i[C][C], TTi[C][C];
 #pragma unroll
-                        for (int b = 0; b < P; ++b) XT[a][b] = X0[a][b] + X1[a][b];
-                    int T0v[C][C], T1v[C][C], TTv[C][C];
-                    complete2<P>(X0, ni0, nm0, N0, T0v);
-                    complete2<P>(X1, ni1, nm1, N1, T1v);
-                    complete2<P>(XT, nit, nmt, N, TTv);
+                    for (int a = 0; a < C; ++a)
+#pragma unroll
+                        for (int b = 0; b < C; ++b) {
+                            T0i[a][b] = f2i_exact(T0v[a][b]);
+                            T1i[a][b] = f2i_exact(T1v[a][b]);
+                            TTi[a][b] = T0i[a][b] + T1i[a][b];
+                        }
                     if constexpr (kDump) {
                         if (ok && (P == 1 || alpha == 0)) {
                             const unsigned long long np = (unsigned long long)M * (M - 1) / 2;
@@ -320,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             for (int a = 0; a < C; ++a)
 #pragma unroll
                                 for (int b = 0; b < C; ++b)
-                                    o[a * C + b] = (uint32_t)T0v[a][b] | ((uint32_t)T1v[a][b] << 16);
+                                    o[a * C + b] = (uint32_t)T0i[a][b] | ((uint32_t)T1i[a][b] << 16);
                         }
                     }
                     int part = 0;
@@ -329,8 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int a = 0; a < C; ++a)
 #pragma unroll
                             for (int b = 0; b < C; ++b)
-                                part += tab32(sTB, TTv[a][b], N) - tab32(sT0, T0v[a][b], N0) -
-                                        tab32(sT1, T1v[a][b], N1);
+                                part += tab32(sTB, TTi[a][b], N) - tab32(sT0, T0i[a][b], N0) -
+                                        tab32(sT1, T1i[a][b], N1);
                     } else {
                         // the two lanes of a variable split the lookups without diverging:
                         // lane alpha = 0 takes class 0 and total voxels 0..4, alpha = 1
@@ -340,22 +428,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int a = 0; a < C; ++a)
 #pragma unroll
-                            for (int b = 0; b < C; ++b) part -= tab32(tcls, alpha ? T1v[a][b] : T0v[a][b], ncls);
+                            for (int b = 0; b < C; ++b) part -= tab32(tcls, alpha ? T1i[a][b] : T0i[a][b], ncls);
 #pragma unroll
                         for (int u = 0; u < 5; ++u) {
-                            const int lo = TTv[u / C][u % C];
-                            const int hi = u + 5 < C * C ? TTv[(u + 5) / C][(u + 5) % C] : 0;
+                            const int lo = TTi[u / C][u % C];
+                            const int hi = u + 5 < C * C ? TTi[(u + 5) / C][(u + 5) % C] : 0;
                             const int v = tab32(sTB, alpha ? hi : lo, N);
                             part += (alpha && u + 5 >= C * C) ? 0 : v;
                         }
                         part += __shfl_xor_sync(0xffffffffu, part, 1);
                     }
                     const int sh2 = part;
+                    const int shm = __shfl_sync(0xffffffffu, csh, jm);
                     unsigned long long k_m = 0ull;
                     if (ok) {
                         if (P == 1 || alpha == 0) {
                             // IG(i | m) = SH1(m) - SH2
-                            const float g = (float)(fx_narrow(s1[vm], fbits) - sh2) * inv_scale;
+                            const float g = (float)(shm - sh2) * inv_scale;
                             ki = umax64(ki, pack_key(g, dM + (uint32_t)vm));
                         }
                         if (P == 1 || alpha == 1) {
@@ -396,7 +485,8 @@ bool k2tc_supported(int c) { return c == 2 || c == 3; }
 
 cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
                         int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
-                        unsigned long long* keys, int* err, cudaStream_t st, uint32_t* dump) {
+                        unsigned long long* keys, int* err, double b0, double b1, bool bound, cudaStream_t st,
+                        uint32_t* dump) {
     if (n_items == 0) return cudaSuccess;
     const size_t smem = k2tc_smem_bytes(tg.N0, tg.N1);
     const void* fn = c == 2 ? (dump ? (const void*)k2tc_kernel<1, true> : (const void*)k2tc_kernel<1, false>)
@@ -413,8 +503,13 @@ cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0,
     const long long n_tiles = (long long)n_items * nd;
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
+    K2Prune prune;
+    prune.on = bound && b0 >= 1e-3 && b1 >= 1e-3;
+    prune.beta0 = (float)b0;
+    prune.beta1 = (float)b1;
     auto launch = [&](auto kern) {
-        kern<<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys, err, dump);
+        kern<<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys, err, prune,
+                                           dump);
     };
     if (c == 2) {
         if (dump) launch(k2tc_kernel<1, true>);

@@ -36,7 +36,7 @@ EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", 
             "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
             "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples",
             "mdfs_release_stream", "mdfs_bench_mma_f8", "mdfs_bench_smem_lookup", "mdfs_testing_counts", "mdfs_testing_k3_wait_fault",
-            "mdfs_testing_k3_exact")
+            "mdfs_testing_exact")
 
 # p-value adjustment methods (MDFS_ADJUST_* of include/mdfs.h)
 P_ADJUST = {"none": 0, "bonferroni": 1, "holm": 2, "hochberg": 3, "BH": 4, "BY": 5}
@@ -125,8 +125,8 @@ def load(path: str = LIB_PATH):
         lib.mdfs_testing_counts.restype = ctypes.c_int
         lib.mdfs_testing_k3_wait_fault.argtypes = [ctypes.c_int, ctypes.c_longlong]
         lib.mdfs_testing_k3_wait_fault.restype = ctypes.c_int
-        lib.mdfs_testing_k3_exact.argtypes = []
-        lib.mdfs_testing_k3_exact.restype = ctypes.c_int
+        lib.mdfs_testing_exact.argtypes = []
+        lib.mdfs_testing_exact.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -627,7 +627,7 @@ def testing_k3_wait_fault(withhold_kb: int = -1, wait_ns: int = 0) -> None:
     _check(load().mdfs_testing_k3_wait_fault(int(withhold_kb), int(wait_ns)))
 
 
-def testing_k3_exact() -> None:
-    """Arms the one-shot hook under which the next k = 3 tensor-core scan
-    evaluates every triple exactly (no SH3 lower-bound skipping)."""
-    _check(load().mdfs_testing_k3_exact())
+def testing_exact() -> None:
+    """Arms the one-shot hook under which the next tensor-core scan (k = 2 or
+    k = 3) evaluates every tuple exactly (no entropy lower-bound skipping)."""
+    _check(load().mdfs_testing_exact())

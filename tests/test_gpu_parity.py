@@ -394,14 +394,14 @@ def test_k4_errors(cuda):
         mdfs.max_ig(xl, yl, 4, 1, 1)  # 1700^3 >= 2^32: keys cannot index the triple
 
 
-def _k3_pair(torch, x, y, D, r, xi, seed):
-    """The k = 3 scan evaluated exactly for every triple (test hook), then the
-    normal scan that skips triples by the SH3 lower bound."""
+def _exact_and_bounded(torch, x, y, k, div, D, r, xi, seed):
+    """The tensor-core scan evaluated exactly for every tuple (test hook), then
+    the normal scan that skips tuples by the entropy lower bound."""
     from paper_1811_00631_gb300 import mdfs
     xt, yt = torch.from_numpy(np.ascontiguousarray(x)).cuda(), torch.from_numpy(np.ascontiguousarray(y)).cuda()
-    mdfs.testing_k3_exact()
-    exact = [t.cpu().numpy() for t in mdfs.max_ig(xt, yt, 3, 1, D, r, xi, seed)]
-    fast = [t.cpu().numpy() for t in mdfs.max_ig(xt, yt, 3, 1, D, r, xi, seed)]
+    mdfs.testing_exact()
+    exact = [t.cpu().numpy() for t in mdfs.max_ig(xt, yt, k, div, D, r, xi, seed)]
+    fast = [t.cpu().numpy() for t in mdfs.max_ig(xt, yt, k, div, D, r, xi, seed)]
     return exact, fast
 
 
@@ -427,6 +427,37 @@ def test_k3_bound_changes_no_result(cuda, case):
         if case == "unbalanced":
             y = (rng.random(N) < 0.12).astype(np.uint8) | ((x[5] > 1.2) & (x[7] > 1.0)).astype(np.uint8)
         xi = {"unbalanced": 0.25, "small_xi": 0.002, "large_xi": 0.95}[case]
-    exact, fast = _k3_pair(cuda, x, y, D, r, xi, seed)
+    exact, fast = _exact_and_bounded(cuda, x, y, 3, 1, D, r, xi, seed)
+    for a, b, name in zip(exact, fast, ("ig", "tuples", "disc")):
+        assert np.array_equal(a, b), f"{case}: {name} differs in {np.count_nonzero(a != b)} entries"
+
+
+@pytest.mark.parametrize("case", ["parity_full", "xor_pairs", "unbalanced", "small_xi", "large_xi", "batched_size"])
+def test_k2_bound_changes_no_result(cuda, case):
+    """k = 2 with three classes per variable: the scan that skips pairs by the
+    SH2 lower bound returns the IG, partners and discretisations of the scan
+    that evaluates every pair exactly, bit for bit, for every variable.
+    Covers the 2000 x 500 parity data with 30 discretisations, strong pair
+    signals, unbalanced classes, small and large pseudocounts and one job of
+    the batched workload's size (1000 x 20000, 10 discretisations)."""
+    rng = np.random.default_rng(hash(case) % 2**32)
+    D, r, xi, seed = 4, 0.5, 0.25, 21
+    if case == "parity_full":
+        ds = synth.madelon_like()
+        x, y, D, seed = ds.x, ds.y, 30, 11
+    elif case == "xor_pairs":
+        ds = synth.xor_pairs(N=1500, M=300, n_pairs=10, flip=0.1, seed=3)
+        x, y = ds.x, ds.y
+    elif case == "batched_size":
+        ds = synth.xor_pairs(N=1000, M=20000, n_pairs=100, seed=4)
+        x, y, D = ds.x, ds.y, 10
+    else:
+        M, N = 260, 900
+        x = rng.standard_normal((M, N)).astype(np.float32)
+        y = ((x[3] > 0) ^ (x[100] > 0) ^ (rng.random(N) < 0.1)).astype(np.uint8)
+        if case == "unbalanced":
+            y = (rng.random(N) < 0.12).astype(np.uint8) | ((x[5] > 1.2) & (x[7] > 1.0)).astype(np.uint8)
+        xi = {"unbalanced": 0.25, "small_xi": 0.002, "large_xi": 0.95}[case]
+    exact, fast = _exact_and_bounded(cuda, x, y, 2, 2, D, r, xi, seed)
     for a, b, name in zip(exact, fast, ("ig", "tuples", "disc")):
         assert np.array_equal(a, b), f"{case}: {name} differs in {np.count_nonzero(a != b)} entries"
