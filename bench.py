@@ -18,8 +18,11 @@ and compared with the FP64 oracle on sampled variables.
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload (the method has no other reference implementation here).
 
-Multi-GPU (torchrun): every rank runs its own independent job (weak scaling,
-no data-path collective); value = all ranks' evaluations / max rank time.
+Multi-GPU (torchrun): one job's tuple tiles are split over the ranks
+(mdfs_max_ig_shard) and the packed max keys merged by one NCCL all-reduce
+(MAX) of 8 M bytes: strong scaling, value = the job's evaluations / max rank
+time.  ``--independent`` runs an independent job per rank instead (weak
+scaling, no collective).  ``--shard`` takes the sharded path on one GPU too.
 """
 from __future__ import annotations
 
@@ -194,23 +197,40 @@ def run_gpu(args, rank, world, local_rank):
 
     from paper_1811_00631_gb300 import build, mdfs, synth
 
+    from paper_1811_00631_gb300 import shard as shard_mod
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    ds = synth.madelon_like(M=max(M_VAR, 20), seed=2 + rank)  # an independent job per rank
+    # sharded: every rank scans its share of one job's tuple tiles and the keys
+    # are merged by one all-reduce (MAX) of 8 M bytes; independent: one job per rank
+    sharded = args.shard or (world > 1 and not args.independent)
+    ds = synth.madelon_like(M=max(M_VAR, 20), seed=2 if sharded else 2 + rank)
     x = torch.from_numpy(ds.x).to(dev)
     y = torch.from_numpy(ds.y).to(dev)
     M = M_VAR
     outs = {k: (torch.empty(M, dtype=torch.float32, device=dev), torch.empty((M, max(k - 1, 1)), dtype=torch.int32,
                                                                               device=dev),
                 torch.empty(M, dtype=torch.int32, device=dev)) for k in (2, 3)}
+    keys_t = {k: torch.empty(M, dtype=torch.int64, device=dev) for k in (2, 3)}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     launches = [0]
 
+    def scan(xx, yy, k, seed, out):
+        if sharded:
+            mdfs.max_ig_shard(xx, yy, k, DIV, DISC, RANGE, XI, seed, shard=rank, n_shards=world, keys_out=keys_t[k])
+            n = mdfs.last_launch_count()
+            if world > 1:
+                shard_mod.allreduce_max_device(keys_t[k])
+            res = mdfs.decode_keys(keys_t[k], k, out=out if out is not None and hasattr(out[0], "is_cuda") else None)
+            launches[0] += n + mdfs.last_launch_count()
+            return res
+        res = mdfs.max_ig(xx, yy, k, DIV, DISC, RANGE, XI, seed, out=out)
+        launches[0] += mdfs.last_launch_count()
+        return res
+
     def step(seed):
         for k in (2, 3):
-            mdfs.max_ig(x, y, k, DIV, DISC, RANGE, XI, seed, out=outs[k])
-            launches[0] += mdfs.last_launch_count()
+            scan(x, y, k, seed, outs[k])
 
     for w in range(args.warmup):
         step(100 + w)
@@ -246,7 +266,8 @@ def run_gpu(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
     UNITS = _units()
-    value = world * UNITS * args.steps / total_s
+    jobs = 1 if sharded else world  # one job split over the ranks, or one per rank
+    value = jobs * UNITS * args.steps / total_s
 
     # ---- end to end through the C ABI with pinned host buffers ----
     x_h = torch.empty(ds.x.shape, dtype=torch.float32, pin_memory=True)
@@ -255,15 +276,23 @@ def run_gpu(args, rank, world, local_rank):
     y_h.copy_(torch.from_numpy(ds.y))
     host_out = {k: (np.empty(M, np.float32), np.empty((M, max(k - 1, 1)), np.int32), np.empty(M, np.int32))
                 for k in (2, 3)}
+    def e2e_scan(k, seed):
+        if sharded:  # host inputs in, merged keys decoded, results read back to the host
+            res = scan(x_h, y_h, k, seed, None)
+            for dst, src in zip(host_out[k], res):
+                dst.reshape(-1)[:] = src.reshape(-1).cpu().numpy()
+        else:
+            mdfs.max_ig(x_h, y_h, k, DIV, DISC, RANGE, XI, seed, out=host_out[k])
+
     for k in (2, 3):
-        mdfs.max_ig(x_h, y_h, k, DIV, DISC, RANGE, XI, 99, out=host_out[k])
+        e2e_scan(k, 99)
     e2e_t = []
     for i in range(args.steps):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in (2, 3):
-            mdfs.max_ig(x_h, y_h, k, DIV, DISC, RANGE, XI, 1 + i, out=host_out[k])
+            e2e_scan(k, 1 + i)
         e2e_t.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_t)
     if world > 1:
@@ -309,14 +338,15 @@ def run_gpu(args, rank, world, local_rank):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 one-hot MMA (f32 exact counts) + int32/int64 fixed-point entropy",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "e4m3 one-hot MMA (f32 exact counts) + int32/int64 fixed-point entropy",
             "data": "synthetic",
-            "config": _config({"parallelism": f"independent job per GPU x{world}"}),
+            "config": _config({"parallelism": (f"one job's tuple tiles split over {world} GPUs, keys merged by "
+                                               f"all-reduce MAX" if sharded else f"independent job per GPU x{world}")}),
             "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
             "wall_s_timed_region": wall,
             "gpu_launches": launches[0],
             "clocks": clk,
-            "e2e": {"value": world * UNITS * args.steps / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": jobs * UNITS * args.steps / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "kernels": shares}
@@ -699,6 +729,10 @@ def main():
     ap.add_argument("--k5-disc", type=int, default=1, help="discretisations of the timed k = 5 scan")
     ap.add_argument("--select-reps", type=int, default=3,
                     help="timed calls of the selection pipeline per k (0: skip)")
+    ap.add_argument("--shard", action="store_true",
+                    help="split one job's tuple space over the ranks (the default with more than one GPU)")
+    ap.add_argument("--independent", action="store_true",
+                    help="with more than one GPU, run an independent job per rank instead (weak scaling)")
     ap.add_argument("--no-peaks", action="store_true", help="skip the tensor-core and shared-memory microbenchmarks")
     ap.add_argument("--configs", type=int, default=1, help="time the other configurations with oracle checks (0: skip)")
     ap.add_argument("--batch-configs", type=int, default=1,

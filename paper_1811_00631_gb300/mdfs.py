@@ -319,26 +319,56 @@ def max_ig_batch(x, y, sample_idx=None, y_perm=None, n_jobs=None, k: int = 2, di
 
 
 def max_ig_shard(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range_: float = 0.0,
-                 pc_xi: float = 0.25, seed: int = 0, shard: int = 0, n_shards: int = 1) -> np.ndarray:
-    """Packed max keys (uint64 [M], host) of shard `shard` of `n_shards` of the scan."""
+                 pc_xi: float = 0.25, seed: int = 0, shard: int = 0, n_shards: int = 1, keys_out=None):
+    """Packed max keys [M] of shard `shard` of `n_shards` of the scan: a uint64
+    numpy array, or, with keys_out (a CUDA int64 tensor of M entries on the
+    device of x), the raw uint64 bits written into that tensor on the
+    current stream."""
     lib = load()
     data, keep = _data(x, y)
-    keys = np.zeros(data.M, dtype=np.uint64)
     stream = _stream_of(x) if _is_cuda(x) else None
+    if keys_out is not None:
+        import torch
+        if not (_is_cuda(keys_out) and keys_out.dtype == torch.int64 and keys_out.is_contiguous()
+                and tuple(keys_out.shape) == (data.M,)):
+            raise ValueError(f"keys_out: expected a contiguous CUDA int64 tensor of shape ({data.M},)")
+        ptr = keys_out.data_ptr()
+        keys = keys_out
+    else:
+        keys = np.zeros(data.M, dtype=np.uint64)
+        ptr = keys.ctypes.data
     rc = lib.mdfs_max_ig_shard(ctypes.byref(data), k, divisions, discretizations, float(range_), float(pc_xi),
-                               int(seed) & (2**64 - 1), shard, n_shards, ctypes.c_void_p(keys.ctypes.data), stream)
+                               int(seed) & (2**64 - 1), shard, n_shards, ctypes.c_void_p(ptr), stream)
     _check(rc)
     del keep
     return keys
 
 
-def decode_keys(keys: np.ndarray, k: int):
-    """(ig, tuples, disc) numpy arrays of merged keys, as max_ig returns them."""
+def decode_keys(keys, k: int, out=None):
+    """(ig, tuples, disc) of merged keys, as max_ig returns them: numpy arrays
+    for numpy keys; for keys in a CUDA int64 tensor (raw uint64 bits), CUDA
+    tensors on its device (or the preallocated `out` of max_ig's kind)."""
     lib = load()
+    kk = max(k - 1, 1)
+    if _is_cuda(keys):
+        import torch
+        M = int(keys.shape[0])
+        if out is None:
+            ig = torch.empty(M, dtype=torch.float32, device=keys.device)
+            tu = torch.empty((M, kk), dtype=torch.int32, device=keys.device)
+            di = torch.empty(M, dtype=torch.int32, device=keys.device)
+        else:
+            ig, tu, di = out
+            _check_out(out, ((M,), (M, kk), (M,)), (np.float32, np.int32, np.int32), keys)
+        rc = lib.mdfs_keys_decode(ctypes.c_void_p(keys.data_ptr()), M, k, ctypes.c_void_p(ig.data_ptr()),
+                                  ctypes.c_void_p(tu.data_ptr()) if k > 1 else None, ctypes.c_void_p(di.data_ptr()),
+                                  _stream_of(keys))
+        _check(rc)
+        return ig, tu[:, : k - 1], di
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     M = len(keys)
     ig = np.empty(M, np.float32)
-    tu = np.empty((M, max(k - 1, 1)), np.int32)
+    tu = np.empty((M, kk), np.int32)
     di = np.empty(M, np.int32)
     rc = lib.mdfs_keys_decode(ctypes.c_void_p(keys.ctypes.data), M, k, ctypes.c_void_p(ig.ctypes.data),
                               ctypes.c_void_p(tu.ctypes.data) if k > 1 else None, ctypes.c_void_p(di.ctypes.data),

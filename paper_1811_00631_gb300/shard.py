@@ -41,6 +41,19 @@ def allreduce_max(keys_u64: np.ndarray, group=None) -> np.ndarray:
     return from_signed_order(t.numpy())
 
 
+def allreduce_max_device(keys_t, group=None):
+    """In-place all-reduce MAX of uint64 keys held as raw bits in a CUDA int64
+    tensor (any backend that reduces CUDA tensors, e.g. NCCL): bit 63 is
+    flipped before and after so that signed order is unsigned order."""
+    import torch
+    import torch.distributed as dist
+    flip = torch.iinfo(torch.int64).min  # -2^63: only bit 63 set
+    keys_t.bitwise_xor_(flip)
+    dist.all_reduce(keys_t, op=dist.ReduceOp.MAX, group=group)
+    keys_t.bitwise_xor_(flip)
+    return keys_t
+
+
 # --- key format (mirrors the device packing; used to build test candidates) ---
 def pack(ig: np.ndarray, index: np.ndarray) -> np.ndarray:
     """Keys of float32 IG values and uint32 tie-break indices."""

@@ -77,8 +77,14 @@ def _rank_main(rank, world, port, out_path):
     M = 37
     var, ig, idx = _candidates(2, M)
     mine = np.arange(len(var))[rank::world]  # disjoint shares of the tuple space
-    merged = shard.allreduce_max(_keys_of(var[mine], ig[mine], idx[mine], M))
+    mine_keys = _keys_of(var[mine], ig[mine], idx[mine], M)
+    merged = shard.allreduce_max(mine_keys)
     np.save(out_path + f".{rank}.npy", merged)
+    # the in-place tensor form the benchmark uses with NCCL on CUDA tensors
+    import torch
+    t = torch.from_numpy(mine_keys.view(np.int64).copy())
+    shard.allreduce_max_device(t)
+    np.save(out_path + f".t{rank}.npy", t.numpy().view(np.uint64))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -92,6 +98,8 @@ def test_gloo_allreduce_merge(tmp_path):
     k0 = np.load(out + ".0.npy")
     k1 = np.load(out + ".1.npy")
     assert np.array_equal(k0, k1)
+    for r in (0, 1):
+        assert np.array_equal(np.load(out + f".t{r}.npy"), k0)
     M = 37
     var, ig, idx = _candidates(2, M)
     ref = _reference(var, ig, idx, M)
