@@ -7,6 +7,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <initializer_list>
 #include <map>
@@ -51,6 +52,7 @@ struct Workspace {
     Buffer pairs2, items2, onehot, err;
     Buffer bx, by, bidx, bperm;  // batch: gathered job data and the job index maps
     Buffer items3;               // k = 2 tensor-core tile list
+    Buffer bcounts, bonehot, btab, bcnt1, bsh1, bkeys;  // batch: class sizes; a chunk's operands and tables
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
     Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
     Buffer items4;                                           // k = 4 work items
@@ -74,7 +76,8 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv};
+                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
+                         &bcounts, &bonehot, &btab, &bcnt1, &bsh1, &bkeys};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -415,11 +418,119 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
 // keys of the unsharded scan.
 // emit != NULL: interesting-tuple emission into that table; the scan then runs on
 // the popcount kernels (the tensor-core kernels do not emit).
+// ---- launch-parameter tuner -------------------------------------------------
+// The tunable launch parameter of the k = 2 tensor-core kernel (its pipeline
+// stages, which also set how many batch jobs one launch can hold) is chosen per
+// shape by timing the candidates on the first call that needs it.  Each
+// candidate runs the real scan: the max keys are idempotent, so running it
+// more than once leaves the same result.  The choice is kept in memory and,
+// when the environment variable MDFS_TUNE_FILE names a file, appended there as
+// "<kernel> M=.. N=.. c=.. D=.. -> <choice>" lines that later processes read
+// back.  MDFS_TUNE=0 skips the measurement (4 stages).
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const char* kernel, int M, int N, int c, int D) {
+    char b[128];
+    snprintf(b, sizeof b, "%s M=%d N=%d c=%d D=%d", kernel, M, N, c, D);
+    return b;
+}
+
+int tune_get(const std::string& key) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (!g_tune_loaded) {
+        g_tune_loaded = true;
+        if (const char* f = getenv("MDFS_TUNE_FILE")) {
+            if (FILE* fp = fopen(f, "r")) {
+                char line[256];
+                while (fgets(line, sizeof line, fp)) {
+                    char* arrow = strstr(line, " -> ");
+                    if (!arrow) continue;
+                    *arrow = 0;
+                    const int v = atoi(arrow + 4);
+                    if (v > 0) g_tune[line] = v;
+                }
+                fclose(fp);
+            }
+        }
+    }
+    auto it = g_tune.find(key);
+    return it == g_tune.end() ? 0 : it->second;
+}
+
+void tune_put(const std::string& key, int v) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = v;
+    if (const char* f = getenv("MDFS_TUNE_FILE")) {
+        if (FILE* fp = fopen(f, "a")) {
+            fprintf(fp, "%s -> %d\n", key.c_str(), v);
+            fclose(fp);
+        }
+    }
+}
+
+// The tuned stage count of the k = 2 tensor-core launch of `jobs` (0 on a CUDA
+// error); `kernel` names the cache entry (single scans and batches apart).
+int tuned_k2_stages(Workspace* ws, const char* kernel, const K2Jobs& jobs, int M, int c, int D, const int2* items,
+                    int n_items, const CUtensorMap& map, int fbits, bool bound) {
+    const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1;
+    const std::string key = tune_key(kernel, M, N, c, D);
+    if (const int v = tune_get(key)) return v;
+    const char* en = getenv("MDFS_TUNE");
+    if (en && en[0] == '0') return 4;
+    cudaStream_t st = ws->stream;
+    // a stream being captured into a graph cannot be timed: untuned default
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return 4;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return 0;
+    }
+    // each candidate twice, alternating, best time of each (the first launch
+    // also warms the caches); the keys are maxima, so the repeats leave them as
+    // one launch would
+    float best_ms[5] = {0, 0, 0, 0, 0};
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+        for (const int stages : {4, 3}) {
+            if (k2tc_smem_bytes(N, jobs.n, stages) > kK3tcMaxSmem) continue;
+            float ms = 0.0f;
+            if (cudaEventRecord(e0, st) != cudaSuccess ||
+                launch_k2tc(map, jobs, M, c, 0, D, D, items, n_items, fbits, (int*)ws->err.p, bound, stages, st) !=
+                    cudaSuccess ||
+                cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaGetLastError();
+                ok = false;
+                break;
+            }
+            if (best_ms[stages] == 0.0f || ms < best_ms[stages]) best_ms[stages] = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) return 0;
+    int best = 0;
+    for (const int stages : {4, 3})
+        if (best_ms[stages] > 0.0f && (!best || best_ms[stages] < best_ms[best])) best = stages;
+    if (best) tune_put(key, best);
+    return best;
+}
+
 // dump != NULL (test hook, mdfs_testing_counts): the tensor-core kernel also
 // writes its class counts there; the call fails if that kernel does not apply.
+// keep_err: leave the tensor-core error flag as it is (a batch clears it once
+// and reads it after its last job).
 int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, int k, int divisions, int D, double range,
               double pc_xi, uint64_t seed, bool* check_err, int shard = 0, int n_shards = 1,
-              const EmitTable* emit = nullptr, uint32_t* dump = nullptr) {
+              const EmitTable* emit = nullptr, uint32_t* dump = nullptr, bool keep_err = false) {
     cudaStream_t st = ws->stream;
     auto share = [&](int n, int* lo) {
         *lo = (int)((long long)n * shard / n_shards);
@@ -455,7 +566,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
     const EmitTable em = emit ? *emit : EmitTable();
-    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
+    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_smem_bytes(N, 1, 4) <= kK3tcMaxSmem);
     const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     TcGeom tg = make_tc_geom(n0, n1);
     if (dump && !use_tc2 && !use_tc3)
@@ -472,7 +583,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                                     k == 1 ? em : EmitTable()));
     if (use_tc2) {
         MDFS_ENSURE(ws, err, sizeof(int));
-        MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
+        if (!keep_err) MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
         if (ws->items3_M != M || ws->items3_c != c) {
             std::vector<int2> items;
             build_k2tc_items(M, c, items);
@@ -489,9 +600,15 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         int lo = 0;
         const int cnt = share(ws->n_items3, &lo);
         const bool exact = take_test_hooks(false).exact;
-        MDFS_LAUNCH("k2", st, launch_k2tc(map, tg, M, c, 0, D, (const int2*)ws->items3.p + lo, cnt, tab,
-                                          k3tc_fraction_bits(N), cnt1, sh1, keys, (int*)ws->err.p, b0, b1,
-                                          !exact, st, dump));
+        K2Jobs jobs{};
+        jobs.n = 1;
+        jobs.job[0] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};
+        const int stages = dump ? 4
+                                : tuned_k2_stages(ws, "k2tc_stages", jobs, M, c, D, (const int2*)ws->items3.p + lo,
+                                                  cnt, map, k3tc_fraction_bits(N), !exact);
+        if (stages <= 0) return fail(MDFS_ECUDA, "k = 2 stage tuning failed (CUDA error)");
+        MDFS_LAUNCH("k2", st, launch_k2tc(map, jobs, M, c, 0, D, D, (const int2*)ws->items3.p + lo, cnt,
+                                          k3tc_fraction_bits(N), (int*)ws->err.p, !exact, stages, st, dump));
         *check_err = true;
     } else if (k == 2) {
         if (shard == 0)
@@ -508,7 +625,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         if (nd > D) nd = D;
         MDFS_ENSURE(ws, pairs2, (size_t)nd * per_disc);
         MDFS_ENSURE(ws, err, sizeof(int));
-        MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
+        if (!keep_err) MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
         if (ws->items2_M != M) {
             std::vector<int2> items;
             build_k3tc_items(M, items);
@@ -899,11 +1016,10 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     g_launches = 0;
     int rc = check_data(data, true);
     if (rc) return rc;
-    const int N = data->N, M = data->M, D = discretizations;
+    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1, P = c - 1;
     if (n_jobs < 1) return fail(MDFS_EINVAL, "n_jobs = %d < 1", n_jobs);
     if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi))) return rc;
     if (!ig) return fail(MDFS_EINVAL, "ig is NULL");
-
     if ((rc = check_devices({{data->x, "x"}, {data->y, "y"}, {sample_idx, "sample_idx"}, {y_perm, "y_perm"}, {ig, "ig"}, {tuples, "tuples"}, {best_disc, "best_disc"}}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Workspace* ws = get_ws(st, &rc);
@@ -927,6 +1043,18 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
         MDFS_CUDA_TRY(cudaMemcpyAsync(ws->bperm.p, y_perm, nidx, cudaMemcpyHostToDevice, st));
         permd = (const int32_t*)ws->bperm.p;
     }
+    // the class sizes of every job in one device pass and one read back: no
+    // job waits for the host after this
+    MDFS_ENSURE(ws, bcounts, (size_t)n_jobs * sizeof(int2));
+    MDFS_LAUNCH("batch_counts", st, launch_batch_counts(yd, N, idxd, permd, n_jobs, (int2*)ws->bcounts.p, st));
+    std::vector<int2> counts((size_t)n_jobs);
+    MDFS_CUDA_TRY(cudaMemcpyAsync(counts.data(), ws->bcounts.p, (size_t)n_jobs * sizeof(int2), cudaMemcpyDeviceToHost,
+                                  st));
+    MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < n_jobs; ++j) {
+        if (counts[j].y) return fail(MDFS_EINVAL, "job %d: sample or permutation index outside [0, N)", j);
+        if (counts[j].x == 0 || counts[j].x == N) return fail(MDFS_EDEGENERATE, "job %d: decision has a single class", j);
+    }
     const size_t xbytes = (size_t)M * N * (data->dtype == MDFS_F32 ? 4 : 1);
     MDFS_ENSURE(ws, bx, xbytes);
     MDFS_ENSURE(ws, by, (size_t)N);
@@ -939,34 +1067,117 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     if (rc) return rc;
     rc = bind_out(ws, ws->disc, best_disc, (size_t)n_jobs * M, &odi);
     if (rc) return rc;
+    MDFS_ENSURE(ws, err, sizeof(int));
+    MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
     int* stats = (int*)ws->stats.p;
-    for (int j = 0; j < n_jobs; ++j) {
-        MDFS_CUDA_TRY(cudaMemsetAsync(stats, 0, 16 * sizeof(int), st));
-        MDFS_LAUNCH("gather", st, launch_gather_job(xd, data->dtype, yd, N, M, idxd ? idxd + (size_t)j * N : nullptr,
-                                                    permd ? permd + (size_t)j * N : nullptr, ws->bx.p,
-                                                    (uint8_t*)ws->by.p, stats + 3, st));
-        MDFS_LAUNCH("stats", st, launch_stats((const uint8_t*)ws->by.p, N, stats, (int*)ws->perm.p, st));
-        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats, stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
-        if (ws->host_stats[3] != 0) return fail(MDFS_EINVAL, "job %d: sample or permutation index outside [0, N)", j);
-        const int n1 = ws->host_stats[0];
-        if (n1 == 0 || n1 == N) return fail(MDFS_EDEGENERATE, "job %d: decision has a single class", j);
-        bool check_err = false;
-        rc = scan_core(ws, ws->bx.p, data->dtype, N, M, n1, k, divisions, D, range, pc_xi, seed, &check_err);
-        if (rc) return rc;
-        MDFS_LAUNCH("finalize", st,
-                    launch_finalize((const unsigned long long*)ws->keys.p, M, k, oig.dev + (size_t)j * M,
-                                    otu.dev ? otu.dev + (size_t)j * M * kk : nullptr,
-                                    odi.dev ? odi.dev + (size_t)j * M : nullptr, st, wide_disc(ws)));
-        if (check_err) {
-            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-            MDFS_CUDA_TRY(cudaStreamSynchronize(st));
-            const int flag = ws->host_stats[8];
-            if (flag) return kernel_flag_error(flag, j);
+    bool check_err = false;
+    // k = 2 on the tensor cores: chunks of jobs share one launch over (job,
+    // discretisation, tile) work items
+    if (k == 2 && k2tc_supported(c) && k2tc_smem_bytes(N, 1, 4) <= kK3tcMaxSmem) {
+        int Kp_max = 0, Ws_max = 0;
+        for (int j = 0; j < n_jobs; ++j) {
+            Kp_max = std::max(Kp_max, make_tc_geom(N - counts[j].x, counts[j].x).Kp);
+            Ws_max = std::max(Ws_max, make_geom(N, N - counts[j].x).Ws);
+        }
+        // jobs per launch: what the entropy tables in shared memory allow, and a
+        // device-memory budget for the chunk's one-hot operands
+        size_t budget = (size_t)8 << 30;
+        if (const char* env = getenv("MDFS_BATCH_BYTES")) budget = (size_t)strtoull(env, nullptr, 10);
+        const size_t op_bytes = (size_t)D * M * P * Kp_max;
+        const int by_mem = (int)std::max<size_t>(1, budget / std::max<size_t>(op_bytes, 1));
+        int stages = tune_get(tune_key("k2tc_batch_stages", M, N, c, D));
+        const int chunk_cap = std::min({n_jobs, by_mem, std::max(1, k2tc_max_jobs(N, stages ? stages : 4,
+                                                                                  kK3tcMaxSmem))});
+        const size_t np1 = (size_t)N + 1;
+        MDFS_ENSURE(ws, bonehot, (size_t)chunk_cap * op_bytes);
+        MDFS_ENSURE(ws, btab, (size_t)chunk_cap * 3 * np1 * sizeof(long long));
+        MDFS_ENSURE(ws, bcnt1, (size_t)chunk_cap * D * M * P * 2 * sizeof(int));
+        MDFS_ENSURE(ws, bsh1, (size_t)chunk_cap * D * M * sizeof(long long));
+        MDFS_ENSURE(ws, bkeys, (size_t)chunk_cap * M * sizeof(unsigned long long));
+        MDFS_ENSURE(ws, planes, (size_t)D * M * P * Ws_max * sizeof(uint32_t));
+        MDFS_ENSURE(ws, perm, (size_t)N * sizeof(int));
+        if (ws->items3_M != M || ws->items3_c != c) {
+            std::vector<int2> items;
+            build_k2tc_items(M, c, items);
+            MDFS_ENSURE(ws, items3, items.size() * sizeof(int2));
+            MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items3.p, items.data(), items.size() * sizeof(int2),
+                                          cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->items3_M = M;
+            ws->items3_c = c;
+            ws->n_items3 = (int)items.size();
+        }
+        const int fbits = k3tc_fraction_bits(N);
+        for (int j0 = 0; j0 < n_jobs; j0 += chunk_cap) {
+            const int nj = std::min(chunk_cap, n_jobs - j0);
+            K2Jobs jobs{};
+            jobs.n = nj;
+            for (int jj = 0; jj < nj; ++jj) {
+                const int j = j0 + jj, n1 = counts[j].x, n0 = N - n1;
+                const double mn = (double)(n0 < n1 ? n0 : n1);
+                const double b0 = pc_xi * n0 / mn, b1 = pc_xi * n1 / mn;
+                MDFS_LAUNCH("gather", st, launch_gather_job(xd, data->dtype, yd, N, M, idxd ? idxd + (size_t)j * N : nullptr,
+                                                            permd ? permd + (size_t)j * N : nullptr, ws->bx.p,
+                                                            (uint8_t*)ws->by.p, stats + 3, st));
+                MDFS_LAUNCH("stats", st, launch_stats((const uint8_t*)ws->by.p, N, stats, (int*)ws->perm.p, st));
+                long long* tab = (long long*)ws->btab.p + (size_t)jj * 3 * np1;
+                int* cnt1 = (int*)ws->bcnt1.p + (size_t)jj * D * M * P * 2;
+                long long* sh1 = (long long*)ws->bsh1.p + (size_t)jj * D * M;
+                unsigned long long* keys = (unsigned long long*)ws->bkeys.p + (size_t)jj * M;
+                uint8_t* onehot = (uint8_t*)ws->bonehot.p + (size_t)jj * op_bytes;
+                const TcGeom tg = make_tc_geom(n0, n1);
+                TcGeom tgd = tg;  // the discretiser writes rows of the chunk's common length
+                tgd.Kp = Kp_max;
+                const PlaneGeom g = make_geom(N, n0);
+                MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
+                MDFS_LAUNCH("discretize", st, launch_discretize(ws->bx.p, data->dtype, N, M, c, D, range, seed,
+                                                                (const int*)ws->perm.p, g, (uint32_t*)ws->planes.p,
+                                                                nullptr, nullptr, onehot, tgd, st));
+                MDFS_LAUNCH("k1", st, launch_k1((const uint32_t*)ws->planes.p, g, M, c, D, tab, cnt1, sh1, nullptr, st));
+                MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
+                jobs.job[jj] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};
+            }
+            CUtensorMap map;
+            MDFS_CUDA_TRY(make_onehot_map(&map, (const uint8_t*)ws->bonehot.p, M * P, nj * D, Kp_max));
+            if (!stages) {
+                stages = tuned_k2_stages(ws, "k2tc_batch_stages", jobs, M, c, D, (const int2*)ws->items3.p,
+                                         ws->n_items3, map, fbits, true);
+                if (stages <= 0) return fail(MDFS_ECUDA, "k = 2 stage tuning failed (CUDA error)");
+                if (k2tc_smem_bytes(N, nj, stages) > kK3tcMaxSmem) stages = 4;
+            }
+            MDFS_LAUNCH("k2", st, launch_k2tc(map, jobs, M, c, 0, D, D, (const int2*)ws->items3.p, ws->n_items3, fbits,
+                                              (int*)ws->err.p, true, stages, st));
+            for (int jj = 0; jj < nj; ++jj) {
+                const int j = j0 + jj;
+                MDFS_LAUNCH("finalize", st,
+                            launch_finalize((const unsigned long long*)ws->bkeys.p + (size_t)jj * M, M, k,
+                                            oig.dev + (size_t)j * M, otu.dev ? otu.dev + (size_t)j * M * kk : nullptr,
+                                            odi.dev ? odi.dev + (size_t)j * M : nullptr, st));
+            }
+        }
+        check_err = true;
+    } else {
+        for (int j = 0; j < n_jobs; ++j) {
+            MDFS_LAUNCH("gather", st, launch_gather_job(xd, data->dtype, yd, N, M, idxd ? idxd + (size_t)j * N : nullptr,
+                                                        permd ? permd + (size_t)j * N : nullptr, ws->bx.p,
+                                                        (uint8_t*)ws->by.p, stats + 3, st));
+            MDFS_LAUNCH("stats", st, launch_stats((const uint8_t*)ws->by.p, N, stats, (int*)ws->perm.p, st));
+            bool job_err = false;
+            rc = scan_core(ws, ws->bx.p, data->dtype, N, M, counts[j].x, k, divisions, D, range, pc_xi, seed, &job_err,
+                           0, 1, nullptr, nullptr, true);
+            if (rc) return rc;
+            check_err |= job_err;
+            MDFS_LAUNCH("finalize", st,
+                        launch_finalize((const unsigned long long*)ws->keys.p, M, k, oig.dev + (size_t)j * M,
+                                        otu.dev ? otu.dev + (size_t)j * M * kk : nullptr,
+                                        odi.dev ? odi.dev + (size_t)j * M : nullptr, st, wide_disc(ws)));
         }
     }
     if ((rc = copy_back(ws, oig)) || (rc = copy_back(ws, otu)) || (rc = copy_back(ws, odi))) return rc;
+    if (check_err)
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (check_err && ws->host_stats[8]) return kernel_flag_error(ws->host_stats[8]);
     return MDFS_OK;
 }
 

@@ -78,6 +78,12 @@ cudaError_t launch_check_finite(const float* x, long long count, int* flag, cuda
 cudaError_t launch_gather_job(const void* x, int dtype, const uint8_t* y, int N, int M, const int* idx,
                               const int* yperm, void* xo, uint8_t* yo, int* flag, cudaStream_t st);
 
+// Class sizes of every batch job: out[j] = (n1, bad) with n1 the number of
+// y[yperm_j[idx_j[t]]] != 0 and bad != 0 when an index lies outside [0, N) or a
+// label outside {0, 1} (idx, yperm [n_jobs][N] or NULL = identity).
+cudaError_t launch_batch_counts(const uint8_t* y, int N, const int* idx, const int* yperm, int n_jobs, int2* out,
+                                cudaStream_t st);
+
 // int64 fixed-point tables T0[n] = f(n + b0), T1[n] = f(n + b1), TB[n] = f(n + b0 + b1),
 // n = 0..N, f(t) = t ln t; laid out as [3][N + 1].
 cudaError_t launch_ftable(int N, double b0, double b1, long long* tab, cudaStream_t st);
@@ -214,19 +220,36 @@ cudaError_t launch_k3tc_operand(const uint8_t* src, uint8_t* dst, const int* per
                                 cudaStream_t st);
 
 // k = 2 on the tensor cores for c = 2, 3: one-hot rows M (c-1) through TMA
-// (map over [D][M (c-1)][Kp]), symmetric tiles (it <= mt) from build_k2tc_items.
+// (map over [jobs x D][M (c-1)][Kp]), symmetric tiles (it <= mt) from
+// build_k2tc_items.  One launch scans up to kMaxK2Jobs jobs of the same N (the
+// resamples of a batch): work items (job, discretisation, tile), every job's
+// entropy tables in shared memory at once.
+constexpr int kMaxK2Jobs = 16;
+struct K2Job {
+    TcGeom tg;                  // class sizes and K geometry of the job
+    const long long* tab;       // int64 entropy tables [3][N + 1]
+    const int* cnt1;            // [D][M][c-1][2] bin class counts
+    const long long* sh1;       // [D][M] SH1
+    unsigned long long* keys;   // [M] max keys of the job
+    float b0, b1;               // pseudocounts of the two decision classes (the SH2 bound)
+};
+struct K2Jobs {
+    int n;
+    K2Job job[kMaxK2Jobs];
+};
 bool k2tc_supported(int c);
 void build_k2tc_items(int M, int c, std::vector<int2>& items);
-size_t k2tc_smem_bytes(int N0, int N1);
-// dump != NULL (test hook): also writes the c x c class counts of every pair
-// i < m, [D][C(M,2)][c c] uint32 n0 | n1 << 16 at the pair's rank in the upper
-// triangle, voxel code_i c + code_m.
-// b0, b1: the pseudocounts of the two decision classes; with bound (and three
-// classes per variable) they enter a lower bound of SH2 that lets the epilogue
-// skip pairs that cannot change a key.
-cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
-                        int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
-                        unsigned long long* keys, int* err, double b0, double b1, bool bound, cudaStream_t st,
+// dynamic shared memory of a launch with n_jobs jobs of N samples and `stages` pipeline stages
+size_t k2tc_smem_bytes(int N, int n_jobs, int stages);
+// the most jobs of N samples one launch can hold within smem_limit bytes (0: none)
+int k2tc_max_jobs(int N, int stages, size_t smem_limit);
+// bound: with three classes, skip the pairs whose SH2 lower bound rules out
+// both roles.  stages: 3 or 4.  dstride: discretisations per job in the map.
+// dump != NULL (test hook, one job, 4 stages): also writes the c x c class
+// counts of every pair i < m, [D][C(M,2)][c c] uint32 n0 | n1 << 16 at the
+// pair's rank in the upper triangle, voxel code_i c + code_m.
+cudaError_t launch_k2tc(const CUtensorMap& map, const K2Jobs& jobs, int M, int c, int d0, int nd, int dstride,
+                        const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,
                         uint32_t* dump = nullptr);
 
 // Contrast rows M .. M + n_contrast - 1 of x_ext (dtype 0 f32, 1 i8); rows

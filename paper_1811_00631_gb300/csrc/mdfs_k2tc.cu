@@ -30,7 +30,6 @@ namespace {
 
 constexpr int kTile = 128;
 constexpr int kBK = 128;
-constexpr int kStages = 4;
 constexpr uint32_t kTileBytes = kTile * kBK;
 constexpr uint32_t kAccCols = 2 * kTile;
 constexpr uint32_t kTmemCols = 2 * kAccCols;
@@ -40,7 +39,10 @@ constexpr int kColsPerWarp = 32;
 constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
 static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
               "register split must add up to the launch allocation");
-constexpr size_t kTabOffset = 2 * kStages * kTileBytes;
+// the entropy tables follow the S pipeline stages (A and B tiles)
+constexpr size_t tab_offset(int S) { return 2 * (size_t)S * kTileBytes; }
+// int32 entries per job in shared memory: T0 (N0 + 1), T1 (N1 + 1), TB (N + 1), rounded to 16 bytes
+__host__ __device__ constexpr int tab_stride(int N) { return (2 * N + 3 + 3) & ~3; }
 
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 
@@ -69,10 +71,6 @@ __device__ __forceinline__ int tab32(const int* t, int n, int nmax) { return t[m
 // and likewise for m, so a pair with LB above both limits (in units of 4 ln 2
 // nats, with the margins kBoundRel |hi| + kBoundAbs for float rounding) cannot
 // change any result and skips its 27 lookups.
-struct K2Prune {
-    int on;
-    float beta0, beta1;  // pseudocounts of the two decision classes
-};
 constexpr float kBoundRel = 1.0f / 4096.0f, kBoundAbs = 0.05f;
 constexpr float kInv4Ln2 = 0.36067376022224085f;            // 1 / (4 ln 2)
 constexpr float kFx32ToCount = 2.3283064365386963e-10f * kInv4Ln2;  // 2^-32 / (4 ln 2)
@@ -125,20 +123,24 @@ __device__ __forceinline__ void complete2(const V (&X)[P][P], const V (&ni)[P], 
 
 }  // namespace
 
-// kDump: also write the c x c class counts of every pair to `dump` (test hook;
-// the scan itself is unchanged).
-template <int P, bool kDump>
+// Work items of a launch: (job, discretisation, tile) for jobs.n jobs of the
+// same N (a batch's resamples; one job for a plain scan), discretisations
+// d0 .. d0 + nd - 1, and the n_items symmetric tiles; job j's operand rows are
+// at z = j dstride + d of the tensor map.  Every job's entropy tables sit in
+// shared memory at once.  S: pipeline stages.  kDump: also write the c x c
+// class counts of every pair of job 0 to `dump` (test hook; the scan itself is
+// unchanged).
+template <int P, int S, bool kDump>
 __global__ void __launch_bounds__(kThreads, 1)
-    k2tc_kernel(const __grid_constant__ CUtensorMap map_oh, TcGeom tg, int M, int d0, int nd,
-                const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
-                const int* __restrict__ cnt1, const long long* __restrict__ sh1, unsigned long long* __restrict__ keys,
-                int* __restrict__ err, K2Prune prune, uint32_t* __restrict__ dump) {
+    k2tc_kernel(const __grid_constant__ CUtensorMap map_oh, const __grid_constant__ K2Jobs jobs, int M, int d0,
+                int nd, int dstride, const int2* __restrict__ items, int n_items, int fbits, int* __restrict__ err,
+                int prune_on, uint32_t* __restrict__ dump) {
     constexpr int C = P + 1;
     // the bound pays for itself with three classes (27 lookups per pair)
-    const bool use_bound = P == 2 && !kDump && prune.on;
+    const bool use_bound = P == 2 && !kDump && prune_on;
     constexpr int VT = kTile / P;  // variables per tile
     extern __shared__ uint8_t dsmem_raw[];
-    __shared__ uint64_t bar_full[kStages], bar_empty[kStages];
+    __shared__ uint64_t bar_full[S], bar_empty[S];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -146,20 +148,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* base = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
     uint8_t* sA = base;
-    uint8_t* sB = base + kStages * kTileBytes;
-    const int N0 = tg.N0, N1 = tg.N1, N = N0 + N1, np1 = N + 1;
-    int* sT0 = reinterpret_cast<int*>(base + kTabOffset);
-    int* sT1 = sT0 + (N0 + 1);
-    int* sTB = sT1 + (N1 + 1);
+    uint8_t* sB = base + S * kTileBytes;
+    const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1, np1 = N + 1;  // the same N for every job
+    const int tstride = tab_stride(N);
+    int* sTab = reinterpret_cast<int*>(base + tab_offset(S));
     volatile int* abort = &s_abort;
 
     uint32_t dyn_bytes;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
-    const bool fits = (size_t)(base - dsmem_raw) + kTabOffset + (size_t)(2 * N + 3) * sizeof(int) <= dyn_bytes;
+    const bool fits = jobs.n >= 1 && jobs.n <= kMaxK2Jobs &&
+                      (size_t)(base - dsmem_raw) + tab_offset(S) + (size_t)jobs.n * tstride * sizeof(int) <= dyn_bytes;
 
     if (tid == 0) {
         s_abort = (*(volatile int*)err ? 1 : 0) | (fits ? 0 : 2);
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             tc::mbar_init(&bar_full[s], 1);
             tc::mbar_init(&bar_empty[s], 1);
         }
@@ -175,16 +177,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tmem_relinquish();
     }
     if (fits) {
-        for (int i = tid; i <= N0; i += kThreads) sT0[i] = fx_narrow(tab[i], fbits);
-        for (int i = tid; i <= N1; i += kThreads) sT1[i] = fx_narrow(tab[np1 + i], fbits);
-        for (int i = tid; i <= N; i += kThreads) sTB[i] = fx_narrow(tab[2 * np1 + i], fbits);
+        for (int j = 0; j < jobs.n; ++j) {
+            const long long* tab = jobs.job[j].tab;
+            const int N0j = jobs.job[j].tg.N0, N1j = jobs.job[j].tg.N1;
+            int* t0 = sTab + j * tstride;
+            for (int i = tid; i <= N0j; i += kThreads) t0[i] = fx_narrow(tab[i], fbits);
+            for (int i = tid; i <= N1j; i += kThreads) t0[N0j + 1 + i] = fx_narrow(tab[np1 + i], fbits);
+            for (int i = tid; i <= N; i += kThreads) t0[N0j + N1j + 2 + i] = fx_narrow(tab[2 * np1 + i], fbits);
+        }
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const int n_tiles = n_items * nd;
-    const int nkb = tg.nkb;
+    const int per_job = n_items * nd;
+    const int n_tiles = per_job * jobs.n;
 
     if (warp < kEpiWarp0) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsProducer));
@@ -193,28 +200,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0 && !*abort) {
                 uint32_t g = 0;
                 int pend_mask = 0;
-                uint32_t pend_use[kStages] = {};
+                uint32_t pend_use[S] = {};
                 for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
-                    const int2 item = items[t % n_items];
-                    const int d = d0 + t / n_items;
+                    const int job = t / per_job, r = t - job * per_job, dl = r / n_items;
+                    const int2 item = items[r - dl * n_items];
+                    const int z = job * dstride + d0 + dl;
+                    const int nkb = jobs.job[job].tg.nkb;
                     const int r0 = item.x * kTile, c0 = item.y * kTile;
                     bool ok = true;
                     for (int kb = 0; kb < nkb; ++kb, ++g) {
-                        const int s = (int)(g % kStages);
-                        const uint32_t use = g / kStages;
+                        const int s = (int)(g % S);
+                        const uint32_t use = g / S;
                         if (use > 0 && !tc::mbar_wait(&bar_empty[s], (use - 1) & 1, abort)) {
                             ok = false;
                             break;
                         }
                         tc::mbar_arrive_expect_tx(&bar_full[s], 2 * kTileBytes);
-                        tc::tma_load_3d(sA + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, r0, d);
-                        tc::tma_load_3d(sB + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, c0, d);
+                        tc::tma_load_3d(sA + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, r0, z);
+                        tc::tma_load_3d(sB + s * kTileBytes, &map_oh, &bar_full[s], kb * kBK, c0, z);
                         pend_mask |= 1 << s;
                         pend_use[s] = use;
                     }
                     if (!ok) break;
                 }
-                for (int s = 0; s < kStages; ++s)
+                for (int s = 0; s < S; ++s)
                     if (pend_mask & (1 << s)) mbar_drain(&bar_full[s], pend_use[s] & 1);
             }
         } else if (warp == 1) {
@@ -227,13 +236,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
                     const int buf = i & 1;
                     const uint32_t tuse = (uint32_t)(i >> 1);
+                    const TcGeom& tg = jobs.job[t / per_job].tg;
+                    const int nkb = tg.nkb;
                     if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort)) break;
                     tc::tc_fence_after();
                     const uint32_t dbase = tmem + (uint32_t)buf * kAccCols;
                     bool ok = true;
                     for (int kb = 0; kb < nkb; ++kb, ++g) {
-                        const int s = (int)(g % kStages);
-                        const uint32_t use = g / kStages;
+                        const int s = (int)(g % S);
+                        const uint32_t use = g / S;
                         if (!tc::mbar_wait(&bar_full[s], use & 1, abort)) {
                             ok = false;
                             break;
@@ -273,13 +284,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
             const int buf = i & 1;
             const uint32_t tuse = (uint32_t)(i >> 1);
-            const int2 item = items[t % n_items];
-            const int dl = t / n_items, d = d0 + dl;
+            const int job = t / per_job, r = t - job * per_job, dl = r / n_items;
+            const int2 item = items[r - dl * n_items];
+            const int d = d0 + dl;
+            const K2Job& J = jobs.job[job];
+            const int N0 = J.tg.N0, N1 = J.tg.N1;
+            const int* sT0 = sTab + job * tstride;
+            const int* sT1 = sT0 + (N0 + 1);
+            const int* sTB = sT1 + (N1 + 1);
+            unsigned long long* keys = J.keys;
+            const float beta0 = J.b0, beta1 = J.b1;
             const int vi = item.x * VT + row / P;       // row variable
             const int vm0 = item.y * VT + (kColsPerWarp / P) * h;  // first column variable of this warp
             const bool diag = item.x == item.y;
-            const int* c1 = cnt1 + (size_t)d * M * P * 2;
-            const long long* s1 = sh1 + (size_t)d * M;
+            const int* c1 = J.cnt1 + (size_t)d * M * P * 2;
+            const long long* s1 = J.sh1 + (size_t)d * M;
             const bool irow = vi < M;
             // row-variable context (class counts of bins 1..P as exact floats)
             float ni0[P], ni1[P];
@@ -367,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int va = u, vb = u + 5;
                             const float n0 = alpha ? (vb < C * C ? T0v[vb / C][vb % C] : 0.0f) : T0v[va / C][va % C];
                             const float n1 = alpha ? (vb < C * C ? T1v[vb / C][vb % C] : 0.0f) : T1v[va / C][va % C];
-                            const float m0 = n0 + prune.beta0, m1 = n1 + prune.beta1;
+                            const float m0 = n0 + beta0, m1 = n1 + beta1;
                             const bool used = !alpha || vb < C * C;
                             pn[u] = used ? m0 * m1 : 0.0f;  // an unused slot adds 0 / 1
                             ps[u] = used ? m0 + m1 : 1.0f;
@@ -477,21 +496,39 @@ void build_k2tc_items(int M, int c, std::vector<int2>& items) {
         for (int mt = it; mt < nt; ++mt) items.push_back(make_int2(it, mt));
 }
 
-size_t k2tc_smem_bytes(int N0, int N1) {
-    return kTabOffset + (size_t)(2 * (N0 + N1) + 3) * sizeof(int) + 1024;
+size_t k2tc_smem_bytes(int N, int n_jobs, int stages) {
+    return tab_offset(stages) + (size_t)n_jobs * tab_stride(N) * sizeof(int) + 1024;
+}
+
+int k2tc_max_jobs(int N, int stages, size_t smem_limit) {
+    const size_t base = tab_offset(stages) + 1024, per = (size_t)tab_stride(N) * sizeof(int);
+    if (smem_limit < base + per) return 0;
+    return (int)std::min<size_t>((smem_limit - base) / per, (size_t)kMaxK2Jobs);
 }
 
 bool k2tc_supported(int c) { return c == 2 || c == 3; }
 
-cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0, int nd, const int2* items,
-                        int n_items, const long long* tab, int fbits, const int* cnt1, const long long* sh1,
-                        unsigned long long* keys, int* err, double b0, double b1, bool bound, cudaStream_t st,
+cudaError_t launch_k2tc(const CUtensorMap& map, const K2Jobs& jobs, int M, int c, int d0, int nd, int dstride,
+                        const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,
                         uint32_t* dump) {
-    if (n_items == 0) return cudaSuccess;
-    const size_t smem = k2tc_smem_bytes(tg.N0, tg.N1);
-    const void* fn = c == 2 ? (dump ? (const void*)k2tc_kernel<1, true> : (const void*)k2tc_kernel<1, false>)
-                            : (dump ? (const void*)k2tc_kernel<2, true> : (const void*)k2tc_kernel<2, false>);
+    if (n_items == 0 || jobs.n == 0) return cudaSuccess;
     if (c != 2 && c != 3) return cudaErrorInvalidValue;
+    if (jobs.n < 1 || jobs.n > kMaxK2Jobs || (stages != 3 && stages != 4) || (dump && (jobs.n != 1 || stages != 4)))
+        return cudaErrorInvalidValue;
+    const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1;
+    for (int j = 0; j < jobs.n; ++j) {
+        if (jobs.job[j].tg.N0 + jobs.job[j].tg.N1 != N) return cudaErrorInvalidValue;
+        // the bound needs pseudocounts that keep its fraction away from 0 and infinity
+        if (!(jobs.job[j].b0 >= 1e-3f && jobs.job[j].b1 >= 1e-3f)) bound = false;
+    }
+    const size_t smem = k2tc_smem_bytes(N, jobs.n, stages);
+    const void* fn = nullptr;
+    if (dump)
+        fn = c == 2 ? (const void*)k2tc_kernel<1, 4, true> : (const void*)k2tc_kernel<2, 4, true>;
+    else if (stages == 4)
+        fn = c == 2 ? (const void*)k2tc_kernel<1, 4, false> : (const void*)k2tc_kernel<2, 4, false>;
+    else
+        fn = c == 2 ? (const void*)k2tc_kernel<1, 3, false> : (const void*)k2tc_kernel<2, 3, false>;
     cudaError_t e = ensure_dynamic_smem(fn, smem);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
@@ -500,23 +537,22 @@ cudaError_t launch_k2tc(const CUtensorMap& map, TcGeom tg, int M, int c, int d0,
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const long long n_tiles = (long long)n_items * nd;
+    const long long n_tiles = (long long)n_items * nd * jobs.n;
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
-    K2Prune prune;
-    prune.on = bound && b0 >= 1e-3 && b1 >= 1e-3;
-    prune.beta0 = (float)b0;
-    prune.beta1 = (float)b1;
+    const int prune_on = bound ? 1 : 0;
     auto launch = [&](auto kern) {
-        kern<<<grid, kThreads, smem, st>>>(map, tg, M, d0, nd, items, n_items, tab, fbits, cnt1, sh1, keys, err, prune,
-                                           dump);
+        kern<<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err, prune_on, dump);
     };
-    if (c == 2) {
-        if (dump) launch(k2tc_kernel<1, true>);
-        else launch(k2tc_kernel<1, false>);
+    if (dump) {
+        if (c == 2) launch(k2tc_kernel<1, 4, true>);
+        else launch(k2tc_kernel<2, 4, true>);
+    } else if (stages == 4) {
+        if (c == 2) launch(k2tc_kernel<1, 4, false>);
+        else launch(k2tc_kernel<2, 4, false>);
     } else {
-        if (dump) launch(k2tc_kernel<2, true>);
-        else launch(k2tc_kernel<2, false>);
+        if (c == 2) launch(k2tc_kernel<1, 3, false>);
+        else launch(k2tc_kernel<2, 3, false>);
     }
     return cudaGetLastError();
 }

@@ -157,6 +157,57 @@ cudaError_t launch_gather_job(const void* x, int dtype, const uint8_t* y, int N,
     return cudaGetLastError();
 }
 
+// Class sizes of every job of a batch in one pass: one CTA per job sums
+// y_j[t] = y[yperm_j[idx_j[t]]] over t (NULL maps = identity) and counts the
+// indices outside [0, N): out[j] = (n1, bad).
+__global__ void __launch_bounds__(256) batch_counts_kernel(const uint8_t* __restrict__ y, int N,
+                                                           const int* __restrict__ idx, const int* __restrict__ yperm,
+                                                           int2* __restrict__ out) {
+    const int j = blockIdx.x;
+    const int* ij = idx ? idx + (size_t)j * N : nullptr;
+    const int* pj = yperm ? yperm + (size_t)j * N : nullptr;
+    int n1 = 0, bad = 0;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        int s = ij ? ij[t] : t;
+        if (s < 0 || s >= N) {
+            bad = 1;
+            s = 0;
+        }
+        int s2 = pj ? pj[s] : s;
+        if (s2 < 0 || s2 >= N) {
+            bad = 1;
+            s2 = 0;
+        }
+        n1 += y[s2] != 0;
+        bad |= y[s2] > 1;
+    }
+    __shared__ int red[2][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = n1;
+        red[1][threadIdx.x >> 5] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b |= red[1][w];
+        }
+        out[j] = make_int2(a, b);
+    }
+}
+
+cudaError_t launch_batch_counts(const uint8_t* y, int N, const int* idx, const int* yperm, int n_jobs, int2* out,
+                                cudaStream_t st) {
+    if (n_jobs < 1) return cudaSuccess;
+    batch_counts_kernel<<<n_jobs, 256, 0, st>>>(y, N, idx, yperm, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Entropy tables (Eqs. H, p, beta).  f(t) = t ln t in FP64, stored as int64
 // multiples of 2^-32 (round to nearest).

@@ -152,3 +152,42 @@ def test_batched_full_size_sampled(cuda):
     assert np.array_equal(ig[j], w_ig.cpu().numpy())
     assert np.array_equal(tu[j], w_tu.cpu().numpy())
     assert np.array_equal(di[j], w_di.cpu().numpy())
+
+
+@pytest.mark.parametrize("div,M,N,chunk_bytes", [(1, 50, 300, None), (2, 33, 257, None), (1, 40, 200, 1)])
+def test_batch_chunks_equal_jobs_one_by_one(cuda, monkeypatch, div, M, N, chunk_bytes):
+    """k = 2 batches of 20 jobs: more jobs than one tensor-core launch holds, or
+    (a one-byte operand budget) one job per launch.  Every job equals the
+    single-job scan of its resampled data bit for bit, whatever the chunking."""
+    torch = cuda
+    from paper_1811_00631_gb300 import mdfs
+    if chunk_bytes is not None:
+        monkeypatch.setenv("MDFS_BATCH_BYTES", str(chunk_bytes))
+    ds = synth.xor_pairs(N=N, M=M, n_pairs=3, seed=N)
+    si, yp = _jobs(N, 5, 4, seed=div + N)
+    x = torch.from_numpy(ds.x).cuda()
+    y = torch.from_numpy(ds.y).cuda()
+    ig, tu, di = mdfs.max_ig_batch(x, y, torch.from_numpy(si).cuda(), torch.from_numpy(yp).cuda(), k=2,
+                                   divisions=div, discretizations=3, range_=0.5, pc_xi=0.25, seed=7)
+    torch.cuda.synchronize()
+    ig, tu, di = ig.cpu().numpy(), tu.cpu().numpy(), di.cpu().numpy()
+    for j in range(len(si)):
+        xj = np.ascontiguousarray(ds.x[:, si[j]])
+        yj = ds.y[yp[j][si[j]]]
+        w_ig, w_tu, w_di = mdfs.max_ig(xj, yj, 2, div, 3, 0.5, 0.25, 7)
+        assert np.array_equal(ig[j], w_ig), f"job {j}"
+        assert np.array_equal(tu[j], w_tu), f"job {j}"
+        assert np.array_equal(di[j], w_di), f"job {j}"
+
+
+def test_batch_names_the_single_class_job(cuda):
+    """A job whose resample holds one class only is refused with its index
+    before any scan runs."""
+    from paper_1811_00631_gb300 import mdfs
+    ds = synth.xor_pairs(N=200, M=20, n_pairs=2, seed=1)
+    si = np.tile(np.arange(200, dtype=np.int32), (3, 1))
+    one = int(np.flatnonzero(ds.y == 1)[0])
+    si[2, :] = one
+    with pytest.raises(mdfs.MdfsError) as e:
+        mdfs.max_ig_batch(ds.x, ds.y, si, None, k=2)
+    assert "job 2" in str(e.value)
