@@ -129,6 +129,46 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class BusySampler:
+    """nvidia-smi utilization.gpu (the share of each sample period in which a
+    kernel ran) every 100 ms over a region: mean and median percent."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        log_dir = os.environ.get("MDFS_BENCH_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(log_dir, f"busy_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", "--query-gpu=utilization.gpu",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        vals = []
+        for line in open(self.path):
+            try:
+                vals.append(float(line.strip()))
+            except ValueError:
+                continue
+        if not vals:
+            return None
+        return {"mean_pct": float(np.mean(vals)), "median_pct": float(np.median(vals)), "samples": len(vals)}
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ----------------------------------------------------------------------------
@@ -644,14 +684,19 @@ def serving_run(n_jobs: int, device: int):
     with serve.Server(n_slots=4, device=device) as srv:  # warm-up: workspaces and modules
         for f in [srv.submit(j) for j in jobs[:8]]:
             f.result()
+        busy = BusySampler(device)
+        busy.start()
         t0 = time.perf_counter()
         for f in [srv.submit(j) for j in jobs]:
             f.result()
         closed_s = time.perf_counter() - t0
+        busy_closed = busy.stop()
         capacity = n_jobs / closed_s
         rate = 0.7 * capacity
         rng = np.random.default_rng(3)
         gaps = rng.exponential(1.0 / rate, size=n_jobs)
+        busy = BusySampler(device)
+        busy.start()
         t0 = time.perf_counter()
         futs = []
         for j, g in zip(jobs, np.cumsum(gaps)):
@@ -661,10 +706,13 @@ def serving_run(n_jobs: int, device: int):
             futs.append(srv.submit(j))
         results = [f.result() for f in futs]
         open_s = time.perf_counter() - t0
+        busy_open = busy.stop()
     st = serve.latency_stats(results)
     return {"jobs": n_jobs, "slots": 4, "capacity_jobs_per_s": capacity, "arrival_rate_jobs_per_s": rate,
             "p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"], "mean_ms": 1e3 * st["mean_s"],
             "evals_per_s_closed_loop": evals / closed_s, "evals_per_s_poisson": evals / open_s,
+            "gpu_busy_closed_loop": busy_closed, "gpu_busy_poisson": busy_open,
+            "staging": "pinned per-slot input buffers, one packed result read per job",
             "mix": "k in 1..3, N U[100,5000], M log-U[100,5000] capped at C(M,k)*D*N <= 2e10, f32/i8, "
                    "divisions 1-3, 5-30 discretisations, each scan followed by the IG_lim fit"}
 

@@ -473,7 +473,7 @@ void tune_put(const std::string& key, int v) {
 // The tuned stage count of the k = 2 tensor-core launch of `jobs` (0 on a CUDA
 // error); `kernel` names the cache entry (single scans and batches apart).
 int tuned_k2_stages(Workspace* ws, const char* kernel, const K2Jobs& jobs, int M, int c, int D, const int2* items,
-                    int n_items, const CUtensorMap& map, int fbits, bool bound) {
+                    int n_items, const uint8_t* oh, int Kp, int zdim, int fbits, bool bound) {
     const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1;
     const std::string key = tune_key(kernel, M, N, c, D);
     if (const int v = tune_get(key)) return v;
@@ -500,10 +500,11 @@ int tuned_k2_stages(Workspace* ws, const char* kernel, const K2Jobs& jobs, int M
     bool ok = true;
     for (int rep = 0; rep < 2 && ok; ++rep) {
         for (const int stages : {4, 3}) {
-            if (k2tc_smem_bytes(N, jobs.n, stages) > kK3tcMaxSmem) continue;
+            if (k2tc_smem_bytes(c, N, jobs.n, stages) > kK3tcMaxSmem) continue;
             float ms = 0.0f;
             if (cudaEventRecord(e0, st) != cudaSuccess ||
-                launch_k2tc(map, jobs, M, c, 0, D, D, items, n_items, fbits, (int*)ws->err.p, bound, stages, st) !=
+                launch_k2tc(oh, Kp, zdim, jobs, M, c, 0, D, D, items, n_items, fbits, (int*)ws->err.p, bound, stages,
+                            st) !=
                     cudaSuccess ||
                 cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -566,7 +567,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
     const EmitTable em = emit ? *emit : EmitTable();
-    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_smem_bytes(N, 1, 4) <= kK3tcMaxSmem);
+    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem);
     const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     TcGeom tg = make_tc_geom(n0, n1);
     if (dump && !use_tc2 && !use_tc3)
@@ -595,8 +596,6 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             ws->items3_c = c;
             ws->n_items3 = (int)items.size();
         }
-        CUtensorMap map;
-        MDFS_CUDA_TRY(make_onehot_map(&map, onehot, M * P, D, tg.Kp));
         int lo = 0;
         const int cnt = share(ws->n_items3, &lo);
         const bool exact = take_test_hooks(false).exact;
@@ -605,9 +604,9 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         jobs.job[0] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};
         const int stages = dump ? 4
                                 : tuned_k2_stages(ws, "k2tc_stages", jobs, M, c, D, (const int2*)ws->items3.p + lo,
-                                                  cnt, map, k3tc_fraction_bits(N), !exact);
+                                                  cnt, onehot, tg.Kp, D, k3tc_fraction_bits(N), !exact);
         if (stages <= 0) return fail(MDFS_ECUDA, "k = 2 stage tuning failed (CUDA error)");
-        MDFS_LAUNCH("k2", st, launch_k2tc(map, jobs, M, c, 0, D, D, (const int2*)ws->items3.p + lo, cnt,
+        MDFS_LAUNCH("k2", st, launch_k2tc(onehot, tg.Kp, D, jobs, M, c, 0, D, D, (const int2*)ws->items3.p + lo, cnt,
                                           k3tc_fraction_bits(N), (int*)ws->err.p, !exact, stages, st, dump));
         *check_err = true;
     } else if (k == 2) {
@@ -1073,7 +1072,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     bool check_err = false;
     // k = 2 on the tensor cores: chunks of jobs share one launch over (job,
     // discretisation, tile) work items
-    if (k == 2 && k2tc_supported(c) && k2tc_smem_bytes(N, 1, 4) <= kK3tcMaxSmem) {
+    if (k == 2 && k2tc_supported(c) && k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem) {
         int Kp_max = 0, Ws_max = 0;
         for (int j = 0; j < n_jobs; ++j) {
             Kp_max = std::max(Kp_max, make_tc_geom(N - counts[j].x, counts[j].x).Kp);
@@ -1086,7 +1085,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
         const size_t op_bytes = (size_t)D * M * P * Kp_max;
         const int by_mem = (int)std::max<size_t>(1, budget / std::max<size_t>(op_bytes, 1));
         int stages = tune_get(tune_key("k2tc_batch_stages", M, N, c, D));
-        const int chunk_cap = std::min({n_jobs, by_mem, std::max(1, k2tc_max_jobs(N, stages ? stages : 4,
+        const int chunk_cap = std::min({n_jobs, by_mem, std::max(1, k2tc_max_jobs(c, N, stages ? stages : 4,
                                                                                   kK3tcMaxSmem))});
         const size_t np1 = (size_t)N + 1;
         MDFS_ENSURE(ws, bonehot, (size_t)chunk_cap * op_bytes);
@@ -1137,16 +1136,15 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
                 MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
                 jobs.job[jj] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};
             }
-            CUtensorMap map;
-            MDFS_CUDA_TRY(make_onehot_map(&map, (const uint8_t*)ws->bonehot.p, M * P, nj * D, Kp_max));
+            const uint8_t* oh = (const uint8_t*)ws->bonehot.p;
             if (!stages) {
+                // 3 stages need less shared memory than the 4 the chunk was sized for
                 stages = tuned_k2_stages(ws, "k2tc_batch_stages", jobs, M, c, D, (const int2*)ws->items3.p,
-                                         ws->n_items3, map, fbits, true);
+                                         ws->n_items3, oh, Kp_max, nj * D, fbits, true);
                 if (stages <= 0) return fail(MDFS_ECUDA, "k = 2 stage tuning failed (CUDA error)");
-                if (k2tc_smem_bytes(N, nj, stages) > kK3tcMaxSmem) stages = 4;
             }
-            MDFS_LAUNCH("k2", st, launch_k2tc(map, jobs, M, c, 0, D, D, (const int2*)ws->items3.p, ws->n_items3, fbits,
-                                              (int*)ws->err.p, true, stages, st));
+            MDFS_LAUNCH("k2", st, launch_k2tc(oh, Kp_max, nj * D, jobs, M, c, 0, D, D, (const int2*)ws->items3.p,
+                                              ws->n_items3, fbits, (int*)ws->err.p, true, stages, st));
             for (int jj = 0; jj < nj; ++jj) {
                 const int j = j0 + jj;
                 MDFS_LAUNCH("finalize", st,

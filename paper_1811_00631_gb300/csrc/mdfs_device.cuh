@@ -101,6 +101,13 @@ __device__ __forceinline__ int fx_narrow(long long v, int s) {
     return (int)((v + (1ll << (shift - 1))) >> shift);
 }
 
+// Packed FP32 pairs: two independent lanes per instruction (sm_100 and later),
+// each rounded as the scalar operation would be.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // Counts index the [0, n] tables; a count outside that range cannot arise from
 // consistent inputs, and clamping keeps every table read inside its buffer.
 __device__ __forceinline__ int clamp_count(int v, int n) { return min(max(v, 0), n); }

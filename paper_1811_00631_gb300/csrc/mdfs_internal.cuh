@@ -219,8 +219,8 @@ cudaError_t launch_k3tc_order(const int* cnt1, int M, int D, int* perm, int* ran
 cudaError_t launch_k3tc_operand(const uint8_t* src, uint8_t* dst, const int* perm, int M, int D, TcGeom tg,
                                 cudaStream_t st);
 
-// k = 2 on the tensor cores for c = 2, 3: one-hot rows M (c-1) through TMA
-// (map over [jobs x D][M (c-1)][Kp]), symmetric tiles (it <= mt) from
+// k = 2 on the tensor cores for c = 2, 3: the one-hot rows [zdim][M (c-1)][Kp]
+// bytes (zdim = jobs x discretisations per job) through TMA, the tiles of
 // build_k2tc_items.  One launch scans up to kMaxK2Jobs jobs of the same N (the
 // resamples of a batch): work items (job, discretisation, tile), every job's
 // entropy tables in shared memory at once.
@@ -240,17 +240,26 @@ struct K2Jobs {
 bool k2tc_supported(int c);
 void build_k2tc_items(int M, int c, std::vector<int2>& items);
 // dynamic shared memory of a launch with n_jobs jobs of N samples and `stages` pipeline stages
-size_t k2tc_smem_bytes(int N, int n_jobs, int stages);
+size_t k2tc_smem_bytes(int c, int N, int n_jobs, int stages);
 // the most jobs of N samples one launch can hold within smem_limit bytes (0: none)
-int k2tc_max_jobs(int N, int stages, size_t smem_limit);
+int k2tc_max_jobs(int c, int N, int stages, size_t smem_limit);
 // bound: with three classes, skip the pairs whose SH2 lower bound rules out
-// both roles.  stages: 3 or 4.  dstride: discretisations per job in the map.
+// both roles.  stages: 3 or 4.  dstride: discretisations per job in the operand.
 // dump != NULL (test hook, one job, 4 stages): also writes the c x c class
 // counts of every pair i < m, [D][C(M,2)][c c] uint32 n0 | n1 << 16 at the
 // pair's rank in the upper triangle, voxel code_i c + code_m.
-cudaError_t launch_k2tc(const CUtensorMap& map, const K2Jobs& jobs, int M, int c, int d0, int nd, int dstride,
-                        const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,
-                        uint32_t* dump = nullptr);
+cudaError_t launch_k2tc(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int c, int d0, int nd,
+                        int dstride, const int2* items, int n_items, int fbits, int* err, bool bound, int stages,
+                        cudaStream_t st, uint32_t* dump = nullptr);
+// the c = 3 kernel (mdfs_k2tc3.cu) behind launch_k2tc
+void build_k2tc3_items(int M, std::vector<int2>& items);
+size_t k2tc3_smem_bytes(int N, int n_jobs, int stages);
+cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int d0, int nd, int dstride,
+                         const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,
+                         uint32_t* dump);
+// byte tensor map with the 128-byte swizzle (box[0] = 128 bytes), strides in bytes
+cudaError_t make_tiled_map_u8(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
+                              const cuuint64_t* strides, const cuuint32_t* box);
 
 // Contrast rows M .. M + n_contrast - 1 of x_ext (dtype 0 f32, 1 i8); rows
 // 0 .. M-1 are not written.  src [n_contrast] or NULL.

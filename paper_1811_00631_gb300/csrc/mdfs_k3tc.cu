@@ -153,12 +153,6 @@ struct K3Prune {
 };
 constexpr float kBoundRel = 1.0f / 4096.0f, kBoundAbs = 0.05f;
 
-// packed FP32 pairs (two lanes per instruction)
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
 // Two fractions per lane pair: (pa / sa) + (pb / sb) as num / den in each lane (sa, sb > 0).
 __device__ __forceinline__ void frac_add2(float2 pa, float2 sa, float2 pb, float2 sb, float2& num, float2& den) {
     num = fma2(pa, sb, mul2(pb, sa));
@@ -829,6 +823,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
         return nullptr;
     }();
     return fn;
+}
+
+// Byte tensor (dims[0] contiguous, strides in bytes of dims 1 .. rank-1) as a
+// tiled tensor map with the 128-byte swizzle; box[0] must be 128 bytes.
+cudaError_t make_tiled_map_u8(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
+                              const cuuint64_t* strides, const cuuint32_t* box) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    if (rank < 2 || rank > 5 || ((uintptr_t)base & 15) != 0 || box[0] != 128) return cudaErrorInvalidValue;
+    for (int i = 0; i < rank - 1; ++i)
+        if (strides[i] % 16 != 0) return cudaErrorInvalidValue;
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // One-hot operand [D][rows][Kp] bytes as a 3-D tensor map with 128 x 128 boxes

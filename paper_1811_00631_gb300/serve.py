@@ -142,6 +142,7 @@ class Server:
         self._executor = executor
         self._release_cb = release_workspace
         self._streams = [None] * n_slots
+        self._staging = [None] * n_slots  # pinned host buffers per slot (GPU executor)
         self._queue = collections.deque()
         self._cv = threading.Condition()
         self._held = [dict() for _ in range(n_slots)]  # bytes retained per buffer group, per slot
@@ -295,6 +296,8 @@ class Server:
             torch.cuda.set_device(self.device)
             ctx = torch.cuda.Stream(self.device)
             self._streams[slot] = ctx
+        staging = _Staging()
+        self._staging[slot] = staging
         while True:
             item = self._next(slot)
             if item is None:
@@ -305,7 +308,7 @@ class Server:
                 if self._executor is not None:
                     out = self._executor(job, slot)
                 else:
-                    out = _run_on_gpu(job, ctx, self.device)
+                    out = _run_on_gpu(job, ctx, self.device, staging)
                 t1 = time.perf_counter()
                 fut.set_result(Result(*out, submit_t=t_sub, start_t=t0, end_t=t1, slot=slot, tag=job.tag))
                 self._log(job, "ok", t_sub, t0, t1, slot)
@@ -336,26 +339,94 @@ class Server:
             self.log_errors += 1
 
 
-def _run_on_gpu(job: Job, stream, device: int):
+class _Staging:
+    """Page-locked host buffers of one slot.  A host input is copied into the
+    input buffer and moved to the device asynchronously on the slot's stream;
+    the job's results are packed into one device buffer and come back in one
+    device-to-host copy.  A slot runs one job at a time and waits for its
+    stream before the next, so the buffers are free again when a job starts."""
+
+    def __init__(self):
+        self.h_in = None
+        self.h_out = None
+        self.h2d_bytes = 0
+        self.d2h_bytes = 0
+
+    @staticmethod
+    def _grow(buf, nbytes: int):
+        import torch
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.empty(max(int(nbytes * 1.25), 1 << 20), dtype=torch.uint8, pin_memory=True)
+        return buf
+
+    def inputs(self, arrays, device: int):
+        """Device tensors of the host arrays (CUDA tensors pass through)."""
+        import torch
+        host = [np.ascontiguousarray(a) for a in arrays if not getattr(a, "is_cuda", False)]
+        offs, total = [], 0
+        for a in host:
+            offs.append(total)
+            total += (a.nbytes + 255) & ~255
+        if total:
+            self.h_in = self._grow(self.h_in, total)
+        out, h = [], 0
+        for a in arrays:
+            if getattr(a, "is_cuda", False):
+                out.append(a)
+                continue
+            a = host[h]
+            view = self.h_in[offs[h]:offs[h] + a.nbytes].numpy().view(a.dtype).reshape(a.shape)
+            np.copyto(view, a)
+            t = self.h_in[offs[h]:offs[h] + a.nbytes].view(torch.from_numpy(a[:0]).dtype).view(a.shape)
+            out.append(t.to(f"cuda:{device}", non_blocking=True))
+            self.h2d_bytes += a.nbytes
+            h += 1
+        return out
+
+    def results(self, tensors, stream):
+        """numpy copies of the CUDA tensors after one packed read (None stays None)."""
+        import torch
+        live = [t.contiguous() for t in tensors if t is not None]
+        flat = [t.reshape(-1).view(torch.uint8) for t in live]
+        sizes = [f.numel() for f in flat]
+        total = sum(sizes)
+        packed = torch.cat(flat) if len(flat) > 1 else flat[0]
+        self.h_out = self._grow(self.h_out, total)
+        self.h_out[:total].copy_(packed, non_blocking=True)
+        stream.synchronize()
+        self.d2h_bytes += total
+        host = self.h_out[:total].numpy()
+        out, o, i = [], 0, 0
+        for t in tensors:
+            if t is None:
+                out.append(None)
+                continue
+            n = sizes[i]
+            dt = torch.empty(0, dtype=t.dtype).numpy().dtype
+            out.append(host[o:o + n].view(dt).reshape(tuple(t.shape)).copy())
+            o += n
+            i += 1
+        return out
+
+
+def _run_on_gpu(job: Job, stream, device: int, staging: Optional[_Staging] = None):
     import torch
 
     from . import mdfs
+    staging = staging or _Staging()
     with torch.cuda.device(device), torch.cuda.stream(stream):
-        x = job.x if getattr(job.x, "is_cuda", False) else torch.as_tensor(np.asarray(job.x)).to(
-            f"cuda:{device}", non_blocking=False)
-        y = job.y if getattr(job.y, "is_cuda", False) else torch.as_tensor(np.asarray(job.y, dtype=np.uint8)).to(
-            f"cuda:{device}", non_blocking=False)
+        y_in = job.y if getattr(job.y, "is_cuda", False) else np.asarray(job.y, dtype=np.uint8)
+        x, y = staging.inputs([job.x, y_in], device)
         ig, tu, di = mdfs.max_ig(x, y, job.k, job.divisions, job.discretizations, job.range_, job.pc_xi, job.seed)
-        p = lim = neff = None
+        p_t = lim = neff = None
         if job.alpha is not None:
             try:
                 p_t, lim, neff = mdfs.ig_lim(ig, job.k, job.divisions, job.discretizations, None, job.alpha)
-                p = p_t.cpu().numpy()
             except mdfs.MdfsError as e:
                 if e.code != -2:  # no variable with IG > 0: no fit for this job
                     raise
-        stream.synchronize()
-        return ig.cpu().numpy(), tu.cpu().numpy(), di.cpu().numpy(), p, lim, neff
+        ig_h, tu_h, di_h, p = staging.results([ig, tu, di, p_t], stream)
+        return ig_h, tu_h, di_h, p, lim, neff
 
 
 def latency_stats(results):
