@@ -426,7 +426,7 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
 // more than once leaves the same result.  The choice is kept in memory and,
 // when the environment variable MDFS_TUNE_FILE names a file, appended there as
 // "<kernel> M=.. N=.. c=.. D=.. -> <choice>" lines that later processes read
-// back.  MDFS_TUNE=0 skips the measurement (4 stages).
+// back.  MDFS_TUNE=0 skips the measurement (the deepest pipeline that fits).
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
@@ -476,9 +476,22 @@ int tuned_k2_stages(Workspace* ws, const char* kernel, const K2Jobs& jobs, int M
                     int n_items, const uint8_t* oh, int Kp, int zdim, int fbits, bool bound) {
     const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1;
     const std::string key = tune_key(kernel, M, N, c, D);
-    if (const int v = tune_get(key)) return v;
+    // a cached choice that does not fit this launch is measured again
+    if (const int v = tune_get(key))
+        if ((v == 3 || v == 4) && k2tc_smem_bytes(c, N, jobs.n, v) <= kK3tcMaxSmem) return v;
+    int n_fit = 0, deepest = 0;
+    for (const int stages : {4, 3})
+        if (k2tc_smem_bytes(c, N, jobs.n, stages) <= kK3tcMaxSmem) {
+            ++n_fit;
+            if (!deepest) deepest = stages;
+        }
+    if (n_fit == 0) return 0;
+    if (n_fit == 1) {  // nothing to choose between
+        tune_put(key, deepest);
+        return deepest;
+    }
     const char* en = getenv("MDFS_TUNE");
-    if (en && en[0] == '0') return 4;
+    if (en && en[0] == '0') return deepest;
     cudaStream_t st = ws->stream;
     // a stream being captured into a graph cannot be timed: untuned default
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -486,7 +499,7 @@ int tuned_k2_stages(Workspace* ws, const char* kernel, const K2Jobs& jobs, int M
         cudaGetLastError();
         return 0;
     }
-    if (cap != cudaStreamCaptureStatusNone) return 4;
+    if (cap != cudaStreamCaptureStatusNone) return deepest;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -567,7 +580,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
     const EmitTable em = emit ? *emit : EmitTable();
-    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem);
+    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_counts_fit(c, n0, n1) &&
+                          k2tc_smem_bytes(c, N, 1, 3) <= kK3tcMaxSmem);
     const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
     TcGeom tg = make_tc_geom(n0, n1);
     if (dump && !use_tc2 && !use_tc3)
@@ -578,7 +592,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         onehot = (uint8_t*)ws->onehot.p;
     }
     MDFS_LAUNCH("discretize", st, launch_discretize(xd, dtype, N, M, c, D, range, seed, (const int*)ws->perm.p, g,
-                                                    planes, nullptr, nullptr, onehot, tg, st));
+                                                    planes, nullptr, nullptr, onehot, tg, st,
+                                                    use_tc2 ? k2tc_class1_byte(c) : 0x38u));
     MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
     MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, (k == 1 && shard == 0) ? keys : nullptr, st,
                                     k == 1 ? em : EmitTable()));
@@ -602,7 +617,8 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         K2Jobs jobs{};
         jobs.n = 1;
         jobs.job[0] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};
-        const int stages = dump ? 4
+        // the count test hook runs the deepest pipeline that fits
+        const int stages = dump ? (k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem ? 4 : 3)
                                 : tuned_k2_stages(ws, "k2tc_stages", jobs, M, c, D, (const int2*)ws->items3.p + lo,
                                                   cnt, onehot, tg.Kp, D, k3tc_fraction_bits(N), !exact);
         if (stages <= 0) return fail(MDFS_ECUDA, "k = 2 stage tuning failed (CUDA error)");
@@ -1072,7 +1088,9 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
     bool check_err = false;
     // k = 2 on the tensor cores: chunks of jobs share one launch over (job,
     // discretisation, tile) work items
-    if (k == 2 && k2tc_supported(c) && k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem) {
+    bool tc_fit = k == 2 && k2tc_supported(c) && k2tc_smem_bytes(c, N, 1, 3) <= kK3tcMaxSmem;
+    for (int j = 0; j < n_jobs && tc_fit; ++j) tc_fit = k2tc_counts_fit(c, N - counts[j].x, counts[j].x);
+    if (tc_fit) {
         int Kp_max = 0, Ws_max = 0;
         for (int j = 0; j < n_jobs; ++j) {
             Kp_max = std::max(Kp_max, make_tc_geom(N - counts[j].x, counts[j].x).Kp);
@@ -1085,8 +1103,12 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
         const size_t op_bytes = (size_t)D * M * P * Kp_max;
         const int by_mem = (int)std::max<size_t>(1, budget / std::max<size_t>(op_bytes, 1));
         int stages = tune_get(tune_key("k2tc_batch_stages", M, N, c, D));
-        const int chunk_cap = std::min({n_jobs, by_mem, std::max(1, k2tc_max_jobs(c, N, stages ? stages : 4,
-                                                                                  kK3tcMaxSmem))});
+        if (stages != 3 && stages != 4) stages = 0;
+        if (stages && k2tc_max_jobs(c, N, stages, kK3tcMaxSmem) < 1) stages = 0;  // a cached choice that cannot run
+        // untuned: size the chunk for the deepest pipeline that holds a job
+        const int cap_stages = stages ? stages : (k2tc_max_jobs(c, N, 4, kK3tcMaxSmem) > 0 ? 4 : 3);
+        const int chunk_cap =
+            std::min({n_jobs, by_mem, std::max(1, k2tc_max_jobs(c, N, cap_stages, kK3tcMaxSmem))});
         const size_t np1 = (size_t)N + 1;
         MDFS_ENSURE(ws, bonehot, (size_t)chunk_cap * op_bytes);
         MDFS_ENSURE(ws, btab, (size_t)chunk_cap * 3 * np1 * sizeof(long long));
@@ -1131,7 +1153,7 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
                 MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
                 MDFS_LAUNCH("discretize", st, launch_discretize(ws->bx.p, data->dtype, N, M, c, D, range, seed,
                                                                 (const int*)ws->perm.p, g, (uint32_t*)ws->planes.p,
-                                                                nullptr, nullptr, onehot, tgd, st));
+                                                                nullptr, nullptr, onehot, tgd, st, k2tc_class1_byte(c)));
                 MDFS_LAUNCH("k1", st, launch_k1((const uint32_t*)ws->planes.p, g, M, c, D, tab, cnt1, sh1, nullptr, st));
                 MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
                 jobs.job[jj] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};

@@ -97,10 +97,12 @@ cudaError_t launch_ftable_wide(double b0, double b1, long long* tab, cudaStream_
 // planes: [D][M][c-1][Ws] u32 (NULL = skip); codes: [D][M][N] u8 (NULL = skip);
 // thr: [D][M][c-1] f32 (NULL = skip).
 // onehot: [D][M (c-1)][Kp] bytes, E4M3 1.0 (0x38) where the sample falls in
-// bin a >= 1 of the row (v, a), class-sorted with the TcGeom padding (NULL = skip).
+// bin a >= 1 of the row (v, a), class-sorted with the TcGeom padding (NULL =
+// skip); class-1 samples (K range [K0p, Kp)) get the byte class1_byte instead.
 cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
                               uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
-                              uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st);
+                              uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st,
+                              uint32_t class1_byte = 0x38);
 
 // Per (disc, variable): class counts of bins 1..c-1 -> cnt1 [D][M][c-1][2] i32,
 // SH1 [D][M] i64.  If keys != NULL also folds IG^1 = SH0 - SH1 into keys.
@@ -238,6 +240,10 @@ struct K2Jobs {
     K2Job job[kMaxK2Jobs];
 };
 bool k2tc_supported(int c);
+// the class sizes the kernel for c classes per variable can count exactly
+bool k2tc_counts_fit(int c, int N0, int N1);
+// the one-hot byte of a class-1 sample in that kernel's operand
+uint32_t k2tc_class1_byte(int c);
 void build_k2tc_items(int M, int c, std::vector<int2>& items);
 // dynamic shared memory of a launch with n_jobs jobs of N samples and `stages` pipeline stages
 size_t k2tc_smem_bytes(int c, int N, int n_jobs, int stages);
@@ -251,8 +257,12 @@ int k2tc_max_jobs(int c, int N, int stages, size_t smem_limit);
 cudaError_t launch_k2tc(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int c, int d0, int nd,
                         int dstride, const int2* items, int n_items, int fbits, int* err, bool bound, int stages,
                         cudaStream_t st, uint32_t* dump = nullptr);
-// the c = 3 kernel (mdfs_k2tc3.cu) behind launch_k2tc
+// the c = 3 kernel (mdfs_k2tc3.cu) behind launch_k2tc; its one-hot operand
+// carries class1_byte (k2tc_class1_byte) for class-1 samples, and it needs
+// class sizes N0, N1 below 4096 (k2tc_counts_fit)
 void build_k2tc3_items(int M, std::vector<int2>& items);
+bool k2tc3_counts_fit(int N0, int N1);
+uint32_t k2tc3_class1_byte();
 size_t k2tc3_smem_bytes(int N, int n_jobs, int stages);
 cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int d0, int nd, int dstride,
                          const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,

@@ -345,6 +345,11 @@ int k2tc_max_jobs(int c, int N, int stages, size_t smem_limit) {
 
 bool k2tc_supported(int c) { return c == 2 || c == 3; }
 
+// c = 2 keeps the classes in separate accumulators: any class sizes below 2^24
+bool k2tc_counts_fit(int c, int N0, int N1) { return c == 3 ? k2tc3_counts_fit(N0, N1) : N0 >= 1 && N1 >= 1; }
+
+uint32_t k2tc_class1_byte(int c) { return c == 3 ? k2tc3_class1_byte() : 0x38u; }
+
 cudaError_t launch_k2tc(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int c, int d0, int nd,
                         int dstride, const int2* items, int n_items, int fbits, int* err, bool bound, int stages,
                         cudaStream_t st, uint32_t* dump) {

@@ -2,23 +2,31 @@
 // bins per variable, P = 2).  Voxel counters of section "Algorithm and
 // implementation"; the two IG roles of Eq. 1 with |S| = 1.
 //
-// One (variable, bin >= 1) is one E4M3 one-hot row over the class-sorted
-// samples, rows v P + p of the operand.  A tile pairs 128 row variables with 32
-// column variables.  The A operand holds the 128 row variables twice, once per
-// bin (a 4-D tensor map selects every second row), and B the 64 rows of the
-// column variables, so four 128 x 64 FP32 accumulators (row bin x class; class
-// 0 and class 1 samples occupy separate K ranges) give every thread, which owns
-// one row variable (one TMEM lane), the whole 2 x 2 block of counts with both
-// bins >= 1 for each of its column variables.  A pair is then completed,
-// bounded and (when the bound cannot rule it out) evaluated by one thread, with
-// no exchange between lanes.
+// One (variable, bin >= 1) is one one-hot row over the class-sorted samples,
+// rows v P + p of the operand, with E4M3 1.0 for a class-0 sample and 64.0 for
+// a class-1 sample in the bin.  A product of two rows is 1 for a class-0 sample
+// in both bins and 4096 for a class-1 sample, so one FP32 accumulator holds
+// n0 + 4096 n1; with n0, n1 < 4096 every partial sum is an integer below 2^24
+// and both class counts are exact.
 //
-// Persistent kernel, one CTA per SM, 640 threads:
+// A tile pairs 128 row variables with 64 column variables.  The A operand holds
+// the 128 row variables twice, once per bin (a 4-D tensor map selects every
+// second row), and B the 128 rows of the column variables, so two 128 x 128
+// accumulators (one per row bin) give every thread, which owns one row
+// variable (one TMEM lane), the whole 2 x 2 block of counts with both bins >= 1
+// for each of its column variables.  A thread splits the classes, completes
+// the 3 x 3 table of a pair by inclusion-exclusion and evaluates the SH2 lower
+// bound with no exchange between lanes.  The few pairs that the bound cannot
+// rule out go to a per-warp queue in shared memory; a full queue is evaluated
+// with one pair per lane (27 table lookups each), so the lookups run on full
+// warps whichever lanes produced the pairs.
+//
+// Persistent kernel, one CTA per SM, 640 threads, 3 pipeline stages:
 //   warp 0       TMA producer (two A tiles and one B tile per K block),
-//   warp 1       TMEM owner and MMA issuer (2 x 2 x 64 x 2 accumulator columns:
-//                bin, class, columns, double buffer = all 512),
+//   warp 1       TMEM owner and MMA issuer (2 row bins x 128 columns x 2
+//                buffers = all 512 columns),
 //   warps 4-19   epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 and
-//                the columns of 8 of the 32 column variables.
+//                the columns of 16 of the 64 column variables.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -32,24 +40,32 @@ namespace {
 
 constexpr int kBK = 128;                                  // K bytes (samples) per block
 constexpr int kRowVars = 128;                             // row variables per tile
-constexpr int kColVars = 32;                              // column variables per tile
+constexpr int kColVars = 64;                              // column variables per tile
 constexpr int kBRows = 2 * kColVars;                      // B rows: (column variable, bin)
 constexpr uint32_t kABytes = kRowVars * kBK;              // one bin's A tile
 constexpr uint32_t kBBytes = kBRows * kBK;
-constexpr uint32_t kStageBytes = 2 * kABytes + kBBytes;   // 40 KB, a multiple of 1024
-constexpr uint32_t kAccCols = kBRows;                     // 64 columns per accumulator
-constexpr uint32_t kBufCols = 4 * kAccCols;               // (row bin, class) accumulators
+constexpr uint32_t kStageBytes = 2 * kABytes + kBBytes;   // 48 KB, a multiple of 1024
+constexpr uint32_t kAccCols = kBRows;                     // 128 columns per accumulator
+constexpr uint32_t kBufCols = 2 * kAccCols;               // one accumulator per row bin
 constexpr uint32_t kTmemCols = 2 * kBufCols;              // double buffer: 512
 constexpr int kThreads = 640;
 constexpr int kEpiWarp0 = 4, kEpiWarps = 16, kEpiThreads = 32 * kEpiWarps;
 constexpr int kColsPerWarp = kColVars / 4;                // column variables per epilogue warp
+constexpr int kColsPerPass = 8;                           // column variables per TMEM read
 constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
 static_assert(128 * kRegsProducer + kEpiThreads * kRegsEpilogue == kThreads * kRegsLaunch,
               "register split must add up to the launch allocation");
+constexpr int kStages = 3;
 // column-variable context per epilogue warp: 2 float4 per column variable
 constexpr uint32_t kCtxBytes = kEpiWarps * kColsPerWarp * 32;
-__host__ __device__ constexpr size_t ctx_offset(int S) { return (size_t)S * kStageBytes; }
-__host__ __device__ constexpr size_t tab_offset3(int S) { return ctx_offset(S) + kCtxBytes; }
+// pair queue per epilogue warp: kQueue records of the 9 voxels' smoothed
+// class counts (float2, structure of arrays) and (vi, vm, SH1(i), SH1(m))
+constexpr int kQueue = 16;
+constexpr uint32_t kQueueWarpBytes = kQueue * (9 * 8 + 16);
+constexpr uint32_t kQueueBytes = kEpiWarps * kQueueWarpBytes;
+__host__ __device__ constexpr size_t ctx_offset() { return (size_t)kStages * kStageBytes; }
+__host__ __device__ constexpr size_t queue_offset() { return ctx_offset() + kCtxBytes; }
+__host__ __device__ constexpr size_t tab_offset3() { return queue_offset() + kQueueBytes; }
 // int32 entries per job: T0 (N0 + 1), T1 (N1 + 1), TB (N + 1), rounded to 16 bytes
 __host__ __device__ constexpr int tab_stride3(int N) { return (2 * N + 3 + 3) & ~3; }
 
@@ -63,20 +79,10 @@ constexpr float kBoundRel = 1.0f / 4096.0f, kBoundAbs = 0.05f;
 constexpr float kInv4Ln2 = 0.36067376022224085f;                    // 1 / (4 ln 2)
 constexpr float kFx32ToCount = 2.3283064365386963e-10f * kInv4Ln2;  // 2^-32 / (4 ln 2)
 
-__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
-
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
     const unsigned long long t0 = tc::global_ns();
     while (!tc::mbar_try_wait(bar, parity))
         if (tc::global_ns() - t0 > tc::kWaitLimitNs) return;
-}
-
-__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long k) {
-    const uint32_t hi = (uint32_t)(k >> 32);
-    const uint32_t hmax = __reduce_max_sync(0xffffffffu, hi);
-    const uint32_t lo = (hi == hmax) ? (uint32_t)k : 0u;
-    const uint32_t lmax = __reduce_max_sync(0xffffffffu, lo);
-    return ((unsigned long long)hmax << 32) | lmax;
 }
 
 // IG of a key in units of 4 ln 2 nats; -inf for a key not yet set
@@ -90,10 +96,21 @@ __device__ __forceinline__ float i2f_exact(int v) { return __int_as_float(0x4B40
 
 __device__ __forceinline__ int tab32(const int* t, int n, int nmax) { return t[min((unsigned)n, (unsigned)nmax)]; }
 
-// regularised voxel term of SH in int32 fixed point: f(n0 + n1 + b0 + b1) - f(n0 + b0) - f(n1 + b1)
-__device__ __forceinline__ int voxel32(const int* sT0, const int* sT1, const int* sTB, int N0, int N1, int N, float f0,
-                                       float f1) {
-    const int n0 = f2i_exact(f0), n1 = f2i_exact(f1);
+// Two accumulator values v = n0 + 4096 n1 (exact integers below 2^24) split
+// into n0 and n1: n1 = floor(v / 4096) is the sum 2^23 + v 2^-12 rounded
+// toward zero (one fused multiply-add; the product is exact), then n0 = v -
+// 4096 n1.  All three steps are exact.
+__device__ __forceinline__ void split_classes(float2 v, float2& n0, float2& n1) {
+    const float2 r = __ffma2_rz(v, make_float2(2.44140625e-4f, 2.44140625e-4f), make_float2(8388608.0f, 8388608.0f));
+    n1 = add2(r, make_float2(-8388608.0f, -8388608.0f));
+    n0 = fma2(n1, make_float2(-4096.0f, -4096.0f), v);
+}
+
+// regularised voxel term of SH in int32 fixed point, f(n0 + n1 + b0 + b1) -
+// f(n0 + b0) - f(n1 + b1), from the smoothed counts m = n + beta
+__device__ __forceinline__ int voxel32(const int* sT0, const int* sT1, const int* sTB, int N0, int N1, int N, float2 m,
+                                       float beta0, float beta1) {
+    const int n0 = f2i_exact(m.x - beta0), n1 = f2i_exact(m.y - beta1);
     return tab32(sTB, n0 + n1, N) - tab32(sT0, n0, N0) - tab32(sT1, n1, N1);
 }
 
@@ -101,16 +118,17 @@ __device__ __forceinline__ int voxel32(const int* sT0, const int* sT1, const int
 
 // Work items: (job, discretisation, tile) for jobs.n jobs of the same N,
 // discretisations d0 .. d0 + nd - 1 and the n_items tiles (row block of 128
-// variables, column block of 32 variables at or after it); job j's operand rows
-// are at z = j dstride + d of both tensor maps.  S: pipeline stages.  kDump:
-// also write the 3 x 3 class counts of every pair of job 0 to `dump` (test hook;
-// the scan itself is unchanged).
-template <int S, bool kDump>
+// variables, column block of 64 variables at or after it); job j's operand rows
+// are at z = j dstride + d of both tensor maps.  kDump: also write the 3 x 3
+// class counts of every pair of job 0 to `dump` (test hook; the scan itself is
+// unchanged).
+template <bool kDump>
 __global__ void __launch_bounds__(kThreads, 1)
     k2tc3_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                  const __grid_constant__ K2Jobs jobs, int M, int d0, int nd, int dstride,
                  const int2* __restrict__ items, int n_items, int fbits, int* __restrict__ err, int prune_on,
                  uint32_t* __restrict__ dump) {
+    constexpr int S = kStages;
     const bool use_bound = !kDump && prune_on;
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[S], bar_empty[S];
@@ -120,16 +138,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* base = dsmem_raw + ((1024 - (tc::smem_u32(dsmem_raw) & 1023)) & 1023);
-    float4* sCtx = reinterpret_cast<float4*>(base + ctx_offset(S));
+    float4* sCtx = reinterpret_cast<float4*>(base + ctx_offset());
+    uint8_t* sQueue = base + queue_offset();
     const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1, np1 = N + 1;  // the same N for every job
     const int tstride = tab_stride3(N);
-    int* sTab = reinterpret_cast<int*>(base + tab_offset3(S));
+    int* sTab = reinterpret_cast<int*>(base + tab_offset3());
     volatile int* abort = &s_abort;
 
     uint32_t dyn_bytes;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
     const bool fits = jobs.n >= 1 && jobs.n <= kMaxK2Jobs &&
-                      (size_t)(base - dsmem_raw) + tab_offset3(S) + (size_t)jobs.n * tstride * sizeof(int) <= dyn_bytes;
+                      (size_t)(base - dsmem_raw) + tab_offset3() + (size_t)jobs.n * tstride * sizeof(int) <= dyn_bytes;
 
     if (tid == 0) {
         s_abort = (*(volatile int*)err ? 1 : 0) | (fits ? 0 : 2);
@@ -210,8 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
                     const int buf = i & 1;
                     const uint32_t tuse = (uint32_t)(i >> 1);
-                    const TcGeom& tg = jobs.job[t / per_job].tg;
-                    const int nkb = tg.nkb;
+                    const int nkb = jobs.job[t / per_job].tg.nkb;
                     if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort)) break;
                     tc::tc_fence_after();
                     const uint32_t dbase = tmem + (uint32_t)buf * kBufCols;
@@ -224,17 +242,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                         tc::tc_fence_after();
-                        const uint32_t cls = kb >= tg.nkb0 ? 1u : 0u;
+                        // both classes accumulate into one accumulator per row bin
                         const uint32_t st = tc::smem_u32(base + (size_t)s * kStageBytes);
+                        const uint64_t dA0 = tc::sw128_kmajor_desc(st), dA1 = tc::sw128_kmajor_desc(st + kABytes);
+                        const uint64_t dB = tc::sw128_kmajor_desc(st + 2 * kABytes);
+                        const uint32_t first = kb == 0 ? 0u : 1u;
 #pragma unroll
-                        for (int a = 0; a < 2; ++a) {
-                            const uint32_t d_tmem = dbase + (uint32_t)(2 * a + cls) * kAccCols;
-#pragma unroll
-                            for (int kk = 0; kk < kBK / 32; ++kk) {
-                                const uint32_t acc = (kb != 0 && kb != tg.nkb0) || kk > 0;
-                                tc::mma_f8(d_tmem, tc::sw128_kmajor_desc(st + a * kABytes + 32 * kk),
-                                           tc::sw128_kmajor_desc(st + 2 * kABytes + 32 * kk), idesc, acc);
-                            }
+                        for (int kk = 0; kk < kBK / 32; ++kk) {
+                            // a 32-byte step along K adds 2 to the descriptors' start address field
+                            const uint32_t acc = kk > 0 ? 1u : first;
+                            tc::mma_f8(dbase, dA0 + 2 * kk, dB + 2 * kk, idesc, acc);
+                            tc::mma_f8(dbase + kAccCols, dA1 + 2 * kk, dB + 2 * kk, idesc, acc);
                         }
                         tc::mma_commit(&bar_empty[s]);
                         issued = true;
@@ -256,7 +274,59 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3, h = ew >> 2;  // TMEM lane quarter, column-variable group
         const int row = 32 * q + lane;
         float4* ctx = sCtx + ew * (2 * kColsPerWarp);
+        // pair queue of this warp: qm[s * kQueue + r] holds slot s of record r,
+        // s = (row bin 1, class 0), (row bin 1, class 1), (row bin 2, class 0),
+        // (row bin 2, class 1) over column bins 1, 2; (row bin 0, class 0),
+        // (row bin 0, class 1) over column bins 1, 2; (row bins 1, 2 at column
+        // bin 0) class 0, class 1; (bin 0, bin 0) of class 0 and class 1
+        float2* qm = reinterpret_cast<float2*>(sQueue + (size_t)ew * kQueueWarpBytes);
+        uint4* qid = reinterpret_cast<uint4*>(sQueue + (size_t)ew * kQueueWarpBytes + 9 * 8 * kQueue);
         const float inv_scale = __int_as_float((127 - fbits) << 23);
+        const uint32_t lanes_below = (1u << lane) - 1u;
+        int qn = 0, q_job = 0, q_d = 0;  // queued records, all of job q_job and discretisation q_d
+
+        // Evaluates records 0 .. n-1 of the queue, one per lane: SH2 from the
+        // tables, then both roles' keys, IG(i | m) = SH1(m) - SH2 and IG(m | i) =
+        // SH1(i) - SH2.
+        auto flush = [&](int n) {
+            __syncwarp();
+            if (lane < n) {
+                const K2Job& J = jobs.job[q_job];
+                const int N0 = J.tg.N0, N1 = J.tg.N1;
+                const int* sT0 = sTab + q_job * tstride;
+                const int* sT1 = sT0 + (N0 + 1);
+                const int* sTB = sT1 + (N1 + 1);
+                const float beta0 = J.b0, beta1 = J.b1;
+                float2 s[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) s[k] = qm[k * kQueue + lane];
+                // voxels in row-major (row bin, column bin) order
+                const float2 vox[9] = {s[8],
+                                       make_float2(s[4].x, s[5].x), make_float2(s[4].y, s[5].y),
+                                       make_float2(s[6].x, s[7].x),
+                                       make_float2(s[0].x, s[1].x), make_float2(s[0].y, s[1].y),
+                                       make_float2(s[6].y, s[7].y),
+                                       make_float2(s[2].x, s[3].x), make_float2(s[2].y, s[3].y)};
+                int sh2 = 0;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) sh2 += voxel32(sT0, sT1, sTB, N0, N1, N, vox[k], beta0, beta1);
+                const uint4 id = qid[lane];  // vi, vm, SH1(i), SH1(m) (int32 fixed point)
+                const uint32_t dM = (uint32_t)q_d * (uint32_t)M;
+                if constexpr (kDump) {
+                    const unsigned long long np = (unsigned long long)M * (M - 1) / 2;
+                    const unsigned long long rank =
+                        (unsigned long long)id.x * (2ull * M - id.x - 1) / 2 + (unsigned long long)(id.y - id.x - 1);
+                    uint32_t* o = dump + ((unsigned long long)q_d * np + rank) * 9;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k)
+                        o[k] = (uint32_t)f2i_exact(vox[k].x - beta0) | ((uint32_t)f2i_exact(vox[k].y - beta1) << 16);
+                }
+                atomicMax(J.keys + id.x, pack_key((float)((int)id.w - sh2) * inv_scale, dM + id.y));
+                atomicMax(J.keys + id.y, pack_key((float)((int)id.z - sh2) * inv_scale, dM + id.x));
+            }
+            __syncwarp();
+        };
+
         int i = 0;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
             if (__any_sync(0xffffffffu, *abort != 0)) break;
@@ -265,11 +335,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int job = t / per_job, r = t - job * per_job, dl = r / n_items;
             const int2 item = items[r - dl * n_items];
             const int d = d0 + dl;
+            if (qn > 0 && (job != q_job || d != q_d)) {  // warp-uniform
+                flush(qn);
+                qn = 0;
+            }
+            q_job = job;
+            q_d = d;
             const K2Job& J = jobs.job[job];
             const int N0 = J.tg.N0, N1 = J.tg.N1;
-            const int* sT0 = sTab + job * tstride;
-            const int* sT1 = sT0 + (N0 + 1);
-            const int* sTB = sT1 + (N1 + 1);
             unsigned long long* keys = J.keys;
             const float beta0 = J.b0, beta1 = J.b1;
             const int vi = item.x * kRowVars + row;                  // row variable
@@ -278,9 +351,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int* c1 = J.cnt1 + (size_t)d * M * 4;
             const long long* s1 = J.sh1 + (size_t)d * M;
             const bool irow = vi < M;
-            // column context, staged by lanes 0-7 of the warp: class-0 counts of
-            // bins 1, 2; class-1 counts of bins 1, 2; SH1 and key in units of
-            // 4 ln 2 nats; SH1 as int32 fixed point
+            // column context, staged by lanes 0-15 of the warp: smoothed class-0
+            // counts of bins 1, 2 and class-1 counts of bins 1, 2 (count + beta);
+            // SH1 and key in units of 4 ln 2 nats; SH1 as int32 fixed point
             __syncwarp();
             if (lane < kColsPerWarp) {
                 const int vc = vm0 + lane;
@@ -288,125 +361,119 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int4 cc = cok ? *reinterpret_cast<const int4*>(c1 + (size_t)vc * 4) : make_int4(0, 0, 0, 0);
                 const long long s = cok ? s1[vc] : 0ll;
                 const unsigned long long kc = cok ? __ldcg(keys + vc) : 0ull;
-                ctx[2 * lane] = make_float4(i2f_exact(cc.x), i2f_exact(cc.z), i2f_exact(cc.y), i2f_exact(cc.w));
+                ctx[2 * lane] = make_float4(i2f_exact(cc.x) + beta0, i2f_exact(cc.z) + beta0,
+                                            i2f_exact(cc.y) + beta1, i2f_exact(cc.w) + beta1);
                 ctx[2 * lane + 1] = make_float4((float)s * kFx32ToCount, cok ? key_ig_count(kc) : 0.0f,
                                                 __int_as_float(fx_narrow(s, fbits)), 0.0f);
             }
             __syncwarp();
-            // row context: class-c count of bin a (ni_c_a), of bin 0 (R_c)
+            // row context, smoothed: class-c count of bin a + 1 plus beta_c
+            // (ni_c_a), of bin 0 plus 3 beta_c (R_c)
             const int4 rc = irow ? *reinterpret_cast<const int4*>(c1 + (size_t)vi * 4) : make_int4(0, 0, 0, 0);
-            const float ni_0_0 = i2f_exact(rc.x), ni_1_0 = i2f_exact(rc.y), ni_0_1 = i2f_exact(rc.z),
-                        ni_1_1 = i2f_exact(rc.w);
-            const float R_0 = i2f_exact(N0 - rc.x - rc.z), R_1 = i2f_exact(N1 - rc.y - rc.w);
+            const float ni_0_0 = i2f_exact(rc.x) + beta0, ni_1_0 = i2f_exact(rc.y) + beta1;
+            const float ni_0_1 = i2f_exact(rc.z) + beta0, ni_1_1 = i2f_exact(rc.w) + beta1;
+            const float R_0 = i2f_exact(N0 - rc.x - rc.z) + 3.0f * beta0;
+            const float R_1 = i2f_exact(N1 - rc.y - rc.w) + 3.0f * beta1;
             const long long s1i = irow ? s1[vi] : 0ll;
             const int shi = fx_narrow(s1i, fbits);
             const float shi_c = (float)s1i * kFx32ToCount;
-            float keyi_c = irow ? key_ig_count(__ldcg(keys + vi)) : 0.0f;
-            const uint32_t dM = (uint32_t)d * (uint32_t)M;
+            const float keyi_c = irow ? key_ig_count(__ldcg(keys + vi)) : 0.0f;
             const float2 B0 = make_float2(beta0, beta0), B1 = make_float2(beta1, beta1);
 
             if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort))) break;  // warp-uniform
             tc::tc_fence_after();
-            unsigned long long ki = 0ull;
             const bool live = (item.x * kRowVars + 32 * q) < M && vm0 < M;  // warp-uniform
             const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kBufCols +
                                    (uint32_t)(2 * kColsPerWarp * h);
 #pragma unroll 1
-            for (int hf = 0; hf < 2; ++hf) {
-                // accumulator k = 2 a + class (row bin a + 1), columns 2 j + b (column bin b + 1)
-                uint32_t v[4][8];
+            for (int pass = 0; pass < kColsPerWarp / kColsPerPass; ++pass) {
+                // accumulator a (row bin a + 1), columns 2 j + b (column bin b + 1):
+                // n0 + 4096 n1
+                uint32_t v[2][2 * kColsPerPass];
                 if (live) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) tc::tmem_ld8(taddr + (uint32_t)k * kAccCols + 8u * hf, v[k]);
+                    tc::tmem_ld16(taddr + 2u * kColsPerPass * pass, v[0]);
+                    tc::tmem_ld16(taddr + kAccCols + 2u * kColsPerPass * pass, v[1]);
                     tc::tmem_ld_wait();
                 }
-                if (hf == 1) {
+                if (pass == kColsPerWarp / kColsPerPass - 1) {
                     // this thread's last TMEM read of the tile: the buffer may be refilled
                     tc::tc_fence_before();
                     tc::mbar_arrive(&bar_tempty[buf]);
                 }
                 if (!live) continue;
 #pragma unroll
-                for (int jj = 0; jj < kColsPerWarp / 2; ++jj) {
-                    const int jv = 4 * hf + jj;
+                for (int jj = 0; jj < kColsPerPass; ++jj) {
+                    const int jv = kColsPerPass * pass + jj;
                     const int vm = vm0 + jv;
                     const bool ok = vi < vm && vm < M;
                     const float4 cA = ctx[2 * jv], cB = ctx[2 * jv + 1];
-                    // counts with both bins >= 1: x_a_c = (row bin a+1 with column bins 1, 2) of class c
-                    const float2 x_0_0 = make_float2(__uint_as_float(v[0][2 * jj]), __uint_as_float(v[0][2 * jj + 1]));
-                    const float2 x_0_1 = make_float2(__uint_as_float(v[1][2 * jj]), __uint_as_float(v[1][2 * jj + 1]));
-                    const float2 x_1_0 = make_float2(__uint_as_float(v[2][2 * jj]), __uint_as_float(v[2][2 * jj + 1]));
-                    const float2 x_1_1 = make_float2(__uint_as_float(v[3][2 * jj]), __uint_as_float(v[3][2 * jj + 1]));
-                    // the rest of the 3 x 3 table by inclusion-exclusion (exact integer floats):
-                    // u_c = row bin 0 with column bins 1, 2; w_c = row bins 1, 2 with column bin 0
+                    // counts with both bins >= 1: x_a_c = (row bin a + 1 with column
+                    // bins 1, 2) of class c, and their smoothed values m_a_c
+                    float2 x_0_0, x_0_1, x_1_0, x_1_1;
+                    split_classes(make_float2(__uint_as_float(v[0][2 * jj]), __uint_as_float(v[0][2 * jj + 1])), x_0_0,
+                                  x_0_1);
+                    split_classes(make_float2(__uint_as_float(v[1][2 * jj]), __uint_as_float(v[1][2 * jj + 1])), x_1_0,
+                                  x_1_1);
+                    const float2 m_0_0 = add2(x_0_0, B0), m_0_1 = add2(x_0_1, B1);
+                    const float2 m_1_0 = add2(x_1_0, B0), m_1_1 = add2(x_1_1, B1);
+                    // the other voxels by inclusion-exclusion from the smoothed margins
+                    // (each carries beta once): u_c row bin 0 with column bins 1, 2;
+                    // w_c row bins 1, 2 with column bin 0; z_c bin 0 with bin 0
                     const float2 u_0 = sub2(sub2(make_float2(cA.x, cA.y), x_0_0), x_1_0);
                     const float2 u_1 = sub2(sub2(make_float2(cA.z, cA.w), x_0_1), x_1_1);
                     const float2 w_0 = make_float2(ni_0_0 - x_0_0.x - x_0_0.y, ni_0_1 - x_1_0.x - x_1_0.y);
                     const float2 w_1 = make_float2(ni_1_0 - x_0_1.x - x_0_1.y, ni_1_1 - x_1_1.x - x_1_1.y);
-                    const float z_0 = R_0 - u_0.x - u_0.y, z_1 = R_1 - u_1.x - u_1.y;  // voxel (0, 0)
+                    const float z_0 = R_0 - u_0.x - u_0.y, z_1 = R_1 - u_1.x - u_1.y;
                     bool need = ok;
                     if (use_bound) {
                         // sum over the 9 voxels of m0 m1 / (m0 + m1) as one fraction,
                         // two voxels per packed lane pair
-                        const float2 ma0 = add2(x_0_0, B0), ma1 = add2(x_0_1, B1);
-                        const float2 mb0 = add2(x_1_0, B0), mb1 = add2(x_1_1, B1);
-                        const float2 mc0 = add2(u_0, B0), mc1 = add2(u_1, B1);
-                        const float2 md0 = add2(w_0, B0), md1 = add2(w_1, B1);
-                        const float2 pna = mul2(ma0, ma1), psa = add2(ma0, ma1);
-                        const float2 pnb = mul2(mb0, mb1), psb = add2(mb0, mb1);
-                        const float2 pnc = mul2(mc0, mc1), psc = add2(mc0, mc1);
-                        const float2 pnd = mul2(md0, md1), psd = add2(md0, md1);
+                        const float2 pna = mul2(m_0_0, m_0_1), psa = add2(m_0_0, m_0_1);
+                        const float2 pnb = mul2(m_1_0, m_1_1), psb = add2(m_1_0, m_1_1);
+                        const float2 pnc = mul2(u_0, u_1), psc = add2(u_0, u_1);
+                        const float2 pnd = mul2(w_0, w_1), psd = add2(w_0, w_1);
                         const float2 nab = fma2(pnb, psa, mul2(pna, psb)), dab = mul2(psa, psb);
                         const float2 ncd = fma2(pnd, psc, mul2(pnc, psd)), dcd = mul2(psc, psd);
                         const float2 n4 = fma2(ncd, dab, mul2(nab, dcd)), d4 = mul2(dab, dcd);
                         float num = fmaf(n4.x, d4.y, n4.y * d4.x), den = d4.x * d4.y;
-                        const float ms0 = z_0 + beta0, ms1 = z_1 + beta1;
-                        num = fmaf(num, ms0 + ms1, ms0 * ms1 * den);
-                        den *= ms0 + ms1;
+                        num = fmaf(num, z_0 + z_1, z_0 * z_1 * den);
+                        den *= z_0 + z_1;
                         // largest SH2 (units of 4 ln 2 nats) that lets one role reach its key
                         const float hi = fmaxf(cB.x - keyi_c, shi_c - cB.y);
                         const float lim = fmaf(fabsf(hi), kBoundRel, hi + kBoundAbs);
                         need = ok && num <= lim * den;
                     }
-                    if (!__any_sync(0xffffffffu, need)) continue;
-                    unsigned long long k_m = 0ull;
-                    if (need) {
-                        const int sh2 = voxel32(sT0, sT1, sTB, N0, N1, N, z_0, z_1) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, u_0.x, u_1.x) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, u_0.y, u_1.y) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, w_0.x, w_1.x) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, x_0_0.x, x_0_1.x) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, x_0_0.y, x_0_1.y) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, w_0.y, w_1.y) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, x_1_0.x, x_1_1.x) +
-                                        voxel32(sT0, sT1, sTB, N0, N1, N, x_1_0.y, x_1_1.y);
-                        if constexpr (kDump) {
-                            const unsigned long long np = (unsigned long long)M * (M - 1) / 2;
-                            const unsigned long long rank =
-                                (unsigned long long)vi * (2ull * M - vi - 1) / 2 + (unsigned long long)(vm - vi - 1);
-                            uint32_t* o = dump + ((unsigned long long)d * np + rank) * 9;
-                            // row-major (row bin, column bin), class 0 | class 1 << 16
-                            const float c0[9] = {z_0, u_0.x, u_0.y, w_0.x, x_0_0.x, x_0_0.y, w_0.y, x_1_0.x, x_1_0.y};
-                            const float c1v[9] = {z_1, u_1.x, u_1.y, w_1.x, x_0_1.x, x_0_1.y, w_1.y, x_1_1.x, x_1_1.y};
-#pragma unroll
-                            for (int e = 0; e < 9; ++e)
-                                o[e] = (uint32_t)f2i_exact(c0[e]) | ((uint32_t)f2i_exact(c1v[e]) << 16);
-                        }
-                        const int shm = __float_as_int(cB.z);
-                        // IG(i | m) = SH1(m) - SH2
-                        const float gi = (float)(shm - sh2) * inv_scale;
-                        ki = umax64(ki, pack_key(gi, dM + (uint32_t)vm));
-                        keyi_c = fmaxf(keyi_c, gi * kInv4Ln2);  // a reached IG tightens the bound
-                        // IG(m | i) = SH1(i) - SH2
-                        const float gm = (float)(shi - sh2) * inv_scale;
-                        k_m = pack_key(gm, dM + (uint32_t)vi);
+                    const uint32_t mask = __ballot_sync(0xffffffffu, need);
+                    if (mask == 0u) continue;
+                    // queue the pairs that need their lookups; a full queue is evaluated
+                    const int cnt = __popc(mask), rank = __popc(mask & lanes_below), room = kQueue - qn;
+                    auto put = [&](int slot) {
+                        qm[0 * kQueue + slot] = m_0_0;
+                        qm[1 * kQueue + slot] = m_0_1;
+                        qm[2 * kQueue + slot] = m_1_0;
+                        qm[3 * kQueue + slot] = m_1_1;
+                        qm[4 * kQueue + slot] = u_0;
+                        qm[5 * kQueue + slot] = u_1;
+                        qm[6 * kQueue + slot] = w_0;
+                        qm[7 * kQueue + slot] = w_1;
+                        qm[8 * kQueue + slot] = make_float2(z_0, z_1);
+                        qid[slot] = make_uint4((uint32_t)vi, (uint32_t)vm, (uint32_t)shi, __float_as_uint(cB.z));
+                    };
+                    // a full queue is evaluated as often as this column's pairs fill it
+                    int room_left = room, placed = 0;
+                    if (need && rank < room_left) put(qn + rank);
+                    while (cnt - placed >= room_left) {  // warp-uniform
+                        flush(kQueue);
+                        placed += room_left;
+                        room_left = kQueue;
+                        qn = 0;
+                        if (need && rank >= placed && rank < placed + room_left) put(rank - placed);
                     }
-                    const unsigned long long mk = warp_max_key(k_m);
-                    if (lane == 0 && mk) atomicMax(keys + vm, mk);
+                    qn += cnt - placed;
                 }
             }
-            if (ki) atomicMax(keys + vi, ki);
         }
+        if (qn > 0 && !__any_sync(0xffffffffu, *abort != 0)) flush(qn);
     }
 
     tc::tc_fence_before();
@@ -415,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0 && *abort) atomicOr(err, *abort);
 }
 
-// Tiles (row block it of 128 variables, column block mt of 32 variables) with
+// Tiles (row block it of 128 variables, column block mt of 64 variables) with
 // column block start >= row block start: every unordered pair once, the pairs
 // i < m of the diagonal tiles selected in the kernel.
 void build_k2tc3_items(int M, std::vector<int2>& items) {
@@ -426,26 +493,32 @@ void build_k2tc3_items(int M, std::vector<int2>& items) {
         for (int mt = it * ratio; mt < nc; ++mt) items.push_back(make_int2(it, mt));
 }
 
+// the kernel runs kStages pipeline stages: any other count does not fit
 size_t k2tc3_smem_bytes(int N, int n_jobs, int stages) {
-    return tab_offset3(stages) + (size_t)n_jobs * tab_stride3(N) * sizeof(int) + 1024;
+    if (stages != kStages) return ~(size_t)0;
+    return tab_offset3() + (size_t)n_jobs * tab_stride3(N) * sizeof(int) + 1024;
 }
+
+bool k2tc3_counts_fit(int N0, int N1) { return N0 >= 1 && N1 >= 1 && N0 < 4096 && N1 < 4096; }
+
+uint32_t k2tc3_class1_byte() { return 0x68; }  // E4M3 64.0
 
 cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int d0, int nd, int dstride,
                          const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,
                          uint32_t* dump) {
     if (n_items == 0 || jobs.n == 0) return cudaSuccess;
-    if (jobs.n < 1 || jobs.n > kMaxK2Jobs || (stages != 3 && stages != 4) || (dump && (jobs.n != 1 || stages != 4)))
-        return cudaErrorInvalidValue;
+    if (jobs.n < 1 || jobs.n > kMaxK2Jobs || stages != kStages || (dump && jobs.n != 1)) return cudaErrorInvalidValue;
     if (Kp <= 0 || Kp % kBK != 0 || M < 1 || zdim < 1) return cudaErrorInvalidValue;
     const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1;
     for (int j = 0; j < jobs.n; ++j) {
         const TcGeom& tg = jobs.job[j].tg;
-        if (tg.N0 + tg.N1 != N || tg.Kp > Kp || tg.nkb * kBK != tg.Kp || tg.nkb0 < 1 || tg.nkb0 >= tg.nkb)
+        if (tg.N0 + tg.N1 != N || !k2tc3_counts_fit(tg.N0, tg.N1) || tg.Kp > Kp || tg.nkb * kBK != tg.Kp ||
+            tg.nkb0 < 1 || tg.nkb0 >= tg.nkb)
             return cudaErrorInvalidValue;
         // the bound needs pseudocounts that keep its fraction away from 0 and infinity
         if (!(jobs.job[j].b0 >= 1e-3f && jobs.job[j].b1 >= 1e-3f)) bound = false;
     }
-    // A: the rows of one bin (every second row) of 128 variables; B: 64 consecutive rows
+    // A: the rows of one bin (every second row) of 128 variables; B: 128 consecutive rows
     CUtensorMap map_a, map_b;
     const cuuint64_t kp = (cuuint64_t)Kp, rows = 2 * (cuuint64_t)M;
     const cuuint64_t dims_a[4] = {kp, 2, (cuuint64_t)M, (cuuint64_t)zdim};
@@ -458,8 +531,7 @@ cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs
     if (e != cudaSuccess) return e;
     if ((e = make_tiled_map_u8(&map_b, oh, 3, dims_b, str_b, box_b)) != cudaSuccess) return e;
     const size_t smem = k2tc3_smem_bytes(N, jobs.n, stages);
-    const void* fn = dump ? (const void*)k2tc3_kernel<4, true>
-                          : (stages == 4 ? (const void*)k2tc3_kernel<4, false> : (const void*)k2tc3_kernel<3, false>);
+    const void* fn = dump ? (const void*)k2tc3_kernel<true> : (const void*)k2tc3_kernel<false>;
     if ((e = ensure_dynamic_smem(fn, smem)) != cudaSuccess) return e;
     // the register split inside the kernel needs exactly kRegsLaunch registers per thread
     cudaFuncAttributes fa;
@@ -473,14 +545,11 @@ cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
     const int prune_on = bound ? 1 : 0;
     if (dump)
-        k2tc3_kernel<4, true><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items,
-                                                            fbits, err, prune_on, dump);
-    else if (stages == 4)
-        k2tc3_kernel<4, false><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items,
-                                                             fbits, err, prune_on, nullptr);
+        k2tc3_kernel<true><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items, fbits,
+                                                         err, prune_on, dump);
     else
-        k2tc3_kernel<3, false><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items,
-                                                             fbits, err, prune_on, nullptr);
+        k2tc3_kernel<false><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items, fbits,
+                                                          err, prune_on, nullptr);
     return cudaGetLastError();
 }
 

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
                                                          const int* __restrict__ perm, PlaneGeom g,
                                                          uint32_t* __restrict__ planes, uint8_t* __restrict__ codes,
                                                          float* __restrict__ thr_out, uint8_t* __restrict__ onehot,
-                                                         TcGeom tg, int scol) {
+                                                         TcGeom tg, int scol, uint32_t class1_byte) {
     extern __shared__ __align__(16) float smem[];
     float* s = smem;           // [scol]: sorted column, then the class-sorted one-hot staging
     float* thr = smem + scol;  // [D][c-1] thresholds
@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
             for (int w = tid; w < ngroup * D; w += blockDim.x) {
                 const int gi = w % ngroup, d = w / ngroup;
                 const int pos0 = gi * 32;
+                const uint32_t one = pos0 < tg.K0p ? 0x38u : class1_byte;  // a group lies in one class range
                 int pw = -1;  // plane word of this group, if any
                 if (pos0 < tg.K0p) {
                     if (gi < g.W0) pw = gi;
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
                             const float xv_ = xs[4 * q + k];
                             // code == a  <=>  x >= thr[a-1] and not x >= thr[a] (thresholds ascending)
                             const bool in = xv_ >= lo && !(xv_ >= hi);
-                            b |= in ? 0x38u << (8 * k) : 0u;
+                            b |= in ? one << (8 * k) : 0u;
                             bits |= in ? 1u << (4 * q + k) : 0u;
                         }
                         wd[q] = b;
@@ -505,7 +506,8 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
 
 cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
                               uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
-                              uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st) {
+                              uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st,
+                              uint32_t class1_byte) {
     int npad = 1;
     while (npad < N) npad <<= 1;
     // sorted column, reused for the class-sorted one-hot staging (Kp may exceed npad)
@@ -518,12 +520,12 @@ cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int
         e = ensure_dynamic_smem((const void*)discretize_kernel<float>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<float><<<M, 512, smem, st>>>((const float*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                       planes, codes, thr, onehot, tg, (int)scol);
+                                                       planes, codes, thr, onehot, tg, (int)scol, class1_byte);
     } else {
         e = ensure_dynamic_smem((const void*)discretize_kernel<int8_t>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<int8_t><<<M, 512, smem, st>>>((const int8_t*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                        planes, codes, thr, onehot, tg, (int)scol);
+                                                        planes, codes, thr, onehot, tg, (int)scol, class1_byte);
     }
     return cudaGetLastError();
 }
