@@ -401,7 +401,7 @@ def run_gpu(args, rank, world, local_rank):
     if peaks:
         line["peaks"] = peaks
     if args.configs and not args.small:
-        line["configs"] = configs_run(local_rank, args)
+        line["configs"] = configs_run(local_rank, args, peaks)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -475,7 +475,7 @@ def _time_scan(torch, fn, reps: int):
     return float(np.median(ts))
 
 
-def configs_run(device: int, args):
+def configs_run(device: int, args, peaks=None):
     """The other workloads of the method's configurations, each timed on the
     device and compared with the FP64 oracle on sampled variables (all of them
     for the small case):
@@ -523,11 +523,12 @@ def configs_run(device: int, args):
     out["parity_N2000_M500_k3_c2"] = {"timing": "the bench step's k = 3 launch (roofline)",
                                       **_parity(codes, ds.y, 2, 3, 0.25, *g, ref, v3)}
     if args.batch_configs:
-        out["batched_N1000_M20000_k2_c3"] = batched_check(device, args.batch_folds, args.batch_perms, args.batch_m)
+        out["batched_N1000_M20000_k2_c3"] = batched_check(device, args.batch_folds, args.batch_perms, args.batch_m,
+                                                           peaks)
     return out
 
 
-def batched_check(device: int, n_folds: int, n_perms: int, M: int):
+def batched_check(device: int, n_folds: int, n_perms: int, M: int, peaks=None):
     """The batched workload in one mdfs_max_ig_batch call, timed with CUDA
     events; three jobs spot-checked against the oracle and one job bit for bit
     against the single-job scan of its resampled data."""
@@ -547,11 +548,14 @@ def batched_check(device: int, n_folds: int, n_perms: int, M: int):
     mdfs.max_ig_batch(x, y, sid[:1], ypd[:1], n_jobs=1, k=2, divisions=div, discretizations=D, range_=r, seed=seed)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mdfs.profile(True)  # per-launch CUDA events, no synchronisation
     a.record()
     ig, tu, di = mdfs.max_ig_batch(x, y, sid, ypd, n_jobs=J, k=2, divisions=div, discretizations=D, range_=r,
                                    pc_xi=xi, seed=seed)
     b.record()
     b.synchronize()
+    prof = mdfs.profile_report()
+    mdfs.profile(False)
     secs = a.elapsed_time(b) / 1e3
     ig, tu, di = ig.cpu().numpy(), tu.cpu().numpy(), di.cpu().numpy()
     pairs = ds.info["pairs"]
@@ -570,7 +574,20 @@ def batched_check(device: int, n_folds: int, n_perms: int, M: int):
     w = mdfs.max_ig(torch.from_numpy(np.ascontiguousarray(ds.x[:, si[j]])).to(dev),
                     torch.from_numpy(ds.y[yp[j][si[j]]]).to(dev), 2, div, D, r, xi, seed)
     single_equal = all(np.array_equal(u, v.cpu().numpy()) for u, v in zip((ig[j], tu[j], di[j]), w))
-    return {"jobs": J, "seconds": secs, "evals_per_s": J * math.comb(M, 2) * D / secs,
+    # the tensor-core k = 2 kernel against the measured E4M3 rate: useful
+    # counting work per (pair, discretisation) is the 2 x 2 block of bin
+    # indicator dot products over the N samples, 2 (c - 1)^2 N FLOP
+    k2 = prof.get("k2", {"count": 0, "ms": 0.0})
+    useful = J * math.comb(M, 2) * D * 2.0 * div * div * N
+    roof = None
+    if peaks and k2["ms"] > 0:
+        achieved = useful / (k2["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k2tc3_kernel", "launches": k2["count"], "kernel_s": k2["ms"] / 1e3,
+                "achieved": achieved, "peak": peaks["fp8_mma_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["fp8_mma_tflops"], "useful_fp8_flop": useful,
+                "peak_note": "dense E4M3 of measured (tcgen05 kind::f8f6f4 microbenchmark, this run)"}
+    return {"jobs": J, "seconds": secs, "evals_per_s": J * math.comb(M, 2) * D / secs, "roofline": roof,
+            "kernels": prof,
             "max_abs_err": max(c["max_abs_err"] for c in checks),
             "argmax_bad": sum(c["argmax_bad"] for c in checks),
             "argmax_equal": sum(c["argmax_equal"] for c in checks),
@@ -751,10 +768,18 @@ def run_batched(args):
     ig0, tu0 = ig[0].cpu().numpy(), tu[0].cpu().numpy()
     for a, b in pairs:
         found += int(tu0[a, 0] == b) + int(tu0[b, 0] == a)
+    roof = None
+    if not args.no_peaks and prof.get("k2", {}).get("ms"):
+        peaks = peaks_run(0)
+        useful = J * math.comb(M, 2) * D * 2.0 * div * div * N  # 2 (c-1)^2 N FLOP per (pair, discretisation)
+        achieved = useful / (prof["k2"]["ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k2tc3_kernel", "achieved": achieved, "peak": peaks["fp8_mma_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["fp8_mma_tflops"],
+                "peak_note": "dense E4M3 of measured (tcgen05 kind::f8f6f4 microbenchmark, this run)"}
     line = {"metric": "batched k=2 tuple*disc evals/sec", "value": evals / secs, "unit": UNIT, "n_gpus": 1,
             "jobs": J, "seconds": secs, "config": {"N": N, "M": M, "divisions": div, "discretizations": D,
                                                    "folds": n_folds, "perms": n_perms},
-            "kernels": {k: v for k, v in prof.items()},
+            "roofline": roof, "kernels": {k: v for k, v in prof.items()},
             "xor_partners_recovered_job0": f"{found}/{2 * len(pairs)}"}
     print(json.dumps(line), flush=True)
     return 0

@@ -59,7 +59,7 @@ constexpr int kStages = 3;
 // column-variable context per epilogue warp: 2 float4 per column variable
 constexpr uint32_t kCtxBytes = kEpiWarps * kColsPerWarp * 32;
 // pair queue per epilogue warp: kQueue records of the 9 voxels' smoothed
-// class counts (float2, structure of arrays) and (vi, vm, SH1(i), SH1(m))
+// class counts (two float arrays, structure of arrays) and (vi, vm, SH1(i), SH1(m))
 constexpr int kQueue = 16;
 constexpr uint32_t kQueueWarpBytes = kQueue * (9 * 8 + 16);
 constexpr uint32_t kQueueBytes = kEpiWarps * kQueueWarpBytes;
@@ -274,20 +274,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3, h = ew >> 2;  // TMEM lane quarter, column-variable group
         const int row = 32 * q + lane;
         float4* ctx = sCtx + ew * (2 * kColsPerWarp);
-        // pair queue of this warp: qm[s * kQueue + r] holds slot s of record r,
-        // s = (row bin 1, class 0), (row bin 1, class 1), (row bin 2, class 0),
-        // (row bin 2, class 1) over column bins 1, 2; (row bin 0, class 0),
-        // (row bin 0, class 1) over column bins 1, 2; (row bins 1, 2 at column
-        // bin 0) class 0, class 1; (bin 0, bin 0) of class 0 and class 1
-        float2* qm = reinterpret_cast<float2*>(sQueue + (size_t)ew * kQueueWarpBytes);
-        uint4* qid = reinterpret_cast<uint4*>(sQueue + (size_t)ew * kQueueWarpBytes + 9 * 8 * kQueue);
+        // pair queue of this warp: q0 / q1 [v * kQueue + r] hold the smoothed
+        // class-0 / class-1 counts of voxel v (row-major (row bin, column bin))
+        // of record r; qid[r] = (vi, vm, SH1(i), SH1(m))
+        float* q0 = reinterpret_cast<float*>(sQueue + (size_t)ew * kQueueWarpBytes);
+        float* q1 = q0 + 9 * kQueue;
+        uint4* qid = reinterpret_cast<uint4*>(q1 + 9 * kQueue);
         const float inv_scale = __int_as_float((127 - fbits) << 23);
         const uint32_t lanes_below = (1u << lane) - 1u;
         int qn = 0, q_job = 0, q_d = 0;  // queued records, all of job q_job and discretisation q_d
 
         // Evaluates records 0 .. n-1 of the queue, one per lane: SH2 from the
         // tables, then both roles' keys, IG(i | m) = SH1(m) - SH2 and IG(m | i) =
-        // SH1(i) - SH2.
+        // SH1(i) - SH2.  A rolled voxel loop keeps this code, inlined at every
+        // call, short.
         auto flush = [&](int n) {
             __syncwarp();
             if (lane < n) {
@@ -297,30 +297,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int* sT1 = sT0 + (N0 + 1);
                 const int* sTB = sT1 + (N1 + 1);
                 const float beta0 = J.b0, beta1 = J.b1;
-                float2 s[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) s[k] = qm[k * kQueue + lane];
-                // voxels in row-major (row bin, column bin) order
-                const float2 vox[9] = {s[8],
-                                       make_float2(s[4].x, s[5].x), make_float2(s[4].y, s[5].y),
-                                       make_float2(s[6].x, s[7].x),
-                                       make_float2(s[0].x, s[1].x), make_float2(s[0].y, s[1].y),
-                                       make_float2(s[6].y, s[7].y),
-                                       make_float2(s[2].x, s[3].x), make_float2(s[2].y, s[3].y)};
-                int sh2 = 0;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) sh2 += voxel32(sT0, sT1, sTB, N0, N1, N, vox[k], beta0, beta1);
                 const uint4 id = qid[lane];  // vi, vm, SH1(i), SH1(m) (int32 fixed point)
-                const uint32_t dM = (uint32_t)q_d * (uint32_t)M;
+                uint32_t* o = nullptr;
                 if constexpr (kDump) {
                     const unsigned long long np = (unsigned long long)M * (M - 1) / 2;
                     const unsigned long long rank =
                         (unsigned long long)id.x * (2ull * M - id.x - 1) / 2 + (unsigned long long)(id.y - id.x - 1);
-                    uint32_t* o = dump + ((unsigned long long)q_d * np + rank) * 9;
-#pragma unroll
-                    for (int k = 0; k < 9; ++k)
-                        o[k] = (uint32_t)f2i_exact(vox[k].x - beta0) | ((uint32_t)f2i_exact(vox[k].y - beta1) << 16);
+                    o = dump + ((unsigned long long)q_d * np + rank) * 9;
                 }
+                int sh2 = 0;
+#pragma unroll 1
+                for (int v = 0; v < 9; ++v) {
+                    const int n0 = f2i_exact(q0[v * kQueue + lane] - beta0), n1 = f2i_exact(q1[v * kQueue + lane] - beta1);
+                    sh2 += tab32(sTB, n0 + n1, N) - tab32(sT0, n0, N0) - tab32(sT1, n1, N1);
+                    if constexpr (kDump) o[v] = (uint32_t)n0 | ((uint32_t)n1 << 16);
+                }
+                const uint32_t dM = (uint32_t)q_d * (uint32_t)M;
                 atomicMax(J.keys + id.x, pack_key((float)((int)id.w - sh2) * inv_scale, dM + id.y));
                 atomicMax(J.keys + id.y, pack_key((float)((int)id.z - sh2) * inv_scale, dM + id.x));
             }
@@ -448,15 +440,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // queue the pairs that need their lookups; a full queue is evaluated
                     const int cnt = __popc(mask), rank = __popc(mask & lanes_below), room = kQueue - qn;
                     auto put = [&](int slot) {
-                        qm[0 * kQueue + slot] = m_0_0;
-                        qm[1 * kQueue + slot] = m_0_1;
-                        qm[2 * kQueue + slot] = m_1_0;
-                        qm[3 * kQueue + slot] = m_1_1;
-                        qm[4 * kQueue + slot] = u_0;
-                        qm[5 * kQueue + slot] = u_1;
-                        qm[6 * kQueue + slot] = w_0;
-                        qm[7 * kQueue + slot] = w_1;
-                        qm[8 * kQueue + slot] = make_float2(z_0, z_1);
+                        const float c0v[9] = {z_0,     u_0.x,   u_0.y, w_0.x, m_0_0.x,
+                                              m_0_0.y, w_0.y,   m_1_0.x, m_1_0.y};
+                        const float c1v[9] = {z_1,     u_1.x,   u_1.y, w_1.x, m_0_1.x,
+                                              m_0_1.y, w_1.y,   m_1_1.x, m_1_1.y};
+#pragma unroll
+                        for (int v = 0; v < 9; ++v) {
+                            q0[v * kQueue + slot] = c0v[v];
+                            q1[v * kQueue + slot] = c1v[v];
+                        }
                         qid[slot] = make_uint4((uint32_t)vi, (uint32_t)vm, (uint32_t)shi, __float_as_uint(cB.z));
                     };
                     // a full queue is evaluated as often as this column's pairs fill it

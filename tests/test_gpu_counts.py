@@ -106,6 +106,25 @@ def test_pair_counts_bit_exact(cuda, M, N, div, D):
         assert np.array_equal(got[d], _pair_counts(codes[d], y, c)), f"discretisation {d}"
 
 
+def test_pair_counts_bit_exact_class_limit(cuda):
+    """Three classes per variable: the k = 2 kernel accumulates n0 + 4096 n1 in
+    one FP32 value; with N1 = 4095 (the largest class size it takes; N = 4700
+    keeps the entropy tables in shared memory) every partial sum is still below
+    2^24 and every count exact."""
+    torch = cuda
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(4095)
+    M, N, div, D = 24, 4700, 2, 1
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    x[3] = np.abs(x[3])  # one variable with most samples in its top bins
+    y = np.zeros(N, dtype=np.uint8)
+    y[rng.permutation(N)[:4095]] = 1
+    codes = oracle.discretize(x, div, D, 0.3, 5)
+    got = mdfs.testing_counts(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), 2, div, D, 0.3, 5)
+    got = got.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got[0], _pair_counts(codes[0], y, div + 1))
+
+
 @pytest.mark.parametrize("div", [1, 2])
 def test_pair_counts_bit_exact_full_size(cuda, div):
     """The 2000 x 500 parity workload with 30 discretisations (the k = 2 launch

@@ -245,6 +245,23 @@ def test_k3_tensor_core_large_class_counts(cuda):
     _check(codes, y, 2, 3, 0.25, *g, ref, range(M))
 
 
+@pytest.mark.parametrize("n1", [4095, 4096])
+def test_k2_three_classes_class_size_limit(cuda, n1):
+    """k = 2 with three classes per variable: one FP32 accumulator per row bin
+    holds n0 + 4096 n1, exact for class sizes below 4096.  At N1 = 4095 the
+    tensor-core kernel runs; at N1 = 4096 the scan takes the bit-plane kernel
+    instead.  Both match the oracle."""
+    rng = np.random.default_rng(n1)
+    M, N = 24, 4700
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = np.zeros(N, dtype=np.uint8)
+    y[rng.permutation(N)[:n1]] = 1
+    codes = oracle.discretize(x, 2, 1, 0.3, 5)
+    ref = oracle.max_ig(codes, y, 3, 2, 0.25)
+    g = _gpu_max_ig(cuda, x, y, 2, 2, 1, 0.3, 0.25, 5)
+    _check(codes, y, 3, 2, 0.25, *g, ref, range(M))
+
+
 def test_k3_permuted_variable_order_and_repeatability(cuda):
     """The triple kernel relabels variables by marginal count and prunes role-e
     updates with the keys found so far.  The same data in two variable orders
