@@ -557,7 +557,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float2 nu0 = make_float2(nu.x, nu.y), nu1 = make_float2(nu.z, nu.w);
                         // class counts of the voxel (1,1,1): X = n0 + 4096 n1, exact in FP32
                         const float X = __uint_as_float(r[j]);
-                        const float x1 = floorf(X * (1.0f / 4096.0f)), x0 = fmaf(x1, -4096.0f, X);
+                        // floor(X / 4096): 2^23 + X 2^-12 rounded toward zero (exact product, one rounding)
+                        const float x1 = __fmaf_rz(X, 1.0f / 4096.0f, 8388608.0f) - 8388608.0f;
+                        const float x0 = fmaf(x1, -4096.0f, X);
                         // pair (a, e) class counts: 4 n in 16-bit fields, read as floats
                         const float q0 = fmaf(__uint_as_float((pcur[j].cnt & 0xFFFFu) | 0x4B000000u), 0.25f,
                                               -2097152.0f);
