@@ -528,6 +528,24 @@ def configs_run(device: int, args, peaks=None):
     return out
 
 
+def k2_roofline(pair_discs: float, N: int, c: int, k2: dict, peaks: dict) -> dict:
+    """Roofline entry of the k = 2 tensor-core kernel: algorithmic work 2 c^2 N
+    FLOP per (pair, discretisation) (every voxel count an N-term dot product of
+    bin indicators), and beside it the work of the products the kernel forms on
+    the tensor cores, 2 (c - 1)^2 N (the bins >= 1; the other voxels follow from
+    the margins)."""
+    secs = k2["ms"] / 1e3
+    useful = pair_discs * 2.0 * c * c * N
+    formed = pair_discs * 2.0 * (c - 1) * (c - 1) * N
+    peak = peaks["fp8_mma_tflops"]
+    return {"bound": "tensor", "kernel": "k2tc3_kernel" if c == 3 else "k2tc_kernel", "launches": k2["count"],
+            "kernel_s": secs, "achieved": useful / secs / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": useful / secs / 1e12 / peak, "algorithmic_flop": useful,
+            "formed_tflops": formed / secs / 1e12, "formed_frac": formed / secs / 1e12 / peak,
+            "unit_note": "2 c^2 N FLOP per (pair, discretisation); formed_*: the 2 (c-1)^2 N the MMAs compute",
+            "peak_note": "dense E4M3 of measured (tcgen05 kind::f8f6f4 microbenchmark, this run)"}
+
+
 def batched_check(device: int, n_folds: int, n_perms: int, M: int, peaks=None):
     """The batched workload in one mdfs_max_ig_batch call, timed with CUDA
     events; three jobs spot-checked against the oracle and one job bit for bit
@@ -574,18 +592,15 @@ def batched_check(device: int, n_folds: int, n_perms: int, M: int, peaks=None):
     w = mdfs.max_ig(torch.from_numpy(np.ascontiguousarray(ds.x[:, si[j]])).to(dev),
                     torch.from_numpy(ds.y[yp[j][si[j]]]).to(dev), 2, div, D, r, xi, seed)
     single_equal = all(np.array_equal(u, v.cpu().numpy()) for u, v in zip((ig[j], tu[j], di[j]), w))
-    # the tensor-core k = 2 kernel against the measured E4M3 rate: useful
-    # counting work per (pair, discretisation) is the 2 x 2 block of bin
-    # indicator dot products over the N samples, 2 (c - 1)^2 N FLOP
+    # the tensor-core k = 2 kernel against the measured E4M3 rate, in the
+    # algorithmic unit of the one-hot formulation: every voxel's class count
+    # is an N-term dot product of bin indicators, 2 c^2 N FLOP per (pair,
+    # discretisation); the kernel forms the 2 x 2 block of bins >= 1 on the
+    # tensor cores (2 (c - 1)^2 N) and derives the other voxels from margins
     k2 = prof.get("k2", {"count": 0, "ms": 0.0})
-    useful = J * math.comb(M, 2) * D * 2.0 * div * div * N
     roof = None
     if peaks and k2["ms"] > 0:
-        achieved = useful / (k2["ms"] / 1e3) / 1e12
-        roof = {"bound": "tensor", "kernel": "k2tc3_kernel", "launches": k2["count"], "kernel_s": k2["ms"] / 1e3,
-                "achieved": achieved, "peak": peaks["fp8_mma_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / peaks["fp8_mma_tflops"], "useful_fp8_flop": useful,
-                "peak_note": "dense E4M3 of measured (tcgen05 kind::f8f6f4 microbenchmark, this run)"}
+        roof = k2_roofline(J * math.comb(M, 2) * D, N, div + 1, k2, peaks)
     return {"jobs": J, "seconds": secs, "evals_per_s": J * math.comb(M, 2) * D / secs, "roofline": roof,
             "kernels": prof,
             "max_abs_err": max(c["max_abs_err"] for c in checks),
@@ -770,12 +785,7 @@ def run_batched(args):
         found += int(tu0[a, 0] == b) + int(tu0[b, 0] == a)
     roof = None
     if not args.no_peaks and prof.get("k2", {}).get("ms"):
-        peaks = peaks_run(0)
-        useful = J * math.comb(M, 2) * D * 2.0 * div * div * N  # 2 (c-1)^2 N FLOP per (pair, discretisation)
-        achieved = useful / (prof["k2"]["ms"] / 1e3) / 1e12
-        roof = {"bound": "tensor", "kernel": "k2tc3_kernel", "achieved": achieved, "peak": peaks["fp8_mma_tflops"],
-                "unit": "TFLOP/s", "frac": achieved / peaks["fp8_mma_tflops"],
-                "peak_note": "dense E4M3 of measured (tcgen05 kind::f8f6f4 microbenchmark, this run)"}
+        roof = k2_roofline(J * math.comb(M, 2) * D, N, div + 1, prof["k2"], peaks_run(0))
     line = {"metric": "batched k=2 tuple*disc evals/sec", "value": evals / secs, "unit": UNIT, "n_gpus": 1,
             "jobs": J, "seconds": secs, "config": {"N": N, "M": M, "divisions": div, "discretizations": D,
                                                    "folds": n_folds, "perms": n_perms},
