@@ -123,8 +123,17 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
  * sample_idx, y_perm:  [n_jobs][N] int32, host or device; entries in [0, N).
  * ig:                  [n_jobs][M] float; tuples [n_jobs][M][k-1] or NULL;
  *                      best_disc [n_jobs][M] or NULL (host or device).
- * A job whose decision has one class fails the call with MDFS_EDEGENERATE
- * (the message names the job).  Returns after all jobs are complete.
+ * Every job's class sizes are computed in one device pass and read back once;
+ * a job whose decision has one class fails the call with MDFS_EDEGENERATE and
+ * an index outside [0, N) with MDFS_EINVAL (the message names the job), before
+ * any scan runs.  With k = 2 and 2 or 3 classes per variable the jobs run in
+ * chunks, one tensor-core launch per chunk over (job, discretisation, tile)
+ * work items; the environment variable MDFS_BATCH_BYTES (default 8 GB) bounds
+ * the device memory of a chunk's one-hot operands.  The launch's pipeline
+ * depth is chosen by timing on the first call per shape and cached in memory
+ * and in the file named by MDFS_TUNE_FILE (lines "<kernel> M=.. N=.. c=.. D=..
+ * -> <stages>"); MDFS_TUNE=0 takes the deepest pipeline that fits.  The
+ * choice never changes a result.  Returns after all jobs are complete.
  */
 int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_idx, const int32_t* y_perm, int k,
                       int divisions, int discretizations, double range, double pc_xi, uint64_t seed, float* ig,
@@ -284,14 +293,15 @@ int mdfs_select(const mdfs_data* data, int n_contrast, int k, int divisions, int
  * discretizations * M * (divisions * (N/8 + 20) + 16) bytes must stay below
  * the array size.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture begins.  The address is kept until mdfs_release(), which a caller
- * must call after a cudaDeviceReset before the next call.  All calls share the
+ * device, with that device current).  The address is kept until
+ * mdfs_release(), which a caller must call after a cudaDeviceReset before the
+ * next call.  All calls share the
  * array and it keeps the last call's contents: two calls whose work overlaps
  * on the GPU (different streams, or different host threads) race and must not
  * be issued; serialise them.  Every call copies a 16-byte validation result of
  * its inputs to a host buffer and synchronises its stream before the scan
- * kernels are enqueued; with a non-NULL stream the rest is stream-ordered.
+ * kernels are enqueued, so a call cannot be captured into a CUDA graph; with a
+ * non-NULL stream the rest is stream-ordered.
  */
 #define MDFS_NOALLOC_SCRATCH_BYTES (32u << 20)
 int mdfs_max_ig_noalloc(const mdfs_data* data, int k, int divisions, int discretizations, double range,
