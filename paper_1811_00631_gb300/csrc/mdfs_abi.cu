@@ -582,7 +582,9 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     const EmitTable em = emit ? *emit : EmitTable();
     const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_counts_fit(c, n0, n1) &&
                           k2tc_smem_bytes(c, N, 1, 3) <= kK3tcMaxSmem);
-    const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) <= kK3tcMaxSmem);
+    // the triple kernel's layout is fixed (it fits the opt-in shared memory of sm_103a); it needs class sizes
+    // below its table capacities
+    const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) != (size_t)-1);
     TcGeom tg = make_tc_geom(n0, n1);
     if (dump && !use_tc2 && !use_tc3)
         return fail(MDFS_EINVAL, "no tensor-core kernel serves k = %d, %d classes, N0 = %d, N1 = %d", k, c, n0, n1);

@@ -94,6 +94,8 @@ constexpr uint32_t kTabEnd = kTBOff + kTBCap * 4;
 static_assert(kT0Off >= 32768 && kTBOff >= 65536, "guard windows below the tables");
 static_assert(kTBOff + 65536 <= kTabEnd + kStages * 2 * kTileBytes, "guard window above TB");
 constexpr size_t kDynBytes = kTabEnd + 1024 + kStages * (kBBytes + kBK);  // + B stages, OH[b] rows
+// dynamic + static (column contexts, barriers) within the 227 KB a block may opt in to on sm_103a
+static_assert(kDynBytes + (size_t)(kEpiThreads / 32) * kChunk * (16 + 8) + 256 <= 232448, "shared memory layout");
 
 // Waits for completion regardless of an abort (draining in-flight work); bounded.
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
@@ -123,15 +125,12 @@ __device__ __forceinline__ int lds(uint32_t addr) {
 // guard windows of the table layout are sized for
 __device__ __forceinline__ bool counts_ok(int any_or) { return (any_or & (int)0xFFFFC003u) == 0; }
 
-// Per-column constants of an item (n_x: class count of bin 1 of x, n_xy: class
-// count of the voxel (1, 1) of the pair (x, y)).
-struct __align__(16) ColCtx {
-    float2 nu0, nu1;  // per class: (n_be, n_e - n_be) + beta of the class (smoothed counts)
-    float sh_c;       // SH(b, e) in LB units (K3Prune)
-    float thr_c;      // role-e key threshold in LB units (see key_threshold)
-    int sh;           // SH(b, e), int32 fixed point
-    int eo;           // original index of e
-};
+// Per-column constants of an item, in two shared arrays per epilogue warp (n_x:
+// class count of bin 1 of x, n_xy: class count of the voxel (1, 1) of the pair
+// (x, y)): nu = per class (n_be, n_e - n_be) + beta of the class (smoothed
+// counts), class 0 then class 1; sht = (SH(b, e), role-e key threshold) in LB
+// units (K3Prune, key_threshold).  The exact path, taken for few columns,
+// reads SH(b, e) and the original index of e from global memory.
 
 // Bound that lets the epilogue skip the exact SH3 of most triples.  Each
 // voxel's term of SH is E(m0, m1) = f(m0 + m1) - f(m0) - f(m1) with the
@@ -227,7 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    __shared__ ColCtx s_col[kEpiThreads / 32][kChunk];
+    __shared__ float4 s_nu[kEpiThreads / 32][kChunk];
+    __shared__ float2 s_sht[kEpiThreads / 32][kChunk];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int* sT0 = reinterpret_cast<int*>(dsmem_raw + kT0Off);
@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3, h = ew >> 2;
         const int row = 32 * q + lane;
         const float inv_scale = __int_as_float((127 - fbits) << 23);  // 2^-fbits
-        ColCtx* cc = s_col[ew];
+        float4* cnu = s_nu[ew];
+        float2* csht = s_sht[ew];
         bool bad = false;       // inconsistent row or column constants
         uint32_t badbits = 0;   // OR of the pair records' count fields (checked at the end)
         int i = 0;
@@ -488,28 +489,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // column constants of this chunk
                     __syncwarp();
                     const int e = ecol0 + lane;
-                    int n0 = 0, n1 = 0, u0 = 0, u1 = 0, thr = INT_MAX;
-                    ColCtx x{};
+                    int n0 = 0, n1 = 0, u0 = 0, u1 = 0, thr = INT_MAX, esh = 0;
                     if (lane < ncols) {
                         const PairC p = pd[(size_t)b * M + e];
                         n0 = (int)(p.cnt & 0xFFFFu);
                         n1 = (int)(p.cnt >> 16);
                         u0 = 4 * c1[2 * e] - n0;
                         u1 = 4 * c1[2 * e + 1] - n1;
-                        x.sh = p.sh;
-                        x.eo = pm[e];
+                        esh = p.sh;
                         // keys only grow during the scan: a stale value is a valid lower bound
-                        thr = key_threshold(__ldcg(keys + x.eo), fbits);
+                        thr = key_threshold(__ldcg(keys + pm[e]), fbits);
                         if (!counts_ok(n0 | n1 | u0 | u1)) {
                             bad = true;
                             n0 = n1 = u0 = u1 = 0;
                         }
                     }
-                    x.nu0 = make_float2(fmaf((float)n0, 0.25f, fb0), fmaf((float)u0, 0.25f, fb0));
-                    x.nu1 = make_float2(fmaf((float)n1, 0.25f, fb1), fmaf((float)u1, 0.25f, fb1));
-                    x.sh_c = (float)x.sh * prune.fx_to_count;
-                    x.thr_c = (float)thr * prune.fx_to_count;
-                    cc[lane] = x;
+                    cnu[lane] = make_float4(fmaf((float)n0, 0.25f, fb0), fmaf((float)u0, 0.25f, fb0),
+                                            fmaf((float)n1, 0.25f, fb1), fmaf((float)u1, 0.25f, fb1));
+                    csht[lane] = make_float2((float)esh * prune.fx_to_count, (float)thr * prune.fx_to_count);
                     __syncwarp();
                     // pair (a, e) records of the first group, fetched before the accumulator is read
 #pragma unroll
@@ -552,8 +549,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             need |= valid ? 1u << j : 0u;
                             continue;
                         }
-                        const float4 nu = *reinterpret_cast<const float4*>(&cc[c0 + j].nu0);
-                        const float2 sht = *reinterpret_cast<const float2*>(&cc[c0 + j].sh_c);
+                        const float4 nu = cnu[c0 + j];
+                        const float2 sht = csht[c0 + j];
                         const float2 nu0 = make_float2(nu.x, nu.y), nu1 = make_float2(nu.z, nu.w);
                         // class counts of the voxel (1,1,1): X = n0 + 4096 n1, exact in FP32
                         const float X = __uint_as_float(r[j]);
@@ -596,12 +593,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (!__any_sync(0xffffffffu, (need >> j) & 1u)) continue;
                         const int col = c0 + j;
                         const bool valid = arow && col < ncols;
-                        const ColCtx cx = cc[col];
+                        const float4 cxn = cnu[col];
+                        const float cx_thr_c = csht[col].y;
+                        // SH(b, e) and the original index of e (rows and columns outside the
+                        // item read the last column's and are masked out below)
+                        const int ecol = min(ecol0 + col, M - 1);
+                        const int cx_sh = pd[(size_t)b * M + ecol].sh;
+                        const int cx_eo = pm[ecol];
                         // exact column counts (times 4), recovered from the smoothed floats
-                        const uint32_t cn0 = 4u * (uint32_t)__float2int_rn(cx.nu0.x - fb0);
-                        const uint32_t cu0 = 4u * (uint32_t)__float2int_rn(cx.nu0.y - fb0);
-                        const uint32_t cn1 = 4u * (uint32_t)__float2int_rn(cx.nu1.x - fb1);
-                        const uint32_t cu1 = 4u * (uint32_t)__float2int_rn(cx.nu1.y - fb1);
+                        const uint32_t cn0 = 4u * (uint32_t)__float2int_rn(cxn.x - fb0);
+                        const uint32_t cu0 = 4u * (uint32_t)__float2int_rn(cxn.y - fb0);
+                        const uint32_t cn1 = 4u * (uint32_t)__float2int_rn(cxn.z - fb1);
+                        const uint32_t cu1 = 4u * (uint32_t)__float2int_rn(cxn.w - fb1);
                         const uint32_t n0b = uT0 + cn0, n1b = uT1 + cn1, u0b = 2 * uT0 + cu0, u1b = 2 * uT1 + cu1;
                         const uint32_t pae0 = pcur[j].cnt & 0x3FFCu, pae1 = (pcur[j].cnt >> 16) & 0x3FFCu;
                         // X = n0 + 4096 n1, exact in FP32
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                          lds(b100) + lds(b000));
                         if constexpr (kDump) {
                             if (valid)
-                                dump_triple(dump, M, d, ao, (int)bo, cx.eo,
+                                dump_triple(dump, M, d, ao, (int)bo, cx_eo,
                                             {(int)(a111 - uT0), (int)(a011 - uT0), (int)(a101 - uT0),
                                              (int)(a110 - uT0), (int)(a001 - uT0), (int)(a010 - uT0),
                                              (int)(a100 - uT0), (int)(a000 - uT0)},
@@ -635,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                              (int)(b100 - uT1), (int)(b000 - uT1)});
                         }
                         // IG(a | b,e), IG(b | a,e), IG(e | a,b): wrap-around int32 differences
-                        const int ig_a = cx.sh - sh3;
+                        const int ig_a = cx_sh - sh3;
                         const int ig_b = pcur[j].sh - sh3;
                         const int ig_e = valid ? shab - sh3 : INT_MIN;
                         if (valid && ig_a > best_a) {
@@ -650,18 +653,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // lowest lane (lowest new label a) holding it; skipped when no lane
                         // reaches the column's key threshold (taken 1024 units low: the
                         // float form of the threshold is not exact)
-                        const float thr_fx = fmaf(cx.thr_c, prune.count_to_fx, -1024.0f);
+                        const float thr_fx = fmaf(cx_thr_c, prune.count_to_fx, -1024.0f);
                         if (__any_sync(0xffffffffu, valid && (float)ig_e >= thr_fx)) {
                             const int emax = __reduce_max_sync(0xffffffffu, ig_e);
                             const unsigned hit = __ballot_sync(0xffffffffu, ig_e == emax);
                             if (lane == __ffs(hit) - 1)
-                                atomicMax(keys + cx.eo,
+                                atomicMax(keys + cx_eo,
                                           pack_key((float)emax * inv_scale, partner_index(dM, M, (uint32_t)ao, bo)));
                         }
                     }
                 }
-                if (ca >= 0) best_a_eo = cc[ca].eo;
-                if (cb >= 0) best_b_eo = cc[cb].eo;
+                if (ca >= 0) best_a_eo = pm[ecol0 + ca];
+                if (cb >= 0) best_b_eo = pm[ecol0 + cb];
             }
             if (!waited) break;  // the accumulator wait gave up
             tc::tc_fence_before();
