@@ -21,8 +21,8 @@
 // written for the original variables with sorted original partner indices.
 //
 // Work item: (b, a tile of 128 rows, e group of up to 256 columns); one MMA
-// of N = 256 (or 128 for a narrow last group) per 32 samples reuses the
-// masked A tile across both halves of the group.
+// per 32 samples, N = the group's columns rounded up to 16 (256 for a full
+// group), reuses the masked A tile across the whole group.
 //
 // Persistent, warp-specialised kernel (one CTA per SM, 640 threads):
 //   warp 0       TMA producer: A (a rows), B (e rows), OH[b] row per K block,
@@ -321,8 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       } else if (warp == 1) {
         // ------------------------------ MMA issuer --------------------------------
         if (lane == 0 && !*abort) {
-            const uint32_t idesc_n128 = tc::idesc_e4m3_f32(kTile, kTile);
-            const uint32_t idesc_n256 = tc::idesc_e4m3_f32(kTile, kTileE);
+
             uint32_t g = 0;
             int i = 0;
             bool issued = false;
@@ -331,7 +330,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t tuse = (uint32_t)(i >> 1);
                 const int2 item = items[t % n_items];
                 const int e0 = item.x + 1 + (item.y & 0xFFFF) * kTileE;
-                const uint32_t idesc = M - e0 > kTile ? idesc_n256 : idesc_n128;
+                // the group's columns rounded up to the MMA's N granularity of 16 (the
+                // accumulator columns past them are never read)
+                const int ncol = min(kTileE, (M - e0 + 15) & ~15);
+                const uint32_t idesc = tc::idesc_e4m3_f32(kTile, max(16, ncol));
                 if (tuse > 0 && !tc::mbar_wait(&bar_tempty[buf], (tuse - 1) & 1, abort, wait_ns)) break;
                 tc::tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)buf * kAccCols;
