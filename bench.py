@@ -389,7 +389,9 @@ def run_gpu(args, rank, world, local_rank):
             "e2e": {"value": jobs * UNITS * args.steps / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
-            "kernels": shares}
+            "kernels": shares,
+            # the stage count the library's tuner chose for this step's k = 2 launch
+            "tuned": tuned_choices("k2tc_stages", M_VAR, N_OBJ, DIV + 1, DISC)}
     if args.serving_jobs > 0:
         line["serving"] = serving_run(args.serving_jobs, local_rank)
     if args.select_reps > 0:
@@ -602,7 +604,7 @@ def batched_check(device: int, n_folds: int, n_perms: int, M: int, peaks=None):
     if peaks and k2["ms"] > 0:
         roof = k2_roofline(J * math.comb(M, 2) * D, N, div + 1, k2, peaks)
     return {"jobs": J, "seconds": secs, "evals_per_s": J * math.comb(M, 2) * D / secs, "roofline": roof,
-            "kernels": prof,
+            "kernels": prof, "tuned": tuned_choices("k2tc_batch_stages", M, N, div + 1, D),
             "max_abs_err": max(c["max_abs_err"] for c in checks),
             "argmax_bad": sum(c["argmax_bad"] for c in checks),
             "argmax_equal": sum(c["argmax_equal"] for c in checks),
@@ -790,12 +792,37 @@ def run_batched(args):
             "jobs": J, "seconds": secs, "config": {"N": N, "M": M, "divisions": div, "discretizations": D,
                                                    "folds": n_folds, "perms": n_perms},
             "roofline": roof, "kernels": {k: v for k, v in prof.items()},
+            "tuned": tuned_choices("k2tc_batch_stages", M, N, div + 1, D),
             "xor_partners_recovered_job0": f"{found}/{2 * len(pairs)}"}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def tuned_choices(kernel: str, M: int, N: int, c: int, D: int):
+    """The library's cached launch choice for a shape, read back from its
+    MDFS_TUNE_FILE ("<kernel> M=.. N=.. c=.. D=.. -> <choice>" lines); None
+    when the file is unset or holds no entry."""
+    path = os.environ.get("MDFS_TUNE_FILE")
+    if not path or not os.path.exists(path):
+        return None
+    key = f"{kernel} M={M} N={N} c={c} D={D} -> "
+    vals = [ln.split(" -> ")[1].strip() for ln in open(path) if ln.startswith(key)]
+    return {"key": key[:-4], "stages": int(vals[-1])} if vals else None
+
+
+def _tune_file_for_this_run():
+    """A fresh tuning cache per bench process (so the line names what this run
+    chose), unless the caller set one."""
+    if "MDFS_TUNE_FILE" not in os.environ:
+        log_dir = os.environ.get("MDFS_BENCH_LOG_DIR") or tempfile.gettempdir()
+        path = os.path.join(log_dir, f"mdfs_tune_{os.getpid()}.txt")
+        if os.path.exists(path):
+            os.remove(path)
+        os.environ["MDFS_TUNE_FILE"] = path
+
+
 def main():
+    _tune_file_for_this_run()
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
