@@ -53,6 +53,7 @@ struct Workspace {
     Buffer bx, by, bidx, bperm;  // batch: gathered job data and the job index maps
     Buffer items3;               // k = 2 tensor-core tile list
     Buffer bcounts, bonehot, btab, bcnt1, bsh1, bkeys;  // batch: class sizes; a chunk's operands and tables
+    Buffer bsorted, bmult, bthr;  // batch: sorted keys of every variable; one job's multiplicities and thresholds
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
     Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
     Buffer items4;                                           // k = 4 work items
@@ -77,7 +78,7 @@ struct Workspace {
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
                          &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
-                         &bcounts, &bonehot, &btab, &bcnt1, &bsh1, &bkeys};
+                         &bcounts, &bonehot, &btab, &bcnt1, &bsh1, &bkeys, &bsorted, &bmult, &bthr};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
         if (host_stats) cudaFreeHost(host_stats);
@@ -1131,6 +1132,15 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
             ws->n_items3 = (int)items.size();
         }
         const int fbits = k3tc_fraction_bits(N);
+        // every variable sorted once for all jobs; a job's thresholds then come from
+        // the sorted keys and the job's sample multiplicities, without a sort
+        const bool presorted = N <= kPresortMaxN;
+        if (presorted) {
+            MDFS_ENSURE(ws, bsorted, (size_t)M * N * sizeof(unsigned long long));
+            MDFS_ENSURE(ws, bmult, (size_t)N * sizeof(int));
+            MDFS_ENSURE(ws, bthr, (size_t)D * M * P * sizeof(float));
+            MDFS_LAUNCH("presort", st, launch_presort(xd, data->dtype, N, M, (unsigned long long*)ws->bsorted.p, st));
+        }
         for (int j0 = 0; j0 < n_jobs; j0 += chunk_cap) {
             const int nj = std::min(chunk_cap, n_jobs - j0);
             K2Jobs jobs{};
@@ -1153,9 +1163,20 @@ int mdfs_max_ig_batch(const mdfs_data* data, int n_jobs, const int32_t* sample_i
                 tgd.Kp = Kp_max;
                 const PlaneGeom g = make_geom(N, n0);
                 MDFS_LAUNCH("ftable", st, launch_ftable(N, b0, b1, tab, st));
+                const float* thr_in = nullptr;
+                if (presorted) {
+                    const int* idx_j = idxd ? idxd + (size_t)j * N : nullptr;
+                    MDFS_LAUNCH("multiplicity", st, launch_multiplicity(idx_j, N, (int*)ws->bmult.p, st));
+                    MDFS_LAUNCH("thresholds", st,
+                                launch_batch_thresholds((const unsigned long long*)ws->bsorted.p,
+                                                        idx_j ? (const int*)ws->bmult.p : nullptr, N, M, c, D, range,
+                                                        seed, (float*)ws->bthr.p, st));
+                    thr_in = (const float*)ws->bthr.p;
+                }
                 MDFS_LAUNCH("discretize", st, launch_discretize(ws->bx.p, data->dtype, N, M, c, D, range, seed,
                                                                 (const int*)ws->perm.p, g, (uint32_t*)ws->planes.p,
-                                                                nullptr, nullptr, onehot, tgd, st, k2tc_class1_byte(c)));
+                                                                nullptr, nullptr, onehot, tgd, st, k2tc_class1_byte(c),
+                                                                thr_in));
                 MDFS_LAUNCH("k1", st, launch_k1((const uint32_t*)ws->planes.p, g, M, c, D, tab, cnt1, sh1, nullptr, st));
                 MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
                 jobs.job[jj] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};

@@ -102,7 +102,22 @@ cudaError_t launch_ftable_wide(double b0, double b1, long long* tab, cudaStream_
 cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
                               uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
                               uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st,
-                              uint32_t class1_byte = 0x38);
+                              uint32_t class1_byte = 0x38, const float* thr_in = nullptr);
+// With thr_in [D][M][c-1] (thresholds of launch_batch_thresholds) the column is
+// not sorted: the given thresholds bin it.
+//
+// Batched resamples without a sort per job: launch_presort stores every
+// variable's samples in ascending order as 64-bit keys (ordered float bits << 32
+// | sample index) [M][N]; launch_multiplicity counts how often each original
+// sample occurs in one job's index map (NULL = once each) into m [N];
+// launch_batch_thresholds takes the cut positions of the resampled column from
+// the sorted keys weighted by m: the thresholds of sort(x[v][idx]) exactly.
+// N <= kPresortMaxN.
+constexpr int kPresortMaxN = 8192;
+cudaError_t launch_presort(const void* x, int dtype, int N, int M, unsigned long long* keys, cudaStream_t st);
+cudaError_t launch_multiplicity(const int* idx, int N, int* m, cudaStream_t st);
+cudaError_t launch_batch_thresholds(const unsigned long long* keys, const int* m, int N, int M, int c, int D,
+                                    double range, uint64_t seed, float* thr, cudaStream_t st);
 
 // Per (disc, variable): class counts of bins 1..c-1 -> cnt1 [D][M][c-1][2] i32,
 // SH1 [D][M] i64.  If keys != NULL also folds IG^1 = SH0 - SH1 into keys.

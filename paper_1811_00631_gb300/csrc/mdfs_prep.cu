@@ -260,6 +260,33 @@ cudaError_t launch_ftable_wide(double b0, double b1, long long* tab, cudaStream_
 // key = seed).  Positions p_j = floor(N S_j / S_c) with S_j = w_0 + .. + w_{j-1},
 // clamped to [j, N-c+j] and made strictly increasing.
 // ---------------------------------------------------------------------------
+// Cut positions pos[1 .. c-1] of (variable v, discretisation d) among N sorted
+// samples, from the shares above.
+__device__ __forceinline__ void cut_positions(int v, int d, int N, int c, uint32_t R, uint32_t key0, uint32_t key1,
+                                              int* pos) {
+    const long long W = 1LL << 20;
+    long long share[kMaxC];
+    uint32_t u[4];
+    for (int j = 0; j < c; ++j) {
+        if ((j & 3) == 0) philox4x32_10((uint32_t)(j >> 2), (uint32_t)v, (uint32_t)d, kPhiloxTag, key0, key1, u);
+        const unsigned long long draw = ((unsigned long long)u[j & 3] * (unsigned long long)(2u * R)) >> 32;
+        share[j] = W - (long long)R + (long long)draw;
+    }
+    long long total = 0;
+    for (int j = 0; j < c; ++j) total += share[j];
+    long long cum = 0, prev = 0;
+    for (int j = 1; j < c; ++j) {
+        cum += share[j - 1];
+        long long p = total > 0 ? (long long)(((unsigned long long)N * (unsigned long long)cum) / (unsigned long long)total)
+                                : ((long long)N * j) / c;
+        if (p < j) p = j;
+        if (p > N - c + j) p = N - c + j;
+        if (j > 1 && p <= prev) p = prev + 1;
+        prev = p;
+        pos[j] = (int)p;
+    }
+}
+
 // Ascending bitonic sort of s[0 .. npad) (npad a power of two) by the whole block,
 // every stage through shared memory.
 __device__ void bitonic_sort_smem(float* s, int npad, int tid, int nthreads) {
@@ -351,52 +378,44 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
                                                          const int* __restrict__ perm, PlaneGeom g,
                                                          uint32_t* __restrict__ planes, uint8_t* __restrict__ codes,
                                                          float* __restrict__ thr_out, uint8_t* __restrict__ onehot,
-                                                         TcGeom tg, int scol, uint32_t class1_byte) {
+                                                         TcGeom tg, int scol, uint32_t class1_byte,
+                                                         const float* __restrict__ thr_in) {
     extern __shared__ __align__(16) float smem[];
     float* s = smem;           // [scol]: sorted column, then the class-sorted one-hot staging
     float* thr = smem + scol;  // [D][c-1] thresholds
     const int v = blockIdx.x;
     const int tid = threadIdx.x;
     const T* xv = x + (size_t)v * N;
-
-    for (int i = tid; i < npad; i += blockDim.x) s[i] = (i < N) ? (float)xv[i] : INFINITY;
-    __syncthreads();
-    switch (blockDim.x == 512 ? npad : 0) {
-        case 1024: bitonic_sort_regs<2>(s, npad, tid); break;
-        case 2048: bitonic_sort_regs<4>(s, npad, tid); break;
-        case 4096: bitonic_sort_regs<8>(s, npad, tid); break;
-        case 8192: bitonic_sort_regs<16>(s, npad, tid); break;
-        default: bitonic_sort_smem(s, npad, tid, blockDim.x); break;
-    }
-
     const int cm1 = c - 1;
-    const long long W = 1LL << 20;
-    for (int d = tid; d < D; d += blockDim.x) {
-        long long share[kMaxC];
-        uint32_t u[4];
-        for (int j = 0; j < c; ++j) {
-            if ((j & 3) == 0) philox4x32_10((uint32_t)(j >> 2), (uint32_t)v, (uint32_t)d, kPhiloxTag, key0, key1, u);
-            const unsigned long long draw = ((unsigned long long)u[j & 3] * (unsigned long long)(2u * R)) >> 32;
-            share[j] = W - (long long)R + (long long)draw;
+
+    if (thr_in) {  // thresholds given: no sort
+        for (int i = tid; i < D * cm1; i += blockDim.x) {
+            const float t = thr_in[((size_t)(i / cm1) * M + v) * cm1 + i % cm1];
+            thr[i] = t;
+            if (thr_out) thr_out[((size_t)(i / cm1) * M + v) * cm1 + i % cm1] = t;
         }
-        long long total = 0;
-        for (int j = 0; j < c; ++j) total += share[j];
-        long long cum = 0, prev = 0;
-        for (int j = 1; j < c; ++j) {
-            cum += share[j - 1];
-            long long p = total > 0 ? (long long)(((unsigned long long)N * (unsigned long long)cum) /
-                                                  (unsigned long long)total)
-                                    : ((long long)N * j) / c;
-            if (p < j) p = j;
-            if (p > N - c + j) p = N - c + j;
-            if (j > 1 && p <= prev) p = prev + 1;
-            prev = p;
-            const float t = s[p];
-            thr[d * cm1 + (j - 1)] = t;
-            if (thr_out) thr_out[((size_t)d * M + v) * cm1 + (j - 1)] = t;
+        __syncthreads();
+    } else {
+        for (int i = tid; i < npad; i += blockDim.x) s[i] = (i < N) ? (float)xv[i] : INFINITY;
+        __syncthreads();
+        switch (blockDim.x == 512 ? npad : 0) {
+            case 1024: bitonic_sort_regs<2>(s, npad, tid); break;
+            case 2048: bitonic_sort_regs<4>(s, npad, tid); break;
+            case 4096: bitonic_sort_regs<8>(s, npad, tid); break;
+            case 8192: bitonic_sort_regs<16>(s, npad, tid); break;
+            default: bitonic_sort_smem(s, npad, tid, blockDim.x); break;
         }
+        for (int d = tid; d < D; d += blockDim.x) {
+            int pos[kMaxC];
+            cut_positions(v, d, N, c, R, key0, key1, pos);
+            for (int j = 1; j < c; ++j) {
+                const float t = s[pos[j]];
+                thr[d * cm1 + (j - 1)] = t;
+                if (thr_out) thr_out[((size_t)d * M + v) * cm1 + (j - 1)] = t;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     if (codes) {
         for (int i = tid; i < N; i += blockDim.x) {
@@ -507,7 +526,7 @@ __global__ void __launch_bounds__(512) discretize_kernel(const T* __restrict__ x
 cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int D, double range,
                               uint64_t seed, const int* perm, PlaneGeom g, uint32_t* planes,
                               uint8_t* codes, float* thr, uint8_t* onehot, TcGeom tg, cudaStream_t st,
-                              uint32_t class1_byte) {
+                              uint32_t class1_byte, const float* thr_in) {
     int npad = 1;
     while (npad < N) npad <<= 1;
     // sorted column, reused for the class-sorted one-hot staging (Kp may exceed npad)
@@ -520,13 +539,143 @@ cudaError_t launch_discretize(const void* x, int dtype, int N, int M, int c, int
         e = ensure_dynamic_smem((const void*)discretize_kernel<float>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<float><<<M, 512, smem, st>>>((const float*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                       planes, codes, thr, onehot, tg, (int)scol, class1_byte);
+                                                       planes, codes, thr, onehot, tg, (int)scol, class1_byte,
+                                                       thr_in);
     } else {
         e = ensure_dynamic_smem((const void*)discretize_kernel<int8_t>, smem);
         if (e != cudaSuccess) return e;
         discretize_kernel<int8_t><<<M, 512, smem, st>>>((const int8_t*)x, N, M, c, D, R, k0, k1, npad, perm, g,
-                                                        planes, codes, thr, onehot, tg, (int)scol, class1_byte);
+                                                        planes, codes, thr, onehot, tg, (int)scol, class1_byte,
+                                                       thr_in);
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched resamples: one sort per variable for all jobs.  Job j's column is
+// x[v][idx_j[t]], t = 0..N-1, whose sorted order is the original sorted order
+// with sample s repeated m_j[s] times (m_j = how often s occurs in idx_j), so
+// its cut thresholds (the values at the cut positions of the sorted column)
+// follow from the original sorted keys (float_order_bits of the value << 32 |
+// the sample index) and a prefix sum of m_j.
+// ---------------------------------------------------------------------------
+// ascending bitonic sort of 64-bit keys s[0 .. npad) by the whole block
+__device__ void bitonic_sort_u64(unsigned long long* s, int npad, int tid, int nthreads) {
+    for (int k = 2; k <= npad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < npad; i += nthreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = s[i], b = s[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) presort_kernel(const T* __restrict__ x, int N, int npad,
+                                                      unsigned long long* __restrict__ keys) {
+    extern __shared__ unsigned long long sk[];
+    const int v = blockIdx.x, tid = threadIdx.x;
+    const T* xv = x + (size_t)v * N;
+    for (int i = tid; i < npad; i += blockDim.x)
+        sk[i] = i < N ? ((unsigned long long)float_order_bits((float)xv[i]) << 32) | (uint32_t)i : ~0ull;
+    __syncthreads();
+    bitonic_sort_u64(sk, npad, tid, blockDim.x);
+    for (int i = tid; i < N; i += blockDim.x) keys[(size_t)v * N + i] = sk[i];
+}
+
+cudaError_t launch_presort(const void* x, int dtype, int N, int M, unsigned long long* keys, cudaStream_t st) {
+    if (N < 1 || N > kPresortMaxN) return cudaErrorInvalidValue;
+    int npad = 2;
+    while (npad < N) npad <<= 1;
+    const size_t smem = (size_t)npad * sizeof(unsigned long long);
+    cudaError_t e;
+    if (dtype == 0) {
+        if ((e = ensure_dynamic_smem((const void*)presort_kernel<float>, smem)) != cudaSuccess) return e;
+        presort_kernel<float><<<M, 512, smem, st>>>((const float*)x, N, npad, keys);
+    } else {
+        if ((e = ensure_dynamic_smem((const void*)presort_kernel<int8_t>, smem)) != cudaSuccess) return e;
+        presort_kernel<int8_t><<<M, 512, smem, st>>>((const int8_t*)x, N, npad, keys);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void multiplicity_kernel(const int* __restrict__ idx, int N, int* __restrict__ m) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) atomicAdd(m + idx[t], 1);
+}
+
+cudaError_t launch_multiplicity(const int* idx, int N, int* m, cudaStream_t st) {
+    if (!idx) return cudaSuccess;  // identity: every sample once (the thresholds kernel takes m = NULL)
+    cudaError_t e = cudaMemsetAsync(m, 0, (size_t)N * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    multiplicity_kernel<<<(N + 255) / 256, 256, 0, st>>>(idx, N, m);
+    return cudaGetLastError();
+}
+
+// One CTA per variable: inclusive prefix C[r] of the multiplicities along the
+// sorted order; the sample at cut position p of the resampled column is the
+// first r with C[r] > p.
+__global__ void __launch_bounds__(512) batch_thresholds_kernel(const unsigned long long* __restrict__ keys,
+                                                               const int* __restrict__ m, int N, int M, int c, int D,
+                                                               uint32_t R, uint32_t key0, uint32_t key1,
+                                                               float* __restrict__ thr) {
+    extern __shared__ int C[];  // [N]
+    __shared__ int warp_sum[16];
+    const int v = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long* kv = keys + (size_t)v * N;
+    const int per = (N + blockDim.x - 1) / blockDim.x;
+    const int lo = min(N, tid * per), hi = min(N, lo + per);
+    int run = 0;
+    for (int r = lo; r < hi; ++r) {
+        run += m ? m[(uint32_t)kv[r]] : 1;
+        C[r] = run;
+    }
+    // exclusive block scan of the threads' totals
+    int incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_sum[w];
+    const int offset = before + incl - run;
+    for (int r = lo; r < hi; ++r) C[r] += offset;
+    __syncthreads();
+    const int cm1 = c - 1;
+    for (int d = tid; d < D; d += blockDim.x) {
+        int pos[kMaxC];
+        cut_positions(v, d, N, c, R, key0, key1, pos);
+        for (int j = 1; j < c; ++j) {
+            const int p = pos[j];
+            int a = 0, b = N - 1;  // C[N - 1] = N > p
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (C[mid] > p) b = mid;
+                else a = mid + 1;
+            }
+            thr[((size_t)d * M + v) * cm1 + (j - 1)] = order_bits_float((uint32_t)(kv[a] >> 32));
+        }
+    }
+}
+
+cudaError_t launch_batch_thresholds(const unsigned long long* keys, const int* m, int N, int M, int c, int D,
+                                    double range, uint64_t seed, float* thr, cudaStream_t st) {
+    if (N < 1 || N > kPresortMaxN) return cudaErrorInvalidValue;
+    const uint32_t R = (uint32_t)floor(range * 1048576.0 + 0.5);
+    const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
+    const size_t smem = (size_t)N * sizeof(int);
+    cudaError_t e = ensure_dynamic_smem((const void*)batch_thresholds_kernel, smem);
+    if (e != cudaSuccess) return e;
+    batch_thresholds_kernel<<<M, 512, smem, st>>>(keys, m, N, M, c, D, R, k0, k1, thr);
     return cudaGetLastError();
 }
 
