@@ -396,6 +396,8 @@ def run_gpu(args, rank, world, local_rank):
         line["serving"] = serving_run(args.serving_jobs, local_rank)
     if args.select_reps > 0:
         line["select"] = select_run(args.select_reps, local_rank)
+    if args.interesting_reps > 0:
+        line["interesting"] = interesting_run(args.interesting_reps, local_rank)
     if args.k4 and DIV == 1 and DISC * M_VAR ** 3 < 2**32:
         line["k4"] = k4_run(local_rank)
     if args.k5_m >= 5 and DIV == 1 and math.comb(args.k5_m, 4) < 2**32:
@@ -652,6 +654,42 @@ def select_run(reps: int, device: int):
     return out
 
 
+def interesting_run(reps: int, device: int):
+    """Interesting tuples (every (variable, partner set) whose IG, maximised
+    over the discretisations, reaches a threshold) on the bench data (2000 x
+    500, 30 discretisations, 2 classes) at k = 2 and k = 3, timed with CUDA
+    events around whole mdfs_interesting_tuples calls with device-resident
+    inputs.  The threshold is the 90th percentile of the variables' IG^k_max
+    (one untimed max scan), so the informative variables' strong tuples
+    qualify.  evals counts unordered tuples x discretisations."""
+    import torch
+    from paper_1811_00631_gb300 import mdfs, synth
+    dev = torch.device("cuda", device)
+    ds = synth.madelon_like(N=N_OBJ, M=M_VAR, seed=2)
+    x = torch.from_numpy(ds.x).to(dev)
+    y = torch.from_numpy(ds.y).to(dev)
+    out = {"workload": f"parity data N={N_OBJ} M={M_VAR}, D={DISC}, c={DIV + 1}; threshold = 90th percentile "
+                       f"of IG^k_max"}
+    for k in (2, 3):
+        best, _, _ = mdfs.max_ig(x, y, k, DIV, DISC, RANGE, XI, 7)
+        thr = float(np.quantile(best.cpu().numpy(), 0.9))
+        cap = 1 << 20
+        got = mdfs.interesting_tuples(x, y, k, DIV, DISC, RANGE, XI, 7, thr, capacity=cap)  # warm-up
+        stream = torch.cuda.current_stream(dev)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            got = mdfs.interesting_tuples(x, y, k, DIV, DISC, RANGE, XI, 7, thr, capacity=cap)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        evals = math.comb(M_VAR, k) * DISC
+        out[f"k{k}"] = {"ms": ms, "evals_per_s": evals / (ms / 1e3), "threshold": thr, "records": int(len(got[0]))}
+    return out
+
+
 def k4_run(device: int):
     """One k = 4 scan of the bench data (2000 x 500, 30 discretisations, 2
     classes): C(500, 4) x 30 = 7.7e10 quadruple x discretisation evaluations,
@@ -839,6 +877,8 @@ def main():
     ap.add_argument("--k5-disc", type=int, default=1, help="discretisations of the timed k = 5 scan")
     ap.add_argument("--select-reps", type=int, default=3,
                     help="timed calls of the selection pipeline per k (0: skip)")
+    ap.add_argument("--interesting-reps", type=int, default=3,
+                    help="timed interesting-tuple calls per k on the bench data (0: skip)")
     ap.add_argument("--shard", action="store_true",
                     help="split one job's tuple space over the ranks (the default with more than one GPU)")
     ap.add_argument("--independent", action="store_true",
@@ -857,6 +897,7 @@ def main():
         args.configs = 0
         args.serving_jobs = 0
         args.select_reps = 0
+        args.interesting_reps = 0
         args.k4 = 0
         args.k5_m = 0
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -417,8 +417,8 @@ void build_k3_items(int M, int c, std::vector<int2>& items) {
 // keys (tensor-core and generic triple paths); the popcount pair path and k = 1
 // run whole on shard 0.  Merging the keys of all shards by maximum gives the
 // keys of the unsharded scan.
-// emit != NULL: interesting-tuple emission into that table; the scan then runs on
-// the popcount kernels (the tensor-core kernels do not emit).
+// emit != NULL: interesting-tuple emission into that table (the tensor-core kernels
+// emit as the popcount kernels do).
 // ---- launch-parameter tuner -------------------------------------------------
 // The tunable launch parameter of the k = 2 tensor-core kernel (its pipeline
 // stages, which also set how many batch jobs one launch can hold) is chosen per
@@ -581,11 +581,11 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
     const EmitTable em = emit ? *emit : EmitTable();
-    const bool use_tc2 = (!emit && k == 2 && k2tc_supported(c) && k2tc_counts_fit(c, n0, n1) &&
+    const bool use_tc2 = (k == 2 && k2tc_supported(c) && k2tc_counts_fit(c, n0, n1) &&
                           k2tc_smem_bytes(c, N, 1, 3) <= kK3tcMaxSmem);
     // the triple kernel's layout is fixed (it fits the opt-in shared memory of sm_103a); it needs class sizes
     // below its table capacities
-    const bool use_tc3 = (!emit && k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) != (size_t)-1);
+    const bool use_tc3 = (k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) != (size_t)-1);
     TcGeom tg = make_tc_geom(n0, n1);
     if (dump && !use_tc2 && !use_tc3)
         return fail(MDFS_EINVAL, "no tensor-core kernel serves k = %d, %d classes, N0 = %d, N1 = %d", k, c, n0, n1);
@@ -620,13 +620,14 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         K2Jobs jobs{};
         jobs.n = 1;
         jobs.job[0] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};
-        // the count test hook runs the deepest pipeline that fits
-        const int stages = dump ? (k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem ? 4 : 3)
-                                : tuned_k2_stages(ws, "k2tc_stages", jobs, M, c, D, (const int2*)ws->items3.p + lo,
-                                                  cnt, onehot, tg.Kp, D, k3tc_fraction_bits(N), !exact);
+        // the count test hook and emission run the deepest pipeline that fits (no tuning runs)
+        const int stages = (dump || emit) ? (k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem ? 4 : 3)
+                                          : tuned_k2_stages(ws, "k2tc_stages", jobs, M, c, D,
+                                                            (const int2*)ws->items3.p + lo, cnt, onehot, tg.Kp, D,
+                                                            k3tc_fraction_bits(N), !exact);
         if (stages <= 0) return fail(MDFS_ECUDA, "k = 2 stage tuning failed (CUDA error)");
         MDFS_LAUNCH("k2", st, launch_k2tc(onehot, tg.Kp, D, jobs, M, c, 0, D, D, (const int2*)ws->items3.p + lo, cnt,
-                                          k3tc_fraction_bits(N), (int*)ws->err.p, !exact, stages, st, dump));
+                                          k3tc_fraction_bits(N), (int*)ws->err.p, !exact, stages, st, dump, em));
         *check_err = true;
     } else if (k == 2) {
         if (shard == 0)
@@ -676,7 +677,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             MDFS_LAUNCH("k3", st, launch_k3tc(map, (const uint8_t*)ws->onehot2.p, tg, M, d0, nn,
                                               (const int2*)ws->items2.p + lo, cnt, tab, fbits, (const int*)ws->cnt1s.p,
                                               lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, b0, b1, st,
-                                              dump, hooks));
+                                              dump, hooks, em));
         }
         *check_err = true;
     } else if (k == 3) {

@@ -67,6 +67,14 @@ struct EmitTable {
     int* full = nullptr;                 // set when an insert found no free slot
 };
 
+// The emission threshold as the int32 fixed point with fbits fraction bits of
+// the tensor-core kernels (multiples of 2^-fbits, rounded up; clamped to the
+// int range).
+inline int emit_threshold_fx(const EmitTable& t, int fbits) {
+    const long long v = (t.thr_fx + (1ll << (32 - fbits)) - 1) >> (32 - fbits);
+    return (int)(v > 2147483647ll ? 2147483647ll : v < -2147483647ll ? -2147483647ll : v);
+}
+
 // ---- launchers (all asynchronous on `st`) -----------------------------------
 // stats[0] = N1 (count of y == 1), stats[1] = number of y not in {0,1},
 // stats[2] = number of non-finite x.  perm = class-stable sample order.
@@ -224,7 +232,8 @@ struct TcTestHooks {
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
                         const int* perm, const PairC* pairs, unsigned long long* keys, int* err, double b0, double b1,
-                        cudaStream_t st, uint32_t* dump = nullptr, TcTestHooks hooks = TcTestHooks());
+                        cudaStream_t st, uint32_t* dump = nullptr, TcTestHooks hooks = TcTestHooks(),
+                        EmitTable emit = EmitTable());
 // Relabelling of the k = 3 tensor path, per discretisation: new labels in
 // ascending order of the bin-1 count (ties by index) for M <= 8192, else the
 // identity.  perm [D][M] new -> original, rank [D][M] original -> new,
@@ -268,10 +277,12 @@ int k2tc_max_jobs(int c, int N, int stages, size_t smem_limit);
 // both roles.  stages: 3 or 4.  dstride: discretisations per job in the operand.
 // dump != NULL (test hook, one job, 4 stages): also writes the c x c class
 // counts of every pair i < m, [D][C(M,2)][c c] uint32 n0 | n1 << 16 at the
-// pair's rank in the upper triangle, voxel code_i c + code_m.
+// pair's rank in the upper triangle, voxel code_i c + code_m.  emit.keys !=
+// NULL (one job, no dump): also inserts every (variable, partner) whose IG
+// reaches emit.thr_fx into that interesting-tuple table.
 cudaError_t launch_k2tc(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int c, int d0, int nd,
                         int dstride, const int2* items, int n_items, int fbits, int* err, bool bound, int stages,
-                        cudaStream_t st, uint32_t* dump = nullptr);
+                        cudaStream_t st, uint32_t* dump = nullptr, EmitTable emit = EmitTable());
 // the c = 3 kernel (mdfs_k2tc3.cu) behind launch_k2tc; its one-hot operand
 // carries class1_byte (k2tc_class1_byte) for class-1 samples, and it needs
 // class sizes N0, N1 below 4096 (k2tc_counts_fit)
@@ -281,7 +292,7 @@ uint32_t k2tc3_class1_byte();
 size_t k2tc3_smem_bytes(int N, int n_jobs, int stages);
 cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int d0, int nd, int dstride,
                          const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,
-                         uint32_t* dump);
+                         uint32_t* dump, EmitTable emit);
 // byte tensor map with the 128-byte swizzle (box[0] = 128 bytes), strides in bytes
 cudaError_t make_tiled_map_u8(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
                               const cuuint64_t* strides, const cuuint32_t* box);

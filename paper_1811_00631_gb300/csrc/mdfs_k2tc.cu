@@ -71,14 +71,17 @@ __device__ __forceinline__ int f2i_exact(float f) { return __float_as_int(f + 12
 // same N (a batch's resamples; one job for a plain scan), discretisations
 // d0 .. d0 + nd - 1, and the n_items symmetric tiles; job j's operand rows are
 // at z = j dstride + d of the tensor map.  Every job's entropy tables sit in
-// shared memory at once.  S: pipeline stages.  kDump: also write the 2 x 2
-// class counts of every pair of job 0 to `dump` (test hook; the scan itself is
-// unchanged).
-template <int S, bool kDump>
+// shared memory at once.  S: pipeline stages.  kMode 1 (kDump): also write
+// the 2 x 2 class counts of every pair of job 0 to `dump` (test hook; the scan
+// itself is unchanged).  kMode 2 (kEmit, one job): also insert every role whose
+// IG reaches emit_thr (int32 fixed point, fbits fraction bits) into the
+// interesting-tuple table `emit`.
+template <int S, int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
     k2tc_kernel(const __grid_constant__ CUtensorMap map_oh, const __grid_constant__ K2Jobs jobs, int M, int d0,
                 int nd, int dstride, const int2* __restrict__ items, int n_items, int fbits, int* __restrict__ err,
-                uint32_t* __restrict__ dump) {
+                uint32_t* __restrict__ dump, EmitTable emit, int emit_thr) {
+    constexpr bool kDump = kMode == 1, kEmit = kMode == 2;
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[S], bar_empty[S];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
@@ -306,6 +309,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ki = umax64(ki, pack_key((float)(shm - sh2) * inv_scale, dM + (uint32_t)vm));
                         // IG(m | i) = SH1(i) - SH2
                         k_m = pack_key((float)(shi - sh2) * inv_scale, dM + (uint32_t)vi);
+                        if constexpr (kEmit) {
+                            if (shm - sh2 >= emit_thr)
+                                emit_insert(emit, emit_key(vi, vm, -1, -1),
+                                            pack_key((float)(shm - sh2) * inv_scale, (uint32_t)d));
+                            if (shi - sh2 >= emit_thr)
+                                emit_insert(emit, emit_key(vm, vi, -1, -1),
+                                            pack_key((float)(shi - sh2) * inv_scale, (uint32_t)d));
+                        }
                     }
                     const unsigned long long mk = warp_max_key(k_m);
                     if (lane == 0 && mk) atomicMax(keys + vm, mk);
@@ -352,13 +363,14 @@ uint32_t k2tc_class1_byte(int c) { return c == 3 ? k2tc3_class1_byte() : 0x38u; 
 
 cudaError_t launch_k2tc(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int c, int d0, int nd,
                         int dstride, const int2* items, int n_items, int fbits, int* err, bool bound, int stages,
-                        cudaStream_t st, uint32_t* dump) {
+                        cudaStream_t st, uint32_t* dump, EmitTable emit) {
     if (c == 3)
         return launch_k2tc3(oh, Kp, zdim, jobs, M, d0, nd, dstride, items, n_items, fbits, err, bound, stages, st,
-                            dump);
+                            dump, emit);
     if (c != 2) return cudaErrorInvalidValue;
     if (n_items == 0 || jobs.n == 0) return cudaSuccess;
-    if (jobs.n < 1 || jobs.n > kMaxK2Jobs || (stages != 3 && stages != 4) || (dump && (jobs.n != 1 || stages != 4)))
+    if (jobs.n < 1 || jobs.n > kMaxK2Jobs || (stages != 3 && stages != 4) || (dump && (jobs.n != 1 || stages != 4)) ||
+        (emit.keys && (jobs.n != 1 || dump)))
         return cudaErrorInvalidValue;
     const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1;
     for (int j = 0; j < jobs.n; ++j) {
@@ -370,8 +382,10 @@ cudaError_t launch_k2tc(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs,
     cudaError_t e = make_onehot_map(&map, oh, M, zdim, Kp);
     if (e != cudaSuccess) return e;
     const size_t smem = k2tc_smem_bytes(c, N, jobs.n, stages);
-    const void* fn = dump ? (const void*)k2tc_kernel<4, true>
-                          : (stages == 4 ? (const void*)k2tc_kernel<4, false> : (const void*)k2tc_kernel<3, false>);
+    const int mode = dump ? 1 : emit.keys ? 2 : 0;
+    const void* fn = mode == 1   ? (const void*)k2tc_kernel<4, 1>
+                     : mode == 2 ? (stages == 4 ? (const void*)k2tc_kernel<4, 2> : (const void*)k2tc_kernel<3, 2>)
+                                 : (stages == 4 ? (const void*)k2tc_kernel<4, 0> : (const void*)k2tc_kernel<3, 0>);
     if ((e = ensure_dynamic_smem(fn, smem)) != cudaSuccess) return e;
     cudaFuncAttributes fa;
     if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
@@ -382,15 +396,22 @@ cudaError_t launch_k2tc(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs,
     const long long n_tiles = (long long)n_items * nd * jobs.n;
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
-    if (dump)
-        k2tc_kernel<4, true><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
-                                                           dump);
+    const int ethr = emit_threshold_fx(emit, fbits);
+    if (mode == 1)
+        k2tc_kernel<4, 1><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
+                                                        dump, emit, ethr);
+    else if (mode == 2 && stages == 4)
+        k2tc_kernel<4, 2><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
+                                                        nullptr, emit, ethr);
+    else if (mode == 2)
+        k2tc_kernel<3, 2><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
+                                                        nullptr, emit, ethr);
     else if (stages == 4)
-        k2tc_kernel<4, false><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
-                                                            nullptr);
+        k2tc_kernel<4, 0><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
+                                                        nullptr, emit, ethr);
     else
-        k2tc_kernel<3, false><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
-                                                            nullptr);
+        k2tc_kernel<3, 0><<<grid, kThreads, smem, st>>>(map, jobs, M, d0, nd, dstride, items, n_items, fbits, err,
+                                                        nullptr, emit, ethr);
     return cudaGetLastError();
 }
 

@@ -119,15 +119,19 @@ __device__ __forceinline__ int voxel32(const int* sT0, const int* sT1, const int
 // Work items: (job, discretisation, tile) for jobs.n jobs of the same N,
 // discretisations d0 .. d0 + nd - 1 and the n_items tiles (row block of 128
 // variables, column block of 64 variables at or after it); job j's operand rows
-// are at z = j dstride + d of both tensor maps.  kDump: also write the 3 x 3
-// class counts of every pair of job 0 to `dump` (test hook; the scan itself is
-// unchanged).
-template <bool kDump>
+// are at z = j dstride + d of both tensor maps.  kMode 1 (kDump): also write
+// the 3 x 3 class counts of every pair of job 0 to `dump` (test hook; the scan
+// itself is unchanged).  kMode 2 (kEmit, one job): also insert every role whose
+// IG reaches emit_thr (int32 fixed point) into the interesting-tuple table
+// `emit`; the bound then also keeps every pair whose roles can reach
+// emit_thr_c (the same threshold in units of 4 ln 2 nats).
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
     k2tc3_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                  const __grid_constant__ K2Jobs jobs, int M, int d0, int nd, int dstride,
                  const int2* __restrict__ items, int n_items, int fbits, int* __restrict__ err, int prune_on,
-                 uint32_t* __restrict__ dump) {
+                 uint32_t* __restrict__ dump, EmitTable emit, int emit_thr, float emit_thr_c) {
+    constexpr bool kDump = kMode == 1, kEmit = kMode == 2;
     constexpr int S = kStages;
     const bool use_bound = !kDump && prune_on;
     extern __shared__ uint8_t dsmem_raw[];
@@ -315,6 +319,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t dM = (uint32_t)q_d * (uint32_t)M;
                 atomicMax(J.keys + id.x, pack_key((float)((int)id.w - sh2) * inv_scale, dM + id.y));
                 atomicMax(J.keys + id.y, pack_key((float)((int)id.z - sh2) * inv_scale, dM + id.x));
+                if constexpr (kEmit) {
+                    const int gi = (int)id.w - sh2, gm = (int)id.z - sh2;
+                    if (gi >= emit_thr)
+                        emit_insert(emit, emit_key((int)id.x, (int)id.y, -1, -1),
+                                    pack_key((float)gi * inv_scale, (uint32_t)q_d));
+                    if (gm >= emit_thr)
+                        emit_insert(emit, emit_key((int)id.y, (int)id.x, -1, -1),
+                                    pack_key((float)gm * inv_scale, (uint32_t)q_d));
+                }
             }
             __syncwarp();
         };
@@ -355,7 +368,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const unsigned long long kc = cok ? __ldcg(keys + vc) : 0ull;
                 ctx[2 * lane] = make_float4(i2f_exact(cc.x) + beta0, i2f_exact(cc.z) + beta0,
                                             i2f_exact(cc.y) + beta1, i2f_exact(cc.w) + beta1);
-                ctx[2 * lane + 1] = make_float4((float)s * kFx32ToCount, cok ? key_ig_count(kc) : 0.0f,
+                float kcc = cok ? key_ig_count(kc) : 0.0f;
+                if constexpr (kEmit) kcc = fminf(kcc, emit_thr_c);
+                ctx[2 * lane + 1] = make_float4((float)s * kFx32ToCount, kcc,
                                                 __int_as_float(fx_narrow(s, fbits)), 0.0f);
             }
             __syncwarp();
@@ -369,7 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const long long s1i = irow ? s1[vi] : 0ll;
             const int shi = fx_narrow(s1i, fbits);
             const float shi_c = (float)s1i * kFx32ToCount;
-            const float keyi_c = irow ? key_ig_count(__ldcg(keys + vi)) : 0.0f;
+            float keyi_c = irow ? key_ig_count(__ldcg(keys + vi)) : 0.0f;
+            if constexpr (kEmit) keyi_c = fminf(keyi_c, emit_thr_c);
             const float2 B0 = make_float2(beta0, beta0), B1 = make_float2(beta1, beta1);
 
             if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_tfull[buf], tuse & 1, abort))) break;  // warp-uniform
@@ -497,9 +513,11 @@ uint32_t k2tc3_class1_byte() { return 0x68; }  // E4M3 64.0
 
 cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs, int M, int d0, int nd, int dstride,
                          const int2* items, int n_items, int fbits, int* err, bool bound, int stages, cudaStream_t st,
-                         uint32_t* dump) {
+                         uint32_t* dump, EmitTable emit) {
     if (n_items == 0 || jobs.n == 0) return cudaSuccess;
-    if (jobs.n < 1 || jobs.n > kMaxK2Jobs || stages != kStages || (dump && jobs.n != 1)) return cudaErrorInvalidValue;
+    if (jobs.n < 1 || jobs.n > kMaxK2Jobs || stages != kStages || (dump && jobs.n != 1) ||
+        (emit.keys && (jobs.n != 1 || dump)))
+        return cudaErrorInvalidValue;
     if (Kp <= 0 || Kp % kBK != 0 || M < 1 || zdim < 1) return cudaErrorInvalidValue;
     const int N = jobs.job[0].tg.N0 + jobs.job[0].tg.N1;
     for (int j = 0; j < jobs.n; ++j) {
@@ -523,7 +541,9 @@ cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs
     if (e != cudaSuccess) return e;
     if ((e = make_tiled_map_u8(&map_b, oh, 3, dims_b, str_b, box_b)) != cudaSuccess) return e;
     const size_t smem = k2tc3_smem_bytes(N, jobs.n, stages);
-    const void* fn = dump ? (const void*)k2tc3_kernel<true> : (const void*)k2tc3_kernel<false>;
+    const void* fn = dump        ? (const void*)k2tc3_kernel<1>
+                     : emit.keys ? (const void*)k2tc3_kernel<2>
+                                 : (const void*)k2tc3_kernel<0>;
     if ((e = ensure_dynamic_smem(fn, smem)) != cudaSuccess) return e;
     // the register split inside the kernel needs exactly kRegsLaunch registers per thread
     cudaFuncAttributes fa;
@@ -536,12 +556,18 @@ cudaError_t launch_k2tc3(const uint8_t* oh, int Kp, int zdim, const K2Jobs& jobs
     if (n_tiles >= (1ll << 31)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
     const int prune_on = bound ? 1 : 0;
+    // the emission threshold as int32 fixed point and in units of 4 ln 2 nats (the bound's)
+    const int ethr = emit_threshold_fx(emit, fbits);
+    const float ethr_c = (float)((double)emit.thr_fx * 2.3283064365386963e-10 / (4.0 * 0.6931471805599453));
     if (dump)
-        k2tc3_kernel<true><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items, fbits,
-                                                         err, prune_on, dump);
+        k2tc3_kernel<1><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items, fbits,
+                                                      err, prune_on, dump, emit, ethr, ethr_c);
+    else if (emit.keys)
+        k2tc3_kernel<2><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items, fbits,
+                                                      err, prune_on, nullptr, emit, ethr, ethr_c);
     else
-        k2tc3_kernel<false><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items, fbits,
-                                                          err, prune_on, nullptr);
+        k2tc3_kernel<0><<<grid, kThreads, smem, st>>>(map_a, map_b, jobs, M, d0, nd, dstride, items, n_items, fbits,
+                                                      err, prune_on, nullptr, emit, ethr, ethr_c);
     return cudaGetLastError();
 }
 

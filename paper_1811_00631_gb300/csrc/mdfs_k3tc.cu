@@ -210,17 +210,24 @@ __device__ __noinline__ void dump_triple(uint32_t* dump, int M, int d, int a, in
 
 }  // namespace
 
-// kDump: also write the 8-voxel class counts of every triple to `dump` (test
-// hook; the scan itself is unchanged).  wait_ns bounds every mbarrier wait;
+// kMode 1 (kDump): also write the 8-voxel class counts of every triple to
+// `dump` (test hook; the scan itself is unchanged).  kMode 2 (kEmit): also
+// insert every role whose IG reaches emit_thr (int32 fixed point, fbits
+// fraction bits) into the interesting-tuple table `emit`, keyed by the
+// original variable and its two partners ascending, valued by the packed (IG,
+// discretisation); the SH3 bound then also keeps every triple whose roles can
+// reach emit_thr.  wait_ns bounds every mbarrier wait;
 // withhold_kb >= 0 makes the producer of CTA 0 skip the copies of that K block
 // of its running count (test hook: the consumers' bounded wait then runs out).
-template <bool kDump>
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
     k3tc_kernel(const __grid_constant__ CUtensorMap map_oh, const uint8_t* __restrict__ oh, TcGeom tg, int M, int d0,
                 int nd, const int2* __restrict__ items, int n_items, const long long* __restrict__ tab, int fbits,
                 const int* __restrict__ cnt1s, const int* __restrict__ perm, const PairC* __restrict__ pairs,
                 unsigned long long* __restrict__ keys, int* __restrict__ err, K3Prune prune,
-                uint32_t* __restrict__ dump, unsigned long long wait_ns, int withhold_kb) {
+                uint32_t* __restrict__ dump, unsigned long long wait_ns, int withhold_kb, EmitTable emit,
+                int emit_thr) {
+    constexpr bool kDump = kMode == 1, kEmit = kMode == 2;
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
@@ -473,8 +480,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             // SH3 <= SH(a,b) - thr_e, IG(a | b,e) only if SH3 <= SH(b,e) - thr_a,
             // IG(b | a,e) only if SH3 <= SH(a,e) - thr_b
             const float shab_c = (float)shab * prune.fx_to_count;
-            const float thra_c = arow ? (float)key_threshold(__ldcg(keys + ao), fbits) * prune.fx_to_count : 0.0f;
-            const float thrb_c = (float)key_threshold(__ldcg(keys + bo), fbits) * prune.fx_to_count;
+            // (with emission: the lower of the key's and the emission threshold)
+            int thra = arow ? key_threshold(__ldcg(keys + ao), fbits) : 0;
+            int thrb = key_threshold(__ldcg(keys + bo), fbits);
+            if constexpr (kEmit) {
+                thra = min(thra, emit_thr);
+                thrb = min(thrb, emit_thr);
+            }
+            const float thra_c = (float)thra * prune.fx_to_count;
+            const float thrb_c = (float)thrb * prune.fx_to_count;
             const uint32_t dM = (uint32_t)d * (uint32_t)M;
             // running maxima of the roles a (over e) and b (over this thread's (a, e));
             // columns are visited in ascending e, so ">" keeps the first maximum
@@ -501,6 +515,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         esh = p.sh;
                         // keys only grow during the scan: a stale value is a valid lower bound
                         thr = key_threshold(__ldcg(keys + pm[e]), fbits);
+                        if constexpr (kEmit) thr = min(thr, emit_thr);
                         if (!counts_ok(n0 | n1 | u0 | u1)) {
                             bad = true;
                             n0 = n1 = u0 = u1 = 0;
@@ -643,6 +658,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int ig_a = cx_sh - sh3;
                         const int ig_b = pcur[j].sh - sh3;
                         const int ig_e = valid ? shab - sh3 : INT_MIN;
+                        if constexpr (kEmit) {
+                            if (valid) {
+                                const int lo_be = min((int)bo, cx_eo), hi_be = max((int)bo, cx_eo);
+                                const int lo_ae = min(ao, cx_eo), hi_ae = max(ao, cx_eo);
+                                const int lo_ab = min(ao, (int)bo), hi_ab = max(ao, (int)bo);
+                                if (ig_a >= emit_thr)
+                                    emit_insert(emit, emit_key(ao, lo_be, hi_be, -1),
+                                                pack_key((float)ig_a * inv_scale, (uint32_t)d));
+                                if (ig_b >= emit_thr)
+                                    emit_insert(emit, emit_key((int)bo, lo_ae, hi_ae, -1),
+                                                pack_key((float)ig_b * inv_scale, (uint32_t)d));
+                                if (ig_e >= emit_thr)
+                                    emit_insert(emit, emit_key(cx_eo, lo_ab, hi_ab, -1),
+                                                pack_key((float)ig_e * inv_scale, (uint32_t)d));
+                            }
+                        }
                         if (valid && ig_a > best_a) {
                             best_a = ig_a;
                             ca = col;
@@ -867,10 +898,13 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
                         const int* perm, const PairC* pairs, unsigned long long* keys, int* err, double b0, double b1,
-                        cudaStream_t st, uint32_t* dump, TcTestHooks hooks) {
+                        cudaStream_t st, uint32_t* dump, TcTestHooks hooks, EmitTable emit) {
     if (n_items == 0) return cudaSuccess;
+    if (dump && emit.keys) return cudaErrorInvalidValue;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
-    const void* fn = dump ? (const void*)k3tc_kernel<true> : (const void*)k3tc_kernel<false>;
+    const void* fn = dump        ? (const void*)k3tc_kernel<1>
+                     : emit.keys ? (const void*)k3tc_kernel<2>
+                                 : (const void*)k3tc_kernel<0>;
     cudaError_t e = ensure_dynamic_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -893,14 +927,19 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     prune.beta1 = (float)b1;
     prune.fx_to_count = (float)(1.0 / scale);
     prune.count_to_fx = (float)scale;
+    const int emit_thr = emit_threshold_fx(emit, fbits);
     if (dump)
-        k3tc_kernel<true><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s,
-                                                        perm, pairs, keys, err, prune, dump, wait_ns,
-                                                        hooks.withhold_kb);
+        k3tc_kernel<1><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
+                                                     pairs, keys, err, prune, dump, wait_ns, hooks.withhold_kb, emit,
+                                                     emit_thr);
+    else if (emit.keys)
+        k3tc_kernel<2><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
+                                                     pairs, keys, err, prune, nullptr, wait_ns, hooks.withhold_kb,
+                                                     emit, emit_thr);
     else
-        k3tc_kernel<false><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s,
-                                                         perm, pairs, keys, err, prune, nullptr, wait_ns,
-                                                         hooks.withhold_kb);
+        k3tc_kernel<0><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
+                                                     pairs, keys, err, prune, nullptr, wait_ns, hooks.withhold_kb,
+                                                     emit, emit_thr);
     return cudaGetLastError();
 }
 

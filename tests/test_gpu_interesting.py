@@ -105,3 +105,60 @@ def test_interesting_tuples_capacity(cuda):
     assert e.value.code == -7 and "380" in str(e.value)
     var, tu, ig, di = mdfs.interesting_tuples(x, y, 2, 1, 1, 0.0, 0.25, 1, 1e6, capacity=10)
     assert len(var) == 0
+
+
+def _oracle_per_d(codes, y, c, xi, v, S):
+    return [oracle.ig_one(codes, y, c, xi, d, v, list(S)) for d in range(codes.shape[0])]
+
+
+@pytest.mark.parametrize("k,div,M,N,D", [(2, 1, 300, 1200, 2), (2, 2, 200, 1000, 2), (3, 1, 120, 900, 2)])
+def test_interesting_tuples_tensor_core_sizes_sampled(cuda, k, div, M, N, D):
+    """Sizes that the tensor-core kernels serve (k = 2 with two or three
+    classes, k = 3 with two) over several tiles and ragged edges: every record
+    of sampled variables against the full oracle enumeration of those
+    variables, and sampled records of every variable against the oracle."""
+    import itertools
+    from paper_1811_00631_gb300 import mdfs
+    rng = np.random.default_rng(1000 * k + M)
+    x = rng.standard_normal((M, N)).astype(np.float32)
+    y = ((x[1] > 0) ^ (x[M - 2] > 0.3) ^ (x[M // 2] > -0.2) ^ (rng.random(N) < 0.05)).astype(np.uint8)
+    c, xi = div + 1, 0.25
+    codes = oracle.discretize(x, div, D, 0.5, 29)
+    sampled = [1, M // 2, M - 2, 7]
+    ref = {}
+    for v in sampled:
+        for S in itertools.combinations([m for m in range(M) if m != v], k - 1):
+            per_d = _oracle_per_d(codes, y, c, xi, v, S)
+            ref[(v, S)] = per_d
+    # a threshold that keeps about the top 5 % of the sampled variables' records
+    thr = float(np.quantile([max(p) for p in ref.values()], 0.95))
+    var, tu, ig, di = mdfs.interesting_tuples(x, y, k, div, D, 0.5, xi, 29, thr,
+                                              capacity=M * math.comb(M - 1, k - 1))
+    var, tu, ig, di = (np.asarray(a) for a in (var, tu, ig, di))
+    keys = [(int(v), tuple(int(p) for p in t)) for v, t in zip(var, tu)]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+    got = {key: (float(s), int(d)) for key, s, d in zip(keys, ig, di)}
+
+    def check(key, per_d):
+        o = max(per_d)
+        t = ATOL + RTOL * abs(o)
+        if key in got:
+            s, d = got[key]
+            assert abs(s - o) <= t, (key, s, o)
+            assert o >= thr - t, f"GPU record {key} ({s}) below the threshold in the oracle ({o})"
+            do = int(np.argmax(per_d))
+            if d != do:
+                second = max(val for dd, val in enumerate(per_d) if dd != do)
+                argmax_rule.check_alternative(o, second, per_d[d], f"record {key}")
+        else:
+            assert o < thr + t, f"oracle record {key} ({o}) missing"
+
+    for key, per_d in ref.items():
+        check(key, per_d)
+    assert any(v in sampled for v, _ in got)
+    # records of all variables, sampled
+    pick = rng.choice(len(keys), size=min(300, len(keys)), replace=False)
+    for j in pick:
+        v, S = keys[j]
+        assert v not in S and list(S) == sorted(S) and len(S) == k - 1
+        check(keys[j], _oracle_per_d(codes, y, c, xi, v, S))
