@@ -55,6 +55,10 @@ struct Workspace {
     Buffer bcounts, bonehot, btab, bcnt1, bsh1, bkeys;  // batch: class sizes; a chunk's operands and tables
     Buffer bsorted, bmult, bthr;  // batch: sorted keys of every variable; one job's multiplicities and thresholds
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
+    Buffer k3sched[2];                    // k = 3 tensor path: tile schedules of recent launch shapes
+    long long k3sched_key[2][5] = {{-1}, {-1}};
+    int k3sched_next = 0;
+    std::vector<int2> items2_host;        // the k = 3 tensor path's tile list (host copy)
     Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
     Buffer items4;                                           // k = 4 work items
     Buffer items5;                                           // k = 5 work items
@@ -77,7 +81,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
+                         &onehot2, &k3sched[0], &k3sched[1], &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
                          &bcounts, &bonehot, &btab, &bcnt1, &bsh1, &bkeys, &bsorted, &bmult, &bthr};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
@@ -646,7 +650,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         MDFS_ENSURE(ws, err, sizeof(int));
         if (!keep_err) MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
         if (ws->items2_M != M) {
-            std::vector<int2> items;
+            std::vector<int2>& items = ws->items2_host;
             build_k3tc_items(M, items);
             MDFS_ENSURE(ws, items2, items.size() * sizeof(int2));
             MDFS_CUDA_TRY(cudaMemcpyAsync(ws->items2.p, items.data(), items.size() * sizeof(int2),
@@ -674,10 +678,32 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                                                    nullptr, (PairC*)ws->pairs2.p, fbits, st, (const int*)ws->lrank.p));
             int lo = 0;
             const int cnt = share(ws->n_items2, &lo);
+            // the tile schedule of this launch shape, built once and kept (two shapes)
+            const int* sched = nullptr;
+            const int grid = cnt > 0 ? k3tc_grid(cnt * nn) : 0;
+            if (grid > 0) {
+                const long long key[5] = {M, lo, cnt, nn, grid};
+                int slot = -1;
+                for (int e = 0; e < 2; ++e)
+                    if (std::equal(key, key + 5, ws->k3sched_key[e])) slot = e;
+                if (slot < 0) {
+                    slot = ws->k3sched_next;
+                    ws->k3sched_next ^= 1;
+                    ws->k3sched_key[slot][0] = -1;
+                    std::vector<int> sv;
+                    build_k3tc_schedule(M, ws->items2_host.data() + lo, cnt, nn, grid, sv);
+                    MDFS_ENSURE(ws, k3sched[slot], sv.size() * sizeof(int));
+                    MDFS_CUDA_TRY(cudaMemcpyAsync(ws->k3sched[slot].p, sv.data(), sv.size() * sizeof(int),
+                                                  cudaMemcpyHostToDevice, st));
+                    MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `sv` is a pageable host vector
+                    std::copy(key, key + 5, ws->k3sched_key[slot]);
+                }
+                sched = (const int*)ws->k3sched[slot].p;
+            }
             MDFS_LAUNCH("k3", st, launch_k3tc(map, (const uint8_t*)ws->onehot2.p, tg, M, d0, nn,
                                               (const int2*)ws->items2.p + lo, cnt, tab, fbits, (const int*)ws->cnt1s.p,
                                               lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, b0, b1, st,
-                                              dump, hooks, em));
+                                              dump, hooks, em, sched, grid));
         }
         *check_err = true;
     } else if (k == 3) {

@@ -46,8 +46,12 @@
 // drains its copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <algorithm>
 #include <climits>
 #include <cmath>
+#include <queue>
+#include <utility>
+#include <vector>
 
 #include "mdfs_device.cuh"
 #include "mdfs_internal.cuh"
@@ -176,7 +180,20 @@ __device__ __forceinline__ int key_threshold(unsigned long long key, int fbits) 
 // TMEM lane quarter q, the rows 32 q .. 32 q + 31 of the accumulator, is read
 // by the warps of one SM sub-partition; alternating the alignment spreads the
 // partial tiles' valid rows evenly over the four quarters.
-__device__ __forceinline__ int tile_a0(int b, int ta) { return (b & 1) ? b - kTile * (ta + 1) : kTile * ta; }
+__host__ __device__ __forceinline__ int tile_a0(int b, int ta) { return (b & 1) ? b - kTile * (ta + 1) : kTile * ta; }
+
+// The tiles of this CTA, in order: list[begin .. begin + count) of a host-built
+// schedule (build_k3tc_schedule), or without one blockIdx.x + j gridDim.x
+// below n_tiles.  at(j) is -1 past the last.
+struct TileSeq {
+    const int* list;
+    int begin, count, n_tiles;
+    __device__ __forceinline__ int at(int j) const {
+        if (list) return j < count ? __ldg(list + begin + j) : -1;
+        const int t = (int)blockIdx.x + j * (int)gridDim.x;
+        return t < n_tiles ? t : -1;
+    }
+};
 
 // partner index of a key: (d M + lo) M + hi with the two partners sorted
 __device__ __forceinline__ uint32_t partner_index(uint32_t dM, int M, uint32_t p, uint32_t q) {
@@ -226,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int* __restrict__ cnt1s, const int* __restrict__ perm, const PairC* __restrict__ pairs,
                 unsigned long long* __restrict__ keys, int* __restrict__ err, K3Prune prune,
                 uint32_t* __restrict__ dump, unsigned long long wait_ns, int withhold_kb, EmitTable emit,
-                int emit_thr) {
+                int emit_thr, const int* __restrict__ sched) {
     constexpr bool kDump = kMode == 1, kEmit = kMode == 2;
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
@@ -286,6 +303,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = s_tmem;
     const int n_tiles = n_items * nd;
     const int nkb = tg.nkb;
+    // sched: [gridDim.x + 1] offsets, then the tile lists
+    const TileSeq seq{sched ? sched + gridDim.x + 1 : nullptr, sched ? sched[blockIdx.x] : 0,
+                      sched ? sched[blockIdx.x + 1] - sched[blockIdx.x] : 0, n_tiles};
     if (warp < kEpiWarp0) {
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsProducer));
       if (warp == 0) {
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t g = 0;  // running K-block counter across this CTA's tiles
             int pend_mask = 0;
             uint32_t pend_use[kStages] = {};
-            for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
+            for (int j = 0, t; (t = seq.at(j)) >= 0 && !*abort; ++j) {
                 const int2 item = items[t % n_items];
                 const int d = d0 + t / n_items;
                 const int b = item.x, a0 = tile_a0(b, item.y >> 16), e0 = b + 1 + (item.y & 0xFFFF) * kTileE;
@@ -330,9 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0 && !*abort) {
 
             uint32_t g = 0;
-            int i = 0;
             bool issued = false;
-            for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
+            for (int i = 0, t; (t = seq.at(i)) >= 0 && !*abort; ++i) {
                 const int buf = i & 1;
                 const uint32_t tuse = (uint32_t)(i >> 1);
                 const int2 item = items[t % n_items];
@@ -383,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int slot = mt & 7, r0 = mt >> 3;
         const int jchunk = slot ^ (r0 & 7);
         uint32_t g = 0;
-        for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x) {
+        for (int j = 0, t; (t = seq.at(j)) >= 0 && !*abort; ++j) {
             const int2 item = items[t % n_items];
             const int a0 = tile_a0(item.x, item.y >> 16);
             const int rows = min(kTile, item.x - a0);  // rows with a < b (rows with a < 0 hold zeros)
@@ -426,8 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float2* csht = s_sht[ew];
         bool bad = false;       // inconsistent row or column constants
         uint32_t badbits = 0;   // OR of the pair records' count fields (checked at the end)
-        int i = 0;
-        for (int t = blockIdx.x; t < n_tiles && !*abort; t += gridDim.x, ++i) {
+        for (int i = 0, t; (t = seq.at(i)) >= 0 && !*abort; ++i) {
             const int buf = i & 1;
             const uint32_t tuse = (uint32_t)(i >> 1);
             const int2 item = items[t % n_items];
@@ -822,6 +840,55 @@ void build_k3tc_items(int M, std::vector<int2>& items) {
     }
 }
 
+// Relative cost of a tile: its epilogue work, the warps (32-row quarters of the
+// a tile) with a valid row times the valid e columns, as a fraction of a full
+// item, but at least the share of the main loop (the same K blocks for every
+// item, overlapped with the epilogue of the previous one; about 0.4 of a full
+// epilogue in the timings of the scan).
+static double tile_cost(int M, int2 item) {
+    const int b = item.x, a0 = tile_a0(b, item.y >> 16), e0 = b + 1 + (item.y & 0xFFFF) * kTileE;
+    int warps = 0;
+    for (int q = 0; q < 4; ++q) warps += (a0 + 32 * q < b && a0 + 32 * q + 31 >= 0) ? 1 : 0;
+    const int cols = std::min(kTileE, M - e0);
+    return std::max(0.4, (double)warps * 32.0 * cols / ((double)kTile * kTileE));
+}
+
+// Longest-processing-time schedule of the n_items * nd tiles (tile t: item
+// t % n_items of discretisation t / n_items) over `grid` CTAs: tiles in
+// descending cost, each to the CTA with the least work so far.  out: grid + 1
+// offsets, then every CTA's tiles in that order.
+void build_k3tc_schedule(int M, const int2* items, int n_items, int nd, int grid, std::vector<int>& out) {
+    const int n_tiles = n_items * nd;
+    std::vector<double> cost(n_items);
+    for (int i = 0; i < n_items; ++i) cost[i] = tile_cost(M, items[i]);
+    std::vector<int> order(n_tiles);
+    for (int t = 0; t < n_tiles; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return cost[x % n_items] > cost[y % n_items]; });
+    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> load;
+    for (int c = 0; c < grid; ++c) load.push({0.0, c});
+    std::vector<int> owner(n_tiles);
+    std::vector<int> count(grid, 0);
+    for (int t : order) {
+        auto [w, c] = load.top();
+        load.pop();
+        owner[t] = c;
+        ++count[c];
+        load.push({w + cost[t % n_items], c});
+    }
+    out.assign((size_t)grid + 1 + n_tiles, 0);
+    for (int c = 0; c < grid; ++c) out[c + 1] = out[c] + count[c];
+    std::vector<int> fill(out.begin(), out.begin() + grid);
+    for (int t : order) out[grid + 1 + fill[owner[t]]++] = t;
+}
+
+int k3tc_grid(int n_tiles) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return std::min(n_tiles, sms);
+}
+
 // the fixed layout above; (size_t)-1 if the tables exceed their capacity
 size_t k3tc_smem_bytes(int N0, int N1) {
     if (N0 >= kT0Cap || N1 >= kT1Cap || N0 + N1 >= kTBCap) return (size_t)-1;
@@ -898,7 +965,8 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
                         const int* perm, const PairC* pairs, unsigned long long* keys, int* err, double b0, double b1,
-                        cudaStream_t st, uint32_t* dump, TcTestHooks hooks, EmitTable emit) {
+                        cudaStream_t st, uint32_t* dump, TcTestHooks hooks, EmitTable emit, const int* sched,
+                        int sched_grid) {
     if (n_items == 0) return cudaSuccess;
     if (dump && emit.keys) return cudaErrorInvalidValue;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
@@ -917,6 +985,7 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
     if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
+    if (sched && sched_grid != grid) return cudaErrorInvalidValue;  // a schedule for another grid
     const unsigned long long wait_ns = hooks.wait_ns ? hooks.wait_ns : tc::kWaitLimitNs;
     K3Prune prune;
     const double scale = 4.0 * 0.6931471805599453 * std::ldexp(1.0, fbits);
@@ -931,15 +1000,15 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if (dump)
         k3tc_kernel<1><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
                                                      pairs, keys, err, prune, dump, wait_ns, hooks.withhold_kb, emit,
-                                                     emit_thr);
+                                                     emit_thr, sched);
     else if (emit.keys)
         k3tc_kernel<2><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
                                                      pairs, keys, err, prune, nullptr, wait_ns, hooks.withhold_kb,
-                                                     emit, emit_thr);
+                                                     emit, emit_thr, sched);
     else
         k3tc_kernel<0><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
                                                      pairs, keys, err, prune, nullptr, wait_ns, hooks.withhold_kb,
-                                                     emit, emit_thr);
+                                                     emit, emit_thr, sched);
     return cudaGetLastError();
 }
 
