@@ -842,15 +842,16 @@ void build_k3tc_items(int M, std::vector<int2>& items) {
 
 // Relative cost of a tile: its epilogue work, the warps (32-row quarters of the
 // a tile) with a valid row times the valid e columns, as a fraction of a full
-// item, but at least the share of the main loop (the same K blocks for every
-// item, overlapped with the epilogue of the previous one; about 0.4 of a full
-// epilogue in the timings of the scan).
+// item, but at least the main loop's (the same K blocks for every item,
+// overlapped with the epilogue of the previous one).  The floor was measured:
+// launch times are flat for floors of 0.6 to 0.9 of a full item, 2-4 % longer
+// at 0.25-0.4, and at 1.0 (every tile alike) as long as the fixed stride.
 static double tile_cost(int M, int2 item) {
     const int b = item.x, a0 = tile_a0(b, item.y >> 16), e0 = b + 1 + (item.y & 0xFFFF) * kTileE;
     int warps = 0;
     for (int q = 0; q < 4; ++q) warps += (a0 + 32 * q < b && a0 + 32 * q + 31 >= 0) ? 1 : 0;
     const int cols = std::min(kTileE, M - e0);
-    return std::max(0.4, (double)warps * 32.0 * cols / ((double)kTile * kTileE));
+    return std::max(0.75, (double)warps * 32.0 * cols / ((double)kTile * kTileE));
 }
 
 // Longest-processing-time schedule of the n_items * nd tiles (tile t: item
