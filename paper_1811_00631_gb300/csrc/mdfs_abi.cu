@@ -55,8 +55,8 @@ struct Workspace {
     Buffer bcounts, bonehot, btab, bcnt1, bsh1, bkeys;  // batch: class sizes; a chunk's operands and tables
     Buffer bsorted, bmult, bthr;  // batch: sorted keys of every variable; one job's multiplicities and thresholds
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
-    Buffer k3sched[2];                    // k = 3 tensor path: tile schedules of recent launch shapes
-    long long k3sched_key[2][5] = {{-1}, {-1}};
+    Buffer k3sched[2], k3claim;           // k = 3 tensor path: tile orders of recent launch shapes, claim counter
+    long long k3sched_key[2][4] = {{-1}, {-1}};
     int k3sched_next = 0;
     std::vector<int2> items2_host;        // the k = 3 tensor path's tile list (host copy)
     Buffer xe, srcb, igx, tux, dix, pext, padj, adjb, relb;  // contrast variables and the selection pipeline
@@ -81,7 +81,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &k3sched[0], &k3sched[1], &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
+                         &onehot2, &k3sched[0], &k3sched[1], &k3claim, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
                          &bcounts, &bonehot, &btab, &bcnt1, &bsh1, &bkeys, &bsorted, &bmult, &bthr};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
@@ -678,32 +678,32 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                                                    nullptr, (PairC*)ws->pairs2.p, fbits, st, (const int*)ws->lrank.p));
             int lo = 0;
             const int cnt = share(ws->n_items2, &lo);
-            // the tile schedule of this launch shape, built once and kept (two shapes)
-            const int* sched = nullptr;
-            const int grid = cnt > 0 ? k3tc_grid(cnt * nn) : 0;
-            if (grid > 0) {
-                const long long key[5] = {M, lo, cnt, nn, grid};
+            // the tiles' claim order for this launch shape, built once and kept (two shapes)
+            const int* order = nullptr;
+            if (cnt > 0) {
+                const long long key[4] = {M, lo, cnt, nn};
                 int slot = -1;
                 for (int e = 0; e < 2; ++e)
-                    if (std::equal(key, key + 5, ws->k3sched_key[e])) slot = e;
+                    if (std::equal(key, key + 4, ws->k3sched_key[e])) slot = e;
                 if (slot < 0) {
                     slot = ws->k3sched_next;
                     ws->k3sched_next ^= 1;
                     ws->k3sched_key[slot][0] = -1;
                     std::vector<int> sv;
-                    build_k3tc_schedule(M, ws->items2_host.data() + lo, cnt, nn, grid, sv);
+                    build_k3tc_order(M, ws->items2_host.data() + lo, cnt, nn, sv);
                     MDFS_ENSURE(ws, k3sched[slot], sv.size() * sizeof(int));
                     MDFS_CUDA_TRY(cudaMemcpyAsync(ws->k3sched[slot].p, sv.data(), sv.size() * sizeof(int),
                                                   cudaMemcpyHostToDevice, st));
                     MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `sv` is a pageable host vector
-                    std::copy(key, key + 5, ws->k3sched_key[slot]);
+                    std::copy(key, key + 4, ws->k3sched_key[slot]);
                 }
-                sched = (const int*)ws->k3sched[slot].p;
+                order = (const int*)ws->k3sched[slot].p;
             }
+            MDFS_ENSURE(ws, k3claim, sizeof(int));
             MDFS_LAUNCH("k3", st, launch_k3tc(map, (const uint8_t*)ws->onehot2.p, tg, M, d0, nn,
                                               (const int2*)ws->items2.p + lo, cnt, tab, fbits, (const int*)ws->cnt1s.p,
                                               lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, b0, b1, st,
-                                              dump, hooks, em, sched, grid));
+                                              dump, hooks, em, order, (int*)ws->k3claim.p));
         }
         *check_err = true;
     } else if (k == 3) {

@@ -233,13 +233,12 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
                         const int* perm, const PairC* pairs, unsigned long long* keys, int* err, double b0, double b1,
                         cudaStream_t st, uint32_t* dump = nullptr, TcTestHooks hooks = TcTestHooks(),
-                        EmitTable emit = EmitTable(), const int* sched = nullptr, int sched_grid = 0);
-// CTAs of a triple-kernel launch over n_tiles tiles (0 on a CUDA error), and
-// its schedule (device copy passed as launch_k3tc's sched with sched_grid =
-// grid): grid + 1 offsets, then each CTA's tiles, longest first by a cost
-// model of the epilogue (longest-processing-time assignment).
-int k3tc_grid(int n_tiles);
-void build_k3tc_schedule(int M, const int2* items, int n_items, int nd, int grid, std::vector<int>& out);
+                        EmitTable emit = EmitTable(), const int* order = nullptr, int* claim = nullptr);
+// Claim order of a triple-kernel launch (launch_k3tc's order, a device copy):
+// its n_items * nd tiles by descending cost of a model of the epilogue; with
+// claim (one device int, zeroed by the launch) the CTAs take tiles from it
+// dynamically, without it at a fixed stride.
+void build_k3tc_order(int M, const int2* items, int n_items, int nd, std::vector<int>& out);
 // Relabelling of the k = 3 tensor path, per discretisation: new labels in
 // ascending order of the bin-1 count (ties by index) for M <= 8192, else the
 // identity.  perm [D][M] new -> original, rank [D][M] original -> new,

@@ -72,6 +72,11 @@ constexpr uint32_t kTmemCols = 2 * kAccCols;   // double buffer
 constexpr int kThreads = 640;
 constexpr int kMaskWarp0 = 2, kMaskThreads = 64;
 constexpr int kEpiWarp0 = 4, kEpiThreads = 512;
+// Tiles are claimed by the producer and handed to the other roles, in order,
+// through a ring of tile ids in shared memory; every slot is released by the
+// MMA thread, each masker thread and each epilogue warp.
+constexpr int kRing = 8;
+constexpr int kRingReaders = 1 + kMaskThreads + kEpiThreads / 32;
 constexpr int kChunk = 32;                     // e columns per epilogue pass of a warp
 constexpr int kGroup = 4;                      // columns per TMEM load; pair records prefetched one group ahead
 constexpr int kRegsLaunch = 96, kRegsProducer = 32, kRegsEpilogue = 112;
@@ -182,18 +187,6 @@ __device__ __forceinline__ int key_threshold(unsigned long long key, int fbits) 
 // partial tiles' valid rows evenly over the four quarters.
 __host__ __device__ __forceinline__ int tile_a0(int b, int ta) { return (b & 1) ? b - kTile * (ta + 1) : kTile * ta; }
 
-// The tiles of this CTA, in order: list[begin .. begin + count) of a host-built
-// schedule (build_k3tc_schedule), or without one blockIdx.x + j gridDim.x
-// below n_tiles.  at(j) is -1 past the last.
-struct TileSeq {
-    const int* list;
-    int begin, count, n_tiles;
-    __device__ __forceinline__ int at(int j) const {
-        if (list) return j < count ? __ldg(list + begin + j) : -1;
-        const int t = (int)blockIdx.x + j * (int)gridDim.x;
-        return t < n_tiles ? t : -1;
-    }
-};
 
 // partner index of a key: (d M + lo) M + hi with the two partners sorted
 __device__ __forceinline__ uint32_t partner_index(uint32_t dM, int M, uint32_t p, uint32_t q) {
@@ -243,11 +236,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int* __restrict__ cnt1s, const int* __restrict__ perm, const PairC* __restrict__ pairs,
                 unsigned long long* __restrict__ keys, int* __restrict__ err, K3Prune prune,
                 uint32_t* __restrict__ dump, unsigned long long wait_ns, int withhold_kb, EmitTable emit,
-                int emit_thr, const int* __restrict__ sched) {
+                int emit_thr, const int* __restrict__ order, int* __restrict__ claim) {
     constexpr bool kDump = kMode == 1, kEmit = kMode == 2;
     extern __shared__ uint8_t dsmem_raw[];
     __shared__ uint64_t bar_full[kStages], bar_ready[kStages], bar_empty[kStages];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
+    __shared__ uint64_t bar_rfull[kRing], bar_rempty[kRing];
+    __shared__ int s_ring[kRing];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ float4 s_nu[kEpiThreads / 32][kChunk];
@@ -285,6 +280,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mbar_init(&bar_tempty[j], kEpiThreads);
         }
         tc::mbar_init(&bar_drain, 1);
+        for (int j = 0; j < kRing; ++j) {
+            tc::mbar_init(&bar_rfull[j], 1);
+            tc::mbar_init(&bar_rempty[j], kRingReaders);
+        }
         tc::mbar_fence_init();
     }
     if (warp == 1) {
@@ -303,9 +302,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = s_tmem;
     const int n_tiles = n_items * nd;
     const int nkb = tg.nkb;
-    // sched: [gridDim.x + 1] offsets, then the tile lists
-    const TileSeq seq{sched ? sched + gridDim.x + 1 : nullptr, sched ? sched[blockIdx.x] : 0,
-                      sched ? sched[blockIdx.x + 1] - sched[blockIdx.x] : 0, n_tiles};
+    volatile int* ring = s_ring;
+    // The j-th tile of this CTA from the ring: waits (bounded) for the producer
+    // to publish it, reads it, releases the slot; -1 when none is left or a
+    // wait gave up.  Every reader takes every tile.
+    auto ring_take = [&](int j) -> int {
+        const int slot = j % kRing;
+        if (!tc::mbar_wait(&bar_rfull[slot], (uint32_t)(j / kRing) & 1, abort, wait_ns)) return -1;
+        const int t = ring[slot];
+        tc::mbar_arrive(&bar_rempty[slot]);
+        return t;
+    };
     if (warp < kEpiWarp0) {
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsProducer));
       if (warp == 0) {
@@ -315,7 +322,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t g = 0;  // running K-block counter across this CTA's tiles
             int pend_mask = 0;
             uint32_t pend_use[kStages] = {};
-            for (int j = 0, t; (t = seq.at(j)) >= 0 && !*abort; ++j) {
+            // claims: the first tile by block index, then from the shared counter
+            // (dynamic; a fixed stride without one), in the order of `order`
+            // (descending cost; the identity without one)
+            int idx = blockIdx.x;
+            for (int j = 0;; ++j) {
+                const int slot = j % kRing;
+                if (j >= kRing && !tc::mbar_wait(&bar_rempty[slot], (uint32_t)(j / kRing - 1) & 1, abort, wait_ns))
+                    break;
+                const int t = (idx < n_tiles && !*abort) ? (order ? __ldg(order + idx) : idx) : -1;
+                ring[slot] = t;
+                tc::mbar_arrive(&bar_rfull[slot]);
+                if (t < 0) break;
+                idx = claim ? (int)gridDim.x + atomicAdd(claim, 1) : idx + (int)gridDim.x;
                 const int2 item = items[t % n_items];
                 const int d = d0 + t / n_items;
                 const int b = item.x, a0 = tile_a0(b, item.y >> 16), e0 = b + 1 + (item.y & 0xFFFF) * kTileE;
@@ -351,7 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
             uint32_t g = 0;
             bool issued = false;
-            for (int i = 0, t; (t = seq.at(i)) >= 0 && !*abort; ++i) {
+            for (int i = 0;; ++i) {
+                const int t = ring_take(i);
+                if (t < 0 || *abort) break;
                 const int buf = i & 1;
                 const uint32_t tuse = (uint32_t)(i >> 1);
                 const int2 item = items[t % n_items];
@@ -402,7 +423,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int slot = mt & 7, r0 = mt >> 3;
         const int jchunk = slot ^ (r0 & 7);
         uint32_t g = 0;
-        for (int j = 0, t; (t = seq.at(j)) >= 0 && !*abort; ++j) {
+        for (int j = 0;; ++j) {
+            const int t = ring_take(j);
+            if (t < 0 || *abort) break;
             const int2 item = items[t % n_items];
             const int a0 = tile_a0(item.x, item.y >> 16);
             const int rows = min(kTile, item.x - a0);  // rows with a < b (rows with a < 0 hold zeros)
@@ -445,7 +468,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         float2* csht = s_sht[ew];
         bool bad = false;       // inconsistent row or column constants
         uint32_t badbits = 0;   // OR of the pair records' count fields (checked at the end)
-        for (int i = 0, t; (t = seq.at(i)) >= 0 && !*abort; ++i) {
+        for (int i = 0;; ++i) {
+            // the tile, warp-uniform: every lane waits, lane 0 releases the slot
+            const int slot = i % kRing;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_rfull[slot], (uint32_t)(i / kRing) & 1, abort, wait_ns)))
+                break;
+            const int t = __shfl_sync(0xffffffffu, ring[slot], 0);
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bar_rempty[slot]);
+            if (t < 0 || __any_sync(0xffffffffu, *abort != 0)) break;
             const int buf = i & 1;
             const uint32_t tuse = (uint32_t)(i >> 1);
             const int2 item = items[t % n_items];
@@ -854,40 +885,18 @@ static double tile_cost(int M, int2 item) {
     return std::max(0.75, (double)warps * 32.0 * cols / ((double)kTile * kTileE));
 }
 
-// Longest-processing-time schedule of the n_items * nd tiles (tile t: item
-// t % n_items of discretisation t / n_items) over `grid` CTAs: tiles in
-// descending cost, each to the CTA with the least work so far.  out: grid + 1
-// offsets, then every CTA's tiles in that order.
-void build_k3tc_schedule(int M, const int2* items, int n_items, int nd, int grid, std::vector<int>& out) {
+// Claim order of the n_items * nd tiles (tile t: item t % n_items of
+// discretisation t / n_items): descending cost, ties by index.  CTAs claim the
+// next tile of this list when their producer is ready for one, so the heavy
+// tiles go first and the light ones fill the end (a dynamic
+// longest-processing-time schedule).
+void build_k3tc_order(int M, const int2* items, int n_items, int nd, std::vector<int>& out) {
     const int n_tiles = n_items * nd;
     std::vector<double> cost(n_items);
     for (int i = 0; i < n_items; ++i) cost[i] = tile_cost(M, items[i]);
-    std::vector<int> order(n_tiles);
-    for (int t = 0; t < n_tiles; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return cost[x % n_items] > cost[y % n_items]; });
-    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> load;
-    for (int c = 0; c < grid; ++c) load.push({0.0, c});
-    std::vector<int> owner(n_tiles);
-    std::vector<int> count(grid, 0);
-    for (int t : order) {
-        auto [w, c] = load.top();
-        load.pop();
-        owner[t] = c;
-        ++count[c];
-        load.push({w + cost[t % n_items], c});
-    }
-    out.assign((size_t)grid + 1 + n_tiles, 0);
-    for (int c = 0; c < grid; ++c) out[c + 1] = out[c] + count[c];
-    std::vector<int> fill(out.begin(), out.begin() + grid);
-    for (int t : order) out[grid + 1 + fill[owner[t]]++] = t;
-}
-
-int k3tc_grid(int n_tiles) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 0;
-    return std::min(n_tiles, sms);
+    out.resize(n_tiles);
+    for (int t = 0; t < n_tiles; ++t) out[t] = t;
+    std::stable_sort(out.begin(), out.end(), [&](int x, int y) { return cost[x % n_items] > cost[y % n_items]; });
 }
 
 // the fixed layout above; (size_t)-1 if the tables exceed their capacity
@@ -966,8 +975,8 @@ cudaError_t make_onehot_map(CUtensorMap* map, const uint8_t* oh, int rows, int D
 cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, int M, int d0, int nd,
                         const int2* items, int n_items, const long long* tab, int fbits, const int* cnt1s,
                         const int* perm, const PairC* pairs, unsigned long long* keys, int* err, double b0, double b1,
-                        cudaStream_t st, uint32_t* dump, TcTestHooks hooks, EmitTable emit, const int* sched,
-                        int sched_grid) {
+                        cudaStream_t st, uint32_t* dump, TcTestHooks hooks, EmitTable emit, const int* order,
+                        int* claim) {
     if (n_items == 0) return cudaSuccess;
     if (dump && emit.keys) return cudaErrorInvalidValue;
     const size_t smem = k3tc_smem_bytes(tg.N0, tg.N1);
@@ -986,7 +995,7 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
     if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(n_tiles, (long long)sms);
-    if (sched && sched_grid != grid) return cudaErrorInvalidValue;  // a schedule for another grid
+    if (claim && (e = cudaMemsetAsync(claim, 0, sizeof(int), st)) != cudaSuccess) return e;
     const unsigned long long wait_ns = hooks.wait_ns ? hooks.wait_ns : tc::kWaitLimitNs;
     K3Prune prune;
     const double scale = 4.0 * 0.6931471805599453 * std::ldexp(1.0, fbits);
@@ -1001,15 +1010,15 @@ cudaError_t launch_k3tc(const CUtensorMap& map, const uint8_t* oh, TcGeom tg, in
     if (dump)
         k3tc_kernel<1><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
                                                      pairs, keys, err, prune, dump, wait_ns, hooks.withhold_kb, emit,
-                                                     emit_thr, sched);
+                                                     emit_thr, order, claim);
     else if (emit.keys)
         k3tc_kernel<2><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
                                                      pairs, keys, err, prune, nullptr, wait_ns, hooks.withhold_kb,
-                                                     emit, emit_thr, sched);
+                                                     emit, emit_thr, order, claim);
     else
         k3tc_kernel<0><<<grid, kThreads, smem, st>>>(map, oh, tg, M, d0, nd, items, n_items, tab, fbits, cnt1s, perm,
                                                      pairs, keys, err, prune, nullptr, wait_ns, hooks.withhold_kb,
-                                                     emit, emit_thr, sched);
+                                                     emit, emit_thr, order, claim);
     return cudaGetLastError();
 }
 
