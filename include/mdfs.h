@@ -112,6 +112,25 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
                 void* stream);
 
 /*
+ * IG^k_max of several dimensions k of the same data and discretisations in
+ * one call (the analyses "in all possible dimensionalities" of section
+ * "Examples", Tables 1-2): entry j is exactly mdfs_max_ig with k = ks[j].
+ *
+ * ks:         n_k (1 .. 5) distinct values in 1 .. 5.
+ * ig:         [n_k] pointers, ig[j] as mdfs_max_ig's ig for k = ks[j].
+ * tuples:     NULL, or [n_k] pointers, each NULL or [M][ks[j]-1] int32.
+ * best_disc:  NULL, or [n_k] pointers, each NULL or [M] int32.
+ * The scans share the staged inputs and their validation (one host round
+ * trip).  Where the tensor-core kernels serve both k = 2 and k = 3 (two
+ * classes, class sizes below 4096), k = 1, 2 and 3 also share one
+ * discretisation, its single counts and its one-hot rows.  Errors and
+ * ownership as for mdfs_max_ig; on an error some outputs may be written.
+ */
+int mdfs_max_ig_multi(const mdfs_data* data, int n_k, const int* ks, int divisions, int discretizations,
+                      double range, double pc_xi, uint64_t seed, float* const* ig, int32_t* const* tuples,
+                      int32_t* const* best_disc, void* stream);
+
+/*
  * Batched scan: n_jobs independent mdfs_max_ig jobs over resamples of one
  * dataset, e.g. bootstrap or cross-validation folds and y-permutation nulls
  * (the null distribution the significance test of section "Theory" is fitted

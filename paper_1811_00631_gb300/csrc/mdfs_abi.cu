@@ -56,6 +56,7 @@ struct Workspace {
     Buffer bsorted, bmult, bthr;  // batch: sorted keys of every variable; one job's multiplicities and thresholds
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
     Buffer k3sched[2], k3claim;           // k = 3 tensor path: tile orders of recent launch shapes, claim counter
+    Buffer mkeys;                         // several-k calls: the k = 1 and k = 2 keys of a fused scan
     long long k3sched_key[2][4] = {{-1}, {-1}};
     int k3sched_next = 0;
     std::vector<int2> items2_host;        // the k = 3 tensor path's tile list (host copy)
@@ -81,7 +82,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &k3sched[0], &k3sched[1], &k3claim, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
+                         &onehot2, &k3sched[0], &k3sched[1], &k3claim, &mkeys, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
                          &bcounts, &bonehot, &btab, &bcnt1, &bsh1, &bkeys, &bsorted, &bmult, &bthr};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
@@ -543,13 +544,27 @@ int tuned_k2_stages(Workspace* ws, const char* kernel, const K2Jobs& jobs, int M
     return best;
 }
 
+// Whether the tensor-core kernels serve k = 2 (two or three classes) and k = 3
+// (two classes): their fixed-point tables must fit shared memory, and the class
+// sizes their counters hold.
+bool tc2_applies(int c, int N, int n0, int n1) {
+    return k2tc_supported(c) && k2tc_counts_fit(c, n0, n1) && k2tc_smem_bytes(c, N, 1, 3) <= kK3tcMaxSmem;
+}
+bool tc3_applies(int c, int n0, int n1) { return c == 2 && k3tc_smem_bytes(n0, n1) != (size_t)-1; }
+// a k = 2 and a k = 3 scan of the same data can share one discretisation and its one-hot rows
+bool fused_k23_applies(int c, int N, int n0, int n1) { return tc3_applies(c, n0, n1) && tc2_applies(c, N, n0, n1); }
+
 // dump != NULL (test hook, mdfs_testing_counts): the tensor-core kernel also
 // writes its class counts there; the call fails if that kernel does not apply.
 // keep_err: leave the tensor-core error flag as it is (a batch clears it once
-// and reads it after its last job).
+// and reads it after its last job).  keys1x != NULL: also the k = 1 keys of the
+// same discretisation there.  keys2x != NULL (k = 3 on the tensor-core path
+// with a k = 2 tensor-core scan that applies, fused_k23_applies): also the k = 2
+// keys, from the same one-hot rows.
 int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, int k, int divisions, int D, double range,
               double pc_xi, uint64_t seed, bool* check_err, int shard = 0, int n_shards = 1,
-              const EmitTable* emit = nullptr, uint32_t* dump = nullptr, bool keep_err = false) {
+              const EmitTable* emit = nullptr, uint32_t* dump = nullptr, bool keep_err = false,
+              unsigned long long* keys1x = nullptr, unsigned long long* keys2x = nullptr) {
     cudaStream_t st = ws->stream;
     auto share = [&](int n, int* lo) {
         *lo = (int)((long long)n * shard / n_shards);
@@ -585,11 +600,10 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
     // tensor-core paths: k = 2 for two or three classes, k = 3 for two classes,
     // when their fixed-point tables fit in shared memory
     const EmitTable em = emit ? *emit : EmitTable();
-    const bool use_tc2 = (k == 2 && k2tc_supported(c) && k2tc_counts_fit(c, n0, n1) &&
-                          k2tc_smem_bytes(c, N, 1, 3) <= kK3tcMaxSmem);
-    // the triple kernel's layout is fixed (it fits the opt-in shared memory of sm_103a); it needs class sizes
-    // below its table capacities
-    const bool use_tc3 = (k == 3 && c == 2 && k3tc_smem_bytes(n0, n1) != (size_t)-1);
+    const bool use_tc2 = k == 2 && tc2_applies(c, N, n0, n1);
+    const bool use_tc3 = k == 3 && tc3_applies(c, n0, n1);
+    if (keys2x && !(use_tc3 && tc2_applies(c, N, n0, n1) && shard == 0 && n_shards == 1 && !emit && !dump))
+        return fail(MDFS_EINVAL, "internal: the fused k = 2, 3 scan does not apply");
     TcGeom tg = make_tc_geom(n0, n1);
     if (dump && !use_tc2 && !use_tc3)
         return fail(MDFS_EINVAL, "no tensor-core kernel serves k = %d, %d classes, N0 = %d, N1 = %d", k, c, n0, n1);
@@ -602,11 +616,15 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                                                     planes, nullptr, nullptr, onehot, tg, st,
                                                     use_tc2 ? k2tc_class1_byte(c) : 0x38u));
     MDFS_CUDA_TRY(cudaMemsetAsync(keys, 0, (size_t)M * sizeof(unsigned long long), st));
-    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, (k == 1 && shard == 0) ? keys : nullptr, st,
+    if (keys1x) MDFS_CUDA_TRY(cudaMemsetAsync(keys1x, 0, (size_t)M * sizeof(unsigned long long), st));
+    if (keys2x) MDFS_CUDA_TRY(cudaMemsetAsync(keys2x, 0, (size_t)M * sizeof(unsigned long long), st));
+    MDFS_LAUNCH("k1", st, launch_k1(planes, g, M, c, D, tab, cnt1, sh1, (k == 1 && shard == 0) ? keys : keys1x, st,
                                     k == 1 ? em : EmitTable()));
-    if (use_tc2) {
+    // the k = 2 tensor-core scan of the one-hot rows into kout (a k = 2 call, or
+    // the k = 2 part of a fused k = 2, 3 call, which clears the error flag once)
+    auto run_tc2 = [&](unsigned long long* kout, bool clear_err) -> int {
         MDFS_ENSURE(ws, err, sizeof(int));
-        if (!keep_err) MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
+        if (clear_err) MDFS_CUDA_TRY(cudaMemsetAsync(ws->err.p, 0, sizeof(int), st));
         if (ws->items3_M != M || ws->items3_c != c) {
             std::vector<int2> items;
             build_k2tc_items(M, c, items);
@@ -623,7 +641,7 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         const bool exact = take_test_hooks(false).exact;
         K2Jobs jobs{};
         jobs.n = 1;
-        jobs.job[0] = K2Job{tg, tab, cnt1, sh1, keys, (float)b0, (float)b1};
+        jobs.job[0] = K2Job{tg, tab, cnt1, sh1, kout, (float)b0, (float)b1};
         // the count test hook and emission run the deepest pipeline that fits (no tuning runs)
         const int stages = (dump || emit) ? (k2tc_smem_bytes(c, N, 1, 4) <= kK3tcMaxSmem ? 4 : 3)
                                           : tuned_k2_stages(ws, "k2tc_stages", jobs, M, c, D,
@@ -633,6 +651,11 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
         MDFS_LAUNCH("k2", st, launch_k2tc(onehot, tg.Kp, D, jobs, M, c, 0, D, D, (const int2*)ws->items3.p + lo, cnt,
                                           k3tc_fraction_bits(N), (int*)ws->err.p, !exact, stages, st, dump, em));
         *check_err = true;
+        return MDFS_OK;
+    };
+    if (use_tc2) {
+        const int rc2 = run_tc2(keys, !keep_err);
+        if (rc2) return rc2;
     } else if (k == 2) {
         if (shard == 0)
             MDFS_LAUNCH("k2", st, launch_k2(planes, g, M, c, D, 0, D, tab, cnt1, sh1, keys, nullptr, nullptr, nullptr, 0, st,
@@ -700,6 +723,10 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
                 order = (const int*)ws->k3sched[slot].p;
             }
             MDFS_ENSURE(ws, k3claim, sizeof(int));
+            if (keys2x && d0 == 0) {  // the k = 2 keys of the fused call, once
+                const int rc2 = run_tc2(keys2x, false);
+                if (rc2) return rc2;
+            }
             MDFS_LAUNCH("k3", st, launch_k3tc(map, (const uint8_t*)ws->onehot2.p, tg, M, d0, nn,
                                               (const int2*)ws->items2.p + lo, cnt, tab, fbits, (const int*)ws->cnt1s.p,
                                               lperm, (const PairC*)ws->pairs2.p, keys, (int*)ws->err.p, b0, b1, st,
@@ -1049,6 +1076,89 @@ int mdfs_max_ig(const mdfs_data* data, int k, int divisions, int discretizations
         const int flag = ws->host_stats[8];
         if (flag) return kernel_flag_error(flag);
     } else if (oig.staged || otu.staged || odi.staged || st == nullptr) {
+        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return MDFS_OK;
+}
+
+int mdfs_max_ig_multi(const mdfs_data* data, int n_k, const int* ks, int divisions, int discretizations, double range,
+                      double pc_xi, uint64_t seed, float* const* ig, int32_t* const* tuples, int32_t* const* best_disc,
+                      void* stream) {
+    g_err.clear();
+    g_launches = 0;
+    int rc = check_data(data, true);
+    if (rc) return rc;
+    const int N = data->N, M = data->M, D = discretizations, c = divisions + 1;
+    if (n_k < 1 || n_k > 5 || !ks || !ig) return fail(MDFS_EINVAL, "n_k = %d outside [1, 5], or ks / ig NULL", n_k);
+    int slot_of[6] = {-1, -1, -1, -1, -1, -1};  // output slot of each k
+    for (int j = 0; j < n_k; ++j) {
+        const int k = ks[j];
+        if (k < 1 || k > 5) return fail(MDFS_EINVAL, "ks[%d] = %d outside [1, 5]", j, k);
+        if (slot_of[k] >= 0) return fail(MDFS_EINVAL, "k = %d appears twice in ks", k);
+        slot_of[k] = j;
+        if ((rc = check_scan_args(k, M, divisions, N, D, range, pc_xi))) return rc;
+        if (!ig[j]) return fail(MDFS_EINVAL, "ig[%d] is NULL", j);
+    }
+    for (int j = 0; j < n_k; ++j)
+        if ((rc = check_devices({{data->x, "x"}, {data->y, "y"}, {ig[j], "ig"}, {tuples ? tuples[j] : nullptr, "tuples"},
+                                 {best_disc ? best_disc[j] : nullptr, "best_disc"}})))
+            return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws(st, &rc);
+    if (!ws) return rc;
+    const void* xd = nullptr;
+    const uint8_t* yd = nullptr;
+    int n1 = 0;
+    rc = stage_inputs(ws, data, true, &xd, &yd, &n1);
+    if (rc) return rc;
+    // decodes keys of dimension k into output slot j (staged outputs copied back at once)
+    bool any_staged = false;
+    auto finish = [&](const unsigned long long* keys, int k) -> int {
+        const int j = slot_of[k];
+        Out<float> oig;
+        Out<int32_t> otu, odi;
+        int r = bind_out(ws, ws->ig, ig[j], (size_t)M, &oig);
+        if (!r) r = bind_out(ws, ws->tuples, (k > 1 && tuples) ? tuples[j] : (int32_t*)nullptr,
+                             (size_t)M * (k > 1 ? k - 1 : 1), &otu);
+        if (!r) r = bind_out(ws, ws->disc, best_disc ? best_disc[j] : (int32_t*)nullptr, (size_t)M, &odi);
+        if (r) return r;
+        MDFS_LAUNCH("finalize", st, launch_finalize(keys, M, k, oig.dev, otu.dev, odi.dev, st, wide_disc(ws)));
+        if ((r = copy_back(ws, oig)) || (r = copy_back(ws, otu)) || (r = copy_back(ws, odi))) return r;
+        any_staged = any_staged || oig.staged || otu.staged || odi.staged;
+        return MDFS_OK;
+    };
+    bool check_err = false, done[6] = {};
+    // k = 1, 2 and 3 from one discretisation where the tensor-core kernels serve k = 2 and k = 3
+    if (slot_of[3] >= 0 && (slot_of[1] >= 0 || slot_of[2] >= 0) && fused_k23_applies(c, N, N - n1, n1)) {
+        MDFS_ENSURE(ws, mkeys, (size_t)2 * M * sizeof(unsigned long long));
+        unsigned long long* k1x = slot_of[1] >= 0 ? (unsigned long long*)ws->mkeys.p : nullptr;
+        unsigned long long* k2x = slot_of[2] >= 0 ? (unsigned long long*)ws->mkeys.p + M : nullptr;
+        bool ce = false;
+        rc = scan_core(ws, xd, data->dtype, N, M, n1, 3, divisions, D, range, pc_xi, seed, &ce, 0, 1, nullptr,
+                       nullptr, false, k1x, k2x);
+        if (rc) return rc;
+        check_err = check_err || ce;
+        if ((rc = finish((const unsigned long long*)ws->keys.p, 3))) return rc;
+        if (k1x && (rc = finish(k1x, 1))) return rc;
+        if (k2x && (rc = finish(k2x, 2))) return rc;
+        done[1] = done[2] = done[3] = true;
+    }
+    for (int k = 1; k <= 5; ++k) {
+        if (slot_of[k] < 0 || done[k]) continue;
+        bool ce = false;
+        // a later scan keeps the tensor-core error flag of an earlier one
+        rc = scan_core(ws, xd, data->dtype, N, M, n1, k, divisions, D, range, pc_xi, seed, &ce, 0, 1, nullptr,
+                       nullptr, check_err);
+        if (rc) return rc;
+        check_err = check_err || ce;
+        if ((rc = finish((const unsigned long long*)ws->keys.p, k))) return rc;
+    }
+    if (check_err) {
+        MDFS_CUDA_TRY(cudaMemcpyAsync(ws->host_stats + 8, ws->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MDFS_CUDA_TRY(cudaStreamSynchronize(st));
+        const int flag = ws->host_stats[8];
+        if (flag) return kernel_flag_error(flag);
+    } else if (any_staged || st == nullptr) {
         MDFS_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return MDFS_OK;

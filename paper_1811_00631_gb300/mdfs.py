@@ -31,7 +31,7 @@ _ERRORS = {
     -7: "MDFS_ETRUNCATED",
 }
 
-EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
+EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_max_ig_multi", "mdfs_ig_lim", "mdfs_last_error", "mdfs_release",
             "mdfs_abi_version", "mdfs_last_launch_count", "mdfs_profile", "mdfs_profile_report",
             "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
             "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples",
@@ -73,6 +73,9 @@ def load(path: str = LIB_PATH):
         lib.mdfs_max_ig.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
         lib.mdfs_max_ig.restype = ctypes.c_int
+        lib.mdfs_max_ig_multi.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
+        lib.mdfs_max_ig_multi.restype = ctypes.c_int
         lib.mdfs_max_ig_noalloc.argtypes = [ctypes.POINTER(_Data), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P, P, P, P]
         lib.mdfs_max_ig_noalloc.restype = ctypes.c_int
@@ -265,6 +268,46 @@ def max_ig(x, y, k: int = 2, divisions: int = 1, discretizations: int = 1, range
     _check(rc)
     del keep
     return ig, tu[:, : k - 1], di
+
+
+def max_ig_multi(x, y, ks=(2, 3), divisions: int = 1, discretizations: int = 1, range_: float = 0.0,
+                 pc_xi: float = 0.25, seed: int = 0, out=None):
+    """mdfs_max_ig_multi: IG^k_max for every k in ``ks`` (distinct, 1..5) of the same
+    data and discretisations in one call; entry k equals max_ig with that k.
+
+    Returns {k: (ig f32[M], tuples i32[M, k-1], disc i32[M])} on the device of x
+    (torch tensors) or on the host (numpy arrays).  ``out`` may pass a dict of
+    preallocated triples of the matching kind.
+    """
+    lib = load()
+    data, keep = _data(x, y)
+    M = data.M
+    ks = [int(k) for k in ks]
+    res, ptrs = {}, []
+    for k in ks:
+        kk = max(k - 1, 1)
+        if out is not None and k in out:
+            _check_out(out[k], ((M,), (M, kk), (M,)), (np.float32, np.int32, np.int32), x)
+            trip = out[k]
+        elif _is_cuda(x):
+            import torch
+            trip = (torch.empty(M, dtype=torch.float32, device=x.device),
+                    torch.empty((M, kk), dtype=torch.int32, device=x.device),
+                    torch.empty(M, dtype=torch.int32, device=x.device))
+        else:
+            trip = (np.empty(M, dtype=np.float32), np.empty((M, kk), dtype=np.int32), np.empty(M, dtype=np.int32))
+        res[k] = trip
+        ptrs.append(tuple(t.data_ptr() if _is_cuda(x) else t.ctypes.data for t in trip))
+    n = len(ks)
+    karr = (ctypes.c_int * n)(*ks)
+    igp = (ctypes.c_void_p * n)(*[p[0] for p in ptrs])
+    tup = (ctypes.c_void_p * n)(*[p[1] if k > 1 else None for p, k in zip(ptrs, ks)])
+    dip = (ctypes.c_void_p * n)(*[p[2] for p in ptrs])
+    rc = lib.mdfs_max_ig_multi(ctypes.byref(data), n, karr, divisions, discretizations, float(range_), float(pc_xi),
+                               int(seed) & (2**64 - 1), igp, tup, dip, _stream_of(x) if _is_cuda(x) else None)
+    _check(rc)
+    del keep
+    return {k: (ig, tu[:, : k - 1], di) for k, (ig, tu, di) in res.items()}
 
 
 def max_ig_batch(x, y, sample_idx=None, y_perm=None, n_jobs=None, k: int = 2, divisions: int = 1,

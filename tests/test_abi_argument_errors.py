@@ -33,7 +33,24 @@ def max_ig(data=None, k=2, div=1, D=1, r=0.5, xi=0.25, ig=P):
     return lambda lib: lib.mdfs_max_ig(data or _data(), k, div, D, r, xi, 1, ig, P, P, None)
 
 
+def max_ig_multi(ks=(2, 3), n_k=None, ig_null=None, ig_all_null=False, k_null=False, div=1):
+    n = len(ks) if n_k is None else n_k
+    karr = (ctypes.c_int * max(len(ks), 1))(*ks)
+    ptrs = (ctypes.c_void_p * max(len(ks), 1))(*[None if j == ig_null else P.value for j in range(len(ks))])
+    return lambda lib: lib.mdfs_max_ig_multi(_data(), n, None if k_null else karr, div, 1, 0.5, 0.25, 1,
+                                             None if ig_all_null else ptrs, None, None, None)
+
+
 CASES = [
+    ("max_ig_multi: n_k = 0", max_ig_multi(n_k=0), "n_k = 0"),
+    ("max_ig_multi: n_k = 6", max_ig_multi(ks=(1, 2, 3, 4, 5, 1)), "n_k = 6"),
+    ("max_ig_multi: ks NULL", max_ig_multi(k_null=True), "ks / ig NULL"),
+    ("max_ig_multi: ig NULL", max_ig_multi(ig_all_null=True), "ks / ig NULL"),
+    ("max_ig_multi: k = 0", max_ig_multi(ks=(2, 0)), "ks[1] = 0"),
+    ("max_ig_multi: k = 6", max_ig_multi(ks=(6,)), "ks[0] = 6"),
+    ("max_ig_multi: k twice", max_ig_multi(ks=(3, 2, 3)), "k = 3 appears twice"),
+    ("max_ig_multi: ig[1] NULL", max_ig_multi(ks=(1, 3), ig_null=1), "ig[1] is NULL"),
+    ("max_ig_multi: k = 4 with three classes", max_ig_multi(ks=(2, 4), div=2), "two classes"),
     ("max_ig: k = 0", max_ig(k=0), "k = 0"),
     ("max_ig: k = 6", max_ig(k=6), "k = 6"),
     ("max_ig: M < k", max_ig(data=_data(M=2), k=3), "smaller than k"),
