@@ -57,6 +57,8 @@ struct Workspace {
     Buffer lperm, lrank, cnt1s, onehot2;  // k = 3 tensor path: relabelling and relabelled operands
     Buffer k3sched[2], k3claim;           // k = 3 tensor path: tile orders of recent launch shapes, claim counter
     Buffer mkeys;                         // several-k calls: the k = 1 and k = 2 keys of a fused scan
+    Buffer itemsg;                        // k = 4, 5 with three or four classes: pair items
+    int itemsg_M = -1, itemsg_k = -1, n_itemsg = 0;
     long long k3sched_key[2][4] = {{-1}, {-1}};
     int k3sched_next = 0;
     std::vector<int2> items2_host;        // the k = 3 tensor path's tile list (host copy)
@@ -82,7 +84,7 @@ struct Workspace {
         Buffer* all[] = {&x,  &y,  &stats, &perm,   &tab, &planes, &cnt1, &sh1,   &keys, &sh2,  &cnt2,
                          &items, &ig, &tuples, &disc, &codes, &mask,  &pv,   &res, &pairs2, &items2,
                          &onehot, &err, &bx,   &by,  &bidx, &bperm, &items3, &lperm, &lrank, &cnt1s,
-                         &onehot2, &k3sched[0], &k3sched[1], &k3claim, &mkeys, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
+                         &onehot2, &k3sched[0], &k3sched[1], &k3claim, &mkeys, &itemsg, &xe, &srcb, &igx, &tux, &dix, &pext, &padj, &adjb, &relb, &items4, &items5, &items3t, &t3c, &t3s, &t4c, &t4s, &tabw, &keys5, &kdisc, &ekeys, &evals, &ecnt, &erk, &erv,
                          &bcounts, &bonehot, &btab, &bcnt1, &bsh1, &bkeys, &bsorted, &bmult, &bthr};
         for (Buffer* b : all)
             if (b->p) cudaFree(b->p);
@@ -272,7 +274,10 @@ unsigned long long binom4(int M) {
     return M < 4 ? 0ull : m * (m - 1) / 2 * (m - 2) / 3 * (m - 3) / 4;
 }
 int check_k5(int M, int c, int D, int N, bool single_key = false) {
-    if (c != 2) return fail(MDFS_EINVAL, "k = 5 supports two classes per variable (divisions = 1)");
+    if (c != 2 && !kgen_supported(5, c))
+        return fail(MDFS_EINVAL, "k = 5 supports two to four classes per variable (divisions 1 .. 3)");
+    // the scan of three or more classes keeps one key word: d C(M,4) + rank
+    if (c != 2) single_key = true;
     if (N > 65535) return fail(MDFS_EINVAL, "k = 5 supports N up to 65535 samples");
     if (binom4(M) >= (1ull << 32)) return fail(MDFS_EINVAL, "C(M, 4) must stay below 2^32 for k = 5");
     if (single_key && (unsigned long long)D * binom4(M) >= (1ull << 32))
@@ -297,7 +302,8 @@ int check_scan_args(int k, int M, int divisions, int N, int D, double range, dou
     if (k == 2 && d * m >= (1ull << 32)) return fail(MDFS_EINVAL, "discretizations * M too large");
     if (k == 3 && d * m * m >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^2 must stay below 2^32 for k = 3");
-    if (k == 4 && c != 2) return fail(MDFS_EINVAL, "k = 4 supports two classes per variable (divisions = 1)");
+    if (k == 4 && c != 2 && !kgen_supported(4, c))
+        return fail(MDFS_EINVAL, "k = 4 supports two to four classes per variable (divisions 1 .. 3)");
     if (k == 4 && d * m * m * m >= (1ull << 32))
         return fail(MDFS_EINVAL, "discretizations * M^3 must stay below 2^32 for k = 4");
     if (k == 5 && (rc = check_k5(M, c, D, N, shard_keys))) return rc;
@@ -762,6 +768,27 @@ int scan_core(Workspace* ws, const void* xd, int dtype, int N, int M, int n1, in
             MDFS_LAUNCH("k3", st, launch_k3_items(planes, g, M, c, d0, nn, (const int2*)ws->items.p + lo, cnt, tab,
                                                   cnt1, (const long long*)ws->sh2.p, (const int*)ws->cnt2.p, keys, st,
                                                   em));
+        }
+    } else if ((k == 4 || k == 5) && c != 2) {
+        // three or four classes: every voxel of every tuple from the bit planes
+        if (ws->itemsg_M != M || ws->itemsg_k != k) {
+            std::vector<int2> items;
+            build_kgen_items(M, k, items);
+            MDFS_ENSURE(ws, itemsg, std::max<size_t>(items.size(), 1) * sizeof(int2));
+            if (!items.empty())
+                MDFS_CUDA_TRY(cudaMemcpyAsync(ws->itemsg.p, items.data(), items.size() * sizeof(int2),
+                                              cudaMemcpyHostToDevice, st));
+            MDFS_CUDA_TRY(cudaStreamSynchronize(st));  // `items` is a pageable host vector
+            ws->itemsg_M = M;
+            ws->itemsg_k = k;
+            ws->n_itemsg = (int)items.size();
+        }
+        int lo = 0;
+        const int cnt = share(ws->n_itemsg, &lo);
+        for (int d0 = 0; d0 < D; d0 += 65535) {
+            const int nn = std::min(65535, D - d0);
+            MDFS_LAUNCH(k == 4 ? "k4" : "k5", st, launch_kgen(planes, g, M, c, k, d0, nn,
+                                                              (const int2*)ws->itemsg.p + lo, cnt, tab, keys, em, st));
         }
     } else if (k == 4) {
         // two classes: pair counts from the pair pass, triple tables, then the quadruple kernel

@@ -207,6 +207,17 @@ cudaError_t launch_emit_collect(EmitTable t, int k, unsigned long long* recs_key
 // operands through TMA, counts in TMEM, fused entropy epilogue.  pairs must be
 // symmetric ([i][m] and [m][i] both written).  err: device flag set on a
 // bounded-wait timeout.
+// k = 4, 5 with three or four classes per variable (mdfs_kgen.cu): every voxel
+// of every tuple counted from the bit planes, one warp per tuple.  items:
+// pairs (a, b) of the two lowest variables (build_kgen_items), one CTA each, for
+// discretisations [d0, d0 + nd); keys indexed as the two-class scans index
+// them (k = 5: D C(M,4) < 2^32); emit.keys != NULL: also every qualifying role.
+bool kgen_supported(int k, int c);
+void build_kgen_items(int M, int k, std::vector<int2>& items);
+cudaError_t launch_kgen(const uint32_t* planes, PlaneGeom g, int M, int c, int k, int d0, int nd, const int2* items,
+                        int n_items, const long long* tab, unsigned long long* keys, EmitTable emit,
+                        cudaStream_t st);
+
 TcGeom make_tc_geom(int N0, int N1);
 void build_k3tc_items(int M, std::vector<int2>& items);
 size_t k3tc_smem_bytes(int N0, int N1);

@@ -33,11 +33,11 @@ def max_ig(data=None, k=2, div=1, D=1, r=0.5, xi=0.25, ig=P):
     return lambda lib: lib.mdfs_max_ig(data or _data(), k, div, D, r, xi, 1, ig, P, P, None)
 
 
-def max_ig_multi(ks=(2, 3), n_k=None, ig_null=None, ig_all_null=False, k_null=False, div=1):
+def max_ig_multi(ks=(2, 3), n_k=None, ig_null=None, ig_all_null=False, k_null=False, div=1, data=None):
     n = len(ks) if n_k is None else n_k
     karr = (ctypes.c_int * max(len(ks), 1))(*ks)
     ptrs = (ctypes.c_void_p * max(len(ks), 1))(*[None if j == ig_null else P.value for j in range(len(ks))])
-    return lambda lib: lib.mdfs_max_ig_multi(_data(), n, None if k_null else karr, div, 1, 0.5, 0.25, 1,
+    return lambda lib: lib.mdfs_max_ig_multi(data or _data(), n, None if k_null else karr, div, 1, 0.5, 0.25, 1,
                                              None if ig_all_null else ptrs, None, None, None)
 
 
@@ -50,7 +50,7 @@ CASES = [
     ("max_ig_multi: k = 6", max_ig_multi(ks=(6,)), "ks[0] = 6"),
     ("max_ig_multi: k twice", max_ig_multi(ks=(3, 2, 3)), "k = 3 appears twice"),
     ("max_ig_multi: ig[1] NULL", max_ig_multi(ks=(1, 3), ig_null=1), "ig[1] is NULL"),
-    ("max_ig_multi: k = 4 with three classes", max_ig_multi(ks=(2, 4), div=2), "two classes"),
+    ("max_ig_multi: k = 4 keys overflow", max_ig_multi(ks=(2, 4), div=2, data=_data(M=2000)), "2^32"),
     ("max_ig: k = 0", max_ig(k=0), "k = 0"),
     ("max_ig: k = 6", max_ig(k=6), "k = 6"),
     ("max_ig: M < k", max_ig(data=_data(M=2), k=3), "smaller than k"),
@@ -72,7 +72,7 @@ CASES = [
     ("max_ig: N above the limit", max_ig(data=_data(N=32769)), "N = 32769"),
     ("max_ig: M = 0", max_ig(data=_data(M=0)), "M = 0"),
     ("max_ig: M = 65536", max_ig(data=_data(M=65536)), "M = 65536"),
-    ("max_ig: k = 4 with three classes", max_ig(k=4, div=2), "two classes"),
+    ("max_ig: k = 5, three classes, keys overflow", max_ig(data=_data(M=200), k=5, div=2, D=67), "2^32"),
     ("max_ig: k = 3 keys overflow", max_ig(data=_data(M=65535), k=3, D=2), "2^32"),
     ("max_ig: k = 4 keys overflow", max_ig(data=_data(M=2000), k=4, D=1), "2^32"),
     ("discretize: divisions = 0",

@@ -91,11 +91,15 @@ def test_k5_errors(cuda):
     x = np.random.default_rng(0).standard_normal((7, 50)).astype(np.float32)
     y = (np.arange(50) % 2).astype(np.uint8)
     with pytest.raises(mdfs.MdfsError):
-        mdfs.max_ig(x, y, 5, 2, 1)  # three classes: not supported at k = 5
+        mdfs.max_ig(x, y, 5, 4, 1)  # five classes: more than any scan supports
     with pytest.raises(mdfs.MdfsError):
         mdfs.max_ig(x[:4], y, 5, 1, 1)  # fewer variables than k
     with pytest.raises(mdfs.MdfsError):
-        mdfs.interesting_tuples(x, y, 5, 2, 1)  # three classes
+        mdfs.interesting_tuples(x, y, 5, 4, 1)  # five classes
+    xm = np.random.default_rng(2).standard_normal((200, 8)).astype(np.float32)
+    ym = (np.arange(8) % 2).astype(np.uint8)
+    with pytest.raises(mdfs.MdfsError):
+        mdfs.max_ig(xm, ym, 5, 2, 67)  # three classes: 67 C(200, 4) >= 2^32 (one key word)
     xl = np.random.default_rng(1).standard_normal((600, 8)).astype(np.float32)
     yl = (np.arange(8) % 2).astype(np.uint8)
     with pytest.raises(mdfs.MdfsError):
