@@ -409,6 +409,8 @@ def run_gpu(args, rank, world, local_rank):
         line["interesting"] = interesting_run(args.interesting_reps, local_rank)
     if args.k4 and DIV == 1 and DISC * M_VAR ** 3 < 2**32:
         line["k4"] = k4_run(local_rank)
+    if args.kgen:
+        line["kgen"] = kgen_run(local_rank)
     if args.k5_m >= 5 and DIV == 1 and math.comb(args.k5_m, 4) < 2**32:
         line["k5"] = k5_run(args.k5_m, args.k5_disc, local_rank)
     if peaks:
@@ -699,6 +701,34 @@ def interesting_run(reps: int, device: int):
     return out
 
 
+def kgen_run(device: int):
+    """k = 4 and k = 5 with three classes per variable (divisions = 2: every
+    voxel of every tuple counted from the bit planes) on madelon-shaped data
+    with N = 2000: k = 4 on M = 120 variables and 10 discretisations, k = 5 on
+    M = 48 and 2, each timed with CUDA events after a one-discretisation
+    warm-up.  evals counts unordered tuples x discretisations."""
+    import torch
+    from paper_1811_00631_gb300 import mdfs, synth
+    dev = torch.device("cuda", device)
+    out = {"workload": f"madelon-shaped parity data N={N_OBJ}, c=3 (divisions 2)"}
+    stream = torch.cuda.current_stream(dev)
+    for k, m, nd in ((4, 120, 10), (5, 48, 2)):
+        ds = synth.madelon_like(N=N_OBJ, M=m, seed=2)
+        x = torch.from_numpy(ds.x).to(dev)
+        y = torch.from_numpy(ds.y).to(dev)
+        mdfs.max_ig(x, y, k, 2, 1, RANGE, XI, 1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mdfs.max_ig(x, y, k, 2, nd, RANGE, XI, 5)
+        b.record(stream)
+        b.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        evals = math.comb(m, k) * nd
+        out[f"k{k}"] = {"M": m, "discretizations": nd, "s": sec, "evals_per_s": evals / sec,
+                        "voxels_per_tuple": 3 ** k}
+    return out
+
+
 def k4_run(device: int):
     """One k = 4 scan of the bench data (2000 x 500, 30 discretisations, 2
     classes): C(500, 4) x 30 = 7.7e10 quadruple x discretisation evaluations,
@@ -880,6 +910,8 @@ def main():
     ap.add_argument("--small-disc", type=int, default=2, help="discretisations of the --small case")
     ap.add_argument("--serving-jobs", type=int, default=512, help="jobs of the serving-mix run (0: skip)")
     ap.add_argument("--k4", type=int, default=1, help="time one k = 4 scan of the bench data (0: skip)")
+    ap.add_argument("--kgen", type=int, default=1,
+                    help="time the k = 4 and k = 5 scans with three classes per variable (0: skip)")
     ap.add_argument("--k5-m", type=int, default=200,
                     help="variables of the timed one-discretisation k = 5 scan (0: skip; 500 = the "
                          "madelon-shaped 5D case, about 19 s per discretisation)")
@@ -907,6 +939,7 @@ def main():
         args.serving_jobs = 0
         args.select_reps = 0
         args.interesting_reps = 0
+        args.kgen = 0
         args.k4 = 0
         args.k5_m = 0
     world = int(os.environ.get("WORLD_SIZE", "1"))

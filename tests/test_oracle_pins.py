@@ -298,6 +298,22 @@ def test_null_scale_k5_c2():
     assert abs(vals.mean() - df) < 3 * math.sqrt(2 * df / reps)
 
 
+def test_null_scale_k4_c3():
+    """k = 4, c = 3: 2 IG of a null single tuple has mean df = (c-1) c^3 = 54
+    (section "Theory").  The chi^2 law is asymptotic: with 162 cells the mean
+    exceeds df by O(cells / N) (about 4 % at N = 8000), so N is large here."""
+    rng = np.random.default_rng(16)
+    N, c, reps = 40000, 3, 300
+    vals = []
+    for r in range(reps):
+        y = (rng.random(N) < 0.5).astype(np.uint8)
+        codes = rng.integers(0, c, (1, 4, N)).astype(np.uint8)
+        vals.append(2 * oracle.ig_one(codes, y, c, 1e-9, 0, 0, [1, 2, 3]))
+    df = (c - 1) * c ** 3
+    vals = np.array(vals)
+    assert abs(vals.mean() - df) < 3 * math.sqrt(2 * df / reps)
+
+
 def test_null_scale_k2_c3():
     rng = np.random.default_rng(13)
     N, c, reps = 5000, 3, 600
