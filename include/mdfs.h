@@ -97,7 +97,8 @@ int mdfs_discretize(const mdfs_data* data, int divisions, int discretizations, d
  *     f(t) = t ln t,  b^d = pc_xi * N^d / min(N^0, N^1),
  * summed over all c^|S| voxels v, and IG(i | S) = SH(S) - SH(S + {i}).
  *
- * k:          1 .. 5 (k = 4, 5: divisions = 1).
+ * k:          1 .. 5 (D M^3 < 2^32 at k = 4; C(M,4) < 2^32 at k = 5, and with
+ *             divisions 2 or 3 also D C(M,4) < 2^32).
  * pc_xi:      the pseudocount parameter xi, 0 < pc_xi < 1.
  * ig:         [M] float, the maximum per variable (may be slightly negative
  *             when the pseudocounts dominate).
@@ -251,8 +252,8 @@ int mdfs_p_adjust(const double* p, int m, int method, double* adjusted, void* st
  * beside the max scan and the selection pipeline): every (variable v,
  * partner set S) with |S| = k - 1, v not in S, whose IG(v | S) maximised
  * over the discretisations reaches ig_threshold (nats).  Same data, k,
- * divisions, discretizations, range, pc_xi and seed as mdfs_max_ig (k = 1..5;
- * k = 4, 5 with divisions = 1); the scan runs on the popcount kernels.
+ * divisions, discretizations, range, pc_xi and seed as mdfs_max_ig (k = 1..5,
+ * the same limits); every scan kernel emits the qualifying roles as it goes.
  *
  * Records are sorted by (v, S) ascending: var [n], tuples [n][k-1] (S
  * ascending; NULL allowed for k = 1), ig [n] float, best_disc [n] (the lowest
