@@ -4,7 +4,8 @@
 // mdfs_k5.cu) that read lower-order tables; here every voxel of a tuple is
 // counted directly from the class-sorted bit planes.
 //
-// One warp per tuple.  The samples are visited in chunks of 32 words (one word
+// One warp per tuple (k = 4: two tuples that differ in the last variable at
+// a time, for independent warp reductions).  The samples are visited in chunks of 32 words (one word
 // of 32 samples per lane), class 0 first, then class 1, so a chunk holds one
 // class.  A lane ANDs its word of the variables' bin planes (bin 0 is the
 // complement of bins 1 .. c-1 among the valid samples) along an unrolled tree
@@ -137,6 +138,63 @@ __device__ __forceinline__ void count_voxels(const uint32_t* __restrict__ pbase,
     }
 }
 
+// The voxel counts of two tuples that differ only in the last variable (v[K-1]
+// and e2), interleaved for independent warp reductions.
+template <int K, int C>
+__device__ __forceinline__ void count_voxels2(const uint32_t* __restrict__ pbase, const PlaneGeom& g, const int* v,
+                                              int e2, int lane, int (&n0)[(ipow(C, K) + 31) / 32],
+                                              int (&n1)[(ipow(C, K) + 31) / 32], int (&m0)[(ipow(C, K) + 31) / 32],
+                                              int (&m1)[(ipow(C, K) + 31) / 32]) {
+    constexpr int V = ipow(C, K), NP = ipow(C, K - 2);
+#pragma unroll
+    for (int t = 0; t < (V + 31) / 32; ++t) n0[t] = n1[t] = m0[t] = m1[t] = 0;
+    for (int cls = 0; cls < 2; ++cls) {
+        const int wbeg = cls ? g.W0 : 0, wend = cls ? g.W : g.W0;
+        for (int w0 = wbeg; w0 < wend; w0 += 32) {
+            const int w = w0 + lane;
+            const int ww = w < wend ? w : g.Ws;
+            uint32_t pl[K][C];
+            load_bins<K, C>(pbase, g, v, ww, pl);
+            uint32_t q[1][C];
+            load_bins<1, C>(pbase, g, &e2, ww, q);
+            uint32_t pre[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                uint32_t x = 0xffffffffu;
+                int r = p;
+#pragma unroll
+                for (int i = K - 3; i >= 0; --i) {
+                    x &= pl[i][r % C];
+                    r /= C;
+                }
+                pre[p] = x;
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+#pragma unroll
+                for (int b1 = 0; b1 < C; ++b1) {
+                    const uint32_t x = pre[p] & pl[K - 2][b1];
+#pragma unroll
+                    for (int b = 0; b < C; ++b) {
+                        const int vx = (p * C + b1) * C + b;
+                        const int sa = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(x & pl[K - 1][b]));
+                        const int sb = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(x & q[0][b]));
+                        if (lane == (vx & 31)) {
+                            if (cls) {
+                                n1[vx >> 5] += sa;
+                                m1[vx >> 5] += sb;
+                            } else {
+                                n0[vx >> 5] += sa;
+                                m0[vx >> 5] += sb;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // IG of every role of the tuple v[0] < .. < v[K-1] (int64 fixed point), from
 // its voxel counts at the owner lanes; scnt: this warp's c^K shared words.
 template <int K, int C>
@@ -179,7 +237,7 @@ __device__ __forceinline__ void tuple_ig(const long long* __restrict__ tab, int 
 }
 
 template <int K, int C>
-__global__ void __launch_bounds__(32 * kWarps, 1) kgen_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M,
+__global__ void __launch_bounds__(32 * kWarps, (K == 4 && C == 3) ? 3 : 1) kgen_kernel(const uint32_t* __restrict__ planes, PlaneGeom g, int M,
                                                            int d0, const int2* __restrict__ items,
                                                            const long long* __restrict__ tab,
                                                            unsigned long long* __restrict__ keys, EmitTable emit) {
@@ -204,12 +262,8 @@ __global__ void __launch_bounds__(32 * kWarps, 1) kgen_kernel(const uint32_t* __
                 if (kfix[i]) atomicMax(keys + v[i], kfix[i]);
         }
     };
-    auto visit = [&](int* v) {
-        int n0[(V + 31) / 32], n1[(V + 31) / 32];
-        count_voxels<K, C>(pbase, g, v, lane, n0, n1);
-        long long ig[K];
-        tuple_ig<K, C>(tab, np1, lane, n0, n1, scnt, ig);
-        if (lane != 0) return;
+    // keys and emission of the roles of tuple v (lane 0)
+    auto keys_of = [&](const int* v, const long long (&ig)[K]) {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             int p[K - 1];
@@ -234,6 +288,26 @@ __global__ void __launch_bounds__(32 * kWarps, 1) kgen_kernel(const uint32_t* __
             }
         }
     };
+    // one tuple
+    auto visit = [&](const int* v) {
+        int n0[(V + 31) / 32], n1[(V + 31) / 32];
+        count_voxels<K, C>(pbase, g, v, lane, n0, n1);
+        long long ig[K];
+        tuple_ig<K, C>(tab, np1, lane, n0, n1, scnt, ig);
+        if (lane == 0) keys_of(v, ig);
+    };
+    // the tuples v and v with its last variable replaced by v[K-1] + 1, counted together (k = 4)
+    auto visit2 = [&](int* v) {
+        int n0[(V + 31) / 32], n1[(V + 31) / 32], m0[(V + 31) / 32], m1[(V + 31) / 32];
+        count_voxels2<K, C>(pbase, g, v, v[K - 1] + 1, lane, n0, n1, m0, m1);
+        long long ig[K];
+        tuple_ig<K, C>(tab, np1, lane, n0, n1, scnt, ig);
+        if (lane == 0) keys_of(v, ig);
+        tuple_ig<K, C>(tab, np1, lane, m0, m1, scnt, ig);
+        ++v[K - 1];
+        if (lane == 0) keys_of(v, ig);
+        --v[K - 1];
+    };
 
     int v[K];
     v[0] = a;
@@ -243,7 +317,12 @@ __global__ void __launch_bounds__(32 * kWarps, 1) kgen_kernel(const uint32_t* __
             v[2] = c;
 #pragma unroll
             for (int i = 0; i < K - 1; ++i) kfix[i] = 0ull;
-            for (int e = c + 1; e < M; ++e) {
+            int e = c + 1;
+            for (; e + 1 < M; e += 2) {
+                v[3] = e;
+                visit2(v);
+            }
+            if (e < M) {
                 v[3] = e;
                 visit(v);
             }
@@ -258,6 +337,8 @@ __global__ void __launch_bounds__(32 * kWarps, 1) kgen_kernel(const uint32_t* __
                 v[3] = e;
 #pragma unroll
                 for (int i = 0; i < K - 1; ++i) kfix[i] = 0ull;
+                // one tuple at a time: two would need more registers than a
+                // useful occupancy allows (measured slower)
                 for (int f = e + 1; f < M; ++f) {
                     v[4] = f;
                     visit(v);
