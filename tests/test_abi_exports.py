@@ -78,8 +78,9 @@ def test_argument_errors_need_no_gpu(lib):
 
 
 def test_k5_limits_need_no_gpu(lib):
-    """k = 5 argument limits: two classes per variable, C(M, 4) < 2^32, and for
-    the single-word keys of a shard also discretizations * C(M, 4) < 2^32."""
+    """k = 5 argument limits: two to four classes per variable, C(M, 4) < 2^32,
+    and for the single-word keys of a shard (and of every scan with three or
+    four classes) also discretizations * C(M, 4) < 2^32."""
     import ctypes
     from paper_1811_00631_gb300 import mdfs
     import numpy as np
@@ -95,7 +96,8 @@ def test_k5_limits_need_no_gpu(lib):
         return lib.mdfs_max_ig(ctypes.byref(d), 5, divisions, D, 0.0, 0.25, 1, ctypes.c_void_p(out.ctypes.data),
                                None, None, None)
 
-    assert call(20, 2, 1) == -1 and b"two classes" in lib.mdfs_last_error()
+    assert call(20, 4, 1) == -1 and b"divisions" in lib.mdfs_last_error()  # five classes
+    assert call(200, 2, 67) == -1 and b"2^32" in lib.mdfs_last_error()  # three classes: 67 C(200, 4) > 2^32
     assert call(569, 1, 1) == -1 and b"C(M, 4)" in lib.mdfs_last_error()  # C(569, 4) > 2^32
     assert call(500, 1, 2, shard=True) == -1 and b"shard" in lib.mdfs_last_error()  # 2 C(500, 4) > 2^32
     assert call(4, 1, 1) == -1 and b"smaller than k" in lib.mdfs_last_error()
