@@ -404,7 +404,7 @@ def test_k4_errors(cuda):
     x = np.random.default_rng(0).standard_normal((6, 50)).astype(np.float32)
     y = (np.arange(50) % 2).astype(np.uint8)
     with pytest.raises(mdfs.MdfsError):
-        mdfs.max_ig(x, y, 4, 2, 1)  # three classes: not supported at k = 4
+        mdfs.max_ig(x, y, 4, 4, 1)  # five classes: more than any scan supports
     xl = np.random.default_rng(1).standard_normal((1700, 8)).astype(np.float32)
     yl = (np.arange(8) % 2).astype(np.uint8)
     with pytest.raises(mdfs.MdfsError):
