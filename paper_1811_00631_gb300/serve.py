@@ -75,7 +75,8 @@ def job_device_parts(M: int, N: int, k: int, divisions: int, discretizations: in
     "onehot" (the tensor-core operand of k = 2 with c <= 3 and k = 3 with
     c = 2), "k3tc" (the relabelled operand and the pair records of the k = 3
     tensor path), "pairs" (pair tables of the generic k = 3 path) and "tables"
-    (pair, triple and quadruple tables of k = 4, 5).  Tables are processed in
+    (pair, triple and quadruple tables of k = 4, 5 with two classes; the work
+    items of k = 4, 5 with three or four).  Tables are processed in
     chunks of discretisations that fit a 4 GB budget (at least one
     discretisation per chunk)."""
     c = divisions + 1
@@ -97,6 +98,8 @@ def job_device_parts(M: int, N: int, k: int, divisions: int, discretizations: in
         parts["k3tc"] = D * M * kp + D * M * 16 + chunked(M * M * 8)
     elif k == 3:
         parts["pairs"] = chunked(M * M * (8 + P * P * 8))
+    elif k in (4, 5) and c != 2:
+        parts["tables"] = M * M * 8 + (1 << 20)  # the generic scan keeps only its pair work items
     elif k in (4, 5):
         per_disc = M * M * 16 + math.comb(M, 3) * 12
         if k == 5:
