@@ -75,3 +75,19 @@ def test_kgen_interesting_tuples(cuda, k, div, M, N, D):
     ref = [r for r in allrec if r[2] >= thr]
     got = mdfs.interesting_tuples(x, y, k, div, D, 0.5, 0.25, 31, thr, capacity=4096)
     _compare(codes, y, c, k, 0.25, thr, got, ref)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_kgen_shards_merge_to_the_scan(cuda, k):
+    """Three shards of the pair items, their keys merged by max, decode to the
+    unsharded scan bit for bit."""
+    from paper_1811_00631_gb300 import mdfs
+    M, N, D = (11, 300, 2) if k == 4 else (8, 250, 1)
+    x, y = _data(M, N, 5 + k, k)
+    full = _gpu_max_ig(cuda, x, y, k, 2, D, 0.5, 0.25, 9, host=True)
+    keys = np.zeros(M, dtype=np.uint64)
+    for s in range(3):
+        keys = np.maximum(keys, mdfs.max_ig_shard(x, y, k, 2, D, 0.5, 0.25, 9, shard=s, n_shards=3))
+    got = mdfs.decode_keys(keys, k)
+    assert np.array_equal(np.asarray(got[0], dtype=np.float64), full[0])
+    assert np.array_equal(np.asarray(got[1]), full[1]) and np.array_equal(np.asarray(got[2]), full[2])
