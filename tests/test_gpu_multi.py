@@ -33,7 +33,7 @@ def _same(a, b, what):
                                           ((3, 1), 1, 600, 90, 2),          # fused without k = 2
                                           ((2, 3), 2, 600, 80, 2),          # three classes: one after another
                                           ((4, 2, 1), 1, 300, 24, 2),       # k = 4 beside k = 1, 2
-                                          ((3, 4), 2, 300, 12, 2)])         # three classes, k = 4 generic
+                                          ((3, 4), 2, 300, 20, 2)])         # three classes, k = 4 generic
 def test_multi_equals_single_calls(cuda, ks, div, N, M, D):
     from paper_1811_00631_gb300 import mdfs, synth
     torch = cuda
