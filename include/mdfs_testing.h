@@ -60,6 +60,17 @@ int mdfs_testing_k3_wait_fault(int withhold_kb, long long wait_ns);
  */
 int mdfs_testing_exact(void);
 
+/*
+ * Host only (no CUDA call): the order in which the k = 3 tensor-core scan of
+ * M variables over nd discretisations hands out its tiles (tile t = item
+ * t % n_items of discretisation t / n_items, items (b, a-tile, e-group) in
+ * the scan's order), by descending modelled epilogue cost.  Writes up to cap
+ * tile indices to order (host memory) and returns the number of tiles, or a
+ * negative MDFS error for M outside [3, 65535], nd outside [1, 1024] or a NULL
+ * order with cap > 0.
+ */
+int mdfs_testing_k3_claim_order(int M, int nd, int32_t* order, int cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1773,6 +1773,19 @@ int mdfs_testing_exact(void) {
     return MDFS_OK;
 }
 
+int mdfs_testing_k3_claim_order(int M, int nd, int32_t* order, int cap) {
+    g_err.clear();
+    if (M < 3 || M > 65535) return fail(MDFS_EINVAL, "M = %d outside [3, 65535]", M);
+    if (nd < 1 || nd > kMaxD) return fail(MDFS_EINVAL, "nd = %d outside [1, %d]", nd, kMaxD);
+    if (cap > 0 && !order) return fail(MDFS_EINVAL, "order is NULL");
+    std::vector<int2> items;
+    build_k3tc_items(M, items);
+    std::vector<int> out;
+    build_k3tc_order(M, items.data(), (int)items.size(), nd, out);
+    for (int i = 0; i < cap && i < (int)out.size(); ++i) order[i] = out[i];
+    return (int)out.size();
+}
+
 int mdfs_testing_k3_wait_fault(int withhold_kb, long long wait_ns) {
     g_err.clear();
     if (withhold_kb < -1) return fail(MDFS_EINVAL, "withhold_kb = %d < -1", withhold_kb);

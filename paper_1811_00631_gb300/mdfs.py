@@ -36,7 +36,7 @@ EXPORTED = ("mdfs_discretize", "mdfs_max_ig", "mdfs_max_ig_multi", "mdfs_ig_lim"
             "mdfs_max_ig_noalloc", "mdfs_max_ig_batch", "mdfs_max_ig_shard", "mdfs_keys_decode",
             "mdfs_contrast", "mdfs_p_adjust", "mdfs_select", "mdfs_interesting_tuples",
             "mdfs_release_stream", "mdfs_bench_mma_f8", "mdfs_bench_smem_lookup", "mdfs_testing_counts", "mdfs_testing_k3_wait_fault",
-            "mdfs_testing_exact")
+            "mdfs_testing_exact", "mdfs_testing_k3_claim_order")
 
 # p-value adjustment methods (MDFS_ADJUST_* of include/mdfs.h)
 P_ADJUST = {"none": 0, "bonferroni": 1, "holm": 2, "hochberg": 3, "BH": 4, "BY": 5}
@@ -128,6 +128,8 @@ def load(path: str = LIB_PATH):
         lib.mdfs_testing_counts.restype = ctypes.c_int
         lib.mdfs_testing_k3_wait_fault.argtypes = [ctypes.c_int, ctypes.c_longlong]
         lib.mdfs_testing_k3_wait_fault.restype = ctypes.c_int
+        lib.mdfs_testing_k3_claim_order.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
+        lib.mdfs_testing_k3_claim_order.restype = ctypes.c_int
         lib.mdfs_testing_exact.argtypes = []
         lib.mdfs_testing_exact.restype = ctypes.c_int
         _lib = lib
